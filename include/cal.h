@@ -1,0 +1,207 @@
+/*
+ * cal.h — C ABI of the GB300 (sm_103a) Calderón-preconditioned PMCHWT library.
+ *
+ * Method: Kleanthous, Betcke, Hewett, Escapil-Inchauspé, Jerez-Hanckes,
+ * Baran, "Accelerated Calderón preconditioning for Maxwell transmission
+ * problems", arXiv 2008.04772. Section and equation names below refer to it.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Return value: 0 on success, a negative CAL_E* code on failure; the
+ *   calling thread's message is then available from cal_last_error().
+ *   No entry point aborts the process or traps the device.
+ * - Ownership: every input array is copied at the call; the caller may free
+ *   it on return. Handles (cal_ctx, cal_mesh, cal_space, cal_op,
+ *   cal_solution, cal_queue) are owned by the library and freed by the
+ *   matching *_destroy, which accepts NULL. Objects created from a context
+ *   must be destroyed before the context.
+ * - Output buffers are allocated by the caller. Where an argument is marked
+ *   "host or device", the library inspects the pointer and copies accordingly.
+ * - Complex numbers are interleaved (re, im); complex64 = 2 x float32,
+ *   complex128 = 2 x float64. Dense matrices are row-major.
+ * - Time convention e^{-i omega t}; relative permittivity/permeability,
+ *   exterior medium eps = mu = 1 (Section 2).
+ * - Basis numbering: primal edges sorted by (scatterer id, lower vertex id,
+ *   higher vertex id); RWG_e and BC_e share the index e (Section 3.2).
+ * - PMCHWT unknowns are component-major: x = [c_0..c_{N-1}, d_0..d_{N-1}],
+ *   u_1 = sum c_e RWG_e = gamma_D E, u_2 = sum d_e RWG_e = (k/mu) gamma_N E
+ *   (eq. boundary_conditions_traces), N = number of primal edges.
+ */
+#ifndef CAL_H
+#define CAL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- error codes --------------------------------------------------------- */
+#define CAL_OK 0
+#define CAL_EINVAL (-1)    /* bad argument (NULL, size, NaN, unsupported option) */
+#define CAL_EMESH (-2)     /* not a closed, consistently oriented 2-manifold, or
+                              scatterers share vertices */
+#define CAL_ENOMEM (-3)    /* device/host allocation or HBM admission refused;
+                              nothing is left partially allocated */
+#define CAL_ENOTCONV (-4)  /* GMRES reached maxit; the solution is still returned */
+#define CAL_ETIMEOUT (-5)  /* a bounded wait gave up (queue) */
+#define CAL_ECUDA (-6)     /* a CUDA runtime call failed */
+
+/* ---- enumerations -------------------------------------------------------- */
+#define CAL_RWG 1          /* Rao–Wilton–Glisson on the primal mesh (Section 3.2) */
+#define CAL_BC 2           /* Buffa–Christiansen on the barycentric refinement    */
+
+#define CAL_OP_S 1         /* electric operator S = gamma_D E (Section 2)          */
+#define CAL_OP_C 2         /* magnetic operator C = gamma_D H (Section 2)          */
+
+#define CAL_FP64 1         /* all assembly and storage in float64 (complex128)    */
+#define CAL_FP32 2         /* regular pairs in float32, singular pairs in float64,
+                              storage complex64 ("FP32 bulk")                      */
+
+#define CAL_DENSE 1
+#define CAL_CSR 2
+
+/* preconditioners of Section 3.1 (P = A is available for one scatterer, where
+   it equals D) */
+#define CAL_PRECOND_NONE 0
+#define CAL_PRECOND_D 1
+#define CAL_PRECOND_DE 2
+#define CAL_PRECOND_DI 3
+#define CAL_PRECOND_SE 4
+#define CAL_PRECOND_SI 5
+
+/* ---- opaque handles ------------------------------------------------------ */
+typedef struct cal_ctx cal_ctx;
+typedef struct cal_mesh cal_mesh;
+typedef struct cal_space cal_space;
+typedef struct cal_op cal_op;
+typedef struct cal_solution cal_solution;
+
+/* ---- context ------------------------------------------------------------- */
+/* Bind a context to CUDA device `device` and create its stream. */
+int cal_init(cal_ctx** out, int device);
+void cal_ctx_destroy(cal_ctx* ctx);
+/* Message of the last failed call on this thread ("" if none). */
+const char* cal_last_error(void);
+/* The context's CUDA stream (cudaStream_t), for callers that order their own work. */
+void* cal_ctx_stream(cal_ctx* ctx);
+
+/* ---- mesh (Section 2: M disjoint closed surfaces Gamma_m) --------------- */
+/* verts [nv][3] float64; tris [nt][3] int32 vertex ids, counter-clockwise seen
+   from outside (normal into the exterior, Section 2); domain [nt] int32
+   scatterer ids 0..M-1, or NULL for M = 1. Validates that every edge is used
+   exactly twice in opposite directions and that scatterers share no vertex
+   (CAL_EMESH otherwise). */
+int cal_mesh_create(cal_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris,
+                    int64_t nt, const int32_t* domain, cal_mesh** out);
+void cal_mesh_destroy(cal_mesh* mesh);
+
+typedef struct {
+  int64_t n_vertices, n_triangles, n_edges, n_scatterers;
+  double h;                 /* maximum primal edge length */
+  int32_t max_valence;      /* maximum number of edges at a vertex */
+} cal_mesh_info;
+int cal_mesh_get_info(const cal_mesh* mesh, cal_mesh_info* info);
+
+/* ---- spaces (Section 3.2, eq. RWG_discretisation1) ----------------------- */
+/* kind CAL_RWG: RWG_e = +l_e f on T+ (the triangle whose counter-clockwise
+   cycle runs lower -> higher vertex along e) and -l_e f on T-, with
+   f(x) = (x - p)/(2|T|), p the vertex opposite e.
+   kind CAL_BC: Buffa–Christiansen function of edge e on the barycentric
+   refinement: flux l_e crosses the dual edge of e from the dual cell of the
+   lower vertex to that of the higher one; divergence integral +-l_e/(2N_v)
+   on each of the 2N_v small triangles of a cell; circulation fixed by mirror
+   symmetry about the half-edge, which carries zero flux. */
+int cal_space_create(cal_mesh* mesh, int kind, cal_space** out);
+void cal_space_destroy(cal_space* space);
+
+/* ---- Galerkin assembly (Sections 2, 3.3) --------------------------------- */
+/* Assembles <S phi_j, phi_i> and/or <C phi_j, phi_i> (op_mask = CAL_OP_S |
+   CAL_OP_C) at wavenumber k = k_re + i k_im over test x trial, both RWG or
+   both BC on the same mesh, with the pairing <a,b> = int a.(n x b)
+   (eq. dualpairingGammam):
+     S_ij = -ik II G phi_i.phi_j + (i/k) II G div phi_i div phi_j,
+     C_ij =     II grad_x G . (phi_i(x) x phi_j(y)),  G = e^{ikr}/(4 pi r).
+   scatterer = -1 assembles the union surface (all pairs, "exterior" use);
+   scatterer = m restricts test and trial to Gamma_m (interior use).
+   near_cutoff: INFINITY = dense; otherwise entry (i,j) is kept iff the
+   bounding boxes of the supports are <= near_cutoff apart (eq. nf_condition
+   read at entry level) and the result is CSR (BC spaces only).
+   q_regular: points per triangle of the regular tensor rule, 6 (degree 4,
+   36 evaluations per pair) or 1 (centroid); q_singular: Gauss–Legendre
+   points per dimension of the Sauter–Schwab rules, 1..16 (4 gives the
+   paper's 512/1280/1536 evaluations). precision: CAL_FP64 or CAL_FP32. */
+int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space* test,
+                 cal_space* trial, int scatterer, double near_cutoff, int q_regular,
+                 int q_singular, int precision, cal_op** out);
+void cal_op_destroy(cal_op* op);
+
+typedef struct {
+  int64_t rows, cols, nnz;  /* nnz = rows*cols for dense */
+  int32_t format;           /* CAL_DENSE or CAL_CSR */
+  int32_t precision;        /* CAL_FP64 (complex128 values) or CAL_FP32 (complex64) */
+  int32_t op_mask;
+  int32_t row_offset;       /* first basis index of the block (scatterer restriction) */
+} cal_op_info;
+int cal_op_get_info(const cal_op* op, cal_op_info* info);
+
+/* Copies operator `which` (CAL_OP_S or CAL_OP_C) to dst (host or device):
+   dense: rows*cols complex values of the op's precision; CSR: nnz values, and
+   when row_ptr/col_idx are non-NULL also rows+1 and nnz int64 indices (host). */
+int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int64_t* col_idx);
+
+/* y = X x for X = operator `which`; x [nrhs][cols], y [nrhs][rows] complex of
+   the op's precision, both device pointers; enqueued on `stream`
+   (cudaStream_t, NULL = the context stream). */
+int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
+
+/* Gram matrix G_ij = <BC_j, RWG_i> = int BC_j . (n x RWG_i) (eqs. MassA,
+   MassP: M_A = diag(G, G), M_P = diag(-G^T, -G^T) in the unknown ordering above)
+   written densely to dst_host [N][N] float64. For tests of small meshes. */
+int cal_gram_export(cal_space* rwg, cal_space* bc, double* dst_host);
+
+/* ---- PMCHWT solve (eqs. PMCHWT_multiple_scatterers, GalA-MassP) --------- */
+typedef struct {
+  int32_t precond;          /* CAL_PRECOND_*                                   */
+  int32_t precision;        /* CAL_FP64 or CAL_FP32 (FP32 bulk)                */
+  int32_t q_regular_A, q_singular_A;   /* A's rules (6, 4 = paper default)     */
+  int32_t q_regular_P, q_singular_P;   /* P's rules (bi-parametric: 1, 1)      */
+  double near_cutoff_P;     /* chi_P in units of h; INFINITY = dense P          */
+  double tol;               /* GMRES relative preconditioned residual           */
+  int32_t restart;          /* GMRES restart (paper: 200)                       */
+  int32_t maxit;            /* iteration cap                                    */
+  int32_t refine;           /* FP32 path: outer FP64 iterative refinement steps */
+  int32_t rhs_mode;         /* 0 = total traces (A^e + A^i) u = u^inc           */
+} cal_solve_opts;
+void cal_solve_opts_default(cal_solve_opts* opts);
+
+typedef struct {
+  int32_t iterations;       /* GMRES iterations (sum over refinement steps)     */
+  int32_t converged;
+  int64_t matvecs;          /* boundary-operator applications, Table tab:matvecs */
+  double residual;          /* final relative preconditioned residual           */
+  double t_setup, t_assemble_A, t_assemble_P, t_solve;  /* seconds              */
+  int64_t bytes_A, bytes_P; /* device bytes of the stored operators             */
+  int64_t n_unknowns;       /* 2N                                               */
+} cal_solve_info;
+
+/* Solves for nrhs incident plane waves inc [nrhs][6] = (direction, polarisation),
+   E^inc = p e^{i k_ext d.x}; eps_r, mu_r [M][2] (re, im) per scatterer (mu_r may
+   be NULL for 1). The returned solution keeps the total boundary traces on the
+   device. Returns CAL_ENOTCONV (with a usable solution) if maxit was reached. */
+int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r,
+                     const double* mu_r, const double* inc, int64_t nrhs,
+                     const cal_solve_opts* opts, cal_solution** out);
+int cal_solution_get_info(const cal_solution* sol, cal_solve_info* info);
+/* Coefficients x [nrhs][2N] complex128 to host memory (component-major, see top). */
+int cal_solution_coefficients(const cal_solution* sol, double* dst_host);
+/* Far-field pattern E_inf(x_hat), E^s ~ E_inf e^{ik r}/r, for unit directions
+   dirs [ndir][3]: out [nrhs][ndir][3] complex128 (host). */
+int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, double* out);
+void cal_solution_destroy(cal_solution* sol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CAL_H */

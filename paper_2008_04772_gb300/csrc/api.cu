@@ -1,0 +1,862 @@
+// C ABI of the library (include/cal.h) and the PMCHWT solve pipeline.
+//
+// arXiv 2008.04772: assembly of A on RWG x RWG and of P on BC x BC
+// (eq. RWG_discretisation1), identical blocks assembled once (Section 3.2:
+// S and C per wavenumber serve both block rows), the strong form
+// M_P^-1 P M_A^-1 A solved by restarted GMRES (Section 4), the incident traces
+// and the far field of the exterior representation.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+#include "solve.h"
+
+namespace cal {
+const char* last_error();
+}
+
+using namespace cal;
+
+namespace {
+
+double now() {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+int is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+// vertices of one scatterer (or all) that own a non-empty dual cell
+std::vector<int> cell_list(const Space& s, int scat) {
+  const Mesh& m = *s.mesh;
+  std::vector<char> used(m.nv, 0);
+  const int64_t t0 = scat < 0 ? 0 : m.tri_off[scat], t1 = scat < 0 ? m.nt : m.tri_off[scat + 1];
+  for (int64_t t = t0; t < t1; ++t)
+    for (int a = 0; a < 3; ++a) used[m.T[3 * t + a]] = 1;
+  std::vector<int> out;
+  for (int64_t v = 0; v < m.nv; ++v)
+    if (used[v]) out.push_back((int)v);
+  return out;
+}
+
+// Assemble S and/or C of one block (scat = -1: union; else scatterer scat).
+int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, int scat, double chi,
+                   int nreg, int nsing, int precision, std::unique_ptr<Op>& out) {
+  const Mesh& m = *sp.mesh;
+  if (scat >= m.M) return fail(CAL_EINVAL, "assemble: scatterer %d out of range", scat);
+  if (!(want & 3)) return fail(CAL_EINVAL, "assemble: op_mask must contain CAL_OP_S or CAL_OP_C");
+  if (precision != CAL_FP32 && precision != CAL_FP64) return fail(CAL_EINVAL, "assemble: bad precision");
+  if (!std::isfinite(kr) || !std::isfinite(ki) || (kr == 0 && ki == 0))
+    return fail(CAL_EINVAL, "assemble: wavenumber must be finite and non-zero");
+  int rc = set_quadrature_tables(nreg, nsing);
+  if (rc) return rc;
+  auto op = std::make_unique<Op>();
+  op->ctx = &ctx;
+  op->op_mask = want;
+  op->precision = precision;
+  op->row_offset = scat < 0 ? 0 : m.edge_off[scat];
+  op->rows = op->cols = (scat < 0 ? m.ne : m.edge_off[scat + 1] - m.edge_off[scat]);
+  const bool dense = std::isinf(chi);
+  op->format = dense ? CAL_DENSE : CAL_CSR;
+  if (!dense) {
+    if (!(chi >= 0)) return fail(CAL_EINVAL, "assemble: near_cutoff must be >= 0 or INFINITY");
+    near_pattern(sp, scat, chi, op->h_rowptr, op->h_col);
+    op->nnz = op->h_rowptr.back();
+  } else {
+    op->nnz = op->rows * op->cols;
+  }
+  const size_t esz = precision == CAL_FP32 ? 8 : 16;
+  const size_t bytes = (size_t)op->nnz * esz;
+  cudaStream_t st = ctx.stream;
+  if (want & 1) {
+    if (cudaMalloc(&op->d_S, std::max<size_t>(bytes, 16)) != cudaSuccess)
+      return fail(CAL_ENOMEM, "assemble: cannot allocate %zu bytes for S", bytes);
+    CAL_TRY_CUDA(cudaMemsetAsync(op->d_S, 0, bytes, st));
+  }
+  if (want & 2) {
+    if (cudaMalloc(&op->d_C, std::max<size_t>(bytes, 16)) != cudaSuccess)
+      return fail(CAL_ENOMEM, "assemble: cannot allocate %zu bytes for C", bytes);
+    CAL_TRY_CUDA(cudaMemsetAsync(op->d_C, 0, bytes, st));
+  }
+  if (!dense) {
+    CAL_TRY_CUDA(cudaMalloc((void**)&op->d_rowptr, op->h_rowptr.size() * sizeof(int64_t)));
+    CAL_TRY_CUDA(cudaMalloc((void**)&op->d_col, std::max<size_t>(op->h_col.size(), 1) * sizeof(int)));
+    CAL_TRY_CUDA(cudaMemcpyAsync(op->d_rowptr, op->h_rowptr.data(), op->h_rowptr.size() * sizeof(int64_t),
+                                 cudaMemcpyHostToDevice, st));
+    if (!op->h_col.empty())
+      CAL_TRY_CUDA(cudaMemcpyAsync(op->d_col, op->h_col.data(), op->h_col.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, st));
+  }
+  AssembleArgs a{};
+  a.sp = &sp;
+  a.scat = scat;
+  a.kr = kr;
+  a.ki = ki;
+  a.want = want;
+  a.nreg = nreg;
+  a.nsing = nsing;
+  a.precision = precision;
+  a.format = op->format;
+  a.row_off = op->row_offset;
+  a.ld = op->cols;
+  a.rowptr = op->d_rowptr;
+  a.col = op->d_col;
+  a.S = op->d_S;
+  a.C = op->d_C;
+  a.stream = st;
+  if (sp.kind == CAL_RWG) {
+    if ((rc = launch_rwg_regular(a))) return rc;
+  } else {
+    std::vector<int> cells = cell_list(sp, scat);
+    int max_cell = 0;
+    for (int v : cells) max_cell = std::max(max_cell, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
+    std::vector<int2> tiles;
+    if (!dense) {
+      const int64_t off = op->row_offset;
+      std::vector<int64_t> keys;
+      for (int64_t i = 0; i < op->rows; ++i)
+        for (int64_t q = op->h_rowptr[i]; q < op->h_rowptr[i + 1]; ++q) {
+          const int64_t j = op->h_col[q];
+          if (j < i) continue;
+          const int vi[2] = {m.e_lo[off + i], m.e_hi[off + i]};
+          const int vj[2] = {m.e_lo[off + j], m.e_hi[off + j]};
+          for (int x : vi)
+            for (int y : vj) keys.push_back(((int64_t)std::min(x, y) << 32) | (int64_t)std::max(x, y));
+        }
+      std::sort(keys.begin(), keys.end());
+      keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
+      tiles.resize(keys.size());
+      for (size_t q = 0; q < keys.size(); ++q) tiles[q] = make_int2((int)(keys[q] >> 32), (int)(keys[q] & 0xffffffff));
+    }
+    int* d_cells = nullptr;
+    int2* d_tiles = nullptr;
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&d_cells, std::max<size_t>(cells.size(), 1) * sizeof(int), st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(d_cells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    if (!dense && !tiles.empty()) {
+      CAL_TRY_CUDA(cudaMallocAsync((void**)&d_tiles, tiles.size() * sizeof(int2), st));
+      CAL_TRY_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    }
+    if (dense || !tiles.empty())
+      rc = launch_bc_regular_tiles(a, d_cells, (int64_t)cells.size(), dense ? nullptr : d_tiles,
+                                   (int64_t)tiles.size(), max_cell, ctx.n_sm);
+    // the tile list must outlive the kernel: free in stream order
+    cudaFreeAsync(d_cells, st);
+    if (d_tiles) cudaFreeAsync(d_tiles, st);
+    if (rc) return rc;
+  }
+  if ((rc = launch_singular(a))) return rc;
+  CAL_TRY_CUDA(cudaGetLastError());
+  out = std::move(op);
+  return CAL_OK;
+}
+
+std::complex<double> interior_k(double k_e, std::complex<double> eps, std::complex<double> mu) {
+  std::complex<double> km = k_e * std::sqrt(eps * mu);
+  if (km.imag() < 0) km = -km;
+  return km;
+}
+
+}  // namespace
+
+// =============================================================================
+// solution object
+// =============================================================================
+struct cal_solution {
+  Ctx* ctx = nullptr;
+  std::unique_ptr<Space> rwg;
+  double2* d_x = nullptr;  // [nrhs][2N]
+  int64_t nrhs = 0, ne = 0;
+  double k_e = 0.0, mu_e = 1.0;
+  cal_solve_info info{};
+  ~cal_solution() { cudaFree(d_x); }
+};
+
+namespace {
+
+struct Pmchwt {
+  Ctx* ctx;
+  Mesh* mesh;
+  int M;
+  int64_t N;  // basis count
+  double k_e;
+  std::vector<std::complex<double>> k_m, mu_m;
+  cal_solve_opts o;
+  std::unique_ptr<Space> rwg, bc;
+  std::unique_ptr<Op> A_ext;
+  std::vector<std::unique_ptr<Op>> A_int, P_ext, P_int;
+  // Gram
+  int64_t* d_grp = nullptr;
+  int* d_gcol = nullptr;
+  int64_t* d_grpT = nullptr;
+  int* d_gcolT = nullptr;
+  double* d_gval = nullptr;
+  double* d_gvalT = nullptr;
+  int64_t gnnz = 0;
+  std::unique_ptr<GramSolver<float>> gsA32, gsP32;
+  std::unique_ptr<GramSolver<double>> gsA64, gsP64;
+  // work vectors
+  void* t1 = nullptr;
+  void* t2 = nullptr;
+  int64_t matvecs = 0;
+  ~Pmchwt() {
+    cudaFree(d_grp); cudaFree(d_gcol); cudaFree(d_grpT); cudaFree(d_gcolT);
+    cudaFree(d_gval); cudaFree(d_gvalT); cudaFree(t1); cudaFree(t2);
+  }
+
+  BlockRef ref(const Op& op, bool withS = true, bool withC = true) const {
+    BlockRef b;
+    b.S = withS ? op.d_S : nullptr;
+    b.C = withC ? op.d_C : nullptr;
+    b.rows = op.rows;
+    b.cols = op.cols;
+    b.row_off = b.col_off = op.row_offset;
+    b.precision = op.precision;
+    b.rowptr = op.format == CAL_CSR ? op.d_rowptr : nullptr;
+    b.col = op.format == CAL_CSR ? op.d_col : nullptr;
+    return b;
+  }
+
+  // y = A x (y overwritten); vec_prec = precision of x, y
+  int apply_A(const void* x, void* y, int vec_prec) {
+    cudaStream_t st = ctx->stream;
+    int rc = zero_vec(y, vec_prec, 2 * N, st);
+    if (rc) return rc;
+    const std::complex<double> a = 1.0 / k_e, b = -k_e;  // mu_e = 1
+    if ((rc = pair_apply(ref(*A_ext), vec_prec, x, y, N, a.real(), a.imag(), b.real(), b.imag(), st))) return rc;
+    for (int m = 0; m < M; ++m) {
+      const std::complex<double> am = mu_m[m] / k_m[m], bm = -k_m[m] / mu_m[m];
+      if ((rc = pair_apply(ref(*A_int[m]), vec_prec, x, y, N, am.real(), am.imag(), bm.real(), bm.imag(), st)))
+        return rc;
+    }
+    matvecs += 4LL * M * M + 4LL * M;
+    return CAL_OK;
+  }
+
+  // y = P x on BC coefficients (y overwritten)
+  int apply_P(const void* x, void* y, int vec_prec) {
+    cudaStream_t st = ctx->stream;
+    int rc = zero_vec(y, vec_prec, 2 * N, st);
+    if (rc) return rc;
+    const int pc = o.precond;
+    const bool ext = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DE || pc == CAL_PRECOND_SE;
+    const bool in = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DI || pc == CAL_PRECOND_SI;
+    const bool onlyS = pc == CAL_PRECOND_SE || pc == CAL_PRECOND_SI;
+    for (int m = 0; m < M; ++m) {
+      if (ext) {
+        const std::complex<double> a = 1.0 / k_e, b = -k_e;
+        if ((rc = pair_apply(ref(*P_ext[m], true, !onlyS), vec_prec, x, y, N, a.real(), a.imag(), b.real(), b.imag(), st)))
+          return rc;
+      }
+      if (in) {
+        const std::complex<double> a = mu_m[m] / k_m[m], b = -k_m[m] / mu_m[m];
+        if ((rc = pair_apply(ref(*P_int[m], true, !onlyS), vec_prec, x, y, N, a.real(), a.imag(), b.real(), b.imag(), st)))
+          return rc;
+      }
+    }
+    matvecs += (ext ? (onlyS ? 2 : 4) : 0) * (int64_t)M + (in ? (onlyS ? 2 : 4) : 0) * (int64_t)M;
+    return CAL_OK;
+  }
+
+  // w = M_P^-1 P M_A^-1 y ; y, w float64 [2N]; the working precision is o.precision
+  int apply_precond(const double2* y, double2* w) {
+    cudaStream_t st = ctx->stream;
+    int rc;
+    if (o.precond == CAL_PRECOND_NONE) {
+      CAL_TRY_CUDA(cudaMemcpyAsync(w, y, 2 * N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      return CAL_OK;
+    }
+    if (o.precision == CAL_FP64) {
+      double2* a = (double2*)t1;
+      double2* b = (double2*)t2;
+      if ((rc = gsA64->solve(y, a, st))) return rc;
+      if ((rc = apply_P(a, b, CAL_FP64))) return rc;
+      return gsP64->solve(b, w, st);
+    }
+    float2* a = (float2*)t1;
+    float2* b = (float2*)t2;
+    if ((rc = convert_vec(y, CAL_FP64, b, CAL_FP32, 2 * N, 1.0, st))) return rc;
+    if ((rc = gsA32->solve(b, a, st))) return rc;
+    if ((rc = apply_P(a, b, CAL_FP32))) return rc;
+    if ((rc = gsP32->solve(b, a, st))) return rc;
+    return convert_vec(a, CAL_FP32, w, CAL_FP64, 2 * N, 1.0, st);
+  }
+
+  // w = B v, B = M_P^-1 P M_A^-1 A ; v, w float64
+  int apply_B(const double2* v, double2* w, double2* scratch) {
+    int rc;
+    cudaStream_t st = ctx->stream;
+    if (o.precision == CAL_FP64) {
+      if ((rc = apply_A(v, scratch, CAL_FP64))) return rc;
+      return apply_precond(scratch, w);
+    }
+    float2* a = (float2*)t1;
+    float2* b = (float2*)t2;
+    if ((rc = convert_vec(v, CAL_FP64, a, CAL_FP32, 2 * N, 1.0, st))) return rc;
+    if ((rc = apply_A(a, b, CAL_FP32))) return rc;
+    if (o.precond == CAL_PRECOND_NONE) return convert_vec(b, CAL_FP32, w, CAL_FP64, 2 * N, 1.0, st);
+    if ((rc = gsA32->solve(b, a, st))) return rc;
+    if ((rc = apply_P(a, b, CAL_FP32))) return rc;
+    if ((rc = gsP32->solve(b, a, st))) return rc;
+    return convert_vec(a, CAL_FP32, w, CAL_FP64, 2 * N, 1.0, st);
+  }
+
+  // Restarted GMRES on B d = rhs, d0 = 0, added into x. Relative target tol on ||rhs||.
+  int gmres(const double2* rhs, double2* x, double tol, int& iters, double& rel_res, int maxit) {
+    cudaStream_t st = ctx->stream;
+    const int64_t n = 2 * N;
+    const int m = std::max(1, std::min<int>(o.restart, maxit));
+    double2 *V, *w, *scr, *H, *cs, *sn, *g, *h1, *h2, *y, *r;
+    double* dscal;
+    double* hres;
+    const size_t vb = n * sizeof(double2);
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&V, (m + 1) * vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&w, vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&scr, vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&r, vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&H, (size_t)(m + 1) * m * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&cs, (m + 1) * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&sn, (m + 1) * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&g, (m + 2) * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&h1, (m + 2) * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&h2, (m + 2) * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&y, (m + 1) * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&dscal, 4 * sizeof(double), st));
+    CAL_TRY_CUDA(cudaMallocHost((void**)&hres, 4 * sizeof(double)));
+    int rc = CAL_OK;
+    auto cleanup = [&]() {
+      cudaFreeAsync(V, st); cudaFreeAsync(w, st); cudaFreeAsync(scr, st); cudaFreeAsync(r, st);
+      cudaFreeAsync(H, st); cudaFreeAsync(cs, st); cudaFreeAsync(sn, st); cudaFreeAsync(g, st);
+      cudaFreeAsync(h1, st); cudaFreeAsync(h2, st); cudaFreeAsync(y, st); cudaFreeAsync(dscal, st);
+      cudaStreamSynchronize(st);
+      cudaFreeHost(hres);
+    };
+    iters = 0;
+    // ||rhs||
+    if ((rc = vec_norm2(rhs, n, dscal, st)) ||
+        (rc = (cudaMemcpyAsync(hres, dscal, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : CAL_ECUDA))) {
+      cleanup();
+      return rc;
+    }
+    cudaStreamSynchronize(st);
+    const double bnorm = std::sqrt(hres[0]);
+    rel_res = 0.0;
+    if (bnorm == 0.0) { cleanup(); return CAL_OK; }
+    CAL_TRY_CUDA(cudaMemcpyAsync(r, rhs, vb, cudaMemcpyDeviceToDevice, st));
+    double beta = bnorm;
+    bool converged = false;
+    while (!converged && iters < maxit) {
+      // V0 = r / beta, g = (beta, 0, ...)
+      CAL_TRY_CUDA(cudaMemsetAsync(g, 0, (m + 2) * sizeof(double2), st));
+      const double2 gb = {beta, 0.0};
+      CAL_TRY_CUDA(cudaMemcpyAsync(g, &gb, sizeof(double2), cudaMemcpyHostToDevice, st));
+      hres[1] = beta * beta;
+      CAL_TRY_CUDA(cudaMemcpyAsync(dscal + 1, hres + 1, sizeof(double), cudaMemcpyHostToDevice, st));
+      if ((rc = gmres_scale(r, n, dscal + 1, V, st))) break;
+      int j = 0;
+      for (; j < m && iters < maxit; ++j) {
+        if ((rc = apply_B(V + (size_t)j * n, w, scr))) break;
+        ++iters;
+        if ((rc = gmres_cgs_step(V, n, j, w, h1, h2, dscal + 2, st))) break;
+        if ((rc = gmres_givens(H, m + 1, j, h1, h2, dscal + 2, cs, sn, g, dscal + 3, st))) break;
+        if ((rc = gmres_scale(w, n, dscal + 2, V + (size_t)(j + 1) * n, st))) break;
+        CAL_TRY_CUDA(cudaMemcpyAsync(hres + 3, dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CAL_TRY_CUDA(cudaStreamSynchronize(st));
+        rel_res = hres[3] / bnorm;
+        if (!std::isfinite(rel_res)) { rc = fail(CAL_ECUDA, "GMRES: non-finite residual"); break; }
+        if (rel_res <= tol && j < m - 1) { converged = true; ++j; break; }
+      }
+      if (rc) break;
+      if ((rc = gmres_update(H, m + 1, j, g, y, V, n, x, st))) break;
+      if (converged || iters >= maxit) break;
+      // end of a full cycle: explicit residual r = rhs - B x
+      if ((rc = apply_B(x, w, scr))) break;
+      if ((rc = vec_axpby(rhs, 1.0, w, -1.0, r, n, st))) break;
+      if ((rc = vec_norm2(r, n, dscal, st))) break;
+      CAL_TRY_CUDA(cudaMemcpyAsync(hres, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CAL_TRY_CUDA(cudaStreamSynchronize(st));
+      beta = std::sqrt(hres[0]);
+      rel_res = beta / bnorm;
+      if (rel_res <= tol) converged = true;
+    }
+    cleanup();
+    return rc;
+  }
+};
+
+void opts_default(cal_solve_opts* o) {
+  o->precond = CAL_PRECOND_D;
+  o->precision = CAL_FP32;
+  o->q_regular_A = 6;
+  o->q_singular_A = 4;
+  o->q_regular_P = 6;
+  o->q_singular_P = 4;
+  o->near_cutoff_P = INFINITY;
+  o->tol = 1e-5;
+  o->restart = 200;
+  o->maxit = 1000;
+  o->refine = 3;
+  o->rhs_mode = 0;
+}
+
+}  // namespace
+
+// =============================================================================
+// C ABI
+// =============================================================================
+extern "C" {
+
+const char* cal_last_error(void) { return cal::last_error(); }
+
+int cal_init(cal_ctx** out, int device) {
+  if (!out) return fail(CAL_EINVAL, "cal_init: out is NULL");
+  int n = 0;
+  if (cudaGetDeviceCount(&n) != cudaSuccess || n == 0) {
+    cudaGetLastError();
+    return fail(CAL_ECUDA, "cal_init: no CUDA device available");
+  }
+  if (device < 0 || device >= n) return fail(CAL_EINVAL, "cal_init: device %d out of range", device);
+  CAL_TRY_CUDA(cudaSetDevice(device));
+  auto* c = new cal_ctx;
+  c->impl.device = device;
+  if (cudaStreamCreateWithFlags(&c->impl.stream, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return fail(CAL_ECUDA, "cal_init: cannot create stream");
+  }
+  cudaDeviceGetAttribute(&c->impl.n_sm, cudaDevAttrMultiProcessorCount, device);
+  *out = c;
+  return CAL_OK;
+}
+
+void cal_ctx_destroy(cal_ctx* ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->impl.stream);
+  cudaStreamDestroy(ctx->impl.stream);
+  delete ctx;
+}
+
+void* cal_ctx_stream(cal_ctx* ctx) { return ctx ? (void*)ctx->impl.stream : nullptr; }
+
+int cal_mesh_create(cal_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                    const int32_t* domain, cal_mesh** out) {
+  if (!ctx || !out) return fail(CAL_EINVAL, "cal_mesh_create: NULL argument");
+  auto* m = new cal_mesh;
+  m->impl.ctx = &ctx->impl;
+  int rc = build_mesh(m->impl, verts, nv, tris, nt, domain);
+  if (rc) { delete m; return rc; }
+  *out = m;
+  return CAL_OK;
+}
+
+void cal_mesh_destroy(cal_mesh* mesh) { delete mesh; }
+
+int cal_mesh_get_info(const cal_mesh* mesh, cal_mesh_info* info) {
+  if (!mesh || !info) return fail(CAL_EINVAL, "cal_mesh_get_info: NULL argument");
+  const Mesh& m = mesh->impl;
+  info->n_vertices = m.nv;
+  info->n_triangles = m.nt;
+  info->n_edges = m.ne;
+  info->n_scatterers = m.M;
+  info->h = m.h;
+  info->max_valence = m.max_valence;
+  return CAL_OK;
+}
+
+int cal_space_create(cal_mesh* mesh, int kind, cal_space** out) {
+  if (!mesh || !out) return fail(CAL_EINVAL, "cal_space_create: NULL argument");
+  if (kind != CAL_RWG && kind != CAL_BC) return fail(CAL_EINVAL, "cal_space_create: kind must be CAL_RWG or CAL_BC");
+  CAL_TRY_CUDA(cudaSetDevice(mesh->impl.ctx->device));
+  auto* s = new cal_space;
+  int rc = kind == CAL_RWG ? build_rwg(s->impl, mesh->impl) : build_bc(s->impl, mesh->impl);
+  if (!rc) rc = upload_space(s->impl);
+  if (rc) { delete s; return rc; }
+  *out = s;
+  return CAL_OK;
+}
+
+void cal_space_destroy(cal_space* space) { delete space; }
+
+int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space* test,
+                 cal_space* trial, int scatterer, double near_cutoff, int q_regular, int q_singular,
+                 int precision, cal_op** out) {
+  if (!ctx || !test || !trial || !out) return fail(CAL_EINVAL, "cal_assemble: NULL argument");
+  if (test != trial) return fail(CAL_EINVAL, "cal_assemble: test and trial must be the same space");
+  CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
+  std::unique_ptr<Op> op;
+  int rc = assemble_block(ctx->impl, op_mask & 3, k_re, k_im, test->impl, scatterer, near_cutoff,
+                          q_regular, q_singular, precision, op);
+  if (rc) return rc;
+  CAL_TRY_CUDA(cudaStreamSynchronize(ctx->impl.stream));
+  auto* o = new cal_op;
+  o->impl = std::move(*op);
+  op->d_S = op->d_C = nullptr;
+  op->d_rowptr = nullptr;
+  op->d_col = nullptr;
+  *out = o;
+  return CAL_OK;
+}
+
+void cal_op_destroy(cal_op* op) { delete op; }
+
+int cal_op_get_info(const cal_op* op, cal_op_info* info) {
+  if (!op || !info) return fail(CAL_EINVAL, "cal_op_get_info: NULL argument");
+  info->rows = op->impl.rows;
+  info->cols = op->impl.cols;
+  info->nnz = op->impl.nnz;
+  info->format = op->impl.format;
+  info->precision = op->impl.precision;
+  info->op_mask = op->impl.op_mask;
+  info->row_offset = (int32_t)op->impl.row_offset;
+  return CAL_OK;
+}
+
+int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int64_t* col_idx) {
+  if (!op || !dst) return fail(CAL_EINVAL, "cal_op_export: NULL argument");
+  const Op& o = op->impl;
+  const void* src = which == CAL_OP_S ? o.d_S : (which == CAL_OP_C ? o.d_C : nullptr);
+  if (!src) return fail(CAL_EINVAL, "cal_op_export: operator %d was not assembled", which);
+  const size_t bytes = (size_t)o.nnz * (o.precision == CAL_FP32 ? 8 : 16);
+  CAL_TRY_CUDA(cudaMemcpy(dst, src, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost));
+  if (o.format == CAL_CSR) {
+    if (row_ptr) std::copy(o.h_rowptr.begin(), o.h_rowptr.end(), row_ptr);
+    if (col_idx)
+      for (size_t q = 0; q < o.h_col.size(); ++q) col_idx[q] = o.h_col[q];
+  }
+  return CAL_OK;
+}
+
+int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream) {
+  if (!op || !x || !y || nrhs < 1) return fail(CAL_EINVAL, "cal_matvec: bad argument");
+  const Op& o = op->impl;
+  const void* X = which == CAL_OP_S ? o.d_S : (which == CAL_OP_C ? o.d_C : nullptr);
+  if (!X) return fail(CAL_EINVAL, "cal_matvec: operator %d was not assembled", which);
+  if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(CAL_EINVAL, "cal_matvec: x and y must be device pointers");
+  cudaStream_t st = stream ? (cudaStream_t)stream : o.ctx->stream;
+  return single_apply(o, X, x, y, nrhs, st);
+}
+
+int cal_gram_export(cal_space* rwg, cal_space* bc, double* dst_host) {
+  if (!rwg || !bc || !dst_host || rwg->impl.kind != CAL_RWG || bc->impl.kind != CAL_BC ||
+      rwg->impl.mesh != bc->impl.mesh)
+    return fail(CAL_EINVAL, "cal_gram_export: need an RWG and a BC space of the same mesh");
+  const Space& B = bc->impl;
+  const int64_t n = B.nbasis;
+  std::vector<int64_t> rp, rpT;
+  std::vector<int> col, colT;
+  gram_pattern(B, rp, col);
+  // transpose pattern
+  rpT.assign(n + 1, 0);
+  for (int c : col) rpT[c + 1]++;
+  for (int64_t i = 0; i < n; ++i) rpT[i + 1] += rpT[i];
+  colT.resize(col.size());
+  {
+    std::vector<int64_t> fill(rpT.begin(), rpT.end() - 1);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q) colT[fill[col[q]]++] = (int)i;
+  }
+  int64_t *drp, *drpT;
+  int *dc, *dcT;
+  double *dv, *dvT;
+  const size_t nnz = col.size();
+  CAL_TRY_CUDA(cudaMalloc((void**)&drp, (n + 1) * sizeof(int64_t)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&drpT, (n + 1) * sizeof(int64_t)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&dc, nnz * sizeof(int)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&dcT, nnz * sizeof(int)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&dv, nnz * sizeof(double)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&dvT, nnz * sizeof(double)));
+  CAL_TRY_CUDA(cudaMemcpy(drp, rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CAL_TRY_CUDA(cudaMemcpy(drpT, rpT.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice));
+  CAL_TRY_CUDA(cudaMemcpy(dc, col.data(), nnz * sizeof(int), cudaMemcpyHostToDevice));
+  CAL_TRY_CUDA(cudaMemcpy(dcT, colT.data(), nnz * sizeof(int), cudaMemcpyHostToDevice));
+  CAL_TRY_CUDA(cudaMemset(dv, 0, nnz * sizeof(double)));
+  CAL_TRY_CUDA(cudaMemset(dvT, 0, nnz * sizeof(double)));
+  int rc = launch_gram(rwg->impl, B, drp, dc, drpT, dcT, dv, dvT, 0);
+  std::vector<double> v(nnz);
+  if (!rc) {
+    CAL_TRY_CUDA(cudaDeviceSynchronize());
+    CAL_TRY_CUDA(cudaMemcpy(v.data(), dv, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    std::fill(dst_host, dst_host + n * n, 0.0);
+    for (int64_t i = 0; i < n; ++i)
+      for (int64_t q = rp[i]; q < rp[i + 1]; ++q) dst_host[i * n + col[q]] = v[q];
+  }
+  cudaFree(drp); cudaFree(drpT); cudaFree(dc); cudaFree(dcT); cudaFree(dv); cudaFree(dvT);
+  return rc;
+}
+
+void cal_solve_opts_default(cal_solve_opts* opts) {
+  if (opts) opts_default(opts);
+}
+
+int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r,
+                     const double* mu_r, const double* inc, int64_t nrhs,
+                     const cal_solve_opts* opts, cal_solution** out) {
+  if (!ctx || !mesh || !eps_r || !inc || nrhs < 1 || !out) return fail(CAL_EINVAL, "cal_pmchwt_solve: bad argument");
+  if (!(k_ext > 0) || !std::isfinite(k_ext)) return fail(CAL_EINVAL, "cal_pmchwt_solve: k_ext must be positive");
+  CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
+  const double t_start = now();
+  Pmchwt P;
+  P.ctx = &ctx->impl;
+  P.mesh = &mesh->impl;
+  P.M = (int)mesh->impl.M;
+  P.N = mesh->impl.ne;
+  P.k_e = k_ext;
+  if (opts) P.o = *opts; else opts_default(&P.o);
+  const cal_solve_opts& o = P.o;
+  if (o.precision != CAL_FP32 && o.precision != CAL_FP64) return fail(CAL_EINVAL, "solve: bad precision");
+  if (o.precond < CAL_PRECOND_NONE || o.precond > CAL_PRECOND_SI) return fail(CAL_EINVAL, "solve: bad preconditioner");
+  if (!(o.tol > 0) || o.restart < 1 || o.maxit < 1) return fail(CAL_EINVAL, "solve: bad tolerance/restart/maxit");
+  if (o.rhs_mode != 0) return fail(CAL_EINVAL, "solve: only the total-trace right-hand side is implemented");
+  for (int m = 0; m < P.M; ++m) {
+    std::complex<double> e(eps_r[2 * m], eps_r[2 * m + 1]);
+    std::complex<double> u = mu_r ? std::complex<double>(mu_r[2 * m], mu_r[2 * m + 1]) : 1.0;
+    if (!std::isfinite(e.real()) || !std::isfinite(e.imag()) || !std::isfinite(u.real()) ||
+        !std::isfinite(u.imag()) || std::abs(e) == 0.0 || std::abs(u) == 0.0)
+      return fail(CAL_EINVAL, "solve: bad eps_r/mu_r for scatterer %d", m);
+    P.k_m.push_back(interior_k(k_ext, e, u));
+    P.mu_m.push_back(u);
+  }
+  for (int64_t q = 0; q < 6 * nrhs; ++q)
+    if (!std::isfinite(inc[q])) return fail(CAL_EINVAL, "solve: non-finite incident field");
+  cudaStream_t st = ctx->impl.stream;
+  int rc;
+  // spaces
+  P.rwg = std::make_unique<Space>();
+  if ((rc = build_rwg(*P.rwg, mesh->impl)) || (rc = upload_space(*P.rwg))) return rc;
+  const bool need_bc = o.precond != CAL_PRECOND_NONE;
+  if (need_bc) {
+    P.bc = std::make_unique<Space>();
+    if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc))) return rc;
+  }
+  const double t_setup = now();
+  // A: S, C at k_e on the union; S, C at k_m on each scatterer
+  const int prec = o.precision;
+  if ((rc = assemble_block(ctx->impl, 3, k_ext, 0.0, *P.rwg, -1, INFINITY, o.q_regular_A, o.q_singular_A,
+                           prec, P.A_ext)))
+    return rc;
+  P.A_int.resize(P.M);
+  for (int m = 0; m < P.M; ++m)
+    if ((rc = assemble_block(ctx->impl, 3, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, INFINITY,
+                             o.q_regular_A, o.q_singular_A, prec, P.A_int[m])))
+      return rc;
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  const double t_A = now();
+  int64_t bytes_A = 0, bytes_P = 0;
+  const size_t esz = prec == CAL_FP32 ? 8 : 16;
+  bytes_A += P.A_ext->nnz * esz * 2;
+  for (auto& a : P.A_int) bytes_A += a->nnz * esz * 2;
+  // P on BC: block diagonal per scatterer
+  if (need_bc) {
+    const int pc = o.precond;
+    const bool ext = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DE || pc == CAL_PRECOND_SE;
+    const bool in = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DI || pc == CAL_PRECOND_SI;
+    const int want = (pc == CAL_PRECOND_SE || pc == CAL_PRECOND_SI) ? 1 : 3;
+    const double chi = std::isinf(o.near_cutoff_P) ? INFINITY : o.near_cutoff_P * mesh->impl.h;
+    P.P_ext.resize(P.M);
+    P.P_int.resize(P.M);
+    for (int m = 0; m < P.M; ++m) {
+      if (ext && (rc = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P,
+                                      o.q_singular_P, prec, P.P_ext[m])))
+        return rc;
+      if (in && (rc = assemble_block(ctx->impl, want, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, chi,
+                                     o.q_regular_P, o.q_singular_P, prec, P.P_int[m])))
+        return rc;
+      for (auto* op : {P.P_ext[m].get(), P.P_int[m].get()})
+        if (op) bytes_P += op->nnz * esz * ((want & 2) ? 2 : 1);
+    }
+    // Gram G (rows RWG, cols BC) and its transpose
+    std::vector<int64_t> rp, rpT;
+    std::vector<int> col, colT;
+    gram_pattern(*P.bc, rp, col);
+    const int64_t n = P.N;
+    rpT.assign(n + 1, 0);
+    for (int c : col) rpT[c + 1]++;
+    for (int64_t i = 0; i < n; ++i) rpT[i + 1] += rpT[i];
+    colT.resize(col.size());
+    {
+      std::vector<int64_t> fill(rpT.begin(), rpT.end() - 1);
+      for (int64_t i = 0; i < n; ++i)
+        for (int64_t q = rp[i]; q < rp[i + 1]; ++q) colT[fill[col[q]]++] = (int)i;
+    }
+    P.gnnz = (int64_t)col.size();
+    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_grp, (n + 1) * sizeof(int64_t)));
+    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_grpT, (n + 1) * sizeof(int64_t)));
+    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gcol, P.gnnz * sizeof(int)));
+    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gcolT, P.gnnz * sizeof(int)));
+    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gval, P.gnnz * sizeof(double)));
+    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gvalT, P.gnnz * sizeof(double)));
+    CAL_TRY_CUDA(cudaMemcpyAsync(P.d_grp, rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(P.d_grpT, rpT.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(P.d_gcol, col.data(), P.gnnz * sizeof(int), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(P.d_gcolT, colT.data(), P.gnnz * sizeof(int), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemsetAsync(P.d_gval, 0, P.gnnz * sizeof(double), st));
+    CAL_TRY_CUDA(cudaMemsetAsync(P.d_gvalT, 0, P.gnnz * sizeof(double), st));
+    if ((rc = launch_gram(*P.rwg, *P.bc, P.d_grp, P.d_gcol, P.d_grpT, P.d_gcolT, P.d_gval, P.d_gvalT, st)))
+      return rc;
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+    // M_A = diag(G, G); M_P = diag(-G^T, -G^T): two component systems per vector
+    if (prec == CAL_FP64) {
+      P.gsA64 = std::make_unique<GramSolver<double>>();
+      P.gsP64 = std::make_unique<GramSolver<double>>();
+      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-13, 60))) return rc;
+      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-13, 60))) return rc;
+    } else {
+      P.gsA32 = std::make_unique<GramSolver<float>>();
+      P.gsP32 = std::make_unique<GramSolver<float>>();
+      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-6, 25))) return rc;
+      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-6, 25))) return rc;
+    }
+  }
+  const size_t vbytes = 2 * P.N * sizeof(double2);
+  CAL_TRY_CUDA(cudaMalloc(&P.t1, vbytes));
+  CAL_TRY_CUDA(cudaMalloc(&P.t2, vbytes));
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  const double t_P = now();
+  // right-hand sides and solves
+  auto sol = std::make_unique<cal_solution>();
+  sol->ctx = &ctx->impl;
+  sol->nrhs = nrhs;
+  sol->ne = P.N;
+  sol->k_e = k_ext;
+  const int64_t n2 = 2 * P.N;
+  double* d_inc;
+  double2 *d_b, *d_rhs, *d_r;
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_inc, 6 * nrhs * sizeof(double)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_b, nrhs * n2 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_rhs, n2 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_r, n2 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&sol->d_x, nrhs * n2 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMemsetAsync(sol->d_x, 0, nrhs * n2 * sizeof(double2), st));
+  CAL_TRY_CUDA(cudaMemcpyAsync(d_inc, inc, 6 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
+  std::unique_ptr<double2, decltype(&cudaFree)> g1(d_b, &cudaFree), g2(d_rhs, &cudaFree), g3(d_r, &cudaFree);
+  std::unique_ptr<double, decltype(&cudaFree)> g4(d_inc, &cudaFree);
+  if ((rc = launch_rhs(*P.rwg, d_inc, (int)nrhs, k_ext, 1.0, d_b, st))) return rc;
+  P.matvecs = 0;
+  int total_it = 0;
+  double worst_res = 0.0;
+  bool all_conv = true;
+  for (int64_t q = 0; q < nrhs; ++q) {
+    double2* b = d_b + q * n2;
+    double2* x = sol->d_x + q * n2;
+    int it = 0;
+    double res = 0.0;
+    if (prec == CAL_FP64 || o.refine <= 0) {
+      // d = GMRES(B, M^-1 b)
+      if ((rc = P.apply_precond(b, d_rhs))) return rc;
+      if (o.precond != CAL_PRECOND_NONE) P.matvecs += 0;  // counted inside apply_P
+      if ((rc = P.gmres(d_rhs, x, o.tol, it, res, o.maxit))) return rc;
+    } else {
+      // FP64 iterative refinement around FP32-bulk GMRES: r = b - A x in
+      // float64 accumulation, correction from the preconditioned system.
+      double r0 = 0.0;
+      double2* r = d_r;
+      for (int step = 0; step <= o.refine; ++step) {
+        if (step == 0) {
+          CAL_TRY_CUDA(cudaMemcpyAsync(r, b, n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+        } else {
+          if ((rc = P.apply_A(x, r, CAL_FP64))) return rc;  // float64 vectors, complex64 matrices
+          if ((rc = vec_axpby(b, 1.0, r, -1.0, r, n2, st))) return rc;
+        }
+        if ((rc = P.apply_precond(r, d_rhs))) return rc;
+        double* dn;
+        double hn;
+        CAL_TRY_CUDA(cudaMalloc((void**)&dn, sizeof(double)));
+        vec_norm2(d_rhs, n2, dn, st);
+        CAL_TRY_CUDA(cudaMemcpyAsync(&hn, dn, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CAL_TRY_CUDA(cudaStreamSynchronize(st));
+        cudaFree(dn);
+        const double rn = std::sqrt(hn);
+        if (step == 0) r0 = rn;
+        res = r0 > 0 ? rn / r0 : 0.0;
+        if (r0 == 0.0 || (step > 0 && res <= o.tol) || step == o.refine) break;
+        const double inner = std::min(0.5, std::max(o.tol * r0 / rn, 2e-6));
+        int it_s = 0;
+        double res_s = 0.0;
+        if ((rc = P.gmres(d_rhs, x, inner, it_s, res_s, o.maxit - it))) return rc;
+        it += it_s;
+        if (it >= o.maxit) {
+          // final residual for the report
+          if ((rc = P.apply_A(x, r, CAL_FP64)) || (rc = vec_axpby(b, 1.0, r, -1.0, r, n2, st)) ||
+              (rc = P.apply_precond(r, d_rhs)))
+            return rc;
+          CAL_TRY_CUDA(cudaMalloc((void**)&dn, sizeof(double)));
+          vec_norm2(d_rhs, n2, dn, st);
+          CAL_TRY_CUDA(cudaMemcpyAsync(&hn, dn, sizeof(double), cudaMemcpyDeviceToHost, st));
+          CAL_TRY_CUDA(cudaStreamSynchronize(st));
+          cudaFree(dn);
+          res = std::sqrt(hn) / r0;
+          break;
+        }
+      }
+    }
+    total_it += it;
+    worst_res = std::max(worst_res, res);
+    if (!(res <= o.tol)) all_conv = false;
+  }
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  const double t_end = now();
+  sol->rwg = std::move(P.rwg);
+  cal_solve_info& info = sol->info;
+  info.iterations = total_it;
+  info.converged = all_conv;
+  info.matvecs = P.matvecs;
+  info.residual = worst_res;
+  info.t_setup = t_setup - t_start;
+  info.t_assemble_A = t_A - t_setup;
+  info.t_assemble_P = t_P - t_A;
+  info.t_solve = t_end - t_P;
+  info.bytes_A = bytes_A;
+  info.bytes_P = bytes_P;
+  info.n_unknowns = 2 * P.N;
+  *out = sol.release();
+  if (!all_conv) return fail(CAL_ENOTCONV, "GMRES reached maxit (residual %.3e > tol %.1e)", worst_res, o.tol);
+  return CAL_OK;
+}
+
+int cal_solution_get_info(const cal_solution* sol, cal_solve_info* info) {
+  if (!sol || !info) return fail(CAL_EINVAL, "cal_solution_get_info: NULL argument");
+  *info = sol->info;
+  return CAL_OK;
+}
+
+int cal_solution_coefficients(const cal_solution* sol, double* dst_host) {
+  if (!sol || !dst_host) return fail(CAL_EINVAL, "cal_solution_coefficients: NULL argument");
+  CAL_TRY_CUDA(cudaMemcpy(dst_host, sol->d_x, sol->nrhs * 2 * sol->ne * sizeof(double2), cudaMemcpyDeviceToHost));
+  return CAL_OK;
+}
+
+int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, double* out) {
+  if (!sol || !dirs || !out || ndir < 1) return fail(CAL_EINVAL, "cal_farfield: bad argument");
+  for (int64_t q = 0; q < 3 * ndir; ++q)
+    if (!std::isfinite(dirs[q])) return fail(CAL_EINVAL, "cal_farfield: non-finite direction");
+  cudaStream_t st = sol->ctx->stream;
+  double* d_dirs;
+  double2* d_out;
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_dirs, 3 * ndir * sizeof(double)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_out, sol->nrhs * ndir * 3 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMemcpyAsync(d_dirs, dirs, 3 * ndir * sizeof(double), cudaMemcpyHostToDevice, st));
+  int rc = launch_farfield(*sol->rwg, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e, sol->mu_e, d_out, st);
+  if (!rc) {
+    CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, sol->nrhs * ndir * 3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  cudaFree(d_dirs);
+  cudaFree(d_out);
+  return rc;
+}
+
+void cal_solution_destroy(cal_solution* sol) { delete sol; }
+
+}  // extern "C"

@@ -1,0 +1,832 @@
+// Galerkin assembly of the Maxwell operators S and C on sm_103a.
+//
+// arXiv 2008.04772, Section 2 (operators, G = e^{ikr}/(4 pi r)) and Section 3.3
+// (tensor Gauss rules on regular triangle pairs, Sauter–Schwab rules on pairs
+// sharing a vertex, an edge or the whole triangle).
+//
+// Every basis piece on a triangle is phi = sigma (x - c) + w (see internal.h).
+// For a triangle pair with centroids c1, c2, Delta = c1 - c2, local points
+// xi = x - c1, eta = y - c2, the kernel sums eighteen complex moments
+//   S: G0 = sum G,  Gx = sum G xi,  Gy = sum G eta,  Gxy = sum G xi.eta
+//   C: g0 = sum g,  gx = sum g xi,  gy = sum g eta,  gxy = sum g xi x eta
+// (weights w_p |T1| w_q |T2| folded in; grad_x G = g (x - y)), turns them into
+// "pair coefficients"
+//   s = Delta.gxy, X1 = Delta x gx + gxy, X2 = gy x Delta - gxy,
+//   V = Delta g0 + gx - gy,
+// and every (test piece a, trial piece b) entry follows in closed form:
+//   S_ab = -ik [sa sb Gxy + sa wb.Gx + sb wa.Gy + (wa.wb) G0] + (4i/k) sa sb G0
+//   C_ab = sa sb s + sa wb.X1 + sb wa.X2 + wa.(wb x V).
+// Local coordinates relative to the centroids keep float32 free of
+// cancellation; Delta is formed from hi+lo float centroids.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "internal.h"
+
+namespace cal {
+
+// ---------------------------------------------------------------------------
+// rules passed by value
+// ---------------------------------------------------------------------------
+struct Rules {
+  float rbf[18], rwf[6];
+  double rbd[18], rwd[6];
+  double gx[16], gw[16];
+  int nreg, ng;
+};
+
+static Rules g_rules;
+
+int set_quadrature_tables(int nreg, int nsing) {
+  if (nreg != 6 && nreg != 1) return fail(CAL_EINVAL, "q_regular must be 6 or 1 (got %d)", nreg);
+  if (nsing < 1 || nsing > 16) return fail(CAL_EINVAL, "q_singular must be in 1..16 (got %d)", nsing);
+  std::vector<double> b, w, x, gw;
+  triangle_rule(nreg, b, w);
+  gauss_legendre01(nsing, x, gw);
+  Rules r{};
+  for (int i = 0; i < 3 * nreg; ++i) { r.rbd[i] = b[i]; r.rbf[i] = (float)b[i]; }
+  for (int i = 0; i < nreg; ++i) { r.rwd[i] = w[i]; r.rwf[i] = (float)w[i]; }
+  for (int i = 0; i < nsing; ++i) { r.gx[i] = x[i]; r.gw[i] = gw[i]; }
+  r.nreg = nreg;
+  r.ng = nsing;
+  g_rules = r;
+  return CAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small vector helpers
+// ---------------------------------------------------------------------------
+template <typename R>
+struct V3 { R x, y, z; };
+
+template <typename R>
+__device__ __forceinline__ V3<R> v3(R a, R b, R c) { return {a, b, c}; }
+
+template <typename R>
+__device__ __forceinline__ R dot3(const V3<R>& a, const V3<R>& b) {
+  return a.x * b.x + a.y * b.y + a.z * b.z;
+}
+template <typename R>
+__device__ __forceinline__ V3<R> cross3(const V3<R>& a, const V3<R>& b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+
+// ---------------------------------------------------------------------------
+// kernel values G = e^{ikr}/(4 pi r) and g = (ikr - 1) e^{ikr}/(4 pi r^3)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, float& Gi,
+                                      float& gr, float& gi) {
+  const float rinv = rsqrtf(r2);
+  const float r = r2 * rinv;
+  const float ph = kr * r;
+  // Cody–Waite reduction of the phase to [-pi, pi] with 2 pi split in two
+  // floats (hi exact in 24 bits, lo the float32 remainder of the float64 value)
+  constexpr double TWO_PI = 6.283185307179586476925286766559;
+  constexpr float TP_HI = (float)TWO_PI;
+  constexpr float TP_LO = (float)(TWO_PI - (double)(float)TWO_PI);
+  constexpr float INV_TP = (float)(1.0 / TWO_PI);
+  const float n = rintf(ph * INV_TP);
+  float th = fmaf(-n, TP_HI, ph);
+  th = fmaf(-n, TP_LO, th);
+  float s, c;
+  __sincosf(th, &s, &c);
+  constexpr float INV_4PI = (float)(0.25 / 3.14159265358979323846);
+  float amp = rinv * INV_4PI;
+  if (ki != 0.0f) amp *= __expf(-ki * r);
+  Gr = amp * c;
+  Gi = amp * s;
+  const float fr = (-ki * r - 1.0f) * rinv * rinv;
+  const float fi = kr * rinv;
+  gr = Gr * fr - Gi * fi;
+  gi = Gr * fi + Gi * fr;
+}
+
+__device__ __forceinline__ void green(double r2, double kr, double ki, double& Gr, double& Gi,
+                                      double& gr, double& gi) {
+  const double r = sqrt(r2);
+  const double rinv = 1.0 / r;
+  double s, c;
+  sincos(kr * r, &s, &c);
+  double amp = rinv * (0.25 / 3.14159265358979323846);
+  if (ki != 0.0) amp *= exp(-ki * r);
+  Gr = amp * c;
+  Gi = amp * s;
+  const double fr = (-ki * r - 1.0) * rinv * rinv;
+  const double fi = kr * rinv;
+  gr = Gr * fr - Gi * fi;
+  gi = Gr * fi + Gi * fr;
+}
+
+// ---------------------------------------------------------------------------
+// moments -> pair coefficients
+// ---------------------------------------------------------------------------
+template <typename R>
+struct Mom {
+  // S moments
+  R G0r, G0i, Gxyr, Gxyi;
+  V3<R> Gxr, Gxi, Gyr, Gyi;
+  // C moments
+  R g0r, g0i;
+  V3<R> gxr, gxi, gyr, gyi, gxyr, gxyi;
+  __device__ void zero() {
+    G0r = G0i = Gxyr = Gxyi = g0r = g0i = R(0);
+    Gxr = Gxi = Gyr = Gyi = gxr = gxi = gyr = gyi = gxyr = gxyi = {R(0), R(0), R(0)};
+  }
+};
+
+// 18 complex pair coefficients, as 36 reals in a fixed order:
+//  0..1 G0, 2..7 Gx, 8..13 Gy, 14..15 Gxy, 16..17 s, 18..23 X1, 24..29 X2, 30..35 V
+// complex vectors are stored (re x, re y, re z, im x, im y, im z)
+template <typename R>
+__device__ __forceinline__ void pair_coeffs(const Mom<R>& m, const V3<R>& D, R* pc) {
+  pc[0] = m.G0r; pc[1] = m.G0i;
+  pc[2] = m.Gxr.x; pc[3] = m.Gxr.y; pc[4] = m.Gxr.z; pc[5] = m.Gxi.x; pc[6] = m.Gxi.y; pc[7] = m.Gxi.z;
+  pc[8] = m.Gyr.x; pc[9] = m.Gyr.y; pc[10] = m.Gyr.z; pc[11] = m.Gyi.x; pc[12] = m.Gyi.y; pc[13] = m.Gyi.z;
+  pc[14] = m.Gxyr; pc[15] = m.Gxyi;
+  pc[16] = dot3(D, m.gxyr);
+  pc[17] = dot3(D, m.gxyi);
+  V3<R> a = cross3(D, m.gxr), b = cross3(D, m.gxi);
+  pc[18] = a.x + m.gxyr.x; pc[19] = a.y + m.gxyr.y; pc[20] = a.z + m.gxyr.z;
+  pc[21] = b.x + m.gxyi.x; pc[22] = b.y + m.gxyi.y; pc[23] = b.z + m.gxyi.z;
+  a = cross3(m.gyr, D); b = cross3(m.gyi, D);
+  pc[24] = a.x - m.gxyr.x; pc[25] = a.y - m.gxyr.y; pc[26] = a.z - m.gxyr.z;
+  pc[27] = b.x - m.gxyi.x; pc[28] = b.y - m.gxyi.y; pc[29] = b.z - m.gxyi.z;
+  pc[30] = D.x * m.g0r + m.gxr.x - m.gyr.x;
+  pc[31] = D.y * m.g0r + m.gxr.y - m.gyr.y;
+  pc[32] = D.z * m.g0r + m.gxr.z - m.gyr.z;
+  pc[33] = D.x * m.g0i + m.gxi.x - m.gyi.x;
+  pc[34] = D.y * m.g0i + m.gxi.y - m.gyi.y;
+  pc[35] = D.z * m.g0i + m.gxi.z - m.gyi.z;
+}
+
+// entry of one (test piece a, trial piece b) combination from pair coefficients
+template <typename R>
+__device__ __forceinline__ void entry_from_pc(const R* pc, R sa, const V3<R>& wa, R sb,
+                                              const V3<R>& wb, R mikr, R miki, R c4r, R c4i,
+                                              bool wantS, bool wantC, R& Sr, R& Si, R& Cr,
+                                              R& Ci) {
+  if (wantS) {
+    const R ss = sa * sb;
+    const V3<R> Gxr = {pc[2], pc[3], pc[4]}, Gxi = {pc[5], pc[6], pc[7]};
+    const V3<R> Gyr = {pc[8], pc[9], pc[10]}, Gyi = {pc[11], pc[12], pc[13]};
+    const R ww = dot3(wa, wb);
+    const R br = ss * pc[14] + sa * dot3(wb, Gxr) + sb * dot3(wa, Gyr) + ww * pc[0];
+    const R bi = ss * pc[15] + sa * dot3(wb, Gxi) + sb * dot3(wa, Gyi) + ww * pc[1];
+    Sr = mikr * br - miki * bi + ss * (c4r * pc[0] - c4i * pc[1]);
+    Si = mikr * bi + miki * br + ss * (c4r * pc[1] + c4i * pc[0]);
+  }
+  if (wantC) {
+    const R ss = sa * sb;
+    const V3<R> X1r = {pc[18], pc[19], pc[20]}, X1i = {pc[21], pc[22], pc[23]};
+    const V3<R> X2r = {pc[24], pc[25], pc[26]}, X2i = {pc[27], pc[28], pc[29]};
+    const V3<R> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
+    const V3<R> wxw = cross3(wa, wb);
+    Cr = ss * pc[16] + sa * dot3(wb, X1r) + sb * dot3(wa, X2r) + dot3(wxw, Vr);
+    Ci = ss * pc[17] + sa * dot3(wb, X1i) + sb * dot3(wa, X2i) + dot3(wxw, Vi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// output sinks: dense (atomics into a row-major block) or CSR (row search)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void atomic_add_c(float* base, int64_t idx, float re, float im) {
+  atomicAdd(reinterpret_cast<float2*>(base) + idx, make_float2(re, im));
+}
+__device__ __forceinline__ void atomic_add_c(double* base, int64_t idx, double re, double im) {
+  atomicAdd(base + 2 * idx, re);
+  atomicAdd(base + 2 * idx + 1, im);
+}
+
+template <typename RO>
+struct Sink {
+  RO* S;
+  RO* C;
+  int64_t off;           // first basis index of the block
+  int64_t ld;            // dense leading dimension; 0 for CSR
+  const int64_t* rowptr; // CSR
+  const int* col;
+  __device__ __forceinline__ int64_t index(int i, int j) const {
+    const int64_t li = i - off, lj = j - off;
+    if (ld) return li * ld + lj;
+    int64_t lo = rowptr[li], hi = rowptr[li + 1] - 1;
+    while (lo <= hi) {
+      int64_t mid = (lo + hi) >> 1;
+      int c = col[mid];
+      if (c == lj) return mid;
+      if (c < lj) lo = mid + 1; else hi = mid - 1;
+    }
+    return -1;
+  }
+  __device__ __forceinline__ void add(int i, int j, bool wS, bool wC, double Sr, double Si,
+                                      double Cr, double Ci) const {
+    const int64_t k = index(i, j);
+    if (k < 0) return;
+    if (wS) atomic_add_c(S, k, (RO)Sr, (RO)Si);
+    if (wC) atomic_add_c(C, k, (RO)Cr, (RO)Ci);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// regular-pair quadrature over the tensor rule (NREG points per triangle)
+// ---------------------------------------------------------------------------
+template <typename R, int NREG>
+__device__ __forceinline__ void regular_moments(const V3<R>* xi, const R* wx, const V3<R>* eta,
+                                                const R* wy, const V3<R>& D, R kr, R ki,
+                                                bool wantC, Mom<R>& m) {
+  m.zero();
+#pragma unroll
+  for (int p = 0; p < NREG; ++p) {
+    R s0r = 0, s0i = 0, t0r = 0, t0i = 0;
+    V3<R> ser = {0, 0, 0}, sei = {0, 0, 0}, ter = {0, 0, 0}, tei = {0, 0, 0};
+    const V3<R> dp = {D.x + xi[p].x, D.y + xi[p].y, D.z + xi[p].z};
+#pragma unroll
+    for (int q = 0; q < NREG; ++q) {
+      const R dx = dp.x - eta[q].x, dy = dp.y - eta[q].y, dz = dp.z - eta[q].z;
+      R Gr, Gi, gr, gi;
+      green(dx * dx + dy * dy + dz * dz, kr, ki, Gr, Gi, gr, gi);
+      Gr *= wy[q]; Gi *= wy[q]; gr *= wy[q]; gi *= wy[q];
+      s0r += Gr; s0i += Gi;
+      ser.x += Gr * eta[q].x; ser.y += Gr * eta[q].y; ser.z += Gr * eta[q].z;
+      sei.x += Gi * eta[q].x; sei.y += Gi * eta[q].y; sei.z += Gi * eta[q].z;
+      if (wantC) {
+        t0r += gr; t0i += gi;
+        ter.x += gr * eta[q].x; ter.y += gr * eta[q].y; ter.z += gr * eta[q].z;
+        tei.x += gi * eta[q].x; tei.y += gi * eta[q].y; tei.z += gi * eta[q].z;
+      }
+    }
+    const R w = wx[p];
+    const V3<R> x = xi[p];
+    m.G0r += w * s0r; m.G0i += w * s0i;
+    m.Gxr.x += w * x.x * s0r; m.Gxr.y += w * x.y * s0r; m.Gxr.z += w * x.z * s0r;
+    m.Gxi.x += w * x.x * s0i; m.Gxi.y += w * x.y * s0i; m.Gxi.z += w * x.z * s0i;
+    m.Gyr.x += w * ser.x; m.Gyr.y += w * ser.y; m.Gyr.z += w * ser.z;
+    m.Gyi.x += w * sei.x; m.Gyi.y += w * sei.y; m.Gyi.z += w * sei.z;
+    m.Gxyr += w * dot3(x, ser); m.Gxyi += w * dot3(x, sei);
+    if (wantC) {
+      m.g0r += w * t0r; m.g0i += w * t0i;
+      m.gxr.x += w * x.x * t0r; m.gxr.y += w * x.y * t0r; m.gxr.z += w * x.z * t0r;
+      m.gxi.x += w * x.x * t0i; m.gxi.y += w * x.y * t0i; m.gxi.z += w * x.z * t0i;
+      m.gyr.x += w * ter.x; m.gyr.y += w * ter.y; m.gyr.z += w * ter.z;
+      m.gyi.x += w * tei.x; m.gyi.y += w * tei.y; m.gyi.z += w * tei.z;
+      const V3<R> cr = cross3(x, ter), ci = cross3(x, tei);
+      m.gxyr.x += w * cr.x; m.gxyr.y += w * cr.y; m.gxyr.z += w * cr.z;
+      m.gxyi.x += w * ci.x; m.gxyi.y += w * ci.y; m.gxyi.z += w * ci.z;
+    }
+  }
+}
+
+// triangle loaders: quadrature points relative to the centroid and weights
+template <int NREG>
+__device__ __forceinline__ void load_points(const TriF& t, const Rules& rl, V3<float>* p, float* w) {
+#pragma unroll
+  for (int q = 0; q < NREG; ++q) {
+    const float b0 = rl.rbf[3 * q], b1 = rl.rbf[3 * q + 1], b2 = rl.rbf[3 * q + 2];
+    p[q] = {b0 * t.off[0][0] + b1 * t.off[1][0] + b2 * t.off[2][0],
+            b0 * t.off[0][1] + b1 * t.off[1][1] + b2 * t.off[2][1],
+            b0 * t.off[0][2] + b1 * t.off[1][2] + b2 * t.off[2][2]};
+    w[q] = rl.rwf[q] * t.area;
+  }
+}
+template <int NREG>
+__device__ __forceinline__ void load_points(const TriD& t, const Rules& rl, V3<double>* p, double* w) {
+#pragma unroll
+  for (int q = 0; q < NREG; ++q) {
+    const double b0 = rl.rbd[3 * q], b1 = rl.rbd[3 * q + 1], b2 = rl.rbd[3 * q + 2];
+    p[q] = {b0 * t.off[0][0] + b1 * t.off[1][0] + b2 * t.off[2][0],
+            b0 * t.off[0][1] + b1 * t.off[1][1] + b2 * t.off[2][1],
+            b0 * t.off[0][2] + b1 * t.off[1][2] + b2 * t.off[2][2]};
+    w[q] = rl.rwd[q] * t.area;
+  }
+}
+__device__ __forceinline__ V3<float> centroid_delta(const TriF& a, const TriF& b) {
+  return {(a.chi[0] - b.chi[0]) + (a.clo[0] - b.clo[0]), (a.chi[1] - b.chi[1]) + (a.clo[1] - b.clo[1]),
+          (a.chi[2] - b.chi[2]) + (a.clo[2] - b.clo[2])};
+}
+__device__ __forceinline__ V3<double> centroid_delta(const TriD& a, const TriD& b) {
+  return {a.c[0] - b.c[0], a.c[1] - b.c[1], a.c[2] - b.c[2]};
+}
+template <typename TRI>
+__device__ __forceinline__ bool touching(const TRI& a, const TRI& b) {
+  bool t = false;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t |= (a.vid[i] == b.vid[j]);
+  return t;
+}
+
+template <typename R> struct TriOf;
+template <> struct TriOf<float> { using T = TriF; };
+template <> struct TriOf<double> { using T = TriD; };
+
+// ---------------------------------------------------------------------------
+// A3: regular RWG pairs, one thread per unordered pair t1 < t2 (the rule is
+// symmetric in the two triangles and both operators are symmetric, so each
+// result is added at (i, j) and (j, i)); touching pairs are left to the
+// singular kernel.
+// ---------------------------------------------------------------------------
+template <typename R, int NREG>
+__global__ void __launch_bounds__(256) rwg_regular_kernel(
+    const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
+    const R* __restrict__ slot_sw, int64_t t0, int64_t ntr, R kr, R ki, R mikr, R miki, R c4r,
+    R c4i, bool wantS, bool wantC, Rules rl, Sink<R> out) {
+  using TRI = typename TriOf<R>::T;
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  const int64_t i1 = (int64_t)bi * 16 + threadIdx.y;
+  const int64_t i2 = (int64_t)bj * 16 + threadIdx.x;
+  if (i1 >= ntr || i2 >= ntr || i1 >= i2) return;
+  const int64_t t1 = t0 + i1, t2 = t0 + i2;
+  const TRI A = tri[t1];
+  const TRI B = tri[t2];
+  if (touching(A, B)) return;
+  V3<R> xi[NREG], eta[NREG];
+  R wx[NREG], wy[NREG];
+  load_points<NREG>(A, rl, xi, wx);
+  load_points<NREG>(B, rl, eta, wy);
+  const V3<R> D = centroid_delta(A, B);
+  Mom<R> m;
+  regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, wantC, m);
+  R pc[36];
+  pair_coeffs(m, D, pc);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const int ea = slot_edge[3 * t1 + a];
+    const R sa = slot_sw[12 * t1 + 4 * a];
+    const V3<R> wa = {slot_sw[12 * t1 + 4 * a + 1], slot_sw[12 * t1 + 4 * a + 2], slot_sw[12 * t1 + 4 * a + 3]};
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int eb = slot_edge[3 * t2 + b];
+      const R sb = slot_sw[12 * t2 + 4 * b];
+      const V3<R> wb = {slot_sw[12 * t2 + 4 * b + 1], slot_sw[12 * t2 + 4 * b + 2], slot_sw[12 * t2 + 4 * b + 3]};
+      R Sr = 0, Si = 0, Cr = 0, Ci = 0;
+      entry_from_pc(pc, sa, wa, sb, wb, mikr, miki, c4r, c4i, wantS, wantC, Sr, Si, Cr, Ci);
+      out.add(ea, eb, wantS, wantC, Sr, Si, Cr, Ci);
+      out.add(eb, ea, wantS, wantC, Sr, Si, Cr, Ci);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A5: BC assembly by dual-cell tiles (v, w), v <= w. Stage 1: pair
+// coefficients of every (tau1 in D(v), tau2 in D(w)) into shared memory;
+// stage 2: contract the trial side per (tau1, trial slot); stage 3: contract
+// the test side per (test slot, trial slot) and add to the output (and to
+// the mirrored entry when v != w).
+// ---------------------------------------------------------------------------
+struct TileList {
+  const int* cells;       // vertex ids of the scatterer (dense enumeration)
+  int64_t ncell;
+  const int2* tiles;      // explicit list (near field) or nullptr
+  int64_t ntile;
+};
+
+__device__ __forceinline__ void decode_upper(int64_t k, int64_t n, int64_t& i, int64_t& j) {
+  // k-th pair (i <= j) in row-major order of the upper triangle of an n x n grid
+  const double nn = 2.0 * n + 1.0;
+  int64_t r = (int64_t)floor((nn - sqrt(nn * nn - 8.0 * (double)k)) * 0.5);
+  if (r < 0) r = 0;
+  while (r > 0 && r * (2 * n - r + 1) / 2 > k) --r;
+  while ((r + 1) * (2 * n - r) / 2 <= k) ++r;
+  i = r;
+  j = r + (k - r * (2 * n - r + 1) / 2);
+}
+
+template <typename R, int NREG>
+__global__ void __launch_bounds__(128) bc_tile_kernel(
+    const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
+    const R* __restrict__ slot_sw, int nslot, const int* __restrict__ cell_ptr,
+    const int* __restrict__ cell_tri, TileList tl, R kr, R ki, R mikr, R miki, R c4r, R c4i,
+    bool wantS, bool wantC, Rules rl, Sink<R> out, int max_cell) {
+  using TRI = typename TriOf<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  R* pcs = reinterpret_cast<R*>(smem_raw);                          // [max_cell^2][36]
+  R* red = pcs + (size_t)max_cell * max_cell * 36;                  // [max_cell][nslot][18]
+  const int64_t ntiles = tl.tiles ? tl.ntile : tl.ncell * (tl.ncell + 1) / 2;
+  for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
+    int v, w;
+    if (tl.tiles) {
+      v = tl.tiles[k].x;
+      w = tl.tiles[k].y;
+    } else {
+      int64_t i, j;
+      decode_upper(k, tl.ncell, i, j);
+      v = tl.cells[i];
+      w = tl.cells[j];
+    }
+    const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
+    const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
+    // stage 1
+    for (int p = threadIdx.x; p < n1 * n2; p += blockDim.x) {
+      const int tau1 = cell_tri[b1 + p / n2], tau2 = cell_tri[b2 + p % n2];
+      const TRI A = tri[tau1];
+      const TRI B = tri[tau2];
+      R* pc = pcs + (size_t)p * 36;
+      if (touching(A, B)) {
+        for (int q = 0; q < 36; ++q) pc[q] = R(0);
+        continue;
+      }
+      V3<R> xi[NREG], eta[NREG];
+      R wx[NREG], wy[NREG];
+      load_points<NREG>(A, rl, xi, wx);
+      load_points<NREG>(B, rl, eta, wy);
+      const V3<R> D = centroid_delta(A, B);
+      Mom<R> m;
+      regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, wantC, m);
+      R tmp[36];
+      pair_coeffs(m, D, tmp);
+#pragma unroll
+      for (int q = 0; q < 36; ++q) pc[q] = tmp[q];
+    }
+    __syncthreads();
+    // number of valid slots of each cell
+    int ns1 = 0, ns2 = 0;
+    {
+      const int tv = cell_tri[b1], tw = cell_tri[b2];
+      while (ns1 < nslot && slot_edge[(size_t)tv * nslot + ns1] >= 0) ++ns1;
+      while (ns2 < nslot && slot_edge[(size_t)tw * nslot + ns2] >= 0) ++ns2;
+    }
+    // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side factors
+    for (int q = threadIdx.x; q < n1 * ns2; q += blockDim.x) {
+      const int i1 = q / ns2, sb_i = q % ns2;
+      R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0, AC_r = 0, AC_i = 0;
+      V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0}, WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
+      for (int i2 = 0; i2 < n2; ++i2) {
+        const int tau2 = cell_tri[b2 + i2];
+        const R* sw = slot_sw + ((size_t)tau2 * nslot + sb_i) * 4;
+        const R sb = sw[0];
+        const V3<R> wb = {sw[1], sw[2], sw[3]};
+        const R* pc = pcs + (size_t)(i1 * n2 + i2) * 36;
+        if (wantS) {
+          AS_r += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
+          AS_i += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
+          BS_r += sb * pc[0];
+          BS_i += sb * pc[1];
+          WS_r.x += sb * pc[8] + wb.x * pc[0]; WS_r.y += sb * pc[9] + wb.y * pc[0]; WS_r.z += sb * pc[10] + wb.z * pc[0];
+          WS_i.x += sb * pc[11] + wb.x * pc[1]; WS_i.y += sb * pc[12] + wb.y * pc[1]; WS_i.z += sb * pc[13] + wb.z * pc[1];
+        }
+        if (wantC) {
+          AC_r += sb * pc[16] + wb.x * pc[18] + wb.y * pc[19] + wb.z * pc[20];
+          AC_i += sb * pc[17] + wb.x * pc[21] + wb.y * pc[22] + wb.z * pc[23];
+          const V3<R> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
+          const V3<R> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
+          WC_r.x += sb * pc[24] + cr.x; WC_r.y += sb * pc[25] + cr.y; WC_r.z += sb * pc[26] + cr.z;
+          WC_i.x += sb * pc[27] + ci.x; WC_i.y += sb * pc[28] + ci.y; WC_i.z += sb * pc[29] + ci.z;
+        }
+      }
+      R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
+      o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
+      o[4] = WS_r.x; o[5] = WS_r.y; o[6] = WS_r.z; o[7] = WS_i.x; o[8] = WS_i.y; o[9] = WS_i.z;
+      o[10] = AC_r; o[11] = AC_i;
+      o[12] = WC_r.x; o[13] = WC_r.y; o[14] = WC_r.z; o[15] = WC_i.x; o[16] = WC_i.y; o[17] = WC_i.z;
+    }
+    __syncthreads();
+    // stage 3: per (test slot a, trial slot b), sum over tau1
+    for (int q = threadIdx.x; q < ns1 * ns2; q += blockDim.x) {
+      const int sa_i = q / ns2, sb_i = q % ns2;
+      R Sr = 0, Si = 0, Cr = 0, Ci = 0;
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const int tau1 = cell_tri[b1 + i1];
+        const R* sw = slot_sw + ((size_t)tau1 * nslot + sa_i) * 4;
+        const R sa = sw[0];
+        const V3<R> wa = {sw[1], sw[2], sw[3]};
+        const R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
+        if (wantS) {
+          // sa (mik AS + c4 BS) + mik (wa . WS)
+          const R pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
+          const R pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
+          Sr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
+          Si += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
+        }
+        if (wantC) {
+          Cr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
+          Ci += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
+        }
+      }
+      const int ea = slot_edge[(size_t)cell_tri[b1] * nslot + sa_i];
+      const int eb = slot_edge[(size_t)cell_tri[b2] * nslot + sb_i];
+      out.add(ea, eb, wantS, wantC, Sr, Si, Cr, Ci);
+      if (v != w) out.add(eb, ea, wantS, wantC, Sr, Si, Cr, Ci);
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A4: singular pairs by Sauter–Schwab rules in float64, one warp per ordered
+// pair; the q^4 Gauss points of all sub-regions are spread over the lanes.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ss_map(int cls, int r, double xi, double e1, double e2, double e3,
+                                       double* xh, double* yh, double& jac) {
+  // maps of [0,1]^4 onto pairs of points of the reference triangle
+  // {0 <= s2 <= s1 <= 1}; shared vertex at (0,0), shared edge (0,0)-(1,0)
+  if (cls == 3) {
+    jac = xi * xi * xi * e1 * e1 * e2;
+    switch (r) {
+      case 0: xh[0] = xi; xh[1] = xi * (1 - e1 + e1 * e2); yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * (1 - e1); break;
+      case 1: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * (1 - e1); yh[0] = xi; yh[1] = xi * (1 - e1 + e1 * e2); break;
+      case 2: xh[0] = xi; xh[1] = xi * e1 * (1 - e2 + e2 * e3); yh[0] = xi * (1 - e1 * e2); yh[1] = xi * e1 * (1 - e2); break;
+      case 3: xh[0] = xi * (1 - e1 * e2); xh[1] = xi * e1 * (1 - e2); yh[0] = xi; yh[1] = xi * e1 * (1 - e2 + e2 * e3); break;
+      case 4: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * (1 - e2 * e3); yh[0] = xi; yh[1] = xi * e1 * (1 - e2); break;
+      default: xh[0] = xi; xh[1] = xi * e1 * (1 - e2); yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * e1 * (1 - e2 * e3); break;
+    }
+  } else if (cls == 2) {
+    jac = xi * xi * xi * e1 * e1 * (r == 0 ? 1.0 : e2);
+    switch (r) {
+      case 0: xh[0] = xi; xh[1] = xi * e1 * e3; yh[0] = xi * (1 - e1 * e2); yh[1] = xi * e1 * (1 - e2); break;
+      case 1: xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * e1 * e2 * (1 - e3); break;
+      case 2: xh[0] = xi * (1 - e1 * e2); xh[1] = xi * e1 * (1 - e2); yh[0] = xi; yh[1] = xi * e1 * e2 * e3; break;
+      case 3: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * e2 * (1 - e3); yh[0] = xi; yh[1] = xi * e1; break;
+      default: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * (1 - e2 * e3); yh[0] = xi; yh[1] = xi * e1 * e2; break;
+    }
+  } else {
+    jac = xi * xi * xi * e2;
+    if (r == 0) { xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * e2; yh[1] = xi * e2 * e3; }
+    else { xh[0] = xi * e2; xh[1] = xi * e2 * e3; yh[0] = xi; yh[1] = xi * e1; }
+  }
+}
+
+template <typename RO>
+__global__ void __launch_bounds__(128) singular_kernel(
+    const TriD* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
+    const int* __restrict__ slot_edge, const double* __restrict__ slot_sw, int nslot, double kr,
+    double ki, double mikr, double miki, double c4r, double c4i, bool wantS, bool wantC,
+    Rules rl, Sink<RO> out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= np) return;
+  const SingPair sp = pairs[p];
+  const TriD A = tri[sp.t1];
+  const TriD B = tri[sp.t2];
+  const int cls = sp.cls;
+  const bool doC = wantC && cls != 3;  // flat identical panels: C vanishes
+  // parametrisation corners relative to each centroid
+  V3<double> Q1[3], Q2[3];
+  for (int a = 0; a < 3; ++a) {
+    Q1[a] = {A.off[sp.o1[a]][0], A.off[sp.o1[a]][1], A.off[sp.o1[a]][2]};
+    Q2[a] = {B.off[sp.o2[a]][0], B.off[sp.o2[a]][1], B.off[sp.o2[a]][2]};
+  }
+  const V3<double> D = {A.c[0] - B.c[0], A.c[1] - B.c[1], A.c[2] - B.c[2]};
+  const double scale = 4.0 * A.area * B.area;
+  const int ng = rl.ng, nreg = (cls == 3 ? 6 : (cls == 2 ? 5 : 2));
+  const int ng2 = ng * ng, ng4 = ng2 * ng2;
+  Mom<double> m;
+  m.zero();
+  for (int idx = lane; idx < nreg * ng4; idx += 32) {
+    const int r = idx / ng4;
+    int rem = idx - r * ng4;
+    const int a0 = rem / (ng2 * ng);
+    rem -= a0 * ng2 * ng;
+    const int a1 = rem / ng2;
+    rem -= a1 * ng2;
+    const int a2 = rem / ng, a3 = rem - a2 * ng;
+    double xh[2], yh[2], jac;
+    ss_map(cls, r, rl.gx[a0], rl.gx[a1], rl.gx[a2], rl.gx[a3], xh, yh, jac);
+    const double w = rl.gw[a0] * rl.gw[a1] * rl.gw[a2] * rl.gw[a3] * jac * scale;
+    const V3<double> x = {Q1[0].x + xh[0] * (Q1[1].x - Q1[0].x) + xh[1] * (Q1[2].x - Q1[1].x),
+                          Q1[0].y + xh[0] * (Q1[1].y - Q1[0].y) + xh[1] * (Q1[2].y - Q1[1].y),
+                          Q1[0].z + xh[0] * (Q1[1].z - Q1[0].z) + xh[1] * (Q1[2].z - Q1[1].z)};
+    const V3<double> y = {Q2[0].x + yh[0] * (Q2[1].x - Q2[0].x) + yh[1] * (Q2[2].x - Q2[1].x),
+                          Q2[0].y + yh[0] * (Q2[1].y - Q2[0].y) + yh[1] * (Q2[2].y - Q2[1].y),
+                          Q2[0].z + yh[0] * (Q2[1].z - Q2[0].z) + yh[1] * (Q2[2].z - Q2[1].z)};
+    const double dx = D.x + x.x - y.x, dy = D.y + x.y - y.y, dz = D.z + x.z - y.z;
+    double Gr, Gi, gr, gi;
+    green(dx * dx + dy * dy + dz * dz, kr, ki, Gr, Gi, gr, gi);
+    Gr *= w; Gi *= w; gr *= w; gi *= w;
+    m.G0r += Gr; m.G0i += Gi;
+    m.Gxr.x += Gr * x.x; m.Gxr.y += Gr * x.y; m.Gxr.z += Gr * x.z;
+    m.Gxi.x += Gi * x.x; m.Gxi.y += Gi * x.y; m.Gxi.z += Gi * x.z;
+    m.Gyr.x += Gr * y.x; m.Gyr.y += Gr * y.y; m.Gyr.z += Gr * y.z;
+    m.Gyi.x += Gi * y.x; m.Gyi.y += Gi * y.y; m.Gyi.z += Gi * y.z;
+    const double xy = dot3(x, y);
+    m.Gxyr += Gr * xy; m.Gxyi += Gi * xy;
+    if (doC) {
+      const V3<double> xy3 = cross3(x, y);
+      m.g0r += gr; m.g0i += gi;
+      m.gxr.x += gr * x.x; m.gxr.y += gr * x.y; m.gxr.z += gr * x.z;
+      m.gxi.x += gi * x.x; m.gxi.y += gi * x.y; m.gxi.z += gi * x.z;
+      m.gyr.x += gr * y.x; m.gyr.y += gr * y.y; m.gyr.z += gr * y.z;
+      m.gyi.x += gi * y.x; m.gyi.y += gi * y.y; m.gyi.z += gi * y.z;
+      m.gxyr.x += gr * xy3.x; m.gxyr.y += gr * xy3.y; m.gxyr.z += gr * xy3.z;
+      m.gxyi.x += gi * xy3.x; m.gxyi.y += gi * xy3.y; m.gxyi.z += gi * xy3.z;
+    }
+  }
+  // warp reduction of the 36 moment reals
+  double* mv = reinterpret_cast<double*>(&m);
+  constexpr int NM = sizeof(Mom<double>) / sizeof(double);
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    double v = mv[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    mv[q] = v;
+  }
+  double pc[36];
+  pair_coeffs(m, D, pc);
+  // lanes take the (test slot, trial slot) combinations
+  for (int q = lane; q < nslot * nslot; q += 32) {
+    const int a = q / nslot, b = q % nslot;
+    const int ea = slot_edge[(size_t)sp.t1 * nslot + a];
+    const int eb = slot_edge[(size_t)sp.t2 * nslot + b];
+    if (ea < 0 || eb < 0) continue;
+    const double* swa = slot_sw + ((size_t)sp.t1 * nslot + a) * 4;
+    const double* swb = slot_sw + ((size_t)sp.t2 * nslot + b) * 4;
+    const V3<double> wa = {swa[1], swa[2], swa[3]}, wb = {swb[1], swb[2], swb[3]};
+    double Sr = 0, Si = 0, Cr = 0, Ci = 0;
+    entry_from_pc(pc, swa[0], wa, swb[0], wb, mikr, miki, c4r, c4i, wantS, doC, Sr, Si, Cr, Ci);
+    out.add(ea, eb, wantS, doC, Sr, Si, Cr, Ci);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A6: Gram matrix G_ij = <BC_j, RWG_i> = int BC_j . (n x RWG_i). On a
+// barycentric triangle tau both are sigma (x - c_tau) + w with constant
+// sigma, w; since int_tau (x - c_tau) = 0 and (x-c).(n x (x-c)) = 0, the
+// integral is exactly |tau| w_BC . (n x w_RWG).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t csr_find(const int64_t* rowptr, const int* col, int row, int c) {
+  int64_t lo = rowptr[row], hi = rowptr[row + 1] - 1;
+  while (lo <= hi) {
+    int64_t mid = (lo + hi) >> 1;
+    if (col[mid] == c) return mid;
+    if (col[mid] < c) lo = mid + 1; else hi = mid - 1;
+  }
+  return -1;
+}
+
+__global__ void gram_kernel(const TriD* __restrict__ btri, const int* __restrict__ bslot_edge,
+                            const double* __restrict__ bslot_sw, int nslot,
+                            const int* __restrict__ parent, const TriD* __restrict__ ptri,
+                            const int* __restrict__ pslot_edge, const double* __restrict__ pslot_sw,
+                            int64_t ntau, const int64_t* rowptr, const int* col,
+                            const int64_t* rowptrT, const int* colT, double* vals, double* valsT) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ntau * nslot) return;
+  const int64_t tau = q / nslot;
+  const int sl = (int)(q % nslot);
+  const int j = bslot_edge[q];
+  if (j < 0) return;
+  const TriD T = btri[tau];
+  const double* swj = bslot_sw + q * 4;
+  const V3<double> wj = {swj[1], swj[2], swj[3]};
+  V3<double> u = {T.off[1][0] - T.off[0][0], T.off[1][1] - T.off[0][1], T.off[1][2] - T.off[0][2]};
+  V3<double> v = {T.off[2][0] - T.off[0][0], T.off[2][1] - T.off[0][1], T.off[2][2] - T.off[0][2]};
+  V3<double> n = cross3(u, v);
+  const double nn = sqrt(dot3(n, n));
+  n = {n.x / nn, n.y / nn, n.z / nn};
+  const int t = parent[tau];
+  const TriD P = ptri[t];
+  const V3<double> dc = {T.c[0] - P.c[0], T.c[1] - P.c[1], T.c[2] - P.c[2]};
+  for (int a = 0; a < 3; ++a) {
+    const int i = pslot_edge[3 * t + a];
+    const double* swi = pslot_sw + (3 * t + a) * 4;
+    const V3<double> wi = {swi[1] + swi[0] * dc.x, swi[2] + swi[0] * dc.y, swi[3] + swi[0] * dc.z};
+    const double val = T.area * dot3(wj, cross3(n, wi));
+    const int64_t k = csr_find(rowptr, col, i, j);
+    if (k >= 0) atomicAdd(vals + k, val);
+    const int64_t kt = csr_find(rowptrT, colT, j, i);
+    if (kt >= 0) atomicAdd(valsT + kt, val);
+  }
+  (void)sl;
+}
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+template <typename R>
+static void wave_scalars(double kr, double ki, R& mikr, R& miki, R& c4r, R& c4i) {
+  // -ik and 4i/k
+  mikr = (R)ki;
+  miki = (R)(-kr);
+  const double k2 = kr * kr + ki * ki;
+  c4r = (R)(4.0 * ki / k2);
+  c4i = (R)(4.0 * kr / k2);
+}
+
+template <typename R>
+static Sink<R> make_sink(const AssembleArgs& a) {
+  Sink<R> s;
+  s.S = reinterpret_cast<R*>(a.S);
+  s.C = reinterpret_cast<R*>(a.C);
+  s.off = a.row_off;
+  s.ld = (a.format == CAL_DENSE) ? a.ld : 0;
+  s.rowptr = a.rowptr;
+  s.col = a.col;
+  return s;
+}
+
+template <typename R>
+static int rwg_regular_t(const AssembleArgs& a) {
+  const Space& s = *a.sp;
+  const int64_t t0 = a.scat < 0 ? 0 : s.tri_off[a.scat];
+  const int64_t ntr = (a.scat < 0 ? s.ntri : s.tri_off[a.scat + 1]) - t0;
+  const int64_t nb = (ntr + 15) / 16;
+  if (nb > 65535) return fail(CAL_EINVAL, "too many triangles for the regular-pair grid (%lld)", (long long)ntr);
+  R mikr, miki, c4r, c4i;
+  wave_scalars(a.kr, a.ki, mikr, miki, c4r, c4i);
+  dim3 grid((unsigned)nb, (unsigned)nb), block(16, 16);
+  const Sink<R> out = make_sink<R>(a);
+  const bool wS = a.want & 1, wC = a.want & 2;
+  const typename TriOf<R>::T* tri;
+  const R* sw;
+  if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
+  else { tri = s.d_triD; sw = s.d_slot_swd; }
+  if (a.nreg == 6)
+    rwg_regular_kernel<R, 6><<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki,
+                                                            mikr, miki, c4r, c4i, wS, wC, g_rules, out);
+  else
+    rwg_regular_kernel<R, 1><<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki,
+                                                            mikr, miki, c4r, c4i, wS, wC, g_rules, out);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int launch_rwg_regular(const AssembleArgs& a) {
+  return a.precision == CAL_FP32 ? rwg_regular_t<float>(a) : rwg_regular_t<double>(a);
+}
+
+struct BcTiles {
+  int* d_cells = nullptr;
+  int2* d_tiles = nullptr;
+};
+
+template <typename R>
+static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
+                        int64_t ntile, int max_cell, int n_sm) {
+  const Space& s = *a.sp;
+  R mikr, miki, c4r, c4i;
+  wave_scalars(a.kr, a.ki, mikr, miki, c4r, c4i);
+  const Sink<R> out = make_sink<R>(a);
+  const bool wS = a.want & 1, wC = a.want & 2;
+  TileList tl{cells, ncell, tiles, ntile};
+  const int64_t ntiles = tiles ? ntile : ncell * (ncell + 1) / 2;
+  if (ntiles == 0) return CAL_OK;
+  const size_t smem = ((size_t)max_cell * max_cell * 36 + (size_t)max_cell * s.nslot * 18) * sizeof(R);
+  if (smem > 227 * 1024) return fail(CAL_EINVAL, "dual cell too large for the tile kernel (%d triangles)", max_cell);
+  const typename TriOf<R>::T* tri;
+  const R* sw;
+  if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
+  else { tri = s.d_triD; sw = s.d_slot_swd; }
+  auto kern6 = bc_tile_kernel<R, 6>;
+  auto kern1 = bc_tile_kernel<R, 1>;
+  auto kern = a.nreg == 6 ? kern6 : kern1;
+  CAL_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * n_sm * 4);
+  kern<<<(unsigned)grid, 128, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr,
+                                                s.d_cell_tri, tl, (R)a.kr, (R)a.ki, mikr, miki, c4r,
+                                                c4i, wS, wC, g_rules, out, max_cell);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int launch_bc_regular_tiles(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
+                            int64_t ntile, int max_cell, int n_sm) {
+  return a.precision == CAL_FP32 ? bc_regular_t<float>(a, cells, ncell, tiles, ntile, max_cell, n_sm)
+                                 : bc_regular_t<double>(a, cells, ncell, tiles, ntile, max_cell, n_sm);
+}
+
+int launch_singular(const AssembleArgs& a) {
+  const Space& s = *a.sp;
+  double mikr, miki, c4r, c4i;
+  wave_scalars(a.kr, a.ki, mikr, miki, c4r, c4i);
+  const bool wS = a.want & 1, wC = a.want & 2;
+  const int d0 = a.scat < 0 ? 0 : a.scat;
+  const int d1 = a.scat < 0 ? (int)s.sing.size() : a.scat + 1;
+  for (int d = d0; d < d1; ++d) {
+    const int64_t np = (int64_t)s.sing[d].size();
+    if (np == 0) continue;
+    const unsigned grid = (unsigned)((np + 3) / 4);
+    if (a.precision == CAL_FP32)
+      singular_kernel<float><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
+                                                         s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,
+                                                         c4r, c4i, wS, wC, g_rules, make_sink<float>(a));
+    else
+      singular_kernel<double><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
+                                                          s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,
+                                                          c4r, c4i, wS, wC, g_rules, make_sink<double>(a));
+    CAL_TRY_CUDA(cudaGetLastError());
+  }
+  return CAL_OK;
+}
+
+int launch_gram(const Space& rwg, const Space& bc, const int64_t* rowptr, const int* col,
+                const int64_t* rowptrT, const int* colT, double* vals, double* valsT,
+                cudaStream_t stream) {
+  int* d_parent = nullptr;
+  CAL_TRY_CUDA(cudaMallocAsync((void**)&d_parent, bc.parent.size() * sizeof(int), stream));
+  CAL_TRY_CUDA(cudaMemcpyAsync(d_parent, bc.parent.data(), bc.parent.size() * sizeof(int),
+                               cudaMemcpyHostToDevice, stream));
+  const int64_t n = bc.ntri * bc.nslot;
+  gram_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
+      bc.d_triD, bc.d_slot_edge, bc.d_slot_swd, bc.nslot, d_parent, rwg.d_triD, rwg.d_slot_edge,
+      rwg.d_slot_swd, bc.ntri, rowptr, col, rowptrT, colT, vals, valsT);
+  CAL_TRY_CUDA(cudaGetLastError());
+  CAL_TRY_CUDA(cudaFreeAsync(d_parent, stream));
+  return CAL_OK;
+}
+
+}  // namespace cal

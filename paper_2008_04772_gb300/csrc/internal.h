@@ -1,0 +1,173 @@
+// Internal declarations of the GB300 PMCHWT library (not part of the C ABI).
+//
+// Every basis function (RWG on primal triangles, BC on barycentric ones) is
+// stored per triangle tau as "slots": on tau it equals sigma * (x - c_tau) + w,
+// with c_tau the centroid, so div = 2 sigma (Section 3.2 spaces, lowest-order
+// Raviart–Thomas pieces). A triangle carries up to `nslot` such pieces, each
+// tagged with its global basis (edge) index, or -1 for an empty slot.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "cal.h"
+
+namespace cal {
+
+// ---- errors ----------------------------------------------------------------
+void set_error(const char* fmt, ...);
+int fail(int code, const char* fmt, ...);
+#define CAL_TRY_CUDA(expr)                                                    \
+  do {                                                                        \
+    cudaError_t _e = (expr);                                                  \
+    if (_e != cudaSuccess)                                                    \
+      return ::cal::fail(CAL_ECUDA, "%s: %s (%s:%d)", #expr,                  \
+                         cudaGetErrorString(_e), __FILE__, __LINE__);         \
+  } while (0)
+
+// ---- device records ----------------------------------------------------------
+// float32 triangle: centroid as hi + lo float pair, vertex offsets from it.
+struct __align__(16) TriF {
+  float chi[3], clo[3];
+  float off[3][3];
+  float area;
+  int vid[3];
+  int pad;
+};
+struct __align__(16) TriD {
+  double c[3];
+  double off[3][3];
+  double area;
+  int vid[3];
+  int pad;
+};
+
+// ordered singular pair (shares >= 1 vertex id) with Sauter–Schwab vertex orders:
+// shared vertices first (in the test triangle's storage order), the rest after
+struct SingPair {
+  int t1, t2;
+  signed char cls;      // 1 vertex, 2 edge, 3 identical
+  signed char o1[3], o2[3];
+  signed char pad;
+};
+
+// ---- host objects --------------------------------------------------------------
+struct Ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  int n_sm = 0;
+};
+
+struct Mesh {
+  Ctx* ctx = nullptr;
+  int64_t nv = 0, nt = 0, ne = 0, M = 0;
+  std::vector<double> X;         // [nv][3]
+  std::vector<int> T;            // [nt][3], triangles grouped by scatterer
+  std::vector<int> dom;          // [nt]
+  std::vector<int> e_lo, e_hi, e_dom, e_tp, e_ap, e_tm, e_am;
+  std::vector<double> e_len;
+  std::vector<int> tri_edge;     // [nt][3]: edge opposite local vertex a
+  std::vector<int> tri_sign;     // [nt][3]: +1 if the triangle is T+ of that edge
+  std::vector<int64_t> tri_off, edge_off, vert_lo, vert_hi;  // per scatterer ranges
+  std::vector<int> valence;      // edges per vertex
+  double h = 0.0;
+  int max_valence = 0;
+};
+
+struct Space {
+  Mesh* mesh = nullptr;
+  int kind = 0;
+  int64_t ntri = 0, nbasis = 0;
+  int nslot = 0;
+  std::vector<TriD> triD;        // host master copy
+  std::vector<int> slot_edge;    // [ntri][nslot]
+  std::vector<double> slot_sw;   // [ntri][nslot][4] = sigma, w
+  std::vector<int> parent;       // BC: primal parent triangle of each tau
+  // dual cells (BC): barycentric triangles and edges of each primal vertex
+  std::vector<int> cell_tri_ptr, cell_tri, cell_edge_ptr, cell_edge;
+  // support bounding boxes per basis
+  std::vector<double> box_lo, box_hi;  // [nbasis][3]
+  // triangle ranges per scatterer
+  std::vector<int64_t> tri_off;
+  // singular ordered pairs per scatterer
+  std::vector<std::vector<SingPair>> sing;
+  // device copies
+  TriF* d_triF = nullptr;
+  TriD* d_triD = nullptr;
+  int* d_slot_edge = nullptr;
+  float* d_slot_swf = nullptr;
+  double* d_slot_swd = nullptr;
+  int* d_cell_tri_ptr = nullptr;
+  int* d_cell_tri = nullptr;
+  std::vector<SingPair*> d_sing;
+  ~Space();
+};
+
+struct Op {
+  Ctx* ctx = nullptr;
+  int op_mask = 0, precision = 0, format = 0;
+  int64_t rows = 0, cols = 0, nnz = 0;
+  int64_t row_offset = 0;
+  void* d_S = nullptr;           // dense [rows][cols] or CSR values
+  void* d_C = nullptr;
+  int64_t* d_rowptr = nullptr;   // CSR
+  int* d_col = nullptr;
+  std::vector<int64_t> h_rowptr; // CSR pattern on the host
+  std::vector<int> h_col;
+  ~Op();
+};
+
+// ---- host construction (host.cpp) ----------------------------------------------
+int build_mesh(Mesh& m, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+               const int32_t* domain);
+int build_rwg(Space& s, Mesh& m);
+int build_bc(Space& s, Mesh& m);
+void build_singular_pairs(Space& s);
+// near-field CSR pattern within one scatterer block: keep (i,j) iff the
+// support boxes are at most chi apart; local indices (edge - edge_off)
+void near_pattern(const Space& s, int scat, double chi, std::vector<int64_t>& rowptr,
+                  std::vector<int>& col);
+// Gram pattern (rows RWG edges, cols BC edges), CSR
+void gram_pattern(const Space& bc, std::vector<int64_t>& rowptr, std::vector<int>& col);
+int upload_space(Space& s);
+
+// quadrature tables (host.cpp): Gauss–Legendre on [0,1] by Newton iteration on
+// Legendre polynomials; the symmetric degree-4 six-point triangle rule from its
+// closed form; the centroid rule.
+void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w);
+void triangle_rule(int npts, std::vector<double>& bary, std::vector<double>& w);
+
+// ---- device launches (assemble.cu) --------------------------------------------
+struct AssembleArgs {
+  const Space* sp;
+  int scat;             // -1 = union
+  double kr, ki;
+  int want;             // bit 1 S, bit 2 C
+  int nreg, nsing;      // regular points per triangle, GL points per dimension
+  int precision;
+  int format;
+  // dense output
+  int64_t row_off, ld;
+  // CSR output (local indices)
+  const int64_t* rowptr;
+  const int* col;
+  void* S;
+  void* C;
+  cudaStream_t stream;
+};
+int set_quadrature_tables(int nreg, int nsing);
+int launch_rwg_regular(const AssembleArgs& a);
+int launch_singular(const AssembleArgs& a);
+int launch_gram(const Space& rwg, const Space& bc, const int64_t* rowptr, const int* col,
+                const int64_t* rowptrT, const int* colT, double* vals, double* valsT,
+                cudaStream_t stream);
+
+}  // namespace cal
+
+struct cal_ctx { cal::Ctx impl; };
+struct cal_mesh { cal::Mesh impl; };
+struct cal_space { cal::Space impl; };
+struct cal_op { cal::Op impl; };

@@ -1,0 +1,905 @@
+// Operator application, Gram solves, GMRES, right-hand side and far field.
+//
+// arXiv 2008.04772: the block operator of eqs. multiple_operator / AimAem, the
+// strong form M_P^-1 P M_A^-1 A of Section 3.2 (eqs. GalA-MassP), restarted
+// GMRES of Section 4, the incident traces of eq. boundary_conditions_traces and
+// the far field of the Stratton–Chu representation (eq. StrattonChu_ext).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "solve.h"
+
+namespace cal {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename R> struct CT;
+template <> struct CT<float> { using T = float2; };
+template <> struct CT<double> { using T = double2; };
+
+template <typename A, typename B>
+__device__ __forceinline__ void cfma(A& acc, const B& a, const B& b) {
+  acc.x += (decltype(acc.x))a.x * b.x - (decltype(acc.x))a.y * b.y;
+  acc.y += (decltype(acc.x))a.x * b.y + (decltype(acc.x))a.y * b.x;
+}
+
+// ---------------------------------------------------------------------------
+// A7: one (S, C) block of the PMCHWT operator applied to both halves of x:
+//   y1[r] += sum C x1 + alpha sum S x2,  y2[r] += sum C x2 + beta sum S x1
+// with x, y component-major. Each matrix element is read once per
+// application; a warp owns ROWS rows and its lanes stride over columns.
+// ---------------------------------------------------------------------------
+template <typename MT, typename VT, typename AT, int ROWS>
+__global__ void __launch_bounds__(256) pair_gemv_kernel(
+    const MT* __restrict__ S, const MT* __restrict__ C, int64_t nr, int64_t nc, int64_t ld,
+    const VT* __restrict__ x1, const VT* __restrict__ x2, VT* __restrict__ y1,
+    VT* __restrict__ y2, double ar, double ai, double br, double bi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t r0 = warp * ROWS;
+  if (r0 >= nr) return;
+  AT cx1[ROWS], cx2[ROWS], sx1[ROWS], sx2[ROWS];
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) cx1[q] = cx2[q] = sx1[q] = sx2[q] = AT{0, 0};
+  for (int64_t c = lane; c < nc; c += 32) {
+    const VT u = x1[c], v = x2[c];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      const int64_t r = r0 + q;
+      if (r < nr) {
+        if (C) {
+          const MT m = C[r * ld + c];
+          cfma(cx1[q], m, MT{(decltype(m.x))u.x, (decltype(m.x))u.y});
+          cfma(cx2[q], m, MT{(decltype(m.x))v.x, (decltype(m.x))v.y});
+        }
+        if (S) {
+          const MT m = S[r * ld + c];
+          cfma(sx1[q], m, MT{(decltype(m.x))u.x, (decltype(m.x))u.y});
+          cfma(sx2[q], m, MT{(decltype(m.x))v.x, (decltype(m.x))v.y});
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cx1[q].x += __shfl_xor_sync(0xffffffffu, cx1[q].x, o);
+      cx1[q].y += __shfl_xor_sync(0xffffffffu, cx1[q].y, o);
+      cx2[q].x += __shfl_xor_sync(0xffffffffu, cx2[q].x, o);
+      cx2[q].y += __shfl_xor_sync(0xffffffffu, cx2[q].y, o);
+      sx1[q].x += __shfl_xor_sync(0xffffffffu, sx1[q].x, o);
+      sx1[q].y += __shfl_xor_sync(0xffffffffu, sx1[q].y, o);
+      sx2[q].x += __shfl_xor_sync(0xffffffffu, sx2[q].x, o);
+      sx2[q].y += __shfl_xor_sync(0xffffffffu, sx2[q].y, o);
+    }
+    const int64_t r = r0 + q;
+    if (lane == 0 && r < nr) {
+      // y1 += C x1 + alpha S x2 ; y2 += C x2 + beta S x1
+      VT a = y1[r], b = y2[r];
+      a.x += cx1[q].x + ar * sx2[q].x - ai * sx2[q].y;
+      a.y += cx1[q].y + ar * sx2[q].y + ai * sx2[q].x;
+      b.x += cx2[q].x + br * sx1[q].x - bi * sx1[q].y;
+      b.y += cx2[q].y + br * sx1[q].y + bi * sx1[q].x;
+      y1[r] = a;
+      y2[r] = b;
+    }
+  }
+}
+
+// CSR variant (near-field P): S and C share the pattern; warp per row
+template <typename MT, typename VT, typename AT>
+__global__ void pair_spmv_kernel(const MT* __restrict__ S, const MT* __restrict__ C,
+                                 const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                 int64_t nr, const VT* __restrict__ x1, const VT* __restrict__ x2,
+                                 VT* __restrict__ y1, VT* __restrict__ y2, double ar, double ai,
+                                 double br, double bi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nr) return;
+  AT cx1{0, 0}, cx2{0, 0}, sx1{0, 0}, sx2{0, 0};
+  for (int64_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) {
+    const int c = col[k];
+    const VT u = x1[c], v = x2[c];
+    if (C) {
+      const MT m = C[k];
+      cfma(cx1, m, MT{(decltype(m.x))u.x, (decltype(m.x))u.y});
+      cfma(cx2, m, MT{(decltype(m.x))v.x, (decltype(m.x))v.y});
+    }
+    if (S) {
+      const MT m = S[k];
+      cfma(sx1, m, MT{(decltype(m.x))u.x, (decltype(m.x))u.y});
+      cfma(sx2, m, MT{(decltype(m.x))v.x, (decltype(m.x))v.y});
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cx1.x += __shfl_xor_sync(0xffffffffu, cx1.x, o); cx1.y += __shfl_xor_sync(0xffffffffu, cx1.y, o);
+    cx2.x += __shfl_xor_sync(0xffffffffu, cx2.x, o); cx2.y += __shfl_xor_sync(0xffffffffu, cx2.y, o);
+    sx1.x += __shfl_xor_sync(0xffffffffu, sx1.x, o); sx1.y += __shfl_xor_sync(0xffffffffu, sx1.y, o);
+    sx2.x += __shfl_xor_sync(0xffffffffu, sx2.x, o); sx2.y += __shfl_xor_sync(0xffffffffu, sx2.y, o);
+  }
+  if (lane == 0) {
+    VT a = y1[r], b = y2[r];
+    a.x += cx1.x + ar * sx2.x - ai * sx2.y;
+    a.y += cx1.y + ar * sx2.y + ai * sx2.x;
+    b.x += cx2.x + br * sx1.x - bi * sx1.y;
+    b.y += cx2.y + br * sx1.y + bi * sx1.x;
+    y1[r] = a;
+    y2[r] = b;
+  }
+}
+
+// plain y = X x for one dense operator (C-ABI cal_matvec)
+template <typename MT>
+__global__ void gemv_kernel(const MT* __restrict__ X, int64_t nr, int64_t nc, const MT* __restrict__ x,
+                            MT* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nr) return;
+  double2 acc{0, 0};
+  for (int64_t c = lane; c < nc; c += 32) cfma(acc, X[r * nc + c], x[c]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) y[r] = MT{(decltype(y[r].x))acc.x, (decltype(y[r].x))acc.y};
+}
+
+template <typename MT>
+__global__ void spmv_kernel(const MT* __restrict__ X, const int64_t* __restrict__ rowptr,
+                            const int* __restrict__ col, int64_t nr, const MT* __restrict__ x,
+                            MT* __restrict__ y) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= nr) return;
+  double2 acc{0, 0};
+  for (int64_t k = rowptr[r] + lane; k < rowptr[r + 1]; k += 32) cfma(acc, X[k], x[col[k]]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
+  }
+  if (lane == 0) y[r] = MT{(decltype(y[r].x))acc.x, (decltype(y[r].x))acc.y};
+}
+
+// ---------------------------------------------------------------------------
+// elementwise helpers
+// ---------------------------------------------------------------------------
+template <typename A, typename B>
+__global__ void convert_kernel(const A* __restrict__ a, B* __restrict__ b, int64_t n, double scale) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = B{(decltype(b[i].x))(a[i].x * scale), (decltype(b[i].x))(a[i].y * scale)};
+}
+
+template <typename T>
+__global__ void zero_kernel(T* a, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) a[i] = T{0, 0};
+}
+
+static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// A6: BiCGStab on the real sparse Gram matrix for nsys complex systems that
+// share it (x, b: [nsys][n]); three kernels per iteration, scalars rebuilt in
+// every thread from float64 accumulators double-buffered by iteration parity.
+// acc layout per (parity, system): 0-1 r0^H v, 2-3 t^H s, 4 t^H t,
+// 5-6 r0^H r (next rho), 7 r^H r.
+// ---------------------------------------------------------------------------
+template <typename R>
+struct BiArgs {
+  const int64_t* rowptr;
+  const int* col;
+  const R* val;
+  int64_t n;
+  int nsys;
+  double neg;        // multiply the solution by this (M_P = -G^T)
+  typename CT<R>::T *x, *r, *r0, *p0, *p1, *v0, *v1, *t;
+  double* acc;       // [2][nsys][8]
+  int* done;         // [nsys]
+  double tol2;       // tol^2
+  double* bnorm2;    // [nsys]
+};
+
+__device__ __forceinline__ double* ACC(double* acc, int nsys, int par, int s) { return acc + ((size_t)par * nsys + s) * 8; }
+
+__device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
+  const double d = br * br + bi * bi;
+  cr = (ar * br + ai * bi) / d;
+  ci = (ai * br - ar * bi) / d;
+}
+
+template <int NV>
+__device__ __forceinline__ void block_accumulate(double (&v)[NV], double* dst) {
+  __shared__ double sh[NV][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double a = v[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) sh[q][wid] = a;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = lane < nw ? sh[q][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0 && a != 0.0) atomicAdd(dst + q, a);
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__global__ void bicg_init(BiArgs<R> A, const typename CT<R>::T* __restrict__ b) {
+  // x = 0, r = r0 = b, p = v = 0; rho_0 = b^H b stored as "next rho" of parity 1
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  double part[1] = {0.0};
+  if (i < A.n) {
+    const int64_t k = (int64_t)s * A.n + i;
+    const auto bv = b[k];
+    A.x[k] = {0, 0};
+    A.r[k] = bv;
+    A.r0[k] = bv;
+    A.p0[k] = A.p1[k] = A.v0[k] = A.v1[k] = {0, 0};
+    part[0] = (double)bv.x * bv.x + (double)bv.y * bv.y;
+  }
+  block_accumulate<1>(part, A.bnorm2 + s);
+}
+
+template <typename R>
+__global__ void bicg_init2(BiArgs<R> A) {
+  const int s = threadIdx.x;
+  if (s >= A.nsys) return;
+  for (int par = 0; par < 2; ++par)
+    for (int q = 0; q < 8; ++q) ACC(A.acc, A.nsys, par, s)[q] = 0.0;
+  ACC(A.acc, A.nsys, 1, s)[5] = A.bnorm2[s];
+  ACC(A.acc, A.nsys, 1, s)[7] = A.bnorm2[s];
+  A.done[s] = A.bnorm2[s] == 0.0;
+}
+
+// K1: p_k = r_k + beta (p_{k-1} - omega_{k-1} v_{k-1});  v_k = G p_k;  acc r0^H v
+template <typename R>
+__global__ void bicg_k1(BiArgs<R> A, int k) {
+  const int s = blockIdx.y;
+  const int P = k & 1;
+  double* a = ACC(A.acc, A.nsys, P, s);
+  double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+  if (A.done[s]) return;
+  // convergence of r_k: r^H r from the previous K3 (or b^H b)
+  if (ap[7] <= A.tol2 * A.bnorm2[s]) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) A.done[s] = 1;
+    return;
+  }
+  double br = 0.0, bi = 0.0, omr = 1.0, omi = 0.0;
+  if (k > 0) {
+    // beta = (rho_k / rho_{k-1}) (alpha_{k-1} / omega_{k-1})
+    double rr, ri, alr, ali;
+    cdiv(ap[5], ap[6], a[5], a[6], rr, ri);           // rho_k / rho_{k-1}
+    cdiv(a[5], a[6], ap[0], ap[1], alr, ali);         // alpha_{k-1} = rho_{k-1}/(r0^H v_{k-1})
+    cdiv(ap[2], ap[3], ap[4], 0.0, omr, omi);         // omega_{k-1}
+    double tr, ti;
+    cdiv(alr, ali, omr, omi, tr, ti);
+    br = rr * tr - ri * ti;
+    bi = rr * ti + ri * tr;
+  }
+  const auto* pprev = (P ? A.p0 : A.p1) + (size_t)s * A.n;  // p_{k-1}
+  const auto* vprev = (P ? A.v0 : A.v1) + (size_t)s * A.n;
+  auto* pcur = (P ? A.p1 : A.p0) + (size_t)s * A.n;
+  auto* vcur = (P ? A.v1 : A.v0) + (size_t)s * A.n;
+  const auto* r = A.r + (size_t)s * A.n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double part[2] = {0.0, 0.0};
+  auto pj = [&](int64_t j) {
+    const auto pp = pprev[j], vv = vprev[j], rj = r[j];
+    const double dx = pp.x - (omr * vv.x - omi * vv.y), dy = pp.y - (omr * vv.y + omi * vv.x);
+    return double2{rj.x + br * dx - bi * dy, rj.y + br * dy + bi * dx};
+  };
+  if (i < A.n) {
+    const double2 pi_ = pj(i);
+    pcur[i] = {(R)pi_.x, (R)pi_.y};
+    double vr = 0, vi = 0;
+    for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+      const double2 pc = pj(A.col[q]);
+      vr += (double)A.val[q] * pc.x;
+      vi += (double)A.val[q] * pc.y;
+    }
+    vcur[i] = {(R)vr, (R)vi};
+    const auto rh = A.r0[(size_t)s * A.n + i];
+    part[0] = (double)rh.x * vr + (double)rh.y * vi;   // conj(r0) v
+    part[1] = (double)rh.x * vi - (double)rh.y * vr;
+  }
+  block_accumulate<2>(part, a + 0);
+}
+
+// K2: alpha = rho_k / (r0^H v_k); s = r - alpha v; t = G s; acc t^H s, t^H t
+template <typename R>
+__global__ void bicg_k2(BiArgs<R> A, int k) {
+  const int s = blockIdx.y;
+  const int P = k & 1;
+  double* a = ACC(A.acc, A.nsys, P, s);
+  double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+  if (A.done[s]) return;
+  if (threadIdx.x == 0 && blockIdx.x == 0) { a[5] = a[6] = a[7] = 0.0; }
+  if (a[0] == 0.0 && a[1] == 0.0) return;
+  double alr, ali;
+  cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
+  const auto* vcur = (P ? A.v1 : A.v0) + (size_t)s * A.n;
+  const auto* r = A.r + (size_t)s * A.n;
+  auto* t = A.t + (size_t)s * A.n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double part[3] = {0, 0, 0};
+  auto sj = [&](int64_t j) {
+    const auto vv = vcur[j], rj = r[j];
+    return double2{rj.x - (alr * vv.x - ali * vv.y), rj.y - (alr * vv.y + ali * vv.x)};
+  };
+  if (i < A.n) {
+    double tr = 0, ti = 0;
+    for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+      const double2 sc = sj(A.col[q]);
+      tr += (double)A.val[q] * sc.x;
+      ti += (double)A.val[q] * sc.y;
+    }
+    t[i] = {(R)tr, (R)ti};
+    const double2 si = sj(i);
+    part[0] = tr * si.x + ti * si.y;   // conj(t) s
+    part[1] = tr * si.y - ti * si.x;
+    part[2] = tr * tr + ti * ti;
+  }
+  block_accumulate<3>(part, a + 2);
+}
+
+// K3: omega = t^H s / t^H t; x += alpha p + omega s; r = s - omega t; acc rho, r^H r
+template <typename R>
+__global__ void bicg_k3(BiArgs<R> A, int k) {
+  const int s = blockIdx.y;
+  const int P = k & 1;
+  double* a = ACC(A.acc, A.nsys, P, s);
+  double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+  if (A.done[s]) return;
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    for (int q = 0; q < 5; ++q) ap[q] = 0.0;   // parity P^1 is free for iteration k+1
+  }
+  if ((a[0] == 0.0 && a[1] == 0.0) || a[4] == 0.0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) A.done[s] = 1;
+    return;
+  }
+  double alr, ali, omr, omi;
+  cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
+  cdiv(a[2], a[3], a[4], 0.0, omr, omi);
+  const auto* pcur = (P ? A.p1 : A.p0) + (size_t)s * A.n;
+  const auto* vcur = (P ? A.v1 : A.v0) + (size_t)s * A.n;
+  auto* x = A.x + (size_t)s * A.n;
+  auto* r = A.r + (size_t)s * A.n;
+  const auto* t = A.t + (size_t)s * A.n;
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double part[3] = {0, 0, 0};
+  if (i < A.n) {
+    const auto vv = vcur[i], ri = r[i], pp = pcur[i], tt = t[i];
+    const double sx = ri.x - (alr * vv.x - ali * vv.y), sy = ri.y - (alr * vv.y + ali * vv.x);
+    auto xi = x[i];
+    const double nx = xi.x + (alr * pp.x - ali * pp.y) + (omr * sx - omi * sy);
+    const double ny = xi.y + (alr * pp.y + ali * pp.x) + (omr * sy + omi * sx);
+    x[i] = {(R)nx, (R)ny};
+    const double rx = sx - (omr * tt.x - omi * tt.y), ry = sy - (omr * tt.y + omi * tt.x);
+    r[i] = {(R)rx, (R)ry};
+    const auto rh = A.r0[(size_t)s * A.n + i];
+    part[0] = (double)rh.x * rx + (double)rh.y * ry;
+    part[1] = (double)rh.x * ry - (double)rh.y * rx;
+    part[2] = rx * rx + ry * ry;
+  }
+  block_accumulate<3>(part, a + 5);
+}
+
+template <typename R>
+__global__ void bicg_finish(BiArgs<R> A, typename CT<R>::T* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int s = blockIdx.y;
+  if (i < A.n) {
+    const auto v = A.x[(size_t)s * A.n + i];
+    out[(size_t)s * A.n + i] = {(R)(A.neg * v.x), (R)(A.neg * v.y)};
+  }
+}
+
+template <typename R>
+int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n_,
+                        int nsys_, int64_t nnz, double neg_, double tol_, int maxit_) {
+  n = n_;
+  nsys = nsys_;
+  neg = neg_;
+  tol = tol_;
+  maxit = maxit_;
+  d_rowptr = rowptr;
+  d_col = col;
+  const size_t vb = (size_t)n * nsys * sizeof(C);
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_val, nnz * sizeof(R)));
+  if (sizeof(R) == 8) {
+    CAL_TRY_CUDA(cudaMemcpy(d_val, vals_dev, nnz * sizeof(R), cudaMemcpyDeviceToDevice));
+  } else {
+    std::vector<double> h(nnz);
+    std::vector<R> hf(nnz);
+    CAL_TRY_CUDA(cudaMemcpy(h.data(), vals_dev, nnz * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < nnz; ++q) hf[q] = (R)h[q];
+    CAL_TRY_CUDA(cudaMemcpy(d_val, hf.data(), nnz * sizeof(R), cudaMemcpyHostToDevice));
+  }
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_work, 8 * vb));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_acc, (2 * nsys * 8 + nsys) * sizeof(double)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_done, nsys * sizeof(int)));
+  return CAL_OK;
+}
+
+template <typename R>
+GramSolver<R>::~GramSolver() {
+  cudaFree(d_val);
+  cudaFree(d_work);
+  cudaFree(d_acc);
+  cudaFree(d_done);
+}
+
+template <typename R>
+int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
+  BiArgs<R> A;
+  A.rowptr = d_rowptr;
+  A.col = d_col;
+  A.val = d_val;
+  A.n = n;
+  A.nsys = nsys;
+  A.neg = neg;
+  const size_t nv = (size_t)n * nsys;
+  A.x = d_work; A.r = d_work + nv; A.r0 = d_work + 2 * nv; A.p0 = d_work + 3 * nv;
+  A.p1 = d_work + 4 * nv; A.v0 = d_work + 5 * nv; A.v1 = d_work + 6 * nv; A.t = d_work + 7 * nv;
+  A.acc = d_acc;
+  A.bnorm2 = d_acc + 2 * nsys * 8;
+  A.done = d_done;
+  A.tol2 = tol * tol;
+  const dim3 grid(blocks_for(n, 256), nsys);
+  CAL_TRY_CUDA(cudaMemsetAsync(A.bnorm2, 0, nsys * sizeof(double), st));
+  bicg_init<R><<<grid, 256, 0, st>>>(A, b);
+  bicg_init2<R><<<1, 32 * ((nsys + 31) / 32), 0, st>>>(A);
+  for (int k = 0; k < maxit; ++k) {
+    bicg_k1<R><<<grid, 256, 0, st>>>(A, k);
+    bicg_k2<R><<<grid, 256, 0, st>>>(A, k);
+    bicg_k3<R><<<grid, 256, 0, st>>>(A, k);
+  }
+  bicg_finish<R><<<grid, 256, 0, st>>>(A, out);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+template struct GramSolver<float>;
+template struct GramSolver<double>;
+
+// ---------------------------------------------------------------------------
+// launch wrappers for the operator application
+// ---------------------------------------------------------------------------
+template <typename MT, typename VT, typename AT>
+static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double ar, double ai,
+                        double br, double bi, cudaStream_t st) {
+  const VT* x1 = x + b.col_off;
+  const VT* x2 = x + n + b.col_off;
+  VT* y1 = y + b.row_off;
+  VT* y2 = y + n + b.row_off;
+  const MT* S = reinterpret_cast<const MT*>(b.S);
+  const MT* C = reinterpret_cast<const MT*>(b.C);
+  if (b.rowptr) {
+    pair_spmv_kernel<MT, VT, AT><<<blocks_for(b.rows * 32, 256), 256, 0, st>>>(
+        S, C, b.rowptr, b.col, b.rows, x1, x2, y1, y2, ar, ai, br, bi);
+  } else {
+    constexpr int ROWS = 4;
+    const int64_t warps = (b.rows + ROWS - 1) / ROWS;
+    pair_gemv_kernel<MT, VT, AT, ROWS><<<blocks_for(warps * 32, 256), 256, 0, st>>>(
+        S, C, b.rows, b.cols, b.cols, x1, x2, y1, y2, ar, ai, br, bi);
+  }
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int pair_apply(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, double ar,
+               double ai, double br, double bi, cudaStream_t st) {
+  if (b.precision == CAL_FP64)
+    return pair_apply_t<double2, double2, double2>(b, (const double2*)x, (double2*)y, n, ar, ai, br, bi, st);
+  if (vec_prec == CAL_FP64)
+    return pair_apply_t<float2, double2, double2>(b, (const double2*)x, (double2*)y, n, ar, ai, br, bi, st);
+  return pair_apply_t<float2, float2, float2>(b, (const float2*)x, (float2*)y, n, ar, ai, br, bi, st);
+}
+
+int zero_vec(void* y, int prec, int64_t n, cudaStream_t st) {
+  if (prec == CAL_FP64) zero_kernel<double2><<<blocks_for(n, 256), 256, 0, st>>>((double2*)y, n);
+  else zero_kernel<float2><<<blocks_for(n, 256), 256, 0, st>>>((float2*)y, n);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale, cudaStream_t st) {
+  const unsigned g = blocks_for(n, 256);
+  if (pa == CAL_FP64 && pb == CAL_FP32) convert_kernel<double2, float2><<<g, 256, 0, st>>>((const double2*)a, (float2*)b, n, scale);
+  else if (pa == CAL_FP32 && pb == CAL_FP64) convert_kernel<float2, double2><<<g, 256, 0, st>>>((const float2*)a, (double2*)b, n, scale);
+  else if (pa == CAL_FP64) convert_kernel<double2, double2><<<g, 256, 0, st>>>((const double2*)a, (double2*)b, n, scale);
+  else convert_kernel<float2, float2><<<g, 256, 0, st>>>((const float2*)a, (float2*)b, n, scale);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st) {
+  for (int64_t q = 0; q < nrhs; ++q) {
+    const unsigned g = blocks_for(op.rows * 32, 256);
+    if (op.precision == CAL_FP64) {
+      const double2* xx = (const double2*)x + q * op.cols;
+      double2* yy = (double2*)y + q * op.rows;
+      if (op.format == CAL_DENSE) gemv_kernel<double2><<<g, 256, 0, st>>>((const double2*)X, op.rows, op.cols, xx, yy);
+      else spmv_kernel<double2><<<g, 256, 0, st>>>((const double2*)X, op.d_rowptr, op.d_col, op.rows, xx, yy);
+    } else {
+      const float2* xx = (const float2*)x + q * op.cols;
+      float2* yy = (float2*)y + q * op.rows;
+      if (op.format == CAL_DENSE) gemv_kernel<float2><<<g, 256, 0, st>>>((const float2*)X, op.rows, op.cols, xx, yy);
+      else spmv_kernel<float2><<<g, 256, 0, st>>>((const float2*)X, op.d_rowptr, op.d_col, op.rows, xx, yy);
+    }
+  }
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES helpers (float64): classical Gram–Schmidt with one reorthogonalisation
+// ---------------------------------------------------------------------------
+__global__ void multi_dot_kernel(const double2* __restrict__ V, int64_t ldv, int m,
+                                 const double2* __restrict__ w, int64_t n, double2* h) {
+  // h[i] += V_i^H w for i < m; block-partial sums, one atomic per (block, i)
+  __shared__ double sr[8][32], si[8][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double2 wk = k < n ? w[k] : double2{0, 0};
+  for (int i = 0; i < m; ++i) {
+    double ar = 0, ai = 0;
+    if (k < n) {
+      const double2 v = V[(size_t)i * ldv + k];
+      ar = v.x * wk.x + v.y * wk.y;
+      ai = v.x * wk.y - v.y * wk.x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      ar += __shfl_xor_sync(0xffffffffu, ar, o);
+      ai += __shfl_xor_sync(0xffffffffu, ai, o);
+    }
+    if (lane == 0) { sr[wid][i & 31] = ar; si[wid][i & 31] = ai; }
+    if ((i & 31) == 31 || i == m - 1) {
+      __syncthreads();
+      const int base = i & ~31;
+      const int cnt = i - base + 1;
+      if (threadIdx.x < cnt) {
+        double tr = 0, ti = 0;
+        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { tr += sr[q][threadIdx.x]; ti += si[q][threadIdx.x]; }
+        atomicAdd(&h[base + threadIdx.x].x, tr);
+        atomicAdd(&h[base + threadIdx.x].y, ti);
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__global__ void multi_axpy_kernel(const double2* __restrict__ V, int64_t ldv, int m,
+                                  const double2* __restrict__ h, double2* __restrict__ w, int64_t n) {
+  // w -= sum_i h_i V_i
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double2 acc = w[k];
+  for (int i = 0; i < m; ++i) {
+    const double2 v = V[(size_t)i * ldv + k], c = h[i];
+    acc.x -= c.x * v.x - c.y * v.y;
+    acc.y -= c.x * v.y + c.y * v.x;
+  }
+  w[k] = acc;
+}
+
+__global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* out) {
+  double part[1] = {0.0};
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) part[0] = w[k].x * w[k].x + w[k].y * w[k].y;
+  block_accumulate<1>(part, out);
+}
+
+__global__ void scale_kernel(const double2* __restrict__ w, int64_t n, const double* nrm2,
+                             double2* __restrict__ out) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  const double s = 1.0 / sqrt(*nrm2);
+  out[k] = {w[k].x * s, w[k].y * s};
+}
+
+// Arnoldi column j finished: H[0..j][j] = h1 + h2, H[j+1][j] = ||w||; apply the
+// previous Givens rotations, build the new one, update g, report |g_{j+1}|.
+__global__ void givens_kernel(double2* H, int ldh, int j, const double2* h1, const double2* h2,
+                              const double* wn2, double2* cs, double2* sn, double2* g,
+                              double* res_out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  double2* col = H + (size_t)j * ldh;
+  for (int i = 0; i <= j; ++i) col[i] = {h1[i].x + h2[i].x, h1[i].y + h2[i].y};
+  col[j + 1] = {sqrt(*wn2), 0.0};
+  for (int i = 0; i < j; ++i) {
+    // [c s; -conj(s) c] with real c
+    const double c = cs[i].x;
+    const double2 s = sn[i];
+    const double2 a = col[i], b = col[i + 1];
+    col[i] = {c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x)};
+    col[i + 1] = {-(s.x * a.x + s.y * a.y) + c * b.x, -(s.x * a.y - s.y * a.x) + c * b.y};
+  }
+  const double2 a = col[j], b = col[j + 1];
+  const double na = sqrt(a.x * a.x + a.y * a.y), nb = sqrt(b.x * b.x + b.y * b.y);
+  const double den = sqrt(na * na + nb * nb);
+  double c;
+  double2 s;
+  if (na == 0.0) { c = 0.0; s = {1.0, 0.0}; }
+  else {
+    c = na / den;
+    // s = (a/|a|) conj(b) / den
+    const double ux = a.x / na, uy = a.y / na;
+    s = {(ux * b.x + uy * b.y) / den, (uy * b.x - ux * b.y) / den};
+  }
+  cs[j] = {c, 0.0};
+  sn[j] = s;
+  col[j] = {c * a.x + (s.x * b.x - s.y * b.y), c * a.y + (s.x * b.y + s.y * b.x)};
+  col[j + 1] = {0.0, 0.0};
+  const double2 gj = g[j];
+  g[j + 1] = {-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x)};
+  g[j] = {c * gj.x, c * gj.y};
+  *res_out = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+}
+
+// y = H[0..m)[0..m)^-1 g (upper triangular), then x += V y
+__global__ void backsolve_kernel(const double2* H, int ldh, int m, const double2* g, double2* y) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  for (int i = m - 1; i >= 0; --i) {
+    double2 acc = g[i];
+    for (int q = i + 1; q < m; ++q) {
+      const double2 h = H[(size_t)q * ldh + i], v = y[q];
+      acc.x -= h.x * v.x - h.y * v.y;
+      acc.y -= h.x * v.y + h.y * v.x;
+    }
+    const double2 d = H[(size_t)i * ldh + i];
+    const double dd = d.x * d.x + d.y * d.y;
+    y[i] = {(acc.x * d.x + acc.y * d.y) / dd, (acc.y * d.x - acc.x * d.y) / dd};
+  }
+}
+
+__global__ void combine_kernel(const double2* __restrict__ V, int64_t ldv, int m,
+                               const double2* __restrict__ y, double2* __restrict__ x, int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double2 acc = x[k];
+  for (int i = 0; i < m; ++i) {
+    const double2 v = V[(size_t)i * ldv + k], c = y[i];
+    acc.x += c.x * v.x - c.y * v.y;
+    acc.y += c.x * v.y + c.y * v.x;
+  }
+  x[k] = acc;
+}
+
+__global__ void axpby_kernel(const double2* a, double sa, const double2* b, double sb, double2* out,
+                             int64_t n) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) out[k] = {sa * a[k].x + sb * b[k].x, sa * a[k].y + sb * b[k].y};
+}
+
+int gmres_cgs_step(const double2* V, int64_t n, int j, double2* w, double2* h1, double2* h2,
+                   double* wn2, cudaStream_t st) {
+  const unsigned g = blocks_for(n, 256);
+  CAL_TRY_CUDA(cudaMemsetAsync(h1, 0, (j + 1) * sizeof(double2), st));
+  CAL_TRY_CUDA(cudaMemsetAsync(h2, 0, (j + 1) * sizeof(double2), st));
+  CAL_TRY_CUDA(cudaMemsetAsync(wn2, 0, sizeof(double), st));
+  multi_dot_kernel<<<g, 256, 0, st>>>(V, n, j + 1, w, n, h1);
+  multi_axpy_kernel<<<g, 256, 0, st>>>(V, n, j + 1, h1, w, n);
+  multi_dot_kernel<<<g, 256, 0, st>>>(V, n, j + 1, w, n, h2);
+  multi_axpy_kernel<<<g, 256, 0, st>>>(V, n, j + 1, h2, w, n);
+  norm2_kernel<<<g, 256, 0, st>>>(w, n, wn2);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int gmres_givens(double2* H, int ldh, int j, const double2* h1, const double2* h2, const double* wn2,
+                 double2* cs, double2* sn, double2* g, double* res, cudaStream_t st) {
+  givens_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, wn2, cs, sn, g, res);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int gmres_scale(const double2* w, int64_t n, const double* nrm2, double2* out, cudaStream_t st) {
+  scale_kernel<<<blocks_for(n, 256), 256, 0, st>>>(w, n, nrm2, out);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int gmres_update(const double2* H, int ldh, int m, const double2* g, double2* y, const double2* V,
+                 int64_t n, double2* x, cudaStream_t st) {
+  backsolve_kernel<<<1, 32, 0, st>>>(H, ldh, m, g, y);
+  combine_kernel<<<blocks_for(n, 256), 256, 0, st>>>(V, n, m, y, x, n);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int vec_norm2(const double2* w, int64_t n, double* out, cudaStream_t st) {
+  CAL_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
+  norm2_kernel<<<blocks_for(n, 256), 256, 0, st>>>(w, n, out);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int vec_axpby(const double2* a, double sa, const double2* b, double sb, double2* out, int64_t n,
+              cudaStream_t st) {
+  axpby_kernel<<<blocks_for(n, 256), 256, 0, st>>>(a, sa, b, sb, out, n);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// A11: right-hand side b = [<u1, RWG_i>; <u2, RWG_i>] with
+// u1 = E x n, u2 = (k/mu) (d x p) e^{ik d.x} x n, <a x n, phi> = -int a.phi,
+// 6-point rule per triangle, float64.
+// ---------------------------------------------------------------------------
+__global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
+                           const double* __restrict__ slot_sw, int64_t nt, const double* inc,
+                           int nrhs, double k, double mu, Rules6 rl, int64_t ne,
+                           double2* __restrict__ b) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (t >= nt || q >= nrhs) return;
+  const TriD T = tri[t];
+  const double d[3] = {inc[6 * q], inc[6 * q + 1], inc[6 * q + 2]};
+  const double p[3] = {inc[6 * q + 3], inc[6 * q + 4], inc[6 * q + 5]};
+  const double dxp[3] = {d[1] * p[2] - d[2] * p[1], d[2] * p[0] - d[0] * p[2], d[0] * p[1] - d[1] * p[0]};
+  double acc1[3][2] = {}, acc2[3][2] = {};
+  for (int u = 0; u < 6; ++u) {
+    double xi[3];
+    for (int c = 0; c < 3; ++c)
+      xi[c] = rl.b[3 * u] * T.off[0][c] + rl.b[3 * u + 1] * T.off[1][c] + rl.b[3 * u + 2] * T.off[2][c];
+    double ph = 0;
+    for (int c = 0; c < 3; ++c) ph += d[c] * (T.c[c] + xi[c]);
+    double s, co;
+    sincos(k * ph, &s, &co);
+    const double w = rl.w[u] * T.area;
+    for (int a = 0; a < 3; ++a) {
+      const double* sw = slot_sw + (3 * t + a) * 4;
+      double phi[3];
+      for (int c = 0; c < 3; ++c) phi[c] = sw[0] * xi[c] + sw[1 + c];
+      const double e1 = p[0] * phi[0] + p[1] * phi[1] + p[2] * phi[2];
+      const double e2 = dxp[0] * phi[0] + dxp[1] * phi[1] + dxp[2] * phi[2];
+      acc1[a][0] -= w * co * e1;
+      acc1[a][1] -= w * s * e1;
+      acc2[a][0] -= (k / mu) * w * co * e2;
+      acc2[a][1] -= (k / mu) * w * s * e2;
+    }
+  }
+  for (int a = 0; a < 3; ++a) {
+    const int e = slot_edge[3 * t + a];
+    double2* bq = b + (size_t)q * 2 * ne;
+    atomicAdd(&bq[e].x, acc1[a][0]);
+    atomicAdd(&bq[e].y, acc1[a][1]);
+    atomicAdd(&bq[ne + e].x, acc2[a][0]);
+    atomicAdd(&bq[ne + e].y, acc2[a][1]);
+  }
+}
+
+// Far field E_inf(xh) = -(ik/4pi) [xh x Ja - xh x (xh x Jb)],
+// Ja = int a e^{-ik xh.y}, Jb = (mu/k) int (sum d_e RWG_e) e^{-ik xh.y}.
+__global__ void farfield_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
+                                const double* __restrict__ slot_sw, int64_t nt,
+                                const double2* __restrict__ x, int64_t ne, const double* dirs,
+                                int64_t ndir, double k, double mu, Rules6 rl, double2* out) {
+  const int64_t dq = blockIdx.x;  // direction
+  const int q = blockIdx.y;       // right-hand side
+  const double xh[3] = {dirs[3 * dq], dirs[3 * dq + 1], dirs[3 * dq + 2]};
+  const double2* xq = x + (size_t)q * 2 * ne;
+  double acc[12] = {};
+  for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
+    const TriD T = tri[t];
+    double ca[3][2], cb[3][2];
+    for (int a = 0; a < 3; ++a) {
+      const int e = slot_edge[3 * t + a];
+      ca[a][0] = xq[e].x; ca[a][1] = xq[e].y;
+      cb[a][0] = xq[ne + e].x * (mu / k); cb[a][1] = xq[ne + e].y * (mu / k);
+    }
+    for (int u = 0; u < 6; ++u) {
+      double xi[3];
+      for (int c = 0; c < 3; ++c)
+        xi[c] = rl.b[3 * u] * T.off[0][c] + rl.b[3 * u + 1] * T.off[1][c] + rl.b[3 * u + 2] * T.off[2][c];
+      double ph = 0;
+      for (int c = 0; c < 3; ++c) ph += xh[c] * (T.c[c] + xi[c]);
+      double s, co;
+      sincos(-k * ph, &s, &co);
+      const double w = rl.w[u] * T.area;
+      for (int a = 0; a < 3; ++a) {
+        const double* sw = slot_sw + (3 * t + a) * 4;
+        for (int c = 0; c < 3; ++c) {
+          const double phi = sw[0] * xi[c] + sw[1 + c];
+          const double er = w * co * phi, ei = w * s * phi;
+          acc[2 * c] += ca[a][0] * er - ca[a][1] * ei;
+          acc[2 * c + 1] += ca[a][0] * ei + ca[a][1] * er;
+          acc[6 + 2 * c] += cb[a][0] * er - cb[a][1] * ei;
+          acc[6 + 2 * c + 1] += cb[a][0] * ei + cb[a][1] * er;
+        }
+      }
+    }
+  }
+  __shared__ double sh[12][32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int c = 0; c < 12; ++c) {
+    double v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) sh[c][wid] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double J[12];
+    for (int c = 0; c < 12; ++c) {
+      J[c] = 0;
+      for (int q2 = 0; q2 < (int)(blockDim.x >> 5); ++q2) J[c] += sh[c][q2];
+    }
+    // complex vectors Ja = J[0..5], Jb = J[6..11] as (re, im) per component
+    double Ja[3][2], Jb[3][2], A[3][2], B1[3][2], B[3][2];
+    for (int c = 0; c < 3; ++c) {
+      Ja[c][0] = J[2 * c]; Ja[c][1] = J[2 * c + 1];
+      Jb[c][0] = J[6 + 2 * c]; Jb[c][1] = J[6 + 2 * c + 1];
+    }
+    for (int z = 0; z < 2; ++z) {
+      // A = xh x Ja ; B1 = xh x Jb ; B = xh x B1
+      A[0][z] = xh[1] * Ja[2][z] - xh[2] * Ja[1][z];
+      A[1][z] = xh[2] * Ja[0][z] - xh[0] * Ja[2][z];
+      A[2][z] = xh[0] * Ja[1][z] - xh[1] * Ja[0][z];
+      B1[0][z] = xh[1] * Jb[2][z] - xh[2] * Jb[1][z];
+      B1[1][z] = xh[2] * Jb[0][z] - xh[0] * Jb[2][z];
+      B1[2][z] = xh[0] * Jb[1][z] - xh[1] * Jb[0][z];
+    }
+    for (int z = 0; z < 2; ++z) {
+      B[0][z] = xh[1] * B1[2][z] - xh[2] * B1[1][z];
+      B[1][z] = xh[2] * B1[0][z] - xh[0] * B1[2][z];
+      B[2][z] = xh[0] * B1[1][z] - xh[1] * B1[0][z];
+    }
+    const double f = k / (4.0 * 3.14159265358979323846);
+    for (int c = 0; c < 3; ++c) {
+      const double vr = A[c][0] - B[c][0], vi = A[c][1] - B[c][1];
+      // -(i f) (vr + i vi) = f vi - i f vr
+      out[((size_t)q * ndir + dq) * 3 + c] = {f * vi, -f * vr};
+    }
+  }
+}
+
+int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
+               cudaStream_t st) {
+  Rules6 rl = rules6();
+  CAL_TRY_CUDA(cudaMemsetAsync(d_b, 0, (size_t)nrhs * 2 * rwg.nbasis * sizeof(double2), st));
+  dim3 grid(blocks_for(rwg.ntri, 128), nrhs);
+  rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_inc, nrhs,
+                                   k, mu, rl, rwg.nbasis, d_b);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,
+                    double k, double mu, double2* d_out, cudaStream_t st) {
+  Rules6 rl = rules6();
+  dim3 grid((unsigned)ndir, nrhs);
+  farfield_kernel<<<grid, 256, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_x,
+                                        rwg.nbasis, d_dirs, ndir, k, mu, rl, d_out);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+Rules6 rules6() {
+  std::vector<double> b, w;
+  triangle_rule(6, b, w);
+  Rules6 r;
+  for (int i = 0; i < 18; ++i) r.b[i] = b[i];
+  for (int i = 0; i < 6; ++i) r.w[i] = w[i];
+  return r;
+}
+
+}  // namespace cal
