@@ -1,0 +1,360 @@
+"""Benchmark: Calderón-preconditioned PMCHWT solves on one GB300 (or N replicas).
+
+Workload (default): dielectric sphere of radius 1, icosphere with 5120
+triangles (7680 RWG/BC functions, 15360 PMCHWT unknowns), k_e = 5,
+eps_r = 3.17 + 0.01i, x-polarised plane wave along +z; A on RWG with the
+6-point regular rule and order-4 Sauter–Schwab singular rules; the full
+block-diagonal Calderón preconditioner D on the barycentric mesh (dense, same
+rules); FP32-bulk assembly and complex64 matvecs with FP64 GMRES recurrences
+and FP64 iterative refinement, tol 1e-5, restart 200.
+
+One step = one complete solve through the C ABI (spaces, assembly of A and P,
+Gram matrix, right-hand side, GMRES, far field on 362 directions). The FP64
+GPU path is timed on the same workload for comparison, and the FP32 far field
+is compared against it. With --gpus N (torchrun) every rank solves its own
+replica of the workload: there is no exchange step.
+
+--impl reference times the CPU oracle (plain FP64, test infrastructure) on a
+bounded sample of the same workload and extrapolates to solves/s.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = {"name": "sphere5120_k5_D_dense", "level": 4, "k": 5.0, "eps": 3.17 + 0.01j,
+            "tol": 1e-5, "restart": 200}
+METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5)"
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f)
+    return {}
+
+
+def _alu_peak(n_sm, sm_max_mhz):
+    """Point-pair evaluations/s bound of the FP32 pipe for the regular rule.
+
+    Per evaluation the formulation needs 42 FP32 instructions (distance 6,
+    phase and Cody–Waite reduction 5, amplitude and G 4, g 7, weights 4,
+    moment sums 16) and 3 XU instructions (rsqrt, sin, cos); an SM issues
+    128 FP32 and 16 XU thread-instructions per clock, so the FP32 pipe binds:
+    128/42 = 3.05 evaluations per SM clock.
+    """
+    per_sm_clk = min(128.0 / 42.0, 16.0 / 3.0)
+    return per_sm_clk * n_sm * sm_max_mhz * 1e6
+
+
+def run_ours(args, rank, world):
+    import torch
+
+    from paper_2008_04772_gb300 import build as libbuild
+    from paper_2008_04772_gb300 import cal, meshgen
+
+    libbuild.build()
+    dev = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(dev)
+    L = cal.lib()
+    ctx = cal.Context(dev)
+    stream = torch.cuda.ExternalStream(L.cal_ctx_stream(ctx.h), device=dev)
+    W = WORKLOAD
+    m = meshgen.icosphere(W["level"])
+    inc = meshgen.plane_wave_x_along_z()
+    dirs = meshgen.sphere_cut_directions(181)
+    opts32 = cal.solve_opts(precond="D", precision=cal.FP32, tol=W["tol"], restart=W["restart"])
+    opts64 = cal.solve_opts(precond="D", precision=cal.FP64, tol=W["tol"], restart=W["restart"])
+
+    def one_step(opts, mesh=None, e2e=False):
+        """One solve; returns (solution info, far field). e2e: mesh from host arrays each step."""
+        if e2e:
+            mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+        sol = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], inc, opts=opts)
+        F = sol.far_field(dirs)
+        return sol.info(), F
+
+    mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    for _ in range(args.warmup):
+        one_step(opts32, mesh)
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    # timed region: K device-timed steps (inputs resident: mesh created before)
+    L.cal_profile_enable(1)
+    n0 = L.cal_kernel_launches()
+    lat = []
+    infos = []
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev) as clk:
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            info, F32 = one_step(opts32, mesh)
+            ev1.record(stream)
+            ev1.synchronize()
+            lat.append(ev0.elapsed_time(ev1))
+            infos.append(info)
+        torch.cuda.synchronize()
+        t_wall = time.perf_counter() - t0
+    if dist:
+        tdist.barrier()
+    n_launch = L.cal_kernel_launches() - n0
+    prof = {}
+    for name in ("bc_tile", "rwg_regular", "singular", "pair_gemv", "bicgstab", "gram"):
+        import ctypes
+        n = ctypes.c_int64()
+        ms = ctypes.c_double()
+        u = ctypes.c_double()
+        L.cal_profile_read(name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(u))
+        prof[name] = {"launches": n.value, "ms": ms.value, "units": u.value}
+    L.cal_profile_enable(0)
+    t_dev = sum(lat) / 1e3
+    if dist:
+        tt = torch.tensor([t_dev, t_wall], dtype=torch.float64)
+        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
+        t_dev, t_wall = float(tt[0]), float(tt[1])
+    # e2e through host buffers: mesh arrays in, far field out, every step
+    t_e2e = []
+    for _ in range(max(1, min(args.steps, 3))):
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        one_step(opts32, e2e=True)
+        torch.cuda.synchronize()
+        t_e2e.append(time.perf_counter() - a)
+    # FP64 GPU path on the same workload, and the FP32 vs FP64 far-field error
+    a = time.perf_counter()
+    info64, F64 = one_step(opts64, mesh)
+    t64 = time.perf_counter() - a
+    err = float(np.linalg.norm(F32 - F64) / np.linalg.norm(F64))
+    if rank != 0:
+        return None
+    info = infos[-1]
+    ms_step = 1e3 * t_dev / args.steps
+    value = world * args.steps / t_dev
+    N = int(info.n_unknowns)
+    entries = 2 * (N // 2) ** 2 * 2 * 2   # S, C at k_e and k_m on RWG and on BC (dense D)
+    bc = prof["bc_tile"]
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peaks = _measured_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    achieved = bc["units"] / (bc["ms"] / 1e3) if bc["ms"] > 0 else 0.0
+    peak = _alu_peak(n_sm, sm_max)
+    clocks = clk.summary()
+    h2d = m.verts.nbytes + m.tris.nbytes + m.domain.nbytes + inc.nbytes
+    d2h = int(np.prod(F32.shape)) * 16
+    out = {
+        "metric": "PMCHWT solves/s",
+        "value": value,
+        "unit": "solves/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": ms_step,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32 bulk (f64 singular pairs, GMRES and refinement)",
+        "data": "synthetic (seeded icosphere, plane wave)",
+        "config": {"workload": W["name"], "triangles": int(len(m.tris)), "unknowns": N,
+                   "k_ext": W["k"], "eps_r": [W["eps"].real, W["eps"].imag],
+                   "preconditioner": "D (full block-diagonal Calderon, dense BC)",
+                   "rules": "A and P: 6-point regular, Sauter-Schwab 4^4 singular",
+                   "tol": W["tol"], "restart": W["restart"], "parallelism": f"replicas{world}",
+                   "l2": "working set > L2 (each step writes ~2.4 GB of operators)"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
+        "iterations": int(info.iterations),
+        "matvecs": int(info.matvecs),
+        "phase_s": {"setup": info.t_setup, "assemble_A": info.t_assemble_A,
+                    "assemble_P": info.t_assemble_P, "solve": info.t_solve},
+        "entries_per_s": entries / (ms_step / 1e3),
+        "fp64_gpu": {"solves_per_s": 1.0 / t64, "iterations": int(info64.iterations)},
+        "err_farfield_fp32_vs_fp64": err,
+        "gpu_launches": int(n_launch),
+        "kernels_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
+        "roofline": {"bound": "alu", "kernel": "bc_tile_kernel<float,6>",
+                     "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
+                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "peak_source": f"derived: {n_sm} SMs x 3.05 eval/clk x {sm_max:.0f} MHz"},
+        "clocks": clocks,
+        "e2e": {"value": 1.0 / statistics.median(t_e2e), "unit": "solves/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+    }
+    if args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
+    return out
+
+
+def cpu_baseline(sample_tris: int):
+    """The oracle (plain FP64 C + numpy) on a bounded sample of the workload.
+
+    Times the oracle's local blocks for `sample_tris` test triangles against
+    all trial triangles — barycentric (P) and primal (A) — at k_e and k_i, and
+    extrapolates by the number of triangle pairs of one solve (P: 2 passes over
+    30720^2 barycentric pairs, A: 2 passes over 5120^2 primal pairs). GMRES
+    and far field (a few % of the oracle's time) are not included.
+    """
+    from oracle import bem, spaces
+    from paper_2008_04772_gb300 import meshgen
+    W = WORKLOAD
+    m = meshgen.icosphere(W["level"])
+    topo = spaces.Topology(m.verts, m.tris, m.domain)
+    rwg, bc = spaces.rwg_space(topo), spaces.bc_space(topo)
+    rules = bem.Rules(6, 4)
+    km = W["k"] * np.sqrt(W["eps"])
+    rng = np.random.default_rng(0)
+    t_total = 0.0
+    pairs_sampled = 0
+    sample_desc = []
+    for sp, name in ((bc, "barycentric"), (rwg, "primal")):
+        X, ids = bem._space_tri_arrays(sp)
+        nt = sp.tri_xyz.shape[0]
+        test = rng.choice(nt, size=min(sample_tris, nt), replace=False)
+        trial = np.arange(nt)
+        t = 0.0
+        for k in (W["k"], km):
+            a = time.perf_counter()
+            bem.local_blocks(X, ids, test, trial, k, rules)
+            t += time.perf_counter() - a
+        per_pair = t / (2 * len(test) * nt)
+        t_total += per_pair * 2 * nt * nt
+        pairs_sampled += 2 * len(test) * nt
+        sample_desc.append(f"{len(test)} {name} test triangles x {nt}")
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": 1.0 / t_total, "unit": "solves/s", "cores": cores, "kind": "oracle",
+            "sample": "oracle local blocks for " + " and ".join(sample_desc) +
+                      " at k_e and k_i, extrapolated by triangle-pair count to one solve "
+                      f"({pairs_sampled} pairs timed); GMRES and far field excluded"}
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands on the host cores (rank 0 only)."""
+    if rank != 0:
+        return None
+    from oracle import bem
+    bem.build()
+    for _ in range(args.warmup):
+        cpu_baseline(4)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(cpu_baseline(args.cpu_sample))
+    v = statistics.median([x["value"] for x in vals])
+    cb = dict(vals[-1])
+    cb["value"] = v
+    return {"metric": "PMCHWT solves/s", "value": v, "unit": "solves/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded icosphere, plane wave)", "impl": "reference",
+            "config": {"workload": WORKLOAD["name"], "parallelism": "host cores"},
+            "cpu_baseline": cb,
+            "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-sample", type=int, default=24, help="test triangles per space for the oracle sample")
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    world = _env_int("WORLD_SIZE", 1)
+    rank = _env_int("RANK", 0)
+    if world > 1 and args.impl == "ours":
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(_env_int("LOCAL_RANK", 0))
+        tdist.init_process_group("nccl")
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        out = run_ours(args, rank, world)
+    if out is not None:
+        print(json.dumps(out))
+    if world > 1 and args.impl == "ours":
+        import torch.distributed as tdist
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

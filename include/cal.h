@@ -201,6 +201,19 @@ int cal_solution_coefficients(const cal_solution* sol, double* dst_host);
 int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, double* out);
 void cal_solution_destroy(cal_solution* sol);
 
+/* ---- instrumentation ------------------------------------------------------ */
+/* Number of kernels this library has launched since load (all contexts). */
+int64_t cal_kernel_launches(void);
+/* on != 0: bracket every assembly kernel launch with CUDA events on its own
+   stream; off clears the records. */
+int cal_profile_enable(int on);
+/* Sum over recorded launches of kernel family `name` ("rwg_regular",
+   "bc_tile", "singular", "gram", "pair_gemv", "bicgstab"): launches,
+   total device milliseconds, and algorithmic work units (point-pair
+   integrand evaluations for assembly kernels, matrix bytes for GEMVs).
+   Waits for the recorded events. */
+int cal_profile_read(const char* name, int64_t* launches, double* total_ms, double* units);
+
 #ifdef __cplusplus
 }
 #endif

@@ -21,6 +21,9 @@
 
 namespace cal {
 const char* last_error();
+int64_t launches();
+int prof_enable(int on);
+int prof_read(const char* name, int64_t* n, double* ms, double* units);
 }
 
 using namespace cal;
@@ -150,9 +153,29 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       CAL_TRY_CUDA(cudaMallocAsync((void**)&d_tiles, tiles.size() * sizeof(int2), st));
       CAL_TRY_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
     }
+    // algorithmic work: cell-pair triangle pairs minus touching ones, times rule points squared
+    double pairs = 0.0;
+    if (dense) {
+      double s1 = 0, s2 = 0;
+      for (int v : cells) { const double n = sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]; s1 += n; s2 += n * n; }
+      pairs = 0.5 * (s1 * s1 + s2);
+    } else {
+      for (const int2& t : tiles)
+        pairs += (double)(sp.cell_tri_ptr[t.x + 1] - sp.cell_tri_ptr[t.x]) * (sp.cell_tri_ptr[t.y + 1] - sp.cell_tri_ptr[t.y]);
+    }
+    {
+      auto cell_of = [&](int tau) {
+        for (int q = 0; q < 3; ++q)
+          if (sp.triD[tau].vid[q] < m.nv) return sp.triD[tau].vid[q];
+        return -1;
+      };
+      const int d0 = scat < 0 ? 0 : scat, d1 = scat < 0 ? (int)sp.sing.size() : scat + 1;
+      for (int d = d0; d < d1; ++d)
+        for (const SingPair& q : sp.sing[d]) pairs -= cell_of(q.t1) == cell_of(q.t2) ? 1.0 : 0.5;
+    }
     if (dense || !tiles.empty())
       rc = launch_bc_regular_tiles(a, d_cells, (int64_t)cells.size(), dense ? nullptr : d_tiles,
-                                   (int64_t)tiles.size(), max_cell, ctx.n_sm);
+                                   (int64_t)tiles.size(), max_cell, ctx.n_sm, pairs * nreg * nreg);
     // the tile list must outlive the kernel: free in stream order
     cudaFreeAsync(d_cells, st);
     if (d_tiles) cudaFreeAsync(d_tiles, st);
@@ -858,5 +881,14 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
 }
 
 void cal_solution_destroy(cal_solution* sol) { delete sol; }
+
+int64_t cal_kernel_launches(void) { return cal::launches(); }
+
+int cal_profile_enable(int on) { return cal::prof_enable(on); }
+
+int cal_profile_read(const char* name, int64_t* launches, double* total_ms, double* units) {
+  if (!name) return fail(CAL_EINVAL, "cal_profile_read: NULL name");
+  return cal::prof_read(name, launches, total_ms, units);
+}
 
 }  // extern "C"

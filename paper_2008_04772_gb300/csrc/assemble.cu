@@ -399,11 +399,12 @@ __global__ void __launch_bounds__(128) bc_tile_kernel(
     const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
     const R* __restrict__ slot_sw, int nslot, const int* __restrict__ cell_ptr,
     const int* __restrict__ cell_tri, TileList tl, R kr, R ki, R mikr, R miki, R c4r, R c4i,
-    bool wantS, bool wantC, Rules rl, Sink<R> out, int max_cell) {
+    bool wantS, bool wantC, Rules rl, Sink<R> out, int max_cell, int chunk) {
   using TRI = typename TriOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* pcs = reinterpret_cast<R*>(smem_raw);                          // [max_cell^2][36]
-  R* red = pcs + (size_t)max_cell * max_cell * 36;                  // [max_cell][nslot][18]
+  R* pcs = reinterpret_cast<R*>(smem_raw);                          // [chunk * max_cell][36]
+  R* red = pcs + (size_t)chunk * max_cell * 36;                     // [chunk][nslot][18]
+  R* acc = red + (size_t)chunk * nslot * 18;                        // [nslot][nslot][4]
   const int64_t ntiles = tl.tiles ? tl.ntile : tl.ncell * (tl.ncell + 1) / 2;
   for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
     int v, w;
@@ -418,29 +419,6 @@ __global__ void __launch_bounds__(128) bc_tile_kernel(
     }
     const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
     const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
-    // stage 1
-    for (int p = threadIdx.x; p < n1 * n2; p += blockDim.x) {
-      const int tau1 = cell_tri[b1 + p / n2], tau2 = cell_tri[b2 + p % n2];
-      const TRI A = tri[tau1];
-      const TRI B = tri[tau2];
-      R* pc = pcs + (size_t)p * 36;
-      if (touching(A, B)) {
-        for (int q = 0; q < 36; ++q) pc[q] = R(0);
-        continue;
-      }
-      V3<R> xi[NREG], eta[NREG];
-      R wx[NREG], wy[NREG];
-      load_points<NREG>(A, rl, xi, wx);
-      load_points<NREG>(B, rl, eta, wy);
-      const V3<R> D = centroid_delta(A, B);
-      Mom<R> m;
-      regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, wantC, m);
-      R tmp[36];
-      pair_coeffs(m, D, tmp);
-#pragma unroll
-      for (int q = 0; q < 36; ++q) pc[q] = tmp[q];
-    }
-    __syncthreads();
     // number of valid slots of each cell
     int ns1 = 0, ns2 = 0;
     {
@@ -448,67 +426,101 @@ __global__ void __launch_bounds__(128) bc_tile_kernel(
       while (ns1 < nslot && slot_edge[(size_t)tv * nslot + ns1] >= 0) ++ns1;
       while (ns2 < nslot && slot_edge[(size_t)tw * nslot + ns2] >= 0) ++ns2;
     }
-    // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side factors
-    for (int q = threadIdx.x; q < n1 * ns2; q += blockDim.x) {
-      const int i1 = q / ns2, sb_i = q % ns2;
-      R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0, AC_r = 0, AC_i = 0;
-      V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0}, WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
-      for (int i2 = 0; i2 < n2; ++i2) {
-        const int tau2 = cell_tri[b2 + i2];
-        const R* sw = slot_sw + ((size_t)tau2 * nslot + sb_i) * 4;
-        const R sb = sw[0];
-        const V3<R> wb = {sw[1], sw[2], sw[3]};
-        const R* pc = pcs + (size_t)(i1 * n2 + i2) * 36;
-        if (wantS) {
-          AS_r += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
-          AS_i += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
-          BS_r += sb * pc[0];
-          BS_i += sb * pc[1];
-          WS_r.x += sb * pc[8] + wb.x * pc[0]; WS_r.y += sb * pc[9] + wb.y * pc[0]; WS_r.z += sb * pc[10] + wb.z * pc[0];
-          WS_i.x += sb * pc[11] + wb.x * pc[1]; WS_i.y += sb * pc[12] + wb.y * pc[1]; WS_i.z += sb * pc[13] + wb.z * pc[1];
+    for (int q = threadIdx.x; q < ns1 * ns2 * 4; q += blockDim.x) acc[q] = R(0);
+    for (int c0 = 0; c0 < n1; c0 += chunk) {
+      const int nc = min(chunk, n1 - c0);
+      // stage 1: pair coefficients of (tau1 in the chunk) x (tau2 in D(w))
+      for (int p = threadIdx.x; p < nc * n2; p += blockDim.x) {
+        const int tau1 = cell_tri[b1 + c0 + p / n2], tau2 = cell_tri[b2 + p % n2];
+        const TRI A = tri[tau1];
+        const TRI B = tri[tau2];
+        R* pc = pcs + (size_t)p * 36;
+        if (touching(A, B)) {
+          for (int q = 0; q < 36; ++q) pc[q] = R(0);
+          continue;
         }
-        if (wantC) {
-          AC_r += sb * pc[16] + wb.x * pc[18] + wb.y * pc[19] + wb.z * pc[20];
-          AC_i += sb * pc[17] + wb.x * pc[21] + wb.y * pc[22] + wb.z * pc[23];
-          const V3<R> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
-          const V3<R> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
-          WC_r.x += sb * pc[24] + cr.x; WC_r.y += sb * pc[25] + cr.y; WC_r.z += sb * pc[26] + cr.z;
-          WC_i.x += sb * pc[27] + ci.x; WC_i.y += sb * pc[28] + ci.y; WC_i.z += sb * pc[29] + ci.z;
-        }
+        V3<R> xi[NREG], eta[NREG];
+        R wx[NREG], wy[NREG];
+        load_points<NREG>(A, rl, xi, wx);
+        load_points<NREG>(B, rl, eta, wy);
+        const V3<R> D = centroid_delta(A, B);
+        Mom<R> m;
+        regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, wantC, m);
+        R tmp[36];
+        pair_coeffs(m, D, tmp);
+#pragma unroll
+        for (int q = 0; q < 36; ++q) pc[q] = tmp[q];
       }
-      R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
-      o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
-      o[4] = WS_r.x; o[5] = WS_r.y; o[6] = WS_r.z; o[7] = WS_i.x; o[8] = WS_i.y; o[9] = WS_i.z;
-      o[10] = AC_r; o[11] = AC_i;
-      o[12] = WC_r.x; o[13] = WC_r.y; o[14] = WC_r.z; o[15] = WC_i.x; o[16] = WC_i.y; o[17] = WC_i.z;
+      __syncthreads();
+      // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side factors
+      for (int q = threadIdx.x; q < nc * ns2; q += blockDim.x) {
+        const int i1 = q / ns2, sb_i = q % ns2;
+        R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0, AC_r = 0, AC_i = 0;
+        V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0}, WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
+        for (int i2 = 0; i2 < n2; ++i2) {
+          const int tau2 = cell_tri[b2 + i2];
+          const R* sw = slot_sw + ((size_t)tau2 * nslot + sb_i) * 4;
+          const R sb = sw[0];
+          const V3<R> wb = {sw[1], sw[2], sw[3]};
+          const R* pc = pcs + (size_t)(i1 * n2 + i2) * 36;
+          if (wantS) {
+            AS_r += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
+            AS_i += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
+            BS_r += sb * pc[0];
+            BS_i += sb * pc[1];
+            WS_r.x += sb * pc[8] + wb.x * pc[0]; WS_r.y += sb * pc[9] + wb.y * pc[0]; WS_r.z += sb * pc[10] + wb.z * pc[0];
+            WS_i.x += sb * pc[11] + wb.x * pc[1]; WS_i.y += sb * pc[12] + wb.y * pc[1]; WS_i.z += sb * pc[13] + wb.z * pc[1];
+          }
+          if (wantC) {
+            AC_r += sb * pc[16] + wb.x * pc[18] + wb.y * pc[19] + wb.z * pc[20];
+            AC_i += sb * pc[17] + wb.x * pc[21] + wb.y * pc[22] + wb.z * pc[23];
+            const V3<R> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
+            const V3<R> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
+            WC_r.x += sb * pc[24] + cr.x; WC_r.y += sb * pc[25] + cr.y; WC_r.z += sb * pc[26] + cr.z;
+            WC_i.x += sb * pc[27] + ci.x; WC_i.y += sb * pc[28] + ci.y; WC_i.z += sb * pc[29] + ci.z;
+          }
+        }
+        R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
+        o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
+        o[4] = WS_r.x; o[5] = WS_r.y; o[6] = WS_r.z; o[7] = WS_i.x; o[8] = WS_i.y; o[9] = WS_i.z;
+        o[10] = AC_r; o[11] = AC_i;
+        o[12] = WC_r.x; o[13] = WC_r.y; o[14] = WC_r.z; o[15] = WC_i.x; o[16] = WC_i.y; o[17] = WC_i.z;
+      }
+      __syncthreads();
+      // stage 3: per (test slot a, trial slot b), sum over the chunk's tau1
+      for (int q = threadIdx.x; q < ns1 * ns2; q += blockDim.x) {
+        const int sa_i = q / ns2, sb_i = q % ns2;
+        R Sr = 0, Si = 0, Cr = 0, Ci = 0;
+        for (int i1 = 0; i1 < nc; ++i1) {
+          const int tau1 = cell_tri[b1 + c0 + i1];
+          const R* sw = slot_sw + ((size_t)tau1 * nslot + sa_i) * 4;
+          const R sa = sw[0];
+          const V3<R> wa = {sw[1], sw[2], sw[3]};
+          const R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
+          if (wantS) {
+            // sa (mik AS + c4 BS) + mik (wa . WS)
+            const R pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
+            const R pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
+            Sr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
+            Si += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
+          }
+          if (wantC) {
+            Cr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
+            Ci += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
+          }
+        }
+        R* a4 = acc + (size_t)q * 4;
+        a4[0] += Sr; a4[1] += Si; a4[2] += Cr; a4[3] += Ci;
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    // stage 3: per (test slot a, trial slot b), sum over tau1
     for (int q = threadIdx.x; q < ns1 * ns2; q += blockDim.x) {
       const int sa_i = q / ns2, sb_i = q % ns2;
-      R Sr = 0, Si = 0, Cr = 0, Ci = 0;
-      for (int i1 = 0; i1 < n1; ++i1) {
-        const int tau1 = cell_tri[b1 + i1];
-        const R* sw = slot_sw + ((size_t)tau1 * nslot + sa_i) * 4;
-        const R sa = sw[0];
-        const V3<R> wa = {sw[1], sw[2], sw[3]};
-        const R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
-        if (wantS) {
-          // sa (mik AS + c4 BS) + mik (wa . WS)
-          const R pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
-          const R pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
-          Sr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
-          Si += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
-        }
-        if (wantC) {
-          Cr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
-          Ci += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
-        }
-      }
+      const R* a4 = acc + (size_t)q * 4;
       const int ea = slot_edge[(size_t)cell_tri[b1] * nslot + sa_i];
       const int eb = slot_edge[(size_t)cell_tri[b2] * nslot + sb_i];
-      out.add(ea, eb, wantS, wantC, Sr, Si, Cr, Ci);
-      if (v != w) out.add(eb, ea, wantS, wantC, Sr, Si, Cr, Ci);
+      out.add(ea, eb, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
+      if (v != w) out.add(eb, ea, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
     }
     __syncthreads();
   }
@@ -733,12 +745,21 @@ static int rwg_regular_t(const AssembleArgs& a) {
   const R* sw;
   if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
   else { tri = s.d_triD; sw = s.d_slot_swd; }
-  if (a.nreg == 6)
+  // algorithmic work: unordered non-touching pairs x rule points squared
+  int64_t nsing = 0;
+  for (int d = (a.scat < 0 ? 0 : a.scat); d < (a.scat < 0 ? (int)s.sing.size() : a.scat + 1); ++d)
+    nsing += (int64_t)s.sing[d].size();
+  const double units = ((double)ntr * (ntr - 1) / 2 - (double)(nsing - ntr) / 2) * a.nreg * a.nreg;
+  const int tok = prof_begin(a.stream, "rwg_regular", units);
+  if (a.nreg == 6) {
     rwg_regular_kernel<R, 6><<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki,
                                                             mikr, miki, c4r, c4i, wS, wC, g_rules, out);
-  else
+  } else {
     rwg_regular_kernel<R, 1><<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki,
                                                             mikr, miki, c4r, c4i, wS, wC, g_rules, out);
+  }
+  prof_end(a.stream, tok);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -754,7 +775,7 @@ struct BcTiles {
 
 template <typename R>
 static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
-                        int64_t ntile, int max_cell, int n_sm) {
+                        int64_t ntile, int max_cell, int n_sm, double units) {
   const Space& s = *a.sp;
   R mikr, miki, c4r, c4i;
   wave_scalars(a.kr, a.ki, mikr, miki, c4r, c4i);
@@ -763,7 +784,13 @@ static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, 
   TileList tl{cells, ncell, tiles, ntile};
   const int64_t ntiles = tiles ? ntile : ncell * (ncell + 1) / 2;
   if (ntiles == 0) return CAL_OK;
-  const size_t smem = ((size_t)max_cell * max_cell * 36 + (size_t)max_cell * s.nslot * 18) * sizeof(R);
+  // test-cell triangles are processed in chunks so that any valence fits
+  auto smem_for = [&](int ch) {
+    return ((size_t)ch * max_cell * 36 + (size_t)ch * s.nslot * 18 + (size_t)s.nslot * s.nslot * 4) * sizeof(R);
+  };
+  int chunk = max_cell;
+  while (chunk > 1 && smem_for(chunk) > 96 * 1024) --chunk;
+  const size_t smem = smem_for(chunk);
   if (smem > 227 * 1024) return fail(CAL_EINVAL, "dual cell too large for the tile kernel (%d triangles)", max_cell);
   const typename TriOf<R>::T* tri;
   const R* sw;
@@ -776,17 +803,20 @@ static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, 
   int per_sm = 0;
   CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * n_sm * 4);
+  const int tok = prof_begin(a.stream, "bc_tile", units);
   kern<<<(unsigned)grid, 128, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr,
                                                 s.d_cell_tri, tl, (R)a.kr, (R)a.ki, mikr, miki, c4r,
-                                                c4i, wS, wC, g_rules, out, max_cell);
+                                                c4i, wS, wC, g_rules, out, max_cell, chunk);
+  prof_end(a.stream, tok);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
 int launch_bc_regular_tiles(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
-                            int64_t ntile, int max_cell, int n_sm) {
-  return a.precision == CAL_FP32 ? bc_regular_t<float>(a, cells, ncell, tiles, ntile, max_cell, n_sm)
-                                 : bc_regular_t<double>(a, cells, ncell, tiles, ntile, max_cell, n_sm);
+                            int64_t ntile, int max_cell, int n_sm, double units) {
+  return a.precision == CAL_FP32 ? bc_regular_t<float>(a, cells, ncell, tiles, ntile, max_cell, n_sm, units)
+                                 : bc_regular_t<double>(a, cells, ncell, tiles, ntile, max_cell, n_sm, units);
 }
 
 int launch_singular(const AssembleArgs& a) {
@@ -800,14 +830,21 @@ int launch_singular(const AssembleArgs& a) {
     const int64_t np = (int64_t)s.sing[d].size();
     if (np == 0) continue;
     const unsigned grid = (unsigned)((np + 3) / 4);
-    if (a.precision == CAL_FP32)
+    double regions = 0;
+    for (const SingPair& q : s.sing[d]) regions += (q.cls == 3 ? 6 : (q.cls == 2 ? 5 : 2));
+    const double ng2 = (double)a.nsing * a.nsing;
+    const int tok = prof_begin(a.stream, "singular", regions * ng2 * ng2);
+    if (a.precision == CAL_FP32) {
       singular_kernel<float><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
                                                          s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,
                                                          c4r, c4i, wS, wC, g_rules, make_sink<float>(a));
-    else
+    } else {
       singular_kernel<double><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
                                                           s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,
                                                           c4r, c4i, wS, wC, g_rules, make_sink<double>(a));
+    }
+    prof_end(a.stream, tok);
+    note_launch();
     CAL_TRY_CUDA(cudaGetLastError());
   }
   return CAL_OK;
@@ -824,6 +861,7 @@ int launch_gram(const Space& rwg, const Space& bc, const int64_t* rowptr, const 
   gram_kernel<<<(unsigned)((n + 255) / 256), 256, 0, stream>>>(
       bc.d_triD, bc.d_slot_edge, bc.d_slot_swd, bc.nslot, d_parent, rwg.d_triD, rwg.d_slot_edge,
       rwg.d_slot_swd, bc.ntri, rowptr, col, rowptrT, colT, vals, valsT);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   CAL_TRY_CUDA(cudaFreeAsync(d_parent, stream));
   return CAL_OK;

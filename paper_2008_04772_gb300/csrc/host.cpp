@@ -5,6 +5,8 @@
 // (RWG on the primal mesh, BC on its barycentric refinement) of
 // arXiv 2008.04772. All O(N) setup; the O(N^2) numerics run on the GPU.
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -36,6 +38,69 @@ int fail(int code, const char* fmt, ...) {
 }
 
 const char* last_error() { return g_err; }
+
+// ---------------------------------------------------------------------------
+// instrumentation
+// ---------------------------------------------------------------------------
+static std::atomic<int64_t> g_launches{0};
+static std::mutex g_prof_mu;
+static bool g_prof_on = false;
+struct ProfRec {
+  std::string name;
+  double units;
+  cudaEvent_t a, b;
+};
+static std::vector<ProfRec> g_prof;
+
+void note_launch(int n) { g_launches += n; }
+int64_t launches() { return g_launches.load(); }
+
+int prof_begin(cudaStream_t st, const char* name, double units) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (!g_prof_on) return -1;
+  ProfRec r{name, units, nullptr, nullptr};
+  if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
+  cudaEventRecord(r.a, st);
+  g_prof.push_back(r);
+  return (int)g_prof.size() - 1;
+}
+
+void prof_end(cudaStream_t st, int token) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (token < 0 || token >= (int)g_prof.size()) return;
+  cudaEventRecord(g_prof[token].b, st);
+}
+
+int prof_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (auto& r : g_prof) {
+    cudaEventSynchronize(r.b);
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  g_prof.clear();
+  g_prof_on = on != 0;
+  return CAL_OK;
+}
+
+int prof_read(const char* name, int64_t* n, double* ms, double* units) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  int64_t cnt = 0;
+  double tot = 0.0, u = 0.0;
+  for (auto& r : g_prof) {
+    if (r.name != name) continue;
+    if (cudaEventSynchronize(r.b) != cudaSuccess) return fail(CAL_ECUDA, "profile: event wait failed");
+    float t = 0.0f;
+    cudaEventElapsedTime(&t, r.a, r.b);
+    ++cnt;
+    tot += t;
+    u += r.units;
+  }
+  if (n) *n = cnt;
+  if (ms) *ms = tot;
+  if (units) *units = u;
+  return CAL_OK;
+}
 
 // ---------------------------------------------------------------------------
 // quadrature tables

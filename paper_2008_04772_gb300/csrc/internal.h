@@ -28,6 +28,12 @@ int fail(int code, const char* fmt, ...);
                          cudaGetErrorString(_e), __FILE__, __LINE__);         \
   } while (0)
 
+// ---- instrumentation (host.cpp) ------------------------------------------------
+void note_launch(int n = 1);
+// events around one launch of kernel family `name` doing `units` of work
+int prof_begin(cudaStream_t st, const char* name, double units);
+void prof_end(cudaStream_t st, int token);
+
 // ---- device records ----------------------------------------------------------
 // float32 triangle: centroid as hi + lo float pair, vertex offsets from it.
 struct __align__(16) TriF {

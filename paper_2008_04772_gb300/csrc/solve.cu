@@ -464,6 +464,7 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   A.tol2 = tol * tol;
   const dim3 grid(blocks_for(n, 256), nsys);
   CAL_TRY_CUDA(cudaMemsetAsync(A.bnorm2, 0, nsys * sizeof(double), st));
+  const int tok = prof_begin(st, "bicgstab", 0.0);
   bicg_init<R><<<grid, 256, 0, st>>>(A, b);
   bicg_init2<R><<<1, 32 * ((nsys + 31) / 32), 0, st>>>(A);
   for (int k = 0; k < maxit; ++k) {
@@ -472,6 +473,8 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
     bicg_k3<R><<<grid, 256, 0, st>>>(A, k);
   }
   bicg_finish<R><<<grid, 256, 0, st>>>(A, out);
+  prof_end(st, tok);
+  note_launch(3 + 3 * maxit);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -494,11 +497,16 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
   if (b.rowptr) {
     pair_spmv_kernel<MT, VT, AT><<<blocks_for(b.rows * 32, 256), 256, 0, st>>>(
         S, C, b.rowptr, b.col, b.rows, x1, x2, y1, y2, ar, ai, br, bi);
+    note_launch();
   } else {
     constexpr int ROWS = 4;
     const int64_t warps = (b.rows + ROWS - 1) / ROWS;
+    const double bytes = (double)b.rows * b.cols * sizeof(MT) * ((S ? 1 : 0) + (C ? 1 : 0));
+    const int tok = prof_begin(st, "pair_gemv", bytes);
     pair_gemv_kernel<MT, VT, AT, ROWS><<<blocks_for(warps * 32, 256), 256, 0, st>>>(
         S, C, b.rows, b.cols, b.cols, x1, x2, y1, y2, ar, ai, br, bi);
+    prof_end(st, tok);
+    note_launch();
   }
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
@@ -514,6 +522,7 @@ int pair_apply(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t 
 }
 
 int zero_vec(void* y, int prec, int64_t n, cudaStream_t st) {
+  note_launch();
   if (prec == CAL_FP64) zero_kernel<double2><<<blocks_for(n, 256), 256, 0, st>>>((double2*)y, n);
   else zero_kernel<float2><<<blocks_for(n, 256), 256, 0, st>>>((float2*)y, n);
   CAL_TRY_CUDA(cudaGetLastError());
@@ -521,6 +530,7 @@ int zero_vec(void* y, int prec, int64_t n, cudaStream_t st) {
 }
 
 int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale, cudaStream_t st) {
+  note_launch();
   const unsigned g = blocks_for(n, 256);
   if (pa == CAL_FP64 && pb == CAL_FP32) convert_kernel<double2, float2><<<g, 256, 0, st>>>((const double2*)a, (float2*)b, n, scale);
   else if (pa == CAL_FP32 && pb == CAL_FP64) convert_kernel<float2, double2><<<g, 256, 0, st>>>((const float2*)a, (double2*)b, n, scale);
@@ -532,6 +542,7 @@ int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale,
 
 int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st) {
   for (int64_t q = 0; q < nrhs; ++q) {
+    note_launch();
     const unsigned g = blocks_for(op.rows * 32, 256);
     if (op.precision == CAL_FP64) {
       const double2* xx = (const double2*)x + q * op.cols;
@@ -701,6 +712,7 @@ int gmres_cgs_step(const double2* V, int64_t n, int j, double2* w, double2* h1, 
   multi_dot_kernel<<<g, 256, 0, st>>>(V, n, j + 1, w, n, h2);
   multi_axpy_kernel<<<g, 256, 0, st>>>(V, n, j + 1, h2, w, n);
   norm2_kernel<<<g, 256, 0, st>>>(w, n, wn2);
+  note_launch(5);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -708,12 +720,14 @@ int gmres_cgs_step(const double2* V, int64_t n, int j, double2* w, double2* h1, 
 int gmres_givens(double2* H, int ldh, int j, const double2* h1, const double2* h2, const double* wn2,
                  double2* cs, double2* sn, double2* g, double* res, cudaStream_t st) {
   givens_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, wn2, cs, sn, g, res);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
 int gmres_scale(const double2* w, int64_t n, const double* nrm2, double2* out, cudaStream_t st) {
   scale_kernel<<<blocks_for(n, 256), 256, 0, st>>>(w, n, nrm2, out);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -722,6 +736,7 @@ int gmres_update(const double2* H, int ldh, int m, const double2* g, double2* y,
                  int64_t n, double2* x, cudaStream_t st) {
   backsolve_kernel<<<1, 32, 0, st>>>(H, ldh, m, g, y);
   combine_kernel<<<blocks_for(n, 256), 256, 0, st>>>(V, n, m, y, x, n);
+  note_launch(2);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -729,6 +744,7 @@ int gmres_update(const double2* H, int ldh, int m, const double2* g, double2* y,
 int vec_norm2(const double2* w, int64_t n, double* out, cudaStream_t st) {
   CAL_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
   norm2_kernel<<<blocks_for(n, 256), 256, 0, st>>>(w, n, out);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -736,6 +752,7 @@ int vec_norm2(const double2* w, int64_t n, double* out, cudaStream_t st) {
 int vec_axpby(const double2* a, double sa, const double2* b, double sb, double2* out, int64_t n,
               cudaStream_t st) {
   axpby_kernel<<<blocks_for(n, 256), 256, 0, st>>>(a, sa, b, sb, out, n);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -879,6 +896,7 @@ int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double
   dim3 grid(blocks_for(rwg.ntri, 128), nrhs);
   rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_inc, nrhs,
                                    k, mu, rl, rwg.nbasis, d_b);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -889,6 +907,7 @@ int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double
   dim3 grid((unsigned)ndir, nrhs);
   farfield_kernel<<<grid, 256, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_x,
                                         rwg.nbasis, d_dirs, ndir, k, mu, rl, d_out);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }

@@ -71,6 +71,6 @@ int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double
 
 // BC tile launcher (assemble.cu)
 int launch_bc_regular_tiles(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
-                            int64_t ntile, int max_cell, int n_sm);
+                            int64_t ntile, int max_cell, int n_sm, double units);
 
 }  // namespace cal

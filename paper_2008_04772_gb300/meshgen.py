@@ -315,6 +315,20 @@ def cube(origin, side: float, n: int):
     return P, T
 
 
+def bipyramid(n: int, radius: float = 1.0, height: float = 1.0) -> SurfaceMesh:
+    """Double cone over a regular n-gon: two apex vertices of valence n (edge case)."""
+    ang = 2 * math.pi * np.arange(n) / n
+    V = np.concatenate([np.column_stack([radius * np.cos(ang), radius * np.sin(ang), np.zeros(n)]),
+                        [[0.0, 0.0, height], [0.0, 0.0, -height]]])
+    T = []
+    for i in range(n):
+        j = (i + 1) % n
+        T.append((i, j, n))
+        T.append((j, i, n + 1))
+    T = _orient_outward(V, np.array(T, dtype=np.int32), np.zeros(3))
+    return SurfaceMesh(V, T, np.zeros(len(T), dtype=np.int32))
+
+
 def three_cubes(h: float) -> SurfaceMesh:
     """Three cubes of side 0.4 with front-bottom-left corners at x = -1, 0, 1."""
     n = max(1, int(math.ceil(0.4 / h)))

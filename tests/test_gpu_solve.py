@@ -1,0 +1,154 @@
+"""GPU PMCHWT solves against the oracle: solution, far field, counters, errors."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_common import EPS, mesh, rel
+from oracle import mie, pmchwt
+from paper_2008_04772_gb300 import cal, meshgen
+
+pytestmark = pytest.mark.gpu
+INC = meshgen.plane_wave_x_along_z()
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2008_04772_gb300 import build
+    build.build()
+    return cal.Context(0)
+
+
+_oracle = {}
+
+
+def oracle_solution(name, k, precond="D", chi=math.inf, rules_P=(6, 4), inc=INC[0]):
+    key = (name, k, precond, chi, rules_P, tuple(inc))
+    if key not in _oracle:
+        m = mesh(name)
+        pb = pmchwt.PMCHWT(m.verts, m.tris, m.domain, k, EPS, precond=precond, chi_P=chi,
+                           rules_P=rules_P)
+        pb.assemble(need_bc=precond != "I")
+        xd = np.linalg.solve(pb.matrix_A(), pb.rhs(inc))
+        c, d = pb.split(xd)
+        _oracle[key] = (pb, xd, np.concatenate([c, d]))
+    return _oracle[key]
+
+
+def gmesh(ctx, name):
+    m = mesh(name)
+    return cal.Mesh(ctx, m.verts, m.tris, m.domain)
+
+
+@pytest.mark.parametrize("name,k", [("sphere1", 2.0), ("sphere2", 2.0), ("cubes", 2.1)])
+def test_fp64_solution_matches_oracle(ctx, name, k):
+    pb, xd, xo = oracle_solution(name, k)
+    sol = cal.pmchwt_solve(ctx, gmesh(ctx, name), k, EPS, INC,
+                           opts=cal.solve_opts(precond="D", precision=cal.FP64, tol=1e-11))
+    x = sol.coefficients()[0]
+    assert rel(x, xo) < 1e-8
+    dirs = meshgen.sphere_cut_directions(19)
+    assert rel(sol.far_field(dirs)[0], pb.far_field(xd, dirs)) < 1e-8
+
+
+@pytest.mark.parametrize("name,k", [("sphere2", 2.0), ("prisms2", 3.0), ("cubes", 2.1)])
+def test_fp32_bulk_far_field_within_1e4(ctx, name, k):
+    pb, xd, xo = oracle_solution(name, k)
+    sol = cal.pmchwt_solve(ctx, gmesh(ctx, name), k, EPS, INC,
+                           opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-6))
+    dirs = meshgen.fibonacci_directions(64)
+    F, Fo = sol.far_field(dirs)[0], pb.far_field(xd, dirs)
+    assert rel(F, Fo) < 1e-4
+    # RCS sigma = 4 pi |E_inf|^2 within the same bar
+    assert rel(np.sum(abs(F) ** 2, 1), np.sum(abs(Fo) ** 2, 1)) < 2e-4
+
+
+@pytest.mark.parametrize("pc,chi,rules", [("none", math.inf, (6, 4)), ("Di", math.inf, (6, 4)),
+                                          ("De", math.inf, (6, 4)), ("Si", math.inf, (6, 4)),
+                                          ("Se", math.inf, (6, 4)), ("Si", 2.0, (1, 1)),
+                                          ("D", 4.0, (1, 1))])
+def test_preconditioners_same_solution_and_matvec_counts(ctx, pc, chi, rules):
+    _, xd, xo = oracle_solution("sphere1", 2.0, "I")
+    opts = cal.solve_opts(precond=pc, precision=cal.FP64, tol=1e-10, near_cutoff_P=chi,
+                          q_regular_P=rules[0], q_singular_P=rules[1], maxit=600)
+    sol = cal.pmchwt_solve(ctx, gmesh(ctx, "sphere1"), 2.0, EPS, INC, opts=opts)
+    inf = sol.info()
+    assert rel(sol.coefficients()[0], xo) < 1e-7
+    name = {"none": "I"}.get(pc, pc)
+    per_it, init = pmchwt.matvec_units(name, 1)
+    R = inf.iterations
+    assert inf.matvecs == per_it * (R + R // 200) + init
+
+
+def test_restart_and_matvec_formula(ctx):
+    for rho in (3, 7):
+        opts = cal.solve_opts(precond="D", precision=cal.FP64, tol=1e-8, restart=rho, maxit=400)
+        sol = cal.pmchwt_solve(ctx, gmesh(ctx, "sphere1"), 2.0, EPS, INC, opts=opts)
+        inf = sol.info()
+        R = inf.iterations
+        assert inf.matvecs == 16 * (R + R // rho) + 8
+        _, _, xo = oracle_solution("sphere1", 2.0)
+        assert rel(sol.coefficients()[0], xo) < 1e-6
+
+
+def test_iterations_match_oracle_gmres(ctx):
+    m = mesh("sphere1")
+    pb = pmchwt.PMCHWT(m.verts, m.tris, m.domain, 2.0, EPS, precond="D")
+    pb.assemble()
+    _, info = pb.solve(INC[0], tol=1e-6)
+    sol = cal.pmchwt_solve(ctx, gmesh(ctx, "sphere1"), 2.0, EPS, INC,
+                           opts=cal.solve_opts(precond="D", precision=cal.FP64, tol=1e-6))
+    assert abs(sol.info().iterations - info["iterations"]) <= 1
+
+
+def test_multiple_right_hand_sides_equal_solo_solves(ctx):
+    d = meshgen.fibonacci_directions(3)
+    inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+    opts = cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-7)
+    gm = gmesh(ctx, "sphere2")
+    dirs = meshgen.fibonacci_directions(32)
+    multi = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc, opts=opts).far_field(dirs)
+    for q in range(3):
+        solo = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc[q:q + 1], opts=opts).far_field(dirs)[0]
+        assert rel(multi[q], solo) < 1e-5
+
+
+def test_far_field_approaches_mie(ctx):
+    errs = []
+    dirs = meshgen.sphere_cut_directions(37)
+    Fm = mie.far_field(2.0, 1.0, EPS, dirs)
+    for level in (2, 3, 4):
+        m = meshgen.icosphere(level)
+        sol = cal.pmchwt_solve(ctx, cal.Mesh(ctx, m.verts, m.tris, m.domain), 2.0, EPS, INC,
+                               opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-6))
+        errs.append(rel(sol.far_field(dirs)[0], Fm))
+    assert errs[0] < 0.05 and errs[0] > errs[1] > errs[2]
+
+
+def test_errors_are_reported_not_faulted(ctx):
+    m = meshgen.icosphere(1)
+    with pytest.raises(cal.CalError) as e:
+        cal.Mesh(ctx, m.verts, m.tris[:-1])          # open surface
+    assert e.value.code == cal.EMESH
+    bad = m.tris.copy()
+    bad[0] = bad[0][::-1]                              # flipped triangle
+    with pytest.raises(cal.CalError) as e:
+        cal.Mesh(ctx, m.verts, bad)
+    assert e.value.code == cal.EMESH
+    v = m.verts.copy()
+    v[3, 1] = np.nan
+    with pytest.raises(cal.CalError) as e:
+        cal.Mesh(ctx, v, m.tris)
+    assert e.value.code == cal.EINVAL
+    gm = gmesh(ctx, "sphere1")
+    with pytest.raises(cal.CalError) as e:
+        cal.pmchwt_solve(ctx, gm, 2.0, EPS, INC, opts=cal.solve_opts(precision=7))
+    assert e.value.code == cal.EINVAL
+    with pytest.raises(cal.CalError) as e:
+        cal.pmchwt_solve(ctx, gm, -1.0, EPS, INC)
+    assert e.value.code == cal.EINVAL
+    sol = cal.pmchwt_solve(ctx, gm, 2.0, EPS, INC, opts=cal.solve_opts(precision=cal.FP64, maxit=2),
+                           allow_not_converged=True)
+    assert sol.rc == cal.ENOTCONV and sol.info().converged == 0 and sol.info().iterations == 2
+    # the context stays usable after every error
+    assert cal.pmchwt_solve(ctx, gm, 2.0, EPS, INC).info().converged == 1
