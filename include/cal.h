@@ -58,6 +58,9 @@ extern "C" {
 #define CAL_FP64 1         /* all assembly and storage in float64 (complex128)    */
 #define CAL_FP32 2         /* regular pairs in float32, singular pairs in float64,
                               storage complex64 ("FP32 bulk")                      */
+#define CAL_FP32_ALL 3     /* regular and singular pairs in float32 (singular point
+                              differences formed in reference coordinates, so no
+                              cancellation), storage complex64                     */
 
 #define CAL_DENSE 1
 #define CAL_CSR 2
@@ -131,7 +134,8 @@ void cal_space_destroy(cal_space* space);
    q_regular: points per triangle of the regular tensor rule, 6 (degree 4,
    36 evaluations per pair) or 1 (centroid); q_singular: Gauss–Legendre
    points per dimension of the Sauter–Schwab rules, 1..16 (4 gives the
-   paper's 512/1280/1536 evaluations). precision: CAL_FP64 or CAL_FP32. */
+   paper's 512/1280/1536 evaluations). precision: CAL_FP64, CAL_FP32 or
+   CAL_FP32_ALL. */
 int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space* test,
                  cal_space* trial, int scatterer, double near_cutoff, int q_regular,
                  int q_singular, int precision, cal_op** out);
@@ -164,7 +168,7 @@ int cal_gram_export(cal_space* rwg, cal_space* bc, double* dst_host);
 /* ---- PMCHWT solve (eqs. PMCHWT_multiple_scatterers, GalA-MassP) --------- */
 typedef struct {
   int32_t precond;          /* CAL_PRECOND_*                                   */
-  int32_t precision;        /* CAL_FP64 or CAL_FP32 (FP32 bulk)                */
+  int32_t precision;        /* CAL_FP64, CAL_FP32 (FP32 bulk) or CAL_FP32_ALL  */
   int32_t q_regular_A, q_singular_A;   /* A's rules (6, 4 = paper default)     */
   int32_t q_regular_P, q_singular_P;   /* P's rules (bi-parametric: 1, 1)      */
   double near_cutoff_P;     /* chi_P in units of h; INFINITY = dense P          */

@@ -50,7 +50,9 @@ def build(force: bool = False, verbose: bool = False) -> str:
     for f in CU_SOURCES:
         o = os.path.join(OUT_DIR, f + ".o")
         objs.append(o)
-        jobs.append([nvcc, *ARCH, "-lineinfo", "-Xcompiler", "-fPIC", *common, "-c",
+        # -ftz=true: no denormal fix-ups around the float32 rsqrt/sin/cos/exp
+        # hardware approximations (the operands here are never denormal)
+        jobs.append([nvcc, *ARCH, "-lineinfo", "-ftz=true", "-Xcompiler", "-fPIC", *common, "-c",
                      os.path.join(SRC, f), "-o", o])
     for f in CXX_SOURCES:
         o = os.path.join(OUT_DIR, f + ".o")

@@ -20,7 +20,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libcal.so")
 OK, EINVAL, EMESH, ENOMEM, ENOTCONV, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
 RWG, BC = 1, 2
 OP_S, OP_C = 1, 2
-FP64, FP32 = 1, 2
+FP64, FP32, FP32_ALL = 1, 2, 3
 DENSE, CSR = 1, 2
 PRECOND = {"none": 0, "D": 1, "De": 2, "Di": 3, "Se": 4, "Si": 5}
 
@@ -105,6 +105,10 @@ def lib():
         "cal_solution_coefficients": ([P, P], ctypes.c_int),
         "cal_farfield": ([P, P, i64, P], ctypes.c_int),
         "cal_solution_destroy": ([P], None),
+        "cal_kernel_launches": ([], i64),
+        "cal_profile_enable": ([ctypes.c_int], ctypes.c_int),
+        "cal_profile_read": ([ctypes.c_char_p, ctypes.POINTER(i64), ctypes.POINTER(d),
+                              ctypes.POINTER(d)], ctypes.c_int),
     }
     for name, (args, res) in sig.items():
         f = getattr(L, name)

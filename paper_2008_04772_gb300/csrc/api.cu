@@ -62,7 +62,10 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
   const Mesh& m = *sp.mesh;
   if (scat >= m.M) return fail(CAL_EINVAL, "assemble: scatterer %d out of range", scat);
   if (!(want & 3)) return fail(CAL_EINVAL, "assemble: op_mask must contain CAL_OP_S or CAL_OP_C");
-  if (precision != CAL_FP32 && precision != CAL_FP64) return fail(CAL_EINVAL, "assemble: bad precision");
+  if (precision != CAL_FP32 && precision != CAL_FP64 && precision != CAL_FP32_ALL)
+    return fail(CAL_EINVAL, "assemble: bad precision");
+  const bool sing32 = precision == CAL_FP32_ALL;
+  if (sing32) precision = CAL_FP32;
   if (!std::isfinite(kr) || !std::isfinite(ki) || (kr == 0 && ki == 0))
     return fail(CAL_EINVAL, "assemble: wavenumber must be finite and non-zero");
   int rc = set_quadrature_tables(nreg, nsing);
@@ -113,6 +116,7 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
   a.nreg = nreg;
   a.nsing = nsing;
   a.precision = precision;
+  a.sing32 = sing32;
   a.format = op->format;
   a.row_off = op->row_offset;
   a.ld = op->cols;
@@ -171,7 +175,10 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       };
       const int d0 = scat < 0 ? 0 : scat, d1 = scat < 0 ? (int)sp.sing.size() : scat + 1;
       for (int d = d0; d < d1; ++d)
-        for (const SingPair& q : sp.sing[d]) pairs -= cell_of(q.t1) == cell_of(q.t2) ? 1.0 : 0.5;
+        for (const SingPair& q : sp.sing[d]) {
+          const double mult = q.cls == 1 ? 2.0 : 1.0;  // vertex pairs are listed once
+          pairs -= mult * (cell_of(q.t1) == cell_of(q.t2) ? 1.0 : 0.5);
+        }
     }
     if (dense || !tiles.empty())
       rc = launch_bc_regular_tiles(a, d_cells, (int64_t)cells.size(), dense ? nullptr : d_tiles,
@@ -638,7 +645,8 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   P.k_e = k_ext;
   if (opts) P.o = *opts; else opts_default(&P.o);
   const cal_solve_opts& o = P.o;
-  if (o.precision != CAL_FP32 && o.precision != CAL_FP64) return fail(CAL_EINVAL, "solve: bad precision");
+  if (o.precision != CAL_FP32 && o.precision != CAL_FP64 && o.precision != CAL_FP32_ALL)
+    return fail(CAL_EINVAL, "solve: bad precision");
   if (o.precond < CAL_PRECOND_NONE || o.precond > CAL_PRECOND_SI) return fail(CAL_EINVAL, "solve: bad preconditioner");
   if (!(o.tol > 0) || o.restart < 1 || o.maxit < 1) return fail(CAL_EINVAL, "solve: bad tolerance/restart/maxit");
   if (o.rhs_mode != 0) return fail(CAL_EINVAL, "solve: only the total-trace right-hand side is implemented");
@@ -665,14 +673,16 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   }
   const double t_setup = now();
   // A: S, C at k_e on the union; S, C at k_m on each scatterer
-  const int prec = o.precision;
+  const int aprec = o.precision;  // assembly mode (CAL_FP32_ALL: float32 singular pairs)
+  const int prec = aprec == CAL_FP64 ? CAL_FP64 : CAL_FP32;  // storage and vector precision
+  P.o.precision = prec;
   if ((rc = assemble_block(ctx->impl, 3, k_ext, 0.0, *P.rwg, -1, INFINITY, o.q_regular_A, o.q_singular_A,
-                           prec, P.A_ext)))
+                           aprec, P.A_ext)))
     return rc;
   P.A_int.resize(P.M);
   for (int m = 0; m < P.M; ++m)
     if ((rc = assemble_block(ctx->impl, 3, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, INFINITY,
-                             o.q_regular_A, o.q_singular_A, prec, P.A_int[m])))
+                             o.q_regular_A, o.q_singular_A, aprec, P.A_int[m])))
       return rc;
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_A = now();
@@ -691,10 +701,10 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     P.P_int.resize(P.M);
     for (int m = 0; m < P.M; ++m) {
       if (ext && (rc = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P,
-                                      o.q_singular_P, prec, P.P_ext[m])))
+                                      o.q_singular_P, aprec, P.P_ext[m])))
         return rc;
       if (in && (rc = assemble_block(ctx->impl, want, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, chi,
-                                     o.q_regular_P, o.q_singular_P, prec, P.P_int[m])))
+                                     o.q_regular_P, o.q_singular_P, aprec, P.P_int[m])))
         return rc;
       for (auto* op : {P.P_ext[m].get(), P.P_int[m].get()})
         if (op) bytes_P += op->nnz * esz * ((want & 2) ? 2 : 1);
@@ -733,13 +743,13 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     if (prec == CAL_FP64) {
       P.gsA64 = std::make_unique<GramSolver<double>>();
       P.gsP64 = std::make_unique<GramSolver<double>>();
-      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-13, 60))) return rc;
-      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-13, 60))) return rc;
+      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-13, 30))) return rc;
+      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-13, 30))) return rc;
     } else {
       P.gsA32 = std::make_unique<GramSolver<float>>();
       P.gsP32 = std::make_unique<GramSolver<float>>();
-      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-6, 25))) return rc;
-      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-6, 25))) return rc;
+      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-6, 14))) return rc;
+      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-6, 14))) return rc;
     }
   }
   const size_t vbytes = 2 * P.N * sizeof(double2);

@@ -76,8 +76,9 @@ __device__ __forceinline__ V3<R> cross3(const V3<R>& a, const V3<R>& b) {
 // ---------------------------------------------------------------------------
 // kernel values G = e^{ikr}/(4 pi r) and g = (ikr - 1) e^{ikr}/(4 pi r^3)
 // ---------------------------------------------------------------------------
+// w: quadrature weight folded into the amplitude (pass 1 for none)
 __device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, float& Gi,
-                                      float& gr, float& gi) {
+                                      float& gr, float& gi, float w = 1.0f) {
   const float rinv = rsqrtf(r2);
   const float r = r2 * rinv;
   const float ph = kr * r;
@@ -93,7 +94,7 @@ __device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, f
   float s, c;
   __sincosf(th, &s, &c);
   constexpr float INV_4PI = (float)(0.25 / 3.14159265358979323846);
-  float amp = rinv * INV_4PI;
+  float amp = rinv * (w * INV_4PI);
   if (ki != 0.0f) amp *= __expf(-ki * r);
   Gr = amp * c;
   Gi = amp * s;
@@ -104,12 +105,12 @@ __device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, f
 }
 
 __device__ __forceinline__ void green(double r2, double kr, double ki, double& Gr, double& Gi,
-                                      double& gr, double& gi) {
+                                      double& gr, double& gi, double w = 1.0) {
   const double r = sqrt(r2);
   const double rinv = 1.0 / r;
   double s, c;
   sincos(kr * r, &s, &c);
-  double amp = rinv * (0.25 / 3.14159265358979323846);
+  double amp = rinv * (w * (0.25 / 3.14159265358979323846));
   if (ki != 0.0) amp *= exp(-ki * r);
   Gr = amp * c;
   Gi = amp * s;
@@ -219,8 +220,8 @@ struct Sink {
     }
     return -1;
   }
-  __device__ __forceinline__ void add(int i, int j, bool wS, bool wC, double Sr, double Si,
-                                      double Cr, double Ci) const {
+  template <typename V>
+  __device__ __forceinline__ void add(int i, int j, bool wS, bool wC, V Sr, V Si, V Cr, V Ci) const {
     const int64_t k = index(i, j);
     if (k < 0) return;
     if (wS) atomic_add_c(S, k, (RO)Sr, (RO)Si);
@@ -276,6 +277,86 @@ __device__ __forceinline__ void regular_moments(const V3<R>* xi, const R* wx, co
     }
   }
 }
+
+// same sums with both point sets staged as (x, y, z, weight) quadruples
+template <typename R> struct __align__(4 * sizeof(R)) P4 { R x, y, z, w; };
+
+template <typename R, int NREG>
+__device__ __forceinline__ void regular_moments_staged(const P4<R>* __restrict__ X,
+                                                       const P4<R>* __restrict__ Y, const V3<R>& D,
+                                                       R kr, R ki, bool wantC, Mom<R>& m) {
+  m.zero();
+#pragma unroll 2
+  for (int p = 0; p < NREG; ++p) {
+    const P4<R> xp = X[p];
+    R s0r = 0, s0i = 0, t0r = 0, t0i = 0;
+    V3<R> ser = {0, 0, 0}, sei = {0, 0, 0}, ter = {0, 0, 0}, tei = {0, 0, 0};
+    const V3<R> dp = {D.x + xp.x, D.y + xp.y, D.z + xp.z};
+#pragma unroll
+    for (int q = 0; q < NREG; ++q) {
+      const P4<R> yq = Y[q];
+      const R dx = dp.x - yq.x, dy = dp.y - yq.y, dz = dp.z - yq.z;
+      R Gr, Gi, gr, gi;
+      green(dx * dx + dy * dy + dz * dz, kr, ki, Gr, Gi, gr, gi, yq.w);
+      s0r += Gr; s0i += Gi;
+      ser.x += Gr * yq.x; ser.y += Gr * yq.y; ser.z += Gr * yq.z;
+      sei.x += Gi * yq.x; sei.y += Gi * yq.y; sei.z += Gi * yq.z;
+      if (wantC) {
+        t0r += gr; t0i += gi;
+        ter.x += gr * yq.x; ter.y += gr * yq.y; ter.z += gr * yq.z;
+        tei.x += gi * yq.x; tei.y += gi * yq.y; tei.z += gi * yq.z;
+      }
+    }
+    const R w = xp.w;
+    const V3<R> x = {xp.x, xp.y, xp.z};
+    m.G0r += w * s0r; m.G0i += w * s0i;
+    m.Gxr.x += w * x.x * s0r; m.Gxr.y += w * x.y * s0r; m.Gxr.z += w * x.z * s0r;
+    m.Gxi.x += w * x.x * s0i; m.Gxi.y += w * x.y * s0i; m.Gxi.z += w * x.z * s0i;
+    m.Gyr.x += w * ser.x; m.Gyr.y += w * ser.y; m.Gyr.z += w * ser.z;
+    m.Gyi.x += w * sei.x; m.Gyi.y += w * sei.y; m.Gyi.z += w * sei.z;
+    m.Gxyr += w * dot3(x, ser); m.Gxyi += w * dot3(x, sei);
+    if (wantC) {
+      m.g0r += w * t0r; m.g0i += w * t0i;
+      m.gxr.x += w * x.x * t0r; m.gxr.y += w * x.y * t0r; m.gxr.z += w * x.z * t0r;
+      m.gxi.x += w * x.x * t0i; m.gxi.y += w * x.y * t0i; m.gxi.z += w * x.z * t0i;
+      m.gyr.x += w * ter.x; m.gyr.y += w * ter.y; m.gyr.z += w * ter.z;
+      m.gyi.x += w * tei.x; m.gyi.y += w * tei.y; m.gyi.z += w * tei.z;
+      const V3<R> cr = cross3(x, ter), ci = cross3(x, tei);
+      m.gxyr.x += w * cr.x; m.gxyr.y += w * cr.y; m.gxyr.z += w * cr.z;
+      m.gxyi.x += w * ci.x; m.gxyi.y += w * ci.y; m.gxyi.z += w * ci.z;
+    }
+  }
+}
+
+// one quadrature point of a triangle (relative to its centroid) and its weight
+__device__ __forceinline__ P4<float> staged_point(const TriF& t, const Rules& rl, int q) {
+  const float b0 = rl.rbf[3 * q], b1 = rl.rbf[3 * q + 1], b2 = rl.rbf[3 * q + 2];
+  return {b0 * t.off[0][0] + b1 * t.off[1][0] + b2 * t.off[2][0],
+          b0 * t.off[0][1] + b1 * t.off[1][1] + b2 * t.off[2][1],
+          b0 * t.off[0][2] + b1 * t.off[1][2] + b2 * t.off[2][2], rl.rwf[q] * t.area};
+}
+__device__ __forceinline__ P4<double> staged_point(const TriD& t, const Rules& rl, int q) {
+  const double b0 = rl.rbd[3 * q], b1 = rl.rbd[3 * q + 1], b2 = rl.rbd[3 * q + 2];
+  return {b0 * t.off[0][0] + b1 * t.off[1][0] + b2 * t.off[2][0],
+          b0 * t.off[0][1] + b1 * t.off[1][1] + b2 * t.off[2][1],
+          b0 * t.off[0][2] + b1 * t.off[1][2] + b2 * t.off[2][2], rl.rwd[q] * t.area};
+}
+
+// centroid difference from staged centroids: float keeps hi + lo parts
+template <typename R> struct Cent;
+template <> struct Cent<float> {
+  float hi[3], lo[3];
+  __device__ void set(const TriF& t) { for (int c = 0; c < 3; ++c) { hi[c] = t.chi[c]; lo[c] = t.clo[c]; } }
+  __device__ V3<float> minus(const Cent& b) const {
+    return {(hi[0] - b.hi[0]) + (lo[0] - b.lo[0]), (hi[1] - b.hi[1]) + (lo[1] - b.lo[1]),
+            (hi[2] - b.hi[2]) + (lo[2] - b.lo[2])};
+  }
+};
+template <> struct Cent<double> {
+  double c[3];
+  __device__ void set(const TriD& t) { for (int q = 0; q < 3; ++q) c[q] = t.c[q]; }
+  __device__ V3<double> minus(const Cent& b) const { return {c[0] - b.c[0], c[1] - b.c[1], c[2] - b.c[2]}; }
+};
 
 // triangle loaders: quadrature points relative to the centroid and weights
 template <int NREG>
@@ -395,30 +476,57 @@ __device__ __forceinline__ void decode_upper(int64_t k, int64_t n, int64_t& i, i
 }
 
 template <typename R, int NREG>
-__global__ void __launch_bounds__(128) bc_tile_kernel(
+__global__ void __launch_bounds__(160, sizeof(R) == 4 ? 3 : 2) bc_tile_kernel(
     const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
     const R* __restrict__ slot_sw, int nslot, const int* __restrict__ cell_ptr,
     const int* __restrict__ cell_tri, TileList tl, R kr, R ki, R mikr, R miki, R c4r, R c4i,
     bool wantS, bool wantC, Rules rl, Sink<R> out, int max_cell, int chunk) {
   using TRI = typename TriOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  R* pcs = reinterpret_cast<R*>(smem_raw);                          // [chunk * max_cell][36]
-  R* red = pcs + (size_t)chunk * max_cell * 36;                     // [chunk][nslot][18]
+  // pair coefficients component-major with an odd stride: pcs[c * PS + pair]
+  const int PS = (chunk * max_cell) | 1;
+  R* pcs = reinterpret_cast<R*>(smem_raw);                          // [36][PS]
+  R* red = pcs + (size_t)PS * 36;                                   // [chunk][nslot][18]
   R* acc = red + (size_t)chunk * nslot * 18;                        // [nslot][nslot][4]
+  const size_t staged_off =
+      ((((size_t)PS * 36 + (size_t)chunk * nslot * 18 + (size_t)nslot * nslot * 4) * sizeof(R) + 15) / 16) * 16;
+  P4<R>* ptsA = reinterpret_cast<P4<R>*>(smem_raw + staged_off);     // [max_cell][NREG]
+  P4<R>* ptsB = ptsA + (size_t)max_cell * NREG;                      // [max_cell][NREG]
+  Cent<R>* cA = reinterpret_cast<Cent<R>*>(ptsB + (size_t)max_cell * NREG);
+  Cent<R>* cB = cA + max_cell;
+  int* vidA = reinterpret_cast<int*>(cB + max_cell);                // [max_cell][3]
+  int* vidB = vidA + 3 * max_cell;
+  __shared__ int s_vw[2];
   const int64_t ntiles = tl.tiles ? tl.ntile : tl.ncell * (tl.ncell + 1) / 2;
   for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
-    int v, w;
-    if (tl.tiles) {
-      v = tl.tiles[k].x;
-      w = tl.tiles[k].y;
-    } else {
-      int64_t i, j;
-      decode_upper(k, tl.ncell, i, j);
-      v = tl.cells[i];
-      w = tl.cells[j];
+    if (threadIdx.x == 0) {
+      if (tl.tiles) {
+        s_vw[0] = tl.tiles[k].x;
+        s_vw[1] = tl.tiles[k].y;
+      } else {
+        int64_t i, j;
+        decode_upper(k, tl.ncell, i, j);
+        s_vw[0] = tl.cells[i];
+        s_vw[1] = tl.cells[j];
+      }
     }
+    __syncthreads();
+    const int v = s_vw[0], w = s_vw[1];
     const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
     const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
+    // stage the quadrature points, centroids and vertex ids of both cells
+    for (int q = threadIdx.x; q < (n1 + n2) * NREG; q += blockDim.x) {
+      const bool first = q < n1 * NREG;
+      const int qq = first ? q : q - n1 * NREG;
+      const int t = qq / NREG, u = qq % NREG;
+      const TRI T = tri[cell_tri[(first ? b1 : b2) + t]];
+      (first ? ptsA : ptsB)[t * NREG + u] = staged_point(T, rl, u);
+      if (u == 0) {
+        (first ? cA : cB)[t].set(T);
+        int* vd = (first ? vidA : vidB) + 3 * t;
+        vd[0] = T.vid[0]; vd[1] = T.vid[1]; vd[2] = T.vid[2];
+      }
+    }
     // number of valid slots of each cell
     int ns1 = 0, ns2 = 0;
     {
@@ -427,29 +535,31 @@ __global__ void __launch_bounds__(128) bc_tile_kernel(
       while (ns2 < nslot && slot_edge[(size_t)tw * nslot + ns2] >= 0) ++ns2;
     }
     for (int q = threadIdx.x; q < ns1 * ns2 * 4; q += blockDim.x) acc[q] = R(0);
+    __syncthreads();
     for (int c0 = 0; c0 < n1; c0 += chunk) {
       const int nc = min(chunk, n1 - c0);
       // stage 1: pair coefficients of (tau1 in the chunk) x (tau2 in D(w))
       for (int p = threadIdx.x; p < nc * n2; p += blockDim.x) {
-        const int tau1 = cell_tri[b1 + c0 + p / n2], tau2 = cell_tri[b2 + p % n2];
-        const TRI A = tri[tau1];
-        const TRI B = tri[tau2];
-        R* pc = pcs + (size_t)p * 36;
-        if (touching(A, B)) {
-          for (int q = 0; q < 36; ++q) pc[q] = R(0);
+        const int i1 = c0 + p / n2, i2 = p % n2;
+        const int* va = vidA + 3 * i1;
+        const int* vb = vidB + 3 * i2;
+        bool touch = false;
+#pragma unroll
+        for (int x = 0; x < 3; ++x)
+#pragma unroll
+          for (int y = 0; y < 3; ++y) touch |= va[x] == vb[y];
+        R* pc = pcs + p;
+        if (touch) {
+          for (int q = 0; q < 36; ++q) pc[q * PS] = R(0);
           continue;
         }
-        V3<R> xi[NREG], eta[NREG];
-        R wx[NREG], wy[NREG];
-        load_points<NREG>(A, rl, xi, wx);
-        load_points<NREG>(B, rl, eta, wy);
-        const V3<R> D = centroid_delta(A, B);
+        const V3<R> D = cA[i1].minus(cB[i2]);
         Mom<R> m;
-        regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, wantC, m);
+        regular_moments_staged<R, NREG>(ptsA + i1 * NREG, ptsB + i2 * NREG, D, kr, ki, wantC, m);
         R tmp[36];
         pair_coeffs(m, D, tmp);
 #pragma unroll
-        for (int q = 0; q < 36; ++q) pc[q] = tmp[q];
+        for (int q = 0; q < 36; ++q) pc[q * PS] = tmp[q];
       }
       __syncthreads();
       // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side factors
@@ -462,23 +572,25 @@ __global__ void __launch_bounds__(128) bc_tile_kernel(
           const R* sw = slot_sw + ((size_t)tau2 * nslot + sb_i) * 4;
           const R sb = sw[0];
           const V3<R> wb = {sw[1], sw[2], sw[3]};
-          const R* pc = pcs + (size_t)(i1 * n2 + i2) * 36;
+          const R* q0 = pcs + (i1 * n2 + i2);
+#define PC(c) q0[(c) * PS]
           if (wantS) {
-            AS_r += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
-            AS_i += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
-            BS_r += sb * pc[0];
-            BS_i += sb * pc[1];
-            WS_r.x += sb * pc[8] + wb.x * pc[0]; WS_r.y += sb * pc[9] + wb.y * pc[0]; WS_r.z += sb * pc[10] + wb.z * pc[0];
-            WS_i.x += sb * pc[11] + wb.x * pc[1]; WS_i.y += sb * pc[12] + wb.y * pc[1]; WS_i.z += sb * pc[13] + wb.z * pc[1];
+            AS_r += sb * PC(14) + wb.x * PC(2) + wb.y * PC(3) + wb.z * PC(4);
+            AS_i += sb * PC(15) + wb.x * PC(5) + wb.y * PC(6) + wb.z * PC(7);
+            BS_r += sb * PC(0);
+            BS_i += sb * PC(1);
+            WS_r.x += sb * PC(8) + wb.x * PC(0); WS_r.y += sb * PC(9) + wb.y * PC(0); WS_r.z += sb * PC(10) + wb.z * PC(0);
+            WS_i.x += sb * PC(11) + wb.x * PC(1); WS_i.y += sb * PC(12) + wb.y * PC(1); WS_i.z += sb * PC(13) + wb.z * PC(1);
           }
           if (wantC) {
-            AC_r += sb * pc[16] + wb.x * pc[18] + wb.y * pc[19] + wb.z * pc[20];
-            AC_i += sb * pc[17] + wb.x * pc[21] + wb.y * pc[22] + wb.z * pc[23];
-            const V3<R> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
+            AC_r += sb * PC(16) + wb.x * PC(18) + wb.y * PC(19) + wb.z * PC(20);
+            AC_i += sb * PC(17) + wb.x * PC(21) + wb.y * PC(22) + wb.z * PC(23);
+            const V3<R> Vr = {PC(30), PC(31), PC(32)}, Vi = {PC(33), PC(34), PC(35)};
             const V3<R> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
-            WC_r.x += sb * pc[24] + cr.x; WC_r.y += sb * pc[25] + cr.y; WC_r.z += sb * pc[26] + cr.z;
-            WC_i.x += sb * pc[27] + ci.x; WC_i.y += sb * pc[28] + ci.y; WC_i.z += sb * pc[29] + ci.z;
+            WC_r.x += sb * PC(24) + cr.x; WC_r.y += sb * PC(25) + cr.y; WC_r.z += sb * PC(26) + cr.z;
+            WC_i.x += sb * PC(27) + ci.x; WC_i.y += sb * PC(28) + ci.y; WC_i.z += sb * PC(29) + ci.z;
           }
+#undef PC
         }
         R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
         o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
@@ -557,6 +669,156 @@ __device__ __forceinline__ void ss_map(int cls, int r, double xi, double e1, dou
     jac = xi * xi * xi * e2;
     if (r == 0) { xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * e2; yh[1] = xi * e2 * e3; }
     else { xh[0] = xi * e2; xh[1] = xi * e2 * e3; yh[0] = xi; yh[1] = xi * e1; }
+  }
+}
+
+// Float32 variant of the singular rules. Near the singularity x - y is small
+// while x and y are not, so instead of subtracting mapped points the
+// difference is assembled from reference-coordinate differences that each
+// map yields in closed form (e.g. x1 - y1 = xi e1 e2 in the first identical
+// sub-region) times the panel edge vectors; shared vertices cancel exactly.
+__device__ __forceinline__ void ss_map_f32(int cls, int r, float xi, float e1, float e2, float e3,
+                                           float* xh, float* yh, float* dh, float& jac) {
+  if (cls == 3) {
+    jac = xi * xi * xi * e1 * e1 * e2;
+    const float a = xi * e1 * e2, b = a * e3;  // xi e1 e2, xi e1 e2 e3
+    switch (r) {
+      case 0: xh[0] = xi; xh[1] = xi * (1 - e1 + e1 * e2); yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * (1 - e1);
+              dh[0] = b; dh[1] = a; break;
+      case 1: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * (1 - e1); yh[0] = xi; yh[1] = xi * (1 - e1 + e1 * e2);
+              dh[0] = -b; dh[1] = -a; break;
+      case 2: xh[0] = xi; xh[1] = xi * e1 * (1 - e2 + e2 * e3); yh[0] = xi * (1 - e1 * e2); yh[1] = xi * e1 * (1 - e2);
+              dh[0] = a; dh[1] = b; break;
+      case 3: xh[0] = xi * (1 - e1 * e2); xh[1] = xi * e1 * (1 - e2); yh[0] = xi; yh[1] = xi * e1 * (1 - e2 + e2 * e3);
+              dh[0] = -a; dh[1] = -b; break;
+      case 4: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * (1 - e2 * e3); yh[0] = xi; yh[1] = xi * e1 * (1 - e2);
+              dh[0] = -b; dh[1] = a * (1 - e3); break;
+      default: xh[0] = xi; xh[1] = xi * e1 * (1 - e2); yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * e1 * (1 - e2 * e3);
+               dh[0] = b; dh[1] = -a * (1 - e3); break;
+    }
+  } else if (cls == 2) {
+    jac = xi * xi * xi * e1 * e1 * (r == 0 ? 1.0f : e2);
+    switch (r) {
+      case 0: xh[0] = xi; xh[1] = xi * e1 * e3; yh[0] = xi * (1 - e1 * e2); yh[1] = xi * e1 * (1 - e2);
+              dh[0] = xi * e1 * e2; break;
+      case 1: xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * (1 - e1 * e2 * e3); yh[1] = xi * e1 * e2 * (1 - e3);
+              dh[0] = xi * e1 * e2 * e3; break;
+      case 2: xh[0] = xi * (1 - e1 * e2); xh[1] = xi * e1 * (1 - e2); yh[0] = xi; yh[1] = xi * e1 * e2 * e3;
+              dh[0] = -xi * e1 * e2; break;
+      case 3: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * e2 * (1 - e3); yh[0] = xi; yh[1] = xi * e1;
+              dh[0] = -xi * e1 * e2 * e3; break;
+      default: xh[0] = xi * (1 - e1 * e2 * e3); xh[1] = xi * e1 * (1 - e2 * e3); yh[0] = xi; yh[1] = xi * e1 * e2;
+               dh[0] = -xi * e1 * e2 * e3; break;
+    }
+    dh[1] = 0.0f;  // unused: the second coordinates lie on different panels
+  } else {
+    jac = xi * xi * xi * e2;
+    if (r == 0) { xh[0] = xi; xh[1] = xi * e1; yh[0] = xi * e2; yh[1] = xi * e2 * e3; }
+    else { xh[0] = xi * e2; xh[1] = xi * e2 * e3; yh[0] = xi; yh[1] = xi * e1; }
+    dh[0] = dh[1] = 0.0f;
+  }
+}
+
+struct RulesF { float gx[16], gw[16]; int ng; };
+
+__global__ void __launch_bounds__(128) singular_kernel_f32(
+    const TriF* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
+    const int* __restrict__ slot_edge, const float* __restrict__ slot_sw, int nslot, float kr,
+    float ki, float mikr, float miki, float c4r, float c4i, bool wantS, bool wantC, RulesF rl,
+    Sink<float> out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= np) return;
+  const SingPair sp = pairs[p];
+  const TriF A = tri[sp.t1];
+  const TriF B = tri[sp.t2];
+  const int cls = sp.cls;
+  const bool doC = wantC && cls != 3;
+  V3<float> Q1[3], Q2[3];
+  for (int a = 0; a < 3; ++a) {
+    Q1[a] = {A.off[sp.o1[a]][0], A.off[sp.o1[a]][1], A.off[sp.o1[a]][2]};
+    Q2[a] = {B.off[sp.o2[a]][0], B.off[sp.o2[a]][1], B.off[sp.o2[a]][2]};
+  }
+  const V3<float> E1 = {Q1[1].x - Q1[0].x, Q1[1].y - Q1[0].y, Q1[1].z - Q1[0].z};
+  const V3<float> F1 = {Q1[2].x - Q1[1].x, Q1[2].y - Q1[1].y, Q1[2].z - Q1[1].z};
+  const V3<float> E2 = {Q2[1].x - Q2[0].x, Q2[1].y - Q2[0].y, Q2[1].z - Q2[0].z};
+  const V3<float> F2 = {Q2[2].x - Q2[1].x, Q2[2].y - Q2[1].y, Q2[2].z - Q2[1].z};
+  const V3<float> D = centroid_delta(A, B);
+  const float scale = 4.0f * A.area * B.area;
+  const int ng = rl.ng, nreg = (cls == 3 ? 6 : (cls == 2 ? 5 : 2));
+  const int ng2 = ng * ng, ng4 = ng2 * ng2;
+  Mom<float> m;
+  m.zero();
+  for (int idx = lane; idx < nreg * ng4; idx += 32) {
+    const int r = idx / ng4;
+    int rem = idx - r * ng4;
+    const int a0 = rem / (ng2 * ng);
+    rem -= a0 * ng2 * ng;
+    const int a1 = rem / ng2;
+    rem -= a1 * ng2;
+    const int a2 = rem / ng, a3 = rem - a2 * ng;
+    float xh[2], yh[2], dh[2], jac;
+    ss_map_f32(cls, r, rl.gx[a0], rl.gx[a1], rl.gx[a2], rl.gx[a3], xh, yh, dh, jac);
+    const float w = rl.gw[a0] * rl.gw[a1] * rl.gw[a2] * rl.gw[a3] * jac * scale;
+    const V3<float> x = {Q1[0].x + xh[0] * E1.x + xh[1] * F1.x, Q1[0].y + xh[0] * E1.y + xh[1] * F1.y,
+                         Q1[0].z + xh[0] * E1.z + xh[1] * F1.z};
+    const V3<float> y = {Q2[0].x + yh[0] * E2.x + yh[1] * F2.x, Q2[0].y + yh[0] * E2.y + yh[1] * F2.y,
+                         Q2[0].z + yh[0] * E2.z + yh[1] * F2.z};
+    V3<float> d;  // x - y without cancellation
+    if (cls == 3) {
+      d = {dh[0] * E1.x + dh[1] * F1.x, dh[0] * E1.y + dh[1] * F1.y, dh[0] * E1.z + dh[1] * F1.z};
+    } else if (cls == 2) {
+      d = {dh[0] * E1.x + xh[1] * F1.x - yh[1] * F2.x, dh[0] * E1.y + xh[1] * F1.y - yh[1] * F2.y,
+           dh[0] * E1.z + xh[1] * F1.z - yh[1] * F2.z};
+    } else {
+      d = {xh[0] * E1.x + xh[1] * F1.x - yh[0] * E2.x - yh[1] * F2.x,
+           xh[0] * E1.y + xh[1] * F1.y - yh[0] * E2.y - yh[1] * F2.y,
+           xh[0] * E1.z + xh[1] * F1.z - yh[0] * E2.z - yh[1] * F2.z};
+    }
+    float Gr, Gi, gr, gi;
+    green(d.x * d.x + d.y * d.y + d.z * d.z, kr, ki, Gr, Gi, gr, gi);
+    Gr *= w; Gi *= w; gr *= w; gi *= w;
+    m.G0r += Gr; m.G0i += Gi;
+    m.Gxr.x += Gr * x.x; m.Gxr.y += Gr * x.y; m.Gxr.z += Gr * x.z;
+    m.Gxi.x += Gi * x.x; m.Gxi.y += Gi * x.y; m.Gxi.z += Gi * x.z;
+    m.Gyr.x += Gr * y.x; m.Gyr.y += Gr * y.y; m.Gyr.z += Gr * y.z;
+    m.Gyi.x += Gi * y.x; m.Gyi.y += Gi * y.y; m.Gyi.z += Gi * y.z;
+    const float xy = dot3(x, y);
+    m.Gxyr += Gr * xy; m.Gxyi += Gi * xy;
+    if (doC) {
+      const V3<float> xy3 = cross3(x, y);
+      m.g0r += gr; m.g0i += gi;
+      m.gxr.x += gr * x.x; m.gxr.y += gr * x.y; m.gxr.z += gr * x.z;
+      m.gxi.x += gi * x.x; m.gxi.y += gi * x.y; m.gxi.z += gi * x.z;
+      m.gyr.x += gr * y.x; m.gyr.y += gr * y.y; m.gyr.z += gr * y.z;
+      m.gyi.x += gi * y.x; m.gyi.y += gi * y.y; m.gyi.z += gi * y.z;
+      m.gxyr.x += gr * xy3.x; m.gxyr.y += gr * xy3.y; m.gxyr.z += gr * xy3.z;
+      m.gxyi.x += gi * xy3.x; m.gxyi.y += gi * xy3.y; m.gxyi.z += gi * xy3.z;
+    }
+  }
+  float* mv = reinterpret_cast<float*>(&m);
+  constexpr int NM = sizeof(Mom<float>) / sizeof(float);
+#pragma unroll
+  for (int q = 0; q < NM; ++q) {
+    float v = mv[q];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    mv[q] = v;
+  }
+  float pc[36];
+  pair_coeffs(m, D, pc);
+  for (int q = lane; q < nslot * nslot; q += 32) {
+    const int a = q / nslot, b = q % nslot;
+    const int ea = slot_edge[(size_t)sp.t1 * nslot + a];
+    const int eb = slot_edge[(size_t)sp.t2 * nslot + b];
+    if (ea < 0 || eb < 0) continue;
+    const float* swa = slot_sw + ((size_t)sp.t1 * nslot + a) * 4;
+    const float* swb = slot_sw + ((size_t)sp.t2 * nslot + b) * 4;
+    const V3<float> wa = {swa[1], swa[2], swa[3]}, wb = {swb[1], swb[2], swb[3]};
+    float Sr = 0, Si = 0, Cr = 0, Ci = 0;
+    entry_from_pc(pc, swa[0], wa, swb[0], wb, mikr, miki, c4r, c4i, wantS, doC, Sr, Si, Cr, Ci);
+    out.add(ea, eb, wantS, doC, Sr, Si, Cr, Ci);
+    if (cls == 1) out.add(eb, ea, wantS, doC, Sr, Si, Cr, Ci);
   }
 }
 
@@ -649,6 +911,9 @@ __global__ void __launch_bounds__(128) singular_kernel(
     double Sr = 0, Si = 0, Cr = 0, Ci = 0;
     entry_from_pc(pc, swa[0], wa, swb[0], wb, mikr, miki, c4r, c4i, wantS, doC, Sr, Si, Cr, Ci);
     out.add(ea, eb, wantS, doC, Sr, Si, Cr, Ci);
+    // vertex-sharing pairs are stored once (t1 < t2): the two-region rule maps
+    // onto itself when the triangles swap roles, so (t2, t1) gives the transpose
+    if (cls == 1) out.add(eb, ea, wantS, doC, Sr, Si, Cr, Ci);
   }
 }
 
@@ -746,9 +1011,9 @@ static int rwg_regular_t(const AssembleArgs& a) {
   if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
   else { tri = s.d_triD; sw = s.d_slot_swd; }
   // algorithmic work: unordered non-touching pairs x rule points squared
-  int64_t nsing = 0;
+  int64_t nsing = 0;  // ordered touching pairs (vertex pairs are listed once)
   for (int d = (a.scat < 0 ? 0 : a.scat); d < (a.scat < 0 ? (int)s.sing.size() : a.scat + 1); ++d)
-    nsing += (int64_t)s.sing[d].size();
+    for (const SingPair& q : s.sing[d]) nsing += q.cls == 1 ? 2 : 1;
   const double units = ((double)ntr * (ntr - 1) / 2 - (double)(nsing - ntr) / 2) * a.nreg * a.nreg;
   const int tok = prof_begin(a.stream, "rwg_regular", units);
   if (a.nreg == 6) {
@@ -786,7 +1051,12 @@ static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, 
   if (ntiles == 0) return CAL_OK;
   // test-cell triangles are processed in chunks so that any valence fits
   auto smem_for = [&](int ch) {
-    return ((size_t)ch * max_cell * 36 + (size_t)ch * s.nslot * 18 + (size_t)s.nslot * s.nslot * 4) * sizeof(R);
+    const size_t reals = (size_t)((ch * max_cell) | 1) * 36 + (size_t)ch * s.nslot * 18 +
+                         (size_t)s.nslot * s.nslot * 4;
+    const size_t staged = 2 * (size_t)max_cell * a.nreg * 4 * sizeof(R) +      // points
+                          2 * (size_t)max_cell * (sizeof(R) == 4 ? 24 : 24) +  // centroids
+                          2 * (size_t)max_cell * 3 * sizeof(int);              // vertex ids
+    return ((reals * sizeof(R) + 15) / 16) * 16 + staged + 64;
   };
   int chunk = max_cell;
   while (chunk > 1 && smem_for(chunk) > 96 * 1024) --chunk;
@@ -801,10 +1071,11 @@ static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, 
   auto kern = a.nreg == 6 ? kern6 : kern1;
   CAL_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
-  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+  constexpr int TILE_THREADS = 160;
+  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_THREADS, smem));
   const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * n_sm * 4);
   const int tok = prof_begin(a.stream, "bc_tile", units);
-  kern<<<(unsigned)grid, 128, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr,
+  kern<<<(unsigned)grid, TILE_THREADS, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr,
                                                 s.d_cell_tri, tl, (R)a.kr, (R)a.ki, mikr, miki, c4r,
                                                 c4i, wS, wC, g_rules, out, max_cell, chunk);
   prof_end(a.stream, tok);
@@ -834,7 +1105,16 @@ int launch_singular(const AssembleArgs& a) {
     for (const SingPair& q : s.sing[d]) regions += (q.cls == 3 ? 6 : (q.cls == 2 ? 5 : 2));
     const double ng2 = (double)a.nsing * a.nsing;
     const int tok = prof_begin(a.stream, "singular", regions * ng2 * ng2);
-    if (a.precision == CAL_FP32) {
+    if (a.sing32) {
+      RulesF rf{};
+      for (int q = 0; q < 16; ++q) { rf.gx[q] = (float)g_rules.gx[q]; rf.gw[q] = (float)g_rules.gw[q]; }
+      rf.ng = g_rules.ng;
+      float fmr, fmi, f4r, f4i;
+      wave_scalars(a.kr, a.ki, fmr, fmi, f4r, f4i);
+      singular_kernel_f32<<<grid, 128, 0, a.stream>>>(s.d_triF, s.d_sing[d], np, s.d_slot_edge, s.d_slot_swf,
+                                                      s.nslot, (float)a.kr, (float)a.ki, fmr, fmi, f4r, f4i,
+                                                      wS, wC, rf, make_sink<float>(a));
+    } else if (a.precision == CAL_FP32) {
       singular_kernel<float><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
                                                          s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,
                                                          c4r, c4i, wS, wC, g_rules, make_sink<float>(a));

@@ -492,6 +492,11 @@ void build_singular_pairs(Space& s) {
       const int* i1 = s.triD[t].vid;
       for (int u : nb) {
         const int* i2 = s.triD[u].vid;
+        int shared = 0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) shared += i1[a] == i2[b];
+        // vertex-sharing pairs: keep one order, the kernel adds the transpose
+        if (shared == 1 && u < t) continue;
         SingPair p{};
         p.t1 = (int)t;
         p.t2 = u;

@@ -153,7 +153,8 @@ struct AssembleArgs {
   double kr, ki;
   int want;             // bit 1 S, bit 2 C
   int nreg, nsing;      // regular points per triangle, GL points per dimension
-  int precision;
+  int precision;         // storage/regular-pair precision: CAL_FP32 or CAL_FP64
+  int sing32;            // singular pairs in float32 (CAL_FP32_ALL)
   int format;
   // dense output
   int64_t row_off, ld;

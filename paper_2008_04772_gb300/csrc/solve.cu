@@ -6,6 +6,7 @@
 // the far field of the Stratton–Chu representation (eq. StrattonChu_ext).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -86,6 +87,201 @@ __global__ void __launch_bounds__(256) pair_gemv_kernel(
       b.y += cx2[q].y + br * sx1[q].y + bi * sx1[q].x;
       y1[r] = a;
       y2[r] = b;
+    }
+  }
+}
+
+// Vectorised variant for complex64 matrices with an even leading dimension:
+// every lane streams 16-byte words (two complex entries) of ROWS rows of S
+// and C, with two column steps in flight, so that enough bytes are
+// outstanding per SM to run at HBM bandwidth. x is read through L1/L2.
+template <typename VT> struct Pair2;
+template <> struct Pair2<float2> {
+  __device__ static void load(const float2* x, int64_t c2, float2& a, float2& b) {
+    const float4 q = reinterpret_cast<const float4*>(x)[c2];
+    a = {q.x, q.y};
+    b = {q.z, q.w};
+  }
+};
+template <> struct Pair2<double2> {
+  __device__ static void load(const double2* x, int64_t c2, double2& a, double2& b) {
+    a = x[2 * c2];
+    b = x[2 * c2 + 1];
+  }
+};
+
+template <typename VT, typename AT, int ROWS>
+__global__ void __launch_bounds__(256, 2) pair_gemv_vec_kernel(
+    const float4* __restrict__ S, const float4* __restrict__ C, int64_t nr, int64_t nc,
+    int64_t ld2, const VT* __restrict__ x1, const VT* __restrict__ x2, VT* __restrict__ y1,
+    VT* __restrict__ y2, double ar, double ai, double br, double bi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t r0 = warp * ROWS;
+  if (r0 >= nr) return;
+  const int64_t nc2 = nc >> 1;
+  AT cx1[ROWS], cx2[ROWS], sx1[ROWS], sx2[ROWS];
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) cx1[q] = cx2[q] = sx1[q] = sx2[q] = AT{0, 0};
+  const bool hasC = C != nullptr, hasS = S != nullptr;
+  // U column steps are loaded before any is consumed: U * ROWS * 2 16-byte words
+  // per lane in flight
+  constexpr int U = 4;
+  int64_t rr[ROWS];
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) rr[q] = min(r0 + q, nr - 1) * ld2;
+  auto consume = [&](const float4* mc, const float4* ms, int64_t c2) {
+    VT u0, u1, v0, v1;
+    Pair2<VT>::load(x1, c2, u0, u1);
+    Pair2<VT>::load(x2, c2, v0, v1);
+    const float2 fu0 = {(float)u0.x, (float)u0.y}, fu1 = {(float)u1.x, (float)u1.y};
+    const float2 fv0 = {(float)v0.x, (float)v0.y}, fv1 = {(float)v1.x, (float)v1.y};
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      if (hasC) {
+        const float2 m0 = {mc[q].x, mc[q].y}, m1 = {mc[q].z, mc[q].w};
+        cfma(cx1[q], m0, fu0); cfma(cx1[q], m1, fu1);
+        cfma(cx2[q], m0, fv0); cfma(cx2[q], m1, fv1);
+      }
+      if (hasS) {
+        const float2 m0 = {ms[q].x, ms[q].y}, m1 = {ms[q].z, ms[q].w};
+        cfma(sx1[q], m0, fu0); cfma(sx1[q], m1, fu1);
+        cfma(sx2[q], m0, fv0); cfma(sx2[q], m1, fv1);
+      }
+    }
+  };
+  int64_t c2 = lane;
+  for (; c2 + 32 * (U - 1) < nc2; c2 += 32 * U) {
+    float4 mc[U][ROWS], ms[U][ROWS];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+#pragma unroll
+      for (int q = 0; q < ROWS; ++q) {
+        if (hasC) mc[u][q] = __ldcs(C + rr[q] + c2 + 32 * u);
+        if (hasS) ms[u][q] = __ldcs(S + rr[q] + c2 + 32 * u);
+      }
+#pragma unroll
+    for (int u = 0; u < U; ++u) consume(mc[u], ms[u], c2 + 32 * u);
+  }
+  for (; c2 < nc2; c2 += 32) {
+    float4 mc[ROWS], ms[ROWS];
+#pragma unroll
+    for (int q = 0; q < ROWS; ++q) {
+      if (hasC) mc[q] = __ldcs(C + rr[q] + c2);
+      if (hasS) ms[q] = __ldcs(S + rr[q] + c2);
+    }
+    consume(mc, ms, c2);
+  }
+#pragma unroll
+  for (int q = 0; q < ROWS; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cx1[q].x += __shfl_xor_sync(0xffffffffu, cx1[q].x, o);
+      cx1[q].y += __shfl_xor_sync(0xffffffffu, cx1[q].y, o);
+      cx2[q].x += __shfl_xor_sync(0xffffffffu, cx2[q].x, o);
+      cx2[q].y += __shfl_xor_sync(0xffffffffu, cx2[q].y, o);
+      sx1[q].x += __shfl_xor_sync(0xffffffffu, sx1[q].x, o);
+      sx1[q].y += __shfl_xor_sync(0xffffffffu, sx1[q].y, o);
+      sx2[q].x += __shfl_xor_sync(0xffffffffu, sx2[q].x, o);
+      sx2[q].y += __shfl_xor_sync(0xffffffffu, sx2[q].y, o);
+    }
+    const int64_t r = r0 + q;
+    if (lane == 0 && r < nr) {
+      // odd column count: the last column of this row
+      if (nc & 1) {
+        const int64_t c = nc - 1;
+        const float2* Cr = reinterpret_cast<const float2*>(C);
+        const float2* Sr = reinterpret_cast<const float2*>(S);
+        const float2 u = {(float)x1[c].x, (float)x1[c].y}, v = {(float)x2[c].x, (float)x2[c].y};
+        if (hasC) { cfma(cx1[q], Cr[r * 2 * ld2 + c], u); cfma(cx2[q], Cr[r * 2 * ld2 + c], v); }
+        if (hasS) { cfma(sx1[q], Sr[r * 2 * ld2 + c], u); cfma(sx2[q], Sr[r * 2 * ld2 + c], v); }
+      }
+      VT a = y1[r], b = y2[r];
+      a.x += cx1[q].x + ar * sx2[q].x - ai * sx2[q].y;
+      a.y += cx1[q].y + ar * sx2[q].y + ai * sx2[q].x;
+      b.x += cx2[q].x + br * sx1[q].x - bi * sx1[q].y;
+      b.y += cx2[q].y + br * sx1[q].y + bi * sx1[q].x;
+      y1[r] = a;
+      y2[r] = b;
+    }
+  }
+}
+
+// Work units of one row and a chunk of CHUNK2 16-byte column words; a grid of
+// a few CTAs per SM strides over the units, so no partial last wave idles
+// SMs, and every unit adds its partial row sums with atomics (y is zeroed by
+// the caller before the operator is applied).
+__device__ __forceinline__ void atomic_add_v(float2* p, float x, float y) {
+  atomicAdd(p, make_float2(x, y));
+}
+__device__ __forceinline__ void atomic_add_v(double2* p, double x, double y) {
+  atomicAdd(&p->x, x);
+  atomicAdd(&p->y, y);
+}
+
+template <typename VT, typename AT>
+__global__ void __launch_bounds__(256, 3) pair_gemv_units_kernel(
+    const float4* __restrict__ S, const float4* __restrict__ C, int64_t nr, int64_t nc2,
+    int64_t ld2, int64_t chunk2, const VT* __restrict__ x1, const VT* __restrict__ x2,
+    VT* __restrict__ y1, VT* __restrict__ y2, double ar, double ai, double br, double bi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsplit = (nc2 + chunk2 - 1) / chunk2;
+  const int64_t nunits = nr * nsplit;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool hasC = C != nullptr, hasS = S != nullptr;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += wstride) {
+    const int64_t r = u / nsplit;
+    const int64_t c_lo = (u % nsplit) * chunk2, c_hi = min(c_lo + chunk2, nc2);
+    const float4* Cr = C + r * ld2;
+    const float4* Sr = S + r * ld2;
+    AT cx1 = {0, 0}, cx2 = {0, 0}, sx1 = {0, 0}, sx2 = {0, 0};
+    constexpr int U = 4;
+    int64_t c2 = c_lo + lane;
+    auto consume = [&](float4 mc, float4 ms, int64_t c) {
+      VT u0, u1, v0, v1;
+      Pair2<VT>::load(x1, c, u0, u1);
+      Pair2<VT>::load(x2, c, v0, v1);
+      using E = decltype(cx1.x);
+      const AT fu0 = {(E)u0.x, (E)u0.y}, fu1 = {(E)u1.x, (E)u1.y};
+      const AT fv0 = {(E)v0.x, (E)v0.y}, fv1 = {(E)v1.x, (E)v1.y};
+      if (hasC) {
+        const AT m0 = {(E)mc.x, (E)mc.y}, m1 = {(E)mc.z, (E)mc.w};
+        cfma(cx1, m0, fu0); cfma(cx1, m1, fu1);
+        cfma(cx2, m0, fv0); cfma(cx2, m1, fv1);
+      }
+      if (hasS) {
+        const AT m0 = {(E)ms.x, (E)ms.y}, m1 = {(E)ms.z, (E)ms.w};
+        cfma(sx1, m0, fu0); cfma(sx1, m1, fu1);
+        cfma(sx2, m0, fv0); cfma(sx2, m1, fv1);
+      }
+    };
+    for (; c2 + 32 * (U - 1) < c_hi; c2 += 32 * U) {
+      float4 mc[U], ms[U];
+#pragma unroll
+      for (int k = 0; k < U; ++k) {
+        if (hasC) mc[k] = __ldcs(Cr + c2 + 32 * k);
+        if (hasS) ms[k] = __ldcs(Sr + c2 + 32 * k);
+      }
+#pragma unroll
+      for (int k = 0; k < U; ++k) consume(mc[k], ms[k], c2 + 32 * k);
+    }
+    for (; c2 < c_hi; c2 += 32) {
+      float4 mc = {0, 0, 0, 0}, ms = {0, 0, 0, 0};
+      if (hasC) mc = __ldcs(Cr + c2);
+      if (hasS) ms = __ldcs(Sr + c2);
+      consume(mc, ms, c2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      cx1.x += __shfl_xor_sync(0xffffffffu, cx1.x, o); cx1.y += __shfl_xor_sync(0xffffffffu, cx1.y, o);
+      cx2.x += __shfl_xor_sync(0xffffffffu, cx2.x, o); cx2.y += __shfl_xor_sync(0xffffffffu, cx2.y, o);
+      sx1.x += __shfl_xor_sync(0xffffffffu, sx1.x, o); sx1.y += __shfl_xor_sync(0xffffffffu, sx1.y, o);
+      sx2.x += __shfl_xor_sync(0xffffffffu, sx2.x, o); sx2.y += __shfl_xor_sync(0xffffffffu, sx2.y, o);
+    }
+    if (lane == 0) {
+      using E = decltype(y1->x);
+      atomic_add_v(y1 + r, (E)(cx1.x + ar * sx2.x - ai * sx2.y), (E)(cx1.y + ar * sx2.y + ai * sx2.x));
+      atomic_add_v(y2 + r, (E)(cx2.x + br * sx1.x - bi * sx1.y), (E)(cx2.y + br * sx1.y + bi * sx1.x));
     }
   }
 }
@@ -440,6 +636,9 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
 
 template <typename R>
 GramSolver<R>::~GramSolver() {
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  cudaFree(d_in);
+  cudaFree(d_out);
   cudaFree(d_val);
   cudaFree(d_work);
   cudaFree(d_acc);
@@ -447,7 +646,7 @@ GramSolver<R>::~GramSolver() {
 }
 
 template <typename R>
-int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
+int GramSolver<R>::enqueue(const C* b, C* out, cudaStream_t st) {
   BiArgs<R> A;
   A.rowptr = d_rowptr;
   A.col = d_col;
@@ -464,7 +663,6 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   A.tol2 = tol * tol;
   const dim3 grid(blocks_for(n, 256), nsys);
   CAL_TRY_CUDA(cudaMemsetAsync(A.bnorm2, 0, nsys * sizeof(double), st));
-  const int tok = prof_begin(st, "bicgstab", 0.0);
   bicg_init<R><<<grid, 256, 0, st>>>(A, b);
   bicg_init2<R><<<1, 32 * ((nsys + 31) / 32), 0, st>>>(A);
   for (int k = 0; k < maxit; ++k) {
@@ -473,9 +671,36 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
     bicg_k3<R><<<grid, 256, 0, st>>>(A, k);
   }
   bicg_finish<R><<<grid, 256, 0, st>>>(A, out);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// The iteration sequence is captured once into a CUDA graph over fixed
+// input/output buffers; each solve copies in, replays it and copies out, so a
+// Gram solve costs one graph launch instead of 3 + 3 maxit kernel launches.
+// Systems that have converged turn the remaining iterations into no-ops.
+template <typename R>
+int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
+  const size_t vb = (size_t)n * nsys * sizeof(C);
+  if (!graph_exec) {
+    CAL_TRY_CUDA(cudaMalloc((void**)&d_in, vb));
+    CAL_TRY_CUDA(cudaMalloc((void**)&d_out, vb));
+    cudaGraph_t g;
+    CAL_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    const int rc = enqueue(d_in, d_out, st);
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc) return rc;
+    if (e != cudaSuccess) return fail(CAL_ECUDA, "Gram solve capture: %s", cudaGetErrorString(e));
+    const cudaError_t ei = cudaGraphInstantiate(&graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) return fail(CAL_ECUDA, "Gram solve instantiate: %s", cudaGetErrorString(ei));
+  }
+  const int tok = prof_begin(st, "bicgstab", 0.0);
+  CAL_TRY_CUDA(cudaMemcpyAsync(d_in, b, vb, cudaMemcpyDeviceToDevice, st));
+  CAL_TRY_CUDA(cudaGraphLaunch(graph_exec, st));
+  CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, vb, cudaMemcpyDeviceToDevice, st));
   prof_end(st, tok);
   note_launch(3 + 3 * maxit);
-  CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
@@ -499,10 +724,30 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
         S, C, b.rowptr, b.col, b.rows, x1, x2, y1, y2, ar, ai, br, bi);
     note_launch();
   } else {
-    constexpr int ROWS = 4;
-    const int64_t warps = (b.rows + ROWS - 1) / ROWS;
     const double bytes = (double)b.rows * b.cols * sizeof(MT) * ((S ? 1 : 0) + (C ? 1 : 0));
     const int tok = prof_begin(st, "pair_gemv", bytes);
+    const bool aligned16 = ((uintptr_t)S % 16 == 0) && ((uintptr_t)C % 16 == 0) &&
+                           ((uintptr_t)x1 % 16 == 0) && ((uintptr_t)x2 % 16 == 0);
+    if constexpr (sizeof(MT) == 8) {
+      if (b.cols % 2 == 0 && aligned16) {
+        int nsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t nc2 = b.cols / 2;
+        const int64_t chunk2 = std::min<int64_t>(nc2, 1024);
+        const int64_t units = b.rows * ((nc2 + chunk2 - 1) / chunk2);
+        const int64_t grid = std::min<int64_t>((units + 7) / 8, (int64_t)nsm * 3);
+        pair_gemv_units_kernel<VT, AT><<<(unsigned)grid, 256, 0, st>>>(
+            reinterpret_cast<const float4*>(S), reinterpret_cast<const float4*>(C), b.rows, nc2,
+            b.cols / 2, chunk2, x1, x2, y1, y2, ar, ai, br, bi);
+        prof_end(st, tok);
+        note_launch();
+        CAL_TRY_CUDA(cudaGetLastError());
+        return CAL_OK;
+      }
+    }
+    constexpr int ROWS = 4;
+    const int64_t warps = (b.rows + ROWS - 1) / ROWS;
     pair_gemv_kernel<MT, VT, AT, ROWS><<<blocks_for(warps * 32, 256), 256, 0, st>>>(
         S, C, b.rows, b.cols, b.cols, x1, x2, y1, y2, ar, ai, br, bi);
     prof_end(st, tok);

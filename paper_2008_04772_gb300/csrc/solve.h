@@ -45,8 +45,12 @@ struct GramSolver {
   double neg = 1.0, tol = 1e-10;
   int maxit = 30;
   C* d_work = nullptr;
+  C* d_in = nullptr;
+  C* d_out = nullptr;
   double* d_acc = nullptr;
   int* d_done = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int enqueue(const C* b, C* out, cudaStream_t st);
   int init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n, int nsys,
            int64_t nnz, double neg, double tol, int maxit);
   int solve(const C* b, C* out, cudaStream_t st);

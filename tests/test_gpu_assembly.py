@@ -13,7 +13,7 @@ from oracle import bem
 from paper_2008_04772_gb300 import cal
 
 pytestmark = pytest.mark.gpu
-TOL = {cal.FP64: 1e-10, cal.FP32: 1e-5}
+TOL = {cal.FP64: 1e-10, cal.FP32: 1e-5, cal.FP32_ALL: 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -38,7 +38,7 @@ def gpu_space(ctx, name, kind):
 
 @pytest.mark.parametrize("name", ["sphere1", "sphere2", "prisms2", "bipyr14", "cubes"])
 @pytest.mark.parametrize("k", [2.0, 2.0 * np.sqrt(EPS)])
-@pytest.mark.parametrize("prec", [cal.FP64, cal.FP32])
+@pytest.mark.parametrize("prec", [cal.FP64, cal.FP32, cal.FP32_ALL])
 def test_rwg_union_blocks(ctx, name, k, prec):
     So, Co = oracle_ops(name, "RWG", complex(k))
     op = cal.assemble(ctx, cal.OP_S | cal.OP_C, k, gpu_space(ctx, name, "RWG"), precision=prec)
@@ -59,7 +59,7 @@ def test_interior_blocks_per_scatterer(ctx, prec):
 
 @pytest.mark.parametrize("name", ["sphere1", "prisms2", "bipyr14", "cubes"])
 @pytest.mark.parametrize("k", [2.0, 3.5 + 0.01j])
-@pytest.mark.parametrize("prec", [cal.FP64, cal.FP32])
+@pytest.mark.parametrize("prec", [cal.FP64, cal.FP32, cal.FP32_ALL])
 def test_bc_blocks(ctx, name, k, prec):
     So, Co = oracle_ops(name, "BC", complex(k))
     op = cal.assemble(ctx, 3, k, gpu_space(ctx, name, "BC"), precision=prec)

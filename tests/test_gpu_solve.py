@@ -52,10 +52,11 @@ def test_fp64_solution_matches_oracle(ctx, name, k):
 
 
 @pytest.mark.parametrize("name,k", [("sphere2", 2.0), ("prisms2", 3.0), ("cubes", 2.1)])
-def test_fp32_bulk_far_field_within_1e4(ctx, name, k):
+@pytest.mark.parametrize("prec", [cal.FP32, cal.FP32_ALL])
+def test_fp32_bulk_far_field_within_1e4(ctx, name, k, prec):
     pb, xd, xo = oracle_solution(name, k)
     sol = cal.pmchwt_solve(ctx, gmesh(ctx, name), k, EPS, INC,
-                           opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-6))
+                           opts=cal.solve_opts(precond="D", precision=prec, tol=1e-6))
     dirs = meshgen.fibonacci_directions(64)
     F, Fo = sol.far_field(dirs)[0], pb.far_field(xd, dirs)
     assert rel(F, Fo) < 1e-4
