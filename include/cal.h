@@ -157,7 +157,9 @@ int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int6
 
 /* y = X x for X = operator `which`; x [nrhs][cols], y [nrhs][rows] complex of
    the op's precision, both device pointers; enqueued on `stream`
-   (cudaStream_t, NULL = the context stream). */
+   (cudaStream_t, NULL = the context stream). For a float32 dense operator and
+   4 <= nrhs <= 128 vectors (even cols) the product runs on the tensor cores
+   as a 3xTF32 GEMM (float32 accuracy); otherwise one GEMV/SpMV per vector. */
 int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
 
 /* Gram matrix G_ij = <BC_j, RWG_i> = int BC_j . (n x RWG_i) (eqs. MassA,

@@ -238,13 +238,23 @@ struct Pmchwt {
   int64_t gnnz = 0;
   std::unique_ptr<GramSolver<float>> gsA32, gsP32;
   std::unique_ptr<GramSolver<double>> gsA64, gsP64;
-  // work vectors
+  // batch of right-hand sides advanced in lockstep
+  int nb = 1;
+  // work vectors [nb][2N] (complex128-sized)
   void* t1 = nullptr;
   void* t2 = nullptr;
+  double2* d_gath = nullptr;
+  // tensor-core product buffers
+  int NB = 0;
+  float* d_Bt = nullptr;
+  float* d_ZS = nullptr;
+  float* d_ZC = nullptr;
+  int* d_gemm_err = nullptr;
   int64_t matvecs = 0;
   ~Pmchwt() {
     cudaFree(d_grp); cudaFree(d_gcol); cudaFree(d_grpT); cudaFree(d_gcolT);
-    cudaFree(d_gval); cudaFree(d_gvalT); cudaFree(t1); cudaFree(t2);
+    cudaFree(d_gval); cudaFree(d_gvalT); cudaFree(t1); cudaFree(t2); cudaFree(d_gath);
+    cudaFree(d_Bt); cudaFree(d_ZS); cudaFree(d_ZC); cudaFree(d_gemm_err);
   }
 
   BlockRef ref(const Op& op, bool withS = true, bool withC = true) const {
@@ -260,112 +270,161 @@ struct Pmchwt {
     return b;
   }
 
-  // y = A x (y overwritten); vec_prec = precision of x, y
-  int apply_A(const void* x, void* y, int vec_prec) {
-    cudaStream_t st = ctx->stream;
-    int rc = zero_vec(y, vec_prec, 2 * N, st);
-    if (rc) return rc;
-    const std::complex<double> a = 1.0 / k_e, b = -k_e;  // mu_e = 1
-    if ((rc = pair_apply(ref(*A_ext), vec_prec, x, y, N, a.real(), a.imag(), b.real(), b.imag(), st))) return rc;
-    for (int m = 0; m < M; ++m) {
-      const std::complex<double> am = mu_m[m] / k_m[m], bm = -k_m[m] / mu_m[m];
-      if ((rc = pair_apply(ref(*A_int[m]), vec_prec, x, y, N, am.real(), am.imag(), bm.real(), bm.imag(), st)))
-        return rc;
+  int alloc_batch(int nrhs) {
+    nb = nrhs;
+    const size_t vbytes = (size_t)nb * 2 * N * sizeof(double2);
+    CAL_TRY_CUDA(cudaMalloc(&t1, vbytes));
+    CAL_TRY_CUDA(cudaMalloc(&t2, vbytes));
+    CAL_TRY_CUDA(cudaMalloc((void**)&d_gath, vbytes));
+    if (o.precision == CAL_FP32 && nb >= 4 && gemm_tc_supported(2, nb)) {
+      NB = ((4 * nb + 15) / 16) * 16;
+      int64_t maxrows = A_ext->rows;
+      CAL_TRY_CUDA(cudaMalloc((void**)&d_Bt, (size_t)NB * 2 * maxrows * sizeof(float)));
+      CAL_TRY_CUDA(cudaMalloc((void**)&d_ZS, (size_t)maxrows * NB * sizeof(float)));
+      CAL_TRY_CUDA(cudaMalloc((void**)&d_ZC, (size_t)maxrows * NB * sizeof(float)));
+      CAL_TRY_CUDA(cudaMalloc((void**)&d_gemm_err, sizeof(int)));
+      CAL_TRY_CUDA(cudaMemset(d_gemm_err, 0, sizeof(int)));
     }
-    matvecs += 4LL * M * M + 4LL * M;
+    return CAL_OK;
+  }
+
+  // y += block applied to x for nrhs right-hand sides ([nrhs][2N] each)
+  int apply_block(const BlockRef& b, const void* x, void* y, int vec_prec, int nrhs, std::complex<double> al,
+                  std::complex<double> be) {
+    cudaStream_t st = ctx->stream;
+    const bool dense32 = b.precision == CAL_FP32 && !b.rowptr && vec_prec == CAL_FP32;
+    if (dense32 && d_Bt && nrhs == nb && gemm_tc_supported(b.cols, nrhs)) {
+      int rc;
+      const float2* X = (const float2*)x;
+      if ((rc = embed_rhs<float2>(X, nrhs, N, b.col_off, b.cols, d_Bt, NB, st))) return rc;
+      const float* ZS = nullptr;
+      const float* ZC = nullptr;
+      if (b.S) {
+        if ((rc = gemm_tf32x3((const float*)b.S, b.rows, 2 * b.cols, d_Bt, NB, d_ZS, d_gemm_err, ctx->n_sm, st)))
+          return rc;
+        ZS = d_ZS;
+      }
+      if (b.C) {
+        if ((rc = gemm_tf32x3((const float*)b.C, b.rows, 2 * b.cols, d_Bt, NB, d_ZC, d_gemm_err, ctx->n_sm, st)))
+          return rc;
+        ZC = d_ZC;
+      }
+      return combine_rhs<float2>(ZS, ZC, b.rows, NB, nrhs, N, b.row_off, (float2*)y, al.real(), al.imag(),
+                                 be.real(), be.imag(), st);
+    }
+    const size_t vsz = vec_prec == CAL_FP64 ? sizeof(double2) : sizeof(float2);
+    for (int q = 0; q < nrhs; ++q) {
+      int rc = pair_apply(b, vec_prec, (const char*)x + q * 2 * N * vsz, (char*)y + q * 2 * N * vsz, N, al.real(),
+                          al.imag(), be.real(), be.imag(), st);
+      if (rc) return rc;
+    }
+    return CAL_OK;
+  }
+
+  // y = A x (y overwritten); vec_prec = precision of x, y
+  int apply_A(const void* x, void* y, int vec_prec, int nrhs) {
+    cudaStream_t st = ctx->stream;
+    int rc = zero_vec(y, vec_prec, 2 * N * nrhs, st);
+    if (rc) return rc;
+    if ((rc = apply_block(ref(*A_ext), x, y, vec_prec, nrhs, 1.0 / k_e, -k_e))) return rc;  // mu_e = 1
+    for (int m = 0; m < M; ++m)
+      if ((rc = apply_block(ref(*A_int[m]), x, y, vec_prec, nrhs, mu_m[m] / k_m[m], -k_m[m] / mu_m[m]))) return rc;
+    matvecs += (4LL * M * M + 4LL * M) * nrhs;
     return CAL_OK;
   }
 
   // y = P x on BC coefficients (y overwritten)
-  int apply_P(const void* x, void* y, int vec_prec) {
+  int apply_P(const void* x, void* y, int vec_prec, int nrhs) {
     cudaStream_t st = ctx->stream;
-    int rc = zero_vec(y, vec_prec, 2 * N, st);
+    int rc = zero_vec(y, vec_prec, 2 * N * nrhs, st);
     if (rc) return rc;
     const int pc = o.precond;
     const bool ext = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DE || pc == CAL_PRECOND_SE;
     const bool in = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DI || pc == CAL_PRECOND_SI;
     const bool onlyS = pc == CAL_PRECOND_SE || pc == CAL_PRECOND_SI;
     for (int m = 0; m < M; ++m) {
-      if (ext) {
-        const std::complex<double> a = 1.0 / k_e, b = -k_e;
-        if ((rc = pair_apply(ref(*P_ext[m], true, !onlyS), vec_prec, x, y, N, a.real(), a.imag(), b.real(), b.imag(), st)))
-          return rc;
-      }
-      if (in) {
-        const std::complex<double> a = mu_m[m] / k_m[m], b = -k_m[m] / mu_m[m];
-        if ((rc = pair_apply(ref(*P_int[m], true, !onlyS), vec_prec, x, y, N, a.real(), a.imag(), b.real(), b.imag(), st)))
-          return rc;
-      }
+      if (ext && (rc = apply_block(ref(*P_ext[m], true, !onlyS), x, y, vec_prec, nrhs, 1.0 / k_e, -k_e))) return rc;
+      if (in && (rc = apply_block(ref(*P_int[m], true, !onlyS), x, y, vec_prec, nrhs, mu_m[m] / k_m[m],
+                                  -k_m[m] / mu_m[m])))
+        return rc;
     }
-    matvecs += (ext ? (onlyS ? 2 : 4) : 0) * (int64_t)M + (in ? (onlyS ? 2 : 4) : 0) * (int64_t)M;
+    matvecs += ((ext ? (onlyS ? 2 : 4) : 0) + (in ? (onlyS ? 2 : 4) : 0)) * (int64_t)M * nrhs;
     return CAL_OK;
   }
 
-  // w = M_P^-1 P M_A^-1 y ; y, w float64 [2N]; the working precision is o.precision
-  int apply_precond(const double2* y, double2* w) {
+  // w = M_P^-1 P M_A^-1 y for nrhs vectors; y, w float64 [nrhs][2N]
+  int apply_precond(const double2* y, double2* w, int nrhs) {
     cudaStream_t st = ctx->stream;
     int rc;
+    const int64_t n2 = 2 * N * nrhs;
     if (o.precond == CAL_PRECOND_NONE) {
-      CAL_TRY_CUDA(cudaMemcpyAsync(w, y, 2 * N * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      CAL_TRY_CUDA(cudaMemcpyAsync(w, y, n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       return CAL_OK;
     }
     if (o.precision == CAL_FP64) {
       double2* a = (double2*)t1;
       double2* b = (double2*)t2;
       if ((rc = gsA64->solve(y, a, st))) return rc;
-      if ((rc = apply_P(a, b, CAL_FP64))) return rc;
+      if ((rc = apply_P(a, b, CAL_FP64, nrhs))) return rc;
       return gsP64->solve(b, w, st);
     }
     float2* a = (float2*)t1;
     float2* b = (float2*)t2;
-    if ((rc = convert_vec(y, CAL_FP64, b, CAL_FP32, 2 * N, 1.0, st))) return rc;
+    if ((rc = convert_vec(y, CAL_FP64, b, CAL_FP32, n2, 1.0, st))) return rc;
     if ((rc = gsA32->solve(b, a, st))) return rc;
-    if ((rc = apply_P(a, b, CAL_FP32))) return rc;
+    if ((rc = apply_P(a, b, CAL_FP32, nrhs))) return rc;
     if ((rc = gsP32->solve(b, a, st))) return rc;
-    return convert_vec(a, CAL_FP32, w, CAL_FP64, 2 * N, 1.0, st);
+    return convert_vec(a, CAL_FP32, w, CAL_FP64, n2, 1.0, st);
   }
 
-  // w = B v, B = M_P^-1 P M_A^-1 A ; v, w float64
+  // w = B v, B = M_P^-1 P M_A^-1 A ; v, w float64 [nb][2N]
   int apply_B(const double2* v, double2* w, double2* scratch) {
     int rc;
     cudaStream_t st = ctx->stream;
+    const int64_t n2 = 2 * N * nb;
     if (o.precision == CAL_FP64) {
-      if ((rc = apply_A(v, scratch, CAL_FP64))) return rc;
-      return apply_precond(scratch, w);
+      if ((rc = apply_A(v, scratch, CAL_FP64, nb))) return rc;
+      return apply_precond(scratch, w, nb);
     }
     float2* a = (float2*)t1;
     float2* b = (float2*)t2;
-    if ((rc = convert_vec(v, CAL_FP64, a, CAL_FP32, 2 * N, 1.0, st))) return rc;
-    if ((rc = apply_A(a, b, CAL_FP32))) return rc;
-    if (o.precond == CAL_PRECOND_NONE) return convert_vec(b, CAL_FP32, w, CAL_FP64, 2 * N, 1.0, st);
+    if ((rc = convert_vec(v, CAL_FP64, a, CAL_FP32, n2, 1.0, st))) return rc;
+    if ((rc = apply_A(a, b, CAL_FP32, nb))) return rc;
+    if (o.precond == CAL_PRECOND_NONE) return convert_vec(b, CAL_FP32, w, CAL_FP64, n2, 1.0, st);
     if ((rc = gsA32->solve(b, a, st))) return rc;
-    if ((rc = apply_P(a, b, CAL_FP32))) return rc;
+    if ((rc = apply_P(a, b, CAL_FP32, nb))) return rc;
     if ((rc = gsP32->solve(b, a, st))) return rc;
-    return convert_vec(a, CAL_FP32, w, CAL_FP64, 2 * N, 1.0, st);
+    return convert_vec(a, CAL_FP32, w, CAL_FP64, n2, 1.0, st);
   }
 
-  // Restarted GMRES on B d = rhs, d0 = 0, added into x. Relative target tol on ||rhs||.
-  int gmres(const double2* rhs, double2* x, double tol, int& iters, double& rel_res, int maxit) {
+  // Restarted GMRES on B d_q = rhs_q for the nb right-hand sides in lockstep,
+  // d_q0 = 0, added into x_q. Per-column relative targets tol[q]; a column
+  // stops when its Givens residual (or explicit residual after a complete
+  // cycle) meets its target, and its iterate is updated at that point.
+  int gmres(const double2* rhs, double2* x, const std::vector<double>& tol, std::vector<int>& iters,
+            std::vector<double>& rel_res, int maxit) {
     cudaStream_t st = ctx->stream;
     const int64_t n = 2 * N;
     const int m = std::max(1, std::min<int>(o.restart, maxit));
+    const int q_n = nb;
     double2 *V, *w, *scr, *H, *cs, *sn, *g, *h1, *h2, *y, *r;
-    double* dscal;
-    double* hres;
+    double *dscal, *hres;
     const size_t vb = n * sizeof(double2);
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&V, (m + 1) * vb, st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&w, vb, st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&scr, vb, st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&r, vb, st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&H, (size_t)(m + 1) * m * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&cs, (m + 1) * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&sn, (m + 1) * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&g, (m + 2) * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&h1, (m + 2) * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&h2, (m + 2) * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&y, (m + 1) * sizeof(double2), st));
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&dscal, 4 * sizeof(double), st));
-    CAL_TRY_CUDA(cudaMallocHost((void**)&hres, 4 * sizeof(double)));
+    const int64_t bV = (int64_t)(m + 1) * n, bH = (int64_t)(m + 1) * m, bh = m + 2;
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&V, q_n * bV * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&w, q_n * vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&scr, q_n * vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&r, q_n * vb, st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&H, q_n * bH * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&cs, q_n * bh * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&sn, q_n * bh * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&g, q_n * bh * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&h1, q_n * bh * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&h2, q_n * bh * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&y, q_n * bh * sizeof(double2), st));
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&dscal, q_n * 4 * sizeof(double), st));
+    CAL_TRY_CUDA(cudaMallocHost((void**)&hres, q_n * 4 * sizeof(double)));
+    std::vector<double2> gh(q_n * bh);
     int rc = CAL_OK;
     auto cleanup = [&]() {
       cudaFreeAsync(V, st); cudaFreeAsync(w, st); cudaFreeAsync(scr, st); cudaFreeAsync(r, st);
@@ -374,55 +433,98 @@ struct Pmchwt {
       cudaStreamSynchronize(st);
       cudaFreeHost(hres);
     };
-    iters = 0;
-    // ||rhs||
-    if ((rc = vec_norm2(rhs, n, dscal, st)) ||
-        (rc = (cudaMemcpyAsync(hres, dscal, sizeof(double), cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : CAL_ECUDA))) {
-      cleanup();
-      return rc;
+    iters.assign(q_n, 0);
+    rel_res.assign(q_n, 0.0);
+    // ||rhs_q||
+    if ((rc = vec_norm2(rhs, n, dscal, 4, q_n, st))) { cleanup(); return rc; }
+    CAL_TRY_CUDA(cudaMemcpyAsync(hres, dscal, q_n * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+    std::vector<double> bnorm(q_n), beta(q_n);
+    std::vector<char> active(q_n);
+    int n_active = 0;
+    for (int q = 0; q < q_n; ++q) {
+      bnorm[q] = std::sqrt(hres[4 * q]);
+      beta[q] = bnorm[q];
+      active[q] = bnorm[q] > 0.0;
+      n_active += active[q];
     }
-    cudaStreamSynchronize(st);
-    const double bnorm = std::sqrt(hres[0]);
-    rel_res = 0.0;
-    if (bnorm == 0.0) { cleanup(); return CAL_OK; }
-    CAL_TRY_CUDA(cudaMemcpyAsync(r, rhs, vb, cudaMemcpyDeviceToDevice, st));
-    double beta = bnorm;
-    bool converged = false;
-    while (!converged && iters < maxit) {
+    CAL_TRY_CUDA(cudaMemcpyAsync(r, rhs, q_n * vb, cudaMemcpyDeviceToDevice, st));
+    int it = 0;
+    while (n_active > 0 && it < maxit) {
       // V0 = r / beta, g = (beta, 0, ...)
-      CAL_TRY_CUDA(cudaMemsetAsync(g, 0, (m + 2) * sizeof(double2), st));
-      const double2 gb = {beta, 0.0};
-      CAL_TRY_CUDA(cudaMemcpyAsync(g, &gb, sizeof(double2), cudaMemcpyHostToDevice, st));
-      hres[1] = beta * beta;
-      CAL_TRY_CUDA(cudaMemcpyAsync(dscal + 1, hres + 1, sizeof(double), cudaMemcpyHostToDevice, st));
-      if ((rc = gmres_scale(r, n, dscal + 1, V, st))) break;
+      std::fill(gh.begin(), gh.end(), double2{0.0, 0.0});
+      for (int q = 0; q < q_n; ++q) {
+        gh[q * bh] = {beta[q], 0.0};
+        hres[4 * q + 1] = beta[q] * beta[q];
+      }
+      CAL_TRY_CUDA(cudaMemcpyAsync(g, gh.data(), gh.size() * sizeof(double2), cudaMemcpyHostToDevice, st));
+      for (int q = 0; q < q_n; ++q)
+        CAL_TRY_CUDA(cudaMemcpyAsync(dscal + 4 * q + 1, hres + 4 * q + 1, sizeof(double), cudaMemcpyHostToDevice, st));
+      if ((rc = gmres_scale(r, n, n, dscal + 1, 4, V, bV, q_n, st))) break;
+      std::vector<char> cycle_active = active;
       int j = 0;
-      for (; j < m && iters < maxit; ++j) {
-        if ((rc = apply_B(V + (size_t)j * n, w, scr))) break;
-        ++iters;
-        if ((rc = gmres_cgs_step(V, n, j, w, h1, h2, dscal + 2, st))) break;
-        if ((rc = gmres_givens(H, m + 1, j, h1, h2, dscal + 2, cs, sn, g, dscal + 3, st))) break;
-        if ((rc = gmres_scale(w, n, dscal + 2, V + (size_t)(j + 1) * n, st))) break;
-        CAL_TRY_CUDA(cudaMemcpyAsync(hres + 3, dscal + 3, sizeof(double), cudaMemcpyDeviceToHost, st));
+      for (; j < m && it < maxit; ++j) {
+        if ((rc = vec_gather(V + (size_t)j * n, bV, d_gath, n, q_n, st))) break;
+        if ((rc = apply_B(d_gath, w, scr))) break;
+        ++it;
+        if ((rc = gmres_cgs_step(V, bV, n, j, w, h1, h2, bh, dscal + 2, 4, q_n, st))) break;
+        if ((rc = gmres_givens(H, m + 1, bH, j, h1, h2, bh, dscal + 2, 4, cs, sn, bh, g, bh, dscal + 3, 4, q_n, st)))
+          break;
+        if ((rc = gmres_scale(w, n, n, dscal + 2, 4, V + (size_t)(j + 1) * n, bV, q_n, st))) break;
+        CAL_TRY_CUDA(cudaMemcpyAsync(hres, dscal, q_n * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
         CAL_TRY_CUDA(cudaStreamSynchronize(st));
-        rel_res = hres[3] / bnorm;
-        if (!std::isfinite(rel_res)) { rc = fail(CAL_ECUDA, "GMRES: non-finite residual"); break; }
-        if (rel_res <= tol && j < m - 1) { converged = true; ++j; break; }
+        for (int q = 0; q < q_n; ++q) {
+          if (!cycle_active[q]) continue;
+          ++iters[q];
+          rel_res[q] = hres[4 * q + 3] / bnorm[q];
+          if (!std::isfinite(rel_res[q])) { rc = fail(CAL_ECUDA, "GMRES: non-finite residual"); break; }
+          if (rel_res[q] <= tol[q] && j < m - 1) {
+            // this column has converged inside the cycle: update it now
+            if ((rc = gmres_update(H + q * bH, m + 1, j + 1, g + q * bh, y + q * bh, V + q * bV, n, x + q * n, st)))
+              break;
+            cycle_active[q] = 0;
+            active[q] = 0;
+            --n_active;
+          }
+        }
+        if (rc || n_active == 0) { ++j; break; }
       }
       if (rc) break;
-      if ((rc = gmres_update(H, m + 1, j, g, y, V, n, x, st))) break;
-      if (converged || iters >= maxit) break;
+      const int ncol = std::min(j, m);
+      for (int q = 0; q < q_n; ++q)
+        if (cycle_active[q] && (rc = gmres_update(H + q * bH, m + 1, ncol, g + q * bh, y + q * bh, V + q * bV, n,
+                                                  x + q * n, st)))
+          break;
+      if (rc || n_active == 0 || it >= maxit) break;
       // end of a full cycle: explicit residual r = rhs - B x
       if ((rc = apply_B(x, w, scr))) break;
-      if ((rc = vec_axpby(rhs, 1.0, w, -1.0, r, n, st))) break;
-      if ((rc = vec_norm2(r, n, dscal, st))) break;
-      CAL_TRY_CUDA(cudaMemcpyAsync(hres, dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+      if ((rc = vec_axpby(rhs, 1.0, w, -1.0, r, n * q_n, st))) break;
+      if ((rc = vec_norm2(r, n, dscal, 4, q_n, st))) break;
+      CAL_TRY_CUDA(cudaMemcpyAsync(hres, dscal, q_n * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
       CAL_TRY_CUDA(cudaStreamSynchronize(st));
-      beta = std::sqrt(hres[0]);
-      rel_res = beta / bnorm;
-      if (rel_res <= tol) converged = true;
+      for (int q = 0; q < q_n; ++q) {
+        if (!active[q]) continue;
+        beta[q] = std::sqrt(hres[4 * q]);
+        rel_res[q] = beta[q] / bnorm[q];
+        if (rel_res[q] <= tol[q]) { active[q] = 0; --n_active; }
+      }
     }
     cleanup();
+    return rc;
+  }
+
+  // relative 2-norms of the nb columns of a [nb][2N] float64 block
+  int norms(const double2* v, std::vector<double>& out) {
+    cudaStream_t st = ctx->stream;
+    double* dn;
+    std::vector<double> h(4 * nb);
+    CAL_TRY_CUDA(cudaMallocAsync((void**)&dn, 4 * nb * sizeof(double), st));
+    int rc = vec_norm2(v, 2 * N, dn, 4, nb, st);
+    CAL_TRY_CUDA(cudaMemcpyAsync(h.data(), dn, 4 * nb * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CAL_TRY_CUDA(cudaFreeAsync(dn, st));
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+    out.resize(nb);
+    for (int q = 0; q < nb; ++q) out[q] = std::sqrt(h[4 * q]);
     return rc;
   }
 };
@@ -575,6 +677,9 @@ int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs
   if (!X) return fail(CAL_EINVAL, "cal_matvec: operator %d was not assembled", which);
   if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(CAL_EINVAL, "cal_matvec: x and y must be device pointers");
   cudaStream_t st = stream ? (cudaStream_t)stream : o.ctx->stream;
+  // several vectors on a float32 dense operator: the tensor-core 3xTF32 product
+  if (o.precision == CAL_FP32 && o.format == CAL_DENSE && nrhs >= 4 && (nrhs + 1) / 2 * 4 <= 256 && o.cols % 2 == 0)
+    return multi_matvec_tc((const float2*)X, o.rows, o.cols, (const float2*)x, (float2*)y, (int)nrhs, o.ctx->n_sm, st);
   return single_apply(o, X, x, y, nrhs, st);
 }
 
@@ -740,21 +845,21 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
       return rc;
     CAL_TRY_CUDA(cudaStreamSynchronize(st));
     // M_A = diag(G, G); M_P = diag(-G^T, -G^T): two component systems per vector
+    const int nbatch = (int)std::min<int64_t>(nrhs, 32);
     if (prec == CAL_FP64) {
       P.gsA64 = std::make_unique<GramSolver<double>>();
       P.gsP64 = std::make_unique<GramSolver<double>>();
-      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-13, 30))) return rc;
-      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-13, 30))) return rc;
+      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-13, 30))) return rc;
+      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-13, 30))) return rc;
     } else {
       P.gsA32 = std::make_unique<GramSolver<float>>();
       P.gsP32 = std::make_unique<GramSolver<float>>();
-      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2, P.gnnz, 1.0, 1e-6, 14))) return rc;
-      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2, P.gnnz, -1.0, 1e-6, 14))) return rc;
+      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-6, 14))) return rc;
+      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-6, 14))) return rc;
     }
   }
-  const size_t vbytes = 2 * P.N * sizeof(double2);
-  CAL_TRY_CUDA(cudaMalloc(&P.t1, vbytes));
-  CAL_TRY_CUDA(cudaMalloc(&P.t2, vbytes));
+  const int nbatch = (int)std::min<int64_t>(nrhs, 32);
+  if ((rc = P.alloc_batch(nbatch))) return rc;
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_P = now();
   // right-hand sides and solves
@@ -768,8 +873,8 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   double2 *d_b, *d_rhs, *d_r;
   CAL_TRY_CUDA(cudaMalloc((void**)&d_inc, 6 * nrhs * sizeof(double)));
   CAL_TRY_CUDA(cudaMalloc((void**)&d_b, nrhs * n2 * sizeof(double2)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_rhs, n2 * sizeof(double2)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_r, n2 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_rhs, nbatch * n2 * sizeof(double2)));
+  CAL_TRY_CUDA(cudaMalloc((void**)&d_r, nbatch * n2 * sizeof(double2)));
   CAL_TRY_CUDA(cudaMalloc((void**)&sol->d_x, nrhs * n2 * sizeof(double2)));
   CAL_TRY_CUDA(cudaMemsetAsync(sol->d_x, 0, nrhs * n2 * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemcpyAsync(d_inc, inc, 6 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
@@ -780,63 +885,88 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   int total_it = 0;
   double worst_res = 0.0;
   bool all_conv = true;
-  for (int64_t q = 0; q < nrhs; ++q) {
-    double2* b = d_b + q * n2;
-    double2* x = sol->d_x + q * n2;
-    int it = 0;
-    double res = 0.0;
+  for (int64_t q0 = 0; q0 < nrhs; q0 += nbatch) {
+    // the last batch may be short: pad it with zero right-hand sides
+    const int nq = (int)std::min<int64_t>(nbatch, nrhs - q0);
+    double2* b = d_b + q0 * n2;
+    std::vector<double2*> xs;
+    double2* x = nullptr;
+    std::unique_ptr<double2, decltype(&cudaFree)> gx(nullptr, &cudaFree), gbb(nullptr, &cudaFree);
+    if (nq == nbatch) {
+      x = sol->d_x + q0 * n2;
+    } else {
+      double2 *xb, *bb;
+      CAL_TRY_CUDA(cudaMalloc((void**)&xb, nbatch * n2 * sizeof(double2)));
+      CAL_TRY_CUDA(cudaMalloc((void**)&bb, nbatch * n2 * sizeof(double2)));
+      gx.reset(xb);
+      gbb.reset(bb);
+      CAL_TRY_CUDA(cudaMemsetAsync(xb, 0, nbatch * n2 * sizeof(double2), st));
+      CAL_TRY_CUDA(cudaMemsetAsync(bb, 0, nbatch * n2 * sizeof(double2), st));
+      CAL_TRY_CUDA(cudaMemcpyAsync(bb, b, nq * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+      x = xb;
+      b = bb;
+    }
+    std::vector<int> its(nbatch, 0);
+    std::vector<double> res(nbatch, 0.0);
     if (prec == CAL_FP64 || o.refine <= 0) {
       // d = GMRES(B, M^-1 b)
-      if ((rc = P.apply_precond(b, d_rhs))) return rc;
-      if (o.precond != CAL_PRECOND_NONE) P.matvecs += 0;  // counted inside apply_P
-      if ((rc = P.gmres(d_rhs, x, o.tol, it, res, o.maxit))) return rc;
+      if ((rc = P.apply_precond(b, d_rhs, nbatch))) return rc;
+      std::vector<double> tol(nbatch, o.tol);
+      if ((rc = P.gmres(d_rhs, x, tol, its, res, o.maxit))) return rc;
     } else {
       // FP64 iterative refinement around FP32-bulk GMRES: r = b - A x in
       // float64 accumulation, correction from the preconditioned system.
-      double r0 = 0.0;
-      double2* r = d_r;
+      std::vector<double> r0, rn;
+      std::vector<char> done(nbatch, 0);
+      int budget = o.maxit;
       for (int step = 0; step <= o.refine; ++step) {
         if (step == 0) {
-          CAL_TRY_CUDA(cudaMemcpyAsync(r, b, n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+          CAL_TRY_CUDA(cudaMemcpyAsync(d_r, b, nbatch * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
         } else {
-          if ((rc = P.apply_A(x, r, CAL_FP64))) return rc;  // float64 vectors, complex64 matrices
-          if ((rc = vec_axpby(b, 1.0, r, -1.0, r, n2, st))) return rc;
+          if ((rc = P.apply_A(x, d_r, CAL_FP64, nbatch))) return rc;  // float64 vectors, complex64 matrices
+          if ((rc = vec_axpby(b, 1.0, d_r, -1.0, d_r, nbatch * n2, st))) return rc;
         }
-        if ((rc = P.apply_precond(r, d_rhs))) return rc;
-        double* dn;
-        double hn;
-        CAL_TRY_CUDA(cudaMalloc((void**)&dn, sizeof(double)));
-        vec_norm2(d_rhs, n2, dn, st);
-        CAL_TRY_CUDA(cudaMemcpyAsync(&hn, dn, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CAL_TRY_CUDA(cudaStreamSynchronize(st));
-        cudaFree(dn);
-        const double rn = std::sqrt(hn);
+        if ((rc = P.apply_precond(d_r, d_rhs, nbatch))) return rc;
+        if ((rc = P.norms(d_rhs, rn))) return rc;
         if (step == 0) r0 = rn;
-        res = r0 > 0 ? rn / r0 : 0.0;
-        if (r0 == 0.0 || (step > 0 && res <= o.tol) || step == o.refine) break;
-        const double inner = std::min(0.5, std::max(o.tol * r0 / rn, 2e-6));
-        int it_s = 0;
-        double res_s = 0.0;
-        if ((rc = P.gmres(d_rhs, x, inner, it_s, res_s, o.maxit - it))) return rc;
-        it += it_s;
-        if (it >= o.maxit) {
-          // final residual for the report
-          if ((rc = P.apply_A(x, r, CAL_FP64)) || (rc = vec_axpby(b, 1.0, r, -1.0, r, n2, st)) ||
-              (rc = P.apply_precond(r, d_rhs)))
+        bool all = true;
+        std::vector<double> tol(nbatch, 1.0);
+        for (int q = 0; q < nbatch; ++q) {
+          res[q] = r0[q] > 0 ? rn[q] / r0[q] : 0.0;
+          if (r0[q] == 0.0 || (step > 0 && res[q] <= o.tol)) done[q] = 1;
+          // columns that are done get an unreachable-to-miss target of 1 (no iteration)
+          tol[q] = done[q] ? 2.0 : std::min(0.5, std::max(o.tol * r0[q] / rn[q], 2e-6));
+          all = all && done[q];
+        }
+        if (all || step == o.refine || budget <= 0) break;
+        std::vector<int> it_s;
+        std::vector<double> res_s;
+        if ((rc = P.gmres(d_rhs, x, tol, it_s, res_s, budget))) return rc;
+        int mx = 0;
+        for (int q = 0; q < nbatch; ++q) { its[q] += it_s[q]; mx = std::max(mx, it_s[q]); }
+        budget -= mx;
+        if (budget <= 0) {
+          if ((rc = P.apply_A(x, d_r, CAL_FP64, nbatch)) || (rc = vec_axpby(b, 1.0, d_r, -1.0, d_r, nbatch * n2, st)) ||
+              (rc = P.apply_precond(d_r, d_rhs, nbatch)) || (rc = P.norms(d_rhs, rn)))
             return rc;
-          CAL_TRY_CUDA(cudaMalloc((void**)&dn, sizeof(double)));
-          vec_norm2(d_rhs, n2, dn, st);
-          CAL_TRY_CUDA(cudaMemcpyAsync(&hn, dn, sizeof(double), cudaMemcpyDeviceToHost, st));
-          CAL_TRY_CUDA(cudaStreamSynchronize(st));
-          cudaFree(dn);
-          res = std::sqrt(hn) / r0;
+          for (int q = 0; q < nbatch; ++q) res[q] = r0[q] > 0 ? rn[q] / r0[q] : 0.0;
           break;
         }
       }
     }
-    total_it += it;
-    worst_res = std::max(worst_res, res);
-    if (!(res <= o.tol)) all_conv = false;
+    if (nq != nbatch)
+      CAL_TRY_CUDA(cudaMemcpyAsync(sol->d_x + q0 * n2, x, nq * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
+    for (int q = 0; q < nq; ++q) {
+      total_it = std::max(total_it, its[q]);
+      worst_res = std::max(worst_res, res[q]);
+      if (!(res[q] <= o.tol)) all_conv = false;
+    }
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  if (P.d_gemm_err) {
+    int herr = 0;
+    CAL_TRY_CUDA(cudaMemcpy(&herr, P.d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (herr) return fail(CAL_ETIMEOUT, "tensor-core product: a bounded wait gave up");
   }
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_end = now();

@@ -806,19 +806,25 @@ int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nr
 }
 
 // ---------------------------------------------------------------------------
-// GMRES helpers (float64): classical Gram–Schmidt with one reorthogonalisation
+// GMRES helpers (float64), batched over right-hand sides (blockIdx.y = q):
+// classical Gram–Schmidt with one reorthogonalisation, Givens rotations and
+// the triangular solve on the device.
 // ---------------------------------------------------------------------------
-__global__ void multi_dot_kernel(const double2* __restrict__ V, int64_t ldv, int m,
-                                 const double2* __restrict__ w, int64_t n, double2* h) {
-  // h[i] += V_i^H w for i < m; block-partial sums, one atomic per (block, i)
+__global__ void multi_dot_kernel(const double2* __restrict__ V, int64_t bV, int m,
+                                 const double2* __restrict__ w, int64_t n, double2* h, int64_t bh) {
+  // h[q][i] += V_q,i^H w_q for i < m; block-partial sums, one atomic per (block, i)
   __shared__ double sr[8][32], si[8][32];
+  const int q = blockIdx.y;
+  V += q * bV;
+  w += q * n;
+  h += q * bh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const double2 wk = k < n ? w[k] : double2{0, 0};
   for (int i = 0; i < m; ++i) {
     double ar = 0, ai = 0;
     if (k < n) {
-      const double2 v = V[(size_t)i * ldv + k];
+      const double2 v = V[(size_t)i * n + k];
       ar = v.x * wk.x + v.y * wk.y;
       ai = v.x * wk.y - v.y * wk.x;
     }
@@ -834,7 +840,7 @@ __global__ void multi_dot_kernel(const double2* __restrict__ V, int64_t ldv, int
       const int cnt = i - base + 1;
       if (threadIdx.x < cnt) {
         double tr = 0, ti = 0;
-        for (int q = 0; q < (int)(blockDim.x >> 5); ++q) { tr += sr[q][threadIdx.x]; ti += si[q][threadIdx.x]; }
+        for (int qq = 0; qq < (int)(blockDim.x >> 5); ++qq) { tr += sr[qq][threadIdx.x]; ti += si[qq][threadIdx.x]; }
         atomicAdd(&h[base + threadIdx.x].x, tr);
         atomicAdd(&h[base + threadIdx.x].y, ti);
       }
@@ -843,44 +849,59 @@ __global__ void multi_dot_kernel(const double2* __restrict__ V, int64_t ldv, int
   }
 }
 
-__global__ void multi_axpy_kernel(const double2* __restrict__ V, int64_t ldv, int m,
-                                  const double2* __restrict__ h, double2* __restrict__ w, int64_t n) {
-  // w -= sum_i h_i V_i
+__global__ void multi_axpy_kernel(const double2* __restrict__ V, int64_t bV, int m,
+                                  const double2* __restrict__ h, int64_t bh, double2* __restrict__ w, int64_t n) {
+  // w_q -= sum_i h_q,i V_q,i
+  const int q = blockIdx.y;
+  V += q * bV;
+  h += q * bh;
+  w += q * n;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
   double2 acc = w[k];
   for (int i = 0; i < m; ++i) {
-    const double2 v = V[(size_t)i * ldv + k], c = h[i];
+    const double2 v = V[(size_t)i * n + k], c = h[i];
     acc.x -= c.x * v.x - c.y * v.y;
     acc.y -= c.x * v.y + c.y * v.x;
   }
   w[k] = acc;
 }
 
-__global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* out) {
+__global__ void norm2_kernel(const double2* __restrict__ w, int64_t n, double* out, int64_t bout) {
+  const int q = blockIdx.y;
+  w += q * n;
   double part[1] = {0.0};
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k < n) part[0] = w[k].x * w[k].x + w[k].y * w[k].y;
-  block_accumulate<1>(part, out);
+  block_accumulate<1>(part, out + q * bout);
 }
 
-__global__ void scale_kernel(const double2* __restrict__ w, int64_t n, const double* nrm2,
-                             double2* __restrict__ out) {
+__global__ void scale_kernel(const double2* __restrict__ w, int64_t bw, int64_t n, const double* nrm2,
+                             int64_t bn, double2* __restrict__ out, int64_t bout) {
+  const int q = blockIdx.y;
   const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= n) return;
-  const double s = 1.0 / sqrt(*nrm2);
-  out[k] = {w[k].x * s, w[k].y * s};
+  const double nn = nrm2[q * bn];
+  const double s = nn > 0 ? 1.0 / sqrt(nn) : 0.0;
+  const double2 v = w[q * bw + k];
+  out[q * bout + k] = {v.x * s, v.y * s};
 }
 
-// Arnoldi column j finished: H[0..j][j] = h1 + h2, H[j+1][j] = ||w||; apply the
-// previous Givens rotations, build the new one, update g, report |g_{j+1}|.
-__global__ void givens_kernel(double2* H, int ldh, int j, const double2* h1, const double2* h2,
-                              const double* wn2, double2* cs, double2* sn, double2* g,
-                              double* res_out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  double2* col = H + (size_t)j * ldh;
+// Arnoldi column j finished for every q: H[0..j][j] = h1 + h2, H[j+1][j] = ||w||;
+// apply the previous rotations, build the new one, update g, report |g_{j+1}|.
+__global__ void givens_kernel(double2* H, int ldh, int64_t bH, int j, const double2* h1, const double2* h2,
+                              int64_t bh, const double* wn2, int64_t bwn, double2* cs, double2* sn, int64_t bcs,
+                              double2* g, int64_t bg, double* res_out, int64_t bres, int nrhs) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nrhs) return;
+  double2* col = H + q * bH + (size_t)j * ldh;
+  h1 += q * bh;
+  h2 += q * bh;
+  cs += q * bcs;
+  sn += q * bcs;
+  g += q * bg;
   for (int i = 0; i <= j; ++i) col[i] = {h1[i].x + h2[i].x, h1[i].y + h2[i].y};
-  col[j + 1] = {sqrt(*wn2), 0.0};
+  col[j + 1] = {sqrt(wn2[q * bwn]), 0.0};
   for (int i = 0; i < j; ++i) {
     // [c s; -conj(s) c] with real c
     const double c = cs[i].x;
@@ -908,10 +929,10 @@ __global__ void givens_kernel(double2* H, int ldh, int j, const double2* h1, con
   const double2 gj = g[j];
   g[j + 1] = {-(s.x * gj.x + s.y * gj.y), -(s.x * gj.y - s.y * gj.x)};
   g[j] = {c * gj.x, c * gj.y};
-  *res_out = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
+  res_out[q * bres] = sqrt(g[j + 1].x * g[j + 1].x + g[j + 1].y * g[j + 1].y);
 }
 
-// y = H[0..m)[0..m)^-1 g (upper triangular), then x += V y
+// y = H[0..m)[0..m)^-1 g (upper triangular), then x += V y (one right-hand side)
 __global__ void backsolve_kernel(const double2* H, int ldh, int m, const double2* g, double2* y) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   for (int i = m - 1; i >= 0; --i) {
@@ -946,32 +967,41 @@ __global__ void axpby_kernel(const double2* a, double sa, const double2* b, doub
   if (k < n) out[k] = {sa * a[k].x + sb * b[k].x, sa * a[k].y + sb * b[k].y};
 }
 
-int gmres_cgs_step(const double2* V, int64_t n, int j, double2* w, double2* h1, double2* h2,
-                   double* wn2, cudaStream_t st) {
-  const unsigned g = blocks_for(n, 256);
-  CAL_TRY_CUDA(cudaMemsetAsync(h1, 0, (j + 1) * sizeof(double2), st));
-  CAL_TRY_CUDA(cudaMemsetAsync(h2, 0, (j + 1) * sizeof(double2), st));
-  CAL_TRY_CUDA(cudaMemsetAsync(wn2, 0, sizeof(double), st));
-  multi_dot_kernel<<<g, 256, 0, st>>>(V, n, j + 1, w, n, h1);
-  multi_axpy_kernel<<<g, 256, 0, st>>>(V, n, j + 1, h1, w, n);
-  multi_dot_kernel<<<g, 256, 0, st>>>(V, n, j + 1, w, n, h2);
-  multi_axpy_kernel<<<g, 256, 0, st>>>(V, n, j + 1, h2, w, n);
-  norm2_kernel<<<g, 256, 0, st>>>(w, n, wn2);
+__global__ void gather_kernel(const double2* __restrict__ src, int64_t bsrc, double2* __restrict__ dst, int64_t n) {
+  const int q = blockIdx.y;
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k < n) dst[q * n + k] = src[q * bsrc + k];
+}
+
+int gmres_cgs_step(const double2* V, int64_t bV, int64_t n, int j, double2* w, double2* h1, double2* h2,
+                   int64_t bh, double* wn2, int64_t bwn, int nrhs, cudaStream_t st) {
+  const dim3 g(blocks_for(n, 256), nrhs);
+  CAL_TRY_CUDA(cudaMemsetAsync(h1, 0, nrhs * bh * sizeof(double2), st));
+  CAL_TRY_CUDA(cudaMemsetAsync(h2, 0, nrhs * bh * sizeof(double2), st));
+  for (int q = 0; q < nrhs; ++q) CAL_TRY_CUDA(cudaMemsetAsync(wn2 + q * bwn, 0, sizeof(double), st));
+  multi_dot_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, w, n, h1, bh);
+  multi_axpy_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, h1, bh, w, n);
+  multi_dot_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, w, n, h2, bh);
+  multi_axpy_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, h2, bh, w, n);
+  norm2_kernel<<<g, 256, 0, st>>>(w, n, wn2, bwn);
   note_launch(5);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
-int gmres_givens(double2* H, int ldh, int j, const double2* h1, const double2* h2, const double* wn2,
-                 double2* cs, double2* sn, double2* g, double* res, cudaStream_t st) {
-  givens_kernel<<<1, 32, 0, st>>>(H, ldh, j, h1, h2, wn2, cs, sn, g, res);
+int gmres_givens(double2* H, int ldh, int64_t bH, int j, const double2* h1, const double2* h2, int64_t bh,
+                 const double* wn2, int64_t bwn, double2* cs, double2* sn, int64_t bcs, double2* g, int64_t bg,
+                 double* res, int64_t bres, int nrhs, cudaStream_t st) {
+  givens_kernel<<<(nrhs + 31) / 32, 32, 0, st>>>(H, ldh, bH, j, h1, h2, bh, wn2, bwn, cs, sn, bcs, g, bg, res,
+                                                 bres, nrhs);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
-int gmres_scale(const double2* w, int64_t n, const double* nrm2, double2* out, cudaStream_t st) {
-  scale_kernel<<<blocks_for(n, 256), 256, 0, st>>>(w, n, nrm2, out);
+int gmres_scale(const double2* w, int64_t bw, int64_t n, const double* nrm2, int64_t bn, double2* out,
+                int64_t bout, int nrhs, cudaStream_t st) {
+  scale_kernel<<<dim3(blocks_for(n, 256), nrhs), 256, 0, st>>>(w, bw, n, nrm2, bn, out, bout);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
@@ -986,9 +1016,9 @@ int gmres_update(const double2* H, int ldh, int m, const double2* g, double2* y,
   return CAL_OK;
 }
 
-int vec_norm2(const double2* w, int64_t n, double* out, cudaStream_t st) {
-  CAL_TRY_CUDA(cudaMemsetAsync(out, 0, sizeof(double), st));
-  norm2_kernel<<<blocks_for(n, 256), 256, 0, st>>>(w, n, out);
+int vec_norm2(const double2* w, int64_t n, double* out, int64_t bout, int nrhs, cudaStream_t st) {
+  for (int q = 0; q < nrhs; ++q) CAL_TRY_CUDA(cudaMemsetAsync(out + q * bout, 0, sizeof(double), st));
+  norm2_kernel<<<dim3(blocks_for(n, 256), nrhs), 256, 0, st>>>(w, n, out, bout);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
@@ -997,6 +1027,13 @@ int vec_norm2(const double2* w, int64_t n, double* out, cudaStream_t st) {
 int vec_axpby(const double2* a, double sa, const double2* b, double sb, double2* out, int64_t n,
               cudaStream_t st) {
   axpby_kernel<<<blocks_for(n, 256), 256, 0, st>>>(a, sa, b, sb, out, n);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int vec_gather(const double2* src, int64_t bsrc, double2* dst, int64_t n, int nrhs, cudaStream_t st) {
+  gather_kernel<<<dim3(blocks_for(n, 256), nrhs), 256, 0, st>>>(src, bsrc, dst, n);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;

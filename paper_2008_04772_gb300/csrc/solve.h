@@ -57,16 +57,32 @@ struct GramSolver {
   ~GramSolver();
 };
 
-int gmres_cgs_step(const double2* V, int64_t n, int j, double2* w, double2* h1, double2* h2,
-                   double* wn2, cudaStream_t st);
-int gmres_givens(double2* H, int ldh, int j, const double2* h1, const double2* h2, const double* wn2,
-                 double2* cs, double2* sn, double2* g, double* res, cudaStream_t st);
-int gmres_scale(const double2* w, int64_t n, const double* nrm2, double2* out, cudaStream_t st);
+int gmres_cgs_step(const double2* V, int64_t bV, int64_t n, int j, double2* w, double2* h1, double2* h2,
+                   int64_t bh, double* wn2, int64_t bwn, int nrhs, cudaStream_t st);
+int gmres_givens(double2* H, int ldh, int64_t bH, int j, const double2* h1, const double2* h2, int64_t bh,
+                 const double* wn2, int64_t bwn, double2* cs, double2* sn, int64_t bcs, double2* g, int64_t bg,
+                 double* res, int64_t bres, int nrhs, cudaStream_t st);
+int gmres_scale(const double2* w, int64_t bw, int64_t n, const double* nrm2, int64_t bn, double2* out,
+                int64_t bout, int nrhs, cudaStream_t st);
 int gmres_update(const double2* H, int ldh, int m, const double2* g, double2* y, const double2* V,
                  int64_t n, double2* x, cudaStream_t st);
-int vec_norm2(const double2* w, int64_t n, double* out, cudaStream_t st);
+int vec_norm2(const double2* w, int64_t n, double* out, int64_t bout, int nrhs, cudaStream_t st);
 int vec_axpby(const double2* a, double sa, const double2* b, double sb, double2* out, int64_t n,
               cudaStream_t st);
+int vec_gather(const double2* src, int64_t bsrc, double2* dst, int64_t n, int nrhs, cudaStream_t st);
+
+// A10 (gemm_tc.cu): tensor-core 3xTF32 product and the right-hand-side embedding
+bool gemm_tc_supported(int64_t cols, int nrhs);
+int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2* x, float2* y, int nrhs, int n_sm,
+                    cudaStream_t st);
+int gemm_tf32x3(const float* A, int64_t M, int64_t K, const float* Bt, int NB, float* Z, int* d_err,
+                int n_sm, cudaStream_t st);
+template <typename VT>
+int embed_rhs(const VT* X, int nrhs, int64_t n_total, int64_t col_off, int64_t ncols, float* Bt, int NB,
+              cudaStream_t st);
+template <typename VT>
+int combine_rhs(const float* ZS, const float* ZC, int64_t rows, int NB, int nrhs, int64_t n_total, int64_t row_off,
+                VT* Y, double ar, double ai, double br, double bi, cudaStream_t st);
 
 int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
                cudaStream_t st);

@@ -1,0 +1,76 @@
+"""Multi-right-hand-side path: tensor-core 3xTF32 product and lockstep GMRES."""
+import numpy as np
+import pytest
+
+from gpu_common import EPS, mesh, oracle_ops, rel
+from paper_2008_04772_gb300 import cal, meshgen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2008_04772_gb300 import build
+    build.build()
+    return cal.Context(0)
+
+
+def _product(ctx, name, nrhs, which, seed=0, with_f32=False):
+    import torch
+    m = mesh(name)
+    gm = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    sp = cal.Space(gm, cal.RWG)
+    op = cal.assemble(ctx, 3, 2.0 + 0.1j, sp, precision=cal.FP32)
+    X = op.export(which).astype(np.complex128)
+    n = X.shape[1]
+    rng = np.random.default_rng(seed)
+    x = (rng.normal(size=(nrhs, n)) + 1j * rng.normal(size=(nrhs, n))).astype(np.complex64)
+    xt = torch.from_numpy(x.view(np.float32).copy()).cuda()
+    yt = torch.zeros((nrhs, 2 * X.shape[0]), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()
+    op.matvec(which, xt.data_ptr(), yt.data_ptr(), nrhs=nrhs)
+    torch.cuda.synchronize()
+    y = yt.cpu().numpy().view(np.complex64)
+    yr = (X @ x.astype(np.complex128).T).T
+    if with_f32:
+        return y, yr, (X.astype(np.complex64) @ x.T).T
+    return y, yr
+
+
+@pytest.mark.parametrize("nrhs", [4, 5, 8, 32, 64])
+@pytest.mark.parametrize("which", [cal.OP_S, cal.OP_C])
+def test_tensor_core_product_matches_float64(ctx, nrhs, which):
+    # 3xTF32 keeps float32 accuracy: relative error of the product ~1e-6
+    y, yr = _product(ctx, "sphere2", nrhs, which)
+    assert rel(y, yr) < 1e-5
+    # every column, not only the aggregate
+    for j in range(nrhs):
+        assert rel(y[j], yr[j]) < 2e-5
+
+
+def test_tensor_core_product_full_size(ctx):
+    # 7680 x 7680 block, 32 vectors (the multi-RHS shape of the solve): each
+    # entry is a 15360-term float32 accumulation, so the bar is the error of a
+    # float32-accumulated product of the same data (numpy complex64 GEMM)
+    y, yr, y32 = _product(ctx, "sphere4", 32, cal.OP_S, seed=3, with_f32=True)
+    floor = rel(y32, yr)
+    assert rel(y, yr) < max(3 * floor, 1e-6), (rel(y, yr), floor)
+    assert rel(y, yr) < 5e-5
+
+
+def test_lockstep_solve_equals_solo_solves(ctx):
+    d = meshgen.fibonacci_directions(8)
+    inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+    m = mesh("sphere2")
+    gm = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    opts = cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-7)
+    dirs = meshgen.fibonacci_directions(32)
+    multi = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc, opts=opts)
+    Fm = multi.far_field(dirs)
+    info = multi.info()
+    assert info.converged == 1
+    for q in (0, 3, 7):
+        solo = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc[q:q + 1], opts=opts).far_field(dirs)[0]
+        assert rel(Fm[q], solo) < 2e-5
+    # matvec accounting covers every column
+    assert info.matvecs >= 8 * 16 * 5
