@@ -182,8 +182,9 @@ class Space:
 
 
 class Operator:
-    def __init__(self, h):
+    def __init__(self, h, ctx=None):
         self.h = h
+        self.ctx = ctx  # keeps the context alive while the operator is
 
     def info(self) -> OpInfo:
         out = OpInfo()
@@ -220,7 +221,7 @@ def assemble(ctx: Context, op_mask: int, k: complex, space: Space, scatterer: in
     k = complex(k)
     _check(lib().cal_assemble(ctx.h, op_mask, k.real, k.imag, space.h, space.h, scatterer,
                               near_cutoff, q_regular, q_singular, precision, ctypes.byref(h)))
-    return Operator(h)
+    return Operator(h, ctx)
 
 
 def gram(rwg: Space, bc: Space):
@@ -241,8 +242,9 @@ def solve_opts(**kw) -> SolveOpts:
 
 
 class Solution:
-    def __init__(self, h, nrhs, n_edges, rc):
+    def __init__(self, h, nrhs, n_edges, rc, ctx=None):
         self.h = h
+        self.ctx = ctx
         self.nrhs = nrhs
         self.n_edges = n_edges
         self.rc = rc
@@ -287,4 +289,4 @@ def pmchwt_solve(ctx: Context, mesh: Mesh, k_ext: float, eps_r, inc, mu_r=None,
     rc = lib().cal_pmchwt_solve(ctx.h, mesh.h, float(k_ext), _ptr(ea), _ptr(ma), _ptr(inc),
                                 len(inc), ctypes.byref(o), ctypes.byref(h))
     _check(rc, allow=(ENOTCONV,) if allow_not_converged else ())
-    return Solution(h, len(inc), mesh.info().n_edges, rc)
+    return Solution(h, len(inc), mesh.info().n_edges, rc, ctx)

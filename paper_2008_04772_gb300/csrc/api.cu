@@ -89,18 +89,18 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
   const size_t bytes = (size_t)op->nnz * esz;
   cudaStream_t st = ctx.stream;
   if (want & 1) {
-    if (cudaMalloc(&op->d_S, std::max<size_t>(bytes, 16)) != cudaSuccess)
+    if (dalloc(&op->d_S, std::max<size_t>(bytes, 16), st) != cudaSuccess)
       return fail(CAL_ENOMEM, "assemble: cannot allocate %zu bytes for S", bytes);
     CAL_TRY_CUDA(cudaMemsetAsync(op->d_S, 0, bytes, st));
   }
   if (want & 2) {
-    if (cudaMalloc(&op->d_C, std::max<size_t>(bytes, 16)) != cudaSuccess)
+    if (dalloc(&op->d_C, std::max<size_t>(bytes, 16), st) != cudaSuccess)
       return fail(CAL_ENOMEM, "assemble: cannot allocate %zu bytes for C", bytes);
     CAL_TRY_CUDA(cudaMemsetAsync(op->d_C, 0, bytes, st));
   }
   if (!dense) {
-    CAL_TRY_CUDA(cudaMalloc((void**)&op->d_rowptr, op->h_rowptr.size() * sizeof(int64_t)));
-    CAL_TRY_CUDA(cudaMalloc((void**)&op->d_col, std::max<size_t>(op->h_col.size(), 1) * sizeof(int)));
+    CAL_TRY_CUDA(dalloc((void**)&op->d_rowptr, op->h_rowptr.size() * sizeof(int64_t), st));
+    CAL_TRY_CUDA(dalloc((void**)&op->d_col, std::max<size_t>(op->h_col.size(), 1) * sizeof(int), st));
     CAL_TRY_CUDA(cudaMemcpyAsync(op->d_rowptr, op->h_rowptr.data(), op->h_rowptr.size() * sizeof(int64_t),
                                  cudaMemcpyHostToDevice, st));
     if (!op->h_col.empty())
@@ -212,7 +212,7 @@ struct cal_solution {
   int64_t nrhs = 0, ne = 0;
   double k_e = 0.0, mu_e = 1.0;
   cal_solve_info info{};
-  ~cal_solution() { cudaFree(d_x); }
+  ~cal_solution() { dfree(d_x, ctx ? ctx->stream : nullptr); }
 };
 
 namespace {
@@ -252,9 +252,10 @@ struct Pmchwt {
   int* d_gemm_err = nullptr;
   int64_t matvecs = 0;
   ~Pmchwt() {
-    cudaFree(d_grp); cudaFree(d_gcol); cudaFree(d_grpT); cudaFree(d_gcolT);
-    cudaFree(d_gval); cudaFree(d_gvalT); cudaFree(t1); cudaFree(t2); cudaFree(d_gath);
-    cudaFree(d_Bt); cudaFree(d_ZS); cudaFree(d_ZC); cudaFree(d_gemm_err);
+    cudaStream_t st = ctx ? ctx->stream : nullptr;
+    for (void* p : {(void*)d_grp, (void*)d_gcol, (void*)d_grpT, (void*)d_gcolT, (void*)d_gval, (void*)d_gvalT, t1,
+                    t2, (void*)d_gath, (void*)d_Bt, (void*)d_ZS, (void*)d_ZC, (void*)d_gemm_err})
+      dfree(p, st);
   }
 
   BlockRef ref(const Op& op, bool withS = true, bool withC = true) const {
@@ -273,17 +274,18 @@ struct Pmchwt {
   int alloc_batch(int nrhs) {
     nb = nrhs;
     const size_t vbytes = (size_t)nb * 2 * N * sizeof(double2);
-    CAL_TRY_CUDA(cudaMalloc(&t1, vbytes));
-    CAL_TRY_CUDA(cudaMalloc(&t2, vbytes));
-    CAL_TRY_CUDA(cudaMalloc((void**)&d_gath, vbytes));
+    cudaStream_t st = ctx->stream;
+    CAL_TRY_CUDA(dalloc(&t1, vbytes, st));
+    CAL_TRY_CUDA(dalloc(&t2, vbytes, st));
+    CAL_TRY_CUDA(dalloc((void**)&d_gath, vbytes, st));
     if (o.precision == CAL_FP32 && nb >= 4 && gemm_tc_supported(2, nb)) {
       NB = ((4 * nb + 15) / 16) * 16;
       int64_t maxrows = A_ext->rows;
-      CAL_TRY_CUDA(cudaMalloc((void**)&d_Bt, (size_t)NB * 2 * maxrows * sizeof(float)));
-      CAL_TRY_CUDA(cudaMalloc((void**)&d_ZS, (size_t)maxrows * NB * sizeof(float)));
-      CAL_TRY_CUDA(cudaMalloc((void**)&d_ZC, (size_t)maxrows * NB * sizeof(float)));
-      CAL_TRY_CUDA(cudaMalloc((void**)&d_gemm_err, sizeof(int)));
-      CAL_TRY_CUDA(cudaMemset(d_gemm_err, 0, sizeof(int)));
+      CAL_TRY_CUDA(dalloc((void**)&d_Bt, (size_t)NB * 2 * maxrows * sizeof(float), st));
+      CAL_TRY_CUDA(dalloc((void**)&d_ZS, (size_t)maxrows * NB * sizeof(float), st));
+      CAL_TRY_CUDA(dalloc((void**)&d_ZC, (size_t)maxrows * NB * sizeof(float), st));
+      CAL_TRY_CUDA(dalloc((void**)&d_gemm_err, sizeof(int), st));
+      CAL_TRY_CUDA(cudaMemsetAsync(d_gemm_err, 0, sizeof(int), st));
     }
     return CAL_OK;
   }
@@ -423,7 +425,7 @@ struct Pmchwt {
     CAL_TRY_CUDA(cudaMallocAsync((void**)&h2, q_n * bh * sizeof(double2), st));
     CAL_TRY_CUDA(cudaMallocAsync((void**)&y, q_n * bh * sizeof(double2), st));
     CAL_TRY_CUDA(cudaMallocAsync((void**)&dscal, q_n * 4 * sizeof(double), st));
-    CAL_TRY_CUDA(cudaMallocHost((void**)&hres, q_n * 4 * sizeof(double)));
+    hres = ctx->pinned;  // 4 doubles per right-hand side; q_n <= 32
     std::vector<double2> gh(q_n * bh);
     int rc = CAL_OK;
     auto cleanup = [&]() {
@@ -431,7 +433,6 @@ struct Pmchwt {
       cudaFreeAsync(H, st); cudaFreeAsync(cs, st); cudaFreeAsync(sn, st); cudaFreeAsync(g, st);
       cudaFreeAsync(h1, st); cudaFreeAsync(h2, st); cudaFreeAsync(y, st); cudaFreeAsync(dscal, st);
       cudaStreamSynchronize(st);
-      cudaFreeHost(hres);
     };
     iters.assign(q_n, 0);
     rel_res.assign(q_n, 0.0);
@@ -569,6 +570,17 @@ int cal_init(cal_ctx** out, int device) {
     return fail(CAL_ECUDA, "cal_init: cannot create stream");
   }
   cudaDeviceGetAttribute(&c->impl.n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (cudaMallocHost((void**)&c->impl.pinned, 4096 * sizeof(double)) != cudaSuccess) {
+    cudaStreamDestroy(c->impl.stream);
+    delete c;
+    return fail(CAL_ENOMEM, "cal_init: cannot allocate pinned scratch");
+  }
+  // keep freed blocks in the stream-ordered pool: repeated solves reuse them
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, device) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   *out = c;
   return CAL_OK;
 }
@@ -577,6 +589,7 @@ void cal_ctx_destroy(cal_ctx* ctx) {
   if (!ctx) return;
   cudaStreamSynchronize(ctx->impl.stream);
   cudaStreamDestroy(ctx->impl.stream);
+  cudaFreeHost(ctx->impl.pinned);
   delete ctx;
 }
 
@@ -613,13 +626,21 @@ int cal_space_create(cal_mesh* mesh, int kind, cal_space** out) {
   CAL_TRY_CUDA(cudaSetDevice(mesh->impl.ctx->device));
   auto* s = new cal_space;
   int rc = kind == CAL_RWG ? build_rwg(s->impl, mesh->impl) : build_bc(s->impl, mesh->impl);
-  if (!rc) rc = upload_space(s->impl);
+  if (!rc) rc = upload_space(s->impl, mesh->impl.ctx->stream);
   if (rc) { delete s; return rc; }
   *out = s;
   return CAL_OK;
 }
 
-void cal_space_destroy(cal_space* space) { delete space; }
+void cal_space_destroy(cal_space* space) {
+  if (!space) return;
+  // the space may still be read by work on any stream, and the context whose
+  // stream ordered its allocation may be gone: wait for the device, then free
+  // on the legacy stream
+  cudaDeviceSynchronize();
+  space->impl.stream = nullptr;
+  delete space;
+}
 
 int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space* test,
                  cal_space* trial, int scatterer, double near_cutoff, int q_regular, int q_singular,
@@ -641,7 +662,14 @@ int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space*
   return CAL_OK;
 }
 
-void cal_op_destroy(cal_op* op) { delete op; }
+void cal_op_destroy(cal_op* op) {
+  if (!op) return;
+  // a matvec on a caller stream may still read the operator, and its context
+  // may already be destroyed: wait for the device, then free on the legacy stream
+  cudaDeviceSynchronize();
+  op->impl.ctx = nullptr;
+  delete op;
+}
 
 int cal_op_get_info(const cal_op* op, cal_op_info* info) {
   if (!op || !info) return fail(CAL_EINVAL, "cal_op_get_info: NULL argument");
@@ -770,11 +798,11 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   int rc;
   // spaces
   P.rwg = std::make_unique<Space>();
-  if ((rc = build_rwg(*P.rwg, mesh->impl)) || (rc = upload_space(*P.rwg))) return rc;
+  if ((rc = build_rwg(*P.rwg, mesh->impl)) || (rc = upload_space(*P.rwg, st))) return rc;
   const bool need_bc = o.precond != CAL_PRECOND_NONE;
   if (need_bc) {
     P.bc = std::make_unique<Space>();
-    if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc))) return rc;
+    if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc, st))) return rc;
   }
   const double t_setup = now();
   // A: S, C at k_e on the union; S, C at k_m on each scatterer
@@ -829,12 +857,12 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
         for (int64_t q = rp[i]; q < rp[i + 1]; ++q) colT[fill[col[q]]++] = (int)i;
     }
     P.gnnz = (int64_t)col.size();
-    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_grp, (n + 1) * sizeof(int64_t)));
-    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_grpT, (n + 1) * sizeof(int64_t)));
-    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gcol, P.gnnz * sizeof(int)));
-    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gcolT, P.gnnz * sizeof(int)));
-    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gval, P.gnnz * sizeof(double)));
-    CAL_TRY_CUDA(cudaMalloc((void**)&P.d_gvalT, P.gnnz * sizeof(double)));
+    CAL_TRY_CUDA(dalloc((void**)&P.d_grp, (n + 1) * sizeof(int64_t), st));
+    CAL_TRY_CUDA(dalloc((void**)&P.d_grpT, (n + 1) * sizeof(int64_t), st));
+    CAL_TRY_CUDA(dalloc((void**)&P.d_gcol, P.gnnz * sizeof(int), st));
+    CAL_TRY_CUDA(dalloc((void**)&P.d_gcolT, P.gnnz * sizeof(int), st));
+    CAL_TRY_CUDA(dalloc((void**)&P.d_gval, P.gnnz * sizeof(double), st));
+    CAL_TRY_CUDA(dalloc((void**)&P.d_gvalT, P.gnnz * sizeof(double), st));
     CAL_TRY_CUDA(cudaMemcpyAsync(P.d_grp, rp.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     CAL_TRY_CUDA(cudaMemcpyAsync(P.d_grpT, rpT.data(), (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
     CAL_TRY_CUDA(cudaMemcpyAsync(P.d_gcol, col.data(), P.gnnz * sizeof(int), cudaMemcpyHostToDevice, st));
@@ -849,13 +877,13 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     if (prec == CAL_FP64) {
       P.gsA64 = std::make_unique<GramSolver<double>>();
       P.gsP64 = std::make_unique<GramSolver<double>>();
-      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-13, 30))) return rc;
-      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-13, 30))) return rc;
+      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-13, 30, st))) return rc;
+      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-13, 30, st))) return rc;
     } else {
       P.gsA32 = std::make_unique<GramSolver<float>>();
       P.gsP32 = std::make_unique<GramSolver<float>>();
-      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-6, 14))) return rc;
-      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-6, 14))) return rc;
+      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-6, 14, st))) return rc;
+      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-6, 14, st))) return rc;
     }
   }
   const int nbatch = (int)std::min<int64_t>(nrhs, 32);
@@ -871,15 +899,19 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   const int64_t n2 = 2 * P.N;
   double* d_inc;
   double2 *d_b, *d_rhs, *d_r;
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_inc, 6 * nrhs * sizeof(double)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_b, nrhs * n2 * sizeof(double2)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_rhs, nbatch * n2 * sizeof(double2)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_r, nbatch * n2 * sizeof(double2)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&sol->d_x, nrhs * n2 * sizeof(double2)));
+  CAL_TRY_CUDA(dalloc((void**)&d_inc, 6 * nrhs * sizeof(double), st));
+  CAL_TRY_CUDA(dalloc((void**)&d_b, nrhs * n2 * sizeof(double2), st));
+  CAL_TRY_CUDA(dalloc((void**)&d_rhs, nbatch * n2 * sizeof(double2), st));
+  CAL_TRY_CUDA(dalloc((void**)&d_r, nbatch * n2 * sizeof(double2), st));
+  CAL_TRY_CUDA(dalloc((void**)&sol->d_x, nrhs * n2 * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemsetAsync(sol->d_x, 0, nrhs * n2 * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemcpyAsync(d_inc, inc, 6 * nrhs * sizeof(double), cudaMemcpyHostToDevice, st));
-  std::unique_ptr<double2, decltype(&cudaFree)> g1(d_b, &cudaFree), g2(d_rhs, &cudaFree), g3(d_r, &cudaFree);
-  std::unique_ptr<double, decltype(&cudaFree)> g4(d_inc, &cudaFree);
+  struct Guard {
+    void* p = nullptr;
+    cudaStream_t s = nullptr;
+    ~Guard() { dfree(p, s); }
+  };
+  Guard g1{d_b, st}, g2{d_rhs, st}, g3{d_r, st}, g4{d_inc, st};
   if ((rc = launch_rhs(*P.rwg, d_inc, (int)nrhs, k_ext, 1.0, d_b, st))) return rc;
   P.matvecs = 0;
   int total_it = 0;
@@ -891,15 +923,15 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     double2* b = d_b + q0 * n2;
     std::vector<double2*> xs;
     double2* x = nullptr;
-    std::unique_ptr<double2, decltype(&cudaFree)> gx(nullptr, &cudaFree), gbb(nullptr, &cudaFree);
+    Guard gx{nullptr, st}, gbb{nullptr, st};
     if (nq == nbatch) {
       x = sol->d_x + q0 * n2;
     } else {
       double2 *xb, *bb;
-      CAL_TRY_CUDA(cudaMalloc((void**)&xb, nbatch * n2 * sizeof(double2)));
-      CAL_TRY_CUDA(cudaMalloc((void**)&bb, nbatch * n2 * sizeof(double2)));
-      gx.reset(xb);
-      gbb.reset(bb);
+      CAL_TRY_CUDA(dalloc((void**)&xb, nbatch * n2 * sizeof(double2), st));
+      CAL_TRY_CUDA(dalloc((void**)&bb, nbatch * n2 * sizeof(double2), st));
+      gx.p = xb;
+      gbb.p = bb;
       CAL_TRY_CUDA(cudaMemsetAsync(xb, 0, nbatch * n2 * sizeof(double2), st));
       CAL_TRY_CUDA(cudaMemsetAsync(bb, 0, nbatch * n2 * sizeof(double2), st));
       CAL_TRY_CUDA(cudaMemcpyAsync(bb, b, nq * n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
@@ -965,7 +997,8 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   }
   if (P.d_gemm_err) {
     int herr = 0;
-    CAL_TRY_CUDA(cudaMemcpy(&herr, P.d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost));
+    CAL_TRY_CUDA(cudaMemcpyAsync(&herr, P.d_gemm_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
     if (herr) return fail(CAL_ETIMEOUT, "tensor-core product: a bounded wait gave up");
   }
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
@@ -996,7 +1029,9 @@ int cal_solution_get_info(const cal_solution* sol, cal_solve_info* info) {
 
 int cal_solution_coefficients(const cal_solution* sol, double* dst_host) {
   if (!sol || !dst_host) return fail(CAL_EINVAL, "cal_solution_coefficients: NULL argument");
-  CAL_TRY_CUDA(cudaMemcpy(dst_host, sol->d_x, sol->nrhs * 2 * sol->ne * sizeof(double2), cudaMemcpyDeviceToHost));
+  CAL_TRY_CUDA(cudaMemcpyAsync(dst_host, sol->d_x, sol->nrhs * 2 * sol->ne * sizeof(double2), cudaMemcpyDeviceToHost,
+                               sol->ctx->stream));
+  CAL_TRY_CUDA(cudaStreamSynchronize(sol->ctx->stream));
   return CAL_OK;
 }
 
@@ -1007,20 +1042,27 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
   cudaStream_t st = sol->ctx->stream;
   double* d_dirs;
   double2* d_out;
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_dirs, 3 * ndir * sizeof(double)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_out, sol->nrhs * ndir * 3 * sizeof(double2)));
+  CAL_TRY_CUDA(dalloc((void**)&d_dirs, 3 * ndir * sizeof(double), st));
+  CAL_TRY_CUDA(dalloc((void**)&d_out, sol->nrhs * ndir * 3 * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemcpyAsync(d_dirs, dirs, 3 * ndir * sizeof(double), cudaMemcpyHostToDevice, st));
   int rc = launch_farfield(*sol->rwg, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e, sol->mu_e, d_out, st);
   if (!rc) {
     CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, sol->nrhs * ndir * 3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
     CAL_TRY_CUDA(cudaStreamSynchronize(st));
   }
-  cudaFree(d_dirs);
-  cudaFree(d_out);
+  dfree(d_dirs, st);
+  dfree(d_out, st);
   return rc;
 }
 
-void cal_solution_destroy(cal_solution* sol) { delete sol; }
+void cal_solution_destroy(cal_solution* sol) {
+  if (!sol) return;
+  // as for operators: the context may be gone, so nothing here touches it
+  cudaDeviceSynchronize();
+  sol->ctx = nullptr;
+  if (sol->rwg) sol->rwg->stream = nullptr;
+  delete sol;
+}
 
 int64_t cal_kernel_launches(void) { return cal::launches(); }
 

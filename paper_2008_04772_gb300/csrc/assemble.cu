@@ -37,7 +37,8 @@ struct Rules {
   int nreg, ng;
 };
 
-static Rules g_rules;
+// per host thread: request streams driven from several threads may use different rules
+static thread_local Rules g_rules;
 
 int set_quadrature_tables(int nreg, int nsing) {
   if (nreg != 6 && nreg != 1) return fail(CAL_EINVAL, "q_regular must be 6 or 1 (got %d)", nreg);

@@ -589,15 +589,16 @@ void gram_pattern(const Space& bc, std::vector<int64_t>& rowptr, std::vector<int
 // device upload
 // ---------------------------------------------------------------------------
 template <typename T>
-static int upload(T** dst, const T* src, size_t n) {
+static int upload(T** dst, const T* src, size_t n, cudaStream_t st) {
   if (n == 0) { *dst = nullptr; return CAL_OK; }
-  if (cudaMalloc((void**)dst, n * sizeof(T)) != cudaSuccess)
-    return fail(CAL_ENOMEM, "cudaMalloc of %zu bytes failed", n * sizeof(T));
-  CAL_TRY_CUDA(cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice));
+  if (dalloc((void**)dst, n * sizeof(T), st) != cudaSuccess)
+    return fail(CAL_ENOMEM, "device allocation of %zu bytes failed", n * sizeof(T));
+  CAL_TRY_CUDA(cudaMemcpyAsync(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice, st));
   return CAL_OK;
 }
 
-int upload_space(Space& s) {
+int upload_space(Space& s, cudaStream_t st) {
+  s.stream = st;
   std::vector<TriF> tf(s.ntri);
   for (int64_t t = 0; t < s.ntri; ++t) {
     const TriD& d = s.triD[t];
@@ -613,37 +614,40 @@ int upload_space(Space& s) {
   }
   std::vector<float> swf(s.slot_sw.begin(), s.slot_sw.end());
   int rc;
-  if ((rc = upload(&s.d_triF, tf.data(), tf.size()))) return rc;
-  if ((rc = upload(&s.d_triD, s.triD.data(), s.triD.size()))) return rc;
-  if ((rc = upload(&s.d_slot_edge, s.slot_edge.data(), s.slot_edge.size()))) return rc;
-  if ((rc = upload(&s.d_slot_swf, swf.data(), swf.size()))) return rc;
-  if ((rc = upload(&s.d_slot_swd, s.slot_sw.data(), s.slot_sw.size()))) return rc;
+  if ((rc = upload(&s.d_triF, tf.data(), tf.size(), st))) return rc;
+  if ((rc = upload(&s.d_triD, s.triD.data(), s.triD.size(), st))) return rc;
+  if ((rc = upload(&s.d_slot_edge, s.slot_edge.data(), s.slot_edge.size(), st))) return rc;
+  if ((rc = upload(&s.d_slot_swf, swf.data(), swf.size(), st))) return rc;
+  if ((rc = upload(&s.d_slot_swd, s.slot_sw.data(), s.slot_sw.size(), st))) return rc;
   if (s.kind == CAL_BC) {
-    if ((rc = upload(&s.d_cell_tri_ptr, s.cell_tri_ptr.data(), s.cell_tri_ptr.size()))) return rc;
-    if ((rc = upload(&s.d_cell_tri, s.cell_tri.data(), s.cell_tri.size()))) return rc;
+    if ((rc = upload(&s.d_cell_tri_ptr, s.cell_tri_ptr.data(), s.cell_tri_ptr.size(), st))) return rc;
+    if ((rc = upload(&s.d_cell_tri, s.cell_tri.data(), s.cell_tri.size(), st))) return rc;
   }
   s.d_sing.assign(s.sing.size(), nullptr);
   for (size_t d = 0; d < s.sing.size(); ++d)
-    if ((rc = upload(&s.d_sing[d], s.sing[d].data(), s.sing[d].size()))) return rc;
+    if ((rc = upload(&s.d_sing[d], s.sing[d].data(), s.sing[d].size(), st))) return rc;
+  // the host arrays are pageable and some are locals: wait until the copies have read them
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
   return CAL_OK;
 }
 
 Space::~Space() {
-  cudaFree(d_triF);
-  cudaFree(d_triD);
-  cudaFree(d_slot_edge);
-  cudaFree(d_slot_swf);
-  cudaFree(d_slot_swd);
-  cudaFree(d_cell_tri_ptr);
-  cudaFree(d_cell_tri);
-  for (auto p : d_sing) cudaFree(p);
+  dfree(d_triF, stream);
+  dfree(d_triD, stream);
+  dfree(d_slot_edge, stream);
+  dfree(d_slot_swf, stream);
+  dfree(d_slot_swd, stream);
+  dfree(d_cell_tri_ptr, stream);
+  dfree(d_cell_tri, stream);
+  for (auto p : d_sing) dfree(p, stream);
 }
 
 Op::~Op() {
-  cudaFree(d_S);
-  cudaFree(d_C);
-  cudaFree(d_rowptr);
-  cudaFree(d_col);
+  cudaStream_t st = ctx ? ctx->stream : nullptr;
+  dfree(d_S, st);
+  dfree(d_C, st);
+  dfree(d_rowptr, st);
+  dfree(d_col, st);
 }
 
 }  // namespace cal

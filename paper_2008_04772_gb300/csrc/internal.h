@@ -65,7 +65,15 @@ struct Ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   int n_sm = 0;
+  double* pinned = nullptr;  // small page-locked scratch for residual read-backs
 };
+
+// stream-ordered device memory: no device-wide synchronisation, so requests on
+// different streams overlap (a plain cudaFree waits for the whole device)
+inline cudaError_t dalloc(void** p, size_t n, cudaStream_t s) { return cudaMallocAsync(p, n ? n : 16, s); }
+inline void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
 
 struct Mesh {
   Ctx* ctx = nullptr;
@@ -85,6 +93,7 @@ struct Mesh {
 
 struct Space {
   Mesh* mesh = nullptr;
+  cudaStream_t stream = nullptr;
   int kind = 0;
   int64_t ntri = 0, nbasis = 0;
   int nslot = 0;
@@ -138,7 +147,7 @@ void near_pattern(const Space& s, int scat, double chi, std::vector<int64_t>& ro
                   std::vector<int>& col);
 // Gram pattern (rows RWG edges, cols BC edges), CSR
 void gram_pattern(const Space& bc, std::vector<int64_t>& rowptr, std::vector<int>& col);
-int upload_space(Space& s);
+int upload_space(Space& s, cudaStream_t st);  // stream-ordered; returns after the copies
 
 // quadrature tables (host.cpp): Gauss–Legendre on [0,1] by Newton iteration on
 // Legendre polynomials; the symmetric degree-4 six-point triangle rule from its

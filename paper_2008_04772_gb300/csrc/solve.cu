@@ -608,8 +608,15 @@ __global__ void bicg_finish(BiArgs<R> A, typename CT<R>::T* __restrict__ out) {
 }
 
 template <typename R>
+__global__ void real_convert_kernel(const double* __restrict__ a, R* __restrict__ b, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (R)a[i];
+}
+
+template <typename R>
 int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n_,
-                        int nsys_, int64_t nnz, double neg_, double tol_, int maxit_) {
+                        int nsys_, int64_t nnz, double neg_, double tol_, int maxit_, cudaStream_t st) {
+  stream = st;
   n = n_;
   nsys = nsys_;
   neg = neg_;
@@ -618,31 +625,27 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
   d_rowptr = rowptr;
   d_col = col;
   const size_t vb = (size_t)n * nsys * sizeof(C);
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_val, nnz * sizeof(R)));
-  if (sizeof(R) == 8) {
-    CAL_TRY_CUDA(cudaMemcpy(d_val, vals_dev, nnz * sizeof(R), cudaMemcpyDeviceToDevice));
-  } else {
-    std::vector<double> h(nnz);
-    std::vector<R> hf(nnz);
-    CAL_TRY_CUDA(cudaMemcpy(h.data(), vals_dev, nnz * sizeof(double), cudaMemcpyDeviceToHost));
-    for (int64_t q = 0; q < nnz; ++q) hf[q] = (R)h[q];
-    CAL_TRY_CUDA(cudaMemcpy(d_val, hf.data(), nnz * sizeof(R), cudaMemcpyHostToDevice));
+  CAL_TRY_CUDA(dalloc((void**)&d_val, nnz * sizeof(R), st));
+  if (nnz > 0) {
+    real_convert_kernel<R><<<(unsigned)((nnz + 255) / 256), 256, 0, st>>>(vals_dev, d_val, nnz);
+    note_launch();
+    CAL_TRY_CUDA(cudaGetLastError());
   }
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_work, 8 * vb));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_acc, (2 * nsys * 8 + nsys) * sizeof(double)));
-  CAL_TRY_CUDA(cudaMalloc((void**)&d_done, nsys * sizeof(int)));
+  CAL_TRY_CUDA(dalloc((void**)&d_work, 8 * vb, st));
+  CAL_TRY_CUDA(dalloc((void**)&d_acc, (2 * nsys * 8 + nsys) * sizeof(double), st));
+  CAL_TRY_CUDA(dalloc((void**)&d_done, nsys * sizeof(int), st));
   return CAL_OK;
 }
 
 template <typename R>
 GramSolver<R>::~GramSolver() {
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
-  cudaFree(d_in);
-  cudaFree(d_out);
-  cudaFree(d_val);
-  cudaFree(d_work);
-  cudaFree(d_acc);
-  cudaFree(d_done);
+  dfree(d_in, stream);
+  dfree(d_out, stream);
+  dfree(d_val, stream);
+  dfree(d_work, stream);
+  dfree(d_acc, stream);
+  dfree(d_done, stream);
 }
 
 template <typename R>
@@ -683,8 +686,8 @@ template <typename R>
 int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   const size_t vb = (size_t)n * nsys * sizeof(C);
   if (!graph_exec) {
-    CAL_TRY_CUDA(cudaMalloc((void**)&d_in, vb));
-    CAL_TRY_CUDA(cudaMalloc((void**)&d_out, vb));
+    CAL_TRY_CUDA(dalloc((void**)&d_in, vb, st));
+    CAL_TRY_CUDA(dalloc((void**)&d_out, vb, st));
     cudaGraph_t g;
     CAL_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     const int rc = enqueue(d_in, d_out, st);
