@@ -162,6 +162,24 @@ int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int6
    as a 3xTF32 GEMM (float32 accuracy); otherwise one GEMV/SpMV per vector. */
 int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
 
+/* The paper has no counterpart to this entry point: it serves callers that
+   may not allocate device memory. Same product and arguments as cal_matvec's
+   tensor-core branch (float32 dense operator, even cols, 3xTF32), for
+   1 <= nrhs <= CAL_MATVEC_STATIC_MAX_NRHS, but every temporary lives in one
+   fixed device array of CAL_MATVEC_STATIC_SCRATCH_BYTES per device; the call
+   allocates nothing (no cudaMalloc/cudaFree, no allocating library routine).
+   The scratch needed is 4*NB*(2*cols + rows) bytes with NB =
+   16*ceil(ceil(nrhs/2)/4), plus (nrhs+1)*cols*8 for odd nrhs, plus a flag
+   (each part rounded up to 256 bytes): a 7680 x 7680 block fits every nrhs up
+   to 128. Larger requests return CAL_EINVAL, with the sizes in
+   cal_last_error(), before any GPU work. All calls share the array: calls whose GPU
+   work overlaps (other streams, other host threads) race on it and must be
+   serialised by the caller. Returns after the product has completed on
+   `stream`; CAL_ETIMEOUT if a bounded wait of the product gave up. */
+#define CAL_MATVEC_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+#define CAL_MATVEC_STATIC_MAX_NRHS 128
+int cal_matvec_static(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
+
 /* Gram matrix G_ij = <BC_j, RWG_i> = int BC_j . (n x RWG_i) (eqs. MassA,
    MassP: M_A = diag(G, G), M_P = diag(-G^T, -G^T) in the unknown ordering above)
    written densely to dst_host [N][N] float64. For tests of small meshes. */

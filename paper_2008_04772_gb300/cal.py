@@ -97,6 +97,7 @@ def lib():
         "cal_op_get_info": ([P, ctypes.POINTER(OpInfo)], ctypes.c_int),
         "cal_op_export": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
         "cal_matvec": ([P, ctypes.c_int, P, P, i64, P], ctypes.c_int),
+        "cal_matvec_static": ([P, ctypes.c_int, P, P, i64, P], ctypes.c_int),
         "cal_gram_export": ([P, P, P], ctypes.c_int),
         "cal_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
         "cal_pmchwt_solve": ([P, P, d, P, P, P, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(P)],
@@ -208,6 +209,12 @@ class Operator:
         """y = X x on device pointers (e.g. torch CUDA tensors' data_ptr())."""
         _check(lib().cal_matvec(self.h, which, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
                                 nrhs, stream))
+
+    def matvec_static(self, which: int, x_ptr: int, y_ptr: int, nrhs: int = 1, stream=None):
+        """y = X x like matvec's tensor-core branch, with no device allocation:
+        the temporaries live in one fixed per-device array shared by all calls."""
+        _check(lib().cal_matvec_static(self.h, which, ctypes.c_void_p(x_ptr), ctypes.c_void_p(y_ptr),
+                                       nrhs, stream))
 
     def __del__(self):
         if getattr(self, "h", None):
