@@ -272,9 +272,113 @@ def run_ours(args, rank, world):
         "e2e": {"value": 1.0 / statistics.median(t_e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
     }
+    if args.serving:
+        out["serving"] = run_serving(dev)
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     return out
+
+
+SERVING = {"name": "aggregate_requests_scaled", "requests": 48, "seed": 0, "prisms": (1, 8),
+           "tris_per_prism": (100, 600), "k": (1.0, 10.0), "eps_re": (2.5, 3.5), "eps_im": 0.01,
+           "nrhs": (1, 16), "ndir": 64, "precond": "Di", "near_cutoff_P": 2.0, "tol": 1e-5,
+           "slots": 4, "load": 0.8}
+
+
+def serving_requests(n, seed):
+    """Seeded request mix shaped like the aggregate serving workload, scaled down
+    in triangles per prism so that the whole run takes well under a minute."""
+    from paper_2008_04772_gb300 import meshgen
+    S = SERVING
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        npr = int(rng.integers(S["prisms"][0], S["prisms"][1] + 1))
+        tpp = [int(t) for t in rng.integers(S["tris_per_prism"][0], S["tris_per_prism"][1] + 1, npr)]
+        m = meshgen.prism_aggregate(npr, tpp, seed=1000 * seed + i, diameter=1.0, gap=0.05)
+        k = float(rng.uniform(*S["k"]))
+        eps = complex(rng.uniform(*S["eps_re"]), S["eps_im"])
+        nrhs = int(rng.integers(S["nrhs"][0], S["nrhs"][1] + 1))
+        d = rng.normal(size=(nrhs, 3))
+        d /= np.linalg.norm(d, axis=1, keepdims=True)
+        inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+        out.append((m, k, eps, inc))
+    return out
+
+
+def run_serving(dev):
+    """Closed-loop saturation run, then Poisson arrivals at `load` x that rate."""
+    from paper_2008_04772_gb300 import cal, meshgen
+    S = SERVING
+    opts = cal.solve_opts(precond=S["precond"], precision=cal.FP32, tol=S["tol"],
+                          near_cutoff_P=S["near_cutoff_P"])
+    dirs = meshgen.fibonacci_directions(S["ndir"])
+    reqs = serving_requests(S["requests"], S["seed"])
+    q = cal.Queue(dev, slots=S["slots"])
+
+    def submit(r):
+        m, k, eps, inc = r
+        return q.submit(m.verts, m.tris, m.domain, k, eps, inc, dirs, opts=opts)
+
+    # warm-up on requests of another seed (kernels, memory pool)
+    for t in [submit(r) for r in serving_requests(4, S["seed"] + 1)]:
+        q.wait(t)
+    # closed loop: every request submitted at once
+    t0 = time.perf_counter()
+    tickets = [submit(r) for r in reqs]
+    res = [q.wait(t)[0] for t in tickets]
+    t_closed = time.perf_counter() - t0
+    ok = sum(r.status == 0 for r in res)
+    cols = sum(len(r[3]) for r in reqs)
+    rate = S["load"] * len(reqs) / t_closed
+    # open loop: Poisson arrivals at `load` x the saturated rate
+    rng = np.random.default_rng(S["seed"] + 2)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, len(reqs)))
+    tk = [None] * len(reqs)
+
+    def feeder():
+        start = time.perf_counter()
+        for i, r in enumerate(reqs):
+            dt = arrivals[i] - (time.perf_counter() - start)
+            if dt > 0:
+                time.sleep(dt)
+            tk[i] = submit(r)
+
+    th = threading.Thread(target=feeder)
+    t1 = time.perf_counter()
+    th.start()
+    lat = []
+    statuses = []
+    for i in range(len(reqs)):
+        while tk[i] is None:
+            time.sleep(0.001)
+        r = q.wait(tk[i])[0]
+        lat.append(1e3 * (r.t_done - r.t_submit))
+        statuses.append(r.status)
+    th.join()
+    t_open = time.perf_counter() - t1
+    st = q.stats()
+    q.close()
+    tri = [len(r[0].tris) for r in reqs]
+    return {
+        "workload": S["name"],
+        "requests": len(reqs),
+        "mix": {"prisms": list(S["prisms"]), "tris_per_prism": list(S["tris_per_prism"]),
+                "triangles": [int(min(tri)), int(max(tri))], "k": list(S["k"]),
+                "eps_r": f"U{list(S['eps_re'])} + {S['eps_im']}i", "nrhs": list(S["nrhs"]),
+                "columns": cols, "far_field_dirs": S["ndir"],
+                "preconditioner": f"{S['precond']} near-field {S['near_cutoff_P']}h", "tol": S["tol"]},
+        "slots": S["slots"],
+        "closed_loop": {"solves_per_s": len(reqs) / t_closed, "columns_per_s": cols / t_closed,
+                        "seconds": t_closed, "ok": ok},
+        "open_loop": {"arrival_rate_per_s": rate, "solves_per_s": len(reqs) / t_open,
+                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                      "ok": sum(s == 0 for s in statuses)},
+        "latency": "arrival (submit) to far field ready, queue clock",
+        "queue": {"peak_running": st.peak_running, "merged": st.merged, "problems_created": st.problems_created,
+                  "evictions": st.evictions, "peak_reserved_gb": st.peak_reserved_bytes / 1e9,
+                  "budget_gb": st.budget_bytes / 1e9},
+    }
 
 
 def cpu_baseline(sample_tris: int):
@@ -350,6 +454,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-sample", type=int, default=24, help="test triangles per space for the oracle sample")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--no-serving", dest="serving", action="store_false",
+                    help="skip the request-queue (continuous batching) run")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

@@ -80,6 +80,8 @@ typedef struct cal_mesh cal_mesh;
 typedef struct cal_space cal_space;
 typedef struct cal_op cal_op;
 typedef struct cal_solution cal_solution;
+typedef struct cal_problem cal_problem;
+typedef struct cal_queue cal_queue;
 
 /* ---- context ------------------------------------------------------------- */
 /* Bind a context to CUDA device `device` and create its stream. */
@@ -224,6 +226,101 @@ int cal_solution_coefficients(const cal_solution* sol, double* dst_host);
    dirs [ndir][3]: out [nrhs][ndir][3] complex128 (host). */
 int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, double* out);
 void cal_solution_destroy(cal_solution* sol);
+
+/* ---- resident problems --------------------------------------------------- */
+/* cal_pmchwt_solve is cal_problem_create + cal_problem_solve +
+   cal_problem_destroy. A problem keeps everything that depends only on
+   (mesh, k_ext, materials, options) on the device: the spaces, the stored A
+   blocks (eq. multiple_operator), the P blocks (§3.1) and the Gram matrices
+   (eqs. MassA, MassP), so that further incident fields (the orientation
+   averages of §5) cost only GMRES. The mesh may be destroyed once create has
+   returned. Solves of one problem must not overlap in time; any context on the
+   problem's device may run them (the work goes on that context's stream). */
+int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r,
+                       const double* mu_r, const cal_solve_opts* opts, cal_problem** out);
+/* Same contract and result as cal_pmchwt_solve for the problem's operators;
+   info.t_setup/t_assemble_* are the problem's creation times. */
+int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_t nrhs,
+                      cal_solution** out);
+typedef struct {
+  int64_t n_unknowns;                 /* 2N                                        */
+  int32_t n_scatterers, precision, precond;
+  int64_t bytes_A, bytes_P, bytes_G;  /* stored blocks and Gram CSR (device bytes) */
+  int64_t bytes_batch;                /* work vectors and Gram-solver state kept for
+                                         the last batch width (0 before a solve)  */
+  int32_t batch_width;                /* right-hand sides per lockstep batch       */
+  double t_setup, t_assemble_A, t_assemble_P;
+} cal_problem_info;
+int cal_problem_get_info(const cal_problem* prob, cal_problem_info* info);
+void cal_problem_destroy(cal_problem* prob);
+
+/* ---- request queue (serving loop) ------------------------------------------
+   Continuous batching of scattering solves: requests of different meshes,
+   wavenumbers, materials and incident fields are submitted at any time and
+   run on `slots` worker streams of one device, so their GPU work overlaps.
+   Admission is by HBM footprint: a request starts once its estimated bytes
+   (stored A and P blocks, Gram matrices, Krylov basis and vectors; reconciled
+   with the real sizes once its operators exist) fit in the budget next to what
+   is running and resident. Operators stay resident after a solve (LRU, evicted
+   when admission needs the room), so a later request of the same problem
+   (same mesh, k_ext, materials and assembly options) goes straight to GMRES,
+   and pending requests of one problem with equal solver options are merged
+   into one lockstep multi-right-hand-side batch (up to 32 columns). The paper
+   motivates many solves of one scatterer by orientation averaging (§5). */
+typedef struct {
+  const double* verts; int64_t nv;     /* as cal_mesh_create                     */
+  const int32_t* tris; int64_t nt;
+  const int32_t* domain;               /* may be NULL (one scatterer)            */
+  double k_ext;
+  const double* eps_r;                 /* [M][2]                                 */
+  const double* mu_r;                  /* [M][2] or NULL                         */
+  const double* inc; int64_t nrhs;     /* [nrhs][6] as cal_pmchwt_solve          */
+  const double* dirs; int64_t ndir;    /* far-field directions [ndir][3]         */
+  cal_solve_opts opts;
+} cal_request;
+
+typedef struct {
+  int32_t status;        /* the request's own result: CAL_OK, CAL_ENOTCONV (far
+                            field still valid), or the error of its solve      */
+  int32_t iterations;
+  double residual;
+  double t_submit, t_start, t_done;  /* seconds on the queue's clock; latency =
+                                        t_done - t_submit (far field ready)     */
+  int64_t footprint_bytes;           /* bytes reserved at admission             */
+  int32_t batch_rhs;                 /* columns of the lockstep batch it ran in */
+  int32_t reused;                    /* 1: operators were already resident      */
+} cal_request_result;
+
+typedef struct {
+  int64_t submitted, completed, rejected;
+  int64_t batches;            /* problem solves run (a merged batch counts once)   */
+  int64_t merged;             /* requests that joined another request's batch     */
+  int64_t problems_created, problem_hits, evictions;
+  int64_t budget_bytes, reserved_bytes, peak_reserved_bytes;
+  int32_t slots, running, peak_running, pending;
+} cal_queue_stats;
+
+/* One queue per device; hbm_budget_bytes = 0 takes 85% of the free device
+   memory at creation. slots >= 1 worker threads, each with its own context
+   and stream. */
+int cal_queue_create(int device, size_t hbm_budget_bytes, int slots, cal_queue** out);
+/* Copies every input (the caller's arrays may be reused at once), checks the
+   mesh (CAL_EMESH) and the footprint: CAL_ENOMEM if the request alone cannot
+   fit the budget. On success *ticket identifies the request. */
+int cal_queue_submit(cal_queue* q, const cal_request* req, int64_t* ticket);
+/* Waits up to timeout_s seconds (< 0: no limit) for the request. CAL_OK when it
+   has completed (its own status in res->status; farfield, if not NULL, receives
+   [nrhs][ndir][3] complex128) and the ticket is released; CAL_ETIMEOUT if it
+   is still pending or running; CAL_EINVAL for an unknown ticket. */
+int cal_queue_wait(cal_queue* q, int64_t ticket, double timeout_s, cal_request_result* res,
+                   double* farfield);
+int cal_queue_get_stats(cal_queue* q, cal_queue_stats* stats);
+/* Finishes the batches that are running, drops pending requests, frees the
+   resident operators and the worker contexts. */
+void cal_queue_destroy(cal_queue* q);
+/* Estimated device bytes of a request (host only, no GPU needed): the
+   resident part (spaces, A, P, Gram) and the per-solve part. */
+int cal_request_footprint(const cal_request* req, int64_t* resident_bytes, int64_t* solve_bytes);
 
 /* ---- instrumentation ------------------------------------------------------ */
 /* Number of kernels this library has launched since load (all contexts). */

@@ -21,7 +21,7 @@ LIB = os.path.join(OUT_DIR, "libcal.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["assemble.cu", "solve.cu", "gemm_tc.cu", "api.cu", "static_scratch.cu"]
-CXX_SOURCES = ["host.cpp"]
+CXX_SOURCES = ["host.cpp", "serve.cpp"]
 
 
 def _nvcc():

@@ -63,6 +63,44 @@ class SolveInfo(ctypes.Structure):
                 ("n_unknowns", ctypes.c_int64)]
 
 
+class ProblemInfo(ctypes.Structure):
+    _fields_ = [("n_unknowns", ctypes.c_int64), ("n_scatterers", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("bytes_A", ctypes.c_int64), ("bytes_P", ctypes.c_int64), ("bytes_G", ctypes.c_int64),
+                ("bytes_batch", ctypes.c_int64), ("batch_width", ctypes.c_int32),
+                ("t_setup", ctypes.c_double), ("t_assemble_A", ctypes.c_double),
+                ("t_assemble_P", ctypes.c_double)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("verts", ctypes.c_void_p), ("nv", ctypes.c_int64),
+                ("tris", ctypes.c_void_p), ("nt", ctypes.c_int64),
+                ("domain", ctypes.c_void_p), ("k_ext", ctypes.c_double),
+                ("eps_r", ctypes.c_void_p), ("mu_r", ctypes.c_void_p),
+                ("inc", ctypes.c_void_p), ("nrhs", ctypes.c_int64),
+                ("dirs", ctypes.c_void_p), ("ndir", ctypes.c_int64),
+                ("opts", SolveOpts)]
+
+
+class RequestResult(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32),
+                ("residual", ctypes.c_double), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("footprint_bytes", ctypes.c_int64), ("batch_rhs", ctypes.c_int32),
+                ("reused", ctypes.c_int32)]
+
+
+class QueueStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("rejected", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("merged", ctypes.c_int64), ("problems_created", ctypes.c_int64),
+                ("problem_hits", ctypes.c_int64), ("evictions", ctypes.c_int64),
+                ("budget_bytes", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64),
+                ("peak_reserved_bytes", ctypes.c_int64), ("slots", ctypes.c_int32),
+                ("running", ctypes.c_int32), ("peak_running", ctypes.c_int32),
+                ("pending", ctypes.c_int32)]
+
+
 def declared_symbols(header=None):
     """Function names declared in include/cal.h."""
     import re
@@ -106,6 +144,17 @@ def lib():
         "cal_solution_coefficients": ([P, P], ctypes.c_int),
         "cal_farfield": ([P, P, i64, P], ctypes.c_int),
         "cal_solution_destroy": ([P], None),
+        "cal_problem_create": ([P, P, d, P, P, ctypes.POINTER(SolveOpts), ctypes.POINTER(P)], ctypes.c_int),
+        "cal_problem_solve": ([P, P, P, i64, ctypes.POINTER(P)], ctypes.c_int),
+        "cal_problem_get_info": ([P, ctypes.POINTER(ProblemInfo)], ctypes.c_int),
+        "cal_problem_destroy": ([P], None),
+        "cal_queue_create": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(P)], ctypes.c_int),
+        "cal_queue_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(i64)], ctypes.c_int),
+        "cal_queue_wait": ([P, i64, d, ctypes.POINTER(RequestResult), P], ctypes.c_int),
+        "cal_queue_get_stats": ([P, ctypes.POINTER(QueueStats)], ctypes.c_int),
+        "cal_queue_destroy": ([P], None),
+        "cal_request_footprint": ([ctypes.POINTER(Request), ctypes.POINTER(i64), ctypes.POINTER(i64)],
+                                  ctypes.c_int),
         "cal_kernel_launches": ([], i64),
         "cal_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "cal_profile_read": ([ctypes.c_char_p, ctypes.POINTER(i64), ctypes.POINTER(d),
@@ -277,9 +326,8 @@ class Solution:
             lib().cal_solution_destroy(self.h)
 
 
-def pmchwt_solve(ctx: Context, mesh: Mesh, k_ext: float, eps_r, inc, mu_r=None,
-                 opts: SolveOpts | None = None, allow_not_converged: bool = False) -> Solution:
-    M = mesh.info().n_scatterers
+def _materials(M, eps_r, mu_r):
+    """(re, im) arrays [M][2] for eps_r and mu_r (a scalar applies to every scatterer)."""
     e = np.asarray(eps_r, dtype=np.complex128).reshape(-1)
     if len(e) == 1:
         e = np.repeat(e, M)
@@ -290,6 +338,12 @@ def pmchwt_solve(ctx: Context, mesh: Mesh, k_ext: float, eps_r, inc, mu_r=None,
         if len(mu) == 1:
             mu = np.repeat(mu, M)
         ma = np.ascontiguousarray(np.stack([mu.real, mu.imag], 1))
+    return ea, ma
+
+
+def pmchwt_solve(ctx: Context, mesh: Mesh, k_ext: float, eps_r, inc, mu_r=None,
+                 opts: SolveOpts | None = None, allow_not_converged: bool = False) -> Solution:
+    ea, ma = _materials(mesh.info().n_scatterers, eps_r, mu_r)
     inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
     h = ctypes.c_void_p()
     o = opts or solve_opts()
@@ -297,3 +351,104 @@ def pmchwt_solve(ctx: Context, mesh: Mesh, k_ext: float, eps_r, inc, mu_r=None,
                                 len(inc), ctypes.byref(o), ctypes.byref(h))
     _check(rc, allow=(ENOTCONV,) if allow_not_converged else ())
     return Solution(h, len(inc), mesh.info().n_edges, rc, ctx)
+
+
+class Problem:
+    """Assembled operators of one (mesh, k_ext, materials, options), resident on the device."""
+
+    def __init__(self, ctx: Context, mesh: Mesh, k_ext: float, eps_r, mu_r=None,
+                 opts: SolveOpts | None = None):
+        ea, ma = _materials(mesh.info().n_scatterers, eps_r, mu_r)
+        self.ctx = ctx
+        self.n_edges = mesh.info().n_edges
+        self.h = ctypes.c_void_p()
+        o = opts or solve_opts()
+        _check(lib().cal_problem_create(ctx.h, mesh.h, float(k_ext), _ptr(ea), _ptr(ma), ctypes.byref(o),
+                                        ctypes.byref(self.h)))
+
+    def info(self) -> ProblemInfo:
+        out = ProblemInfo()
+        _check(lib().cal_problem_get_info(self.h, ctypes.byref(out)))
+        return out
+
+    def solve(self, inc, ctx: Context | None = None, allow_not_converged: bool = False) -> Solution:
+        c = ctx or self.ctx
+        inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+        h = ctypes.c_void_p()
+        rc = lib().cal_problem_solve(c.h, self.h, _ptr(inc), len(inc), ctypes.byref(h))
+        _check(rc, allow=(ENOTCONV,) if allow_not_converged else ())
+        return Solution(h, len(inc), self.n_edges, rc, c)
+
+    def __del__(self):
+        if getattr(self, "h", None):
+            lib().cal_problem_destroy(self.h)
+
+
+def make_request(verts, tris, domain, k_ext, eps_r, inc, dirs, mu_r=None, opts: SolveOpts | None = None):
+    """A cal_request and the arrays it points to (keep both alive until submitted)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    dm = None if domain is None else np.ascontiguousarray(domain, dtype=np.int32)
+    M = 1 if dm is None else int(dm.max()) + 1
+    ea, ma = _materials(M, eps_r, mu_r)
+    inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
+    d = np.ascontiguousarray(np.atleast_2d(dirs), dtype=np.float64)
+    r = Request()
+    r.verts, r.nv = v.ctypes.data, len(v)
+    r.tris, r.nt = t.ctypes.data, len(t)
+    r.domain = None if dm is None else dm.ctypes.data
+    r.k_ext = float(k_ext)
+    r.eps_r = ea.ctypes.data
+    r.mu_r = None if ma is None else ma.ctypes.data
+    r.inc, r.nrhs = inc.ctypes.data, len(inc)
+    r.dirs, r.ndir = d.ctypes.data, len(d)
+    r.opts = opts or solve_opts()
+    return r, (v, t, dm, ea, ma, inc, d)
+
+
+def request_footprint(req: Request):
+    """(resident bytes, per-solve bytes) the queue reserves for a request (host only)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(lib().cal_request_footprint(ctypes.byref(req), ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+class Queue:
+    """Serving loop: continuous batching of solve requests on one device."""
+
+    def __init__(self, device: int = 0, budget_bytes: int = 0, slots: int = 4):
+        self.h = ctypes.c_void_p()
+        _check(lib().cal_queue_create(device, budget_bytes, slots, ctypes.byref(self.h)))
+        self._shape = {}
+
+    def submit(self, verts, tris, domain, k_ext, eps_r, inc, dirs, mu_r=None,
+               opts: SolveOpts | None = None) -> int:
+        r, keep = make_request(verts, tris, domain, k_ext, eps_r, inc, dirs, mu_r, opts)
+        t = ctypes.c_int64()
+        _check(lib().cal_queue_submit(self.h, ctypes.byref(r), ctypes.byref(t)))
+        del keep  # the queue copied every input
+        self._shape[t.value] = (r.nrhs, r.ndir)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0):
+        """(RequestResult, far field [nrhs][ndir][3] complex128 or None if it failed)."""
+        nrhs, ndir = self._shape.get(ticket, (0, 0))
+        res = RequestResult()
+        far = np.zeros((nrhs, ndir, 3), dtype=np.complex128) if nrhs else None
+        _check(lib().cal_queue_wait(self.h, ticket, float(timeout), ctypes.byref(res), _ptr(far)))
+        self._shape.pop(ticket, None)
+        ok = res.status in (OK, ENOTCONV)
+        return res, (far if ok else None)
+
+    def stats(self) -> QueueStats:
+        out = QueueStats()
+        _check(lib().cal_queue_get_stats(self.h, ctypes.byref(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().cal_queue_destroy(self.h)
+            self.h = ctypes.c_void_p()
+
+    def __del__(self):
+        self.close()

@@ -207,25 +207,25 @@ std::complex<double> interior_k(double k_e, std::complex<double> eps, std::compl
 // =============================================================================
 struct cal_solution {
   Ctx* ctx = nullptr;
-  std::unique_ptr<Space> rwg;
+  std::shared_ptr<Space> rwg;  // shared with the problem it came from
   double2* d_x = nullptr;  // [nrhs][2N]
   int64_t nrhs = 0, ne = 0;
   double k_e = 0.0, mu_e = 1.0;
   cal_solve_info info{};
-  ~cal_solution() { dfree(d_x, ctx ? ctx->stream : nullptr); }
+  ~cal_solution() { dfree(d_x, nullptr); }  // far-field and copy calls are synchronous
 };
 
 namespace {
 
 struct Pmchwt {
-  Ctx* ctx;
-  Mesh* mesh;
+  Ctx* ctx = nullptr;    // context of the call in progress (create or solve)
+  Mesh* mesh = nullptr;  // only during create
   int M;
   int64_t N;  // basis count
   double k_e;
   std::vector<std::complex<double>> k_m, mu_m;
   cal_solve_opts o;
-  std::unique_ptr<Space> rwg, bc;
+  std::shared_ptr<Space> rwg, bc;
   std::unique_ptr<Op> A_ext;
   std::vector<std::unique_ptr<Op>> A_int, P_ext, P_int;
   // Gram
@@ -252,7 +252,7 @@ struct Pmchwt {
   int* d_gemm_err = nullptr;
   int64_t matvecs = 0;
   ~Pmchwt() {
-    cudaStream_t st = ctx ? ctx->stream : nullptr;
+    cudaStream_t st = nullptr;  // every solve has completed: the legacy stream orders the release
     for (void* p : {(void*)d_grp, (void*)d_gcol, (void*)d_grpT, (void*)d_gcolT, (void*)d_gval, (void*)d_gvalT, t1,
                     t2, (void*)d_gath, (void*)d_Bt, (void*)d_ZS, (void*)d_ZC, (void*)d_gemm_err})
       dfree(p, st);
@@ -269,6 +269,41 @@ struct Pmchwt {
     b.rowptr = op.format == CAL_CSR ? op.d_rowptr : nullptr;
     b.col = op.format == CAL_CSR ? op.d_col : nullptr;
     return b;
+  }
+
+  // Batch state for nbatch right-hand sides in lockstep: work vectors,
+  // tensor-core product buffers and the Gram solvers (2 nbatch systems).
+  // Kept between solves of the same batch width.
+  int setup_batch(int nbatch) {
+    if (nbatch == nb && t1) return CAL_OK;
+    for (void* p : {t1, t2, (void*)d_gath, (void*)d_Bt, (void*)d_ZS, (void*)d_ZC, (void*)d_gemm_err})
+      dfree(p, nullptr);  // the previous solve has completed
+    t1 = t2 = nullptr;
+    d_gath = nullptr;
+    d_Bt = d_ZS = d_ZC = nullptr;
+    d_gemm_err = nullptr;
+    NB = 0;
+    gsA32.reset();
+    gsP32.reset();
+    gsA64.reset();
+    gsP64.reset();
+    cudaStream_t st = ctx->stream;
+    int rc;
+    if (o.precond != CAL_PRECOND_NONE) {
+      // M_A = diag(G, G); M_P = diag(-G^T, -G^T): two component systems per vector
+      if (o.precision == CAL_FP64) {
+        gsA64 = std::make_unique<GramSolver<double>>();
+        gsP64 = std::make_unique<GramSolver<double>>();
+        if ((rc = gsA64->init(d_grp, d_gcol, d_gval, N, 2 * nbatch, gnnz, 1.0, 1e-13, 30, st))) return rc;
+        if ((rc = gsP64->init(d_grpT, d_gcolT, d_gvalT, N, 2 * nbatch, gnnz, -1.0, 1e-13, 30, st))) return rc;
+      } else {
+        gsA32 = std::make_unique<GramSolver<float>>();
+        gsP32 = std::make_unique<GramSolver<float>>();
+        if ((rc = gsA32->init(d_grp, d_gcol, d_gval, N, 2 * nbatch, gnnz, 1.0, 1e-6, 14, st))) return rc;
+        if ((rc = gsP32->init(d_grpT, d_gcolT, d_gvalT, N, 2 * nbatch, gnnz, -1.0, 1e-6, 14, st))) return rc;
+      }
+    }
+    return alloc_batch(nbatch);
   }
 
   int alloc_batch(int nrhs) {
@@ -547,6 +582,24 @@ void opts_default(cal_solve_opts* o) {
 
 }  // namespace
 
+// A problem: the assembled A and P blocks, the Gram matrices and the spaces of
+// one (mesh, k, material, options), resident on the device between solves.
+struct cal_problem {
+  int device = 0;
+  Pmchwt P;
+  double t_setup = 0, t_assemble_A = 0, t_assemble_P = 0;  // seconds, at creation
+  int64_t bytes_A = 0, bytes_P = 0, bytes_G = 0;
+  int64_t batch_bytes() const {
+    if (!P.t1) return 0;
+    const int64_t n2 = 2 * P.N;
+    int64_t b = 3 * (int64_t)P.nb * n2 * 16;
+    if (P.d_Bt) b += (int64_t)P.NB * 2 * P.A_ext->rows * 4 + 2 * (int64_t)P.A_ext->rows * P.NB * 4;
+    const int64_t csz = P.o.precision == CAL_FP64 ? 16 : 8, rsz = csz / 2;
+    if (P.o.precond != CAL_PRECOND_NONE) b += 2 * (P.gnnz * rsz + 10 * (int64_t)P.nb * P.N * csz);
+    return b;
+  }
+};
+
 // =============================================================================
 // C ABI
 // =============================================================================
@@ -632,15 +685,7 @@ int cal_space_create(cal_mesh* mesh, int kind, cal_space** out) {
   return CAL_OK;
 }
 
-void cal_space_destroy(cal_space* space) {
-  if (!space) return;
-  // the space may still be read by work on any stream, and the context whose
-  // stream ordered its allocation may be gone: wait for the device, then free
-  // on the legacy stream
-  cudaDeviceSynchronize();
-  space->impl.stream = nullptr;
-  delete space;
-}
+void cal_space_destroy(cal_space* space) { delete space; }  // every call that reads it is synchronous
 
 int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space* test,
                  cal_space* trial, int scatterer, double near_cutoff, int q_regular, int q_singular,
@@ -664,10 +709,8 @@ int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space*
 
 void cal_op_destroy(cal_op* op) {
   if (!op) return;
-  // a matvec on a caller stream may still read the operator, and its context
-  // may already be destroyed: wait for the device, then free on the legacy stream
+  // a matvec on a caller stream may still read the operator: wait for the device
   cudaDeviceSynchronize();
-  op->impl.ctx = nullptr;
   delete op;
 }
 
@@ -763,14 +806,15 @@ void cal_solve_opts_default(cal_solve_opts* opts) {
   if (opts) opts_default(opts);
 }
 
-int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r,
-                     const double* mu_r, const double* inc, int64_t nrhs,
-                     const cal_solve_opts* opts, cal_solution** out) {
-  if (!ctx || !mesh || !eps_r || !inc || nrhs < 1 || !out) return fail(CAL_EINVAL, "cal_pmchwt_solve: bad argument");
-  if (!(k_ext > 0) || !std::isfinite(k_ext)) return fail(CAL_EINVAL, "cal_pmchwt_solve: k_ext must be positive");
+int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r, const double* mu_r,
+                       const cal_solve_opts* opts, cal_problem** out) {
+  if (!ctx || !mesh || !eps_r || !out) return fail(CAL_EINVAL, "cal_problem_create: bad argument");
+  if (!(k_ext > 0) || !std::isfinite(k_ext)) return fail(CAL_EINVAL, "cal_problem_create: k_ext must be positive");
   CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
   const double t_start = now();
-  Pmchwt P;
+  auto prob = std::make_unique<cal_problem>();
+  prob->device = ctx->impl.device;
+  Pmchwt& P = prob->P;
   P.ctx = &ctx->impl;
   P.mesh = &mesh->impl;
   P.M = (int)mesh->impl.M;
@@ -792,16 +836,14 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     P.k_m.push_back(interior_k(k_ext, e, u));
     P.mu_m.push_back(u);
   }
-  for (int64_t q = 0; q < 6 * nrhs; ++q)
-    if (!std::isfinite(inc[q])) return fail(CAL_EINVAL, "solve: non-finite incident field");
   cudaStream_t st = ctx->impl.stream;
   int rc;
   // spaces
-  P.rwg = std::make_unique<Space>();
+  P.rwg = std::make_shared<Space>();
   if ((rc = build_rwg(*P.rwg, mesh->impl)) || (rc = upload_space(*P.rwg, st))) return rc;
   const bool need_bc = o.precond != CAL_PRECOND_NONE;
   if (need_bc) {
-    P.bc = std::make_unique<Space>();
+    P.bc = std::make_shared<Space>();
     if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc, st))) return rc;
   }
   const double t_setup = now();
@@ -819,9 +861,9 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
       return rc;
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_A = now();
-  int64_t bytes_A = 0, bytes_P = 0;
+  int64_t bytes_A = 0, bytes_P = 0, bytes_G = 0;
   const size_t esz = prec == CAL_FP32 ? 8 : 16;
-  bytes_A += P.A_ext->nnz * esz * 2;
+  for (auto* a : {P.A_ext.get()}) bytes_A += a->nnz * esz * 2;
   for (auto& a : P.A_int) bytes_A += a->nnz * esz * 2;
   // P on BC: block diagonal per scatterer
   if (need_bc) {
@@ -840,7 +882,9 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
                                      o.q_regular_P, o.q_singular_P, aprec, P.P_int[m])))
         return rc;
       for (auto* op : {P.P_ext[m].get(), P.P_int[m].get()})
-        if (op) bytes_P += op->nnz * esz * ((want & 2) ? 2 : 1);
+        if (op)
+          bytes_P += op->nnz * esz * ((want & 2) ? 2 : 1) +
+                     (op->format == CAL_CSR ? (int64_t)(op->h_rowptr.size() * 8 + op->h_col.size() * 4) : 0);
     }
     // Gram G (rows RWG, cols BC) and its transpose
     std::vector<int64_t> rp, rpT;
@@ -872,30 +916,68 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     if ((rc = launch_gram(*P.rwg, *P.bc, P.d_grp, P.d_gcol, P.d_grpT, P.d_gcolT, P.d_gval, P.d_gvalT, st)))
       return rc;
     CAL_TRY_CUDA(cudaStreamSynchronize(st));
-    // M_A = diag(G, G); M_P = diag(-G^T, -G^T): two component systems per vector
-    const int nbatch = (int)std::min<int64_t>(nrhs, 32);
-    if (prec == CAL_FP64) {
-      P.gsA64 = std::make_unique<GramSolver<double>>();
-      P.gsP64 = std::make_unique<GramSolver<double>>();
-      if ((rc = P.gsA64->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-13, 30, st))) return rc;
-      if ((rc = P.gsP64->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-13, 30, st))) return rc;
-    } else {
-      P.gsA32 = std::make_unique<GramSolver<float>>();
-      P.gsP32 = std::make_unique<GramSolver<float>>();
-      if ((rc = P.gsA32->init(P.d_grp, P.d_gcol, P.d_gval, n, 2 * nbatch, P.gnnz, 1.0, 1e-6, 14, st))) return rc;
-      if ((rc = P.gsP32->init(P.d_grpT, P.d_gcolT, P.d_gvalT, n, 2 * nbatch, P.gnnz, -1.0, 1e-6, 14, st))) return rc;
-    }
+    bytes_G = 2 * ((n + 1) * 8 + P.gnnz * (4 + 8));
   }
-  const int nbatch = (int)std::min<int64_t>(nrhs, 32);
-  if ((rc = P.alloc_batch(nbatch))) return rc;
-  CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_P = now();
+  prob->t_setup = t_setup - t_start;
+  prob->t_assemble_A = t_A - t_setup;
+  prob->t_assemble_P = t_P - t_A;
+  prob->bytes_A = bytes_A;
+  prob->bytes_P = bytes_P;
+  prob->bytes_G = bytes_G;
+  P.mesh = nullptr;  // the mesh may go: the solves need only the spaces and blocks
+  P.ctx = nullptr;
+  *out = prob.release();
+  return CAL_OK;
+}
+
+void cal_problem_destroy(cal_problem* prob) { delete prob; }  // its solves are synchronous
+
+int cal_problem_get_info(const cal_problem* prob, cal_problem_info* info) {
+  if (!prob || !info) return fail(CAL_EINVAL, "cal_problem_get_info: NULL argument");
+  const Pmchwt& P = prob->P;
+  info->n_unknowns = 2 * P.N;
+  info->n_scatterers = P.M;
+  info->precision = P.o.precision;
+  info->precond = P.o.precond;
+  info->bytes_A = prob->bytes_A;
+  info->bytes_P = prob->bytes_P;
+  info->bytes_G = prob->bytes_G;
+  info->bytes_batch = prob->batch_bytes();
+  info->batch_width = P.t1 ? P.nb : 0;
+  info->t_setup = prob->t_setup;
+  info->t_assemble_A = prob->t_assemble_A;
+  info->t_assemble_P = prob->t_assemble_P;
+  return CAL_OK;
+}
+
+int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_t nrhs, cal_solution** out) {
+  if (!ctx || !prob || !inc || nrhs < 1 || !out) return fail(CAL_EINVAL, "cal_problem_solve: bad argument");
+  if (ctx->impl.device != prob->device)
+    return fail(CAL_EINVAL, "cal_problem_solve: the problem lives on device %d", prob->device);
+  for (int64_t q = 0; q < 6 * nrhs; ++q)
+    if (!std::isfinite(inc[q])) return fail(CAL_EINVAL, "solve: non-finite incident field");
+  CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
+  Pmchwt& P = prob->P;
+  struct Bind {  // the problem runs on this call's context until it returns
+    Pmchwt& P;
+    ~Bind() { P.ctx = nullptr; }
+  } bind{P};
+  P.ctx = &ctx->impl;
+  const cal_solve_opts& o = P.o;
+  const int prec = o.precision;
+  cudaStream_t st = ctx->impl.stream;
+  const double t0 = now();
+  int rc;
+  const int nbatch = (int)std::min<int64_t>(nrhs, 32);
+  if ((rc = P.setup_batch(nbatch))) return rc;
+  if (P.d_gemm_err) CAL_TRY_CUDA(cudaMemsetAsync(P.d_gemm_err, 0, sizeof(int), st));
   // right-hand sides and solves
   auto sol = std::make_unique<cal_solution>();
   sol->ctx = &ctx->impl;
   sol->nrhs = nrhs;
   sol->ne = P.N;
-  sol->k_e = k_ext;
+  sol->k_e = P.k_e;
   const int64_t n2 = 2 * P.N;
   double* d_inc;
   double2 *d_b, *d_rhs, *d_r;
@@ -912,7 +994,7 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
     ~Guard() { dfree(p, s); }
   };
   Guard g1{d_b, st}, g2{d_rhs, st}, g3{d_r, st}, g4{d_inc, st};
-  if ((rc = launch_rhs(*P.rwg, d_inc, (int)nrhs, k_ext, 1.0, d_b, st))) return rc;
+  if ((rc = launch_rhs(*P.rwg, d_inc, (int)nrhs, P.k_e, 1.0, d_b, st))) return rc;
   P.matvecs = 0;
   int total_it = 0;
   double worst_res = 0.0;
@@ -1003,22 +1085,36 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   }
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_end = now();
-  sol->rwg = std::move(P.rwg);
+  sol->rwg = P.rwg;
   cal_solve_info& info = sol->info;
   info.iterations = total_it;
   info.converged = all_conv;
   info.matvecs = P.matvecs;
   info.residual = worst_res;
-  info.t_setup = t_setup - t_start;
-  info.t_assemble_A = t_A - t_setup;
-  info.t_assemble_P = t_P - t_A;
-  info.t_solve = t_end - t_P;
-  info.bytes_A = bytes_A;
-  info.bytes_P = bytes_P;
+  info.t_setup = prob->t_setup;
+  info.t_assemble_A = prob->t_assemble_A;
+  info.t_assemble_P = prob->t_assemble_P;
+  info.t_solve = t_end - t0;
+  info.bytes_A = prob->bytes_A;
+  info.bytes_P = prob->bytes_P;
   info.n_unknowns = 2 * P.N;
   *out = sol.release();
   if (!all_conv) return fail(CAL_ENOTCONV, "GMRES reached maxit (residual %.3e > tol %.1e)", worst_res, o.tol);
   return CAL_OK;
+}
+
+int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r,
+                     const double* mu_r, const double* inc, int64_t nrhs,
+                     const cal_solve_opts* opts, cal_solution** out) {
+  if (!ctx || !mesh || !eps_r || !inc || nrhs < 1 || !out) return fail(CAL_EINVAL, "cal_pmchwt_solve: bad argument");
+  for (int64_t q = 0; q < 6 * nrhs; ++q)
+    if (!std::isfinite(inc[q])) return fail(CAL_EINVAL, "solve: non-finite incident field");
+  cal_problem* prob = nullptr;
+  int rc = cal_problem_create(ctx, mesh, k_ext, eps_r, mu_r, opts, &prob);
+  if (rc) return rc;
+  rc = cal_problem_solve(ctx, prob, inc, nrhs, out);
+  cal_problem_destroy(prob);
+  return rc;
 }
 
 int cal_solution_get_info(const cal_solution* sol, cal_solve_info* info) {
@@ -1055,14 +1151,7 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
   return rc;
 }
 
-void cal_solution_destroy(cal_solution* sol) {
-  if (!sol) return;
-  // as for operators: the context may be gone, so nothing here touches it
-  cudaDeviceSynchronize();
-  sol->ctx = nullptr;
-  if (sol->rwg) sol->rwg->stream = nullptr;
-  delete sol;
-}
+void cal_solution_destroy(cal_solution* sol) { delete sol; }
 
 int64_t cal_kernel_launches(void) { return cal::launches(); }
 

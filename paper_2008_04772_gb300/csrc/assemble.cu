@@ -1070,7 +1070,7 @@ static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, 
   auto kern6 = bc_tile_kernel<R, 6>;
   auto kern1 = bc_tile_kernel<R, 1>;
   auto kern = a.nreg == 6 ? kern6 : kern1;
-  CAL_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  if (int rc = ensure_dyn_smem((const void*)kern, (int)smem)) return rc;
   int per_sm = 0;
   constexpr int TILE_THREADS = 160;
   CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_THREADS, smem));

@@ -363,7 +363,7 @@ int gemm_tf32x3(const float* A, int64_t M, int64_t K, const float* Bt, int NB, f
   const int per = (int)((ktotal + split - 1) / split);
   split = (ktotal + per - 1) / per;
   const int smem = STAGES * 2 * (BM * BK * 4 + NB * BK * 4) + (int)sizeof(Bars) + 1024;
-  CAL_TRY_CUDA(cudaFuncSetAttribute(gemm_tf32x3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  if (int rc = ensure_dyn_smem((const void*)gemm_tf32x3_kernel, smem)) return rc;
   const int tok = prof_begin(st, "gemm_tc", 2.0 * 3.0 * (double)M * K * NB);
   gemm_tf32x3_kernel<<<dim3((unsigned)mt, (unsigned)split), THREADS, smem, st>>>(mA, mB, Z, M, NB, NB, K, per, d_err);
   prof_end(st, tok);

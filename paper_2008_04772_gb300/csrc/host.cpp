@@ -598,7 +598,6 @@ static int upload(T** dst, const T* src, size_t n, cudaStream_t st) {
 }
 
 int upload_space(Space& s, cudaStream_t st) {
-  s.stream = st;
   std::vector<TriF> tf(s.ntri);
   for (int64_t t = 0; t < s.ntri; ++t) {
     const TriD& d = s.triD[t];
@@ -631,23 +630,21 @@ int upload_space(Space& s, cudaStream_t st) {
   return CAL_OK;
 }
 
+// Long-lived objects are used only by calls that return after their GPU work
+// has completed, so their memory is released in order on the legacy stream: no
+// context (whose stream might already be destroyed) is needed at that point.
 Space::~Space() {
-  dfree(d_triF, stream);
-  dfree(d_triD, stream);
-  dfree(d_slot_edge, stream);
-  dfree(d_slot_swf, stream);
-  dfree(d_slot_swd, stream);
-  dfree(d_cell_tri_ptr, stream);
-  dfree(d_cell_tri, stream);
-  for (auto p : d_sing) dfree(p, stream);
+  for (void* p : {(void*)d_triF, (void*)d_triD, (void*)d_slot_edge, (void*)d_slot_swf, (void*)d_slot_swd,
+                  (void*)d_cell_tri_ptr, (void*)d_cell_tri})
+    dfree(p, nullptr);
+  for (auto p : d_sing) dfree(p, nullptr);
 }
 
 Op::~Op() {
-  cudaStream_t st = ctx ? ctx->stream : nullptr;
-  dfree(d_S, st);
-  dfree(d_C, st);
-  dfree(d_rowptr, st);
-  dfree(d_col, st);
+  dfree(d_S, nullptr);
+  dfree(d_C, nullptr);
+  dfree(d_rowptr, nullptr);
+  dfree(d_col, nullptr);
 }
 
 }  // namespace cal

@@ -10,7 +10,10 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "cal.h"
@@ -27,6 +30,23 @@ int fail(int code, const char* fmt, ...);
       return ::cal::fail(CAL_ECUDA, "%s: %s (%s:%d)", #expr,                  \
                          cudaGetErrorString(_e), __FILE__, __LINE__);         \
   } while (0)
+
+// Raise a kernel's dynamic shared-memory limit to at least `bytes` on the
+// current device. The limit only grows, so a launch from another host thread
+// that was sized for less stays valid (setting it per launch would race).
+inline int ensure_dyn_smem(const void* kern, int bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, int> limit;
+  int dev = 0;
+  CAL_TRY_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(mu);
+  int& cur = limit[{dev, kern}];
+  if (bytes > cur) {
+    CAL_TRY_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    cur = bytes;
+  }
+  return CAL_OK;
+}
 
 // ---- instrumentation (host.cpp) ------------------------------------------------
 void note_launch(int n = 1);
@@ -93,7 +113,6 @@ struct Mesh {
 
 struct Space {
   Mesh* mesh = nullptr;
-  cudaStream_t stream = nullptr;
   int kind = 0;
   int64_t ntri = 0, nbasis = 0;
   int nslot = 0;

@@ -616,7 +616,6 @@ __global__ void real_convert_kernel(const double* __restrict__ a, R* __restrict_
 template <typename R>
 int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n_,
                         int nsys_, int64_t nnz, double neg_, double tol_, int maxit_, cudaStream_t st) {
-  stream = st;
   n = n_;
   nsys = nsys_;
   neg = neg_;
@@ -640,12 +639,9 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
 template <typename R>
 GramSolver<R>::~GramSolver() {
   if (graph_exec) cudaGraphExecDestroy(graph_exec);
-  dfree(d_in, stream);
-  dfree(d_out, stream);
-  dfree(d_val, stream);
-  dfree(d_work, stream);
-  dfree(d_acc, stream);
-  dfree(d_done, stream);
+  // every solve has completed when the solver is destroyed: release on the legacy stream
+  for (void* p : {(void*)d_in, (void*)d_out, (void*)d_val, (void*)d_work, (void*)d_acc, (void*)d_done})
+    dfree(p, nullptr);
 }
 
 template <typename R>

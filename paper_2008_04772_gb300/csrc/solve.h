@@ -50,7 +50,6 @@ struct GramSolver {
   double* d_acc = nullptr;
   int* d_done = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
-  cudaStream_t stream = nullptr;  // allocations are ordered on this stream
   int enqueue(const C* b, C* out, cudaStream_t st);
   int init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n, int nsys,
            int64_t nnz, double neg, double tol, int maxit, cudaStream_t st);
