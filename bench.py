@@ -272,6 +272,8 @@ def run_ours(args, rank, world):
         "e2e": {"value": 1.0 / statistics.median(t_e2e), "unit": "solves/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
     }
+    if args.multirhs:
+        out["multi_rhs"] = run_multirhs(dev)
     if args.serving:
         out["serving"] = run_serving(dev)
     if args.cpu_baseline:
@@ -279,9 +281,66 @@ def run_ours(args, rank, world):
     return out
 
 
+MULTI_RHS = {"name": "aggregate8x2500_kD20_Di_near2h_32rhs", "prisms": 8, "tris_per_prism": 2500, "seed": 0,
+             "k": 20.0, "eps": 3.17 + 0.01j, "nrhs": 32, "precond": "Di", "near_cutoff_P": 2.0, "tol": 1e-5}
+
+
+def run_multirhs(dev):
+    """The 32-direction aggregate: FP32-bulk solve whose GMRES applies the stored
+    blocks to all 32 columns at once through the tcgen05 3xTF32 product."""
+    import ctypes
+
+    import torch
+
+    from paper_2008_04772_gb300 import cal, meshgen
+    W = MULTI_RHS
+    L = cal.lib()
+    ctx = cal.Context(dev)
+    m = meshgen.prism_aggregate(W["prisms"], W["tris_per_prism"], seed=W["seed"], diameter=1.0, gap=0.05)
+    mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    d = meshgen.fibonacci_directions(W["nrhs"])
+    inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+    opts = cal.solve_opts(precond=W["precond"], precision=cal.FP32, tol=W["tol"], near_cutoff_P=W["near_cutoff_P"])
+    L.cal_profile_enable(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    sol = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], inc, opts=opts)
+    sol.far_field(meshgen.fibonacci_directions(64))
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    fam = {}
+    for name in ("gemm_tc", "pair_gemv", "pair_spmv", "bicgstab", "gmres_cgs", "bc_tile", "rwg_regular", "singular"):
+        n_, ms_, u_ = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+        L.cal_profile_read(name.encode(), ctypes.byref(n_), ctypes.byref(ms_), ctypes.byref(u_))
+        fam[name] = {"launches": n_.value, "ms": round(ms_.value, 3)}
+    n, ms, u = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    L.cal_profile_read(b"gemm_tc", ctypes.byref(n), ctypes.byref(ms), ctypes.byref(u))
+    L.cal_profile_enable(0)
+    info = sol.info()
+    peaks = _measured_peaks()
+    tf32_peak = peaks.get("bf16_tflops", 1900.0) * 1.1 / 2.25  # nominal dense TF32 / BF16 ratio
+    achieved = u.value / (ms.value / 1e3) / 1e12 if ms.value > 0 else 0.0
+    N = int(info.n_unknowns) // 2
+    return {
+        "workload": W["name"], "triangles": int(len(m.tris)), "unknowns": int(info.n_unknowns),
+        "k_ext": W["k"], "nrhs": W["nrhs"], "preconditioner": f"{W['precond']} near-field {W['near_cutoff_P']}h",
+        "seconds": t, "solves_per_s": W["nrhs"] / t, "iterations": int(info.iterations),
+        "phase_s": {"setup": info.t_setup, "assemble_A": info.t_assemble_A, "assemble_P": info.t_assemble_P,
+                    "solve": info.t_solve},
+        "bytes_A_gb": info.bytes_A / 1e9, "bytes_P_gb": info.bytes_P / 1e9,
+        "gemm_tc": {"launches": n.value, "ms": ms.value,
+                    "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                                 "frac": achieved / tf32_peak,
+                                 "flops": "executed TF32 flops, 3 products x 2 M K NB per launch",
+                                 "peak_source": "measured bf16 burst x 1.1/2.25 (nominal TF32/BF16)"}},
+        "columns_N": N,
+        "kernels": fam,
+    }
+
+
 SERVING = {"name": "aggregate_requests_scaled", "requests": 48, "seed": 0, "prisms": (1, 8),
            "tris_per_prism": (100, 600), "k": (1.0, 10.0), "eps_re": (2.5, 3.5), "eps_im": 0.01,
-           "nrhs": (1, 16), "ndir": 64, "precond": "Di", "near_cutoff_P": 2.0, "tol": 1e-5,
+           "nrhs": (1, 16), "ndir": 64, "precond": "D", "near_cutoff_P": math.inf, "tol": 1e-5,
            "slots": 4, "load": 0.8}
 
 
@@ -349,12 +408,15 @@ def run_serving(dev):
     th.start()
     lat = []
     statuses = []
+    detail = []
     for i in range(len(reqs)):
         while tk[i] is None:
             time.sleep(0.001)
         r = q.wait(tk[i])[0]
         lat.append(1e3 * (r.t_done - r.t_submit))
         statuses.append(r.status)
+        detail.append((len(reqs[i][0].tris), round(reqs[i][1], 2), len(reqs[i][3]), r.status, r.iterations,
+                       round(1e3 * (r.t_done - r.t_start))))
     th.join()
     t_open = time.perf_counter() - t1
     st = q.stats()
@@ -367,7 +429,9 @@ def run_serving(dev):
                 "triangles": [int(min(tri)), int(max(tri))], "k": list(S["k"]),
                 "eps_r": f"U{list(S['eps_re'])} + {S['eps_im']}i", "nrhs": list(S["nrhs"]),
                 "columns": cols, "far_field_dirs": S["ndir"],
-                "preconditioner": f"{S['precond']} near-field {S['near_cutoff_P']}h", "tol": S["tol"]},
+                "preconditioner": S["precond"] + (f" near-field {S['near_cutoff_P']}h"
+                                                  if math.isfinite(S["near_cutoff_P"]) else " dense"),
+                "tol": S["tol"]},
         "slots": S["slots"],
         "closed_loop": {"solves_per_s": len(reqs) / t_closed, "columns_per_s": cols / t_closed,
                         "seconds": t_closed, "ok": ok},
@@ -375,6 +439,8 @@ def run_serving(dev):
                       "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                       "ok": sum(s == 0 for s in statuses)},
         "latency": "arrival (submit) to far field ready, queue clock",
+        "slowest": sorted(detail, key=lambda x: -x[5])[:6],
+        "statuses": {str(k): statuses.count(k) for k in set(statuses)},
         "queue": {"peak_running": st.peak_running, "merged": st.merged, "problems_created": st.problems_created,
                   "evictions": st.evictions, "peak_reserved_gb": st.peak_reserved_bytes / 1e9,
                   "budget_gb": st.budget_bytes / 1e9},
@@ -456,6 +522,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the request-queue (continuous batching) run")
+    ap.add_argument("--no-multirhs", dest="multirhs", action="store_false",
+                    help="skip the 32-direction aggregate run")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)

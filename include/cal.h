@@ -199,6 +199,9 @@ typedef struct {
   int32_t maxit;            /* iteration cap                                    */
   int32_t refine;           /* FP32 path: outer FP64 iterative refinement steps */
   int32_t rhs_mode;         /* 0 = total traces (A^e + A^i) u = u^inc           */
+  int32_t matrix_free;      /* 1: A is not stored; its regular pairs are
+                               recomputed in every application (only the
+                               touching-pair entries are kept, sparse)          */
 } cal_solve_opts;
 void cal_solve_opts_default(cal_solve_opts* opts);
 
@@ -239,9 +242,11 @@ void cal_solution_destroy(cal_solution* sol);
 int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* eps_r,
                        const double* mu_r, const cal_solve_opts* opts, cal_problem** out);
 /* Same contract and result as cal_pmchwt_solve for the problem's operators;
-   info.t_setup/t_assemble_* are the problem's creation times. */
+   info.t_setup/t_assemble_* are the problem's creation times. `solver` (may be
+   NULL: the options given at creation) supplies tol, restart, maxit and refine
+   for this solve; its assembly fields are ignored. */
 int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_t nrhs,
-                      cal_solution** out);
+                      const cal_solve_opts* solver, cal_solution** out);
 typedef struct {
   int64_t n_unknowns;                 /* 2N                                        */
   int32_t n_scatterers, precision, precond;
@@ -251,6 +256,12 @@ typedef struct {
   int32_t batch_width;                /* right-hand sides per lockstep batch       */
   double t_setup, t_assemble_A, t_assemble_P;
 } cal_problem_info;
+/* y = A x with the problem's PMCHWT operator A (eqs. multiple_operator,
+   AimAem: the exterior blocks on the union plus each scatterer's interior
+   blocks), stored or matrix-free as it was created; x, y [nrhs][2N] complex128
+   host arrays in the unknown ordering above. Vectors are applied in float64
+   (the operator's entries keep the problem's precision). */
+int cal_problem_apply(cal_ctx* ctx, cal_problem* prob, const double* x, double* y, int64_t nrhs);
 int cal_problem_get_info(const cal_problem* prob, cal_problem_info* info);
 void cal_problem_destroy(cal_problem* prob);
 
@@ -323,6 +334,12 @@ void cal_queue_destroy(cal_queue* q);
 int cal_request_footprint(const cal_request* req, int64_t* resident_bytes, int64_t* solve_bytes);
 
 /* ---- instrumentation ------------------------------------------------------ */
+/* The paper has no counterpart: a check of the double-precision e^{i x} and
+   e^{-|x|} that the singular-pair kernel evaluates itself (Cody–Waite
+   reduction, Taylor series), against the CUDA library's sincos and exp, on n
+   points evenly spread over [lo, hi] on the current device. Writes the max
+   absolute error of (cos, sin) and the max relative error of exp. */
+int cal_check_elementary(int64_t n, double lo, double hi, double* err_cis, double* err_exp);
 /* Number of kernels this library has launched since load (all contexts). */
 int64_t cal_kernel_launches(void);
 /* on != 0: bracket every assembly kernel launch with CUDA events on its own

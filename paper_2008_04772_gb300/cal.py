@@ -51,7 +51,8 @@ class SolveOpts(ctypes.Structure):
                 ("q_regular_P", ctypes.c_int32), ("q_singular_P", ctypes.c_int32),
                 ("near_cutoff_P", ctypes.c_double), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
-                ("refine", ctypes.c_int32), ("rhs_mode", ctypes.c_int32)]
+                ("refine", ctypes.c_int32), ("rhs_mode", ctypes.c_int32),
+                ("matrix_free", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -145,8 +146,9 @@ def lib():
         "cal_farfield": ([P, P, i64, P], ctypes.c_int),
         "cal_solution_destroy": ([P], None),
         "cal_problem_create": ([P, P, d, P, P, ctypes.POINTER(SolveOpts), ctypes.POINTER(P)], ctypes.c_int),
-        "cal_problem_solve": ([P, P, P, i64, ctypes.POINTER(P)], ctypes.c_int),
+        "cal_problem_solve": ([P, P, P, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(P)], ctypes.c_int),
         "cal_problem_get_info": ([P, ctypes.POINTER(ProblemInfo)], ctypes.c_int),
+        "cal_problem_apply": ([P, P, P, P, i64], ctypes.c_int),
         "cal_problem_destroy": ([P], None),
         "cal_queue_create": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(P)], ctypes.c_int),
         "cal_queue_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(i64)], ctypes.c_int),
@@ -156,6 +158,7 @@ def lib():
         "cal_request_footprint": ([ctypes.POINTER(Request), ctypes.POINTER(i64), ctypes.POINTER(i64)],
                                   ctypes.c_int),
         "cal_kernel_launches": ([], i64),
+        "cal_check_elementary": ([i64, d, d, ctypes.POINTER(d), ctypes.POINTER(d)], ctypes.c_int),
         "cal_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "cal_profile_read": ([ctypes.c_char_p, ctypes.POINTER(i64), ctypes.POINTER(d),
                               ctypes.POINTER(d)], ctypes.c_int),
@@ -371,13 +374,24 @@ class Problem:
         _check(lib().cal_problem_get_info(self.h, ctypes.byref(out)))
         return out
 
-    def solve(self, inc, ctx: Context | None = None, allow_not_converged: bool = False) -> Solution:
+    def solve(self, inc, ctx: Context | None = None, solver: SolveOpts | None = None,
+              allow_not_converged: bool = False) -> Solution:
+        """solver: tol/restart/maxit/refine for this solve (None: those given at creation)."""
         c = ctx or self.ctx
         inc = np.ascontiguousarray(np.atleast_2d(inc), dtype=np.float64)
         h = ctypes.c_void_p()
-        rc = lib().cal_problem_solve(c.h, self.h, _ptr(inc), len(inc), ctypes.byref(h))
+        rc = lib().cal_problem_solve(c.h, self.h, _ptr(inc), len(inc),
+                                     ctypes.byref(solver) if solver is not None else None, ctypes.byref(h))
         _check(rc, allow=(ENOTCONV,) if allow_not_converged else ())
         return Solution(h, len(inc), self.n_edges, rc, c)
+
+    def apply(self, x, ctx: Context | None = None):
+        """y = A x for x [nrhs][2N] complex (the PMCHWT operator of the problem)."""
+        c = ctx or self.ctx
+        xx = np.ascontiguousarray(np.atleast_2d(x), dtype=np.complex128)
+        y = np.zeros_like(xx)
+        _check(lib().cal_problem_apply(c.h, self.h, _ptr(xx), _ptr(y), len(xx)))
+        return y
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -194,6 +194,81 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
   return CAL_OK;
 }
 
+// Sparse block holding only the touching-pair (Sauter–Schwab) entries of S and C
+// on an RWG space: the stored part of a matrix-free operator. Its pattern is
+// every (i, j) whose supports share a triangle pair of the singular list.
+int assemble_singular_block(Ctx& ctx, double kr, double ki, const Space& sp, int scat, int nsing, int precision,
+                            std::unique_ptr<Op>& out) {
+  const Mesh& m = *sp.mesh;
+  const bool sing32 = precision == CAL_FP32_ALL;
+  if (sing32) precision = CAL_FP32;
+  int rc = set_quadrature_tables(6, nsing);
+  if (rc) return rc;
+  auto op = std::make_unique<Op>();
+  op->ctx = &ctx;
+  op->op_mask = 3;
+  op->precision = precision;
+  op->row_offset = scat < 0 ? 0 : m.edge_off[scat];
+  op->rows = op->cols = (scat < 0 ? m.ne : m.edge_off[scat + 1] - m.edge_off[scat]);
+  op->format = CAL_CSR;
+  const int64_t off = op->row_offset;
+  std::vector<std::vector<int>> rows(op->rows);
+  const int d0 = scat < 0 ? 0 : scat, d1 = scat < 0 ? (int)sp.sing.size() : scat + 1;
+  for (int d = d0; d < d1; ++d)
+    for (const SingPair& q : sp.sing[d])
+      for (int a = 0; a < sp.nslot; ++a)
+        for (int b = 0; b < sp.nslot; ++b) {
+          const int ea = sp.slot_edge[(size_t)q.t1 * sp.nslot + a], eb = sp.slot_edge[(size_t)q.t2 * sp.nslot + b];
+          if (ea < 0 || eb < 0) continue;
+          rows[ea - off].push_back((int)(eb - off));
+          rows[eb - off].push_back((int)(ea - off));
+        }
+  op->h_rowptr.assign(op->rows + 1, 0);
+  for (int64_t i = 0; i < op->rows; ++i) {
+    std::sort(rows[i].begin(), rows[i].end());
+    rows[i].erase(std::unique(rows[i].begin(), rows[i].end()), rows[i].end());
+    op->h_col.insert(op->h_col.end(), rows[i].begin(), rows[i].end());
+    op->h_rowptr[i + 1] = (int64_t)op->h_col.size();
+  }
+  op->nnz = op->h_rowptr.back();
+  const size_t bytes = (size_t)op->nnz * (precision == CAL_FP32 ? 8 : 16);
+  cudaStream_t st = ctx.stream;
+  CAL_TRY_CUDA(dalloc(&op->d_S, std::max<size_t>(bytes, 16), st));
+  CAL_TRY_CUDA(dalloc(&op->d_C, std::max<size_t>(bytes, 16), st));
+  CAL_TRY_CUDA(cudaMemsetAsync(op->d_S, 0, bytes, st));
+  CAL_TRY_CUDA(cudaMemsetAsync(op->d_C, 0, bytes, st));
+  CAL_TRY_CUDA(dalloc((void**)&op->d_rowptr, op->h_rowptr.size() * sizeof(int64_t), st));
+  CAL_TRY_CUDA(dalloc((void**)&op->d_col, std::max<size_t>(op->h_col.size(), 1) * sizeof(int), st));
+  CAL_TRY_CUDA(cudaMemcpyAsync(op->d_rowptr, op->h_rowptr.data(), op->h_rowptr.size() * sizeof(int64_t),
+                               cudaMemcpyHostToDevice, st));
+  if (!op->h_col.empty())
+    CAL_TRY_CUDA(cudaMemcpyAsync(op->d_col, op->h_col.data(), op->h_col.size() * sizeof(int), cudaMemcpyHostToDevice,
+                                 st));
+  AssembleArgs a{};
+  a.sp = &sp;
+  a.scat = scat;
+  a.kr = kr;
+  a.ki = ki;
+  a.want = 3;
+  a.nreg = 6;
+  a.nsing = nsing;
+  a.precision = precision;
+  a.sing32 = sing32;
+  a.format = CAL_CSR;
+  a.row_off = off;
+  a.ld = 0;
+  a.rowptr = op->d_rowptr;
+  a.col = op->d_col;
+  a.S = op->d_S;
+  a.C = op->d_C;
+  a.stream = st;
+  if ((rc = launch_singular(a))) return rc;
+  // the host pattern must outlive the copies
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  out = std::move(op);
+  return CAL_OK;
+}
+
 std::complex<double> interior_k(double k_e, std::complex<double> eps, std::complex<double> mu) {
   std::complex<double> km = k_e * std::sqrt(eps * mu);
   if (km.imag() < 0) km = -km;
@@ -349,6 +424,9 @@ struct Pmchwt {
       return combine_rhs<float2>(ZS, ZC, b.rows, NB, nrhs, N, b.row_off, (float2*)y, al.real(), al.imag(),
                                  be.real(), be.imag(), st);
     }
+    if (b.precision == CAL_FP32 && !b.rowptr && nrhs >= 2)
+      return pair_apply_multi(b, vec_prec, x, y, N, nrhs, al.real(), al.imag(), be.real(), be.imag(), ctx->n_sm,
+                              st);
     const size_t vsz = vec_prec == CAL_FP64 ? sizeof(double2) : sizeof(float2);
     for (int q = 0; q < nrhs; ++q) {
       int rc = pair_apply(b, vec_prec, (const char*)x + q * 2 * N * vsz, (char*)y + q * 2 * N * vsz, N, al.real(),
@@ -363,9 +441,20 @@ struct Pmchwt {
     cudaStream_t st = ctx->stream;
     int rc = zero_vec(y, vec_prec, 2 * N * nrhs, st);
     if (rc) return rc;
-    if ((rc = apply_block(ref(*A_ext), x, y, vec_prec, nrhs, 1.0 / k_e, -k_e))) return rc;  // mu_e = 1
-    for (int m = 0; m < M; ++m)
-      if ((rc = apply_block(ref(*A_int[m]), x, y, vec_prec, nrhs, mu_m[m] / k_m[m], -k_m[m] / mu_m[m]))) return rc;
+    const std::complex<double> ae = 1.0 / k_e, be = -k_e;  // mu_e = 1
+    if ((rc = apply_block(ref(*A_ext), x, y, vec_prec, nrhs, ae, be))) return rc;
+    if (o.matrix_free &&
+        (rc = launch_rwg_free(*rwg, -1, k_e, 0.0, o.q_regular_A, o.precision, vec_prec, x, y, N, nrhs, ae.real(),
+                              ae.imag(), be.real(), be.imag(), st)))
+      return rc;
+    for (int m = 0; m < M; ++m) {
+      const std::complex<double> am = mu_m[m] / k_m[m], bm = -k_m[m] / mu_m[m];
+      if ((rc = apply_block(ref(*A_int[m]), x, y, vec_prec, nrhs, am, bm))) return rc;
+      if (o.matrix_free &&
+          (rc = launch_rwg_free(*rwg, m, k_m[m].real(), k_m[m].imag(), o.q_regular_A, o.precision, vec_prec, x, y,
+                                N, nrhs, am.real(), am.imag(), bm.real(), bm.imag(), st)))
+        return rc;
+    }
     matvecs += (4LL * M * M + 4LL * M) * nrhs;
     return CAL_OK;
   }
@@ -578,6 +667,7 @@ void opts_default(cal_solve_opts* o) {
   o->maxit = 1000;
   o->refine = 3;
   o->rhs_mode = 0;
+  o->matrix_free = 0;
 }
 
 }  // namespace
@@ -851,14 +941,25 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   const int aprec = o.precision;  // assembly mode (CAL_FP32_ALL: float32 singular pairs)
   const int prec = aprec == CAL_FP64 ? CAL_FP64 : CAL_FP32;  // storage and vector precision
   P.o.precision = prec;
-  if ((rc = assemble_block(ctx->impl, 3, k_ext, 0.0, *P.rwg, -1, INFINITY, o.q_regular_A, o.q_singular_A,
-                           aprec, P.A_ext)))
-    return rc;
   P.A_int.resize(P.M);
-  for (int m = 0; m < P.M; ++m)
-    if ((rc = assemble_block(ctx->impl, 3, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, INFINITY,
-                             o.q_regular_A, o.q_singular_A, aprec, P.A_int[m])))
+  if (o.matrix_free) {
+    // only the touching-pair entries are stored; the rest is recomputed per application
+    if (o.q_regular_A != 6 && o.q_regular_A != 1) return fail(CAL_EINVAL, "q_regular must be 6 or 1");
+    if ((rc = assemble_singular_block(ctx->impl, k_ext, 0.0, *P.rwg, -1, o.q_singular_A, aprec, P.A_ext)))
       return rc;
+    for (int m = 0; m < P.M; ++m)
+      if ((rc = assemble_singular_block(ctx->impl, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, o.q_singular_A,
+                                        aprec, P.A_int[m])))
+        return rc;
+  } else {
+    if ((rc = assemble_block(ctx->impl, 3, k_ext, 0.0, *P.rwg, -1, INFINITY, o.q_regular_A, o.q_singular_A,
+                             aprec, P.A_ext)))
+      return rc;
+    for (int m = 0; m < P.M; ++m)
+      if ((rc = assemble_block(ctx->impl, 3, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, INFINITY,
+                               o.q_regular_A, o.q_singular_A, aprec, P.A_int[m])))
+        return rc;
+  }
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_A = now();
   int64_t bytes_A = 0, bytes_P = 0, bytes_G = 0;
@@ -931,6 +1032,35 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   return CAL_OK;
 }
 
+int cal_problem_apply(cal_ctx* ctx, cal_problem* prob, const double* x, double* y, int64_t nrhs) {
+  if (!ctx || !prob || !x || !y || nrhs < 1) return fail(CAL_EINVAL, "cal_problem_apply: bad argument");
+  if (ctx->impl.device != prob->device)
+    return fail(CAL_EINVAL, "cal_problem_apply: the problem lives on device %d", prob->device);
+  CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
+  Pmchwt& P = prob->P;
+  struct Bind {
+    Pmchwt& P;
+    ~Bind() { P.ctx = nullptr; }
+  } bind{P};
+  P.ctx = &ctx->impl;
+  cudaStream_t st = ctx->impl.stream;
+  const size_t bytes = (size_t)nrhs * 2 * P.N * sizeof(double2);
+  void *dx = nullptr, *dy = nullptr;
+  CAL_TRY_CUDA(dalloc(&dx, bytes, st));
+  if (dalloc(&dy, bytes, st) != cudaSuccess) {
+    dfree(dx, st);
+    return fail(CAL_ENOMEM, "cal_problem_apply: device allocation failed");
+  }
+  int rc = CAL_OK;
+  if (cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = fail(CAL_ECUDA, "copy failed");
+  if (!rc) rc = P.apply_A(dx, dy, CAL_FP64, (int)nrhs);
+  if (!rc && cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = fail(CAL_ECUDA, "copy failed");
+  dfree(dx, st);
+  dfree(dy, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = fail(CAL_ECUDA, "cal_problem_apply: stream failed");
+  return rc;
+}
+
 void cal_problem_destroy(cal_problem* prob) { delete prob; }  // its solves are synchronous
 
 int cal_problem_get_info(const cal_problem* prob, cal_problem_info* info) {
@@ -951,19 +1081,36 @@ int cal_problem_get_info(const cal_problem* prob, cal_problem_info* info) {
   return CAL_OK;
 }
 
-int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_t nrhs, cal_solution** out) {
+int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_t nrhs,
+                      const cal_solve_opts* solver, cal_solution** out) {
   if (!ctx || !prob || !inc || nrhs < 1 || !out) return fail(CAL_EINVAL, "cal_problem_solve: bad argument");
+  if (solver && (!(solver->tol > 0) || solver->restart < 1 || solver->maxit < 1 || solver->refine < 0))
+    return fail(CAL_EINVAL, "cal_problem_solve: bad tolerance/restart/maxit/refine");
+  if (solver && solver->rhs_mode != 0)
+    return fail(CAL_EINVAL, "solve: only the total-trace right-hand side is implemented");
   if (ctx->impl.device != prob->device)
     return fail(CAL_EINVAL, "cal_problem_solve: the problem lives on device %d", prob->device);
   for (int64_t q = 0; q < 6 * nrhs; ++q)
     if (!std::isfinite(inc[q])) return fail(CAL_EINVAL, "solve: non-finite incident field");
   CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
   Pmchwt& P = prob->P;
-  struct Bind {  // the problem runs on this call's context until it returns
+  // the problem runs on this call's context, with this call's solver
+  // settings, until it returns
+  struct Bind {
     Pmchwt& P;
-    ~Bind() { P.ctx = nullptr; }
-  } bind{P};
+    cal_solve_opts saved;
+    ~Bind() {
+      P.ctx = nullptr;
+      P.o = saved;
+    }
+  } bind{P, P.o};
   P.ctx = &ctx->impl;
+  if (solver) {
+    P.o.tol = solver->tol;
+    P.o.restart = solver->restart;
+    P.o.maxit = solver->maxit;
+    P.o.refine = solver->refine;
+  }
   const cal_solve_opts& o = P.o;
   const int prec = o.precision;
   cudaStream_t st = ctx->impl.stream;
@@ -1112,7 +1259,7 @@ int cal_pmchwt_solve(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double* e
   cal_problem* prob = nullptr;
   int rc = cal_problem_create(ctx, mesh, k_ext, eps_r, mu_r, opts, &prob);
   if (rc) return rc;
-  rc = cal_problem_solve(ctx, prob, inc, nrhs, out);
+  rc = cal_problem_solve(ctx, prob, inc, nrhs, nullptr, out);
   cal_problem_destroy(prob);
   return rc;
 }
@@ -1152,6 +1299,10 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
 }
 
 void cal_solution_destroy(cal_solution* sol) { delete sol; }
+
+int cal_check_elementary(int64_t n, double lo, double hi, double* err_cis, double* err_exp) {
+  return cal::check_elementary(n, lo, hi, err_cis, err_exp);
+}
 
 int64_t cal_kernel_launches(void) { return cal::launches(); }
 

@@ -22,6 +22,7 @@
 
 #include <cmath>
 #include <cstdint>
+#include <cstring>
 
 #include "internal.h"
 
@@ -452,6 +453,187 @@ __global__ void __launch_bounds__(256) rwg_regular_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// A8: matrix-free application of the regular part of a PMCHWT block. Every
+// non-touching pair t1 < t2 forms its 3 x 3 local S and C entries exactly as
+// the stored assembly does and applies them at once,
+//   y1 += C x1 + alpha S x2,  y2 += C x2 + beta S x1,
+// at the rows of t1 and, mirrored (both operators are symmetric), at the rows
+// of t2. A 16 x 16 tile of pairs is reduced with warp shuffles and shared
+// memory and added to y with one atomic per (triangle, slot, half, rhs).
+// Touching pairs are left to the stored sparse singular block.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void load_c(const float2* p, float& re, float& im) { const float2 v = *p; re = v.x; im = v.y; }
+__device__ __forceinline__ void load_c(const float2* p, double& re, double& im) { const float2 v = *p; re = v.x; im = v.y; }
+__device__ __forceinline__ void load_c(const double2* p, float& re, float& im) { const double2 v = *p; re = (float)v.x; im = (float)v.y; }
+__device__ __forceinline__ void load_c(const double2* p, double& re, double& im) { const double2 v = *p; re = v.x; im = v.y; }
+__device__ __forceinline__ void atomic_add_v(float2* p, float re, float im) { atomicAdd(p, make_float2(re, im)); }
+__device__ __forceinline__ void atomic_add_v(double2* p, float re, float im) {
+  atomicAdd(&p->x, (double)re);
+  atomicAdd(&p->y, (double)im);
+}
+__device__ __forceinline__ void atomic_add_v(double2* p, double re, double im) {
+  atomicAdd(&p->x, re);
+  atomicAdd(&p->y, im);
+}
+
+// AT: arithmetic of the application (float64 for float64 vectors, so that a
+// refinement residual gets exact products of the float32 entries)
+template <typename R, int NREG, typename VT, typename AT>
+__global__ void __launch_bounds__(256) rwg_free_kernel(
+    const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
+    const R* __restrict__ slot_sw, int64_t t0, int64_t ntr, R kr, R ki, R mikr, R miki, R c4r, R c4i,
+    Rules rl, const VT* __restrict__ x, VT* __restrict__ y, int64_t n, int nrhs, AT ar, AT ai, AT br, AT bi) {
+  using TRI = typename TriOf<R>::T;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  // acc[((((side * 16 + t) * 3 + slot) * 2 + half) * nrhs + rhs) * 2 + (re, im)]
+  AT* acc = reinterpret_cast<AT*>(smem_raw);
+  const int tbi = blockIdx.y, tbj = blockIdx.x;
+  if (tbi > tbj) return;  // the whole block: the tile lies below the diagonal
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+  const int nacc = 2 * 16 * 3 * 2 * nrhs * 2;
+  for (int q = tid; q < nacc; q += 256) acc[q] = AT(0);
+  __syncthreads();
+  const int64_t i1 = (int64_t)tbi * 16 + ty, i2 = (int64_t)tbj * 16 + tx;
+  bool active = i1 < ntr && i2 < ntr && i1 < i2;
+  const int64_t t1 = t0 + (active ? i1 : 0), t2 = t0 + (active ? i2 : 0);
+  AT Sr[9], Si[9], Cr[9], Ci[9];
+  int ea[3], eb[3];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Sr[q] = Si[q] = Cr[q] = Ci[q] = AT(0);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) ea[a] = eb[a] = 0;
+  if (active) {
+    const TRI A = tri[t1];
+    const TRI B = tri[t2];
+    active = !touching(A, B);
+    if (active) {
+      V3<R> xi[NREG], eta[NREG];
+      R wx[NREG], wy[NREG];
+      load_points<NREG>(A, rl, xi, wx);
+      load_points<NREG>(B, rl, eta, wy);
+      const V3<R> D = centroid_delta(A, B);
+      Mom<R> m;
+      regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, true, m);
+      R pc[36];
+      pair_coeffs(m, D, pc);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        ea[a] = slot_edge[3 * t1 + a];
+        eb[a] = slot_edge[3 * t2 + a];
+        const R sa = slot_sw[12 * t1 + 4 * a];
+        const V3<R> wa = {slot_sw[12 * t1 + 4 * a + 1], slot_sw[12 * t1 + 4 * a + 2], slot_sw[12 * t1 + 4 * a + 3]};
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const R sb = slot_sw[12 * t2 + 4 * b];
+          const V3<R> wb = {slot_sw[12 * t2 + 4 * b + 1], slot_sw[12 * t2 + 4 * b + 2],
+                            slot_sw[12 * t2 + 4 * b + 3]};
+          R er = 0, ei = 0, fr = 0, fi = 0;
+          entry_from_pc(pc, sa, wa, sb, wb, mikr, miki, c4r, c4i, true, true, er, ei, fr, fi);
+          Sr[3 * a + b] = er; Si[3 * a + b] = ei; Cr[3 * a + b] = fr; Ci[3 * a + b] = fi;
+        }
+      }
+    }
+  }
+  for (int r = 0; r < nrhs; ++r) {
+    const VT* x1 = x + (int64_t)r * 2 * n;
+    const VT* x2 = x1 + n;
+    AT u1r[3], u1i[3], u2r[3], u2i[3], v1r[3], v1i[3], v2r[3], v2i[3];  // x at t1 (u) and t2 (v)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      u1r[a] = u1i[a] = u2r[a] = u2i[a] = v1r[a] = v1i[a] = v2r[a] = v2i[a] = AT(0);
+      if (active) {
+        load_c(x1 + ea[a], u1r[a], u1i[a]);
+        load_c(x2 + ea[a], u2r[a], u2i[a]);
+        load_c(x1 + eb[a], v1r[a], v1i[a]);
+        load_c(x2 + eb[a], v2r[a], v2i[a]);
+      }
+    }
+    // row side (t1): 3 slots x 2 halves, complex; col side (t2) the same
+    AT row[12], col[12];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      AT c1r = 0, c1i = 0, c2r = 0, c2i = 0, s1r = 0, s1i = 0, s2r = 0, s2i = 0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int k = 3 * a + b;
+        c1r += Cr[k] * v1r[b] - Ci[k] * v1i[b]; c1i += Cr[k] * v1i[b] + Ci[k] * v1r[b];
+        c2r += Cr[k] * v2r[b] - Ci[k] * v2i[b]; c2i += Cr[k] * v2i[b] + Ci[k] * v2r[b];
+        s2r += Sr[k] * v2r[b] - Si[k] * v2i[b]; s2i += Sr[k] * v2i[b] + Si[k] * v2r[b];
+        s1r += Sr[k] * v1r[b] - Si[k] * v1i[b]; s1i += Sr[k] * v1i[b] + Si[k] * v1r[b];
+      }
+      row[4 * a + 0] = c1r + ar * s2r - ai * s2i;
+      row[4 * a + 1] = c1i + ar * s2i + ai * s2r;
+      row[4 * a + 2] = c2r + br * s1r - bi * s1i;
+      row[4 * a + 3] = c2i + br * s1i + bi * s1r;
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      AT c1r = 0, c1i = 0, c2r = 0, c2i = 0, s1r = 0, s1i = 0, s2r = 0, s2i = 0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int k = 3 * a + b;
+        c1r += Cr[k] * u1r[a] - Ci[k] * u1i[a]; c1i += Cr[k] * u1i[a] + Ci[k] * u1r[a];
+        c2r += Cr[k] * u2r[a] - Ci[k] * u2i[a]; c2i += Cr[k] * u2i[a] + Ci[k] * u2r[a];
+        s2r += Sr[k] * u2r[a] - Si[k] * u2i[a]; s2i += Sr[k] * u2i[a] + Si[k] * u2r[a];
+        s1r += Sr[k] * u1r[a] - Si[k] * u1i[a]; s1i += Sr[k] * u1i[a] + Si[k] * u1r[a];
+      }
+      col[4 * b + 0] = c1r + ar * s2r - ai * s2i;
+      col[4 * b + 1] = c1i + ar * s2i + ai * s2r;
+      col[4 * b + 2] = c2r + br * s1r - bi * s1i;
+      col[4 * b + 3] = c2i + br * s1i + bi * s1r;
+    }
+    // rows share t1 across the 16 lanes of a half warp; columns share t2
+    // across the two half warps
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      AT v = row[q];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      row[q] = v;
+      col[q] += __shfl_xor_sync(0xffffffffu, col[q], 16);
+    }
+    if (tx == 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          AT* o = acc + ((((0 * 16 + ty) * 3 + a) * 2 + h) * nrhs + r) * 2;
+          o[0] += row[4 * a + 2 * h];
+          o[1] += row[4 * a + 2 * h + 1];
+        }
+    }
+    if ((ty & 1) == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          AT* o = acc + ((((1 * 16 + tx) * 3 + b) * 2 + h) * nrhs + r) * 2;
+          atomicAdd(o, col[4 * b + 2 * h]);
+          atomicAdd(o + 1, col[4 * b + 2 * h + 1]);
+        }
+    }
+  }
+  __syncthreads();
+  // flush: one atomic per (side, triangle, slot, half, rhs)
+  for (int q = tid; q < nacc / 2; q += 256) {
+    const int r = q % nrhs;
+    int rest = q / nrhs;
+    const int h = rest % 2;
+    rest /= 2;
+    const int slot = rest % 3;
+    rest /= 3;
+    const int t = rest % 16, side = rest / 16;
+    const int64_t tt = (int64_t)(side == 0 ? tbi : tbj) * 16 + t;
+    if (tt >= ntr) continue;
+    const AT vr = acc[2 * q], vi = acc[2 * q + 1];
+    if (vr == AT(0) && vi == AT(0)) continue;
+    const int e = slot_edge[3 * (t0 + tt) + slot];
+    if (e < 0) continue;
+    atomic_add_v(y + (int64_t)r * 2 * n + (int64_t)h * n + e, vr, vi);
+  }
+}
+
+// ---------------------------------------------------------------------------
 // A5: BC assembly by dual-cell tiles (v, w), v <= w. Stage 1: pair
 // coefficients of every (tau1 in D(v), tau2 in D(w)) into shared memory;
 // stage 2: contract the trial side per (tau1, trial slot); stage 3: contract
@@ -493,7 +675,9 @@ __global__ void __launch_bounds__(160, sizeof(R) == 4 ? 3 : 2) bc_tile_kernel(
       ((((size_t)PS * 36 + (size_t)chunk * nslot * 18 + (size_t)nslot * nslot * 4) * sizeof(R) + 15) / 16) * 16;
   P4<R>* ptsA = reinterpret_cast<P4<R>*>(smem_raw + staged_off);     // [max_cell][NREG]
   P4<R>* ptsB = ptsA + (size_t)max_cell * NREG;                      // [max_cell][NREG]
-  Cent<R>* cA = reinterpret_cast<Cent<R>*>(ptsB + (size_t)max_cell * NREG);
+  P4<R>* swA = ptsB + (size_t)max_cell * NREG;                       // [max_cell][nslot] (s, w)
+  P4<R>* swB = swA + (size_t)max_cell * nslot;                       // [max_cell][nslot]
+  Cent<R>* cA = reinterpret_cast<Cent<R>*>(swB + (size_t)max_cell * nslot);
   Cent<R>* cB = cA + max_cell;
   int* vidA = reinterpret_cast<int*>(cB + max_cell);                // [max_cell][3]
   int* vidB = vidA + 3 * max_cell;
@@ -526,6 +710,11 @@ __global__ void __launch_bounds__(160, sizeof(R) == 4 ? 3 : 2) bc_tile_kernel(
         (first ? cA : cB)[t].set(T);
         int* vd = (first ? vidA : vidB) + 3 * t;
         vd[0] = T.vid[0]; vd[1] = T.vid[1]; vd[2] = T.vid[2];
+        // slot coefficients (sigma, w) of the triangle
+        const int tau = cell_tri[(first ? b1 : b2) + t];
+        const P4<R>* src = reinterpret_cast<const P4<R>*>(slot_sw) + (size_t)tau * nslot;
+        P4<R>* dst = (first ? swA : swB) + (size_t)t * nslot;
+        for (int sl = 0; sl < nslot; ++sl) dst[sl] = src[sl];
       }
     }
     // number of valid slots of each cell
@@ -563,27 +752,41 @@ __global__ void __launch_bounds__(160, sizeof(R) == 4 ? 3 : 2) bc_tile_kernel(
         for (int q = 0; q < 36; ++q) pc[q * PS] = tmp[q];
       }
       __syncthreads();
-      // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side factors
-      for (int q = threadIdx.x; q < nc * ns2; q += blockDim.x) {
-        const int i1 = q / ns2, sb_i = q % ns2;
-        R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0, AC_r = 0, AC_i = 0;
-        V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0}, WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
-        for (int i2 = 0; i2 < n2; ++i2) {
-          const int tau2 = cell_tri[b2 + i2];
-          const R* sw = slot_sw + ((size_t)tau2 * nslot + sb_i) * 4;
-          const R sb = sw[0];
-          const V3<R> wb = {sw[1], sw[2], sw[3]};
-          const R* q0 = pcs + (i1 * n2 + i2);
-#define PC(c) q0[(c) * PS]
-          if (wantS) {
+      // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side
+      // factors; the S and C halves are separate work items (S items first,
+      // so that a warp takes one branch)
+      const int nS2 = wantS ? nc * ns2 : 0, nC2 = wantC ? nc * ns2 : 0;
+      for (int q = threadIdx.x; q < nS2 + nC2; q += blockDim.x) {
+        const bool isS = q < nS2;
+        const int it = isS ? q : q - nS2;
+        const int i1 = it / ns2, sb_i = it % ns2;
+        const R* q1 = pcs + i1 * n2;
+        R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
+#define PC(c) q1[i2 + (c) * PS]
+        if (isS) {
+          R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0;
+          V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0};
+          for (int i2 = 0; i2 < n2; ++i2) {
+            const P4<R> u = swB[i2 * nslot + sb_i];
+            const R sb = u.x;
+            const V3<R> wb = {u.y, u.z, u.w};
+            const R g0r = PC(0), g0i = PC(1);
             AS_r += sb * PC(14) + wb.x * PC(2) + wb.y * PC(3) + wb.z * PC(4);
             AS_i += sb * PC(15) + wb.x * PC(5) + wb.y * PC(6) + wb.z * PC(7);
-            BS_r += sb * PC(0);
-            BS_i += sb * PC(1);
-            WS_r.x += sb * PC(8) + wb.x * PC(0); WS_r.y += sb * PC(9) + wb.y * PC(0); WS_r.z += sb * PC(10) + wb.z * PC(0);
-            WS_i.x += sb * PC(11) + wb.x * PC(1); WS_i.y += sb * PC(12) + wb.y * PC(1); WS_i.z += sb * PC(13) + wb.z * PC(1);
+            BS_r += sb * g0r;
+            BS_i += sb * g0i;
+            WS_r.x += sb * PC(8) + wb.x * g0r; WS_r.y += sb * PC(9) + wb.y * g0r; WS_r.z += sb * PC(10) + wb.z * g0r;
+            WS_i.x += sb * PC(11) + wb.x * g0i; WS_i.y += sb * PC(12) + wb.y * g0i; WS_i.z += sb * PC(13) + wb.z * g0i;
           }
-          if (wantC) {
+          o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
+          o[4] = WS_r.x; o[5] = WS_r.y; o[6] = WS_r.z; o[7] = WS_i.x; o[8] = WS_i.y; o[9] = WS_i.z;
+        } else {
+          R AC_r = 0, AC_i = 0;
+          V3<R> WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
+          for (int i2 = 0; i2 < n2; ++i2) {
+            const P4<R> u = swB[i2 * nslot + sb_i];
+            const R sb = u.x;
+            const V3<R> wb = {u.y, u.z, u.w};
             AC_r += sb * PC(16) + wb.x * PC(18) + wb.y * PC(19) + wb.z * PC(20);
             AC_i += sb * PC(17) + wb.x * PC(21) + wb.y * PC(22) + wb.z * PC(23);
             const V3<R> Vr = {PC(30), PC(31), PC(32)}, Vi = {PC(33), PC(34), PC(35)};
@@ -591,39 +794,38 @@ __global__ void __launch_bounds__(160, sizeof(R) == 4 ? 3 : 2) bc_tile_kernel(
             WC_r.x += sb * PC(24) + cr.x; WC_r.y += sb * PC(25) + cr.y; WC_r.z += sb * PC(26) + cr.z;
             WC_i.x += sb * PC(27) + ci.x; WC_i.y += sb * PC(28) + ci.y; WC_i.z += sb * PC(29) + ci.z;
           }
-#undef PC
+          o[10] = AC_r; o[11] = AC_i;
+          o[12] = WC_r.x; o[13] = WC_r.y; o[14] = WC_r.z; o[15] = WC_i.x; o[16] = WC_i.y; o[17] = WC_i.z;
         }
-        R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
-        o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
-        o[4] = WS_r.x; o[5] = WS_r.y; o[6] = WS_r.z; o[7] = WS_i.x; o[8] = WS_i.y; o[9] = WS_i.z;
-        o[10] = AC_r; o[11] = AC_i;
-        o[12] = WC_r.x; o[13] = WC_r.y; o[14] = WC_r.z; o[15] = WC_i.x; o[16] = WC_i.y; o[17] = WC_i.z;
+#undef PC
       }
       __syncthreads();
       // stage 3: per (test slot a, trial slot b), sum over the chunk's tau1
-      for (int q = threadIdx.x; q < ns1 * ns2; q += blockDim.x) {
-        const int sa_i = q / ns2, sb_i = q % ns2;
-        R Sr = 0, Si = 0, Cr = 0, Ci = 0;
+      const int nS3 = wantS ? ns1 * ns2 : 0, nC3 = wantC ? ns1 * ns2 : 0;
+      for (int q = threadIdx.x; q < nS3 + nC3; q += blockDim.x) {
+        const bool isS = q < nS3;
+        const int it = isS ? q : q - nS3;
+        const int sa_i = it / ns2, sb_i = it % ns2;
+        R vr = 0, vi = 0;
         for (int i1 = 0; i1 < nc; ++i1) {
-          const int tau1 = cell_tri[b1 + c0 + i1];
-          const R* sw = slot_sw + ((size_t)tau1 * nslot + sa_i) * 4;
-          const R sa = sw[0];
-          const V3<R> wa = {sw[1], sw[2], sw[3]};
+          const P4<R> u = swA[(c0 + i1) * nslot + sa_i];
+          const R sa = u.x;
+          const V3<R> wa = {u.y, u.z, u.w};
           const R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
-          if (wantS) {
+          if (isS) {
             // sa (mik AS + c4 BS) + mik (wa . WS)
             const R pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
             const R pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
-            Sr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
-            Si += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
-          }
-          if (wantC) {
-            Cr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
-            Ci += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
+            vr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
+            vi += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
+          } else {
+            vr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
+            vi += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
           }
         }
-        R* a4 = acc + (size_t)q * 4;
-        a4[0] += Sr; a4[1] += Si; a4[2] += Cr; a4[3] += Ci;
+        R* a4 = acc + (size_t)it * 4 + (isS ? 0 : 2);
+        a4[0] += vr;
+        a4[1] += vi;
       }
       __syncthreads();
     }
@@ -823,6 +1025,122 @@ __global__ void __launch_bounds__(128) singular_kernel_f32(
   }
 }
 
+// ---------------------------------------------------------------------------
+// Double-precision e^{i theta} and e^{z} for the singular-pair kernel. Argument
+// reduction after Cody and Waite (pi/2 split into three parts and ln 2 into
+// two, each leading part short enough that n * part is exact), then truncated
+// Taylor series on the reduced interval: |t| <= pi/4 with terms up to t^17
+// (the first omitted term is below 1e-19) and |t| <= ln(2)/2 with terms up to
+// t^13 (below 5e-18). Arguments outside the reduction's range go to the CUDA
+// library. The split constants are the binary expansions of pi/2 and ln 2.
+// ---------------------------------------------------------------------------
+namespace dm {
+constexpr double PIO2_A = 1.5707963267341256, PIO2_B = 6.077100506303966e-11, PIO2_C = 2.0222662487959506e-21;
+constexpr double TWO_OVER_PI = 0.6366197723675814;
+constexpr double LN2_A = 0.6931471805598903, LN2_B = 5.497923018708371e-14;
+constexpr double LOG2E = 1.4426950408889634;
+}  // namespace dm
+
+__device__ __forceinline__ void cis_f64(double th, double& c, double& s) {
+  if (!(fabs(th) < 1.0e6)) {
+    sincos(th, &s, &c);
+    return;
+  }
+  const double n = rint(th * dm::TWO_OVER_PI);
+  double t = fma(-n, dm::PIO2_A, th);
+  t = fma(-n, dm::PIO2_B, t);
+  t = fma(-n, dm::PIO2_C, t);
+  const double u = -t * t;
+  // cos t = sum_k u^k / (2k)!,  sin t = t sum_k u^k / (2k+1)!,  k = 0..8
+  double pc = 1.0 / 20922789888000.0;
+  pc = fma(pc, u, 1.0 / 87178291200.0);
+  pc = fma(pc, u, 1.0 / 479001600.0);
+  pc = fma(pc, u, 1.0 / 3628800.0);
+  pc = fma(pc, u, 1.0 / 40320.0);
+  pc = fma(pc, u, 1.0 / 720.0);
+  pc = fma(pc, u, 1.0 / 24.0);
+  pc = fma(pc, u, 0.5);
+  pc = fma(pc, u, 1.0);
+  double ps = 1.0 / 355687428096000.0;
+  ps = fma(ps, u, 1.0 / 1307674368000.0);
+  ps = fma(ps, u, 1.0 / 6227020800.0);
+  ps = fma(ps, u, 1.0 / 39916800.0);
+  ps = fma(ps, u, 1.0 / 362880.0);
+  ps = fma(ps, u, 1.0 / 5040.0);
+  ps = fma(ps, u, 1.0 / 120.0);
+  ps = fma(ps, u, 1.0 / 6.0);
+  ps = fma(ps, u, 1.0);
+  ps *= t;
+  // e^{i theta} = e^{i t} i^q
+  const int q = (int)n & 3;
+  c = q == 0 ? pc : (q == 1 ? -ps : (q == 2 ? -pc : ps));
+  s = q == 0 ? ps : (q == 1 ? pc : (q == 2 ? -ps : -pc));
+}
+
+__device__ __forceinline__ double exp_f64(double z) {
+  if (!(fabs(z) < 700.0)) return exp(z);
+  const double n = rint(z * dm::LOG2E);
+  double t = fma(-n, dm::LN2_A, z);
+  t = fma(-n, dm::LN2_B, t);
+  double p = 1.0 / 6227020800.0;
+  p = fma(p, t, 1.0 / 479001600.0);
+  p = fma(p, t, 1.0 / 39916800.0);
+  p = fma(p, t, 1.0 / 3628800.0);
+  p = fma(p, t, 1.0 / 362880.0);
+  p = fma(p, t, 1.0 / 40320.0);
+  p = fma(p, t, 1.0 / 5040.0);
+  p = fma(p, t, 1.0 / 720.0);
+  p = fma(p, t, 1.0 / 120.0);
+  p = fma(p, t, 1.0 / 24.0);
+  p = fma(p, t, 1.0 / 6.0);
+  p = fma(p, t, 0.5);
+  p = fma(p, t, 1.0);
+  p = fma(p, t, 1.0);
+  return p * __longlong_as_double((long long)((int)n + 1023) << 52);
+}
+
+// max |cis_f64 - (cos, sin)| and max relative |exp_f64 - exp| over n points
+// spread evenly on [lo, hi] (the library functions as the yardstick)
+__global__ void elementary_check_kernel(int64_t n, double lo, double hi, unsigned long long* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double x = lo + (hi - lo) * ((double)i / (double)(n > 1 ? n - 1 : 1));
+  double c, s, c0, s0;
+  cis_f64(x, c, s);
+  sincos(x, &s0, &c0);
+  const double ec = fmax(fabs(c - c0), fabs(s - s0));
+  const double e0 = exp(-fabs(x));
+  const double ee = e0 > 0 ? fabs(exp_f64(-fabs(x)) - e0) / e0 : 0.0;
+  // non-negative doubles order like their bit patterns
+  atomicMax(err, (unsigned long long)__double_as_longlong(ec));
+  atomicMax(err + 1, (unsigned long long)__double_as_longlong(ee));
+}
+
+int check_elementary(int64_t n, double lo, double hi, double* err_cis, double* err_exp) {
+  if (n < 1 || !(hi >= lo) || !err_cis || !err_exp) return fail(CAL_EINVAL, "elementary check: bad arguments");
+  unsigned long long* d = nullptr;
+  CAL_TRY_CUDA(cudaMalloc((void**)&d, 2 * sizeof(unsigned long long)));
+  cudaMemset(d, 0, 2 * sizeof(unsigned long long));
+  elementary_check_kernel<<<(unsigned)((n + 255) / 256), 256>>>(n, lo, hi, d);
+  note_launch();
+  unsigned long long h[2] = {0, 0};
+  const cudaError_t e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  CAL_TRY_CUDA(e);
+  double v[2];
+  std::memcpy(v, h, sizeof(v));
+  *err_cis = v[0];
+  *err_exp = v[1];
+  return CAL_OK;
+}
+
+// Every Sauter–Schwab map is x = xi f(e), y = xi g(e) in the reference
+// coordinates of the two triangles (shared vertex at the origin of both), and
+// its jacobian is xi^3 J(e). So x - y = xi rho(e), the 1/r of G cancels two
+// powers of xi, and a basis monomial m(x, y) of degree d carries xi^d. For
+// each (region, e1, e2, e3) a lane therefore forms rho and the monomials once
+// and sums the kernel over the Gauss nodes of xi in three radial sums (xi^0,
+// xi^1, xi^2); the same quadrature points and weights as the direct form.
 template <typename RO>
 __global__ void __launch_bounds__(128) singular_kernel(
     const TriD* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
@@ -837,84 +1155,144 @@ __global__ void __launch_bounds__(128) singular_kernel(
   const TriD B = tri[sp.t2];
   const int cls = sp.cls;
   const bool doC = wantC && cls != 3;  // flat identical panels: C vanishes
-  // parametrisation corners relative to each centroid
+  // parametrisation corners relative to each centroid, shared vertices first
   V3<double> Q1[3], Q2[3];
   for (int a = 0; a < 3; ++a) {
     Q1[a] = {A.off[sp.o1[a]][0], A.off[sp.o1[a]][1], A.off[sp.o1[a]][2]};
     Q2[a] = {B.off[sp.o2[a]][0], B.off[sp.o2[a]][1], B.off[sp.o2[a]][2]};
   }
+  const V3<double> ea = {Q1[1].x - Q1[0].x, Q1[1].y - Q1[0].y, Q1[1].z - Q1[0].z};
+  const V3<double> eb = {Q1[2].x - Q1[1].x, Q1[2].y - Q1[1].y, Q1[2].z - Q1[1].z};
+  const V3<double> ec = {Q2[1].x - Q2[0].x, Q2[1].y - Q2[0].y, Q2[1].z - Q2[0].z};
+  const V3<double> ed = {Q2[2].x - Q2[1].x, Q2[2].y - Q2[1].y, Q2[2].z - Q2[1].z};
   const V3<double> D = {A.c[0] - B.c[0], A.c[1] - B.c[1], A.c[2] - B.c[2]};
   const double scale = 4.0 * A.area * B.area;
   const int ng = rl.ng, nreg = (cls == 3 ? 6 : (cls == 2 ? 5 : 2));
-  const int ng2 = ng * ng, ng4 = ng2 * ng2;
-  Mom<double> m;
-  m.zero();
-  for (int idx = lane; idx < nreg * ng4; idx += 32) {
-    const int r = idx / ng4;
-    int rem = idx - r * ng4;
-    const int a0 = rem / (ng2 * ng);
-    rem -= a0 * ng2 * ng;
+  const int ng2 = ng * ng, ng3 = ng2 * ng;
+  constexpr double INV_4PI = 0.25 / 3.14159265358979323846;
+  // monomial moments sum K w m(x, y), m in {1, x0, x1, y0, y1, x0 y0, x0 y1,
+  // x1 y0, x1 y1} (reference coordinates), K = G and g; (re, im) pairs
+  double MG[18], Mg[18];
+#pragma unroll
+  for (int q = 0; q < 18; ++q) MG[q] = Mg[q] = 0.0;
+  for (int idx = lane; idx < nreg * ng3; idx += 32) {
+    const int r = idx / ng3;
+    int rem = idx - r * ng3;
     const int a1 = rem / ng2;
     rem -= a1 * ng2;
     const int a2 = rem / ng, a3 = rem - a2 * ng;
     double xh[2], yh[2], jac;
-    ss_map(cls, r, rl.gx[a0], rl.gx[a1], rl.gx[a2], rl.gx[a3], xh, yh, jac);
-    const double w = rl.gw[a0] * rl.gw[a1] * rl.gw[a2] * rl.gw[a3] * jac * scale;
-    const V3<double> x = {Q1[0].x + xh[0] * (Q1[1].x - Q1[0].x) + xh[1] * (Q1[2].x - Q1[1].x),
-                          Q1[0].y + xh[0] * (Q1[1].y - Q1[0].y) + xh[1] * (Q1[2].y - Q1[1].y),
-                          Q1[0].z + xh[0] * (Q1[1].z - Q1[0].z) + xh[1] * (Q1[2].z - Q1[1].z)};
-    const V3<double> y = {Q2[0].x + yh[0] * (Q2[1].x - Q2[0].x) + yh[1] * (Q2[2].x - Q2[1].x),
-                          Q2[0].y + yh[0] * (Q2[1].y - Q2[0].y) + yh[1] * (Q2[2].y - Q2[1].y),
-                          Q2[0].z + yh[0] * (Q2[1].z - Q2[0].z) + yh[1] * (Q2[2].z - Q2[1].z)};
-    const double dx = D.x + x.x - y.x, dy = D.y + x.y - y.y, dz = D.z + x.z - y.z;
-    double Gr, Gi, gr, gi;
-    green(dx * dx + dy * dy + dz * dz, kr, ki, Gr, Gi, gr, gi);
-    Gr *= w; Gi *= w; gr *= w; gi *= w;
-    m.G0r += Gr; m.G0i += Gi;
-    m.Gxr.x += Gr * x.x; m.Gxr.y += Gr * x.y; m.Gxr.z += Gr * x.z;
-    m.Gxi.x += Gi * x.x; m.Gxi.y += Gi * x.y; m.Gxi.z += Gi * x.z;
-    m.Gyr.x += Gr * y.x; m.Gyr.y += Gr * y.y; m.Gyr.z += Gr * y.z;
-    m.Gyi.x += Gi * y.x; m.Gyi.y += Gi * y.y; m.Gyi.z += Gi * y.z;
-    const double xy = dot3(x, y);
-    m.Gxyr += Gr * xy; m.Gxyi += Gi * xy;
-    if (doC) {
-      const V3<double> xy3 = cross3(x, y);
-      m.g0r += gr; m.g0i += gi;
-      m.gxr.x += gr * x.x; m.gxr.y += gr * x.y; m.gxr.z += gr * x.z;
-      m.gxi.x += gi * x.x; m.gxi.y += gi * x.y; m.gxi.z += gi * x.z;
-      m.gyr.x += gr * y.x; m.gyr.y += gr * y.y; m.gyr.z += gr * y.z;
-      m.gyi.x += gi * y.x; m.gyi.y += gi * y.y; m.gyi.z += gi * y.z;
-      m.gxyr.x += gr * xy3.x; m.gxyr.y += gr * xy3.y; m.gxyr.z += gr * xy3.z;
-      m.gxyi.x += gi * xy3.x; m.gxyi.y += gi * xy3.y; m.gxyi.z += gi * xy3.z;
+    ss_map(cls, r, 1.0, rl.gx[a1], rl.gx[a2], rl.gx[a3], xh, yh, jac);
+    // x - y at xi = 1; the shared vertex cancels exactly
+    const V3<double> dr = {xh[0] * ea.x + xh[1] * eb.x - yh[0] * ec.x - yh[1] * ed.x,
+                           xh[0] * ea.y + xh[1] * eb.y - yh[0] * ec.y - yh[1] * ed.y,
+                           xh[0] * ea.z + xh[1] * eb.z - yh[0] * ec.z - yh[1] * ed.z};
+    const double rho = sqrt(dot3(dr, dr));
+    const double irho = 1.0 / rho;
+    const double We = rl.gw[a1] * rl.gw[a2] * rl.gw[a3] * jac * scale;
+    double SG[6] = {0, 0, 0, 0, 0, 0}, Sg[6] = {0, 0, 0, 0, 0, 0};  // (re, im) for xi^0, xi^1, xi^2
+    for (int j = 0; j < ng; ++j) {
+      const double xi = rl.gx[j], wj = rl.gw[j];
+      const double rr = xi * rho;
+      double cth, sth;
+      cis_f64(kr * rr, cth, sth);
+      if (ki != 0.0) {
+        const double e = exp_f64(-ki * rr);
+        cth *= e;
+        sth *= e;
+      }
+      // G w = e^{ikr} w_j xi^2 We / (4 pi rho)
+      const double tg = wj * xi * xi;
+      const double Tr = cth * tg, Ti = sth * tg;
+      SG[0] += Tr; SG[1] += Ti;
+      SG[2] = fma(Tr, xi, SG[2]); SG[3] = fma(Ti, xi, SG[3]);
+      SG[4] = fma(Tr, xi * xi, SG[4]); SG[5] = fma(Ti, xi * xi, SG[5]);
+      if (doC) {
+        // g w = (ikr - 1) e^{ikr} w_j We / (4 pi rho^3)
+        const double fr = -ki * rr - 1.0, fi = kr * rr;
+        const double Ur = (fr * cth - fi * sth) * wj, Ui = (fr * sth + fi * cth) * wj;
+        Sg[0] += Ur; Sg[1] += Ui;
+        Sg[2] = fma(Ur, xi, Sg[2]); Sg[3] = fma(Ui, xi, Sg[3]);
+        Sg[4] = fma(Ur, xi * xi, Sg[4]); Sg[5] = fma(Ui, xi * xi, Sg[5]);
+      }
+    }
+    const double cG = We * irho * INV_4PI, cg = cG * irho * irho;
+    const double mono[9] = {1.0, xh[0], xh[1], yh[0], yh[1], xh[0] * yh[0], xh[0] * yh[1], xh[1] * yh[0],
+                            xh[1] * yh[1]};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int d = k == 0 ? 0 : (k < 5 ? 2 : 4);  // radial sum of the monomial's degree
+      const double fG = cG * mono[k], fg = cg * mono[k];
+      MG[2 * k] = fma(fG, SG[d], MG[2 * k]);
+      MG[2 * k + 1] = fma(fG, SG[d + 1], MG[2 * k + 1]);
+      if (doC) {
+        Mg[2 * k] = fma(fg, Sg[d], Mg[2 * k]);
+        Mg[2 * k + 1] = fma(fg, Sg[d + 1], Mg[2 * k + 1]);
+      }
     }
   }
-  // warp reduction of the 36 moment reals
-  double* mv = reinterpret_cast<double*>(&m);
-  constexpr int NM = sizeof(Mom<double>) / sizeof(double);
 #pragma unroll
-  for (int q = 0; q < NM; ++q) {
-    double v = mv[q];
+  for (int q = 0; q < 18; ++q) {
+    double v = MG[q], u = Mg[q];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    mv[q] = v;
+    for (int o = 16; o > 0; o >>= 1) {
+      v += __shfl_xor_sync(0xffffffffu, v, o);
+      u += __shfl_xor_sync(0xffffffffu, u, o);
+    }
+    MG[q] = v;
+    Mg[q] = u;
+  }
+  // back to the centroid-relative moments: x = q0 + x0 a + x1 b, y = p0 + y0 c + y1 d
+  const V3<double> q0 = Q1[0], p0 = Q2[0];
+  const V3<double> vx[3] = {q0, ea, eb};  // factors of 1, x0, x1
+  const V3<double> vy[3] = {p0, ec, ed};  // factors of 1, y0, y1
+  // monomial index of (i, j): i, j in {0: 1, 1: first, 2: second}
+  auto mix = [](int i, int j) { return i == 0 ? (j == 0 ? 0 : 2 + j) : (j == 0 ? i : 2 * i + j + 2); };
+  Mom<double> m;
+  m.zero();
+  for (int h = 0; h < 2; ++h) {  // re, im
+    double G0 = MG[h], g0 = Mg[h];
+    V3<double> Gx = {0, 0, 0}, Gy = {0, 0, 0}, gx = {0, 0, 0}, gy = {0, 0, 0}, gxy = {0, 0, 0};
+    double Gxy = 0.0;
+    for (int i = 0; i < 3; ++i) {
+      const double Mxi = MG[2 * mix(i, 0) + h], mxi = Mg[2 * mix(i, 0) + h];
+      Gx = {Gx.x + vx[i].x * Mxi, Gx.y + vx[i].y * Mxi, Gx.z + vx[i].z * Mxi};
+      gx = {gx.x + vx[i].x * mxi, gx.y + vx[i].y * mxi, gx.z + vx[i].z * mxi};
+      const double Myi = MG[2 * mix(0, i) + h], myi = Mg[2 * mix(0, i) + h];
+      Gy = {Gy.x + vy[i].x * Myi, Gy.y + vy[i].y * Myi, Gy.z + vy[i].z * Myi};
+      gy = {gy.x + vy[i].x * myi, gy.y + vy[i].y * myi, gy.z + vy[i].z * myi};
+      for (int j = 0; j < 3; ++j) {
+        const double Mij = MG[2 * mix(i, j) + h], mij = Mg[2 * mix(i, j) + h];
+        Gxy += dot3(vx[i], vy[j]) * Mij;
+        const V3<double> cxy = cross3(vx[i], vy[j]);
+        gxy = {gxy.x + cxy.x * mij, gxy.y + cxy.y * mij, gxy.z + cxy.z * mij};
+      }
+    }
+    if (h == 0) {
+      m.G0r = G0; m.Gxr = Gx; m.Gyr = Gy; m.Gxyr = Gxy;
+      m.g0r = g0; m.gxr = gx; m.gyr = gy; m.gxyr = gxy;
+    } else {
+      m.G0i = G0; m.Gxi = Gx; m.Gyi = Gy; m.Gxyi = Gxy;
+      m.g0i = g0; m.gxi = gx; m.gyi = gy; m.gxyi = gxy;
+    }
   }
   double pc[36];
   pair_coeffs(m, D, pc);
   // lanes take the (test slot, trial slot) combinations
   for (int q = lane; q < nslot * nslot; q += 32) {
     const int a = q / nslot, b = q % nslot;
-    const int ea = slot_edge[(size_t)sp.t1 * nslot + a];
-    const int eb = slot_edge[(size_t)sp.t2 * nslot + b];
-    if (ea < 0 || eb < 0) continue;
+    const int e1 = slot_edge[(size_t)sp.t1 * nslot + a];
+    const int e2 = slot_edge[(size_t)sp.t2 * nslot + b];
+    if (e1 < 0 || e2 < 0) continue;
     const double* swa = slot_sw + ((size_t)sp.t1 * nslot + a) * 4;
     const double* swb = slot_sw + ((size_t)sp.t2 * nslot + b) * 4;
     const V3<double> wa = {swa[1], swa[2], swa[3]}, wb = {swb[1], swb[2], swb[3]};
     double Sr = 0, Si = 0, Cr = 0, Ci = 0;
     entry_from_pc(pc, swa[0], wa, swb[0], wb, mikr, miki, c4r, c4i, wantS, doC, Sr, Si, Cr, Ci);
-    out.add(ea, eb, wantS, doC, Sr, Si, Cr, Ci);
+    out.add(e1, e2, wantS, doC, Sr, Si, Cr, Ci);
     // vertex-sharing pairs are stored once (t1 < t2): the two-region rule maps
     // onto itself when the triangles swap roles, so (t2, t1) gives the transpose
-    if (cls == 1) out.add(eb, ea, wantS, doC, Sr, Si, Cr, Ci);
+    if (cls == 1) out.add(e2, e1, wantS, doC, Sr, Si, Cr, Ci);
   }
 }
 
@@ -1055,6 +1433,7 @@ static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, 
     const size_t reals = (size_t)((ch * max_cell) | 1) * 36 + (size_t)ch * s.nslot * 18 +
                          (size_t)s.nslot * s.nslot * 4;
     const size_t staged = 2 * (size_t)max_cell * a.nreg * 4 * sizeof(R) +      // points
+                          2 * (size_t)max_cell * s.nslot * 4 * sizeof(R) +     // slot coefficients
                           2 * (size_t)max_cell * (sizeof(R) == 4 ? 24 : 24) +  // centroids
                           2 * (size_t)max_cell * 3 * sizeof(int);              // vertex ids
     return ((reals * sizeof(R) + 15) / 16) * 16 + staged + 64;
@@ -1146,6 +1525,55 @@ int launch_gram(const Space& rwg, const Space& bc, const int64_t* rowptr, const 
   CAL_TRY_CUDA(cudaGetLastError());
   CAL_TRY_CUDA(cudaFreeAsync(d_parent, stream));
   return CAL_OK;
+}
+
+template <typename R, typename VT, typename AT>
+static int rwg_free_t(const Space& s, int scat, double kr, double ki, int nreg, const VT* x, VT* y, int64_t n,
+                      int nrhs, double ar, double ai, double br, double bi, cudaStream_t st) {
+  const int64_t t0 = scat < 0 ? 0 : s.tri_off[scat];
+  const int64_t ntr = (scat < 0 ? s.ntri : s.tri_off[scat + 1]) - t0;
+  const int64_t nb = (ntr + 15) / 16;
+  if (nb > 65535) return fail(CAL_EINVAL, "too many triangles for the regular-pair grid (%lld)", (long long)ntr);
+  if (ntr < 2) return CAL_OK;
+  R mikr, miki, c4r, c4i;
+  wave_scalars(kr, ki, mikr, miki, c4r, c4i);
+  const typename TriOf<R>::T* tri;
+  const R* sw;
+  if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
+  else { tri = s.d_triD; sw = s.d_slot_swd; }
+  int64_t nsing = 0;
+  for (int d = (scat < 0 ? 0 : scat); d < (scat < 0 ? (int)s.sing.size() : scat + 1); ++d)
+    for (const SingPair& q : s.sing[d]) nsing += q.cls == 1 ? 2 : 1;
+  const double units = ((double)ntr * (ntr - 1) / 2 - (double)(nsing - ntr) / 2) * nreg * nreg;
+  dim3 grid((unsigned)nb, (unsigned)nb), block(16, 16);
+  for (int r0 = 0; r0 < nrhs; r0 += 32) {
+    const int nr = std::min(32, nrhs - r0);
+    const int smem = 2 * 16 * 3 * 2 * nr * 2 * (int)sizeof(AT);
+    auto kern = nreg == 6 ? rwg_free_kernel<R, 6, VT, AT> : rwg_free_kernel<R, 1, VT, AT>;
+    if (int rc = ensure_dyn_smem((const void*)kern, smem)) return rc;
+    const int tok = prof_begin(st, "rwg_free", units * nr);
+    kern<<<grid, block, smem, st>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)kr, (R)ki, mikr, miki, c4r, c4i, g_rules,
+                                    x + (int64_t)r0 * 2 * n, y + (int64_t)r0 * 2 * n, n, nr, (AT)ar, (AT)ai,
+                                    (AT)br, (AT)bi);
+    prof_end(st, tok);
+    note_launch();
+    CAL_TRY_CUDA(cudaGetLastError());
+  }
+  return CAL_OK;
+}
+
+int launch_rwg_free(const Space& s, int scat, double kr, double ki, int nreg, int precision, int vec_prec,
+                    const void* x, void* y, int64_t n, int nrhs, double ar, double ai, double br, double bi,
+                    cudaStream_t st) {
+  if (int rc = set_quadrature_tables(nreg, 1)) return rc;
+  if (precision == CAL_FP64)
+    return rwg_free_t<double, double2, double>(s, scat, kr, ki, nreg, (const double2*)x, (double2*)y, n, nrhs, ar,
+                                               ai, br, bi, st);
+  if (vec_prec == CAL_FP64)
+    return rwg_free_t<float, double2, double>(s, scat, kr, ki, nreg, (const double2*)x, (double2*)y, n, nrhs, ar,
+                                              ai, br, bi, st);
+  return rwg_free_t<float, float2, float>(s, scat, kr, ki, nreg, (const float2*)x, (float2*)y, n, nrhs, ar, ai, br,
+                                          bi, st);
 }
 
 }  // namespace cal

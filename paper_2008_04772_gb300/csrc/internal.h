@@ -195,7 +195,16 @@ struct AssembleArgs {
 };
 int set_quadrature_tables(int nreg, int nsing);
 int launch_rwg_regular(const AssembleArgs& a);
+// max errors of the singular kernel's own double cis/exp against the CUDA library
+int check_elementary(int64_t n, double lo, double hi, double* err_cis, double* err_exp);
 int launch_singular(const AssembleArgs& a);
+// A8: y += the regular (non-touching) part of the PMCHWT block of space s
+// restricted to scatterer scat (-1: union) at wavenumber k, computed on the
+// fly: y1 += C x1 + alpha S x2, y2 += C x2 + beta S x1 for nrhs vectors
+// [nrhs][2n]; precision CAL_FP32 or CAL_FP64 (kernel), vec_prec of x and y
+int launch_rwg_free(const Space& s, int scat, double kr, double ki, int nreg, int precision, int vec_prec,
+                    const void* x, void* y, int64_t n, int nrhs, double ar, double ai, double br, double bi,
+                    cudaStream_t st);
 int launch_gram(const Space& rwg, const Space& bc, const int64_t* rowptr, const int* col,
                 const int64_t* rowptrT, const int* colT, double* vals, double* valsT,
                 cudaStream_t stream);

@@ -40,10 +40,17 @@ struct Footprint {
 int64_t resident_bytes(const Mesh& m, const std::vector<double>& area_m, const cal_solve_opts& o) {
   const int64_t esz = o.precision == CAL_FP64 ? 16 : 8;
   const int64_t N = m.ne;
-  int64_t b = 2 * N * N * esz;  // S, C at k_e on the union
-  for (int64_t d = 0; d < m.M; ++d) {
-    const int64_t n = m.edge_off[d + 1] - m.edge_off[d];
-    b += 2 * n * n * esz;  // S, C at k_m
+  int64_t b = 0;
+  if (o.matrix_free) {
+    // only touching-pair entries, S and C, at k_e and at k_m: about 30 edges
+    // reach one edge through touching triangles at valence 6; 40 per row taken
+    b += 2 * (2 * N * 40 * esz + N * 40 * 4 + (N + 1) * 8);
+  } else {
+    b += 2 * N * N * esz;  // S, C at k_e on the union
+    for (int64_t d = 0; d < m.M; ++d) {
+      const int64_t n = m.edge_off[d + 1] - m.edge_off[d];
+      b += 2 * n * n * esz;  // S, C at k_m
+    }
   }
   if (o.precond != CAL_PRECOND_NONE) {
     const int pc = o.precond;
@@ -312,7 +319,7 @@ void cal_queue::run(cal_ctx* ctx, Pick& p) {
   cal_solution* sol = nullptr;
   cal_solve_info info{};
   if (!rc) {
-    rc = cal_problem_solve(ctx, prob, inc.data(), cols, &sol);
+    rc = cal_problem_solve(ctx, prob, inc.data(), cols, &r0->opts, &sol);
     if (sol) cal_solution_get_info(sol, &info);
   }
   // far field per request, from its own columns

@@ -9,6 +9,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <type_traits>
 
 #include "solve.h"
 
@@ -496,24 +497,27 @@ __global__ void bicg_k1(BiArgs<R> A, int k) {
   const auto* r = A.r + (size_t)s * A.n;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double part[2] = {0.0, 0.0};
+  // vector arithmetic in the storage precision (float32 on the FP32 path: the
+  // FP64 pipe is a small fraction of FP32 here); the dot products are summed
+  // in float64 across the grid
+  const R bR = (R)br, bI = (R)bi, oR = (R)omr, oI = (R)omi;
   auto pj = [&](int64_t j) {
     const auto pp = pprev[j], vv = vprev[j], rj = r[j];
-    const double dx = pp.x - (omr * vv.x - omi * vv.y), dy = pp.y - (omr * vv.y + omi * vv.x);
-    return double2{rj.x + br * dx - bi * dy, rj.y + br * dy + bi * dx};
+    const R dx = pp.x - (oR * vv.x - oI * vv.y), dy = pp.y - (oR * vv.y + oI * vv.x);
+    return typename CT<R>::T{rj.x + bR * dx - bI * dy, rj.y + bR * dy + bI * dx};
   };
   if (i < A.n) {
-    const double2 pi_ = pj(i);
-    pcur[i] = {(R)pi_.x, (R)pi_.y};
-    double vr = 0, vi = 0;
+    pcur[i] = pj(i);
+    R vr = 0, vi = 0;
     for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-      const double2 pc = pj(A.col[q]);
-      vr += (double)A.val[q] * pc.x;
-      vi += (double)A.val[q] * pc.y;
+      const auto pc = pj(A.col[q]);
+      vr += A.val[q] * pc.x;
+      vi += A.val[q] * pc.y;
     }
-    vcur[i] = {(R)vr, (R)vi};
+    vcur[i] = {vr, vi};
     const auto rh = A.r0[(size_t)s * A.n + i];
-    part[0] = (double)rh.x * vr + (double)rh.y * vi;   // conj(r0) v
-    part[1] = (double)rh.x * vi - (double)rh.y * vr;
+    part[0] = (double)(rh.x * vr + rh.y * vi);   // conj(r0) v
+    part[1] = (double)(rh.x * vi - rh.y * vr);
   }
   block_accumulate<2>(part, a + 0);
 }
@@ -535,22 +539,23 @@ __global__ void bicg_k2(BiArgs<R> A, int k) {
   auto* t = A.t + (size_t)s * A.n;
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double part[3] = {0, 0, 0};
+  const R aR = (R)alr, aI = (R)ali;
   auto sj = [&](int64_t j) {
     const auto vv = vcur[j], rj = r[j];
-    return double2{rj.x - (alr * vv.x - ali * vv.y), rj.y - (alr * vv.y + ali * vv.x)};
+    return typename CT<R>::T{rj.x - (aR * vv.x - aI * vv.y), rj.y - (aR * vv.y + aI * vv.x)};
   };
   if (i < A.n) {
-    double tr = 0, ti = 0;
+    R tr = 0, ti = 0;
     for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-      const double2 sc = sj(A.col[q]);
-      tr += (double)A.val[q] * sc.x;
-      ti += (double)A.val[q] * sc.y;
+      const auto sc = sj(A.col[q]);
+      tr += A.val[q] * sc.x;
+      ti += A.val[q] * sc.y;
     }
-    t[i] = {(R)tr, (R)ti};
-    const double2 si = sj(i);
-    part[0] = tr * si.x + ti * si.y;   // conj(t) s
-    part[1] = tr * si.y - ti * si.x;
-    part[2] = tr * tr + ti * ti;
+    t[i] = {tr, ti};
+    const auto si = sj(i);
+    part[0] = (double)(tr * si.x + ti * si.y);   // conj(t) s
+    part[1] = (double)(tr * si.y - ti * si.x);
+    part[2] = (double)(tr * tr + ti * ti);
   }
   block_accumulate<3>(part, a + 2);
 }
@@ -581,18 +586,17 @@ __global__ void bicg_k3(BiArgs<R> A, int k) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   double part[3] = {0, 0, 0};
   if (i < A.n) {
+    const R aR = (R)alr, aI = (R)ali, oR = (R)omr, oI = (R)omi;
     const auto vv = vcur[i], ri = r[i], pp = pcur[i], tt = t[i];
-    const double sx = ri.x - (alr * vv.x - ali * vv.y), sy = ri.y - (alr * vv.y + ali * vv.x);
-    auto xi = x[i];
-    const double nx = xi.x + (alr * pp.x - ali * pp.y) + (omr * sx - omi * sy);
-    const double ny = xi.y + (alr * pp.y + ali * pp.x) + (omr * sy + omi * sx);
-    x[i] = {(R)nx, (R)ny};
-    const double rx = sx - (omr * tt.x - omi * tt.y), ry = sy - (omr * tt.y + omi * tt.x);
-    r[i] = {(R)rx, (R)ry};
+    const R sx = ri.x - (aR * vv.x - aI * vv.y), sy = ri.y - (aR * vv.y + aI * vv.x);
+    const auto xi = x[i];
+    x[i] = {xi.x + (aR * pp.x - aI * pp.y) + (oR * sx - oI * sy), xi.y + (aR * pp.y + aI * pp.x) + (oR * sy + oI * sx)};
+    const R rx = sx - (oR * tt.x - oI * tt.y), ry = sy - (oR * tt.y + oI * tt.x);
+    r[i] = {rx, ry};
     const auto rh = A.r0[(size_t)s * A.n + i];
-    part[0] = (double)rh.x * rx + (double)rh.y * ry;
-    part[1] = (double)rh.x * ry - (double)rh.y * rx;
-    part[2] = rx * rx + ry * ry;
+    part[0] = (double)(rh.x * rx + rh.y * ry);
+    part[1] = (double)(rh.x * ry - rh.y * rx);
+    part[2] = (double)(rx * rx + ry * ry);
   }
   block_accumulate<3>(part, a + 5);
 }
@@ -719,8 +723,10 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
   const MT* S = reinterpret_cast<const MT*>(b.S);
   const MT* C = reinterpret_cast<const MT*>(b.C);
   if (b.rowptr) {
+    const int tok = prof_begin(st, "pair_spmv", 0.0);
     pair_spmv_kernel<MT, VT, AT><<<blocks_for(b.rows * 32, 256), 256, 0, st>>>(
         S, C, b.rowptr, b.col, b.rows, x1, x2, y1, y2, ar, ai, br, bi);
+    prof_end(st, tok);
     note_launch();
   } else {
     const double bytes = (double)b.rows * b.cols * sizeof(MT) * ((S ? 1 : 0) + (C ? 1 : 0));
@@ -752,6 +758,119 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
     prof_end(st, tok);
     note_launch();
   }
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Several right-hand sides on a dense complex64 block pair at once:
+//   y1_q += C x1_q + alpha S x2_q,  y2_q += C x2_q + beta S x1_q,  q < nrhs.
+// One thread per row walks a 64-column chunk; the chunk of x for G right-hand
+// sides is staged in shared memory and read by broadcast, so each matrix entry
+// is read once per group of G vectors. AT is the arithmetic: float32 for
+// float32 vectors (G = 8), float64 products and sums for float64 vectors
+// (G = 4), so that the refinement residual b - A x is exact up to float64
+// rounding for the stored complex64 A.
+// ---------------------------------------------------------------------------
+constexpr int MV_W = 64;
+
+template <typename VT, typename AT, int G>
+__global__ void __launch_bounds__(256) pair_gemv_multi_kernel(
+    const float2* __restrict__ S, const float2* __restrict__ C, int64_t rows, int64_t cols, int64_t ld,
+    const VT* __restrict__ x1, const VT* __restrict__ x2, int64_t xstride, VT* __restrict__ y1,
+    VT* __restrict__ y2, int nrhs, AT ar, AT ai, AT br, AT bi) {
+  using AT2 = typename std::conditional<sizeof(AT) == 4, float2, double2>::type;
+  __shared__ AT2 xsh[2][G][MV_W];
+  const int64_t nrb = (rows + 255) / 256;
+  const int64_t nch = (cols + MV_W - 1) / MV_W;
+  const int ngr = (nrhs + G - 1) / G;
+  const int64_t units = nrb * nch * ngr;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int g = (int)(u % ngr);
+    const int64_t rest = u / ngr;
+    const int64_t ch = rest % nch, rb = rest / nch;
+    const int64_t c0 = ch * MV_W;
+    const int q0 = g * G;
+    const int nc = (int)(cols - c0 < MV_W ? cols - c0 : MV_W);
+    __syncthreads();  // the previous unit's readers are done with xsh
+    for (int t = threadIdx.x; t < 2 * G * MV_W; t += 256) {
+      const int c = t % MV_W, q = (t / MV_W) % G, h = t / (MV_W * G);
+      AT2 v = {AT(0), AT(0)};
+      if (c < nc && q0 + q < nrhs) {
+        const VT xv = (h ? x2 : x1)[(int64_t)(q0 + q) * xstride + c0 + c];
+        v = {(AT)xv.x, (AT)xv.y};
+      }
+      xsh[h][q][c] = v;
+    }
+    __syncthreads();
+    const int64_t row = rb * 256 + threadIdx.x;
+    if (row >= rows) continue;
+    AT acc[G][8];
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[q][k] = AT(0);
+    const float2* Sr = S + row * ld + c0;
+    const float2* Cr = C + row * ld + c0;
+    for (int c = 0; c < nc; ++c) {
+      const float2 sf = S ? Sr[c] : make_float2(0.f, 0.f);
+      const float2 cf = C ? Cr[c] : make_float2(0.f, 0.f);
+      const AT svx = sf.x, svy = sf.y, cvx = cf.x, cvy = cf.y;
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const AT2 a1 = xsh[0][q][c], a2 = xsh[1][q][c];
+        acc[q][0] = fma(cvx, a1.x, fma(-cvy, a1.y, acc[q][0]));
+        acc[q][1] = fma(cvx, a1.y, fma(cvy, a1.x, acc[q][1]));
+        acc[q][2] = fma(svx, a2.x, fma(-svy, a2.y, acc[q][2]));
+        acc[q][3] = fma(svx, a2.y, fma(svy, a2.x, acc[q][3]));
+        acc[q][4] = fma(cvx, a2.x, fma(-cvy, a2.y, acc[q][4]));
+        acc[q][5] = fma(cvx, a2.y, fma(cvy, a2.x, acc[q][5]));
+        acc[q][6] = fma(svx, a1.x, fma(-svy, a1.y, acc[q][6]));
+        acc[q][7] = fma(svx, a1.y, fma(svy, a1.x, acc[q][7]));
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      if (q0 + q >= nrhs) break;
+      const AT r1 = acc[q][0] + ar * acc[q][2] - ai * acc[q][3];
+      const AT i1 = acc[q][1] + ar * acc[q][3] + ai * acc[q][2];
+      const AT r2 = acc[q][4] + br * acc[q][6] - bi * acc[q][7];
+      const AT i2 = acc[q][5] + br * acc[q][7] + bi * acc[q][6];
+      VT* o1 = y1 + (int64_t)(q0 + q) * xstride + row;
+      VT* o2 = y2 + (int64_t)(q0 + q) * xstride + row;
+      atomicAdd(&o1->x, (decltype(o1->x))r1);
+      atomicAdd(&o1->y, (decltype(o1->y))i1);
+      atomicAdd(&o2->x, (decltype(o2->x))r2);
+      atomicAdd(&o2->y, (decltype(o2->y))i2);
+    }
+  }
+}
+
+int pair_apply_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, int nrhs, double ar,
+                     double ai, double br, double bi, int n_sm, cudaStream_t st) {
+  if (b.precision != CAL_FP32 || b.rowptr) return fail(CAL_EINVAL, "multi-vector GEMV: dense float32 blocks only");
+  const int G = vec_prec == CAL_FP64 ? 4 : 8;
+  const int64_t units = ((b.rows + 255) / 256) * ((b.cols + MV_W - 1) / MV_W) * ((nrhs + G - 1) / G);
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(units, (int64_t)n_sm * 8));
+  const double bytes = (double)b.rows * b.cols * 8.0 * ((b.S ? 1 : 0) + (b.C ? 1 : 0));
+  const int tok = prof_begin(st, "pair_gemv", bytes * ((nrhs + G - 1) / G));
+  const float2* S = reinterpret_cast<const float2*>(b.S);
+  const float2* C = reinterpret_cast<const float2*>(b.C);
+  if (vec_prec == CAL_FP64) {
+    const double2* xx = (const double2*)x;
+    double2* yy = (double2*)y;
+    pair_gemv_multi_kernel<double2, double, 4><<<grid, 256, 0, st>>>(
+        S, C, b.rows, b.cols, b.cols, xx + b.col_off, xx + n + b.col_off, 2 * n, yy + b.row_off,
+        yy + n + b.row_off, nrhs, ar, ai, br, bi);
+  } else {
+    const float2* xx = (const float2*)x;
+    float2* yy = (float2*)y;
+    pair_gemv_multi_kernel<float2, float, 8><<<grid, 256, 0, st>>>(
+        S, C, b.rows, b.cols, b.cols, xx + b.col_off, xx + n + b.col_off, 2 * n, yy + b.row_off,
+        yy + n + b.row_off, nrhs, (float)ar, (float)ai, (float)br, (float)bi);
+  }
+  prof_end(st, tok);
+  note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -975,6 +1094,8 @@ __global__ void gather_kernel(const double2* __restrict__ src, int64_t bsrc, dou
 int gmres_cgs_step(const double2* V, int64_t bV, int64_t n, int j, double2* w, double2* h1, double2* h2,
                    int64_t bh, double* wn2, int64_t bwn, int nrhs, cudaStream_t st) {
   const dim3 g(blocks_for(n, 256), nrhs);
+  // two dot/axpy passes over the j+1 basis vectors of every column
+  const int tok = prof_begin(st, "gmres_cgs", 4.0 * (j + 1) * (double)n * sizeof(double2) * nrhs);
   CAL_TRY_CUDA(cudaMemsetAsync(h1, 0, nrhs * bh * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemsetAsync(h2, 0, nrhs * bh * sizeof(double2), st));
   for (int q = 0; q < nrhs; ++q) CAL_TRY_CUDA(cudaMemsetAsync(wn2 + q * bwn, 0, sizeof(double), st));
@@ -983,6 +1104,7 @@ int gmres_cgs_step(const double2* V, int64_t bV, int64_t n, int j, double2* w, d
   multi_dot_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, w, n, h2, bh);
   multi_axpy_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, h2, bh, w, n);
   norm2_kernel<<<g, 256, 0, st>>>(w, n, wn2, bwn);
+  prof_end(st, tok);
   note_launch(5);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;

@@ -29,6 +29,10 @@ struct BlockRef {
 // x, y component-major of length 2n (n = total basis count)
 int pair_apply(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, double ar,
                double ai, double br, double bi, cudaStream_t st);
+// the same for nrhs vectors [nrhs][2n] at once (dense float32 blocks; float32
+// arithmetic for float32 vectors, float64 products and sums for float64 ones)
+int pair_apply_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, int nrhs, double ar,
+                     double ai, double br, double bi, int n_sm, cudaStream_t st);
 int zero_vec(void* y, int prec, int64_t n, cudaStream_t st);
 int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale, cudaStream_t st);
 int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st);

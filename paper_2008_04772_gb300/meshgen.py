@@ -100,14 +100,25 @@ def _orient_outward(V, T, centre):
 # hexagonal prisms
 # --------------------------------------------------------------------------
 def _merge_points(points, tol=1e-10):
-    """Unique points by rounded coordinates; returns (unique array, index map)."""
+    """Unique points by rounded coordinates; returns (unique array, index map).
+
+    A point whose rounded key is new also looks in the 26 neighbouring keys,
+    so that two copies of one point computed by different formulas merge even
+    when they straddle a rounding boundary."""
     key_of = {}
     out = []
     idx = np.empty(len(points), dtype=np.int64)
     scale = 1.0 / tol
+    near = [(a, b, c) for a in (-1, 0, 1) for b in (-1, 0, 1) for c in (-1, 0, 1) if (a, b, c) != (0, 0, 0)]
     for i, p in enumerate(points):
         key = (round(p[0] * scale), round(p[1] * scale), round(p[2] * scale))
         j = key_of.get(key)
+        if j is None:
+            for d in near:
+                j = key_of.get((key[0] + d[0], key[1] + d[1], key[2] + d[2]))
+                if j is not None and max(abs(out[j][q] - p[q]) for q in range(3)) <= tol:
+                    break
+                j = None
         if j is None:
             j = len(out)
             key_of[key] = j
@@ -204,21 +215,19 @@ def _prism_axes(R):
     return faces, edges
 
 
-def _sat_gap(P1, F1, E1, P2, F2, E2):
-    """Largest separation along the separating-axis candidates (<= true distance)."""
-    axes = [f for f in F1] + [f for f in F2]
-    for e1 in E1:
-        for e2 in E2:
-            c = np.cross(e1, e2)
-            nc = np.linalg.norm(c)
-            if nc > 1e-9:
-                axes.append(c / nc)
-    best = -np.inf
-    for ax in axes:
-        p1, p2 = P1 @ ax, P2 @ ax
-        gap = max(p2.min() - p1.max(), p1.min() - p2.max())
-        best = max(best, gap)
-    return best
+def _sat_axes(F1, E1, F2, E2):
+    """Separating-axis candidates of two prisms: face normals and edge cross products."""
+    c = np.cross(E1[:, None, :], E2[None, :, :]).reshape(-1, 3)
+    nc = np.linalg.norm(c, axis=1)
+    keep = nc > 1e-9
+    return np.concatenate([F1, F2, c[keep] / nc[keep, None]])
+
+
+def _sat_gap(P1, P2, axes):
+    """Largest separation along the candidate axes (<= true distance)."""
+    p1, p2 = P1 @ axes.T, P2 @ axes.T
+    gaps = np.maximum(p2.min(0) - p1.max(0), p1.min(0) - p2.max(0))
+    return float(gaps.max())
 
 
 def prism_aggregate(n_prisms: int, tris_per_prism: int | list, seed: int,
@@ -247,13 +256,14 @@ def prism_aggregate(n_prisms: int, tris_per_prism: int | list, seed: int,
                 ok = False
                 break
             F, E = _prism_axes(rots[m])
+            axes = [_sat_axes(F, E, q[1], q[2]) for q in placed]
             while True:
                 c = rng.uniform(-0.5 * diameter, 0.5 * diameter, 3)
                 if np.linalg.norm(c) + rho > 0.5 * diameter:
                     rejections += 1
                 else:
                     P = _prism_corners(a, L, rots[m], c)
-                    if all(_sat_gap(P, F, E, q[0], q[1], q[2]) >= gap for q in placed):
+                    if all(_sat_gap(P, q[0], ax) >= gap for q, ax in zip(placed, axes)):
                         placed.append((P, F, E, c, L))
                         break
                     rejections += 1

@@ -157,3 +157,13 @@ def test_full_size_sampled_rows(ctx, sphere4):
         # singular-rule asymmetry (~1e-6 at Gauss order 4)
         assert rel(S.T, S) < 1e-4 and rel(C.T, C) < 1e-4
         del S, C, op
+
+
+@pytest.mark.parametrize("lo,hi", [(-3.2, 3.2), (-60.0, 60.0), (0.0, 700.0)])
+def test_singular_kernel_elementary_functions(ctx, lo, hi):
+    # the singular-pair kernel's own double cis/exp against CUDA's sincos/exp
+    import ctypes
+    ec, ee = ctypes.c_double(), ctypes.c_double()
+    assert cal.lib().cal_check_elementary(1 << 20, lo, hi, ctypes.byref(ec), ctypes.byref(ee)) == cal.OK
+    assert ec.value < 4e-16 * max(1.0, abs(hi) / 64), ec.value
+    assert ee.value < 6e-16, ee.value

@@ -75,6 +75,11 @@ def test_problem_solves_equal_the_one_shot_solve(ctx, solo):
     ctx2 = cal.Context(0)
     F2 = prob.solve(_inc(nrhs, 1), ctx=ctx2).far_field(DIRS)
     assert rel(F2, solo[1]) < 1e-5
+    # per-solve solver settings: a cap of two iterations does not converge,
+    # and the problem's own settings apply again on the next solve
+    s = prob.solve(_inc(1), solver=cal.solve_opts(tol=1e-12, maxit=2, refine=0), allow_not_converged=True)
+    assert s.rc == cal.ENOTCONV and s.info().iterations <= 2
+    assert prob.solve(_inc(nrhs, 1)).rc == cal.OK
 
 
 def _submit(q, i):
