@@ -131,6 +131,10 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     std::vector<int> cells = cell_list(sp, scat);
     int max_cell = 0;
     for (int v : cells) max_cell = std::max(max_cell, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
+    // tiles (v, w), v <= w, grouped into units of one test cell and up to 16 trial cells
+    constexpr int UNIT = 16;
+    std::vector<int> units;  // {v, begin, count, 0} per unit
+    std::vector<int> wlist;
     std::vector<int2> tiles;
     if (!dense) {
       const int64_t off = op->row_offset;
@@ -148,14 +152,28 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
       tiles.resize(keys.size());
       for (size_t q = 0; q < keys.size(); ++q) tiles[q] = make_int2((int)(keys[q] >> 32), (int)(keys[q] & 0xffffffff));
+      wlist.resize(tiles.size());
+      for (size_t q = 0; q < tiles.size(); ++q) wlist[q] = tiles[q].y;
+      for (size_t q = 0; q < tiles.size();) {
+        size_t e = q;
+        while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < (size_t)UNIT) ++e;
+        units.insert(units.end(), {tiles[q].x, (int)q, (int)(e - q), 0});
+        q = e;
+      }
+    } else {
+      wlist = cells;
+      const int nc = (int)cells.size();
+      for (int i = 0; i < nc; ++i)
+        for (int j0 = i; j0 < nc; j0 += UNIT) units.insert(units.end(), {cells[i], j0, std::min(UNIT, nc - j0), 0});
     }
-    int* d_cells = nullptr;
-    int2* d_tiles = nullptr;
-    CAL_TRY_CUDA(cudaMallocAsync((void**)&d_cells, std::max<size_t>(cells.size(), 1) * sizeof(int), st));
-    CAL_TRY_CUDA(cudaMemcpyAsync(d_cells, cells.data(), cells.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    if (!dense && !tiles.empty()) {
-      CAL_TRY_CUDA(cudaMallocAsync((void**)&d_tiles, tiles.size() * sizeof(int2), st));
-      CAL_TRY_CUDA(cudaMemcpyAsync(d_tiles, tiles.data(), tiles.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+    const int64_t nunits = (int64_t)units.size() / 4;
+    int* d_units = nullptr;
+    int* d_wlist = nullptr;
+    if (nunits > 0) {
+      CAL_TRY_CUDA(cudaMallocAsync((void**)&d_units, units.size() * sizeof(int), st));
+      CAL_TRY_CUDA(cudaMallocAsync((void**)&d_wlist, std::max<size_t>(wlist.size(), 1) * sizeof(int), st));
+      CAL_TRY_CUDA(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+      CAL_TRY_CUDA(cudaMemcpyAsync(d_wlist, wlist.data(), wlist.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     }
     // algorithmic work: cell-pair triangle pairs minus touching ones, times rule points squared
     double pairs = 0.0;
@@ -180,12 +198,12 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
           pairs -= mult * (cell_of(q.t1) == cell_of(q.t2) ? 1.0 : 0.5);
         }
     }
-    if (dense || !tiles.empty())
-      rc = launch_bc_regular_tiles(a, d_cells, (int64_t)cells.size(), dense ? nullptr : d_tiles,
-                                   (int64_t)tiles.size(), max_cell, ctx.n_sm, pairs * nreg * nreg);
-    // the tile list must outlive the kernel: free in stream order
-    cudaFreeAsync(d_cells, st);
-    if (d_tiles) cudaFreeAsync(d_tiles, st);
+    if (nunits > 0)
+      rc = launch_bc_regular_units(a, d_units, nunits, d_wlist, max_cell, ctx.n_sm, pairs * nreg * nreg);
+    // the unit lists must outlive the kernel: free in stream order; the host
+    // vectors are read by the copies before this function returns (pageable)
+    if (d_units) cudaFreeAsync(d_units, st);
+    if (d_wlist) cudaFreeAsync(d_wlist, st);
     if (rc) return rc;
   }
   if ((rc = launch_singular(a))) return rc;

@@ -634,210 +634,214 @@ __global__ void __launch_bounds__(256) rwg_free_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// A5: BC assembly by dual-cell tiles (v, w), v <= w. Stage 1: pair
-// coefficients of every (tau1 in D(v), tau2 in D(w)) into shared memory;
-// stage 2: contract the trial side per (tau1, trial slot); stage 3: contract
-// the test side per (test slot, trial slot) and add to the output (and to
-// the mirrored entry when v != w).
+// A5: BC assembly by dual-cell tiles (v, w), v <= w. A block takes a "unit":
+// one test cell v and up to 16 trial cells w (a run of the tile list); v's
+// quadrature points, centroids, vertex ids and slot coefficients are staged
+// in shared memory once per unit, w's once per tile. Per tile, stage 1 forms
+// the pair coefficients of every (tau1 in D(v), tau2 in D(w)) in shared
+// memory (pair-major, 36 reals, vector stores); stage 2 contracts the trial
+// side per (tau1, trial slot) and stage 3 the test side per (test slot, trial
+// slot), S and C as separate work items; the result is added to the output
+// and to the mirrored entry when v != w.
 // ---------------------------------------------------------------------------
-struct TileList {
-  const int* cells;       // vertex ids of the scatterer (dense enumeration)
-  int64_t ncell;
-  const int2* tiles;      // explicit list (near field) or nullptr
-  int64_t ntile;
+struct BcUnit {
+  int v;      // test cell (vertex id)
+  int begin;  // first trial cell in the w list
+  int count;  // trial cells
+  int pad;
 };
 
-__device__ __forceinline__ void decode_upper(int64_t k, int64_t n, int64_t& i, int64_t& j) {
-  // k-th pair (i <= j) in row-major order of the upper triangle of an n x n grid
-  const double nn = 2.0 * n + 1.0;
-  int64_t r = (int64_t)floor((nn - sqrt(nn * nn - 8.0 * (double)k)) * 0.5);
-  if (r < 0) r = 0;
-  while (r > 0 && r * (2 * n - r + 1) / 2 > k) --r;
-  while ((r + 1) * (2 * n - r) / 2 <= k) ++r;
-  i = r;
-  j = r + (k - r * (2 * n - r + 1) / 2);
+template <typename R> struct Vec4Of;
+template <> struct Vec4Of<float> { using T = float4; static constexpr int N = 4; };
+template <> struct Vec4Of<double> { using T = double2; static constexpr int N = 2; };
+
+// copy n reals (n a multiple of 4, both pointers 16-byte aligned) with vector moves
+template <typename R>
+__device__ __forceinline__ void vcopy(R* __restrict__ dst, const R* __restrict__ src, int n) {
+  using V = typename Vec4Of<R>::T;
+  constexpr int K = Vec4Of<R>::N;
+  const V* s = reinterpret_cast<const V*>(src);
+  V* d = reinterpret_cast<V*>(dst);
+  for (int q = 0; q < n / K; ++q) d[q] = s[q];
 }
 
-template <typename R, int NREG>
-__global__ void __launch_bounds__(160, sizeof(R) == 4 ? 3 : 2) bc_tile_kernel(
+constexpr int BC_RED = 20;  // stage-2 record: S part [0, 12), C part [12, 20)
+
+template <typename R, int NREG, int TT>
+__global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
     const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
     const R* __restrict__ slot_sw, int nslot, const int* __restrict__ cell_ptr,
-    const int* __restrict__ cell_tri, TileList tl, R kr, R ki, R mikr, R miki, R c4r, R c4i,
-    bool wantS, bool wantC, Rules rl, Sink<R> out, int max_cell, int chunk) {
+    const int* __restrict__ cell_tri, const BcUnit* __restrict__ units, int64_t nunits,
+    const int* __restrict__ wlist, R kr, R ki, R mikr, R miki, R c4r, R c4i, bool wantS, bool wantC,
+    Rules rl, Sink<R> out, int max_cell, int chunk) {
   using TRI = typename TriOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  // pair coefficients component-major with an odd stride: pcs[c * PS + pair]
-  const int PS = (chunk * max_cell) | 1;
-  R* pcs = reinterpret_cast<R*>(smem_raw);                          // [36][PS]
-  R* red = pcs + (size_t)PS * 36;                                   // [chunk][nslot][18]
-  R* acc = red + (size_t)chunk * nslot * 18;                        // [nslot][nslot][4]
+  R* pcs = reinterpret_cast<R*>(smem_raw);                        // [chunk * max_cell][36]
+  R* red = pcs + (size_t)chunk * max_cell * 36;                   // [chunk][nslot][BC_RED]
+  R* acc = red + (size_t)chunk * nslot * BC_RED;                  // [nslot][nslot][4]
   const size_t staged_off =
-      ((((size_t)PS * 36 + (size_t)chunk * nslot * 18 + (size_t)nslot * nslot * 4) * sizeof(R) + 15) / 16) * 16;
-  P4<R>* ptsA = reinterpret_cast<P4<R>*>(smem_raw + staged_off);     // [max_cell][NREG]
-  P4<R>* ptsB = ptsA + (size_t)max_cell * NREG;                      // [max_cell][NREG]
-  P4<R>* swA = ptsB + (size_t)max_cell * NREG;                       // [max_cell][nslot] (s, w)
-  P4<R>* swB = swA + (size_t)max_cell * nslot;                       // [max_cell][nslot]
+      ((((size_t)chunk * max_cell * 36 + (size_t)chunk * nslot * BC_RED + (size_t)nslot * nslot * 4) *
+            sizeof(R) + 15) / 16) * 16;
+  P4<R>* ptsA = reinterpret_cast<P4<R>*>(smem_raw + staged_off);  // [max_cell][NREG]
+  P4<R>* ptsB = ptsA + (size_t)max_cell * NREG;
+  P4<R>* swA = ptsB + (size_t)max_cell * NREG;                    // [max_cell][nslot] (s, w)
+  P4<R>* swB = swA + (size_t)max_cell * nslot;
   Cent<R>* cA = reinterpret_cast<Cent<R>*>(swB + (size_t)max_cell * nslot);
   Cent<R>* cB = cA + max_cell;
-  int* vidA = reinterpret_cast<int*>(cB + max_cell);                // [max_cell][3]
+  int* vidA = reinterpret_cast<int*>(cB + max_cell);              // [max_cell][3]
   int* vidB = vidA + 3 * max_cell;
-  __shared__ int s_vw[2];
-  const int64_t ntiles = tl.tiles ? tl.ntile : tl.ncell * (tl.ncell + 1) / 2;
-  for (int64_t k = blockIdx.x; k < ntiles; k += gridDim.x) {
-    if (threadIdx.x == 0) {
-      if (tl.tiles) {
-        s_vw[0] = tl.tiles[k].x;
-        s_vw[1] = tl.tiles[k].y;
-      } else {
-        int64_t i, j;
-        decode_upper(k, tl.ncell, i, j);
-        s_vw[0] = tl.cells[i];
-        s_vw[1] = tl.cells[j];
-      }
-    }
-    __syncthreads();
-    const int v = s_vw[0], w = s_vw[1];
-    const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
-    const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
-    // stage the quadrature points, centroids and vertex ids of both cells
-    for (int q = threadIdx.x; q < (n1 + n2) * NREG; q += blockDim.x) {
-      const bool first = q < n1 * NREG;
-      const int qq = first ? q : q - n1 * NREG;
-      const int t = qq / NREG, u = qq % NREG;
-      const TRI T = tri[cell_tri[(first ? b1 : b2) + t]];
-      (first ? ptsA : ptsB)[t * NREG + u] = staged_point(T, rl, u);
+  // stage one cell's quadrature points, centroid, vertex ids and slot coefficients
+  auto stage_cell = [&](int cell, P4<R>* pts, Cent<R>* cen, int* vid, P4<R>* swc) {
+    const int b0 = cell_ptr[cell], n = cell_ptr[cell + 1] - b0;
+    for (int q = threadIdx.x; q < n * NREG; q += TT) {
+      const int t = q / NREG, u = q % NREG;
+      const int tau = cell_tri[b0 + t];
+      const TRI T = tri[tau];
+      pts[t * NREG + u] = staged_point(T, rl, u);
       if (u == 0) {
-        (first ? cA : cB)[t].set(T);
-        int* vd = (first ? vidA : vidB) + 3 * t;
-        vd[0] = T.vid[0]; vd[1] = T.vid[1]; vd[2] = T.vid[2];
-        // slot coefficients (sigma, w) of the triangle
-        const int tau = cell_tri[(first ? b1 : b2) + t];
+        cen[t].set(T);
+        vid[3 * t] = T.vid[0];
+        vid[3 * t + 1] = T.vid[1];
+        vid[3 * t + 2] = T.vid[2];
         const P4<R>* src = reinterpret_cast<const P4<R>*>(slot_sw) + (size_t)tau * nslot;
-        P4<R>* dst = (first ? swA : swB) + (size_t)t * nslot;
-        for (int sl = 0; sl < nslot; ++sl) dst[sl] = src[sl];
+        for (int sl = 0; sl < nslot; ++sl) swc[t * nslot + sl] = src[sl];
       }
     }
-    // number of valid slots of each cell
-    int ns1 = 0, ns2 = 0;
-    {
-      const int tv = cell_tri[b1], tw = cell_tri[b2];
-      while (ns1 < nslot && slot_edge[(size_t)tv * nslot + ns1] >= 0) ++ns1;
-      while (ns2 < nslot && slot_edge[(size_t)tw * nslot + ns2] >= 0) ++ns2;
-    }
-    for (int q = threadIdx.x; q < ns1 * ns2 * 4; q += blockDim.x) acc[q] = R(0);
-    __syncthreads();
-    for (int c0 = 0; c0 < n1; c0 += chunk) {
-      const int nc = min(chunk, n1 - c0);
-      // stage 1: pair coefficients of (tau1 in the chunk) x (tau2 in D(w))
-      for (int p = threadIdx.x; p < nc * n2; p += blockDim.x) {
-        const int i1 = c0 + p / n2, i2 = p % n2;
-        const int* va = vidA + 3 * i1;
-        const int* vb = vidB + 3 * i2;
-        bool touch = false;
-#pragma unroll
-        for (int x = 0; x < 3; ++x)
-#pragma unroll
-          for (int y = 0; y < 3; ++y) touch |= va[x] == vb[y];
-        R* pc = pcs + p;
-        if (touch) {
-          for (int q = 0; q < 36; ++q) pc[q * PS] = R(0);
-          continue;
-        }
-        const V3<R> D = cA[i1].minus(cB[i2]);
-        Mom<R> m;
-        regular_moments_staged<R, NREG>(ptsA + i1 * NREG, ptsB + i2 * NREG, D, kr, ki, wantC, m);
-        R tmp[36];
-        pair_coeffs(m, D, tmp);
-#pragma unroll
-        for (int q = 0; q < 36; ++q) pc[q * PS] = tmp[q];
-      }
+  };
+  auto nvalid = [&](int cell) {
+    const int tv = cell_tri[cell_ptr[cell]];
+    int ns = 0;
+    while (ns < nslot && slot_edge[(size_t)tv * nslot + ns] >= 0) ++ns;
+    return ns;
+  };
+  for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
+    const BcUnit U = units[uidx];
+    const int v = U.v;
+    const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
+    const int ns1 = nvalid(v);
+    __syncthreads();  // the previous unit is done with the A side
+    stage_cell(v, ptsA, cA, vidA, swA);
+    for (int wi = 0; wi < U.count; ++wi) {
+      const int w = wlist[U.begin + wi];
+      const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
+      const int ns2 = nvalid(w);
+      __syncthreads();  // the previous tile is done with the B side and acc
+      stage_cell(w, ptsB, cB, vidB, swB);
+      for (int q = threadIdx.x; q < ns1 * ns2 * 4; q += TT) acc[q] = R(0);
       __syncthreads();
-      // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side
-      // factors; the S and C halves are separate work items (S items first,
-      // so that a warp takes one branch)
-      const int nS2 = wantS ? nc * ns2 : 0, nC2 = wantC ? nc * ns2 : 0;
-      for (int q = threadIdx.x; q < nS2 + nC2; q += blockDim.x) {
-        const bool isS = q < nS2;
-        const int it = isS ? q : q - nS2;
-        const int i1 = it / ns2, sb_i = it % ns2;
-        const R* q1 = pcs + i1 * n2;
-        R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
-#define PC(c) q1[i2 + (c) * PS]
-        if (isS) {
-          R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0;
-          V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0};
-          for (int i2 = 0; i2 < n2; ++i2) {
-            const P4<R> u = swB[i2 * nslot + sb_i];
-            const R sb = u.x;
-            const V3<R> wb = {u.y, u.z, u.w};
-            const R g0r = PC(0), g0i = PC(1);
-            AS_r += sb * PC(14) + wb.x * PC(2) + wb.y * PC(3) + wb.z * PC(4);
-            AS_i += sb * PC(15) + wb.x * PC(5) + wb.y * PC(6) + wb.z * PC(7);
-            BS_r += sb * g0r;
-            BS_i += sb * g0i;
-            WS_r.x += sb * PC(8) + wb.x * g0r; WS_r.y += sb * PC(9) + wb.y * g0r; WS_r.z += sb * PC(10) + wb.z * g0r;
-            WS_i.x += sb * PC(11) + wb.x * g0i; WS_i.y += sb * PC(12) + wb.y * g0i; WS_i.z += sb * PC(13) + wb.z * g0i;
-          }
-          o[0] = AS_r; o[1] = AS_i; o[2] = BS_r; o[3] = BS_i;
-          o[4] = WS_r.x; o[5] = WS_r.y; o[6] = WS_r.z; o[7] = WS_i.x; o[8] = WS_i.y; o[9] = WS_i.z;
-        } else {
-          R AC_r = 0, AC_i = 0;
-          V3<R> WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
-          for (int i2 = 0; i2 < n2; ++i2) {
-            const P4<R> u = swB[i2 * nslot + sb_i];
-            const R sb = u.x;
-            const V3<R> wb = {u.y, u.z, u.w};
-            AC_r += sb * PC(16) + wb.x * PC(18) + wb.y * PC(19) + wb.z * PC(20);
-            AC_i += sb * PC(17) + wb.x * PC(21) + wb.y * PC(22) + wb.z * PC(23);
-            const V3<R> Vr = {PC(30), PC(31), PC(32)}, Vi = {PC(33), PC(34), PC(35)};
-            const V3<R> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
-            WC_r.x += sb * PC(24) + cr.x; WC_r.y += sb * PC(25) + cr.y; WC_r.z += sb * PC(26) + cr.z;
-            WC_i.x += sb * PC(27) + ci.x; WC_i.y += sb * PC(28) + ci.y; WC_i.z += sb * PC(29) + ci.z;
-          }
-          o[10] = AC_r; o[11] = AC_i;
-          o[12] = WC_r.x; o[13] = WC_r.y; o[14] = WC_r.z; o[15] = WC_i.x; o[16] = WC_i.y; o[17] = WC_i.z;
-        }
-#undef PC
-      }
-      __syncthreads();
-      // stage 3: per (test slot a, trial slot b), sum over the chunk's tau1
-      const int nS3 = wantS ? ns1 * ns2 : 0, nC3 = wantC ? ns1 * ns2 : 0;
-      for (int q = threadIdx.x; q < nS3 + nC3; q += blockDim.x) {
-        const bool isS = q < nS3;
-        const int it = isS ? q : q - nS3;
-        const int sa_i = it / ns2, sb_i = it % ns2;
-        R vr = 0, vi = 0;
-        for (int i1 = 0; i1 < nc; ++i1) {
-          const P4<R> u = swA[(c0 + i1) * nslot + sa_i];
-          const R sa = u.x;
-          const V3<R> wa = {u.y, u.z, u.w};
-          const R* o = red + (size_t)(i1 * nslot + sb_i) * 18;
-          if (isS) {
-            // sa (mik AS + c4 BS) + mik (wa . WS)
-            const R pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
-            const R pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
-            vr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
-            vi += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
+      for (int c0 = 0; c0 < n1; c0 += chunk) {
+        const int nc = min(chunk, n1 - c0);
+        // stage 1: pair coefficients of (tau1 in the chunk) x (tau2 in D(w))
+        for (int p = threadIdx.x; p < nc * n2; p += TT) {
+          const int i1 = c0 + p / n2, i2 = p % n2;
+          const int* va = vidA + 3 * i1;
+          const int* vb = vidB + 3 * i2;
+          bool touch = false;
+#pragma unroll
+          for (int x = 0; x < 3; ++x)
+#pragma unroll
+            for (int y = 0; y < 3; ++y) touch |= va[x] == vb[y];
+          __align__(16) R tmp[36];
+          if (touch) {
+#pragma unroll
+            for (int q = 0; q < 36; ++q) tmp[q] = R(0);
           } else {
-            vr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
-            vi += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
+            const V3<R> D = cA[i1].minus(cB[i2]);
+            Mom<R> m;
+            regular_moments_staged<R, NREG>(ptsA + i1 * NREG, ptsB + i2 * NREG, D, kr, ki, wantC, m);
+            pair_coeffs(m, D, tmp);
+          }
+          vcopy(pcs + (size_t)p * 36, tmp, 36);
+        }
+        __syncthreads();
+        // stage 2: per (tau1, trial slot b), sum over tau2 of the trial-side factors
+        const int nS2 = wantS ? nc * ns2 : 0, nC2 = wantC ? nc * ns2 : 0;
+        for (int q = threadIdx.x; q < nS2 + nC2; q += TT) {
+          const bool isS = q < nS2;
+          const int it = isS ? q : q - nS2;
+          const int i1 = it / ns2, sb_i = it % ns2;
+          R* o = red + (size_t)(i1 * nslot + sb_i) * BC_RED;
+          if (isS) {
+            R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0;
+            V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0};
+            for (int i2 = 0; i2 < n2; ++i2) {
+              const P4<R> u = swB[i2 * nslot + sb_i];
+              const R sb = u.x;
+              const V3<R> wb = {u.y, u.z, u.w};
+              __align__(16) R pc[16];
+              vcopy(pc, pcs + (size_t)(i1 * n2 + i2) * 36, 16);
+              AS_r += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
+              AS_i += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
+              BS_r += sb * pc[0];
+              BS_i += sb * pc[1];
+              WS_r.x += sb * pc[8] + wb.x * pc[0]; WS_r.y += sb * pc[9] + wb.y * pc[0]; WS_r.z += sb * pc[10] + wb.z * pc[0];
+              WS_i.x += sb * pc[11] + wb.x * pc[1]; WS_i.y += sb * pc[12] + wb.y * pc[1]; WS_i.z += sb * pc[13] + wb.z * pc[1];
+            }
+            __align__(16) R rec[12] = {AS_r, AS_i, BS_r, BS_i, WS_r.x, WS_r.y, WS_r.z, WS_i.x, WS_i.y, WS_i.z, R(0), R(0)};
+            vcopy(o, rec, 12);
+          } else {
+            R AC_r = 0, AC_i = 0;
+            V3<R> WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
+            for (int i2 = 0; i2 < n2; ++i2) {
+              const P4<R> u = swB[i2 * nslot + sb_i];
+              const R sb = u.x;
+              const V3<R> wb = {u.y, u.z, u.w};
+              __align__(16) R pc[20];
+              vcopy(pc, pcs + (size_t)(i1 * n2 + i2) * 36 + 16, 20);  // components 16..35
+              AC_r += sb * pc[0] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
+              AC_i += sb * pc[1] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
+              const V3<R> Vr = {pc[14], pc[15], pc[16]}, Vi = {pc[17], pc[18], pc[19]};
+              const V3<R> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
+              WC_r.x += sb * pc[8] + cr.x; WC_r.y += sb * pc[9] + cr.y; WC_r.z += sb * pc[10] + cr.z;
+              WC_i.x += sb * pc[11] + ci.x; WC_i.y += sb * pc[12] + ci.y; WC_i.z += sb * pc[13] + ci.z;
+            }
+            __align__(16) R rec[8] = {AC_r, AC_i, WC_r.x, WC_r.y, WC_r.z, WC_i.x, WC_i.y, WC_i.z};
+            vcopy(o + 12, rec, 8);
           }
         }
-        R* a4 = acc + (size_t)it * 4 + (isS ? 0 : 2);
-        a4[0] += vr;
-        a4[1] += vi;
+        __syncthreads();
+        // stage 3: per (test slot a, trial slot b), sum over the chunk's tau1
+        const int nS3 = wantS ? ns1 * ns2 : 0, nC3 = wantC ? ns1 * ns2 : 0;
+        for (int q = threadIdx.x; q < nS3 + nC3; q += TT) {
+          const bool isS = q < nS3;
+          const int it = isS ? q : q - nS3;
+          const int sa_i = it / ns2, sb_i = it % ns2;
+          R vr = 0, vi = 0;
+          for (int i1 = 0; i1 < nc; ++i1) {
+            const P4<R> u = swA[(c0 + i1) * nslot + sa_i];
+            const R sa = u.x;
+            const V3<R> wa = {u.y, u.z, u.w};
+            const R* orec = red + (size_t)(i1 * nslot + sb_i) * BC_RED;
+            if (isS) {
+              __align__(16) R o[12];
+              vcopy(o, orec, 12);
+              // sa (mik AS + c4 BS) + mik (wa . WS)
+              const R pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
+              const R pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
+              vr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
+              vi += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
+            } else {
+              __align__(16) R o[8];
+              vcopy(o, orec + 12, 8);
+              vr += sa * o[0] + wa.x * o[2] + wa.y * o[3] + wa.z * o[4];
+              vi += sa * o[1] + wa.x * o[5] + wa.y * o[6] + wa.z * o[7];
+            }
+          }
+          R* a4 = acc + (size_t)it * 4 + (isS ? 0 : 2);
+          a4[0] += vr;
+          a4[1] += vi;
+        }
+        __syncthreads();
       }
-      __syncthreads();
+      for (int q = threadIdx.x; q < ns1 * ns2; q += TT) {
+        const int sa_i = q / ns2, sb_i = q % ns2;
+        const R* a4 = acc + (size_t)q * 4;
+        const int ea = slot_edge[(size_t)cell_tri[b1] * nslot + sa_i];
+        const int eb = slot_edge[(size_t)cell_tri[b2] * nslot + sb_i];
+        out.add(ea, eb, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
+        if (v != w) out.add(eb, ea, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
+      }
     }
-    for (int q = threadIdx.x; q < ns1 * ns2; q += blockDim.x) {
-      const int sa_i = q / ns2, sb_i = q % ns2;
-      const R* a4 = acc + (size_t)q * 4;
-      const int ea = slot_edge[(size_t)cell_tri[b1] * nslot + sa_i];
-      const int eb = slot_edge[(size_t)cell_tri[b2] * nslot + sb_i];
-      out.add(ea, eb, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
-      if (v != w) out.add(eb, ea, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
-    }
-    __syncthreads();
   }
 }
 
@@ -1134,6 +1138,41 @@ int check_elementary(int64_t n, double lo, double hi, double* err_cis, double* e
   return CAL_OK;
 }
 
+// Radial sums of one (region, e) direction: over the Gauss nodes xi_j of the
+// radial variable, with r = xi_j rho,
+//   SG_d += e^{ikr} w_j xi_j^2 xi_j^d,  Sg_d += (ikr - 1) e^{ikr} w_j xi_j^d,  d = 0, 1, 2,
+// as (re, im) pairs. NG > 0 fixes the node count at compile time (unrolled).
+template <int NG>
+__device__ __forceinline__ void radial_sums(const double* gx, const double* gw, int ng, double rho, double kr,
+                                            double ki, bool doC, double* SG, double* Sg) {
+  const int nn = NG > 0 ? NG : ng;
+#pragma unroll
+  for (int j = 0; j < (NG > 0 ? NG : 16); ++j) {
+    if (NG == 0 && j >= nn) break;
+    const double xi = gx[j], wj = gw[j];
+    const double rr = xi * rho;
+    double cth, sth;
+    cis_f64(kr * rr, cth, sth);
+    if (ki != 0.0) {
+      const double e = exp_f64(-ki * rr);
+      cth *= e;
+      sth *= e;
+    }
+    const double tg = wj * xi * xi;
+    const double Tr = cth * tg, Ti = sth * tg;
+    SG[0] += Tr; SG[1] += Ti;
+    SG[2] = fma(Tr, xi, SG[2]); SG[3] = fma(Ti, xi, SG[3]);
+    SG[4] = fma(Tr, xi * xi, SG[4]); SG[5] = fma(Ti, xi * xi, SG[5]);
+    if (doC) {
+      const double fr = -ki * rr - 1.0, fi = kr * rr;
+      const double Ur = (fr * cth - fi * sth) * wj, Ui = (fr * sth + fi * cth) * wj;
+      Sg[0] += Ur; Sg[1] += Ui;
+      Sg[2] = fma(Ur, xi, Sg[2]); Sg[3] = fma(Ui, xi, Sg[3]);
+      Sg[4] = fma(Ur, xi * xi, Sg[4]); Sg[5] = fma(Ui, xi * xi, Sg[5]);
+    }
+  }
+}
+
 // Every Sauter–Schwab map is x = xi f(e), y = xi g(e) in the reference
 // coordinates of the two triangles (shared vertex at the origin of both), and
 // its jacobian is xi^3 J(e). So x - y = xi rho(e), the 1/r of G cancels two
@@ -1191,31 +1230,10 @@ __global__ void __launch_bounds__(128) singular_kernel(
     const double irho = 1.0 / rho;
     const double We = rl.gw[a1] * rl.gw[a2] * rl.gw[a3] * jac * scale;
     double SG[6] = {0, 0, 0, 0, 0, 0}, Sg[6] = {0, 0, 0, 0, 0, 0};  // (re, im) for xi^0, xi^1, xi^2
-    for (int j = 0; j < ng; ++j) {
-      const double xi = rl.gx[j], wj = rl.gw[j];
-      const double rr = xi * rho;
-      double cth, sth;
-      cis_f64(kr * rr, cth, sth);
-      if (ki != 0.0) {
-        const double e = exp_f64(-ki * rr);
-        cth *= e;
-        sth *= e;
-      }
-      // G w = e^{ikr} w_j xi^2 We / (4 pi rho)
-      const double tg = wj * xi * xi;
-      const double Tr = cth * tg, Ti = sth * tg;
-      SG[0] += Tr; SG[1] += Ti;
-      SG[2] = fma(Tr, xi, SG[2]); SG[3] = fma(Ti, xi, SG[3]);
-      SG[4] = fma(Tr, xi * xi, SG[4]); SG[5] = fma(Ti, xi * xi, SG[5]);
-      if (doC) {
-        // g w = (ikr - 1) e^{ikr} w_j We / (4 pi rho^3)
-        const double fr = -ki * rr - 1.0, fi = kr * rr;
-        const double Ur = (fr * cth - fi * sth) * wj, Ui = (fr * sth + fi * cth) * wj;
-        Sg[0] += Ur; Sg[1] += Ui;
-        Sg[2] = fma(Ur, xi, Sg[2]); Sg[3] = fma(Ui, xi, Sg[3]);
-        Sg[4] = fma(Ur, xi * xi, Sg[4]); Sg[5] = fma(Ui, xi * xi, Sg[5]);
-      }
-    }
+    if (ng == 4)
+      radial_sums<4>(rl.gx, rl.gw, 4, rho, kr, ki, doC, SG, Sg);  // unrolled: four independent chains
+    else
+      radial_sums<0>(rl.gx, rl.gw, ng, rho, kr, ki, doC, SG, Sg);
     const double cG = We * irho * INV_4PI, cg = cG * irho * irho;
     const double mono[9] = {1.0, xh[0], xh[1], yh[0], yh[1], xh[0] * yh[0], xh[0] * yh[1], xh[1] * yh[0],
                             xh[1] * yh[1]};
@@ -1250,10 +1268,12 @@ __global__ void __launch_bounds__(128) singular_kernel(
   auto mix = [](int i, int j) { return i == 0 ? (j == 0 ? 0 : 2 + j) : (j == 0 ? i : 2 * i + j + 2); };
   Mom<double> m;
   m.zero();
-  for (int h = 0; h < 2; ++h) {  // re, im
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // re, im (unrolled: the moment arrays stay in registers)
     double G0 = MG[h], g0 = Mg[h];
     V3<double> Gx = {0, 0, 0}, Gy = {0, 0, 0}, gx = {0, 0, 0}, gy = {0, 0, 0}, gxy = {0, 0, 0};
     double Gxy = 0.0;
+#pragma unroll
     for (int i = 0; i < 3; ++i) {
       const double Mxi = MG[2 * mix(i, 0) + h], mxi = Mg[2 * mix(i, 0) + h];
       Gx = {Gx.x + vx[i].x * Mxi, Gx.y + vx[i].y * Mxi, Gx.z + vx[i].z * Mxi};
@@ -1261,6 +1281,7 @@ __global__ void __launch_bounds__(128) singular_kernel(
       const double Myi = MG[2 * mix(0, i) + h], myi = Mg[2 * mix(0, i) + h];
       Gy = {Gy.x + vy[i].x * Myi, Gy.y + vy[i].y * Myi, Gy.z + vy[i].z * Myi};
       gy = {gy.x + vy[i].x * myi, gy.y + vy[i].y * myi, gy.z + vy[i].z * myi};
+#pragma unroll
       for (int j = 0; j < 3; ++j) {
         const double Mij = MG[2 * mix(i, j) + h], mij = Mg[2 * mix(i, j) + h];
         Gxy += dot3(vx[i], vy[j]) * Mij;
@@ -1418,56 +1439,52 @@ struct BcTiles {
 };
 
 template <typename R>
-static int bc_regular_t(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
-                        int64_t ntile, int max_cell, int n_sm, double units) {
+static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nunits, const int* wlist, int max_cell,
+                        int n_sm, double work) {
   const Space& s = *a.sp;
   R mikr, miki, c4r, c4i;
   wave_scalars(a.kr, a.ki, mikr, miki, c4r, c4i);
   const Sink<R> out = make_sink<R>(a);
   const bool wS = a.want & 1, wC = a.want & 2;
-  TileList tl{cells, ncell, tiles, ntile};
-  const int64_t ntiles = tiles ? ntile : ncell * (ncell + 1) / 2;
-  if (ntiles == 0) return CAL_OK;
+  if (nunits == 0) return CAL_OK;
   // test-cell triangles are processed in chunks so that any valence fits
   auto smem_for = [&](int ch) {
-    const size_t reals = (size_t)((ch * max_cell) | 1) * 36 + (size_t)ch * s.nslot * 18 +
-                         (size_t)s.nslot * s.nslot * 4;
+    const size_t reals = (size_t)ch * max_cell * 36 + (size_t)ch * s.nslot * BC_RED + (size_t)s.nslot * s.nslot * 4;
     const size_t staged = 2 * (size_t)max_cell * a.nreg * 4 * sizeof(R) +      // points
                           2 * (size_t)max_cell * s.nslot * 4 * sizeof(R) +     // slot coefficients
-                          2 * (size_t)max_cell * (sizeof(R) == 4 ? 24 : 24) +  // centroids
+                          2 * (size_t)max_cell * 24 +                          // centroids
                           2 * (size_t)max_cell * 3 * sizeof(int);              // vertex ids
     return ((reals * sizeof(R) + 15) / 16) * 16 + staged + 64;
   };
   int chunk = max_cell;
-  while (chunk > 1 && smem_for(chunk) > 96 * 1024) --chunk;
+  while (chunk > 1 && smem_for(chunk) > 56 * 1024) --chunk;
   const size_t smem = smem_for(chunk);
   if (smem > 227 * 1024) return fail(CAL_EINVAL, "dual cell too large for the tile kernel (%d triangles)", max_cell);
   const typename TriOf<R>::T* tri;
   const R* sw;
   if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
   else { tri = s.d_triD; sw = s.d_slot_swd; }
-  auto kern6 = bc_tile_kernel<R, 6>;
-  auto kern1 = bc_tile_kernel<R, 1>;
-  auto kern = a.nreg == 6 ? kern6 : kern1;
+  constexpr int TT = 128;
+  auto kern = a.nreg == 6 ? bc_tile_kernel<R, 6, TT> : bc_tile_kernel<R, 1, TT>;
   if (int rc = ensure_dyn_smem((const void*)kern, (int)smem)) return rc;
   int per_sm = 0;
-  constexpr int TILE_THREADS = 160;
-  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TILE_THREADS, smem));
-  const int64_t grid = std::min<int64_t>(ntiles, (int64_t)std::max(1, per_sm) * n_sm * 4);
-  const int tok = prof_begin(a.stream, "bc_tile", units);
-  kern<<<(unsigned)grid, TILE_THREADS, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr,
-                                                s.d_cell_tri, tl, (R)a.kr, (R)a.ki, mikr, miki, c4r,
-                                                c4i, wS, wC, g_rules, out, max_cell, chunk);
+  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT, smem));
+  const int64_t grid = std::min<int64_t>(nunits, (int64_t)std::max(1, per_sm) * n_sm * 2);
+  const int tok = prof_begin(a.stream, "bc_tile", work);
+  kern<<<(unsigned)grid, TT, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr, s.d_cell_tri,
+                                              units, nunits, wlist, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
+                                              g_rules, out, max_cell, chunk);
   prof_end(a.stream, tok);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
-int launch_bc_regular_tiles(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
-                            int64_t ntile, int max_cell, int n_sm, double units) {
-  return a.precision == CAL_FP32 ? bc_regular_t<float>(a, cells, ncell, tiles, ntile, max_cell, n_sm, units)
-                                 : bc_regular_t<double>(a, cells, ncell, tiles, ntile, max_cell, n_sm, units);
+int launch_bc_regular_units(const AssembleArgs& a, const void* units, int64_t nunits, const int* wlist, int max_cell,
+                            int n_sm, double work) {
+  const BcUnit* u = reinterpret_cast<const BcUnit*>(units);
+  return a.precision == CAL_FP32 ? bc_regular_t<float>(a, u, nunits, wlist, max_cell, n_sm, work)
+                                 : bc_regular_t<double>(a, u, nunits, wlist, max_cell, n_sm, work);
 }
 
 int launch_singular(const AssembleArgs& a) {

@@ -94,7 +94,9 @@ int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double
                     double k, double mu, double2* d_out, cudaStream_t st);
 
 // BC tile launcher (assemble.cu)
-int launch_bc_regular_tiles(const AssembleArgs& a, const int* cells, int64_t ncell, const int2* tiles,
-                            int64_t ntile, int max_cell, int n_sm, double units);
+// A5 over units: units [nunits] of {v, begin, count, pad} ints, each a test
+// cell v with the trial cells wlist[begin .. begin + count)
+int launch_bc_regular_units(const AssembleArgs& a, const void* units, int64_t nunits, const int* wlist, int max_cell,
+                            int n_sm, double work);
 
 }  // namespace cal
