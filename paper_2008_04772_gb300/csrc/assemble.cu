@@ -667,14 +667,43 @@ __device__ __forceinline__ void vcopy(R* __restrict__ dst, const R* __restrict__
 
 constexpr int BC_RED = 20;  // stage-2 record: S part [0, 12), C part [12, 20)
 
+// Per-launch copies of what a tile stages, in cell order (cell_tri order), so
+// that staging a cell is a few contiguous, coalesced copies.
+template <typename R>
+struct CellData {
+  P4<R>* pts;    // [ncelltri][NREG] quadrature points relative to the centroid, with weights
+  P4<R>* sw;     // [ncelltri][nslot] slot coefficients (sigma, w)
+  Cent<R>* cen;  // [ncelltri]
+  int* vid;      // [ncelltri][3]
+};
+
+template <typename R, int NREG>
+__global__ void bc_cell_prep_kernel(const typename TriOf<R>::T* __restrict__ tri, const R* __restrict__ slot_sw,
+                                    int nslot, const int* __restrict__ cell_tri, int64_t ncelltri, Rules rl,
+                                    CellData<R> cd) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= ncelltri * NREG) return;
+  const int64_t t = q / NREG;
+  const int u = (int)(q % NREG);
+  const int tau = cell_tri[t];
+  const typename TriOf<R>::T T = tri[tau];
+  cd.pts[q] = staged_point(T, rl, u);
+  if (u == 0) {
+    cd.cen[t].set(T);
+    cd.vid[3 * t] = T.vid[0];
+    cd.vid[3 * t + 1] = T.vid[1];
+    cd.vid[3 * t + 2] = T.vid[2];
+    const P4<R>* src = reinterpret_cast<const P4<R>*>(slot_sw) + (size_t)tau * nslot;
+    for (int sl = 0; sl < nslot; ++sl) cd.sw[t * nslot + sl] = src[sl];
+  }
+}
+
 template <typename R, int NREG, int TT>
 __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
-    const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
-    const R* __restrict__ slot_sw, int nslot, const int* __restrict__ cell_ptr,
-    const int* __restrict__ cell_tri, const BcUnit* __restrict__ units, int64_t nunits,
+    CellData<R> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
+    const int* __restrict__ cell_edge, const BcUnit* __restrict__ units, int64_t nunits,
     const int* __restrict__ wlist, R kr, R ki, R mikr, R miki, R c4r, R c4i, bool wantS, bool wantC,
-    Rules rl, Sink<R> out, int max_cell, int chunk) {
-  using TRI = typename TriOf<R>::T;
+    Sink<R> out, int max_cell, int chunk) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* pcs = reinterpret_cast<R*>(smem_raw);                        // [chunk * max_cell][36]
   R* red = pcs + (size_t)chunk * max_cell * 36;                   // [chunk][nslot][BC_RED]
@@ -690,30 +719,22 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
   Cent<R>* cB = cA + max_cell;
   int* vidA = reinterpret_cast<int*>(cB + max_cell);              // [max_cell][3]
   int* vidB = vidA + 3 * max_cell;
-  // stage one cell's quadrature points, centroid, vertex ids and slot coefficients
+  // stage one cell's quadrature points, centroids, vertex ids and slot
+  // coefficients: contiguous copies of the cell-ordered arrays
   auto stage_cell = [&](int cell, P4<R>* pts, Cent<R>* cen, int* vid, P4<R>* swc) {
     const int b0 = cell_ptr[cell], n = cell_ptr[cell + 1] - b0;
-    for (int q = threadIdx.x; q < n * NREG; q += TT) {
-      const int t = q / NREG, u = q % NREG;
-      const int tau = cell_tri[b0 + t];
-      const TRI T = tri[tau];
-      pts[t * NREG + u] = staged_point(T, rl, u);
-      if (u == 0) {
-        cen[t].set(T);
-        vid[3 * t] = T.vid[0];
-        vid[3 * t + 1] = T.vid[1];
-        vid[3 * t + 2] = T.vid[2];
-        const P4<R>* src = reinterpret_cast<const P4<R>*>(slot_sw) + (size_t)tau * nslot;
-        for (int sl = 0; sl < nslot; ++sl) swc[t * nslot + sl] = src[sl];
-      }
-    }
+    const P4<R>* sp = cd.pts + (size_t)b0 * NREG;
+    const P4<R>* ss = cd.sw + (size_t)b0 * nslot;
+    for (int q = threadIdx.x; q < n * NREG; q += TT) pts[q] = sp[q];
+    for (int q = threadIdx.x; q < n * nslot; q += TT) swc[q] = ss[q];
+    const int* sc = reinterpret_cast<const int*>(cd.cen + b0);
+    int* dc = reinterpret_cast<int*>(cen);
+    constexpr int CW = (int)(sizeof(Cent<R>) / sizeof(int));
+    for (int q = threadIdx.x; q < n * CW; q += TT) dc[q] = sc[q];
+    for (int q = threadIdx.x; q < n * 3; q += TT) vid[q] = cd.vid[(size_t)b0 * 3 + q];
   };
-  auto nvalid = [&](int cell) {
-    const int tv = cell_tri[cell_ptr[cell]];
-    int ns = 0;
-    while (ns < nslot && slot_edge[(size_t)tv * nslot + ns] >= 0) ++ns;
-    return ns;
-  };
+  // the slots of every triangle of a cell are the cell's edges, in one order
+  auto nvalid = [&](int cell) { return cell_edge_ptr[cell + 1] - cell_edge_ptr[cell]; };
   for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
     const BcUnit U = units[uidx];
     const int v = U.v;
@@ -764,6 +785,7 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
           if (isS) {
             R AS_r = 0, AS_i = 0, BS_r = 0, BS_i = 0;
             V3<R> WS_r = {0, 0, 0}, WS_i = {0, 0, 0};
+#pragma unroll 4
             for (int i2 = 0; i2 < n2; ++i2) {
               const P4<R> u = swB[i2 * nslot + sb_i];
               const R sb = u.x;
@@ -782,6 +804,7 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
           } else {
             R AC_r = 0, AC_i = 0;
             V3<R> WC_r = {0, 0, 0}, WC_i = {0, 0, 0};
+#pragma unroll 4
             for (int i2 = 0; i2 < n2; ++i2) {
               const P4<R> u = swB[i2 * nslot + sb_i];
               const R sb = u.x;
@@ -807,6 +830,7 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
           const int it = isS ? q : q - nS3;
           const int sa_i = it / ns2, sb_i = it % ns2;
           R vr = 0, vi = 0;
+#pragma unroll 4
           for (int i1 = 0; i1 < nc; ++i1) {
             const P4<R> u = swA[(c0 + i1) * nslot + sa_i];
             const R sa = u.x;
@@ -836,8 +860,8 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
       for (int q = threadIdx.x; q < ns1 * ns2; q += TT) {
         const int sa_i = q / ns2, sb_i = q % ns2;
         const R* a4 = acc + (size_t)q * 4;
-        const int ea = slot_edge[(size_t)cell_tri[b1] * nslot + sa_i];
-        const int eb = slot_edge[(size_t)cell_tri[b2] * nslot + sb_i];
+        const int ea = cell_edge[cell_edge_ptr[v] + sa_i];
+        const int eb = cell_edge[cell_edge_ptr[w] + sb_i];
         out.add(ea, eb, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
         if (v != w) out.add(eb, ea, wantS, wantC, a4[0], a4[1], a4[2], a4[3]);
       }
@@ -1464,20 +1488,44 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   const R* sw;
   if constexpr (sizeof(R) == 4) { tri = s.d_triF; sw = s.d_slot_swf; }
   else { tri = s.d_triD; sw = s.d_slot_swd; }
-  constexpr int TT = 128;
-  auto kern = a.nreg == 6 ? bc_tile_kernel<R, 6, TT> : bc_tile_kernel<R, 1, TT>;
-  if (int rc = ensure_dyn_smem((const void*)kern, (int)smem)) return rc;
-  int per_sm = 0;
-  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT, smem));
-  const int64_t grid = std::min<int64_t>(nunits, (int64_t)std::max(1, per_sm) * n_sm * 2);
-  const int tok = prof_begin(a.stream, "bc_tile", work);
-  kern<<<(unsigned)grid, TT, smem, a.stream>>>(tri, s.d_slot_edge, sw, s.nslot, s.d_cell_tri_ptr, s.d_cell_tri,
-                                              units, nunits, wlist, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
-                                              g_rules, out, max_cell, chunk);
-  prof_end(a.stream, tok);
+  // cell-ordered copies of the staged data (per launch: the points depend on the rule)
+  const int64_t nct = (int64_t)s.cell_tri.size();
+  const int nreg = a.nreg;
+  CellData<R> cd{};
+  const size_t b_pts = (size_t)nct * nreg * sizeof(P4<R>), b_sw = (size_t)nct * s.nslot * sizeof(P4<R>);
+  const size_t b_cen = (size_t)nct * sizeof(Cent<R>), b_vid = (size_t)nct * 3 * sizeof(int);
+  auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
+  unsigned char* buf = nullptr;
+  CAL_TRY_CUDA(cudaMallocAsync((void**)&buf, r256(b_pts) + r256(b_sw) + r256(b_cen) + r256(b_vid), a.stream));
+  cd.pts = reinterpret_cast<P4<R>*>(buf);
+  cd.sw = reinterpret_cast<P4<R>*>(buf + r256(b_pts));
+  cd.cen = reinterpret_cast<Cent<R>*>(buf + r256(b_pts) + r256(b_sw));
+  cd.vid = reinterpret_cast<int*>(buf + r256(b_pts) + r256(b_sw) + r256(b_cen));
+  if (nreg == 6)
+    bc_cell_prep_kernel<R, 6><<<(unsigned)((nct * 6 + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri,
+                                                                                       nct, g_rules, cd);
+  else
+    bc_cell_prep_kernel<R, 1><<<(unsigned)((nct + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri,
+                                                                                   nct, g_rules, cd);
   note_launch();
-  CAL_TRY_CUDA(cudaGetLastError());
-  return CAL_OK;
+  constexpr int TT = 128;
+  auto kern = nreg == 6 ? bc_tile_kernel<R, 6, TT> : bc_tile_kernel<R, 1, TT>;
+  int rc = ensure_dyn_smem((const void*)kern, (int)smem);
+  int per_sm = 0;
+  if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT, smem) != cudaSuccess)
+    rc = fail(CAL_ECUDA, "bc tile kernel: occupancy query failed");
+  if (!rc) {
+    const int64_t grid = std::min<int64_t>(nunits, (int64_t)std::max(1, per_sm) * n_sm * 2);
+    const int tok = prof_begin(a.stream, "bc_tile", work);
+    kern<<<(unsigned)grid, TT, smem, a.stream>>>(cd, s.nslot, s.d_cell_tri_ptr, s.d_cell_edge_ptr, s.d_cell_edge,
+                                                units, nunits, wlist, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
+                                                out, max_cell, chunk);
+    prof_end(a.stream, tok);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) rc = fail(CAL_ECUDA, "bc tile kernel launch failed");
+  }
+  cudaFreeAsync(buf, a.stream);  // stream-ordered: after the kernel
+  return rc;
 }
 
 int launch_bc_regular_units(const AssembleArgs& a, const void* units, int64_t nunits, const int* wlist, int max_cell,

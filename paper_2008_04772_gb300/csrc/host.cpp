@@ -621,6 +621,8 @@ int upload_space(Space& s, cudaStream_t st) {
   if (s.kind == CAL_BC) {
     if ((rc = upload(&s.d_cell_tri_ptr, s.cell_tri_ptr.data(), s.cell_tri_ptr.size(), st))) return rc;
     if ((rc = upload(&s.d_cell_tri, s.cell_tri.data(), s.cell_tri.size(), st))) return rc;
+    if ((rc = upload(&s.d_cell_edge_ptr, s.cell_edge_ptr.data(), s.cell_edge_ptr.size(), st))) return rc;
+    if ((rc = upload(&s.d_cell_edge, s.cell_edge.data(), s.cell_edge.size(), st))) return rc;
   }
   s.d_sing.assign(s.sing.size(), nullptr);
   for (size_t d = 0; d < s.sing.size(); ++d)
@@ -635,7 +637,7 @@ int upload_space(Space& s, cudaStream_t st) {
 // context (whose stream might already be destroyed) is needed at that point.
 Space::~Space() {
   for (void* p : {(void*)d_triF, (void*)d_triD, (void*)d_slot_edge, (void*)d_slot_swf, (void*)d_slot_swd,
-                  (void*)d_cell_tri_ptr, (void*)d_cell_tri})
+                  (void*)d_cell_tri_ptr, (void*)d_cell_tri, (void*)d_cell_edge_ptr, (void*)d_cell_edge})
     dfree(p, nullptr);
   for (auto p : d_sing) dfree(p, nullptr);
 }

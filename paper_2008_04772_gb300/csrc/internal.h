@@ -136,6 +136,8 @@ struct Space {
   double* d_slot_swd = nullptr;
   int* d_cell_tri_ptr = nullptr;
   int* d_cell_tri = nullptr;
+  int* d_cell_edge_ptr = nullptr;  // BC: slot sl of every triangle of cell v is cell_edge[cell_edge_ptr[v] + sl]
+  int* d_cell_edge = nullptr;
   std::vector<SingPair*> d_sing;
   ~Space();
 };

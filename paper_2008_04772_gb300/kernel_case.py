@@ -6,7 +6,12 @@ sphere (k = 5):
         (one bc_tile_kernel launch plus the FP64 singular-pair launch);
   gemv  an unpreconditioned FP32 solve capped at 3 GMRES iterations (the
         PMCHWT GEMV launches on the stored A blocks);
-  all   both, in this order.
+  gemm  the tensor-core product of the stored 7680 x 7680 complex64 S block
+        with 32 vectors (cal_matvec, 3xTF32 on tcgen05);
+  free  one matrix-free application of the PMCHWT operator (A8) with one vector;
+  solve one complete solve of the benchmark workload (FP32 bulk, full D, tol 1e-5),
+        for the launch list;
+  all   bc, gemv, gemm and free, in this order.
 """
 import sys
 
@@ -22,10 +27,34 @@ def main(which: str = "all") -> None:
         bc = cal.Space(mesh, cal.BC)
         op = cal.assemble(ctx, cal.OP_S | cal.OP_C, 5.0, bc, precision=cal.FP32)
         del op
+    if which in ("all", "gemm"):
+        import numpy as np
+        import torch
+        rwg = cal.Space(mesh, cal.RWG)
+        op = cal.assemble(ctx, cal.OP_S, 5.0, rwg, precision=cal.FP32)
+        n = op.info().cols
+        x = torch.randn((32, 2 * n), dtype=torch.float32, device="cuda")
+        y = torch.zeros((32, 2 * n), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(3):
+            op.matvec(cal.OP_S, x.data_ptr(), y.data_ptr(), nrhs=32)
+        torch.cuda.synchronize()
+        del op, np
+    if which in ("all", "free"):
+        import numpy as np
+        prob = cal.Problem(ctx, mesh, 5.0, 3.17 + 0.01j, opts=cal.solve_opts(precond="none", precision=cal.FP32,
+                                                                            matrix_free=1))
+        x = np.random.default_rng(0).normal(size=(1, 2 * mesh.info().n_edges)).astype(np.complex128)
+        prob.apply(x)
+        del prob
     if which in ("all", "gemv"):
         cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
                          opts=cal.solve_opts(precond="none", precision=cal.FP32, maxit=3, refine=0),
                          allow_not_converged=True)
+    if which == "solve":
+        sol = cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
+                               opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-5))
+        sol.far_field(meshgen.sphere_cut_directions(181))
     print("kernel_case done:", which)
 
 
