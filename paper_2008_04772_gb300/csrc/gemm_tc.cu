@@ -144,8 +144,15 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
   const int64_t nk_full = ktotal - kt0 < (int64_t)ktiles_per_cta ? ktotal - kt0 : (int64_t)ktiles_per_cta;
   const int nk = nk_full > 0 ? (int)nk_full : 0;
   if (nk == 0) return;
-  int tmem_cols = 32;
-  while (tmem_cols < BN) tmem_cols <<= 1;
+  int acc_cols = 32;
+  while (acc_cols < BN) acc_cols <<= 1;
+  // up to 4 accumulators taking the K tiles in turn (at most 256 TMEM columns,
+  // so that two CTAs share an SM): the tensor core adds each MMA step into its
+  // float32 accumulator without a round-to-nearest, so the error grows with the
+  // chain length; the epilogue adds the partial sums
+  const int nacc_max = min(4, 256 / acc_cols) > 1 ? min(4, 256 / acc_cols) : 1;
+  const int nacc = nacc_max < nk ? nacc_max : nk;
+  const int tmem_cols = acc_cols * (nacc <= 1 ? 1 : (nacc <= 2 ? 2 : 4));
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -206,13 +213,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
     if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
+      const uint32_t tacc = tmem + (uint32_t)((kt % nacc) * acc_cols);
       for (int k8 = 0; k8 < BK / 8; ++k8) {
         const uint64_t a_h = smem_desc(Ah(s) + 8 * k8), b_h = smem_desc(Bh(s) + 8 * k8);
         const uint64_t a_l = smem_desc(Al(s) + 8 * k8), b_l = smem_desc(Bl(s) + 8 * k8);
-        const uint32_t first = (kt == 0 && k8 == 0) ? 0u : 1u;
-        mma_tf32(tmem, a_h, b_h, idesc, first);
-        mma_tf32(tmem, a_h, b_l, idesc, 1u);
-        mma_tf32(tmem, a_l, b_h, idesc, 1u);
+        const uint32_t first = (kt < nacc && k8 == 0) ? 0u : 1u;
+        mma_tf32(tacc, a_h, b_h, idesc, first);
+        mma_tf32(tacc, a_h, b_l, idesc, 1u);
+        mma_tf32(tacc, a_l, b_h, idesc, 1u);
       }
       mma_commit(&bars->done[s]);
     }
@@ -227,22 +235,29 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
     // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows), 32 columns per load
     const int64_t row = row0 + warp * 32 + lane;
     for (int c0 = 0; c0 < BN; c0 += 32) {
-      uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0;
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-          "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-            "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-            "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-          : "r"(taddr));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      float sum[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) sum[q] = 0.f;
+      for (int a = 0; a < nacc; ++a) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * acc_cols + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 32; ++q) sum[q] += __uint_as_float(v[q]);
+      }
       if (row < M) {
         float* zr = Z + row * NB + c0;
 #pragma unroll
         for (int q = 0; q < 32; ++q)
-          if (c0 + q < NB) atomicAdd(zr + q, __uint_as_float(v[q]));
+          if (c0 + q < NB) atomicAdd(zr + q, sum[q]);
       }
     }
   } else if (tid == 0) {
@@ -254,6 +269,172 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
   __syncthreads();
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+// ---------------------------------------------------------------------------
+// The same product with both operands split beforehand (A = Ah + Al stored
+// once per operator, B = Bh + Bl per call), so no thread touches a tile: one
+// thread issues the TMA loads of a ring of stages, one thread issues the MMAs
+// (3 per K step into up to 4 round-robin accumulators) and commits each stage
+// back to the producer, and all warps run the epilogue. STAGES_S stages of
+// (Ah, Al, Bh, Bl) tiles are in flight.
+// ---------------------------------------------------------------------------
+constexpr int STAGES_S = 3;
+
+struct __align__(8) BarsS {
+  uint64_t full[STAGES_S];
+  uint64_t empty[STAGES_S];
+  uint32_t tmem_base;
+  uint32_t fail;
+  int32_t issued;  // K tiles whose loads were issued
+};
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_split_kernel(
+    const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
+    const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, float* __restrict__ Z,
+    int64_t M, int NB, int BN, int64_t K, int ktiles_per_cta, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int a_bytes = BM * BK * 4, b_bytes = BN * BK * 4;
+  const int stage_bytes = 2 * (a_bytes + b_bytes);
+  BarsS* bars = reinterpret_cast<BarsS*>(base + STAGES_S * stage_bytes);
+  auto Ah = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes); };
+  auto Al = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + a_bytes); };
+  auto Bh = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + 2 * a_bytes); };
+  auto Bl = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + 2 * a_bytes + b_bytes); };
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int64_t ktotal = (K + BK - 1) / BK;
+  const int64_t kt0 = (int64_t)blockIdx.y * ktiles_per_cta;
+  const int64_t nk_full = ktotal - kt0 < (int64_t)ktiles_per_cta ? ktotal - kt0 : (int64_t)ktiles_per_cta;
+  const int nk = nk_full > 0 ? (int)nk_full : 0;
+  if (nk == 0) return;
+  int acc_cols = 32;
+  while (acc_cols < BN) acc_cols <<= 1;
+  const int nacc_max = min(4, 512 / acc_cols) > 1 ? min(4, 512 / acc_cols) : 1;
+  const int nacc = nacc_max < nk ? nacc_max : nk;
+  const int tmem_cols = acc_cols * (nacc <= 1 ? 1 : (nacc <= 2 ? 2 : 4));
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES_S; ++s) {
+      mbar_init(&bars->full[s], 1);
+      mbar_init(&bars->empty[s], 1);
+    }
+    bars->fail = 0;
+    bars->issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tmem_base)),
+                 "r"(tmem_cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = bars->tmem_base;
+  const uint32_t idesc = instr_desc(BN);
+  const unsigned tx_bytes = (unsigned)(2 * (a_bytes + b_bytes));
+
+  if (tid == 0) {
+    // producer: stage s is free again once the MMAs of the tile that last used it completed
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES_S;
+      if (kt >= STAGES_S && !mbar_wait(&bars->empty[s], ((kt / STAGES_S) - 1) & 1)) {
+        atomicOr(&bars->fail, 1u);
+        break;
+      }
+      if (*(volatile uint32_t*)&bars->fail) break;
+      const int x = (int)((kt0 + kt) * BK);
+      mbar_expect_tx(&bars->full[s], tx_bytes);
+      tma_load_2d(Ah(s), &mapAh, &bars->full[s], x, (int)row0);
+      tma_load_2d(Al(s), &mapAl, &bars->full[s], x, (int)row0);
+      tma_load_2d(Bh(s), &mapBh, &bars->full[s], x, 0);
+      tma_load_2d(Bl(s), &mapBl, &bars->full[s], x, 0);
+      *(volatile int32_t*)&bars->issued = kt + 1;
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    int last = -1;  // last tile whose MMAs were committed
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % STAGES_S;
+      if (!mbar_wait(&bars->full[s], (kt / STAGES_S) & 1)) {
+        atomicOr(&bars->fail, 1u);
+        break;
+      }
+      if (*(volatile uint32_t*)&bars->fail) break;
+      last = kt;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tacc = tmem + (uint32_t)((kt % nacc) * acc_cols);
+#pragma unroll
+      for (int k8 = 0; k8 < BK / 8; ++k8) {
+        const uint64_t a_h = smem_desc(Ah(s) + 8 * k8), b_h = smem_desc(Bh(s) + 8 * k8);
+        const uint64_t a_l = smem_desc(Al(s) + 8 * k8), b_l = smem_desc(Bl(s) + 8 * k8);
+        const uint32_t first = (kt < nacc && k8 == 0) ? 0u : 1u;
+        mma_tf32(tacc, a_h, b_h, idesc, first);
+        mma_tf32(tacc, a_h, b_l, idesc, 1u);
+        mma_tf32(tacc, a_l, b_h, idesc, 1u);
+      }
+      mma_commit(&bars->empty[s]);
+    }
+    // the commit of the last issued tile covers every earlier MMA; wait for it
+    // (bounded) also after a failure, before the TMEM is returned
+    if (last >= 0 && !mbar_wait(&bars->empty[last % STAGES_S], (last / STAGES_S) & 1)) atomicOr(&bars->fail, 1u);
+    if (last != nk - 1) atomicOr(&bars->fail, 1u);
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (!bars->fail) {
+    const int64_t row = row0 + warp * 32 + lane;
+    for (int c0 = 0; c0 < BN; c0 += 32) {
+      float sum[32];
+#pragma unroll
+      for (int q = 0; q < 32; ++q) sum[q] = 0.f;
+      for (int a = 0; a < nacc; ++a) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * acc_cols + c0);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
+              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int q = 0; q < 32; ++q) sum[q] += __uint_as_float(v[q]);
+      }
+      if (row < M) {
+        float* zr = Z + row * NB + c0;
+#pragma unroll
+        for (int q = 0; q < 32; ++q)
+          if (c0 + q < NB) atomicAdd(zr + q, sum[q]);
+      }
+    }
+  } else if (tid == 0) {
+    atomicOr(err, 1);
+    // bounded drain of the loads that were issued, so no copy lands after exit
+    const int issued = bars->issued;
+    for (int kt = (issued > STAGES_S ? issued - STAGES_S : 0); kt < issued; ++kt)
+      mbar_wait(&bars->full[kt % STAGES_S], (kt / STAGES_S) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+}
+
+__global__ void split_tf32_kernel(const float* __restrict__ x, float* __restrict__ hi, float* __restrict__ lo,
+                                  int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) {
+    const float v = x[i], h = tf32_round(v);
+    hi[i] = h;
+    lo[i] = v - h;
+  }
 }
 
 // real embedding of the right-hand sides of one block (see the file header):
@@ -372,6 +553,45 @@ int gemm_tf32x3(const float* A, int64_t M, int64_t K, const float* Bt, int NB, f
   return CAL_OK;
 }
 
+int split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
+  if (n <= 0) return CAL_OK;
+  split_tf32_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, hi, lo, n);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// Z[M][NB] = (Ah + Al)[M][K] (Bh + Bl)[NB][K]^T (Z is zeroed here), 3xTF32
+int gemm_tf32x3_split(const float* Ah, const float* Al, int64_t M, int64_t K, const float* Bh, const float* Bl, int NB,
+                      float* Z, int* d_err, int n_sm, cudaStream_t st) {
+  if (NB < 16 || NB > 256 || NB % 16) return fail(CAL_EINVAL, "gemm: NB must be a multiple of 16 in [16, 256]");
+  for (const float* p : {Ah, Al, Bh, Bl})
+    if ((uintptr_t)p % 16) return fail(CAL_EINVAL, "gemm: operands not 16-byte aligned");
+  if ((K * 4) % 16) return fail(CAL_EINVAL, "gemm: rows not 16-byte aligned");
+  CUtensorMap mAh, mAl, mBh, mBl;
+  int rc;
+  if ((rc = make_map(&mAh, Ah, K, M, BM)) || (rc = make_map(&mAl, Al, K, M, BM)) ||
+      (rc = make_map(&mBh, Bh, K, NB, NB)) || (rc = make_map(&mBl, Bl, K, NB, NB)))
+    return rc;
+  CAL_TRY_CUDA(cudaMemsetAsync(Z, 0, (size_t)M * NB * sizeof(float), st));
+  const int64_t mt = (M + BM - 1) / BM;
+  const int64_t ktotal = (K + BK - 1) / BK;
+  const int smem = STAGES_S * 2 * (BM * BK * 4 + NB * BK * 4) + (int)sizeof(BarsS) + 1024;
+  if (smem > 227 * 1024) return fail(CAL_EINVAL, "gemm: %d columns do not fit the split-operand pipeline", NB);
+  if (int rc2 = ensure_dyn_smem((const void*)gemm_tf32x3_split_kernel, smem)) return rc2;
+  // one CTA per SM; about two waves of (row tile, K slice) units
+  int64_t split = std::max<int64_t>(1, std::min<int64_t>(ktotal, (2 * (int64_t)n_sm + mt - 1) / mt));
+  const int per = (int)((ktotal + split - 1) / split);
+  split = (ktotal + per - 1) / per;
+  const int tok = prof_begin(st, "gemm_tc", 2.0 * 3.0 * (double)M * K * NB);
+  gemm_tf32x3_split_kernel<<<dim3((unsigned)mt, (unsigned)split), THREADS, smem, st>>>(mAh, mAl, mBh, mBl, Z, M, NB,
+                                                                                      NB, K, per, d_err);
+  prof_end(st, tok);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
 template <typename VT>
 int embed_rhs(const VT* X, int nrhs, int64_t n_total, int64_t col_off, int64_t ncols, float* Bt, int NB,
               cudaStream_t st) {
@@ -402,7 +622,7 @@ __global__ void unembed_kernel(const float* __restrict__ Z, int64_t rows, int NB
 // Y[nrhs][rows] = X^T applied: plain complex product of a float32 dense operator
 // with nrhs vectors x [nrhs][cols] through the tensor-core path
 int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2* x, float2* y, int nrhs, int n_sm,
-                    cudaStream_t st) {
+                    cudaStream_t st, const float* Xh, const float* Xl) {
   const int npair = (nrhs + 1) / 2;  // the embedding works on (x1, x2) column pairs
   const int NB = ((4 * npair + 15) / 16) * 16;
   if (NB > 256 || cols % 2) return fail(CAL_EINVAL, "multi-vector product: unsupported size");
@@ -421,7 +641,17 @@ int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2*
     xin = xp;
   }
   int rc = embed_rhs<float2>(xin, npair, cols, 0, cols, Bt, NB, st);
-  if (!rc) rc = gemm_tf32x3(reinterpret_cast<const float*>(Xop), rows, 2 * cols, Bt, NB, Z, err, n_sm, st);
+  float* Bs = nullptr;  // split operand: [2][NB][2 cols]
+  const bool split = Xh && Xl && NB <= 128;
+  if (!rc && split) {
+    if (cudaMallocAsync((void**)&Bs, (size_t)2 * NB * 2 * cols * sizeof(float), st) != cudaSuccess)
+      rc = fail(CAL_ENOMEM, "multi-vector product: cannot allocate the split operand");
+    else
+      rc = split_tf32(Bt, Bs, Bs + (size_t)NB * 2 * cols, (int64_t)NB * 2 * cols, st);
+  }
+  if (!rc)
+    rc = split ? gemm_tf32x3_split(Xh, Xl, rows, 2 * cols, Bs, Bs + (size_t)NB * 2 * cols, NB, Z, err, n_sm, st)
+               : gemm_tf32x3(reinterpret_cast<const float*>(Xop), rows, 2 * cols, Bt, NB, Z, err, n_sm, st);
   if (!rc) {
     unembed_kernel<<<dim3((unsigned)((rows + 255) / 256), nrhs), 256, 0, st>>>(Z, rows, NB, nrhs, y);
     note_launch();
@@ -430,6 +660,7 @@ int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2*
   cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
   cudaStreamSynchronize(st);
   cudaFreeAsync(Bt, st);
+  if (Bs) cudaFreeAsync(Bs, st);
   cudaFreeAsync(Z, st);
   cudaFreeAsync(err, st);
   if (xp) cudaFreeAsync(xp, st);

@@ -645,6 +645,7 @@ Space::~Space() {
 Op::~Op() {
   dfree(d_S, nullptr);
   dfree(d_C, nullptr);
+  for (void* p : {(void*)d_Sh, (void*)d_Sl, (void*)d_Ch, (void*)d_Cl}) dfree(p, nullptr);
   dfree(d_rowptr, nullptr);
   dfree(d_col, nullptr);
 }

@@ -79,7 +79,7 @@ int64_t resident_bytes(const Mesh& m, const std::vector<double>& area_m, const c
   return b;
 }
 
-int64_t solve_bytes(const Mesh& m, const cal_solve_opts& o, int64_t nrhs, int64_t ndir) {
+int64_t solve_bytes(const Mesh& m, const cal_solve_opts& o, int64_t nrhs, int64_t ndir, int64_t resident) {
   const int64_t N = m.ne, n2 = 2 * N, z = 16;
   const int64_t nb = std::min<int64_t>(nrhs, kMaxBatch);
   const int64_t mk = std::max(1, std::min(o.restart, o.maxit));
@@ -90,7 +90,8 @@ int64_t solve_bytes(const Mesh& m, const cal_solve_opts& o, int64_t nrhs, int64_
   b += 3 * nb * n2 * z;                           // work vectors of the batch
   if (o.precision != CAL_FP64 && nb >= 4) {
     const int64_t NB = ((4 * nb + 15) / 16) * 16;
-    b += NB * 2 * N * 4 + 2 * N * NB * 4;  // tensor-core operand and outputs
+    b += 3 * NB * 2 * N * 4 + 2 * N * NB * 4;  // tensor-core operands (and their split) and outputs
+    b += 2 * resident;                         // split copies of the dense blocks
   }
   if (o.precond != CAL_PRECOND_NONE) {
     const int64_t c = o.precision == CAL_FP64 ? 16 : 8;
@@ -242,7 +243,7 @@ struct cal_queue {
       }
       int64_t ndir = 0;
       for (Request* g : group) ndir = std::max(ndir, g->ndir);
-      const int64_t need = solve_bytes(r->mesh, r->opts, cols, ndir) + (hit ? 0 : r->fp.resident);
+      const int64_t need = solve_bytes(r->mesh, r->opts, cols, ndir, r->fp.resident) + (hit ? 0 : r->fp.resident);
       if (reserved + need > budget && !evict_for(need, hit)) continue;
       // admitted
       if (i > 0) ++head_skips;
@@ -413,7 +414,8 @@ int cal_request_footprint(const cal_request* req, int64_t* resident, int64_t* so
   if (req->domain) d.assign(req->domain, req->domain + req->nt);
   const std::vector<double> area = scatterer_areas(v, t, d, m.M);
   if (resident) *resident = resident_bytes(m, area, req->opts);
-  if (solve) *solve = solve_bytes(m, req->opts, req->nrhs, std::max<int64_t>(req->ndir, 0));
+  const int64_t res = resident_bytes(m, area, req->opts);
+  if (solve) *solve = solve_bytes(m, req->opts, req->nrhs, std::max<int64_t>(req->ndir, 0), res);
   return CAL_OK;
 }
 
@@ -485,7 +487,7 @@ int cal_queue_submit(cal_queue* q, const cal_request* req, int64_t* ticket) {
   append_bytes(id, &o.near_cutoff_P, 1);
   const std::vector<double> area = scatterer_areas(r->verts, r->tris, r->domain, M);
   r->fp.resident = resident_bytes(r->mesh, area, o);
-  r->fp.solve = solve_bytes(r->mesh, o, r->nrhs, r->ndir);
+  r->fp.solve = solve_bytes(r->mesh, o, r->nrhs, r->ndir, r->fp.resident);
   if (r->fp.resident + r->fp.solve > q->budget)
     return fail(CAL_ENOMEM, "cal_queue_submit: request needs ~%lld bytes, above the budget of %lld",
                 (long long)(r->fp.resident + r->fp.solve), (long long)q->budget);
