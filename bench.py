@@ -37,6 +37,9 @@ sys.path.insert(0, ROOT)
 WORKLOAD = {"name": "sphere5120_k5_D_dense", "level": 4, "k": 5.0, "eps": 3.17 + 0.01j,
             "tol": 1e-5, "restart": 200}
 METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5)"
+# dram__bytes_read.sum + dram__bytes_write.sum of one bc_tile launch (exterior pass of
+# the workload), from the ncu capture summarised in profiles/; None once the kernel changes
+BC_TILE_TRAFFIC = 2.870043e9 + 2.759060e9
 
 
 def _env_int(name, default):
@@ -264,9 +267,12 @@ def run_ours(args, rank, world):
                              "note": "singular pairs also in float32 (CAL_FP32_ALL)"},
         "gpu_launches": int(n_launch),
         "kernels_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": "bc_tile_kernel<float,6>",
+        "roofline": {"bound": "alu", "kernel": "bc_tile_kernel<float,6,128>",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
-                     "frac": achieved / peak if peak else None, "traffic": None,
+                     "frac": achieved / peak if peak else None, "traffic": BC_TILE_TRAFFIC,
+                     "traffic_note": "dram read+write bytes of one exterior launch, one ncu capture "
+                                     "(profiles/bc_tile_kernel_sphere5120.md); the per-launch work is "
+                                     f"{bc['units'] / max(bc['launches'], 1) / 1e9:.1f} G evaluations",
                      "peak_source": f"derived: {n_sm} SMs x 3.05 eval/clk x {sm_max:.0f} MHz"},
         "clocks": clocks,
         "e2e": {"value": 1.0 / statistics.median(t_e2e), "unit": "solves/s",
@@ -274,6 +280,8 @@ def run_ours(args, rank, world):
     }
     if args.multirhs:
         out["multi_rhs"] = run_multirhs(dev)
+    if args.matrix_free:
+        out["matrix_free_vs_stored"] = run_matrix_free(dev)
     if args.serving:
         out["serving"] = run_serving(dev)
     if args.cpu_baseline:
@@ -336,6 +344,63 @@ def run_multirhs(dev):
         "columns_N": N,
         "kernels": fam,
     }
+
+
+MATRIX_FREE = {"name": "aggregate8x1000_kD40_Di_near3h", "prisms": 8, "tris_per_prism": 1000, "seed": 0,
+               "k": 40.0, "eps": 3.17 + 0.01j, "precond": "Di", "near_cutoff_P": 3.0, "tol": 1e-5}
+
+
+def run_matrix_free(dev):
+    """Stored versus matrix-free A on a scaled-down version of the largest aggregate:
+    the same solve both ways, with the time per operator application."""
+    import ctypes
+
+    import torch
+
+    from paper_2008_04772_gb300 import cal, meshgen
+    W = MATRIX_FREE
+    L = cal.lib()
+    ctx = cal.Context(dev)
+    m = meshgen.prism_aggregate(W["prisms"], W["tris_per_prism"], seed=W["seed"], diameter=1.0, gap=0.05)
+    mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    inc = meshgen.plane_wave_x_along_z()
+    dirs = meshgen.fibonacci_directions(64)
+    out = {"workload": W["name"], "triangles": int(len(m.tris)), "unknowns": 2 * mesh.info().n_edges,
+           "k_ext": W["k"], "preconditioner": f"{W['precond']} near-field {W['near_cutoff_P']}h"}
+    far = {}
+    for free in (0, 1):
+        opts = cal.solve_opts(precond=W["precond"], precision=cal.FP32, tol=W["tol"],
+                              near_cutoff_P=W["near_cutoff_P"], matrix_free=free)
+        L.cal_profile_enable(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        sol = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], inc, opts=opts)
+        far[free] = sol.far_field(dirs)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        fam = {}
+        for name in ("rwg_free", "pair_gemv", "pair_spmv", "rwg_regular", "singular"):
+            n_, ms_, u_ = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+            L.cal_profile_read(name.encode(), ctypes.byref(n_), ctypes.byref(ms_), ctypes.byref(u_))
+            fam[name] = (n_.value, ms_.value, u_.value)
+        L.cal_profile_enable(0)
+        info = sol.info()
+        key = "matrix_free" if free else "stored"
+        out[key] = {"seconds": t, "iterations": int(info.iterations), "matvecs": int(info.matvecs),
+                    "bytes_A_gb": info.bytes_A / 1e9, "phase_s": {"assemble_A": info.t_assemble_A,
+                                                                 "assemble_P": info.t_assemble_P,
+                                                                 "solve": info.t_solve},
+                    "kernels_ms": {k: round(v[1], 3) for k, v in fam.items() if v[0]}}
+        if free and fam["rwg_free"][0]:
+            n_, ms_, u_ = fam["rwg_free"]
+            n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+            peak = _alu_peak(n_sm, _measured_peaks().get("sm_max_mhz", 2070.0))
+            out[key]["rwg_free"] = {"launches": n_, "ms_per_launch": ms_ / n_,
+                                    "roofline": {"bound": "alu", "achieved": u_ / (ms_ / 1e3) / 1e9,
+                                                 "peak": peak / 1e9, "unit": "Geval/s",
+                                                 "frac": u_ / (ms_ / 1e3) / peak}}
+    out["far_field_rel_diff"] = float(np.linalg.norm(far[1] - far[0]) / np.linalg.norm(far[0]))
+    return out
 
 
 SERVING = {"name": "aggregate_requests_scaled", "requests": 48, "seed": 0, "prisms": (1, 8),
@@ -524,6 +589,8 @@ def main():
                     help="skip the request-queue (continuous batching) run")
     ap.add_argument("--no-multirhs", dest="multirhs", action="store_false",
                     help="skip the 32-direction aggregate run")
+    ap.add_argument("--no-matrix-free", dest="matrix_free", action="store_false",
+                    help="skip the stored versus matrix-free comparison")
     args = ap.parse_args()
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
