@@ -873,7 +873,7 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
 // A4: singular pairs by Sauter–Schwab rules in float64, one warp per ordered
 // pair; the q^4 Gauss points of all sub-regions are spread over the lanes.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ss_map(int cls, int r, double xi, double e1, double e2, double e3,
+__host__ __device__ __forceinline__ void ss_map(int cls, int r, double xi, double e1, double e2, double e3,
                                        double* xh, double* yh, double& jac) {
   // maps of [0,1]^4 onto pairs of points of the reference triangle
   // {0 <= s2 <= s1 <= 1}; shared vertex at (0,0), shared edge (0,0)-(1,0)
@@ -1197,6 +1197,74 @@ __device__ __forceinline__ void radial_sums(const double* gx, const double* gw, 
   }
 }
 
+// Reference-coordinate moments MG, Mg (18 reals each: (re, im) of the nine
+// monomials) -> centroid-relative moments -> pair coefficients -> entries of
+// the (test slot, trial slot) combinations q = first, first + step, ...
+template <typename RO>
+__device__ __forceinline__ void sing_emit(const double* MG, const double* Mg, const V3<double>* Q1,
+                                          const V3<double>* Q2, const V3<double>& ea, const V3<double>& eb,
+                                          const V3<double>& ec, const V3<double>& ed, const V3<double>& D,
+                                          const SingPair& sp, const int* __restrict__ slot_edge,
+                                          const double* __restrict__ slot_sw, int nslot, double mikr, double miki,
+                                          double c4r, double c4i, bool wantS, bool doC, int first, int step,
+                                          const Sink<RO>& out) {
+  const int cls = sp.cls;
+  // x = q0 + x0 a + x1 b, y = p0 + y0 c + y1 d
+  const V3<double> q0 = Q1[0], p0 = Q2[0];
+  const V3<double> vx[3] = {q0, ea, eb};  // factors of 1, x0, x1
+  const V3<double> vy[3] = {p0, ec, ed};  // factors of 1, y0, y1
+  // monomial index of (i, j): i, j in {0: 1, 1: first, 2: second}
+  auto mix = [](int i, int j) { return i == 0 ? (j == 0 ? 0 : 2 + j) : (j == 0 ? i : 2 * i + j + 2); };
+  Mom<double> m;
+  m.zero();
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {  // re, im (unrolled: the moment arrays stay in registers)
+    double G0 = MG[h], g0 = Mg[h];
+    V3<double> Gx = {0, 0, 0}, Gy = {0, 0, 0}, gx = {0, 0, 0}, gy = {0, 0, 0}, gxy = {0, 0, 0};
+    double Gxy = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const double Mxi = MG[2 * mix(i, 0) + h], mxi = Mg[2 * mix(i, 0) + h];
+      Gx = {Gx.x + vx[i].x * Mxi, Gx.y + vx[i].y * Mxi, Gx.z + vx[i].z * Mxi};
+      gx = {gx.x + vx[i].x * mxi, gx.y + vx[i].y * mxi, gx.z + vx[i].z * mxi};
+      const double Myi = MG[2 * mix(0, i) + h], myi = Mg[2 * mix(0, i) + h];
+      Gy = {Gy.x + vy[i].x * Myi, Gy.y + vy[i].y * Myi, Gy.z + vy[i].z * Myi};
+      gy = {gy.x + vy[i].x * myi, gy.y + vy[i].y * myi, gy.z + vy[i].z * myi};
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const double Mij = MG[2 * mix(i, j) + h], mij = Mg[2 * mix(i, j) + h];
+        Gxy += dot3(vx[i], vy[j]) * Mij;
+        const V3<double> cxy = cross3(vx[i], vy[j]);
+        gxy = {gxy.x + cxy.x * mij, gxy.y + cxy.y * mij, gxy.z + cxy.z * mij};
+      }
+    }
+    if (h == 0) {
+      m.G0r = G0; m.Gxr = Gx; m.Gyr = Gy; m.Gxyr = Gxy;
+      m.g0r = g0; m.gxr = gx; m.gyr = gy; m.gxyr = gxy;
+    } else {
+      m.G0i = G0; m.Gxi = Gx; m.Gyi = Gy; m.Gxyi = Gxy;
+      m.g0i = g0; m.gxi = gx; m.gyi = gy; m.gxyi = gxy;
+    }
+  }
+  double pc[36];
+  pair_coeffs(m, D, pc);
+  for (int q = first; q < nslot * nslot; q += step) {
+    const int a = q / nslot, b = q % nslot;
+    const int e1 = slot_edge[(size_t)sp.t1 * nslot + a];
+    const int e2 = slot_edge[(size_t)sp.t2 * nslot + b];
+    if (e1 < 0 || e2 < 0) continue;
+    const double* swa = slot_sw + ((size_t)sp.t1 * nslot + a) * 4;
+    const double* swb = slot_sw + ((size_t)sp.t2 * nslot + b) * 4;
+    const V3<double> wa = {swa[1], swa[2], swa[3]}, wb = {swb[1], swb[2], swb[3]};
+    double Sr = 0, Si = 0, Cr = 0, Ci = 0;
+    entry_from_pc(pc, swa[0], wa, swb[0], wb, mikr, miki, c4r, c4i, wantS, doC, Sr, Si, Cr, Ci);
+    out.add(e1, e2, wantS, doC, Sr, Si, Cr, Ci);
+    // vertex-sharing pairs are stored once (t1 < t2): the two-region rule maps
+    // onto itself when the triangles swap roles, so (t2, t1) gives the transpose
+    if (cls == 1) out.add(e2, e1, wantS, doC, Sr, Si, Cr, Ci);
+  }
+}
+
 // Every Sauter–Schwab map is x = xi f(e), y = xi g(e) in the reference
 // coordinates of the two triangles (shared vertex at the origin of both), and
 // its jacobian is xi^3 J(e). So x - y = xi rho(e), the 1/r of G cancels two
@@ -1284,61 +1352,260 @@ __global__ void __launch_bounds__(128) singular_kernel(
     MG[q] = v;
     Mg[q] = u;
   }
-  // back to the centroid-relative moments: x = q0 + x0 a + x1 b, y = p0 + y0 c + y1 d
-  const V3<double> q0 = Q1[0], p0 = Q2[0];
-  const V3<double> vx[3] = {q0, ea, eb};  // factors of 1, x0, x1
-  const V3<double> vy[3] = {p0, ec, ed};  // factors of 1, y0, y1
-  // monomial index of (i, j): i, j in {0: 1, 1: first, 2: second}
-  auto mix = [](int i, int j) { return i == 0 ? (j == 0 ? 0 : 2 + j) : (j == 0 ? i : 2 * i + j + 2); };
-  Mom<double> m;
-  m.zero();
+  sing_emit(MG, Mg, Q1, Q2, ea, eb, ec, ed, D, sp, slot_edge, slot_sw, nslot, mikr, miki, c4r, c4i, wantS, doC,
+            lane, 32, out);
+}
+
+// ---------------------------------------------------------------------------
+// A4 with float32 output: one lane per pair, and the kernel split into a
+// static and a dynamic part,
+//   G = 1/(4 pi r) + (e^{ikr} - 1)/(4 pi r),
+//   g = -1/(4 pi r^3) + ((ikr - 1) e^{ikr} + 1)/(4 pi r^3).
+// The static parts carry the singularity and, for g, the large moments that
+// cancel when they are combined into entries: they are summed in float64, and
+// their radial sums are the rule's own sums of xi^d (no transcendental
+// function). The dynamic parts are smooth (O(kr) and O((kr)^2) relative to
+// the static ones); they are evaluated in float32 with relative accuracy
+// (series of e^z - 1 - z for |z| <= 2) and summed in float32 per region, then
+// in float64. Both use the same quadrature points and weights as the float64
+// kernel, whose result this reproduces to float32 output accuracy.
+// ---------------------------------------------------------------------------
+struct SsPt {                      // one (region, e1, e2, e3) direction at xi = 1
+  double x0, x1, y0, y1;           // reference coordinates of x and y
+  double m00, m01, m10, m11;       // x0 y0, x0 y1, x1 y0, x1 y1
+  double w;                        // gw(e1) gw(e2) gw(e3) J(e)
+  float fx0, fx1, fy0, fy1, fw, pad;
+};
+
+struct SsRadial {
+  double sG[3], sg[3];             // sum_j w_j xi_j^{2+d}, -sum_j w_j xi_j^d (d = 0, 1, 2)
+  float xi[16], wG[16][3], wg[16][3];
+  int ng;
+};
+
+// v = e^z - 1 - z in float32 with relative accuracy. |z| <= 2: Taylor series
+// z^2 sum_{m=0..12} z^m / (m + 2)!, the first omitted term below 2e-8 |v|;
+// otherwise e^z from expf and sincosf (|v| > 1 there).
+__device__ __forceinline__ void expm1mz_f32(float zr, float zi, float& vr, float& vi) {
+  if (zr * zr + zi * zi <= 4.0f) {
+    constexpr float c[13] = {1.0f / 2, 1.0f / 6, 1.0f / 24, 1.0f / 120, 1.0f / 720, 1.0f / 5040, 1.0f / 40320,
+                             1.0f / 362880, 1.0f / 3628800, 1.0f / 39916800, 1.0f / 479001600,
+                             1.0f / 6227020800.0f, 1.0f / 87178291200.0f};
+    float pr = c[12], pi = 0.0f;
 #pragma unroll
-  for (int h = 0; h < 2; ++h) {  // re, im (unrolled: the moment arrays stay in registers)
-    double G0 = MG[h], g0 = Mg[h];
-    V3<double> Gx = {0, 0, 0}, Gy = {0, 0, 0}, gx = {0, 0, 0}, gy = {0, 0, 0}, gxy = {0, 0, 0};
-    double Gxy = 0.0;
+    for (int m = 11; m >= 0; --m) {
+      const float tr = fmaf(pr, zr, fmaf(-pi, zi, c[m]));
+      pi = fmaf(pr, zi, pi * zr);
+      pr = tr;
+    }
+    const float z2r = (zr - zi) * (zr + zi), z2i = 2.0f * zr * zi;
+    vr = fmaf(z2r, pr, -z2i * pi);
+    vi = fmaf(z2r, pi, z2i * pr);
+  } else {
+    const float e = expf(zr);
+    float sn, cs;
+    sincosf(zi, &sn, &cs);
+    vr = fmaf(e, cs, -1.0f) - zr;
+    vi = fmaf(e, sn, -zi);
+  }
+}
+
+// dynamic radial sums over the Gauss nodes xi_j (r = xi_j rho, z = ikr):
+//   SG_d += w_j xi_j^{2+d} (e^z - 1),  Sg_d += w_j xi_j^d ((z - 1) e^z + 1)
+template <int NG>
+__device__ __forceinline__ void dyn_radial(const SsRadial& rs, float rho, float kr, float ki, bool doC, float* SG,
+                                           float* Sg) {
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      const double Mxi = MG[2 * mix(i, 0) + h], mxi = Mg[2 * mix(i, 0) + h];
-      Gx = {Gx.x + vx[i].x * Mxi, Gx.y + vx[i].y * Mxi, Gx.z + vx[i].z * Mxi};
-      gx = {gx.x + vx[i].x * mxi, gx.y + vx[i].y * mxi, gx.z + vx[i].z * mxi};
-      const double Myi = MG[2 * mix(0, i) + h], myi = Mg[2 * mix(0, i) + h];
-      Gy = {Gy.x + vy[i].x * Myi, Gy.y + vy[i].y * Myi, Gy.z + vy[i].z * Myi};
-      gy = {gy.x + vy[i].x * myi, gy.y + vy[i].y * myi, gy.z + vy[i].z * myi};
+  for (int j = 0; j < (NG > 0 ? NG : 16); ++j) {
+    if (NG == 0 && j >= rs.ng) break;
+    const float t = rho * rs.xi[j];
+    const float zr = -ki * t, zi = kr * t;
+    float vr, vi;
+    expm1mz_f32(zr, zi, vr, vi);
+    const float ur = vr + zr, ui = vi + zi;  // e^z - 1
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const double Mij = MG[2 * mix(i, j) + h], mij = Mg[2 * mix(i, j) + h];
-        Gxy += dot3(vx[i], vy[j]) * Mij;
-        const V3<double> cxy = cross3(vx[i], vy[j]);
-        gxy = {gxy.x + cxy.x * mij, gxy.y + cxy.y * mij, gxy.z + cxy.z * mij};
+    for (int d = 0; d < 3; ++d) {
+      SG[2 * d] = fmaf(rs.wG[j][d], ur, SG[2 * d]);
+      SG[2 * d + 1] = fmaf(rs.wG[j][d], ui, SG[2 * d + 1]);
+    }
+    if (doC) {
+      // (z - 1) e^z + 1 = z (e^z - 1) - (e^z - 1 - z)
+      const float fr = fmaf(zr, ur, -fmaf(zi, ui, vr)), fi = fmaf(zr, ui, fmaf(zi, ur, -vi));
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        Sg[2 * d] = fmaf(rs.wg[j][d], fr, Sg[2 * d]);
+        Sg[2 * d + 1] = fmaf(rs.wg[j][d], fi, Sg[2 * d + 1]);
       }
     }
-    if (h == 0) {
-      m.G0r = G0; m.Gxr = Gx; m.Gyr = Gy; m.Gxyr = Gxy;
-      m.g0r = g0; m.gxr = gx; m.gyr = gy; m.gxyr = gxy;
-    } else {
-      m.G0i = G0; m.Gxi = Gx; m.Gyi = Gy; m.Gxyi = Gxy;
-      m.g0i = g0; m.gxi = gx; m.gyi = gy; m.gxyi = gxy;
+  }
+}
+
+template <int NG>
+__global__ void __launch_bounds__(128) singular_split_kernel(
+    const TriD* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
+    const int* __restrict__ slot_edge, const double* __restrict__ slot_sw, int nslot, double kr,
+    double ki, double mikr, double miki, double c4r, double c4i, bool wantS, bool wantC,
+    const SsPt* __restrict__ tab, SsRadial rs, Sink<float> out) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const SingPair sp = pairs[p];
+  const int cls = sp.cls;
+  const bool doC = wantC && cls != 3;  // flat identical panels: C vanishes
+  V3<double> ea, eb, ec, ed;
+  {
+    const TriD& A = tri[sp.t1];
+    const TriD& B = tri[sp.t2];
+    const int a0 = sp.o1[0], a1 = sp.o1[1], a2 = sp.o1[2], b0 = sp.o2[0], b1 = sp.o2[1], b2 = sp.o2[2];
+    ea = {A.off[a1][0] - A.off[a0][0], A.off[a1][1] - A.off[a0][1], A.off[a1][2] - A.off[a0][2]};
+    eb = {A.off[a2][0] - A.off[a1][0], A.off[a2][1] - A.off[a1][1], A.off[a2][2] - A.off[a1][2]};
+    ec = {B.off[b1][0] - B.off[b0][0], B.off[b1][1] - B.off[b0][1], B.off[b1][2] - B.off[b0][2]};
+    ed = {B.off[b2][0] - B.off[b1][0], B.off[b2][1] - B.off[b1][1], B.off[b2][2] - B.off[b1][2]};
+  }
+  const int ng = NG > 0 ? NG : rs.ng, ng3 = ng * ng * ng;
+  const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
+  const SsPt* T = tab + (cls == 1 ? 0 : (cls == 2 ? 2 : 7)) * ng3;
+  const float fkr = (float)kr, fki = (float)ki;
+  // static moments (real, float64) and dynamic moments ((re, im), float64 over regions)
+  double TG[9], Tg[9], DG[18], Dg[18];
+#pragma unroll
+  for (int q = 0; q < 9; ++q) TG[q] = Tg[q] = 0.0;
+#pragma unroll
+  for (int q = 0; q < 18; ++q) DG[q] = Dg[q] = 0.0;
+  for (int r = 0; r < nreg; ++r) {
+    float dG[18], dg[18];
+#pragma unroll
+    for (int q = 0; q < 18; ++q) dG[q] = dg[q] = 0.0f;
+    for (int q = 0; q < ng3; ++q) {
+      const SsPt& e = T[r * ng3 + q];
+      const double x0 = e.x0, x1 = e.x1, y0 = e.y0, y1 = e.y1;
+      // x - y at xi = 1; the shared vertex cancels exactly
+      const V3<double> dr = {x0 * ea.x + x1 * eb.x - y0 * ec.x - y1 * ed.x,
+                             x0 * ea.y + x1 * eb.y - y0 * ec.y - y1 * ed.y,
+                             x0 * ea.z + x1 * eb.z - y0 * ec.z - y1 * ed.z};
+      const double r2 = dot3(dr, dr);
+      const float r2f = (float)r2;
+      float yf;
+      double y;
+      if (r2f > 1e-30f && r2f < 1e30f) {
+        // float32 seed and one Newton step y <- y + y (1 - r2 y^2) / 2 for
+        // r2^{-1/2}: relative error about 1.5 e0^2 < 1e-13
+        yf = rsqrtf(r2f);
+        const double y0 = (double)yf;
+        const double h = fma(-r2 * y0, y0, 1.0);
+        y = fma(0.5 * y0, h, y0);
+      } else {
+        y = 1.0 / sqrt(r2);
+        yf = (float)y;
+      }
+      const double cG = e.w * y, cg = cG * (y * y);
+      const double mono[9] = {1.0, x0, x1, y0, y1, e.m00, e.m01, e.m10, e.m11};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) TG[k] = fma(cG, mono[k], TG[k]);
+      if (doC) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Tg[k] = fma(cg, mono[k], Tg[k]);
+      }
+      // dynamic part in float32
+      float SG[6] = {0, 0, 0, 0, 0, 0}, Sg[6] = {0, 0, 0, 0, 0, 0};
+      dyn_radial<NG>(rs, r2f * yf, fkr, fki, doC, SG, Sg);
+      const float cGf = e.fw * yf, cgf = cGf * yf * yf;
+      const float fx0 = e.fx0, fx1 = e.fx1, fy0 = e.fy0, fy1 = e.fy1;
+      const float fm[9] = {1.0f, fx0, fx1, fy0, fy1, fx0 * fy0, fx0 * fy1, fx1 * fy0, fx1 * fy1};
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const int d = k == 0 ? 0 : (k < 5 ? 2 : 4);
+        const float a = cGf * fm[k];
+        dG[2 * k] = fmaf(a, SG[d], dG[2 * k]);
+        dG[2 * k + 1] = fmaf(a, SG[d + 1], dG[2 * k + 1]);
+        if (doC) {
+          const float b = cgf * fm[k];
+          dg[2 * k] = fmaf(b, Sg[d], dg[2 * k]);
+          dg[2 * k + 1] = fmaf(b, Sg[d + 1], dg[2 * k + 1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 18; ++q) {
+      DG[q] += (double)dG[q];
+      if (doC) Dg[q] += (double)dg[q];
     }
   }
-  double pc[36];
-  pair_coeffs(m, D, pc);
-  // lanes take the (test slot, trial slot) combinations
-  for (int q = lane; q < nslot * nslot; q += 32) {
-    const int a = q / nslot, b = q % nslot;
-    const int e1 = slot_edge[(size_t)sp.t1 * nslot + a];
-    const int e2 = slot_edge[(size_t)sp.t2 * nslot + b];
-    if (e1 < 0 || e2 < 0) continue;
-    const double* swa = slot_sw + ((size_t)sp.t1 * nslot + a) * 4;
-    const double* swb = slot_sw + ((size_t)sp.t2 * nslot + b) * 4;
-    const V3<double> wa = {swa[1], swa[2], swa[3]}, wb = {swb[1], swb[2], swb[3]};
-    double Sr = 0, Si = 0, Cr = 0, Ci = 0;
-    entry_from_pc(pc, swa[0], wa, swb[0], wb, mikr, miki, c4r, c4i, wantS, doC, Sr, Si, Cr, Ci);
-    out.add(e1, e2, wantS, doC, Sr, Si, Cr, Ci);
-    // vertex-sharing pairs are stored once (t1 < t2): the two-region rule maps
-    // onto itself when the triangles swap roles, so (t2, t1) gives the transpose
-    if (cls == 1) out.add(e2, e1, wantS, doC, Sr, Si, Cr, Ci);
+  const TriD& A = tri[sp.t1];
+  const TriD& B = tri[sp.t2];
+  V3<double> Q1[3], Q2[3];
+  for (int a = 0; a < 3; ++a) {
+    Q1[a] = {A.off[sp.o1[a]][0], A.off[sp.o1[a]][1], A.off[sp.o1[a]][2]};
+    Q2[a] = {B.off[sp.o2[a]][0], B.off[sp.o2[a]][1], B.off[sp.o2[a]][2]};
   }
+  const V3<double> D = {A.c[0] - B.c[0], A.c[1] - B.c[1], A.c[2] - B.c[2]};
+  constexpr double INV_4PI = 0.25 / 3.14159265358979323846;
+  const double sc = 4.0 * A.area * B.area * INV_4PI;
+  double MG[18], Mg[18];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int d = k == 0 ? 0 : (k < 5 ? 1 : 2);
+    MG[2 * k] = sc * fma(rs.sG[d], TG[k], DG[2 * k]);
+    MG[2 * k + 1] = sc * DG[2 * k + 1];
+    Mg[2 * k] = sc * fma(rs.sg[d], Tg[k], Dg[2 * k]);
+    Mg[2 * k + 1] = sc * Dg[2 * k + 1];
+  }
+  sing_emit(MG, Mg, Q1, Q2, ea, eb, ec, ed, D, sp, slot_edge, slot_sw, nslot, mikr, miki, c4r, c4i, wantS, doC, 0,
+            1, out);
+}
+
+// Host-built table of the Sauter–Schwab directions for ng Gauss points per
+// dimension: classes 1, 2, 3 (vertex, edge, identical) at offsets 0, 2 ng^3,
+// 7 ng^3, region-major. One copy per (device, ng), kept for the process.
+static const SsPt* ss_table(int ng, const double* gx, const double* gw, cudaStream_t st) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, SsPt*> cache;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find({dev, ng});
+  if (it != cache.end()) return it->second;
+  const int ng3 = ng * ng * ng;
+  std::vector<SsPt> h((size_t)13 * ng3);
+  const int cls_of[3] = {1, 2, 3}, nreg_of[3] = {2, 5, 6}, off_of[3] = {0, 2, 7};
+  for (int c = 0; c < 3; ++c)
+    for (int idx = 0; idx < nreg_of[c] * ng3; ++idx) {
+      const int r = idx / ng3, a1 = (idx / (ng * ng)) % ng, a2 = (idx / ng) % ng, a3 = idx % ng;
+      double xh[2], yh[2], jac;
+      ss_map(cls_of[c], r, 1.0, gx[a1], gx[a2], gx[a3], xh, yh, jac);
+      SsPt& e = h[(size_t)off_of[c] * ng3 + idx];
+      e.x0 = xh[0]; e.x1 = xh[1]; e.y0 = yh[0]; e.y1 = yh[1];
+      e.m00 = xh[0] * yh[0]; e.m01 = xh[0] * yh[1]; e.m10 = xh[1] * yh[0]; e.m11 = xh[1] * yh[1];
+      e.w = gw[a1] * gw[a2] * gw[a3] * jac;
+      e.fx0 = (float)xh[0]; e.fx1 = (float)xh[1]; e.fy0 = (float)yh[0]; e.fy1 = (float)yh[1];
+      e.fw = (float)e.w;
+      e.pad = 0.0f;
+    }
+  SsPt* d = nullptr;
+  if (cudaMalloc((void**)&d, h.size() * sizeof(SsPt)) != cudaSuccess) return nullptr;
+  if (cudaMemcpyAsync(d, h.data(), h.size() * sizeof(SsPt), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    cudaFree(d);
+    return nullptr;
+  }
+  cache[{dev, ng}] = d;
+  return d;
+}
+
+static SsRadial ss_radial(const Rules& rl) {
+  SsRadial rs{};
+  rs.ng = rl.ng;
+  for (int j = 0; j < rl.ng; ++j) {
+    const double x = rl.gx[j], w = rl.gw[j];
+    rs.xi[j] = (float)x;
+    for (int d = 0; d < 3; ++d) {
+      const double xd = d == 0 ? 1.0 : (d == 1 ? x : x * x);
+      rs.sG[d] += w * x * x * xd;
+      rs.sg[d] -= w * xd;
+      rs.wG[j][d] = (float)(w * x * x * xd);
+      rs.wg[j][d] = (float)(w * xd);
+    }
+  }
+  return rs;
 }
 
 // ---------------------------------------------------------------------------
@@ -1560,9 +1827,21 @@ int launch_singular(const AssembleArgs& a) {
                                                       s.nslot, (float)a.kr, (float)a.ki, fmr, fmi, f4r, f4i,
                                                       wS, wC, rf, make_sink<float>(a));
     } else if (a.precision == CAL_FP32) {
-      singular_kernel<float><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
-                                                         s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,
-                                                         c4r, c4i, wS, wC, g_rules, make_sink<float>(a));
+      const SsPt* tab = ss_table(g_rules.ng, g_rules.gx, g_rules.gw, a.stream);
+      if (!tab) {
+        prof_end(a.stream, tok);
+        return fail(CAL_ECUDA, "singular rule table: device allocation failed");
+      }
+      const SsRadial rs = ss_radial(g_rules);
+      const unsigned g1 = (unsigned)((np + 127) / 128);
+      if (g_rules.ng == 4)
+        singular_split_kernel<4><<<g1, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge, s.d_slot_swd,
+                                                           s.nslot, a.kr, a.ki, mikr, miki, c4r, c4i, wS, wC, tab,
+                                                           rs, make_sink<float>(a));
+      else
+        singular_split_kernel<0><<<g1, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge, s.d_slot_swd,
+                                                           s.nslot, a.kr, a.ki, mikr, miki, c4r, c4i, wS, wC, tab,
+                                                           rs, make_sink<float>(a));
     } else {
       singular_kernel<double><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
                                                           s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,

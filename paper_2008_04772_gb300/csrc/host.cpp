@@ -517,6 +517,10 @@ void build_singular_pairs(Space& s) {
         out.push_back(p);
       }
     }
+    // grouped by class, costliest rules first: lanes of one warp then run the
+    // same rule (the float32-output kernel takes one pair per lane)
+    auto rank = [](const SingPair& q) { return q.cls == 2 ? 0 : (q.cls == 3 ? 1 : 2); };
+    std::stable_sort(out.begin(), out.end(), [&](const SingPair& x, const SingPair& y) { return rank(x) < rank(y); });
   }
 }
 
