@@ -137,21 +137,40 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     std::vector<int> wlist;
     std::vector<int2> tiles;
     if (!dense) {
+      // tiles (v, w), v <= w, of the cell pairs that hold a kept entry (i, j):
+      // v and w end cells of i and j; per test cell a stamp array deduplicates
       const int64_t off = op->row_offset;
-      std::vector<int64_t> keys;
-      for (int64_t i = 0; i < op->rows; ++i)
-        for (int64_t q = op->h_rowptr[i]; q < op->h_rowptr[i + 1]; ++q) {
-          const int64_t j = op->h_col[q];
-          if (j < i) continue;
-          const int vi[2] = {m.e_lo[off + i], m.e_hi[off + i]};
-          const int vj[2] = {m.e_lo[off + j], m.e_hi[off + j]};
-          for (int x : vi)
-            for (int y : vj) keys.push_back(((int64_t)std::min(x, y) << 32) | (int64_t)std::max(x, y));
+      std::vector<int> cell_rows_ptr(m.nv + 1, 0), cell_rows;
+      for (int64_t i = 0; i < op->rows; ++i) {
+        ++cell_rows_ptr[m.e_lo[off + i] + 1];
+        ++cell_rows_ptr[m.e_hi[off + i] + 1];
+      }
+      for (int64_t v = 0; v < m.nv; ++v) cell_rows_ptr[v + 1] += cell_rows_ptr[v];
+      cell_rows.resize(cell_rows_ptr[m.nv]);
+      {
+        std::vector<int> fill(cell_rows_ptr.begin(), cell_rows_ptr.end() - 1);
+        for (int64_t i = 0; i < op->rows; ++i) {
+          cell_rows[fill[m.e_lo[off + i]]++] = (int)i;
+          cell_rows[fill[m.e_hi[off + i]]++] = (int)i;
         }
-      std::sort(keys.begin(), keys.end());
-      keys.erase(std::unique(keys.begin(), keys.end()), keys.end());
-      tiles.resize(keys.size());
-      for (size_t q = 0; q < keys.size(); ++q) tiles[q] = make_int2((int)(keys[q] >> 32), (int)(keys[q] & 0xffffffff));
+      }
+      std::vector<int> stamp(m.nv, -1), ws;
+      for (int v : cells) {
+        ws.clear();
+        for (int r = cell_rows_ptr[v]; r < cell_rows_ptr[v + 1]; ++r) {
+          const int64_t i = cell_rows[r];
+          for (int64_t q = op->h_rowptr[i]; q < op->h_rowptr[i + 1]; ++q) {
+            const int64_t j = off + op->h_col[q];
+            for (int w : {m.e_lo[j], m.e_hi[j]})
+              if (w >= v && stamp[w] != v) {
+                stamp[w] = v;
+                ws.push_back(w);
+              }
+          }
+        }
+        std::sort(ws.begin(), ws.end());
+        for (int w : ws) tiles.push_back(make_int2(v, w));
+      }
       wlist.resize(tiles.size());
       for (size_t q = 0; q < tiles.size(); ++q) wlist[q] = tiles[q].y;
       for (size_t q = 0; q < tiles.size();) {
