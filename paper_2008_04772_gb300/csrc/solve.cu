@@ -436,22 +436,85 @@ __device__ __forceinline__ void block_accumulate(double (&v)[NV], double* dst) {
   __syncthreads();
 }
 
+// Vectors are stored system-interleaved, element (i, s) at i * nsys + s, so
+// that the lanes of a warp (consecutive systems of one row, or consecutive
+// rows of few systems) read the entries of a gathered column contiguously and
+// load each matrix entry once. A block is nsys x rpb threads (rpb rows per
+// pass, grid-stride over rows); its first nsys threads form the per-system
+// scalars of the step once, in float64, from the sums of the previous step.
+struct BiLayout {
+  int ns, rpb, s, r0;
+  __device__ BiLayout(int nsys) : ns(nsys), rpb(blockDim.x / nsys), s(threadIdx.x % nsys), r0(threadIdx.x / nsys) {}
+  __device__ int64_t first() const { return (int64_t)blockIdx.x * rpb + r0; }
+  __device__ int64_t step() const { return (int64_t)gridDim.x * rpb; }
+};
+
+// per-system sums of the block's partials (NV per thread), added to dst(s)
+// (nsys dividing 32: lanes of one system are nsys apart in a warp, summed by
+// shuffles first; otherwise each system's rpb partials are summed directly)
+template <int NV>
+__device__ __forceinline__ void system_sums(const BiLayout& L, double (&v)[NV], double* red) {
+  const int ns = L.ns, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  if ((32 % ns) == 0 && (blockDim.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      double a = v[q];
+      for (int o = 16; o >= ns; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane < ns) red[(q * nw + wid) * ns + lane] = a;
+    }
+    __syncthreads();
+    if (threadIdx.x < ns)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        double a = 0.0;
+        for (int w = 0; w < nw; ++w) a += red[(q * nw + w) * ns + threadIdx.x];
+        v[q] = a;
+      }
+  } else {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[q * blockDim.x + threadIdx.x] = v[q];
+    __syncthreads();
+    if (threadIdx.x < ns)
+#pragma unroll
+      for (int q = 0; q < NV; ++q) {
+        double a = 0.0;
+        for (int r = 0; r < L.rpb; ++r) a += red[q * blockDim.x + r * ns + threadIdx.x];
+        v[q] = a;
+      }
+  }
+}
+
+template <int NV>
+__device__ __forceinline__ void system_accumulate(const BiLayout& L, const double (&v)[NV], double* red,
+                                                  double* acc, int nsys, int par, int off) {
+  double w[NV];
+#pragma unroll
+  for (int q = 0; q < NV; ++q) w[q] = v[q];
+  system_sums<NV>(L, w, red);
+  if (threadIdx.x < L.ns)
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      if (w[q] != 0.0) atomicAdd(ACC(acc, nsys, par, threadIdx.x) + off + q, w[q]);
+}
+
 template <typename R>
 __global__ void bicg_init(BiArgs<R> A, const typename CT<R>::T* __restrict__ b) {
   // x = 0, r = r0 = b, p = v = 0; rho_0 = b^H b stored as "next rho" of parity 1
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
+  extern __shared__ double red[];
+  const BiLayout L(A.nsys);
   double part[1] = {0.0};
-  if (i < A.n) {
-    const int64_t k = (int64_t)s * A.n + i;
-    const auto bv = b[k];
-    A.x[k] = {0, 0};
-    A.r[k] = bv;
-    A.r0[k] = bv;
-    A.p0[k] = A.p1[k] = A.v0[k] = A.v1[k] = {0, 0};
-    part[0] = (double)bv.x * bv.x + (double)bv.y * bv.y;
-  }
-  block_accumulate<1>(part, A.bnorm2 + s);
+  if (L.r0 < L.rpb)
+    for (int64_t i = L.first(); i < A.n; i += L.step()) {
+      const int64_t k = i * L.ns + L.s;
+      const auto bv = b[(int64_t)L.s * A.n + i];
+      A.x[k] = {0, 0};
+      A.r[k] = bv;
+      A.r0[k] = bv;
+      A.p0[k] = A.p1[k] = A.v0[k] = A.v1[k] = {0, 0};
+      part[0] += (double)bv.x * bv.x + (double)bv.y * bv.y;
+    }
+  system_sums<1>(L, part, red);
+  if (threadIdx.x < L.ns && part[0] != 0.0) atomicAdd(A.bnorm2 + threadIdx.x, part[0]);
 }
 
 template <typename R>
@@ -468,146 +531,179 @@ __global__ void bicg_init2(BiArgs<R> A) {
 // K1: p_k = r_k + beta (p_{k-1} - omega_{k-1} v_{k-1});  v_k = G p_k;  acc r0^H v
 template <typename R>
 __global__ void bicg_k1(BiArgs<R> A, int k) {
-  const int s = blockIdx.y;
+  extern __shared__ double red[];            // [3][blockDim] partials, then [nsys][5] scalars
+  double* sc = red + 3 * blockDim.x;
+  const BiLayout L(A.nsys);
   const int P = k & 1;
-  double* a = ACC(A.acc, A.nsys, P, s);
-  double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
-  if (A.done[s]) return;
-  // convergence of r_k: r^H r from the previous K3 (or b^H b)
-  if (ap[7] <= A.tol2 * A.bnorm2[s]) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) A.done[s] = 1;
-    return;
+  if (threadIdx.x < L.ns) {
+    const int s = threadIdx.x;
+    double* a = ACC(A.acc, A.nsys, P, s);
+    double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+    bool act = !A.done[s];
+    // convergence of r_k: r^H r from the previous K3 (or b^H b)
+    if (act && ap[7] <= A.tol2 * A.bnorm2[s]) {
+      act = false;
+      if (blockIdx.x == 0) A.done[s] = 1;
+    }
+    double br = 0.0, bi = 0.0, omr = 1.0, omi = 0.0;
+    if (act && k > 0) {
+      // beta = (rho_k / rho_{k-1}) (alpha_{k-1} / omega_{k-1})
+      double rr, ri, alr, ali;
+      cdiv(ap[5], ap[6], a[5], a[6], rr, ri);           // rho_k / rho_{k-1}
+      cdiv(a[5], a[6], ap[0], ap[1], alr, ali);         // alpha_{k-1} = rho_{k-1}/(r0^H v_{k-1})
+      cdiv(ap[2], ap[3], ap[4], 0.0, omr, omi);         // omega_{k-1}
+      double tr, ti;
+      cdiv(alr, ali, omr, omi, tr, ti);
+      br = rr * tr - ri * ti;
+      bi = rr * ti + ri * tr;
+    }
+    sc[5 * s] = act ? 1.0 : 0.0;
+    sc[5 * s + 1] = br; sc[5 * s + 2] = bi; sc[5 * s + 3] = omr; sc[5 * s + 4] = omi;
   }
-  double br = 0.0, bi = 0.0, omr = 1.0, omi = 0.0;
-  if (k > 0) {
-    // beta = (rho_k / rho_{k-1}) (alpha_{k-1} / omega_{k-1})
-    double rr, ri, alr, ali;
-    cdiv(ap[5], ap[6], a[5], a[6], rr, ri);           // rho_k / rho_{k-1}
-    cdiv(a[5], a[6], ap[0], ap[1], alr, ali);         // alpha_{k-1} = rho_{k-1}/(r0^H v_{k-1})
-    cdiv(ap[2], ap[3], ap[4], 0.0, omr, omi);         // omega_{k-1}
-    double tr, ti;
-    cdiv(alr, ali, omr, omi, tr, ti);
-    br = rr * tr - ri * ti;
-    bi = rr * ti + ri * tr;
-  }
-  const auto* pprev = (P ? A.p0 : A.p1) + (size_t)s * A.n;  // p_{k-1}
-  const auto* vprev = (P ? A.v0 : A.v1) + (size_t)s * A.n;
-  auto* pcur = (P ? A.p1 : A.p0) + (size_t)s * A.n;
-  auto* vcur = (P ? A.v1 : A.v0) + (size_t)s * A.n;
-  const auto* r = A.r + (size_t)s * A.n;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double part[2] = {0.0, 0.0};
+  __syncthreads();
+  const int s = L.s;
+  const bool act = L.r0 < L.rpb && sc[5 * s] != 0.0;
   // vector arithmetic in the storage precision (float32 on the FP32 path: the
-  // FP64 pipe is a small fraction of FP32 here); the dot products are summed
-  // in float64 across the grid
-  const R bR = (R)br, bI = (R)bi, oR = (R)omr, oI = (R)omi;
+  // FP64 pipe is a small fraction of FP32 here); the dot products in float64
+  const R bR = (R)sc[5 * s + 1], bI = (R)sc[5 * s + 2], oR = (R)sc[5 * s + 3], oI = (R)sc[5 * s + 4];
+  const auto* pprev = P ? A.p0 : A.p1;  // p_{k-1}
+  const auto* vprev = P ? A.v0 : A.v1;
+  auto* pcur = P ? A.p1 : A.p0;
+  auto* vcur = P ? A.v1 : A.v0;
+  const int ns = L.ns;
   auto pj = [&](int64_t j) {
-    const auto pp = pprev[j], vv = vprev[j], rj = r[j];
+    const int64_t kk = j * ns + s;
+    const auto pp = pprev[kk], vv = vprev[kk], rj = A.r[kk];
     const R dx = pp.x - (oR * vv.x - oI * vv.y), dy = pp.y - (oR * vv.y + oI * vv.x);
     return typename CT<R>::T{rj.x + bR * dx - bI * dy, rj.y + bR * dy + bI * dx};
   };
-  if (i < A.n) {
-    pcur[i] = pj(i);
-    R vr = 0, vi = 0;
-    for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-      const auto pc = pj(A.col[q]);
-      vr += A.val[q] * pc.x;
-      vi += A.val[q] * pc.y;
+  double part[2] = {0.0, 0.0};
+  if (act)
+    for (int64_t i = L.first(); i < A.n; i += L.step()) {
+      pcur[i * ns + s] = pj(i);
+      R vr = 0, vi = 0;
+      for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+        const auto pc = pj(A.col[q]);
+        const R g = A.val[q];
+        vr += g * pc.x;
+        vi += g * pc.y;
+      }
+      vcur[i * ns + s] = {vr, vi};
+      const auto rh = A.r0[i * ns + s];
+      part[0] += (double)(rh.x * vr + rh.y * vi);   // conj(r0) v
+      part[1] += (double)(rh.x * vi - rh.y * vr);
     }
-    vcur[i] = {vr, vi};
-    const auto rh = A.r0[(size_t)s * A.n + i];
-    part[0] = (double)(rh.x * vr + rh.y * vi);   // conj(r0) v
-    part[1] = (double)(rh.x * vi - rh.y * vr);
-  }
-  block_accumulate<2>(part, a + 0);
+  system_accumulate<2>(L, part, red, A.acc, A.nsys, P, 0);
 }
 
 // K2: alpha = rho_k / (r0^H v_k); s = r - alpha v; t = G s; acc t^H s, t^H t
 template <typename R>
 __global__ void bicg_k2(BiArgs<R> A, int k) {
-  const int s = blockIdx.y;
+  extern __shared__ double red[];
+  double* sc = red + 3 * blockDim.x;         // [nsys][3]: active, alpha (re, im)
+  const BiLayout L(A.nsys);
   const int P = k & 1;
-  double* a = ACC(A.acc, A.nsys, P, s);
-  double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
-  if (A.done[s]) return;
-  if (threadIdx.x == 0 && blockIdx.x == 0) { a[5] = a[6] = a[7] = 0.0; }
-  if (a[0] == 0.0 && a[1] == 0.0) return;
-  double alr, ali;
-  cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
-  const auto* vcur = (P ? A.v1 : A.v0) + (size_t)s * A.n;
-  const auto* r = A.r + (size_t)s * A.n;
-  auto* t = A.t + (size_t)s * A.n;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double part[3] = {0, 0, 0};
-  const R aR = (R)alr, aI = (R)ali;
+  if (threadIdx.x < L.ns) {
+    const int s = threadIdx.x;
+    double* a = ACC(A.acc, A.nsys, P, s);
+    double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+    bool act = !A.done[s];
+    if (act && blockIdx.x == 0) { a[5] = a[6] = a[7] = 0.0; }
+    if (a[0] == 0.0 && a[1] == 0.0) act = false;
+    double alr = 0.0, ali = 0.0;
+    if (act) cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
+    sc[3 * s] = act ? 1.0 : 0.0;
+    sc[3 * s + 1] = alr;
+    sc[3 * s + 2] = ali;
+  }
+  __syncthreads();
+  const int s = L.s, ns = L.ns;
+  const bool act = L.r0 < L.rpb && sc[3 * s] != 0.0;
+  const R aR = (R)sc[3 * s + 1], aI = (R)sc[3 * s + 2];
+  const auto* vcur = P ? A.v1 : A.v0;
   auto sj = [&](int64_t j) {
-    const auto vv = vcur[j], rj = r[j];
+    const int64_t kk = j * ns + s;
+    const auto vv = vcur[kk], rj = A.r[kk];
     return typename CT<R>::T{rj.x - (aR * vv.x - aI * vv.y), rj.y - (aR * vv.y + aI * vv.x)};
   };
-  if (i < A.n) {
-    R tr = 0, ti = 0;
-    for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-      const auto sc = sj(A.col[q]);
-      tr += A.val[q] * sc.x;
-      ti += A.val[q] * sc.y;
+  double part[3] = {0, 0, 0};
+  if (act)
+    for (int64_t i = L.first(); i < A.n; i += L.step()) {
+      R tr = 0, ti = 0;
+      for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
+        const auto sc2 = sj(A.col[q]);
+        const R g = A.val[q];
+        tr += g * sc2.x;
+        ti += g * sc2.y;
+      }
+      A.t[i * ns + s] = {tr, ti};
+      const auto si = sj(i);
+      part[0] += (double)(tr * si.x + ti * si.y);   // conj(t) s
+      part[1] += (double)(tr * si.y - ti * si.x);
+      part[2] += (double)(tr * tr + ti * ti);
     }
-    t[i] = {tr, ti};
-    const auto si = sj(i);
-    part[0] = (double)(tr * si.x + ti * si.y);   // conj(t) s
-    part[1] = (double)(tr * si.y - ti * si.x);
-    part[2] = (double)(tr * tr + ti * ti);
-  }
-  block_accumulate<3>(part, a + 2);
+  system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 2);
 }
 
 // K3: omega = t^H s / t^H t; x += alpha p + omega s; r = s - omega t; acc rho, r^H r
 template <typename R>
 __global__ void bicg_k3(BiArgs<R> A, int k) {
-  const int s = blockIdx.y;
+  extern __shared__ double red[];
+  double* sc = red + 3 * blockDim.x;         // [nsys][5]: active, alpha, omega
+  const BiLayout L(A.nsys);
   const int P = k & 1;
-  double* a = ACC(A.acc, A.nsys, P, s);
-  double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
-  if (A.done[s]) return;
-  if (threadIdx.x == 0 && blockIdx.x == 0) {
-    for (int q = 0; q < 5; ++q) ap[q] = 0.0;   // parity P^1 is free for iteration k+1
+  if (threadIdx.x < L.ns) {
+    const int s = threadIdx.x;
+    double* a = ACC(A.acc, A.nsys, P, s);
+    double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+    bool act = !A.done[s];
+    if (act && blockIdx.x == 0) {
+      for (int q = 0; q < 5; ++q) ap[q] = 0.0;   // parity P^1 is free for iteration k+1
+    }
+    if (act && ((a[0] == 0.0 && a[1] == 0.0) || a[4] == 0.0)) {
+      act = false;
+      if (blockIdx.x == 0) A.done[s] = 1;
+    }
+    double alr = 0, ali = 0, omr = 0, omi = 0;
+    if (act) {
+      cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
+      cdiv(a[2], a[3], a[4], 0.0, omr, omi);
+    }
+    sc[5 * s] = act ? 1.0 : 0.0;
+    sc[5 * s + 1] = alr; sc[5 * s + 2] = ali; sc[5 * s + 3] = omr; sc[5 * s + 4] = omi;
   }
-  if ((a[0] == 0.0 && a[1] == 0.0) || a[4] == 0.0) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) A.done[s] = 1;
-    return;
-  }
-  double alr, ali, omr, omi;
-  cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
-  cdiv(a[2], a[3], a[4], 0.0, omr, omi);
-  const auto* pcur = (P ? A.p1 : A.p0) + (size_t)s * A.n;
-  const auto* vcur = (P ? A.v1 : A.v0) + (size_t)s * A.n;
-  auto* x = A.x + (size_t)s * A.n;
-  auto* r = A.r + (size_t)s * A.n;
-  const auto* t = A.t + (size_t)s * A.n;
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  __syncthreads();
+  const int s = L.s, ns = L.ns;
+  const bool act = L.r0 < L.rpb && sc[5 * s] != 0.0;
+  const R aR = (R)sc[5 * s + 1], aI = (R)sc[5 * s + 2], oR = (R)sc[5 * s + 3], oI = (R)sc[5 * s + 4];
+  const auto* pcur = P ? A.p1 : A.p0;
+  const auto* vcur = P ? A.v1 : A.v0;
   double part[3] = {0, 0, 0};
-  if (i < A.n) {
-    const R aR = (R)alr, aI = (R)ali, oR = (R)omr, oI = (R)omi;
-    const auto vv = vcur[i], ri = r[i], pp = pcur[i], tt = t[i];
-    const R sx = ri.x - (aR * vv.x - aI * vv.y), sy = ri.y - (aR * vv.y + aI * vv.x);
-    const auto xi = x[i];
-    x[i] = {xi.x + (aR * pp.x - aI * pp.y) + (oR * sx - oI * sy), xi.y + (aR * pp.y + aI * pp.x) + (oR * sy + oI * sx)};
-    const R rx = sx - (oR * tt.x - oI * tt.y), ry = sy - (oR * tt.y + oI * tt.x);
-    r[i] = {rx, ry};
-    const auto rh = A.r0[(size_t)s * A.n + i];
-    part[0] = (double)(rh.x * rx + rh.y * ry);
-    part[1] = (double)(rh.x * ry - rh.y * rx);
-    part[2] = (double)(rx * rx + ry * ry);
-  }
-  block_accumulate<3>(part, a + 5);
+  if (act)
+    for (int64_t i = L.first(); i < A.n; i += L.step()) {
+      const int64_t kk = i * ns + s;
+      const auto vv = vcur[kk], ri = A.r[kk], pp = pcur[kk], tt = A.t[kk];
+      const R sx = ri.x - (aR * vv.x - aI * vv.y), sy = ri.y - (aR * vv.y + aI * vv.x);
+      const auto xi = A.x[kk];
+      A.x[kk] = {xi.x + (aR * pp.x - aI * pp.y) + (oR * sx - oI * sy),
+                 xi.y + (aR * pp.y + aI * pp.x) + (oR * sy + oI * sx)};
+      const R rx = sx - (oR * tt.x - oI * tt.y), ry = sy - (oR * tt.y + oI * tt.x);
+      A.r[kk] = {rx, ry};
+      const auto rh = A.r0[kk];
+      part[0] += (double)(rh.x * rx + rh.y * ry);
+      part[1] += (double)(rh.x * ry - rh.y * rx);
+      part[2] += (double)(rx * rx + ry * ry);
+    }
+  system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 5);
 }
 
 template <typename R>
 __global__ void bicg_finish(BiArgs<R> A, typename CT<R>::T* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int s = blockIdx.y;
-  if (i < A.n) {
-    const auto v = A.x[(size_t)s * A.n + i];
-    out[(size_t)s * A.n + i] = {(R)(A.neg * v.x), (R)(A.neg * v.y)};
+  const BiLayout L(A.nsys);
+  if (L.r0 >= L.rpb) return;
+  for (int64_t i = L.first(); i < A.n; i += L.step()) {
+    const auto v = A.x[i * L.ns + L.s];
+    out[(size_t)L.s * A.n + i] = {(R)(A.neg * v.x), (R)(A.neg * v.y)};
   }
 }
 
@@ -664,16 +760,27 @@ int GramSolver<R>::enqueue(const C* b, C* out, cudaStream_t st) {
   A.bnorm2 = d_acc + 2 * nsys * 8;
   A.done = d_done;
   A.tol2 = tol * tol;
-  const dim3 grid(blocks_for(n, 256), nsys);
+  if (nsys < 1 || nsys > 256) return fail(CAL_EINVAL, "Gram solve: %d systems (1..256)", nsys);
+  // nsys x rpb threads per block, rows grid-strided over a few blocks per SM
+  const int rpb = std::max(1, 256 / nsys);
+  const int threads = nsys * rpb;
+  const int64_t row_blocks = (n + rpb - 1) / rpb;
+  int n_sm = 148;
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  }
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(row_blocks, (int64_t)n_sm * 8));
+  const size_t smem = (3 * (size_t)threads + 5 * (size_t)nsys) * sizeof(double);
   CAL_TRY_CUDA(cudaMemsetAsync(A.bnorm2, 0, nsys * sizeof(double), st));
-  bicg_init<R><<<grid, 256, 0, st>>>(A, b);
+  bicg_init<R><<<grid, threads, smem, st>>>(A, b);
   bicg_init2<R><<<1, 32 * ((nsys + 31) / 32), 0, st>>>(A);
   for (int k = 0; k < maxit; ++k) {
-    bicg_k1<R><<<grid, 256, 0, st>>>(A, k);
-    bicg_k2<R><<<grid, 256, 0, st>>>(A, k);
-    bicg_k3<R><<<grid, 256, 0, st>>>(A, k);
+    bicg_k1<R><<<grid, threads, smem, st>>>(A, k);
+    bicg_k2<R><<<grid, threads, smem, st>>>(A, k);
+    bicg_k3<R><<<grid, threads, smem, st>>>(A, k);
   }
-  bicg_finish<R><<<grid, 256, 0, st>>>(A, out);
+  bicg_finish<R><<<grid, threads, 0, st>>>(A, out);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
@@ -846,6 +953,103 @@ __global__ void __launch_bounds__(256) pair_gemv_multi_kernel(
   }
 }
 
+// The same product for float64 vectors without float64 arithmetic (float64
+// runs at 1/64 of the float32 rate here). Each float32 entry a times a
+// float64 value x = xh + xl (two floats, |xl| <= ulp(xh)/2) is
+//   a xh = p + e exactly (p = fl(a xh), e = fma(a, xh, -p)), plus fl(a xl),
+// and the sums are double-float (hi, lo) pairs: TwoSum (Knuth) carries the
+// rounding error of every hi addition into lo. Relative error of each sum
+// about 2^-48 per term, far below the float32 operator it applies.
+// (explicitly rounded operations: no contraction of the product into the sums)
+__device__ __forceinline__ void df_mac(float& hi, float& lo, float a, float xh, float xl) {
+  const float p = __fmul_rn(a, xh);
+  const float e = fmaf(a, xh, -p);
+  const float c = fmaf(a, xl, e);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, c));
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) pair_gemv_multi_df_kernel(
+    const float2* __restrict__ S, const float2* __restrict__ C, int64_t rows, int64_t cols, int64_t ld,
+    const double2* __restrict__ x1, const double2* __restrict__ x2, int64_t xstride, double2* __restrict__ y1,
+    double2* __restrict__ y2, int nrhs, double ar, double ai, double br, double bi) {
+  __shared__ float4 xsh[2][G][MV_W];  // (re hi, re lo, im hi, im lo)
+  const int64_t nrb = (rows + 255) / 256;
+  const int64_t nch = (cols + MV_W - 1) / MV_W;
+  const int ngr = (nrhs + G - 1) / G;
+  const int64_t units = nrb * nch * ngr;
+  for (int64_t u = blockIdx.x; u < units; u += gridDim.x) {
+    const int g = (int)(u % ngr);
+    const int64_t rest = u / ngr;
+    const int64_t ch = rest % nch, rb = rest / nch;
+    const int64_t c0 = ch * MV_W;
+    const int q0 = g * G;
+    const int nc = (int)(cols - c0 < MV_W ? cols - c0 : MV_W);
+    __syncthreads();  // the previous unit's readers are done with xsh
+    for (int t = threadIdx.x; t < 2 * G * MV_W; t += 256) {
+      const int c = t % MV_W, q = (t / MV_W) % G, h = t / (MV_W * G);
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (c < nc && q0 + q < nrhs) {
+        const double2 xv = (h ? x2 : x1)[(int64_t)(q0 + q) * xstride + c0 + c];
+        const float rh = (float)xv.x, ih = (float)xv.y;
+        v = make_float4(rh, (float)(xv.x - (double)rh), ih, (float)(xv.y - (double)ih));
+      }
+      xsh[h][q][c] = v;
+    }
+    __syncthreads();
+    const int64_t row = rb * 256 + threadIdx.x;
+    if (row >= rows) continue;
+    float hi[G][8], lo[G][8];
+#pragma unroll
+    for (int q = 0; q < G; ++q)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) hi[q][k] = lo[q][k] = 0.0f;
+    const float2* Sr = S + row * ld + c0;
+    const float2* Cr = C + row * ld + c0;
+    for (int c = 0; c < nc; ++c) {
+      const float2 sf = S ? Sr[c] : make_float2(0.f, 0.f);
+      const float2 cf = C ? Cr[c] : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int q = 0; q < G; ++q) {
+        const float4 a1 = xsh[0][q][c], a2 = xsh[1][q][c];
+        // C x1
+        df_mac(hi[q][0], lo[q][0], cf.x, a1.x, a1.y); df_mac(hi[q][0], lo[q][0], -cf.y, a1.z, a1.w);
+        df_mac(hi[q][1], lo[q][1], cf.x, a1.z, a1.w); df_mac(hi[q][1], lo[q][1], cf.y, a1.x, a1.y);
+        // S x2
+        df_mac(hi[q][2], lo[q][2], sf.x, a2.x, a2.y); df_mac(hi[q][2], lo[q][2], -sf.y, a2.z, a2.w);
+        df_mac(hi[q][3], lo[q][3], sf.x, a2.z, a2.w); df_mac(hi[q][3], lo[q][3], sf.y, a2.x, a2.y);
+        // C x2
+        df_mac(hi[q][4], lo[q][4], cf.x, a2.x, a2.y); df_mac(hi[q][4], lo[q][4], -cf.y, a2.z, a2.w);
+        df_mac(hi[q][5], lo[q][5], cf.x, a2.z, a2.w); df_mac(hi[q][5], lo[q][5], cf.y, a2.x, a2.y);
+        // S x1
+        df_mac(hi[q][6], lo[q][6], sf.x, a1.x, a1.y); df_mac(hi[q][6], lo[q][6], -sf.y, a1.z, a1.w);
+        df_mac(hi[q][7], lo[q][7], sf.x, a1.z, a1.w); df_mac(hi[q][7], lo[q][7], sf.y, a1.x, a1.y);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < G; ++q) {
+      if (q0 + q >= nrhs) break;
+      double acc[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) acc[k] = (double)hi[q][k] + (double)lo[q][k];
+      const double r1 = acc[0] + ar * acc[2] - ai * acc[3];
+      const double i1 = acc[1] + ar * acc[3] + ai * acc[2];
+      const double r2 = acc[4] + br * acc[6] - bi * acc[7];
+      const double i2 = acc[5] + br * acc[7] + bi * acc[6];
+      double2* o1 = y1 + (int64_t)(q0 + q) * xstride + row;
+      double2* o2 = y2 + (int64_t)(q0 + q) * xstride + row;
+      atomicAdd(&o1->x, r1);
+      atomicAdd(&o1->y, i1);
+      atomicAdd(&o2->x, r2);
+      atomicAdd(&o2->y, i2);
+    }
+  }
+}
+
 int pair_apply_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, int nrhs, double ar,
                      double ai, double br, double bi, int n_sm, cudaStream_t st) {
   if (b.precision != CAL_FP32 || b.rowptr) return fail(CAL_EINVAL, "multi-vector GEMV: dense float32 blocks only");
@@ -859,9 +1063,9 @@ int pair_apply_multi(const BlockRef& b, int vec_prec, const void* x, void* y, in
   if (vec_prec == CAL_FP64) {
     const double2* xx = (const double2*)x;
     double2* yy = (double2*)y;
-    pair_gemv_multi_kernel<double2, double, 4><<<grid, 256, 0, st>>>(
-        S, C, b.rows, b.cols, b.cols, xx + b.col_off, xx + n + b.col_off, 2 * n, yy + b.row_off,
-        yy + n + b.row_off, nrhs, ar, ai, br, bi);
+    pair_gemv_multi_df_kernel<4><<<grid, 256, 0, st>>>(S, C, b.rows, b.cols, b.cols, xx + b.col_off,
+                                                      xx + n + b.col_off, 2 * n, yy + b.row_off,
+                                                      yy + n + b.row_off, nrhs, ar, ai, br, bi);
   } else {
     const float2* xx = (const float2*)x;
     float2* yy = (float2*)y;

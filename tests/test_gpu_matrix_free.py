@@ -113,3 +113,21 @@ def test_matrix_free_fp64_solve_matches_oracle(ctx):
     o = cal.solve_opts(precond="D", precision=cal.FP64, tol=1e-11, matrix_free=1)
     Fg = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc, opts=o).far_field(dirs)[0]
     assert rel(Fg, Fo) < 1e-8, rel(Fg, Fo)
+
+
+@pytest.mark.parametrize("name,k", [("sphere3", 4.0), ("prisms2", 3.0)])
+def test_fp32_operator_fp64_vectors_multi_equals_single(ctx, name, k):
+    """Float64 vectors on a float32 operator: several vectors at once use
+    double-float (float32 pair) products and sums, one vector at a time uses
+    float64 arithmetic. Both are the exact product of the float32 entries to
+    far below float32 rounding: bar 1e-12 relative (double-float: ~2^-48 per term)."""
+    m = mesh(name)
+    gm = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    N = gm.info().n_edges
+    rng = np.random.default_rng(11)
+    X = rng.normal(size=(5, 2 * N)) + 1j * rng.normal(size=(5, 2 * N))
+    prob = cal.Problem(ctx, gm, k, EPS, opts=cal.solve_opts(precond="none", precision=cal.FP32))
+    Ym = prob.apply(X)
+    for j in range(5):
+        y1 = prob.apply(X[j:j + 1])[0]
+        assert rel(Ym[j], y1) < 1e-12, (j, rel(Ym[j], y1))
