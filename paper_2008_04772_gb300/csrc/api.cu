@@ -374,6 +374,7 @@ struct Pmchwt {
   void* t1 = nullptr;
   void* t2 = nullptr;
   double2* d_gath = nullptr;
+  void* d_xt = nullptr;  // right-hand-side-interleaved copy of x for the CSR blocks
   // tensor-core product buffers
   int NB = 0;
   float* d_Bt = nullptr;
@@ -386,7 +387,7 @@ struct Pmchwt {
   ~Pmchwt() {
     cudaStream_t st = nullptr;  // every solve has completed: the legacy stream orders the release
     for (void* p : {(void*)d_grp, (void*)d_gcol, (void*)d_grpT, (void*)d_gcolT, (void*)d_gval, (void*)d_gvalT, t1,
-                    t2, (void*)d_gath, (void*)d_Bt, (void*)d_Bh, (void*)d_Bl, (void*)d_ZS, (void*)d_ZC,
+                    t2, (void*)d_gath, d_xt, (void*)d_Bt, (void*)d_Bh, (void*)d_Bl, (void*)d_ZS, (void*)d_ZC,
                     (void*)d_gemm_err})
       dfree(p, st);
   }
@@ -411,11 +412,12 @@ struct Pmchwt {
   // Kept between solves of the same batch width.
   int setup_batch(int nbatch) {
     if (nbatch == nb && t1) return CAL_OK;
-    for (void* p : {t1, t2, (void*)d_gath, (void*)d_Bt, (void*)d_Bh, (void*)d_Bl, (void*)d_ZS, (void*)d_ZC,
+    for (void* p : {t1, t2, (void*)d_gath, d_xt, (void*)d_Bt, (void*)d_Bh, (void*)d_Bl, (void*)d_ZS, (void*)d_ZC,
                     (void*)d_gemm_err})
       dfree(p, nullptr);  // the previous solve has completed
     t1 = t2 = nullptr;
     d_gath = nullptr;
+    d_xt = nullptr;
     d_Bt = d_Bh = d_Bl = d_ZS = d_ZC = nullptr;
     d_gemm_err = nullptr;
     NB = 0;
@@ -449,6 +451,7 @@ struct Pmchwt {
     CAL_TRY_CUDA(dalloc(&t1, vbytes, st));
     CAL_TRY_CUDA(dalloc(&t2, vbytes, st));
     CAL_TRY_CUDA(dalloc((void**)&d_gath, vbytes, st));
+    CAL_TRY_CUDA(dalloc(&d_xt, vbytes, st));
     if (o.precision == CAL_FP32 && nb >= 4 && gemm_tc_supported(2, nb)) {
       NB = ((4 * nb + 15) / 16) * 16;
       int64_t maxrows = A_ext->rows;
@@ -502,6 +505,8 @@ struct Pmchwt {
     if (b.precision == CAL_FP32 && !b.rowptr && nrhs >= 2)
       return pair_apply_multi(b, vec_prec, x, y, N, nrhs, al.real(), al.imag(), be.real(), be.imag(), ctx->n_sm,
                               st);
+    if (b.rowptr && nrhs >= 2 && d_xt && nrhs <= nb)
+      return pair_spmv_multi(b, vec_prec, x, y, N, nrhs, al.real(), al.imag(), be.real(), be.imag(), d_xt, st);
     const size_t vsz = vec_prec == CAL_FP64 ? sizeof(double2) : sizeof(float2);
     for (int q = 0; q < nrhs; ++q) {
       int rc = pair_apply(b, vec_prec, (const char*)x + q * 2 * N * vsz, (char*)y + q * 2 * N * vsz, N, al.real(),

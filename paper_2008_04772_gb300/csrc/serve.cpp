@@ -87,7 +87,7 @@ int64_t solve_bytes(const Mesh& m, const cal_solve_opts& o, int64_t nrhs, int64_
   b += 4 * nb * n2 * z;                           // preconditioned rhs, residual, batch padding
   b += nb * (mk + 1) * n2 * z + 3 * nb * n2 * z;  // Krylov basis and GMRES vectors
   b += nb * (mk + 1) * mk * z;                    // Hessenberg matrices
-  b += 3 * nb * n2 * z;                           // work vectors of the batch
+  b += 4 * nb * n2 * z;                           // work vectors of the batch, interleaved copy for CSR blocks
   if (o.precision != CAL_FP64 && nb >= 4) {
     const int64_t NB = ((4 * nb + 15) / 16) * 16;
     b += 3 * NB * 2 * N * 4 + 2 * N * NB * 4;  // tensor-core operands (and their split) and outputs

@@ -330,6 +330,112 @@ __global__ void pair_spmv_kernel(const MT* __restrict__ S, const MT* __restrict_
   }
 }
 
+// The CSR variant for nrhs vectors at once. The block's columns of x are
+// first copied right-hand-side-interleaved (xt[h][c][q]); a warp takes one row
+// and qw right-hand sides (qw a power of two <= 32), its lanes split the
+// row's entries into 32 / qw parts, so each matrix entry is read once per
+// row and group and the gathered x values of a column are contiguous.
+template <typename VT>
+__global__ void interleave_rhs_kernel(const VT* __restrict__ x, int64_t n, int64_t col_off, int64_t cols,
+                                      int nrhs, VT* __restrict__ xt) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * cols * nrhs) return;
+  const int q = (int)(t % nrhs);
+  const int64_t rest = t / nrhs;
+  const int64_t c = rest % cols;
+  const int h = (int)(rest / cols);
+  xt[t] = x[(int64_t)q * 2 * n + h * n + col_off + c];
+}
+
+template <typename MT, typename VT, typename AT>
+__global__ void pair_spmv_multi_kernel(const MT* __restrict__ S, const MT* __restrict__ C,
+                                       const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                       int64_t nr, const VT* __restrict__ xt, int64_t cols, int nrhs, int qw,
+                                       VT* __restrict__ y, int64_t n, int64_t row_off, double ar, double ai,
+                                       double br, double bi) {
+  const int lane = threadIdx.x & 31;
+  const int ngr = (nrhs + qw - 1) / qw;
+  const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t r = w / ngr;
+  if (r >= nr) return;
+  const int g = (int)(w % ngr);
+  const int ql = lane % qw, part = lane / qw, parts = 32 / qw;
+  const int q = g * qw + ql;
+  const bool on = q < nrhs;
+  const VT* x1t = xt;
+  const VT* x2t = xt + cols * nrhs;
+  AT cx1{0, 0}, cx2{0, 0}, sx1{0, 0}, sx2{0, 0};
+  for (int64_t k = rowptr[r] + part; k < rowptr[r + 1]; k += parts) {
+    const int c = col[k];
+    VT u{0, 0}, v{0, 0};
+    if (on) {
+      u = x1t[(int64_t)c * nrhs + q];
+      v = x2t[(int64_t)c * nrhs + q];
+    }
+    if (C) {
+      const MT m = C[k];
+      cfma(cx1, m, MT{(decltype(m.x))u.x, (decltype(m.x))u.y});
+      cfma(cx2, m, MT{(decltype(m.x))v.x, (decltype(m.x))v.y});
+    }
+    if (S) {
+      const MT m = S[k];
+      cfma(sx1, m, MT{(decltype(m.x))u.x, (decltype(m.x))u.y});
+      cfma(sx2, m, MT{(decltype(m.x))v.x, (decltype(m.x))v.y});
+    }
+  }
+  for (int o = 16; o >= qw; o >>= 1) {
+    cx1.x += __shfl_xor_sync(0xffffffffu, cx1.x, o); cx1.y += __shfl_xor_sync(0xffffffffu, cx1.y, o);
+    cx2.x += __shfl_xor_sync(0xffffffffu, cx2.x, o); cx2.y += __shfl_xor_sync(0xffffffffu, cx2.y, o);
+    sx1.x += __shfl_xor_sync(0xffffffffu, sx1.x, o); sx1.y += __shfl_xor_sync(0xffffffffu, sx1.y, o);
+    sx2.x += __shfl_xor_sync(0xffffffffu, sx2.x, o); sx2.y += __shfl_xor_sync(0xffffffffu, sx2.y, o);
+  }
+  if (part == 0 && on) {
+    VT* y1 = y + (int64_t)q * 2 * n + row_off + r;
+    VT* y2 = y1 + n;
+    VT a = *y1, b = *y2;
+    a.x += cx1.x + ar * sx2.x - ai * sx2.y;
+    a.y += cx1.y + ar * sx2.y + ai * sx2.x;
+    b.x += cx2.x + br * sx1.x - bi * sx1.y;
+    b.y += cx2.y + br * sx1.y + bi * sx1.x;
+    *y1 = a;
+    *y2 = b;
+  }
+}
+
+template <typename MT, typename VT, typename AT>
+static int pair_spmv_multi_t(const BlockRef& b, const VT* x, VT* y, int64_t n, int nrhs, double ar, double ai,
+                             double br, double bi, VT* xt, cudaStream_t st) {
+  const int64_t tot = 2 * b.cols * nrhs;
+  if (tot > 0) {
+    interleave_rhs_kernel<VT><<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(x, n, b.col_off, b.cols, nrhs, xt);
+    note_launch();
+  }
+  int qw = 1;
+  while (qw < nrhs && qw < 32) qw <<= 1;
+  const int64_t warps = b.rows * ((nrhs + qw - 1) / qw);
+  const int tok = prof_begin(st, "pair_spmv", 0.0);
+  pair_spmv_multi_kernel<MT, VT, AT><<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+      reinterpret_cast<const MT*>(b.S), reinterpret_cast<const MT*>(b.C), b.rowptr, b.col, b.rows, xt, b.cols,
+      nrhs, qw, y, n, b.row_off, ar, ai, br, bi);
+  prof_end(st, tok);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int pair_spmv_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, int nrhs, double ar,
+                    double ai, double br, double bi, void* scratch, cudaStream_t st) {
+  if (!b.rowptr) return fail(CAL_EINVAL, "multi-vector SpMV: CSR blocks only");
+  if (b.precision == CAL_FP64)
+    return pair_spmv_multi_t<double2, double2, double2>(b, (const double2*)x, (double2*)y, n, nrhs, ar, ai, br, bi,
+                                                        (double2*)scratch, st);
+  if (vec_prec == CAL_FP64)
+    return pair_spmv_multi_t<float2, double2, double2>(b, (const double2*)x, (double2*)y, n, nrhs, ar, ai, br, bi,
+                                                       (double2*)scratch, st);
+  return pair_spmv_multi_t<float2, float2, float2>(b, (const float2*)x, (float2*)y, n, nrhs, ar, ai, br, bi,
+                                                   (float2*)scratch, st);
+}
+
 // plain y = X x for one dense operator (C-ABI cal_matvec)
 template <typename MT>
 __global__ void gemv_kernel(const MT* __restrict__ X, int64_t nr, int64_t nc, const MT* __restrict__ x,

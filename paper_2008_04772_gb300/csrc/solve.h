@@ -37,6 +37,10 @@ int pair_apply(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t 
 // arithmetic for float32 vectors, float64 products and sums for float64 ones)
 int pair_apply_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, int nrhs, double ar,
                      double ai, double br, double bi, int n_sm, cudaStream_t st);
+// the same for a CSR block (near-field P, touching-pair blocks); scratch holds
+// 2 * cols * nrhs vector elements (the interleaved copy of x)
+int pair_spmv_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int64_t n, int nrhs, double ar,
+                    double ai, double br, double bi, void* scratch, cudaStream_t st);
 int zero_vec(void* y, int prec, int64_t n, cudaStream_t st);
 int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale, cudaStream_t st);
 int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st);
