@@ -5,6 +5,7 @@
 // (RWG on the primal mesh, BC on its barycentric refinement) of
 // arXiv 2008.04772. All O(N) setup; the O(N^2) numerics run on the GPU.
 #include <algorithm>
+#include <thread>
 #include <atomic>
 #include <mutex>
 #include <cmath>
@@ -474,23 +475,38 @@ int build_bc(Space& s, Mesh& m) {
 void build_singular_pairs(Space& s) {
   const Mesh& m = *s.mesh;
   s.sing.assign(m.M, {});
+  // vertex -> triangles (CSR over the vertex ids of the space's triangles)
+  int maxid = 0;
+  for (int64_t t = 0; t < s.ntri; ++t)
+    for (int a = 0; a < 3; ++a) maxid = std::max(maxid, s.triD[t].vid[a]);
+  std::vector<int> vptr(maxid + 2, 0), vtri;
+  for (int64_t t = 0; t < s.ntri; ++t)
+    for (int a = 0; a < 3; ++a) ++vptr[s.triD[t].vid[a] + 1];
+  for (int v = 0; v <= maxid; ++v) vptr[v + 1] += vptr[v];
+  vtri.resize(vptr[maxid + 1]);
+  {
+    std::vector<int> fill(vptr.begin(), vptr.end() - 1);
+    for (int64_t t = 0; t < s.ntri; ++t)
+      for (int a = 0; a < 3; ++a) vtri[fill[s.triD[t].vid[a]]++] = (int)t;
+  }
+  std::vector<int> stamp(s.ntri, -1), nb;
   for (int64_t d = 0; d < m.M; ++d) {
-    int64_t t0 = s.tri_off[d], t1 = s.tri_off[d + 1];
-    std::unordered_map<int, std::vector<int>> adj;
-    for (int64_t t = t0; t < t1; ++t)
-      for (int a = 0; a < 3; ++a) adj[s.triD[t].vid[a]].push_back((int)t);
+    const int64_t t0 = s.tri_off[d], t1 = s.tri_off[d + 1];
     auto& out = s.sing[d];
-    std::vector<int> nb;
     for (int64_t t = t0; t < t1; ++t) {
       nb.clear();
-      for (int a = 0; a < 3; ++a) {
-        auto& L = adj[s.triD[t].vid[a]];
-        nb.insert(nb.end(), L.begin(), L.end());
-      }
-      std::sort(nb.begin(), nb.end());
-      nb.erase(std::unique(nb.begin(), nb.end()), nb.end());
       const int* i1 = s.triD[t].vid;
+      for (int a = 0; a < 3; ++a)
+        for (int q = vptr[i1[a]]; q < vptr[i1[a] + 1]; ++q) {
+          const int u = vtri[q];
+          if (stamp[u] != (int)t) {
+            stamp[u] = (int)t;
+            nb.push_back(u);
+          }
+        }
+      std::sort(nb.begin(), nb.end());
       for (int u : nb) {
+        if (u < t0 || u >= t1) continue;  // touching triangles of one scatterer only
         const int* i2 = s.triD[u].vid;
         int shared = 0;
         for (int a = 0; a < 3; ++a)
@@ -520,49 +536,124 @@ void build_singular_pairs(Space& s) {
     // grouped by class, costliest rules first: lanes of one warp then run the
     // same rule (the float32-output kernel takes one pair per lane)
     auto rank = [](const SingPair& q) { return q.cls == 2 ? 0 : (q.cls == 3 ? 1 : 2); };
-    std::stable_sort(out.begin(), out.end(), [&](const SingPair& x, const SingPair& y) { return rank(x) < rank(y); });
+    size_t cnt[4] = {0, 0, 0, 0};
+    for (const SingPair& q : out) ++cnt[rank(q) + 1];
+    for (int c = 0; c < 3; ++c) cnt[c + 1] += cnt[c];
+    std::vector<SingPair> sorted(out.size());
+    for (const SingPair& q : out) sorted[cnt[rank(q)]++] = q;
+    out.swap(sorted);
   }
 }
 
+// Support-box pattern: (i, j) kept iff the boxes are <= chi apart. Box
+// centres are binned on a uniform grid of cell size >= (largest box extent +
+// chi) / 2, so every partner of i lies within two cells of i's cell; the
+// boxes are copied in cell order for contiguous scans, and rows are
+// independent and are built by a few host threads.
 void near_pattern(const Space& s, int scat, double chi, std::vector<int64_t>& rowptr,
                   std::vector<int>& col) {
   const Mesh& m = *s.mesh;
   const int64_t e0 = scat < 0 ? 0 : m.edge_off[scat];
   const int64_t e1 = scat < 0 ? m.ne : m.edge_off[scat + 1];
   const int64_t n = e1 - e0;
-  std::vector<int64_t> ord(n);
-  std::iota(ord.begin(), ord.end(), 0);
-  std::sort(ord.begin(), ord.end(), [&](int64_t a, int64_t b) {
-    return s.box_lo[3 * (e0 + a)] < s.box_lo[3 * (e0 + b)];
-  });
-  std::vector<std::vector<int>> rows(n);
-  for (int64_t ii = 0; ii < n; ++ii) {
-    int64_t i = ord[ii];
-    const double* li = &s.box_lo[3 * (e0 + i)];
-    const double* hi = &s.box_hi[3 * (e0 + i)];
-    for (int64_t jj = ii; jj < n; ++jj) {
-      int64_t j = ord[jj];
-      const double* lj = &s.box_lo[3 * (e0 + j)];
-      const double* hj = &s.box_hi[3 * (e0 + j)];
-      if (lj[0] - hi[0] > chi) break;
-      double g2 = 0;
-      for (int c = 0; c < 3; ++c) {
-        double g = std::max(0.0, std::max(lj[c] - hi[c], li[c] - hj[c]));
-        g2 += g * g;
-      }
-      if (std::sqrt(g2) <= chi) {
-        rows[i].push_back((int)j);
-        if (j != i) rows[j].push_back((int)i);
-      }
-    }
-  }
   rowptr.assign(n + 1, 0);
   col.clear();
-  for (int64_t i = 0; i < n; ++i) {
-    std::sort(rows[i].begin(), rows[i].end());
-    col.insert(col.end(), rows[i].begin(), rows[i].end());
-    rowptr[i + 1] = (int64_t)col.size();
+  if (n == 0) return;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300}, ext = 0.0;
+  for (int64_t i = 0; i < n; ++i)
+    for (int c = 0; c < 3; ++c) {
+      const double a = s.box_lo[3 * (e0 + i) + c], b = s.box_hi[3 * (e0 + i) + c];
+      lo[c] = std::min(lo[c], 0.5 * (a + b));
+      hi[c] = std::max(hi[c], 0.5 * (a + b));
+      ext = std::max(ext, b - a);
+    }
+  // centres of partners differ by at most ext + chi per coordinate
+  double cell = std::max(0.5 * (ext + chi), 1e-300);
+  int dim[3];
+  for (int c = 0; c < 3; ++c) dim[c] = (int)std::min<double>(std::floor((hi[c] - lo[c]) / cell) + 1, 1 << 20);
+  while ((double)dim[0] * dim[1] * dim[2] > 8.0 * (double)n + 64) {  // bounded grid size
+    cell *= 1.25;
+    for (int c = 0; c < 3; ++c) dim[c] = (int)std::floor((hi[c] - lo[c]) / cell) + 1;
   }
+  const int reach = (int)std::ceil((ext + chi) / cell - 1e-12);
+  auto cidx = [&](int64_t i, int* g) {
+    for (int c = 0; c < 3; ++c) {
+      const double x = 0.5 * (s.box_lo[3 * (e0 + i) + c] + s.box_hi[3 * (e0 + i) + c]);
+      g[c] = std::min(dim[c] - 1, std::max(0, (int)((x - lo[c]) / cell)));
+    }
+  };
+  const int64_t ncell = (int64_t)dim[0] * dim[1] * dim[2];
+  std::vector<int64_t> cptr(ncell + 1, 0);
+  std::vector<int> cell_of(n), citems(n);
+  for (int64_t i = 0; i < n; ++i) {
+    int g[3];
+    cidx(i, g);
+    cell_of[i] = (int)(((int64_t)g[2] * dim[1] + g[1]) * dim[0] + g[0]);
+    ++cptr[cell_of[i] + 1];
+  }
+  for (int64_t c = 0; c < ncell; ++c) cptr[c + 1] += cptr[c];
+  {
+    std::vector<int64_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int64_t i = 0; i < n; ++i) citems[fill[cell_of[i]]++] = (int)i;
+  }
+  // boxes in cell order: bx[6 q .. 6 q + 5] = lo, hi of citems[q]
+  std::vector<double> bx(6 * (size_t)n);
+  for (int64_t q = 0; q < n; ++q)
+    for (int c = 0; c < 3; ++c) {
+      bx[6 * q + c] = s.box_lo[3 * (e0 + citems[q]) + c];
+      bx[6 * q + 3 + c] = s.box_hi[3 * (e0 + citems[q]) + c];
+    }
+  const double chi2 = chi * chi;
+  const int nth = (int)std::max<int64_t>(1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(),
+                                                                 n / 256 + 1}));
+  std::vector<std::vector<int>> cols(nth);
+  std::vector<std::vector<int64_t>> counts(nth);
+  auto work = [&](int w) {
+    const int64_t r0 = n * w / nth, r1 = n * (w + 1) / nth;
+    auto& cw = cols[w];
+    auto& nw = counts[w];
+    nw.assign(r1 - r0, 0);
+    std::vector<int> row;
+    for (int64_t i = r0; i < r1; ++i) {
+      row.clear();
+      const double* li = &s.box_lo[3 * (e0 + i)];
+      const double* hi_ = &s.box_hi[3 * (e0 + i)];
+      int g[3];
+      cidx(i, g);
+      for (int z = std::max(0, g[2] - reach); z <= std::min(dim[2] - 1, g[2] + reach); ++z)
+        for (int y = std::max(0, g[1] - reach); y <= std::min(dim[1] - 1, g[1] + reach); ++y) {
+          // cells x0..x1 of this (y, z) line are contiguous in cell order
+          const int x0 = std::max(0, g[0] - reach), x1 = std::min(dim[0] - 1, g[0] + reach);
+          const int64_t c0 = ((int64_t)z * dim[1] + y) * dim[0];
+          for (int64_t q = cptr[c0 + x0]; q < cptr[c0 + x1 + 1]; ++q) {
+            const double* b = &bx[6 * q];
+            double g2 = 0;
+            for (int k = 0; k < 3; ++k) {
+              const double gap = std::max(0.0, std::max(b[k] - hi_[k], li[k] - b[3 + k]));
+              g2 += gap * gap;
+            }
+            if (g2 <= chi2) row.push_back(citems[q]);
+          }
+        }
+      std::sort(row.begin(), row.end());
+      cw.insert(cw.end(), row.begin(), row.end());
+      nw[i - r0] = (int64_t)row.size();
+    }
+  };
+  if (nth == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int w = 0; w < nth; ++w) th.emplace_back(work, w);
+    for (auto& t : th) t.join();
+  }
+  int64_t k = 0;
+  for (int w = 0; w < nth; ++w) {
+    const int64_t r0 = n * w / nth;
+    for (size_t q = 0; q < counts[w].size(); ++q) rowptr[r0 + q + 1] = (k += counts[w][q]);
+  }
+  col.reserve(k);
+  for (int w = 0; w < nth; ++w) col.insert(col.end(), cols[w].begin(), cols[w].end());
 }
 
 void gram_pattern(const Space& bc, std::vector<int64_t>& rowptr, std::vector<int>& col) {
