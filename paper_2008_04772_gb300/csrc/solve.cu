@@ -111,6 +111,52 @@ template <> struct Pair2<double2> {
   }
 };
 
+// Float64 vectors applied to float32 operators without float64 arithmetic
+// (float64 runs at 1/64 of the float32 rate here). Each float32 entry a times
+// a float64 value x = xh + xl (two floats, |xl| <= ulp(xh)/2) is
+//   a xh = p + e exactly (p = fl(a xh), e = fma(a, xh, -p)), plus fl(a xl),
+// and the sums are double-float (hi, lo) pairs: TwoSum (Knuth) carries the
+// rounding error of every hi addition into lo. Relative error of each sum
+// about 2^-48 per term, far below the float32 operator it applies.
+// (explicitly rounded operations: no contraction of the product into the sums)
+__device__ __forceinline__ void df_mac(float& hi, float& lo, float a, float xh, float xl) {
+  const float p = __fmul_rn(a, xh);
+  const float e = fmaf(a, xh, -p);
+  const float c = fmaf(a, xl, e);
+  const float s = __fadd_rn(hi, p);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, c));
+}
+
+// (hi, lo) += (hi2, lo2), TwoSum on the high parts
+__device__ __forceinline__ void df_add(float& hi, float& lo, float hi2, float lo2) {
+  const float s = __fadd_rn(hi, hi2);
+  const float v = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(hi2, v));
+  hi = s;
+  lo = __fadd_rn(__fadd_rn(lo, lo2), err);
+}
+
+// complex (hr + i hi) += (mr + i mi)(x), x = (re hi, re lo, im hi, im lo)
+__device__ __forceinline__ void df_cmac(float& hr, float& lr, float& hi, float& li, float mr, float mi,
+                                        const float4& x) {
+  df_mac(hr, lr, mr, x.x, x.y);
+  df_mac(hr, lr, -mi, x.z, x.w);
+  df_mac(hi, li, mr, x.z, x.w);
+  df_mac(hi, li, mi, x.x, x.y);
+}
+
+// x (float64 complex) -> (re hi, re lo, im hi, im lo)
+__global__ void split_df_kernel(const double2* __restrict__ x, float4* __restrict__ xs, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double2 v = x[i];
+  const float rh = (float)v.x, ih = (float)v.y;
+  xs[i] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 template <typename VT, typename AT, int ROWS>
 __global__ void __launch_bounds__(256, 2) pair_gemv_vec_kernel(
     const float4* __restrict__ S, const float4* __restrict__ C, int64_t nr, int64_t nc,
@@ -283,6 +329,58 @@ __global__ void __launch_bounds__(256, 3) pair_gemv_units_kernel(
       using E = decltype(y1->x);
       atomic_add_v(y1 + r, (E)(cx1.x + ar * sx2.x - ai * sx2.y), (E)(cx1.y + ar * sx2.y + ai * sx2.x));
       atomic_add_v(y2 + r, (E)(cx2.x + br * sx1.x - bi * sx1.y), (E)(cx2.y + br * sx1.y + bi * sx1.x));
+    }
+  }
+}
+
+// pair_gemv_units_kernel for one float64 vector on float32 blocks, in
+// double-float arithmetic: x pre-split into (hi, lo) floats, per-lane
+// (hi, lo) sums, a double-float warp reduction and one float64 atomic per row.
+__global__ void __launch_bounds__(256, 3) pair_gemv_df_kernel(
+    const float4* __restrict__ S, const float4* __restrict__ C, int64_t nr, int64_t nc2, int64_t ld2,
+    int64_t chunk2, const float4* __restrict__ xs1, const float4* __restrict__ xs2, double2* __restrict__ y1,
+    double2* __restrict__ y2, double ar, double ai, double br, double bi) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nsplit = (nc2 + chunk2 - 1) / chunk2;
+  const int64_t nunits = nr * nsplit;
+  const int64_t wstride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const bool hasC = C != nullptr, hasS = S != nullptr;
+  for (int64_t u = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; u < nunits; u += wstride) {
+    const int64_t r = u / nsplit;
+    const int64_t c_lo = (u % nsplit) * chunk2, c_hi = min(c_lo + chunk2, nc2);
+    const float4* Cr = C + r * ld2;
+    const float4* Sr = S + r * ld2;
+    // (hi, lo) of: C x1 (re, im), C x2, S x1, S x2
+    float h[8], l[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = l[k] = 0.0f;
+    for (int64_t c2 = c_lo + lane; c2 < c_hi; c2 += 32) {
+      const float4 u0 = xs1[2 * c2], u1 = xs1[2 * c2 + 1], v0 = xs2[2 * c2], v1 = xs2[2 * c2 + 1];
+      if (hasC) {
+        const float4 m = __ldcs(Cr + c2);
+        df_cmac(h[0], l[0], h[1], l[1], m.x, m.y, u0); df_cmac(h[0], l[0], h[1], l[1], m.z, m.w, u1);
+        df_cmac(h[2], l[2], h[3], l[3], m.x, m.y, v0); df_cmac(h[2], l[2], h[3], l[3], m.z, m.w, v1);
+      }
+      if (hasS) {
+        const float4 m = __ldcs(Sr + c2);
+        df_cmac(h[4], l[4], h[5], l[5], m.x, m.y, u0); df_cmac(h[4], l[4], h[5], l[5], m.z, m.w, u1);
+        df_cmac(h[6], l[6], h[7], l[7], m.x, m.y, v0); df_cmac(h[6], l[6], h[7], l[7], m.z, m.w, v1);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h[k], o), l2 = __shfl_xor_sync(0xffffffffu, l[k], o);
+        df_add(h[k], l[k], h2, l2);
+      }
+    if (lane == 0) {
+      double d[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) d[k] = (double)h[k] + (double)l[k];
+      // d: C x1 = (d0, d1), C x2 = (d2, d3), S x1 = (d4, d5), S x2 = (d6, d7)
+      atomic_add_v(y1 + r, d[0] + ar * d[6] - ai * d[7], d[1] + ar * d[7] + ai * d[6]);
+      atomic_add_v(y2 + r, d[2] + br * d[4] - bi * d[5], d[3] + br * d[5] + bi * d[4]);
     }
   }
 }
@@ -946,7 +1044,34 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
     const int tok = prof_begin(st, "pair_gemv", bytes);
     const bool aligned16 = ((uintptr_t)S % 16 == 0) && ((uintptr_t)C % 16 == 0) &&
                            ((uintptr_t)x1 % 16 == 0) && ((uintptr_t)x2 % 16 == 0);
-    if constexpr (sizeof(MT) == 8) {
+    if constexpr (sizeof(MT) == 8 && std::is_same<VT, double2>::value) {
+      if (b.cols % 2 == 0 && aligned16) {
+        int nsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        // x split once into (hi, lo) floats; stream-ordered scratch
+        float4* xs = nullptr;
+        if (dalloc((void**)&xs, 2 * (size_t)b.cols * sizeof(float4), st) != cudaSuccess) {
+          prof_end(st, tok);
+          return fail(CAL_ENOMEM, "float64-vector product: scratch allocation failed");
+        }
+        split_df_kernel<<<blocks_for(b.cols, 256), 256, 0, st>>>(x1, xs, b.cols);
+        split_df_kernel<<<blocks_for(b.cols, 256), 256, 0, st>>>(x2, xs + b.cols, b.cols);
+        const int64_t nc2 = b.cols / 2;
+        const int64_t chunk2 = std::min<int64_t>(nc2, 1024);
+        const int64_t units = b.rows * ((nc2 + chunk2 - 1) / chunk2);
+        const int64_t grid = std::min<int64_t>((units + 7) / 8, (int64_t)nsm * 3);
+        pair_gemv_df_kernel<<<(unsigned)grid, 256, 0, st>>>(reinterpret_cast<const float4*>(S),
+                                                           reinterpret_cast<const float4*>(C), b.rows, nc2,
+                                                           b.cols / 2, chunk2, xs, xs + b.cols, y1, y2, ar, ai, br,
+                                                           bi);
+        dfree(xs, st);
+        prof_end(st, tok);
+        note_launch(3);
+        CAL_TRY_CUDA(cudaGetLastError());
+        return CAL_OK;
+      }
+    } else if constexpr (sizeof(MT) == 8) {
       if (b.cols % 2 == 0 && aligned16) {
         int nsm = 0, dev = 0;
         cudaGetDevice(&dev);
@@ -1059,25 +1184,7 @@ __global__ void __launch_bounds__(256) pair_gemv_multi_kernel(
   }
 }
 
-// The same product for float64 vectors without float64 arithmetic (float64
-// runs at 1/64 of the float32 rate here). Each float32 entry a times a
-// float64 value x = xh + xl (two floats, |xl| <= ulp(xh)/2) is
-//   a xh = p + e exactly (p = fl(a xh), e = fma(a, xh, -p)), plus fl(a xl),
-// and the sums are double-float (hi, lo) pairs: TwoSum (Knuth) carries the
-// rounding error of every hi addition into lo. Relative error of each sum
-// about 2^-48 per term, far below the float32 operator it applies.
-// (explicitly rounded operations: no contraction of the product into the sums)
-__device__ __forceinline__ void df_mac(float& hi, float& lo, float a, float xh, float xl) {
-  const float p = __fmul_rn(a, xh);
-  const float e = fmaf(a, xh, -p);
-  const float c = fmaf(a, xl, e);
-  const float s = __fadd_rn(hi, p);
-  const float v = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, v)), __fsub_rn(p, v));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, c));
-}
-
+// The same product for float64 vectors in double-float arithmetic (df_mac).
 template <int G>
 __global__ void __launch_bounds__(256) pair_gemv_multi_df_kernel(
     const float2* __restrict__ S, const float2* __restrict__ C, int64_t rows, int64_t cols, int64_t ld,

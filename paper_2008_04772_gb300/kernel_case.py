@@ -11,6 +11,9 @@ sphere (k = 5):
   free  three FP32 GMRES iterations with the matrix-free PMCHWT operator (A8);
   solve one complete solve of the benchmark workload (FP32 bulk, full D, tol 1e-5),
         for the launch list;
+  multi one FP32 solve of 32 incident directions with the near-field reduced
+        preconditioner Di (chi = 2h): the multi-vector CSR product, the 64-system
+        Gram BiCGStab and the double-float float64 refinement product;
   all   bc, gemv, gemm and free, in this order.
 """
 import sys
@@ -50,6 +53,12 @@ def main(which: str = "all") -> None:
         cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
                          opts=cal.solve_opts(precond="none", precision=cal.FP32, maxit=3, refine=0),
                          allow_not_converged=True)
+    if which == "multi":
+        d = meshgen.fibonacci_directions(32)
+        import numpy as np
+        inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+        cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, inc,
+                         opts=cal.solve_opts(precond="Di", near_cutoff_P=2.0, precision=cal.FP32, tol=1e-5))
     if which == "solve":
         sol = cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
                                opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-5))

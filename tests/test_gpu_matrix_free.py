@@ -117,10 +117,11 @@ def test_matrix_free_fp64_solve_matches_oracle(ctx):
 
 @pytest.mark.parametrize("name,k", [("sphere3", 4.0), ("prisms2", 3.0)])
 def test_fp32_operator_fp64_vectors_multi_equals_single(ctx, name, k):
-    """Float64 vectors on a float32 operator: several vectors at once use
-    double-float (float32 pair) products and sums, one vector at a time uses
-    float64 arithmetic. Both are the exact product of the float32 entries to
-    far below float32 rounding: bar 1e-12 relative (double-float: ~2^-48 per term)."""
+    """Float64 vectors on a float32 operator: several vectors at once (thread
+    per row, vectors staged in shared memory) and one vector at a time (warp
+    per row chunk, warp reduction) are two double-float (float32 pair)
+    implementations of the exact product of the float32 entries; they agree
+    far below float32 rounding: bar 1e-12 relative (~2^-48 per term)."""
     m = mesh(name)
     gm = cal.Mesh(ctx, m.verts, m.tris, m.domain)
     N = gm.info().n_edges

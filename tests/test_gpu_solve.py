@@ -114,6 +114,21 @@ def test_multiple_right_hand_sides_equal_solo_solves(ctx):
         assert rel(multi[q], solo) < 1e-5
 
 
+@pytest.mark.parametrize("nrhs", [1, 3])
+def test_refinement_reaches_tolerance_below_float32(ctx, nrhs):
+    """FP32 bulk with float64 refinement: the residual b - A x of the float32
+    operator is formed in double-float arithmetic (products exact, sums to
+    about 2^-48). A residual only float32-accurate would stall near 1e-7; the
+    refined solve must reach 1e-10."""
+    d = meshgen.fibonacci_directions(nrhs)
+    inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+    opts = cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-10, refine=5, maxit=400)
+    sol = cal.pmchwt_solve(ctx, gmesh(ctx, "sphere2"), 2.0, EPS, inc, opts=opts)
+    info = sol.info()
+    assert sol.rc == cal.OK and info.converged == 1
+    assert info.residual <= 1e-10, info.residual
+
+
 def test_far_field_approaches_mie(ctx):
     errs = []
     dirs = meshgen.sphere_cut_directions(37)
