@@ -148,6 +148,20 @@ __device__ __forceinline__ void df_cmac(float& hr, float& lr, float& hi, float& 
   df_mac(hi, li, mi, x.x, x.y);
 }
 
+// x [q][2n] (float64 complex), columns [off, off + cols) of both halves ->
+// xs [q][h][cols] as (re hi, re lo, im hi, im lo)
+__global__ void split_df_multi_kernel(const double2* __restrict__ x, int64_t n, int64_t off, int64_t cols,
+                                      int nrhs, float4* __restrict__ xs) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 2 * cols * nrhs) return;
+  const int64_t c = t % cols, qh = t / cols;
+  const int h = (int)(qh & 1);
+  const int64_t q = qh >> 1;
+  const double2 v = x[q * 2 * n + h * n + off + c];
+  const float rh = (float)v.x, ih = (float)v.y;
+  xs[t] = make_float4(rh, (float)(v.x - (double)rh), ih, (float)(v.y - (double)ih));
+}
+
 // x (float64 complex) -> (re hi, re lo, im hi, im lo)
 __global__ void split_df_kernel(const double2* __restrict__ x, float4* __restrict__ xs, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -615,6 +629,26 @@ __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi,
   ci = (ai * br - ar * bi) / d;
 }
 
+// The step scalars in the storage precision R: float32 on the FP32 path, where
+// the vectors they scale are float32 (float64 division is slow here); the
+// sums they come from stay float64.
+template <typename R>
+__device__ __forceinline__ void cdiv_r(double ar, double ai, double br, double bi, double& cr, double& ci) {
+  if constexpr (sizeof(R) == 4) {
+    // scale by a power of two near the larger part of b (exact; no float64
+    // division) so that |b|^2 stays in float range
+    const double sb = fmax(fabs(br), fabs(bi));
+    const int e = ((__double2hiint(sb) >> 20) & 0x7ff) - 1023;
+    const double sc = __hiloint2double((1023 - max(-1000, min(1000, e))) << 20, 0);  // 2^-e
+    const float xr = (float)(ar * sc), xi = (float)(ai * sc), yr = (float)(br * sc), yi = (float)(bi * sc);
+    const float inv = 1.0f / (yr * yr + yi * yi);
+    cr = (double)((xr * yr + xi * yi) * inv);
+    ci = (double)((xi * yr - xr * yi) * inv);
+  } else {
+    cdiv(ar, ai, br, bi, cr, ci);
+  }
+}
+
 template <int NV>
 __device__ __forceinline__ void block_accumulate(double (&v)[NV], double* dst) {
   __shared__ double sh[NV][32];
@@ -753,11 +787,11 @@ __global__ void bicg_k1(BiArgs<R> A, int k) {
     if (act && k > 0) {
       // beta = (rho_k / rho_{k-1}) (alpha_{k-1} / omega_{k-1})
       double rr, ri, alr, ali;
-      cdiv(ap[5], ap[6], a[5], a[6], rr, ri);           // rho_k / rho_{k-1}
-      cdiv(a[5], a[6], ap[0], ap[1], alr, ali);         // alpha_{k-1} = rho_{k-1}/(r0^H v_{k-1})
-      cdiv(ap[2], ap[3], ap[4], 0.0, omr, omi);         // omega_{k-1}
+      cdiv_r<R>(ap[5], ap[6], a[5], a[6], rr, ri);           // rho_k / rho_{k-1}
+      cdiv_r<R>(a[5], a[6], ap[0], ap[1], alr, ali);         // alpha_{k-1} = rho_{k-1}/(r0^H v_{k-1})
+      cdiv_r<R>(ap[2], ap[3], ap[4], 0.0, omr, omi);         // omega_{k-1}
       double tr, ti;
-      cdiv(alr, ali, omr, omi, tr, ti);
+      cdiv_r<R>(alr, ali, omr, omi, tr, ti);
       br = rr * tr - ri * ti;
       bi = rr * ti + ri * tr;
     }
@@ -815,7 +849,7 @@ __global__ void bicg_k2(BiArgs<R> A, int k) {
     if (act && blockIdx.x == 0) { a[5] = a[6] = a[7] = 0.0; }
     if (a[0] == 0.0 && a[1] == 0.0) act = false;
     double alr = 0.0, ali = 0.0;
-    if (act) cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
+    if (act) cdiv_r<R>(ap[5], ap[6], a[0], a[1], alr, ali);
     sc[3 * s] = act ? 1.0 : 0.0;
     sc[3 * s + 1] = alr;
     sc[3 * s + 2] = ali;
@@ -870,8 +904,8 @@ __global__ void bicg_k3(BiArgs<R> A, int k) {
     }
     double alr = 0, ali = 0, omr = 0, omi = 0;
     if (act) {
-      cdiv(ap[5], ap[6], a[0], a[1], alr, ali);
-      cdiv(a[2], a[3], a[4], 0.0, omr, omi);
+      cdiv_r<R>(ap[5], ap[6], a[0], a[1], alr, ali);
+      cdiv_r<R>(a[2], a[3], a[4], 0.0, omr, omi);
     }
     sc[5 * s] = act ? 1.0 : 0.0;
     sc[5 * s + 1] = alr; sc[5 * s + 2] = ali; sc[5 * s + 3] = omr; sc[5 * s + 4] = omi;
@@ -1188,9 +1222,10 @@ __global__ void __launch_bounds__(256) pair_gemv_multi_kernel(
 template <int G>
 __global__ void __launch_bounds__(256) pair_gemv_multi_df_kernel(
     const float2* __restrict__ S, const float2* __restrict__ C, int64_t rows, int64_t cols, int64_t ld,
-    const double2* __restrict__ x1, const double2* __restrict__ x2, int64_t xstride, double2* __restrict__ y1,
-    double2* __restrict__ y2, int nrhs, double ar, double ai, double br, double bi) {
-  __shared__ float4 xsh[2][G][MV_W];  // (re hi, re lo, im hi, im lo)
+    const float4* __restrict__ xs, int64_t xstride, double2* __restrict__ y1, double2* __restrict__ y2, int nrhs,
+    double ar, double ai, double br, double bi) {
+  // xs: x split into (re hi, re lo, im hi, im lo), [q][h][cols]; y stride xstride
+  __shared__ float4 xsh[2][G][MV_W];
   const int64_t nrb = (rows + 255) / 256;
   const int64_t nch = (cols + MV_W - 1) / MV_W;
   const int ngr = (nrhs + G - 1) / G;
@@ -1206,11 +1241,7 @@ __global__ void __launch_bounds__(256) pair_gemv_multi_df_kernel(
     for (int t = threadIdx.x; t < 2 * G * MV_W; t += 256) {
       const int c = t % MV_W, q = (t / MV_W) % G, h = t / (MV_W * G);
       float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (c < nc && q0 + q < nrhs) {
-        const double2 xv = (h ? x2 : x1)[(int64_t)(q0 + q) * xstride + c0 + c];
-        const float rh = (float)xv.x, ih = (float)xv.y;
-        v = make_float4(rh, (float)(xv.x - (double)rh), ih, (float)(xv.y - (double)ih));
-      }
+      if (c < nc && q0 + q < nrhs) v = xs[((int64_t)(q0 + q) * 2 + h) * cols + c0 + c];
       xsh[h][q][c] = v;
     }
     __syncthreads();
@@ -1276,9 +1307,18 @@ int pair_apply_multi(const BlockRef& b, int vec_prec, const void* x, void* y, in
   if (vec_prec == CAL_FP64) {
     const double2* xx = (const double2*)x;
     double2* yy = (double2*)y;
-    pair_gemv_multi_df_kernel<4><<<grid, 256, 0, st>>>(S, C, b.rows, b.cols, b.cols, xx + b.col_off,
-                                                      xx + n + b.col_off, 2 * n, yy + b.row_off,
+    // x split once into (hi, lo) floats; stream-ordered scratch
+    float4* xs = nullptr;
+    const int64_t nxs = 2 * b.cols * nrhs;
+    if (dalloc((void**)&xs, std::max<int64_t>(nxs, 1) * sizeof(float4), st) != cudaSuccess) {
+      prof_end(st, tok);
+      return fail(CAL_ENOMEM, "multi-vector GEMV: scratch allocation failed");
+    }
+    split_df_multi_kernel<<<(unsigned)((nxs + 255) / 256), 256, 0, st>>>(xx, n, b.col_off, b.cols, nrhs, xs);
+    note_launch();
+    pair_gemv_multi_df_kernel<4><<<grid, 256, 0, st>>>(S, C, b.rows, b.cols, b.cols, xs, 2 * n, yy + b.row_off,
                                                       yy + n + b.row_off, nrhs, ar, ai, br, bi);
+    dfree(xs, st);
   } else {
     const float2* xx = (const float2*)x;
     float2* yy = (float2*)y;
