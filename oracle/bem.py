@@ -19,7 +19,7 @@ import subprocess
 import numpy as np
 import scipy.sparse as sp
 
-from .quadrature import gauss_legendre_01, triangle_rule
+from .quadrature import CLASS_BOUNDS, CLASS_POINTS, gauss_legendre_01, triangle_rule
 from .spaces import aabb_distance
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
@@ -46,7 +46,7 @@ def lib():
         _LIB = ctypes.CDLL(build())
         d, l, i = ctypes.c_double, ctypes.c_long, ctypes.c_int
         P = ctypes.c_void_p
-        _LIB.orc_blocks.argtypes = [P, P, P, l, P, l, d, d, i, i, P, P, i, P, P, P, P, P]
+        _LIB.orc_blocks.argtypes = [P, P, P, l, P, l, d, d, i, P, P, P, d, d, i, P, P, P, P, P]
         _LIB.orc_blocks.restype = None
         _LIB.orc_ss_polynomial.argtypes = [P, P, i, P, P, P, P, i, P, P]
         _LIB.orc_ss_polynomial.restype = d
@@ -58,12 +58,23 @@ def _ptr(a):
 
 
 class Rules:
-    """Quadrature choice: regular points per triangle (6 or 1) and Gauss points per dimension (4 or 1)."""
+    """Quadrature choice: regular points per triangle and Gauss points per dimension.
+
+    n_regular = 6 or 1: that rule for every regular pair. n_regular = 0: the
+    near / medium / far classes with 6 / 4 / 3 points (orders 4 / 3 / 2, the
+    paper's defaults), bounds in ``quadrature.CLASS_BOUNDS``.
+    """
 
     def __init__(self, n_regular: int = 6, n_gauss: int = 4):
         self.n_regular = n_regular
         self.n_gauss = n_gauss
-        self.rb, self.rw = triangle_rule(n_regular)
+        pts = CLASS_POINTS if n_regular == 0 else (n_regular,) * 3
+        rules = [triangle_rule(n) for n in pts]
+        self.class_points = np.array(pts, dtype=np.int32)
+        self.class_rb = np.concatenate([r[0].reshape(-1) for r in rules])
+        self.class_rw = np.concatenate([r[1] for r in rules])
+        self.bounds = CLASS_BOUNDS
+        self.rb, self.rw = rules[0]
         self.gx, self.gw = gauss_legendre_01(n_gauss)
 
 
@@ -76,15 +87,16 @@ def local_blocks(X, ids, test, trial, k, rules: Rules, want=3, counts=None):
     n1, n2 = len(test), len(trial)
     S = np.zeros((n1, n2, 3, 3), dtype=np.complex128)
     C = np.zeros((n1, n2, 3, 3), dtype=np.complex128)
-    rb = np.ascontiguousarray(rules.rb, dtype=np.float64)
-    rw = np.ascontiguousarray(rules.rw, dtype=np.float64)
+    npts = np.ascontiguousarray(rules.class_points, dtype=np.int32)
+    rb = np.ascontiguousarray(rules.class_rb, dtype=np.float64)
+    rw = np.ascontiguousarray(rules.class_rw, dtype=np.float64)
     gx = np.ascontiguousarray(rules.gx, dtype=np.float64)
     gw = np.ascontiguousarray(rules.gw, dtype=np.float64)
     cnt = np.zeros(4, dtype=np.int64)
     k = complex(k)
     lib().orc_blocks(_ptr(X), _ptr(ids), _ptr(test), n1, _ptr(trial), n2, k.real, k.imag,
-                     int(want), rules.n_regular, _ptr(rb), _ptr(rw), rules.n_gauss, _ptr(gx),
-                     _ptr(gw), _ptr(S), _ptr(C), _ptr(cnt))
+                     int(want), _ptr(npts), _ptr(rb), _ptr(rw), rules.bounds[0], rules.bounds[1],
+                     rules.n_gauss, _ptr(gx), _ptr(gw), _ptr(S), _ptr(C), _ptr(cnt))
     if counts is not None:
         counts += cnt
     return S, C

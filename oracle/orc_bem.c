@@ -17,7 +17,9 @@
  * f_a(x) = (x - P_a) / (2|tau|), div f_a = 1/|tau|.
  *
  * Quadrature (Section 3.3): disjoint closures -> tensor product of a symmetric
- * triangle rule; shared vertex / edge / identical -> Sauter–Schwab rules on
+ * triangle rule, chosen by the pair's near / medium / far class (relative
+ * distance |c1 - c2| / max(d1, d2) of centroids and longest edges, against
+ * the bounds b_near, b_med); shared vertex / edge / identical -> Sauter–Schwab rules on
  * [0,1]^4 (2 / 5 / 6 sub-regions, Gauss–Legendre in each coordinate).  The
  * integrand is evaluated directly from the formulas above — no moment algebra.
  */
@@ -170,11 +172,36 @@ static int classify(const long *i1, const long *i2, int o1[3], int o2[3]) {
  * S, C: [n1][n2][3][3] complex (interleaved doubles); want bit 1 = S, 2 = C.
  * counts[0..3]: integrand evaluations for regular / vertex / edge / identical pairs.
  */
+/* centroid and longest edge of a triangle */
+static void tri_size(const tri_t *t, double *c, double *d) {
+    double l = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double e[3];
+        sub3(t->P[(a + 1) % 3], t->P[a], e);
+        const double q = sqrt(dot3(e, e));
+        if (q > l) l = q;
+    }
+    for (int k = 0; k < 3; ++k) c[k] = (t->P[0][k] + t->P[1][k] + t->P[2][k]) / 3.0;
+    *d = l;
+}
+
+/* class of a regular pair: 0 near, 1 medium, 2 far */
+static int regular_class(const tri_t *t1, const tri_t *t2, double b_near, double b_med) {
+    double c1[3], c2[3], d1, d2, dc[3];
+    tri_size(t1, c1, &d1);
+    tri_size(t2, c2, &d2);
+    sub3(c1, c2, dc);
+    const double rel = sqrt(dot3(dc, dc)) / (d1 > d2 ? d1 : d2);
+    return rel <= b_near ? 0 : (rel <= b_med ? 1 : 2);
+}
+
+/* npts[3], rbary (3 npts[c] per class, concatenated), rw (npts[c] per class):
+ * the near / medium / far rules; the same rule three times for one rule. */
 void orc_blocks(const double *X, const long *ids, const long *test, long n1,
                 const long *trial, long n2, double kr, double ki, int want,
-                int nreg, const double *rbary, const double *rw, int ng,
-                const double *gx, const double *gw, double *Sout, double *Cout,
-                long *counts) {
+                const int *npts, const double *rbary_all, const double *rw_all, double b_near,
+                double b_med, int ng, const double *gx, const double *gw, double *Sout,
+                double *Cout, long *counts) {
     cplx k = kr + I * ki;
     long cnt[4] = {0, 0, 0, 0};
 #pragma omp parallel
@@ -194,6 +221,11 @@ void orc_blocks(const double *X, const long *ids, const long *test, long n1,
                 int o1[3], o2[3];
                 int cls = classify(i1, i2, o1, o2);
                 if (cls == 0) {
+                    const int rc = regular_class(&t1, &t2, b_near, b_med);
+                    int off = 0;
+                    for (int c = 0; c < rc; ++c) off += npts[c];
+                    const int nreg = npts[rc];
+                    const double *rbary = rbary_all + 3 * off, *rw = rw_all + off;
                     for (int u = 0; u < nreg; ++u) {
                         double x[3], y[3];
                         for (int c = 0; c < 3; ++c)

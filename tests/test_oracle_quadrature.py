@@ -20,7 +20,7 @@ def test_gauss_legendre_exact_to_degree_2n_minus_1(n):
     assert abs(np.dot(w, x ** (2 * n)) - 1.0 / (2 * n + 1)) > 1e-12
 
 
-@pytest.mark.parametrize("npts,degree", [(1, 1), (3, 2), (6, 4)])
+@pytest.mark.parametrize("npts,degree", [(1, 1), (3, 2), (4, 3), (6, 4)])
 def test_triangle_rule_exact_monomials(npts, degree):
     # int over the unit triangle of l1^a l2^b l3^c, normalised by area:
     # 2 a! b! c! / (a+b+c+2)!
@@ -104,3 +104,42 @@ def test_evaluation_counts_match_paper(oracle_lib):
             cnt = np.zeros(4, dtype=np.int64)
             bem.local_blocks(X, ids, test, trial, 1.0, rules, 3, cnt)
             assert cnt[col] == expect and cnt.sum() == expect
+
+
+@pytest.mark.parametrize("rel,expect", [(1.5, 36), (3.0, 16), (6.0, 9)])
+def test_regular_class_by_relative_distance(oracle_lib, rel, expect):
+    # Section 3.3: the default orders (4, 3, 2) give 36 / 16 / 9 evaluations for
+    # near / medium / far pairs; the class follows |c1 - c2| / max(d1, d2)
+    # (bounds 2 and 4). Two copies of a right triangle (longest edge sqrt 2).
+    T = np.array([[0.0, 0.0, 0.0], [1.0, 0.0, 0.0], [0.0, 1.0, 0.0]])
+    L = rel * math.sqrt(2.0)
+    X = np.concatenate([T, T + np.array([0.0, 0.0, L])])
+    ids = np.array([[0, 1, 2], [3, 4, 5]])
+    cnt = np.zeros(4, dtype=np.int64)
+    bem.local_blocks(X, ids, [0], [1], 1.5, bem.Rules(0, 4), 3, cnt)
+    assert cnt[0] == expect and cnt.sum() == expect
+
+
+@pytest.mark.parametrize("rel", [3.0, 6.0, 12.0])
+def test_medium_and_far_rules_approach_the_near_rule(oracle_lib, rel):
+    # The cheaper rules integrate the same smooth integrand: the classed blocks
+    # of a medium or far pair stay within the low-order rules' error of the
+    # 36-point ones (about (k d)^3 for the oscillatory factor, d the element size).
+    rng = np.random.default_rng(int(rel))
+    T1 = rng.normal(size=(3, 3)) * 0.5
+    T2 = rng.normal(size=(3, 3)) * 0.5
+    d = max(np.linalg.norm(T1[(a + 1) % 3] - T1[a]) for a in range(3))
+    d = max(d, max(np.linalg.norm(T2[(a + 1) % 3] - T2[a]) for a in range(3)))
+    shift = np.array([1.0, 0.3, -0.2]) / np.linalg.norm([1.0, 0.3, -0.2])
+    c1, c2 = T1.mean(0), T2.mean(0)
+    T2 = T2 - c2 + c1 + shift * rel * d * 1.01
+    X = np.concatenate([T1, T2])
+    ids = np.array([[0, 1, 2], [3, 4, 5]])
+    errs = []
+    # wavenumbers with k d about 0.5 and 0.25, as on a mesh of several elements per wavelength
+    for k in (0.5 / d, 0.25 / d * (1.0 + 0.02j)):
+        Sc, Cc = bem.local_blocks(X, ids, [0], [1], k, bem.Rules(0, 4))
+        Sn, Cn = bem.local_blocks(X, ids, [0], [1], k, bem.Rules(6, 4))
+        errs.append(max(np.abs(Sc - Sn).max() / np.abs(Sn).max(), np.abs(Cc - Cn).max() / np.abs(Cn).max()))
+        assert not np.allclose(Sc, Sn, rtol=1e-14, atol=0)  # a different rule was used
+    assert max(errs) < {3.0: 1e-3, 6.0: 5e-4, 12.0: 5e-4}[rel], errs
