@@ -134,7 +134,11 @@ void cal_space_destroy(cal_space* space);
    bounding boxes of the supports are <= near_cutoff apart (eq. nf_condition
    read at entry level) and the result is CSR (BC spaces only).
    q_regular: points per triangle of the regular tensor rule, 6 (degree 4,
-   36 evaluations per pair) or 1 (centroid); q_singular: Gauss–Legendre
+   36 evaluations per pair) or 1 (centroid) for every regular pair; or 0: by
+   the pair's class (Section 3.3, default orders q_near, q_medium, q_far =
+   4, 3, 2): 6, 4 or 3 points (36 / 16 / 9 evaluations) for a pair whose
+   centroid distance is <= 2, <= 4 or > 4 times the longer of the two
+   longest edges (the paper names the classes, not these bounds); q_singular: Gauss–Legendre
    points per dimension of the Sauter–Schwab rules, 1..16 (4 gives the
    paper's 512/1280/1536 evaluations). precision: CAL_FP64, CAL_FP32 or
    CAL_FP32_ALL. */
@@ -193,7 +197,7 @@ int cal_gram_export(cal_space* rwg, cal_space* bc, double* dst_host);
 typedef struct {
   int32_t precond;          /* CAL_PRECOND_*                                   */
   int32_t precision;        /* CAL_FP64, CAL_FP32 (FP32 bulk) or CAL_FP32_ALL  */
-  int32_t q_regular_A, q_singular_A;   /* A's rules (6, 4 = paper default)     */
+  int32_t q_regular_A, q_singular_A;   /* A's rules (6 / 1 / 0 = by class, 4)  */
   int32_t q_regular_P, q_singular_P;   /* P's rules (bi-parametric: 1, 1)      */
   double near_cutoff_P;     /* chi_P in units of h; INFINITY = dense P          */
   double tol;               /* GMRES relative preconditioned residual           */

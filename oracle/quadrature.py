@@ -11,6 +11,8 @@ evaluations for coincident/edge/vertex pairs, q = 1: 6/5/2).
 Near / medium / far (the paper names the classes, not their bounds): a pair
 is near if |c1 - c2| <= 2 max(d1, d2), medium if <= 4 max(d1, d2), far
 otherwise, with c the centroids and d the longest edges of the triangles.
+The bounds carry a relative margin of 2^-20, so that pairs exactly at 2 or 4
+(common on structured meshes) fall on the same side in every precision.
 """
 import numpy as np
 
@@ -35,7 +37,7 @@ _DUNAVANT6 = ((0.445948490915965, 0.223381589678011),
 
 
 # relative distance bounds of the near and medium classes (see the module note)
-CLASS_BOUNDS = (2.0, 4.0)
+CLASS_BOUNDS = (2.0 * (1.0 + 2.0 ** -20), 4.0 * (1.0 + 2.0 ** -20))
 # points per triangle of the near, medium and far rules at the default orders
 CLASS_POINTS = (6, 4, 3)
 

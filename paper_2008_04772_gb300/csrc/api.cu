@@ -1042,7 +1042,8 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   P.A_int.resize(P.M);
   if (o.matrix_free) {
     // only the touching-pair entries are stored; the rest is recomputed per application
-    if (o.q_regular_A != 6 && o.q_regular_A != 1) return fail(CAL_EINVAL, "q_regular must be 6 or 1");
+    if (o.q_regular_A != 6 && o.q_regular_A != 1 && o.q_regular_A != 0)
+      return fail(CAL_EINVAL, "q_regular must be 6, 1 or 0 (classes)");
     if ((rc = assemble_singular_block(ctx->impl, k_ext, 0.0, *P.rwg, -1, o.q_singular_A, aprec, P.A_ext)))
       return rc;
     for (int m = 0; m < P.M; ++m)

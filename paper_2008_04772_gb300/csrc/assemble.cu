@@ -31,25 +31,39 @@ namespace cal {
 // ---------------------------------------------------------------------------
 // rules passed by value
 // ---------------------------------------------------------------------------
+// Regular rules: nreg = 6 or 1 applies that rule to every regular pair (table
+// entries 0 .. nreg-1). nreg = 0 selects by the pair's class (Section 3.3,
+// default orders q_near, q_medium, q_far = 4, 3, 2): the near rule (6 points)
+// at entries 0..5, the medium rule (4 points) at 6..9, the far rule (3 points)
+// at 10..12. A pair is near if |c1 - c2| <= 2 max(d1, d2), medium if <= 4 max,
+// far otherwise (c centroids, d longest edges; the paper states no bounds), the
+// bounds with a relative margin of 2^-20 (pair_class).
 struct Rules {
-  float rbf[18], rwf[6];
-  double rbd[18], rwd[6];
+  float rbf[39], rwf[13];
+  double rbd[39], rwd[13];
   double gx[16], gw[16];
   int nreg, ng;
 };
+constexpr int RULE_OFF_MEDIUM = 6, RULE_OFF_FAR = 10, RULE_POINTS_ALL = 13;
 
 // per host thread: request streams driven from several threads may use different rules
 static thread_local Rules g_rules;
 
 int set_quadrature_tables(int nreg, int nsing) {
-  if (nreg != 6 && nreg != 1) return fail(CAL_EINVAL, "q_regular must be 6 or 1 (got %d)", nreg);
+  if (nreg != 6 && nreg != 1 && nreg != 0)
+    return fail(CAL_EINVAL, "q_regular must be 6, 1 or 0 (classes) (got %d)", nreg);
   if (nsing < 1 || nsing > 16) return fail(CAL_EINVAL, "q_singular must be in 1..16 (got %d)", nsing);
-  std::vector<double> b, w, x, gw;
-  triangle_rule(nreg, b, w);
+  std::vector<double> x, gw;
   gauss_legendre01(nsing, x, gw);
   Rules r{};
-  for (int i = 0; i < 3 * nreg; ++i) { r.rbd[i] = b[i]; r.rbf[i] = (float)b[i]; }
-  for (int i = 0; i < nreg; ++i) { r.rwd[i] = w[i]; r.rwf[i] = (float)w[i]; }
+  int at = 0;
+  for (int n : (nreg == 0 ? std::vector<int>{6, 4, 3} : std::vector<int>{nreg})) {
+    std::vector<double> b, w;
+    triangle_rule(n, b, w);
+    for (int i = 0; i < 3 * n; ++i) { r.rbd[3 * at + i] = b[i]; r.rbf[3 * at + i] = (float)b[i]; }
+    for (int i = 0; i < n; ++i) { r.rwd[at + i] = w[i]; r.rwf[at + i] = (float)w[i]; }
+    at += n;
+  }
   for (int i = 0; i < nsing; ++i) { r.gx[i] = x[i]; r.gw[i] = gw[i]; }
   r.nreg = nreg;
   r.ng = nsing;
@@ -347,40 +361,46 @@ __device__ __forceinline__ P4<double> staged_point(const TriD& t, const Rules& r
 // centroid difference from staged centroids: float keeps hi + lo parts
 template <typename R> struct Cent;
 template <> struct Cent<float> {
-  float hi[3], lo[3];
-  __device__ void set(const TriF& t) { for (int c = 0; c < 3; ++c) { hi[c] = t.chi[c]; lo[c] = t.clo[c]; } }
+  float hi[3], lo[3], d;  // d: longest edge
+  __device__ void set(const TriF& t) {
+    for (int c = 0; c < 3; ++c) { hi[c] = t.chi[c]; lo[c] = t.clo[c]; }
+    d = t.diam;
+  }
   __device__ V3<float> minus(const Cent& b) const {
     return {(hi[0] - b.hi[0]) + (lo[0] - b.lo[0]), (hi[1] - b.hi[1]) + (lo[1] - b.lo[1]),
             (hi[2] - b.hi[2]) + (lo[2] - b.lo[2])};
   }
 };
 template <> struct Cent<double> {
-  double c[3];
-  __device__ void set(const TriD& t) { for (int q = 0; q < 3; ++q) c[q] = t.c[q]; }
+  double c[3], d;  // d: longest edge
+  __device__ void set(const TriD& t) {
+    for (int q = 0; q < 3; ++q) c[q] = t.c[q];
+    d = t.diam;
+  }
   __device__ V3<double> minus(const Cent& b) const { return {c[0] - b.c[0], c[1] - b.c[1], c[2] - b.c[2]}; }
 };
 
 // triangle loaders: quadrature points relative to the centroid and weights
 template <int NREG>
-__device__ __forceinline__ void load_points(const TriF& t, const Rules& rl, V3<float>* p, float* w) {
+__device__ __forceinline__ void load_points(const TriF& t, const Rules& rl, V3<float>* p, float* w, int off = 0) {
 #pragma unroll
   for (int q = 0; q < NREG; ++q) {
-    const float b0 = rl.rbf[3 * q], b1 = rl.rbf[3 * q + 1], b2 = rl.rbf[3 * q + 2];
+    const float b0 = rl.rbf[3 * (off + q)], b1 = rl.rbf[3 * (off + q) + 1], b2 = rl.rbf[3 * (off + q) + 2];
     p[q] = {b0 * t.off[0][0] + b1 * t.off[1][0] + b2 * t.off[2][0],
             b0 * t.off[0][1] + b1 * t.off[1][1] + b2 * t.off[2][1],
             b0 * t.off[0][2] + b1 * t.off[1][2] + b2 * t.off[2][2]};
-    w[q] = rl.rwf[q] * t.area;
+    w[q] = rl.rwf[off + q] * t.area;
   }
 }
 template <int NREG>
-__device__ __forceinline__ void load_points(const TriD& t, const Rules& rl, V3<double>* p, double* w) {
+__device__ __forceinline__ void load_points(const TriD& t, const Rules& rl, V3<double>* p, double* w, int off = 0) {
 #pragma unroll
   for (int q = 0; q < NREG; ++q) {
-    const double b0 = rl.rbd[3 * q], b1 = rl.rbd[3 * q + 1], b2 = rl.rbd[3 * q + 2];
+    const double b0 = rl.rbd[3 * (off + q)], b1 = rl.rbd[3 * (off + q) + 1], b2 = rl.rbd[3 * (off + q) + 2];
     p[q] = {b0 * t.off[0][0] + b1 * t.off[1][0] + b2 * t.off[2][0],
             b0 * t.off[0][1] + b1 * t.off[1][1] + b2 * t.off[2][1],
             b0 * t.off[0][2] + b1 * t.off[1][2] + b2 * t.off[2][2]};
-    w[q] = rl.rwd[q] * t.area;
+    w[q] = rl.rwd[off + q] * t.area;
   }
 }
 __device__ __forceinline__ V3<float> centroid_delta(const TriF& a, const TriF& b) {
@@ -400,6 +420,54 @@ __device__ __forceinline__ bool touching(const TRI& a, const TRI& b) {
   return t;
 }
 
+// class of a regular pair: 0 near, 1 medium, 2 far: |D|^2 against (2 b dmax)^2
+// and (4 b dmax)^2 with b = 1 + 2^-20 (a margin far above float32 rounding of
+// the distance, so that ties exactly at 2 or 4 are near / medium on every path)
+template <typename R>
+__device__ __forceinline__ int pair_class(const V3<R>& D, R d1, R d2) {
+  constexpr double B = 1.0 + 1.0 / 1048576.0;
+  const R dm = d1 > d2 ? d1 : d2;
+  const R r2 = D.x * D.x + D.y * D.y + D.z * D.z, m2 = dm * dm;
+  return r2 <= R(4.0 * B * B) * m2 ? 0 : (r2 <= R(16.0 * B * B) * m2 ? 1 : 2);
+}
+
+template <typename R, int N, typename TRI>
+__device__ __forceinline__ void pair_moments_n(const TRI& A, const TRI& B, const Rules& rl, int off, const V3<R>& D,
+                                               R kr, R ki, bool wantC, Mom<R>& m) {
+  V3<R> xi[N], eta[N];
+  R wx[N], wy[N];
+  load_points<N>(A, rl, xi, wx, off);
+  load_points<N>(B, rl, eta, wy, off);
+  regular_moments<R, N>(xi, wx, eta, wy, D, kr, ki, wantC, m);
+}
+
+// moments of a regular pair with the rule NREG (6 or 1), or by class (NREG 0);
+// returns the integrand evaluations
+template <typename R, int NREG, typename TRI>
+__device__ __forceinline__ int pair_moments(const TRI& A, const TRI& B, const Rules& rl, const V3<R>& D, R kr, R ki,
+                                            bool wantC, Mom<R>& m) {
+  if constexpr (NREG > 0) {
+    pair_moments_n<R, NREG>(A, B, rl, 0, D, kr, ki, wantC, m);
+    return NREG * NREG;
+  } else {
+    const int c = pair_class<R>(D, (R)A.diam, (R)B.diam);
+    if (c == 2) { pair_moments_n<R, 3>(A, B, rl, RULE_OFF_FAR, D, kr, ki, wantC, m); return 9; }
+    if (c == 1) { pair_moments_n<R, 4>(A, B, rl, RULE_OFF_MEDIUM, D, kr, ki, wantC, m); return 16; }
+    pair_moments_n<R, 6>(A, B, rl, 0, D, kr, ki, wantC, m);
+    return 36;
+  }
+}
+
+// adds a per-thread count to *cnt with one atomic per converged group of lanes
+__device__ __forceinline__ void count_add(unsigned long long* cnt, unsigned v) {
+  if (!cnt) return;
+  unsigned lane;
+  asm volatile("mov.u32 %0, %%laneid;" : "=r"(lane));
+  const unsigned mask = __activemask();
+  const unsigned tot = __reduce_add_sync(mask, v);
+  if (lane == (unsigned)(__ffs(mask) - 1) && tot) atomicAdd(cnt, (unsigned long long)tot);
+}
+
 template <typename R> struct TriOf;
 template <> struct TriOf<float> { using T = TriF; };
 template <> struct TriOf<double> { using T = TriD; };
@@ -414,7 +482,7 @@ template <typename R, int NREG>
 __global__ void __launch_bounds__(256) rwg_regular_kernel(
     const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
     const R* __restrict__ slot_sw, int64_t t0, int64_t ntr, R kr, R ki, R mikr, R miki, R c4r,
-    R c4i, bool wantS, bool wantC, Rules rl, Sink<R> out) {
+    R c4i, bool wantS, bool wantC, Rules rl, Sink<R> out, unsigned long long* cnt) {
   using TRI = typename TriOf<R>::T;
   const int bi = blockIdx.y, bj = blockIdx.x;
   if (bi > bj) return;
@@ -425,13 +493,10 @@ __global__ void __launch_bounds__(256) rwg_regular_kernel(
   const TRI A = tri[t1];
   const TRI B = tri[t2];
   if (touching(A, B)) return;
-  V3<R> xi[NREG], eta[NREG];
-  R wx[NREG], wy[NREG];
-  load_points<NREG>(A, rl, xi, wx);
-  load_points<NREG>(B, rl, eta, wy);
   const V3<R> D = centroid_delta(A, B);
   Mom<R> m;
-  regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, wantC, m);
+  const int ev = pair_moments<R, NREG>(A, B, rl, D, kr, ki, wantC, m);
+  count_add(cnt, (unsigned)ev);
   R pc[36];
   pair_coeffs(m, D, pc);
 #pragma unroll
@@ -482,7 +547,8 @@ template <typename R, int NREG, typename VT, typename AT>
 __global__ void __launch_bounds__(256) rwg_free_kernel(
     const typename TriOf<R>::T* __restrict__ tri, const int* __restrict__ slot_edge,
     const R* __restrict__ slot_sw, int64_t t0, int64_t ntr, R kr, R ki, R mikr, R miki, R c4r, R c4i,
-    Rules rl, const VT* __restrict__ x, VT* __restrict__ y, int64_t n, int nrhs, AT ar, AT ai, AT br, AT bi) {
+    Rules rl, const VT* __restrict__ x, VT* __restrict__ y, int64_t n, int nrhs, AT ar, AT ai, AT br, AT bi,
+    unsigned long long* cnt) {
   using TRI = typename TriOf<R>::T;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   // acc[((((side * 16 + t) * 3 + slot) * 2 + half) * nrhs + rhs) * 2 + (re, im)]
@@ -507,13 +573,10 @@ __global__ void __launch_bounds__(256) rwg_free_kernel(
     const TRI B = tri[t2];
     active = !touching(A, B);
     if (active) {
-      V3<R> xi[NREG], eta[NREG];
-      R wx[NREG], wy[NREG];
-      load_points<NREG>(A, rl, xi, wx);
-      load_points<NREG>(B, rl, eta, wy);
       const V3<R> D = centroid_delta(A, B);
       Mom<R> m;
-      regular_moments<R, NREG>(xi, wx, eta, wy, D, kr, ki, true, m);
+      const int ev = pair_moments<R, NREG>(A, B, rl, D, kr, ki, true, m);
+      count_add(cnt, (unsigned)(ev * nrhs));
       R pc[36];
       pair_coeffs(m, D, pc);
 #pragma unroll
@@ -677,14 +740,18 @@ struct CellData {
   int* vid;      // [ncelltri][3]
 };
 
+// staged points per triangle: the rule's, or all three class rules (13)
+template <int NREG> __host__ __device__ constexpr int staged_points() { return NREG > 0 ? NREG : RULE_POINTS_ALL; }
+
 template <typename R, int NREG>
 __global__ void bc_cell_prep_kernel(const typename TriOf<R>::T* __restrict__ tri, const R* __restrict__ slot_sw,
                                     int nslot, const int* __restrict__ cell_tri, int64_t ncelltri, Rules rl,
                                     CellData<R> cd) {
+  constexpr int NS = staged_points<NREG>();
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ncelltri * NREG) return;
-  const int64_t t = q / NREG;
-  const int u = (int)(q % NREG);
+  if (q >= ncelltri * NS) return;
+  const int64_t t = q / NS;
+  const int u = (int)(q % NS);
   const int tau = cell_tri[t];
   const typename TriOf<R>::T T = tri[tau];
   cd.pts[q] = staged_point(T, rl, u);
@@ -703,7 +770,8 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
     CellData<R> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
     const int* __restrict__ cell_edge, const BcUnit* __restrict__ units, int64_t nunits,
     const int* __restrict__ wlist, R kr, R ki, R mikr, R miki, R c4r, R c4i, bool wantS, bool wantC,
-    Sink<R> out, int max_cell, int chunk) {
+    Sink<R> out, int max_cell, int chunk, unsigned long long* cnt) {
+  constexpr int NS = staged_points<NREG>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R* pcs = reinterpret_cast<R*>(smem_raw);                        // [chunk * max_cell][36]
   R* red = pcs + (size_t)chunk * max_cell * 36;                   // [chunk][nslot][BC_RED]
@@ -711,9 +779,9 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
   const size_t staged_off =
       ((((size_t)chunk * max_cell * 36 + (size_t)chunk * nslot * BC_RED + (size_t)nslot * nslot * 4) *
             sizeof(R) + 15) / 16) * 16;
-  P4<R>* ptsA = reinterpret_cast<P4<R>*>(smem_raw + staged_off);  // [max_cell][NREG]
-  P4<R>* ptsB = ptsA + (size_t)max_cell * NREG;
-  P4<R>* swA = ptsB + (size_t)max_cell * NREG;                    // [max_cell][nslot] (s, w)
+  P4<R>* ptsA = reinterpret_cast<P4<R>*>(smem_raw + staged_off);  // [max_cell][NS]
+  P4<R>* ptsB = ptsA + (size_t)max_cell * NS;
+  P4<R>* swA = ptsB + (size_t)max_cell * NS;                      // [max_cell][nslot] (s, w)
   P4<R>* swB = swA + (size_t)max_cell * nslot;
   Cent<R>* cA = reinterpret_cast<Cent<R>*>(swB + (size_t)max_cell * nslot);
   Cent<R>* cB = cA + max_cell;
@@ -723,9 +791,9 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
   // coefficients: contiguous copies of the cell-ordered arrays
   auto stage_cell = [&](int cell, P4<R>* pts, Cent<R>* cen, int* vid, P4<R>* swc) {
     const int b0 = cell_ptr[cell], n = cell_ptr[cell + 1] - b0;
-    const P4<R>* sp = cd.pts + (size_t)b0 * NREG;
+    const P4<R>* sp = cd.pts + (size_t)b0 * NS;
     const P4<R>* ss = cd.sw + (size_t)b0 * nslot;
-    for (int q = threadIdx.x; q < n * NREG; q += TT) pts[q] = sp[q];
+    for (int q = threadIdx.x; q < n * NS; q += TT) pts[q] = sp[q];
     for (int q = threadIdx.x; q < n * nslot; q += TT) swc[q] = ss[q];
     const int* sc = reinterpret_cast<const int*>(cd.cen + b0);
     int* dc = reinterpret_cast<int*>(cen);
@@ -735,6 +803,7 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
   };
   // the slots of every triangle of a cell are the cell's edges, in one order
   auto nvalid = [&](int cell) { return cell_edge_ptr[cell + 1] - cell_edge_ptr[cell]; };
+  unsigned evals = 0;  // integrand evaluations of this thread (profiling count)
   for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
     const BcUnit U = units[uidx];
     const int v = U.v;
@@ -769,7 +838,24 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
           } else {
             const V3<R> D = cA[i1].minus(cB[i2]);
             Mom<R> m;
-            regular_moments_staged<R, NREG>(ptsA + i1 * NREG, ptsB + i2 * NREG, D, kr, ki, wantC, m);
+            const P4<R>* X = ptsA + i1 * NS;
+            const P4<R>* Y = ptsB + i2 * NS;
+            if constexpr (NREG > 0) {
+              regular_moments_staged<R, NREG>(X, Y, D, kr, ki, wantC, m);
+              evals += NREG * NREG;
+            } else {
+              const int c = pair_class<R>(D, cA[i1].d, cB[i2].d);
+              if (c == 2) {
+                regular_moments_staged<R, 3>(X + RULE_OFF_FAR, Y + RULE_OFF_FAR, D, kr, ki, wantC, m);
+                evals += 9;
+              } else if (c == 1) {
+                regular_moments_staged<R, 4>(X + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki, wantC, m);
+                evals += 16;
+              } else {
+                regular_moments_staged<R, 6>(X, Y, D, kr, ki, wantC, m);
+                evals += 36;
+              }
+            }
             pair_coeffs(m, D, tmp);
           }
           vcopy(pcs + (size_t)p * 36, tmp, 36);
@@ -867,6 +953,7 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
       }
     }
   }
+  count_add(cnt, evals);
 }
 
 // ---------------------------------------------------------------------------
@@ -1707,13 +1794,11 @@ static int rwg_regular_t(const AssembleArgs& a) {
     for (const SingPair& q : s.sing[d]) nsing += q.cls == 1 ? 2 : 1;
   const double units = ((double)ntr * (ntr - 1) / 2 - (double)(nsing - ntr) / 2) * a.nreg * a.nreg;
   const int tok = prof_begin(a.stream, "rwg_regular", units);
-  if (a.nreg == 6) {
-    rwg_regular_kernel<R, 6><<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki,
-                                                            mikr, miki, c4r, c4i, wS, wC, g_rules, out);
-  } else {
-    rwg_regular_kernel<R, 1><<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki,
-                                                            mikr, miki, c4r, c4i, wS, wC, g_rules, out);
-  }
+  // by class the evaluations depend on the geometry: counted on the device
+  unsigned long long* cnt = a.nreg == 0 ? prof_counter(tok, a.stream) : nullptr;
+  auto kern = a.nreg == 6 ? rwg_regular_kernel<R, 6> : (a.nreg == 1 ? rwg_regular_kernel<R, 1> : rwg_regular_kernel<R, 0>);
+  kern<<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
+                                     g_rules, out, cnt);
   prof_end(a.stream, tok);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
@@ -1741,9 +1826,10 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   // test-cell triangles are processed in chunks so that any valence fits
   auto smem_for = [&](int ch) {
     const size_t reals = (size_t)ch * max_cell * 36 + (size_t)ch * s.nslot * BC_RED + (size_t)s.nslot * s.nslot * 4;
-    const size_t staged = 2 * (size_t)max_cell * a.nreg * 4 * sizeof(R) +      // points
+    const size_t ns = a.nreg > 0 ? (size_t)a.nreg : (size_t)RULE_POINTS_ALL;
+    const size_t staged = 2 * (size_t)max_cell * ns * 4 * sizeof(R) +           // points
                           2 * (size_t)max_cell * s.nslot * 4 * sizeof(R) +     // slot coefficients
-                          2 * (size_t)max_cell * 24 +                          // centroids
+                          2 * (size_t)max_cell * sizeof(Cent<R>) +             // centroids
                           2 * (size_t)max_cell * 3 * sizeof(int);              // vertex ids
     return ((reals * sizeof(R) + 15) / 16) * 16 + staged + 64;
   };
@@ -1759,7 +1845,8 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   const int64_t nct = (int64_t)s.cell_tri.size();
   const int nreg = a.nreg;
   CellData<R> cd{};
-  const size_t b_pts = (size_t)nct * nreg * sizeof(P4<R>), b_sw = (size_t)nct * s.nslot * sizeof(P4<R>);
+  const int nsp = nreg > 0 ? nreg : RULE_POINTS_ALL;  // staged points per triangle
+  const size_t b_pts = (size_t)nct * nsp * sizeof(P4<R>), b_sw = (size_t)nct * s.nslot * sizeof(P4<R>);
   const size_t b_cen = (size_t)nct * sizeof(Cent<R>), b_vid = (size_t)nct * 3 * sizeof(int);
   auto r256 = [](size_t b) { return (b + 255) / 256 * 256; };
   unsigned char* buf = nullptr;
@@ -1768,15 +1855,11 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   cd.sw = reinterpret_cast<P4<R>*>(buf + r256(b_pts));
   cd.cen = reinterpret_cast<Cent<R>*>(buf + r256(b_pts) + r256(b_sw));
   cd.vid = reinterpret_cast<int*>(buf + r256(b_pts) + r256(b_sw) + r256(b_cen));
-  if (nreg == 6)
-    bc_cell_prep_kernel<R, 6><<<(unsigned)((nct * 6 + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri,
-                                                                                       nct, g_rules, cd);
-  else
-    bc_cell_prep_kernel<R, 1><<<(unsigned)((nct + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri,
-                                                                                   nct, g_rules, cd);
+  auto prep = nreg == 6 ? bc_cell_prep_kernel<R, 6> : (nreg == 1 ? bc_cell_prep_kernel<R, 1> : bc_cell_prep_kernel<R, 0>);
+  prep<<<(unsigned)((nct * nsp + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri, nct, g_rules, cd);
   note_launch();
   constexpr int TT = 128;
-  auto kern = nreg == 6 ? bc_tile_kernel<R, 6, TT> : bc_tile_kernel<R, 1, TT>;
+  auto kern = nreg == 6 ? bc_tile_kernel<R, 6, TT> : (nreg == 1 ? bc_tile_kernel<R, 1, TT> : bc_tile_kernel<R, 0, TT>);
   int rc = ensure_dyn_smem((const void*)kern, (int)smem);
   int per_sm = 0;
   if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TT, smem) != cudaSuccess)
@@ -1784,9 +1867,10 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   if (!rc) {
     const int64_t grid = std::min<int64_t>(nunits, (int64_t)std::max(1, per_sm) * n_sm * 2);
     const int tok = prof_begin(a.stream, "bc_tile", work);
+    unsigned long long* cnt = nreg == 0 ? prof_counter(tok, a.stream) : nullptr;
     kern<<<(unsigned)grid, TT, smem, a.stream>>>(cd, s.nslot, s.d_cell_tri_ptr, s.d_cell_edge_ptr, s.d_cell_edge,
                                                 units, nunits, wlist, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
-                                                out, max_cell, chunk);
+                                                out, max_cell, chunk, cnt);
     prof_end(a.stream, tok);
     note_launch();
     if (cudaGetLastError() != cudaSuccess) rc = fail(CAL_ECUDA, "bc tile kernel launch failed");
@@ -1893,12 +1977,14 @@ static int rwg_free_t(const Space& s, int scat, double kr, double ki, int nreg, 
   for (int r0 = 0; r0 < nrhs; r0 += 32) {
     const int nr = std::min(32, nrhs - r0);
     const int smem = 2 * 16 * 3 * 2 * nr * 2 * (int)sizeof(AT);
-    auto kern = nreg == 6 ? rwg_free_kernel<R, 6, VT, AT> : rwg_free_kernel<R, 1, VT, AT>;
+    auto kern = nreg == 6 ? rwg_free_kernel<R, 6, VT, AT>
+                          : (nreg == 1 ? rwg_free_kernel<R, 1, VT, AT> : rwg_free_kernel<R, 0, VT, AT>);
     if (int rc = ensure_dyn_smem((const void*)kern, smem)) return rc;
     const int tok = prof_begin(st, "rwg_free", units * nr);
+    unsigned long long* cnt = nreg == 0 ? prof_counter(tok, st) : nullptr;
     kern<<<grid, block, smem, st>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)kr, (R)ki, mikr, miki, c4r, c4i, g_rules,
                                     x + (int64_t)r0 * 2 * n, y + (int64_t)r0 * 2 * n, n, nr, (AT)ar, (AT)ai,
-                                    (AT)br, (AT)bi);
+                                    (AT)br, (AT)bi, cnt);
     prof_end(st, tok);
     note_launch();
     CAL_TRY_CUDA(cudaGetLastError());

@@ -50,6 +50,7 @@ struct ProfRec {
   std::string name;
   double units;
   cudaEvent_t a, b;
+  unsigned long long* counter;  // device-counted units (replaces `units` when set)
 };
 static std::vector<ProfRec> g_prof;
 
@@ -59,7 +60,7 @@ int64_t launches() { return g_launches.load(); }
 int prof_begin(cudaStream_t st, const char* name, double units) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   if (!g_prof_on) return -1;
-  ProfRec r{name, units, nullptr, nullptr};
+  ProfRec r{name, units, nullptr, nullptr, nullptr};
   if (cudaEventCreate(&r.a) != cudaSuccess || cudaEventCreate(&r.b) != cudaSuccess) return -1;
   cudaEventRecord(r.a, st);
   g_prof.push_back(r);
@@ -72,12 +73,27 @@ void prof_end(cudaStream_t st, int token) {
   cudaEventRecord(g_prof[token].b, st);
 }
 
+unsigned long long* prof_counter(int token, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  if (token < 0 || token >= (int)g_prof.size()) return nullptr;
+  ProfRec& r = g_prof[token];
+  if (!r.counter) {
+    if (cudaMallocAsync((void**)&r.counter, sizeof(unsigned long long), st) != cudaSuccess) {
+      r.counter = nullptr;
+      return nullptr;
+    }
+    cudaMemsetAsync(r.counter, 0, sizeof(unsigned long long), st);
+  }
+  return r.counter;
+}
+
 int prof_enable(int on) {
   std::lock_guard<std::mutex> lk(g_prof_mu);
   for (auto& r : g_prof) {
     cudaEventSynchronize(r.b);
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
+    if (r.counter) cudaFree(r.counter);
   }
   g_prof.clear();
   g_prof_on = on != 0;
@@ -95,7 +111,14 @@ int prof_read(const char* name, int64_t* n, double* ms, double* units) {
     cudaEventElapsedTime(&t, r.a, r.b);
     ++cnt;
     tot += t;
-    u += r.units;
+    if (r.counter) {
+      unsigned long long c = 0;
+      if (cudaMemcpy(&c, r.counter, sizeof(c), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(CAL_ECUDA, "profile: counter read failed");
+      u += (double)c;
+    } else {
+      u += r.units;
+    }
   }
   if (n) *n = cnt;
   if (ms) *ms = tot;
@@ -154,6 +177,16 @@ void triangle_rule(int npts, std::vector<double>& bary, std::vector<double>& w) 
   if (npts == 1) {
     bary = {1.0 / 3, 1.0 / 3, 1.0 / 3};
     w = {1.0};
+    return;
+  }
+  if (npts == 3) {  // degree 2 (Strang–Fix): (2/3, 1/6, 1/6) and permutations, equal weights
+    bary = {2.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 2.0 / 3, 1.0 / 6, 1.0 / 6, 1.0 / 6, 2.0 / 3};
+    w = {1.0 / 3, 1.0 / 3, 1.0 / 3};
+    return;
+  }
+  if (npts == 4) {  // degree 3 (Strang–Fix): centroid -27/48, (3/5, 1/5, 1/5) and permutations 25/48
+    bary = {1.0 / 3, 1.0 / 3, 1.0 / 3, 0.6, 0.2, 0.2, 0.2, 0.6, 0.2, 0.2, 0.2, 0.6};
+    w = {-27.0 / 48, 25.0 / 48, 25.0 / 48, 25.0 / 48};
     return;
   }
   // symmetric degree-4 rule with 6 points (Strang–Fix, Dunavant), closed form
@@ -301,6 +334,13 @@ static TriD make_tri(const double* P0, const double* P1, const double* P2, int v
   double n0 = u[1] * v[2] - u[2] * v[1], n1 = u[2] * v[0] - u[0] * v[2], n2 = u[0] * v[1] - u[1] * v[0];
   t.area = 0.5 * std::sqrt(n0 * n0 + n1 * n1 + n2 * n2);
   t.vid[0] = v0; t.vid[1] = v1; t.vid[2] = v2;
+  double d2 = 0.0;
+  for (int a = 0; a < 3; ++a) {
+    double q = 0.0;
+    for (int c = 0; c < 3; ++c) q += (P[(a + 1) % 3][c] - P[a][c]) * (P[(a + 1) % 3][c] - P[a][c]);
+    d2 = std::max(d2, q);
+  }
+  t.diam = std::sqrt(d2);
   return t;
 }
 
@@ -703,6 +743,7 @@ int upload_space(Space& s, cudaStream_t st) {
       for (int a = 0; a < 3; ++a) f.off[a][c] = (float)d.off[a][c];
     }
     f.area = (float)d.area;
+    f.diam = (float)d.diam;
     for (int a = 0; a < 3; ++a) f.vid[a] = d.vid[a];
     tf[t] = f;
   }

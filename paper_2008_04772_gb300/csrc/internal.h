@@ -53,15 +53,19 @@ void note_launch(int n = 1);
 // events around one launch of kernel family `name` doing `units` of work
 int prof_begin(cudaStream_t st, const char* name, double units);
 void prof_end(cudaStream_t st, int token);
+// a zeroed device counter whose value (read after the launch) replaces the
+// token's units; nullptr when profiling is off or the token is invalid
+unsigned long long* prof_counter(int token, cudaStream_t st);
 
 // ---- device records ----------------------------------------------------------
 // float32 triangle: centroid as hi + lo float pair, vertex offsets from it.
+// diam: longest edge (the size in the near / medium / far class of a pair)
 struct __align__(16) TriF {
   float chi[3], clo[3];
   float off[3][3];
   float area;
   int vid[3];
-  int pad;
+  float diam;
 };
 struct __align__(16) TriD {
   double c[3];
@@ -69,6 +73,7 @@ struct __align__(16) TriD {
   double area;
   int vid[3];
   int pad;
+  double diam;
 };
 
 // ordered singular pair (shares >= 1 vertex id) with Sauter–Schwab vertex orders:

@@ -110,6 +110,42 @@ def test_near_field_csr(ctx, name, mult):
         assert rel(D, ref * mask) < 1e-10
 
 
+@pytest.mark.parametrize("name", ["sphere2", "prisms2", "cubes"])
+@pytest.mark.parametrize("k", [2.0, 2.0 * np.sqrt(EPS)])
+@pytest.mark.parametrize("prec", [cal.FP64, cal.FP32])
+def test_class_rules_rwg_blocks(ctx, name, k, prec):
+    """q_regular = 0: near / medium / far pairs take the 6 / 4 / 3-point rules
+    (Section 3.3 default orders 4, 3, 2), on both sides."""
+    So, Co = oracle_ops(name, "RWG", complex(k), 0, 4)
+    op = cal.assemble(ctx, 3, k, gpu_space(ctx, name, "RWG"), q_regular=0, precision=prec)
+    assert rel(op.export(cal.OP_S), So) < TOL[prec]
+    assert rel(op.export(cal.OP_C), Co) < TOL[prec]
+
+
+@pytest.mark.parametrize("name", ["sphere1", "prisms2"])
+@pytest.mark.parametrize("prec", [cal.FP64, cal.FP32])
+def test_class_rules_bc_blocks(ctx, name, prec):
+    So, Co = oracle_ops(name, "BC", 3.5 + 0.01j, 0, 4)
+    op = cal.assemble(ctx, 3, 3.5 + 0.01j, gpu_space(ctx, name, "BC"), q_regular=0, precision=prec)
+    assert rel(op.export(cal.OP_S), So) < TOL[prec]
+    assert rel(op.export(cal.OP_C), Co) < TOL[prec]
+
+
+def test_class_rules_near_field_csr(ctx):
+    topo, rwg_o, bc_o = oracle_spaces("prisms2")
+    chi = 2.0 * topo.h
+    So, Co = oracle_ops("prisms2", "BC", 2.0, 0, 4)
+    mask = bem.near_field_mask(bc_o, bc_o, chi)
+    op = cal.assemble(ctx, 3, 2.0, gpu_space(ctx, "prisms2", "BC"), near_cutoff=chi, q_regular=0,
+                      precision=cal.FP64)
+    for which, ref in ((cal.OP_S, So), (cal.OP_C, Co)):
+        vals, rp, ci = op.export(which)
+        D = np.zeros_like(ref)
+        for i in range(len(rp) - 1):
+            D[i, ci[rp[i]:rp[i + 1]]] = vals[rp[i]:rp[i + 1]]
+        assert rel(D, ref * mask) < 1e-10
+
+
 def test_gram_matrix(ctx):
     for name in ("sphere1", "prisms2", "bipyr14", "cubes"):
         topo, rwg_o, bc_o = oracle_spaces(name)

@@ -44,9 +44,9 @@ def _oracle_rows_to_gpu(P, yo):
     return y
 
 
-def _oracle_apply(name, k):
+def _oracle_apply(name, k, nreg=6):
     m = mesh(name)
-    P = pmchwt.PMCHWT(m.verts, m.tris, m.domain, k, EPS)
+    P = pmchwt.PMCHWT(m.verts, m.tris, m.domain, k, EPS, rules_A=(nreg, 4))
     P.assemble(need_bc=False)
     A = P.matrix_A()
     rng = np.random.default_rng(5)
@@ -59,10 +59,12 @@ def _oracle_apply(name, k):
 
 @pytest.mark.parametrize("name,k", [("sphere2", 2.0), ("prisms2", 3.0)])
 @pytest.mark.parametrize("free", [0, 1])
-def test_operator_fp64_matches_oracle(ctx, name, k, free):
-    m, X, Y = _oracle_apply(name, k)
+@pytest.mark.parametrize("nreg", [6, 0])
+def test_operator_fp64_matches_oracle(ctx, name, k, free, nreg):
+    m, X, Y = _oracle_apply(name, k, nreg)
     gm = cal.Mesh(ctx, m.verts, m.tris, m.domain)
-    prob = cal.Problem(ctx, gm, k, EPS, opts=cal.solve_opts(precond="none", precision=cal.FP64, matrix_free=free))
+    prob = cal.Problem(ctx, gm, k, EPS, opts=cal.solve_opts(precond="none", precision=cal.FP64, matrix_free=free,
+                                                            q_regular_A=nreg))
     Yg = prob.apply(X)
     assert rel(Yg, Y) < 1e-11, rel(Yg, Y)
     if free:

@@ -22,12 +22,12 @@ def ctx():
 _oracle = {}
 
 
-def oracle_solution(name, k, precond="D", chi=math.inf, rules_P=(6, 4), inc=INC[0]):
-    key = (name, k, precond, chi, rules_P, tuple(inc))
+def oracle_solution(name, k, precond="D", chi=math.inf, rules_P=(6, 4), inc=INC[0], rules_A=(6, 4)):
+    key = (name, k, precond, chi, rules_P, tuple(inc), rules_A)
     if key not in _oracle:
         m = mesh(name)
         pb = pmchwt.PMCHWT(m.verts, m.tris, m.domain, k, EPS, precond=precond, chi_P=chi,
-                           rules_P=rules_P)
+                           rules_P=rules_P, rules_A=rules_A)
         pb.assemble(need_bc=precond != "I")
         xd = np.linalg.solve(pb.matrix_A(), pb.rhs(inc))
         c, d = pb.split(xd)
@@ -49,6 +49,21 @@ def test_fp64_solution_matches_oracle(ctx, name, k):
     assert rel(x, xo) < 1e-8
     dirs = meshgen.sphere_cut_directions(19)
     assert rel(sol.far_field(dirs)[0], pb.far_field(xd, dirs)) < 1e-8
+
+
+@pytest.mark.parametrize("name,k", [("sphere2", 2.0), ("prisms2", 3.0)])
+def test_class_rules_solution_matches_oracle(ctx, name, k):
+    """A and P with the near / medium / far rules (q_regular = 0, the paper's
+    default orders): float64 to 1e-8, FP32 bulk far field to 1e-4."""
+    pb, xd, xo = oracle_solution(name, k, rules_A=(0, 4))
+    dirs = meshgen.fibonacci_directions(32)
+    F0 = pb.far_field(xd, dirs)
+    o64 = cal.solve_opts(precond="D", precision=cal.FP64, tol=1e-11, q_regular_A=0, q_regular_P=0)
+    sol = cal.pmchwt_solve(ctx, gmesh(ctx, name), k, EPS, INC, opts=o64)
+    assert rel(sol.coefficients()[0], xo) < 1e-8
+    o32 = cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-6, q_regular_A=0, q_regular_P=0)
+    F = cal.pmchwt_solve(ctx, gmesh(ctx, name), k, EPS, INC, opts=o32).far_field(dirs)[0]
+    assert rel(F, F0) < 1e-4, rel(F, F0)
 
 
 @pytest.mark.parametrize("name,k", [("sphere2", 2.0), ("prisms2", 3.0), ("cubes", 2.1)])
