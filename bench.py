@@ -3,10 +3,12 @@
 Workload (default): dielectric sphere of radius 1, icosphere with 5120
 triangles (7680 RWG/BC functions, 15360 PMCHWT unknowns), k_e = 5,
 eps_r = 3.17 + 0.01i, x-polarised plane wave along +z; A on RWG with the
-6-point regular rule and order-4 Sauter–Schwab singular rules; the full
-block-diagonal Calderón preconditioner D on the barycentric mesh (dense, same
-rules); FP32-bulk assembly and complex64 matvecs with FP64 GMRES recurrences
-and FP64 iterative refinement, tol 1e-5, restart 200.
+paper's default quadrature orders (q_near, q_medium, q_far, q_singular) =
+(4, 3, 2, 6): 36 / 16 / 9 evaluations per regular pair by its near / medium /
+far class and order-4 Sauter–Schwab singular rules; the full block-diagonal
+Calderón preconditioner D on the barycentric mesh (dense, same rules);
+FP32-bulk assembly and complex64 matvecs with FP64 GMRES recurrences and FP64
+iterative refinement, tol 1e-5, restart 200.
 
 One step = one complete solve through the C ABI (spaces, assembly of A and P,
 Gram matrix, right-hand side, GMRES, far field on 362 directions). The FP64
@@ -35,11 +37,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WORKLOAD = {"name": "sphere5120_k5_D_dense", "level": 4, "k": 5.0, "eps": 3.17 + 0.01j,
-            "tol": 1e-5, "restart": 200}
+            "tol": 1e-5, "restart": 200, "q_regular": 0}
+# regular rules of every workload: 0 = near / medium / far classes at the paper's
+# default orders (4, 3, 2); 6 = the 6-point rule for every regular pair
+Q = dict(q_regular_A=0, q_regular_P=0)
 METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bc_tile launch (exterior pass of
 # the workload), from the ncu capture summarised in profiles/; None once the kernel changes
-BC_TILE_TRAFFIC = 2.870043e9 + 2.759060e9
+BC_TILE_TRAFFIC = None
 
 
 def _env_int(name, default):
@@ -141,9 +146,9 @@ def run_ours(args, rank, world):
     m = meshgen.icosphere(W["level"])
     inc = meshgen.plane_wave_x_along_z()
     dirs = meshgen.sphere_cut_directions(181)
-    opts32 = cal.solve_opts(precond="D", precision=cal.FP32, tol=W["tol"], restart=W["restart"])
-    opts64 = cal.solve_opts(precond="D", precision=cal.FP64, tol=W["tol"], restart=W["restart"])
-    opts32all = cal.solve_opts(precond="D", precision=cal.FP32_ALL, tol=W["tol"], restart=W["restart"])
+    opts32 = cal.solve_opts(precond="D", precision=cal.FP32, tol=W["tol"], restart=W["restart"], **Q)
+    opts64 = cal.solve_opts(precond="D", precision=cal.FP64, tol=W["tol"], restart=W["restart"], **Q)
+    opts32all = cal.solve_opts(precond="D", precision=cal.FP32_ALL, tol=W["tol"], restart=W["restart"], **Q)
 
     def one_step(opts, mesh=None, e2e=False):
         """One solve; returns (solution info, far field). e2e: mesh from host arrays each step."""
@@ -210,6 +215,17 @@ def run_ours(args, rank, world):
     info64, F64 = one_step(opts64, mesh)
     t64 = time.perf_counter() - a
     err = float(np.linalg.norm(F32 - F64) / np.linalg.norm(F64))
+    # the same comparison with the stopping error taken out: a converged float64
+    # solve (tol 1e-10) against float32 bulk at tol 1e-5 and at tol 1e-9
+    _, F64c = one_step(cal.solve_opts(precond="D", precision=cal.FP64, tol=1e-10, restart=W["restart"],
+                                      maxit=2000, **Q), mesh)
+    _, F32c = one_step(cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-9, restart=W["restart"],
+                                      maxit=2000, **Q), mesh)
+    rel_c = lambda F: float(np.linalg.norm(F - F64c) / np.linalg.norm(F64c))  # noqa: E731
+    err_detail = {"fp32_tol1e-5_vs_converged_fp64": rel_c(F32), "fp64_tol1e-5_vs_converged_fp64": rel_c(F64),
+                  "fp32_tol1e-9_vs_converged_fp64": rel_c(F32c),
+                  "note": "at tol 1e-5 both solves carry their GMRES stopping error (~1e-5..1e-4); "
+                          "the float32 floor is the tol-1e-9 line"}
     # variant: float32 singular pairs as well
     one_step(opts32all, mesh)
     torch.cuda.synchronize()
@@ -251,7 +267,8 @@ def run_ours(args, rank, world):
         "config": {"workload": W["name"], "triangles": int(len(m.tris)), "unknowns": N,
                    "k_ext": W["k"], "eps_r": [W["eps"].real, W["eps"].imag],
                    "preconditioner": "D (full block-diagonal Calderon, dense BC)",
-                   "rules": "A and P: 6-point regular, Sauter-Schwab 4^4 singular",
+                   "rules": "A and P: paper default orders (4,3,2,6): regular 6/4/3-point rules by "
+                            "near/medium/far class (relative distance 2, 4), Sauter-Schwab 4^4 singular",
                    "tol": W["tol"], "restart": W["restart"], "parallelism": f"replicas{world}",
                    "l2": "working set > L2 (each step writes ~2.4 GB of operators)"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99))},
@@ -262,12 +279,13 @@ def run_ours(args, rank, world):
         "entries_per_s": entries / (ms_step / 1e3),
         "fp64_gpu": {"solves_per_s": 1.0 / t64, "iterations": int(info64.iterations)},
         "err_farfield_fp32_vs_fp64": err,
+        "err_detail": err_detail,
         "fp32_all_variant": {"solves_per_s": 1.0 / t_all, "err_farfield_vs_fp64": err_all,
                              "iterations": int(info_all.iterations),
                              "note": "singular pairs also in float32 (CAL_FP32_ALL)"},
         "gpu_launches": int(n_launch),
         "kernels_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": "bc_tile_kernel<float,6,128>",
+        "roofline": {"bound": "alu", "kernel": "bc_tile_kernel<float,0,128>",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak if peak else None, "traffic": BC_TILE_TRAFFIC,
                      "traffic_note": "dram read+write bytes of one exterior launch, one ncu capture "
@@ -294,18 +312,19 @@ def run_ours(args, rank, world):
 # Preconditioner variants of the headline sphere (full vs reduced vs near-field-only,
 # and the bi-parametric cheaper rules for P of Section 3.2): name, options
 VARIANTS = [
-    ("none", dict(precond="none", maxit=2000)),
-    ("D", dict(precond="D")),
-    ("De", dict(precond="De")),
-    ("Di", dict(precond="Di")),
-    ("Se", dict(precond="Se")),
-    ("Si", dict(precond="Si")),
-    ("Di_near2h", dict(precond="Di", near_cutoff_P=2.0)),
-    ("Di_near4h", dict(precond="Di", near_cutoff_P=4.0)),
-    ("Si_near2h", dict(precond="Si", near_cutoff_P=2.0)),
-    ("Si_near4h", dict(precond="Si", near_cutoff_P=4.0)),
-    ("D_bp_q11", dict(precond="D", q_regular_P=1, q_singular_P=1)),
-    ("Si_near0_bp_q11", dict(precond="Si", near_cutoff_P=0.0, q_regular_P=1, q_singular_P=1)),
+    ("none", dict(precond="none", maxit=2000, **Q)),
+    ("D", dict(precond="D", **Q)),
+    ("D_uniform6", dict(precond="D", q_regular_A=6, q_regular_P=6)),
+    ("De", dict(precond="De", **Q)),
+    ("Di", dict(precond="Di", **Q)),
+    ("Se", dict(precond="Se", **Q)),
+    ("Si", dict(precond="Si", **Q)),
+    ("Di_near2h", dict(precond="Di", near_cutoff_P=2.0, **Q)),
+    ("Di_near4h", dict(precond="Di", near_cutoff_P=4.0, **Q)),
+    ("Si_near2h_bp_q11", dict(precond="Si", near_cutoff_P=2.0, q_regular_A=0, q_regular_P=1, q_singular_P=1)),
+    ("Si_near4h_bp_q11", dict(precond="Si", near_cutoff_P=4.0, q_regular_A=0, q_regular_P=1, q_singular_P=1)),
+    ("D_bp_q11", dict(precond="D", q_regular_A=0, q_regular_P=1, q_singular_P=1)),
+    ("Si_near0_bp_q11", dict(precond="Si", near_cutoff_P=0.0, q_regular_A=0, q_regular_P=1, q_singular_P=1)),
 ]
 
 
@@ -328,7 +347,8 @@ def run_variants(dev, F64, dirs):
            "note": "every variant stops at a preconditioned residual of 1e-5; its distance to the float64 "
                    "D solution is set by that stopping point, not by float32 arithmetic (see the headline "
                    "err_farfield_fp32_vs_fp64 for the same preconditioner)",
-           "rules": "q = (q_regular, q_singular); default (6, 4) for A and P, bi-parametric P (1, 1)"}
+           "rules": "q_regular 0 = near/medium/far classes at the paper's default orders (4,3,2) for A and P, "
+                    "6 = the 6-point rule for all regular pairs (D_uniform6), bi-parametric P (1, 1) (the *_bp_q11 lines)"}
     for name, o in VARIANTS:
         opts = cal.solve_opts(precision=cal.FP32, tol=W["tol"], restart=W["restart"], **o)
         ts = []
@@ -377,7 +397,7 @@ def run_multirhs(dev):
     mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
     d = meshgen.fibonacci_directions(W["nrhs"])
     inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
-    opts = cal.solve_opts(precond=W["precond"], precision=cal.FP32, tol=W["tol"], near_cutoff_P=W["near_cutoff_P"])
+    opts = cal.solve_opts(precond=W["precond"], precision=cal.FP32, tol=W["tol"], near_cutoff_P=W["near_cutoff_P"], **Q)
     L.cal_profile_enable(1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -439,7 +459,7 @@ def run_matrix_free(dev):
     far = {}
     for free in (0, 1):
         opts = cal.solve_opts(precond=W["precond"], precision=cal.FP32, tol=W["tol"],
-                              near_cutoff_P=W["near_cutoff_P"], matrix_free=free)
+                              near_cutoff_P=W["near_cutoff_P"], matrix_free=free, **Q)
         L.cal_profile_enable(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -504,7 +524,7 @@ def run_serving(dev):
     from paper_2008_04772_gb300 import cal, meshgen
     S = SERVING
     opts = cal.solve_opts(precond=S["precond"], precision=cal.FP32, tol=S["tol"],
-                          near_cutoff_P=S["near_cutoff_P"])
+                          near_cutoff_P=S["near_cutoff_P"], **Q)
     dirs = meshgen.fibonacci_directions(S["ndir"])
     reqs = serving_requests(S["requests"], S["seed"])
     q = cal.Queue(dev, slots=S["slots"])
@@ -596,7 +616,7 @@ def cpu_baseline(sample_tris: int):
     m = meshgen.icosphere(W["level"])
     topo = spaces.Topology(m.verts, m.tris, m.domain)
     rwg, bc = spaces.rwg_space(topo), spaces.bc_space(topo)
-    rules = bem.Rules(6, 4)
+    rules = bem.Rules(W["q_regular"], 4)
     km = W["k"] * np.sqrt(W["eps"])
     rng = np.random.default_rng(0)
     t_total = 0.0

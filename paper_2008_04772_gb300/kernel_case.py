@@ -1,7 +1,8 @@
 """Single-kernel cases for profiling (the launches named in profiles/).
 
 ``python -m paper_2008_04772_gb300.kernel_case [bc|gemv|all]`` on the 5120-triangle
-sphere (k = 5):
+sphere (k = 5), with the benchmark's regular rules (near / medium / far classes at
+the paper's default orders 4, 3, 2):
   bc    one dense FP32 assembly of S and C on the Buffa–Christiansen space
         (one bc_tile_kernel launch plus the FP64 singular-pair launch);
   gemv  an unpreconditioned FP32 solve capped at 3 GMRES iterations (the
@@ -28,7 +29,7 @@ def main(which: str = "all") -> None:
     mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
     if which in ("all", "bc"):
         bc = cal.Space(mesh, cal.BC)
-        op = cal.assemble(ctx, cal.OP_S | cal.OP_C, 5.0, bc, precision=cal.FP32)
+        op = cal.assemble(ctx, cal.OP_S | cal.OP_C, 5.0, bc, q_regular=0, precision=cal.FP32)
         del op
     if which in ("all", "gemm"):
         import numpy as np
@@ -47,7 +48,7 @@ def main(which: str = "all") -> None:
         # three FP32 GMRES iterations with the matrix-free operator (float32 vectors)
         cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
                          opts=cal.solve_opts(precond="none", precision=cal.FP32, maxit=3, refine=0,
-                                             matrix_free=1),
+                                             matrix_free=1, q_regular_A=0),
                          allow_not_converged=True)
     if which in ("all", "gemv"):
         cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
@@ -58,10 +59,12 @@ def main(which: str = "all") -> None:
         import numpy as np
         inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
         cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, inc,
-                         opts=cal.solve_opts(precond="Di", near_cutoff_P=2.0, precision=cal.FP32, tol=1e-5))
+                         opts=cal.solve_opts(precond="Di", near_cutoff_P=2.0, precision=cal.FP32, tol=1e-5,
+                                             q_regular_A=0, q_regular_P=0))
     if which == "solve":
         sol = cal.pmchwt_solve(ctx, mesh, 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z(),
-                               opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-5))
+                               opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-5, q_regular_A=0,
+                                                   q_regular_P=0))
         sol.far_field(meshgen.sphere_cut_directions(181))
     print("kernel_case done:", which)
 
