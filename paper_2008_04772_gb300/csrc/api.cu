@@ -131,8 +131,12 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     std::vector<int> cells = cell_list(sp, scat);
     int max_cell = 0;
     for (int v : cells) max_cell = std::max(max_cell, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
-    // tiles (v, w), v <= w, grouped into units of one test cell and up to 16 trial cells
-    constexpr int UNIT = 16;
+    // tiles (v, w), v <= w, grouped into units of one test cell and up to 16 trial
+    // cells (or as many as fill the block of the float32 per-thread kernel)
+    auto unit_of = [&](int v) {
+      const int w = bc_owner_width(sp, precision, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
+      return w > 0 ? w : 16;
+    };
     std::vector<int> units;  // {v, begin, count, 0} per unit
     std::vector<int> wlist;
     std::vector<int2> tiles;
@@ -175,15 +179,18 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       for (size_t q = 0; q < tiles.size(); ++q) wlist[q] = tiles[q].y;
       for (size_t q = 0; q < tiles.size();) {
         size_t e = q;
-        while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < (size_t)UNIT) ++e;
+        const size_t unit = (size_t)unit_of(tiles[q].x);
+        while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < unit) ++e;
         units.insert(units.end(), {tiles[q].x, (int)q, (int)(e - q), 0});
         q = e;
       }
     } else {
       wlist = cells;
       const int nc = (int)cells.size();
-      for (int i = 0; i < nc; ++i)
-        for (int j0 = i; j0 < nc; j0 += UNIT) units.insert(units.end(), {cells[i], j0, std::min(UNIT, nc - j0), 0});
+      for (int i = 0; i < nc; ++i) {
+        const int unit = unit_of(cells[i]);
+        for (int j0 = i; j0 < nc; j0 += unit) units.insert(units.end(), {cells[i], j0, std::min(unit, nc - j0), 0});
+      }
     }
     const int64_t nunits = (int64_t)units.size() / 4;
     int* d_units = nullptr;

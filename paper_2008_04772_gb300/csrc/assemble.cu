@@ -957,6 +957,170 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
 }
 
 // ---------------------------------------------------------------------------
+// A5, float32, cells of at most BC_OWN_SLOTS edges: one thread per (test
+// triangle tau1 of v, trial cell w_j) of a unit. The thread walks the
+// triangles tau2 of w_j, forms each pair's moments and pair coefficients and
+// contracts them with w_j's trial slots at once into register sums (the
+// stage-2 records of bc_tile_kernel), so pair coefficients never go through
+// shared memory and the pair loop has no barrier. The records are then written
+// to shared memory once and contracted with the test slots per (j, a, b).
+// Units hold floor(TT / n1) trial cells so that the items fill the block.
+// ---------------------------------------------------------------------------
+constexpr int BC_OWN_SLOTS = 6;
+constexpr int BC_OWN_REC = 20;  // S record [0, 10), C record [10, 18), padding
+
+template <int NREG, int TT>
+__global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
+    CellData<float> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
+    const int* __restrict__ cell_edge, const BcUnit* __restrict__ units, int64_t nunits,
+    const int* __restrict__ wlist, float kr, float ki, float mikr, float miki, float c4r, float c4i, bool wantS,
+    bool wantC, Sink<float> out, int max_cell, unsigned long long* cnt) {
+  constexpr int NS = staged_points<NREG>();
+  constexpr int NSL = BC_OWN_SLOTS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* rec = reinterpret_cast<float*>(smem_raw);                                  // [TT][NSL][BC_OWN_REC]
+  P4<float>* ptsA = reinterpret_cast<P4<float>*>(rec + (size_t)TT * NSL * BC_OWN_REC);  // [max_cell][NS]
+  P4<float>* swA = ptsA + (size_t)max_cell * NS;                                    // [max_cell][nslot]
+  Cent<float>* cA = reinterpret_cast<Cent<float>*>(swA + (size_t)max_cell * nslot);
+  int* vidA = reinterpret_cast<int*>(cA + max_cell);                                // [max_cell][3]
+  unsigned evals = 0;
+  for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
+    const BcUnit U = units[uidx];
+    const int v = U.v;
+    const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
+    const int ns1 = cell_edge_ptr[v + 1] - cell_edge_ptr[v];
+    __syncthreads();  // the previous unit is done with the test-cell data and the records
+    for (int q = threadIdx.x; q < n1 * NS; q += TT) ptsA[q] = cd.pts[(size_t)b1 * NS + q];
+    for (int q = threadIdx.x; q < n1 * nslot; q += TT) swA[q] = cd.sw[(size_t)b1 * nslot + q];
+    for (int q = threadIdx.x; q < n1; q += TT) {
+      cA[q] = cd.cen[b1 + q];
+      for (int c = 0; c < 3; ++c) vidA[3 * q + c] = cd.vid[(size_t)(b1 + q) * 3 + c];
+    }
+    __syncthreads();
+    const int items = n1 * U.count;
+    // pair loop: thread t = j n1 + i1
+    if ((int)threadIdx.x < items) {
+      const int j = threadIdx.x / n1, i1 = threadIdx.x - j * n1;
+      const int w = wlist[U.begin + j];
+      const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
+      const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
+      const Cent<float> ca = cA[i1];
+      const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
+      const P4<float>* X = ptsA + i1 * NS;
+      float r[NSL][18];
+#pragma unroll
+      for (int b = 0; b < NSL; ++b)
+#pragma unroll
+        for (int f = 0; f < 18; ++f) r[b][f] = 0.0f;
+      for (int i2 = 0; i2 < n2; ++i2) {
+        const int t2 = b2 + i2;
+        const int* vb = cd.vid + (size_t)t2 * 3;
+        const int vb0 = vb[0], vb1 = vb[1], vb2 = vb[2];
+        const bool touch = va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 ||
+                           va2 == vb0 || va2 == vb1 || va2 == vb2;
+        if (touch) continue;  // Sauter–Schwab pairs: the singular kernel
+        const Cent<float> cb = cd.cen[t2];
+        const V3<float> D = ca.minus(cb);
+        const P4<float>* Y = cd.pts + (size_t)t2 * NS;
+        Mom<float> m;
+        if constexpr (NREG > 0) {
+          regular_moments_staged<float, NREG>(X, Y, D, kr, ki, wantC, m);
+          evals += NREG * NREG;
+        } else {
+          const int c = pair_class<float>(D, ca.d, cb.d);
+          if (c == 2) {
+            regular_moments_staged<float, 3>(X + RULE_OFF_FAR, Y + RULE_OFF_FAR, D, kr, ki, wantC, m);
+            evals += 9;
+          } else if (c == 1) {
+            regular_moments_staged<float, 4>(X + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki, wantC, m);
+            evals += 16;
+          } else {
+            regular_moments_staged<float, 6>(X, Y, D, kr, ki, wantC, m);
+            evals += 36;
+          }
+        }
+        float pc[36];
+        pair_coeffs(m, D, pc);
+        const P4<float>* swb = cd.sw + (size_t)t2 * nslot;
+#pragma unroll
+        for (int b = 0; b < NSL; ++b) {
+          if (b >= ns2) break;
+          const P4<float> u = swb[b];
+          const float sb = u.x;
+          const V3<float> wb = {u.y, u.z, u.w};
+          float* o = r[b];
+          // S: AS (re, im), BS (re, im), WS_r, WS_i
+          o[0] += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
+          o[1] += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
+          o[2] += sb * pc[0];
+          o[3] += sb * pc[1];
+          o[4] += sb * pc[8] + wb.x * pc[0]; o[5] += sb * pc[9] + wb.y * pc[0]; o[6] += sb * pc[10] + wb.z * pc[0];
+          o[7] += sb * pc[11] + wb.x * pc[1]; o[8] += sb * pc[12] + wb.y * pc[1]; o[9] += sb * pc[13] + wb.z * pc[1];
+          // C: AC (re, im), WC_r, WC_i
+          o[10] += sb * pc[16] + wb.x * pc[18] + wb.y * pc[19] + wb.z * pc[20];
+          o[11] += sb * pc[17] + wb.x * pc[21] + wb.y * pc[22] + wb.z * pc[23];
+          const V3<float> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
+          const V3<float> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
+          o[12] += sb * pc[24] + cr.x; o[13] += sb * pc[25] + cr.y; o[14] += sb * pc[26] + cr.z;
+          o[15] += sb * pc[27] + ci.x; o[16] += sb * pc[28] + ci.y; o[17] += sb * pc[29] + ci.z;
+        }
+      }
+      float* dst = rec + (size_t)threadIdx.x * NSL * BC_OWN_REC;
+#pragma unroll
+      for (int b = 0; b < NSL; ++b) {
+        if (b >= ns2) break;
+        __align__(16) float tmp[BC_OWN_REC];
+#pragma unroll
+        for (int f = 0; f < 18; ++f) tmp[f] = r[b][f];
+        tmp[18] = tmp[19] = 0.0f;
+        vcopy(dst + b * BC_OWN_REC, tmp, BC_OWN_REC);
+      }
+    }
+    __syncthreads();
+    // test-side contraction per (j, a, b), S and C together, summed over tau1
+    for (int q = threadIdx.x; q < U.count * ns1 * NSL; q += TT) {
+      const int j = q / (ns1 * NSL);
+      const int rest = q - j * ns1 * NSL;
+      const int sa_i = rest / NSL, sb_i = rest - (rest / NSL) * NSL;
+      const int w = wlist[U.begin + j];
+      const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
+      if (sb_i >= ns2) continue;
+      float sr = 0, si = 0, cr = 0, ci = 0;
+      for (int i1 = 0; i1 < n1; ++i1) {
+        const P4<float> u = swA[i1 * nslot + sa_i];
+        const float sa = u.x;
+        const V3<float> wa = {u.y, u.z, u.w};
+        __align__(16) float o[BC_OWN_REC];
+        vcopy(o, rec + ((size_t)(j * n1 + i1) * NSL + sb_i) * BC_OWN_REC, BC_OWN_REC);
+        // S: sa (mik AS + c4 BS) + mik (wa . WS)
+        const float pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
+        const float pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
+        sr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
+        si += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
+        // C: sa AC + wa . WC
+        cr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
+        ci += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
+      }
+      const int ea = cell_edge[cell_edge_ptr[v] + sa_i];
+      const int eb = cell_edge[cell_edge_ptr[w] + sb_i];
+      out.add(ea, eb, wantS, wantC, sr, si, cr, ci);
+      if (v != w) out.add(eb, ea, wantS, wantC, sr, si, cr, ci);
+    }
+  }
+  count_add(cnt, evals);
+}
+
+constexpr int BC_OWNER_TT = 128;
+
+// trial cells per unit for the one-thread-per-(test triangle, trial cell)
+// kernel with a test cell of n1 triangles; 0 when that kernel does not apply
+// (float64, or cells with more than BC_OWN_SLOTS edges)
+int bc_owner_width(const Space& s, int precision, int n1) {
+  if (precision != CAL_FP32 || s.nslot > BC_OWN_SLOTS || n1 < 1 || n1 > BC_OWNER_TT) return 0;
+  return std::max(1, BC_OWNER_TT / n1);
+}
+
+// ---------------------------------------------------------------------------
 // A4: singular pairs by Sauter–Schwab rules in float64, one warp per ordered
 // pair; the q^4 Gauss points of all sub-regions are spread over the lanes.
 // ---------------------------------------------------------------------------
@@ -1858,6 +2022,34 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   auto prep = nreg == 6 ? bc_cell_prep_kernel<R, 6> : (nreg == 1 ? bc_cell_prep_kernel<R, 1> : bc_cell_prep_kernel<R, 0>);
   prep<<<(unsigned)((nct * nsp + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri, nct, g_rules, cd);
   note_launch();
+  if constexpr (sizeof(R) == 4) {
+    if (bc_owner_width(s, a.precision, max_cell) > 0) {
+      // one thread per (test triangle, trial cell); units sized by bc_owner_width
+      constexpr int OT = BC_OWNER_TT;
+      auto okern = nreg == 6 ? bc_owner_kernel<6, OT> : (nreg == 1 ? bc_owner_kernel<1, OT> : bc_owner_kernel<0, OT>);
+      const int nsp_o = nreg > 0 ? nreg : RULE_POINTS_ALL;
+      const size_t osmem = (size_t)OT * BC_OWN_SLOTS * BC_OWN_REC * sizeof(float) +
+                           (size_t)max_cell * nsp_o * sizeof(P4<float>) + (size_t)max_cell * s.nslot * sizeof(P4<float>) +
+                           (size_t)max_cell * sizeof(Cent<float>) + (size_t)max_cell * 3 * sizeof(int) + 64;
+      int rc = ensure_dyn_smem((const void*)okern, (int)osmem);
+      int per_sm = 0;
+      if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, OT, osmem) != cudaSuccess)
+        rc = fail(CAL_ECUDA, "bc owner kernel: occupancy query failed");
+      if (!rc) {
+        const int64_t grid = std::min<int64_t>(nunits, (int64_t)std::max(1, per_sm) * n_sm * 2);
+        const int tok = prof_begin(a.stream, "bc_tile", work);
+        unsigned long long* cnt = nreg == 0 ? prof_counter(tok, a.stream) : nullptr;
+        okern<<<(unsigned)grid, OT, osmem, a.stream>>>(cd, s.nslot, s.d_cell_tri_ptr, s.d_cell_edge_ptr, s.d_cell_edge,
+                                                      units, nunits, wlist, (float)a.kr, (float)a.ki, mikr, miki, c4r,
+                                                      c4i, wS, wC, out, max_cell, cnt);
+        prof_end(a.stream, tok);
+        note_launch();
+        if (cudaGetLastError() != cudaSuccess) rc = fail(CAL_ECUDA, "bc owner kernel launch failed");
+      }
+      cudaFreeAsync(buf, a.stream);
+      return rc;
+    }
+  }
   constexpr int TT = 128;
   auto kern = nreg == 6 ? bc_tile_kernel<R, 6, TT> : (nreg == 1 ? bc_tile_kernel<R, 1, TT> : bc_tile_kernel<R, 0, TT>);
   int rc = ensure_dyn_smem((const void*)kern, (int)smem);

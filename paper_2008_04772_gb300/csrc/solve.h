@@ -109,5 +109,8 @@ int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double
 // cell v with the trial cells wlist[begin .. begin + count)
 int launch_bc_regular_units(const AssembleArgs& a, const void* units, int64_t nunits, const int* wlist, int max_cell,
                             int n_sm, double work);
+// trial cells per unit for a test cell of n1 triangles when the float32
+// one-thread-per-(test triangle, trial cell) kernel applies, else 0
+int bc_owner_width(const Space& s, int precision, int n1);
 
 }  // namespace cal
