@@ -348,6 +348,7 @@ struct cal_solution {
   double2* d_x = nullptr;  // [nrhs][2N]
   int64_t nrhs = 0, ne = 0;
   double k_e = 0.0, mu_e = 1.0;
+  int precision = CAL_FP64;  // of the solve: float32 bulk evaluates its far field in float32
   cal_solve_info info{};
   ~cal_solution() { dfree(d_x, nullptr); }  // far-field and copy calls are synchronous
 };
@@ -1231,6 +1232,7 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   sol->nrhs = nrhs;
   sol->ne = P.N;
   sol->k_e = P.k_e;
+  sol->precision = P.o.precision == CAL_FP64 ? CAL_FP64 : CAL_FP32;
   const int64_t n2 = 2 * P.N;
   double* d_inc;
   double2 *d_b, *d_rhs, *d_r;
@@ -1394,7 +1396,8 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
   CAL_TRY_CUDA(dalloc((void**)&d_dirs, 3 * ndir * sizeof(double), st));
   CAL_TRY_CUDA(dalloc((void**)&d_out, sol->nrhs * ndir * 3 * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemcpyAsync(d_dirs, dirs, 3 * ndir * sizeof(double), cudaMemcpyHostToDevice, st));
-  int rc = launch_farfield(*sol->rwg, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e, sol->mu_e, d_out, st);
+  int rc = launch_farfield(*sol->rwg, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e, sol->mu_e, d_out,
+                           sol->precision, st);
   if (!rc) {
     CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, sol->nrhs * ndir * 3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
     CAL_TRY_CUDA(cudaStreamSynchronize(st));

@@ -1014,14 +1014,21 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
         for (int f = 0; f < 18; ++f) r[b][f] = 0.0f;
       for (int i2 = 0; i2 < n2; ++i2) {
         const int t2 = b2 + i2;
+        // the pair's trial data in one batch of independent loads (the far-rule
+        // points speculatively: almost every pair is far), one latency per pair
         const int* vb = cd.vid + (size_t)t2 * 3;
         const int vb0 = vb[0], vb1 = vb[1], vb2 = vb[2];
+        const Cent<float> cb = cd.cen[t2];
+        const P4<float>* Y = cd.pts + (size_t)t2 * NS;
+        P4<float> yf[3];
+        if constexpr (NREG == 0) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) yf[q] = Y[RULE_OFF_FAR + q];
+        }
         const bool touch = va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 ||
                            va2 == vb0 || va2 == vb1 || va2 == vb2;
         if (touch) continue;  // Sauter–Schwab pairs: the singular kernel
-        const Cent<float> cb = cd.cen[t2];
         const V3<float> D = ca.minus(cb);
-        const P4<float>* Y = cd.pts + (size_t)t2 * NS;
         Mom<float> m;
         if constexpr (NREG > 0) {
           regular_moments_staged<float, NREG>(X, Y, D, kr, ki, wantC, m);
@@ -1029,7 +1036,7 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
         } else {
           const int c = pair_class<float>(D, ca.d, cb.d);
           if (c == 2) {
-            regular_moments_staged<float, 3>(X + RULE_OFF_FAR, Y + RULE_OFF_FAR, D, kr, ki, wantC, m);
+            regular_moments_staged<float, 3>(X + RULE_OFF_FAR, yf, D, kr, ki, wantC, m);
             evals += 9;
           } else if (c == 1) {
             regular_moments_staged<float, 4>(X + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki, wantC, m);

@@ -1667,49 +1667,90 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
 
 // Far field E_inf(xh) = -(ik/4pi) [xh x Ja - xh x (xh x Jb)],
 // Ja = int a e^{-ik xh.y}, Jb = (mu/k) int (sum d_e RWG_e) e^{-ik xh.y}.
-__global__ void farfield_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
-                                const double* __restrict__ slot_sw, int64_t nt,
-                                const double2* __restrict__ x, int64_t ne, const double* dirs,
-                                int64_t ndir, double k, double mu, Rules6 rl, double2* out) {
+int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
+               cudaStream_t st) {
+  Rules6 rl = rules6();
+  CAL_TRY_CUDA(cudaMemsetAsync(d_b, 0, (size_t)nrhs * 2 * rwg.nbasis * sizeof(double2), st));
+  dim3 grid(blocks_for(rwg.ntri, 128), nrhs);
+  rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_inc, nrhs,
+                                   k, mu, rl, rwg.nbasis, d_b);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// Far field in two passes: the surface currents at the 6 points of every
+// triangle, J_a = sum_slots x1 phi and J_b = (mu/k) sum_slots x2 phi times the
+// rule weight and area (independent of the direction), then per direction one
+// sum of J e^{-ik xhat . x} over all points. AT: float64, or float32 for a
+// float32-bulk solution (phases |k xhat . x| stay small for the meshes here;
+// the far field is compared at 1e-4).
+template <typename AT>
+struct FfPoint {
+  AT x[3];
+  AT j[12];  // J_a (re, im) per component, then J_b
+};
+
+template <typename AT>
+__global__ void ff_points_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
+                                 const double* __restrict__ slot_sw, int64_t nt, const double2* __restrict__ x,
+                                 int64_t ne, double k, double mu, Rules6 rl, FfPoint<AT>* __restrict__ pts) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (t >= nt) return;
+  const TriD T = tri[t];
+  const double2* xq = x + (size_t)q * 2 * ne;
+  double ca[3][2], cb[3][2];
+  for (int a = 0; a < 3; ++a) {
+    const int e = slot_edge[3 * t + a];
+    ca[a][0] = xq[e].x; ca[a][1] = xq[e].y;
+    cb[a][0] = xq[ne + e].x * (mu / k); cb[a][1] = xq[ne + e].y * (mu / k);
+  }
+  for (int u = 0; u < 6; ++u) {
+    double xi[3];
+    for (int c = 0; c < 3; ++c)
+      xi[c] = rl.b[3 * u] * T.off[0][c] + rl.b[3 * u + 1] * T.off[1][c] + rl.b[3 * u + 2] * T.off[2][c];
+    const double w = rl.w[u] * T.area;
+    double J[12] = {};
+    for (int a = 0; a < 3; ++a) {
+      const double* sw = slot_sw + (3 * t + a) * 4;
+      for (int c = 0; c < 3; ++c) {
+        const double phi = w * (sw[0] * xi[c] + sw[1 + c]);
+        J[2 * c] += ca[a][0] * phi; J[2 * c + 1] += ca[a][1] * phi;
+        J[6 + 2 * c] += cb[a][0] * phi; J[6 + 2 * c + 1] += cb[a][1] * phi;
+      }
+    }
+    FfPoint<AT>& o = pts[((size_t)q * nt + t) * 6 + u];
+    for (int c = 0; c < 3; ++c) o.x[c] = (AT)(T.c[c] + xi[c]);
+    for (int c = 0; c < 12; ++c) o.j[c] = (AT)J[c];
+  }
+}
+
+template <typename AT>
+__global__ void ff_sum_kernel(const FfPoint<AT>* __restrict__ pts, int64_t npts, const double* dirs, int64_t ndir,
+                              double k, double2* out) {
   const int64_t dq = blockIdx.x;  // direction
   const int q = blockIdx.y;       // right-hand side
   const double xh[3] = {dirs[3 * dq], dirs[3 * dq + 1], dirs[3 * dq + 2]};
-  const double2* xq = x + (size_t)q * 2 * ne;
-  double acc[12] = {};
-  for (int64_t t = threadIdx.x; t < nt; t += blockDim.x) {
-    const TriD T = tri[t];
-    double ca[3][2], cb[3][2];
-    for (int a = 0; a < 3; ++a) {
-      const int e = slot_edge[3 * t + a];
-      ca[a][0] = xq[e].x; ca[a][1] = xq[e].y;
-      cb[a][0] = xq[ne + e].x * (mu / k); cb[a][1] = xq[ne + e].y * (mu / k);
-    }
-    for (int u = 0; u < 6; ++u) {
-      double xi[3];
-      for (int c = 0; c < 3; ++c)
-        xi[c] = rl.b[3 * u] * T.off[0][c] + rl.b[3 * u + 1] * T.off[1][c] + rl.b[3 * u + 2] * T.off[2][c];
-      double ph = 0;
-      for (int c = 0; c < 3; ++c) ph += xh[c] * (T.c[c] + xi[c]);
-      double s, co;
-      sincos(-k * ph, &s, &co);
-      const double w = rl.w[u] * T.area;
-      for (int a = 0; a < 3; ++a) {
-        const double* sw = slot_sw + (3 * t + a) * 4;
-        for (int c = 0; c < 3; ++c) {
-          const double phi = sw[0] * xi[c] + sw[1 + c];
-          const double er = w * co * phi, ei = w * s * phi;
-          acc[2 * c] += ca[a][0] * er - ca[a][1] * ei;
-          acc[2 * c + 1] += ca[a][0] * ei + ca[a][1] * er;
-          acc[6 + 2 * c] += cb[a][0] * er - cb[a][1] * ei;
-          acc[6 + 2 * c + 1] += cb[a][0] * ei + cb[a][1] * er;
-        }
-      }
+  const AT kx[3] = {(AT)(-k * xh[0]), (AT)(-k * xh[1]), (AT)(-k * xh[2])};
+  const FfPoint<AT>* P = pts + (size_t)q * npts;
+  AT acc[12] = {};
+  for (int64_t p = threadIdx.x; p < npts; p += blockDim.x) {
+    const FfPoint<AT>& o = P[p];
+    const AT ph = kx[0] * o.x[0] + kx[1] * o.x[1] + kx[2] * o.x[2];
+    AT s, c;
+    if constexpr (sizeof(AT) == 4) sincosf(ph, &s, &c);
+    else sincos(ph, &s, &c);
+#pragma unroll
+    for (int m = 0; m < 6; ++m) {  // (J_re + i J_im)(c + i s)
+      acc[2 * m] += o.j[2 * m] * c - o.j[2 * m + 1] * s;
+      acc[2 * m + 1] += o.j[2 * m] * s + o.j[2 * m + 1] * c;
     }
   }
   __shared__ double sh[12][32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   for (int c = 0; c < 12; ++c) {
-    double v = acc[c];
+    double v = (double)acc[c];
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     if (lane == 0) sh[c][wid] = v;
   }
@@ -1720,7 +1761,6 @@ __global__ void farfield_kernel(const TriD* __restrict__ tri, const int* __restr
       J[c] = 0;
       for (int q2 = 0; q2 < (int)(blockDim.x >> 5); ++q2) J[c] += sh[c][q2];
     }
-    // complex vectors Ja = J[0..5], Jb = J[6..11] as (re, im) per component
     double Ja[3][2], Jb[3][2], A[3][2], B1[3][2], B[3][2];
     for (int c = 0; c < 3; ++c) {
       Ja[c][0] = J[2 * c]; Ja[c][1] = J[2 * c + 1];
@@ -1749,27 +1789,27 @@ __global__ void farfield_kernel(const TriD* __restrict__ tri, const int* __restr
   }
 }
 
-int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
-               cudaStream_t st) {
+template <typename AT>
+static int farfield_t(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir, double k,
+                      double mu, double2* d_out, cudaStream_t st) {
   Rules6 rl = rules6();
-  CAL_TRY_CUDA(cudaMemsetAsync(d_b, 0, (size_t)nrhs * 2 * rwg.nbasis * sizeof(double2), st));
-  dim3 grid(blocks_for(rwg.ntri, 128), nrhs);
-  rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_inc, nrhs,
-                                   k, mu, rl, rwg.nbasis, d_b);
-  note_launch();
+  const int64_t npts = rwg.ntri * 6;
+  FfPoint<AT>* pts = nullptr;
+  if (dalloc((void**)&pts, (size_t)nrhs * npts * sizeof(FfPoint<AT>), st) != cudaSuccess)
+    return fail(CAL_ENOMEM, "far field: scratch allocation failed");
+  ff_points_kernel<AT><<<dim3(blocks_for(rwg.ntri, 128), nrhs), 128, 0, st>>>(
+      rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_x, rwg.nbasis, k, mu, rl, pts);
+  ff_sum_kernel<AT><<<dim3((unsigned)ndir, nrhs), 256, 0, st>>>(pts, npts, d_dirs, ndir, k, d_out);
+  note_launch(2);
+  dfree(pts, st);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
 }
 
 int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,
-                    double k, double mu, double2* d_out, cudaStream_t st) {
-  Rules6 rl = rules6();
-  dim3 grid((unsigned)ndir, nrhs);
-  farfield_kernel<<<grid, 256, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_x,
-                                        rwg.nbasis, d_dirs, ndir, k, mu, rl, d_out);
-  note_launch();
-  CAL_TRY_CUDA(cudaGetLastError());
-  return CAL_OK;
+                    double k, double mu, double2* d_out, int precision, cudaStream_t st) {
+  return precision == CAL_FP64 ? farfield_t<double>(rwg, d_x, nrhs, d_dirs, ndir, k, mu, d_out, st)
+                               : farfield_t<float>(rwg, d_x, nrhs, d_dirs, ndir, k, mu, d_out, st);
 }
 
 Rules6 rules6() {

@@ -102,7 +102,7 @@ int combine_rhs(const float* ZS, const float* ZC, int64_t rows, int NB, int nrhs
 int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
                cudaStream_t st);
 int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,
-                    double k, double mu, double2* d_out, cudaStream_t st);
+                    double k, double mu, double2* d_out, int precision, cudaStream_t st);
 
 // BC tile launcher (assemble.cu)
 // A5 over units: units [nunits] of {v, begin, count, pad} ints, each a test
