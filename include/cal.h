@@ -216,7 +216,9 @@ typedef struct {
   int32_t converged;
   int64_t matvecs;          /* boundary-operator applications, Table tab:matvecs */
   double residual;          /* final relative preconditioned residual           */
-  double t_setup, t_assemble_A, t_assemble_P, t_solve;  /* seconds              */
+  double t_setup, t_assemble_A, t_assemble_P, t_solve;  /* seconds: host time of the
+                            spaces (the BC space is built while A is assembled), device time of
+                            A's and P's assembly, wall time of the solve                       */
   int64_t bytes_A, bytes_P; /* device bytes of the stored operators             */
   int64_t n_unknowns;       /* 2N                                               */
 } cal_solve_info;

@@ -1034,15 +1034,19 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   }
   cudaStream_t st = ctx->impl.stream;
   int rc;
-  // spaces
+  // spaces: the RWG space now; the BC space is built on the host while the
+  // device assembles A (the launches below are asynchronous)
   P.rwg = std::make_shared<Space>();
   if ((rc = build_rwg(*P.rwg, mesh->impl)) || (rc = upload_space(*P.rwg, st))) return rc;
   const bool need_bc = o.precond != CAL_PRECOND_NONE;
-  if (need_bc) {
-    P.bc = std::make_shared<Space>();
-    if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc, st))) return rc;
-  }
-  const double t_setup = now();
+  double t_setup_host = now() - t_start;
+  // device phase times from events on the stream (the host does not wait in between)
+  struct Ev {
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    ~Ev() { for (auto x : e) if (x) cudaEventDestroy(x); }
+  } ev;
+  for (auto& x : ev.e) CAL_TRY_CUDA(cudaEventCreate(&x));
+  CAL_TRY_CUDA(cudaEventRecord(ev.e[0], st));
   // A: S, C at k_e on the union; S, C at k_m on each scatterer
   const int aprec = o.precision;  // assembly mode (CAL_FP32_ALL: float32 singular pairs)
   const int prec = aprec == CAL_FP64 ? CAL_FP64 : CAL_FP32;  // storage and vector precision
@@ -1067,8 +1071,14 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
                                o.q_regular_A, o.q_singular_A, aprec, P.A_int[m])))
         return rc;
   }
-  CAL_TRY_CUDA(cudaStreamSynchronize(st));
-  const double t_A = now();
+  CAL_TRY_CUDA(cudaEventRecord(ev.e[1], st));
+  if (need_bc) {
+    const double tb = now();
+    P.bc = std::make_shared<Space>();
+    if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc, st))) return rc;
+    t_setup_host += now() - tb;
+  }
+  CAL_TRY_CUDA(cudaEventRecord(ev.e[2], st));
   int64_t bytes_A = 0, bytes_P = 0, bytes_G = 0;
   const size_t esz = prec == CAL_FP32 ? 8 : 16;
   for (auto* a : {P.A_ext.get()}) bytes_A += a->nnz * esz * 2;
@@ -1123,13 +1133,16 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     CAL_TRY_CUDA(cudaMemsetAsync(P.d_gvalT, 0, P.gnnz * sizeof(double), st));
     if ((rc = launch_gram(*P.rwg, *P.bc, P.d_grp, P.d_gcol, P.d_grpT, P.d_gcolT, P.d_gval, P.d_gvalT, st)))
       return rc;
-    CAL_TRY_CUDA(cudaStreamSynchronize(st));
     bytes_G = 2 * ((n + 1) * 8 + P.gnnz * (4 + 8));
   }
-  const double t_P = now();
-  prob->t_setup = t_setup - t_start;
-  prob->t_assemble_A = t_A - t_setup;
-  prob->t_assemble_P = t_P - t_A;
+  CAL_TRY_CUDA(cudaEventRecord(ev.e[3], st));
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  float ms_A = 0.0f, ms_P = 0.0f;
+  cudaEventElapsedTime(&ms_A, ev.e[0], ev.e[1]);
+  cudaEventElapsedTime(&ms_P, ev.e[2], ev.e[3]);
+  prob->t_setup = t_setup_host;       // host: spaces (the BC space overlaps A's assembly)
+  prob->t_assemble_A = 1e-3 * ms_A;   // device time of A's launches
+  prob->t_assemble_P = 1e-3 * ms_P;   // device time of P's launches and the Gram matrix
   prob->bytes_A = bytes_A;
   prob->bytes_P = bytes_P;
   prob->bytes_G = bytes_G;
