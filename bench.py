@@ -44,7 +44,7 @@ Q = dict(q_regular_A=0, q_regular_P=0)
 METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bc_tile launch (exterior pass of
 # the workload), from the ncu capture summarised in profiles/; None once the kernel changes
-BC_TILE_TRAFFIC = None
+BC_TILE_TRAFFIC = 3.657359e9 + 4.079958e9
 
 
 def _env_int(name, default):
@@ -285,11 +285,11 @@ def run_ours(args, rank, world):
                              "note": "singular pairs also in float32 (CAL_FP32_ALL)"},
         "gpu_launches": int(n_launch),
         "kernels_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": "bc_tile_kernel<float,0,128>",
+        "roofline": {"bound": "alu", "kernel": "bc_owner_kernel<0,128>",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak if peak else None, "traffic": BC_TILE_TRAFFIC,
                      "traffic_note": "dram read+write bytes of one exterior launch, one ncu capture "
-                                     "(profiles/bc_tile_kernel_sphere5120.md); the per-launch work is "
+                                     "(profiles/bc_owner_kernel_sphere5120.md); the per-launch work is "
                                      f"{bc['units'] / max(bc['launches'], 1) / 1e9:.1f} G evaluations",
                      "peak_source": f"derived: {n_sm} SMs x 3.05 eval/clk x {sm_max:.0f} MHz"},
         "clocks": clocks,
