@@ -1703,7 +1703,10 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
     const TriD* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
     const int* __restrict__ slot_edge, const double* __restrict__ slot_sw, int nslot, double kr,
     double ki, double mikr, double miki, double c4r, double c4i, bool wantS, bool wantC,
-    const SsPt* __restrict__ tab, SsRadial rs, Sink<float> out) {
+    const SsPt* __restrict__ tab, SsRadial rs, Sink<float> out, double* __restrict__ stat_out,
+    const double* __restrict__ stat_in) {
+  // stat_out: store this pair's static sums (TG, Tg) for the space's next
+  // wavenumber; stat_in: read them and run the float32 remainder only
   const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const SingPair sp = pairs[p];
@@ -1729,10 +1732,54 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
   for (int q = 0; q < 9; ++q) TG[q] = Tg[q] = 0.0;
 #pragma unroll
   for (int q = 0; q < 18; ++q) DG[q] = Dg[q] = 0.0;
+  const V3<float> fa = {(float)ea.x, (float)ea.y, (float)ea.z}, fb = {(float)eb.x, (float)eb.y, (float)eb.z};
+  const V3<float> fc = {(float)ec.x, (float)ec.y, (float)ec.z}, fd = {(float)ed.x, (float)ed.y, (float)ed.z};
+  if (stat_in) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      TG[k] = stat_in[p * 18 + k];
+      Tg[k] = stat_in[p * 18 + 9 + k];
+    }
+  }
   for (int r = 0; r < nreg; ++r) {
     float dG[18], dg[18];
 #pragma unroll
     for (int q = 0; q < 18; ++q) dG[q] = dg[q] = 0.0f;
+    if (stat_in) {
+      // the static sums are known: only the float32 remainder, with x - y in
+      // float32 (its rounding near the singular set touches only O((kr)^2) terms)
+      for (int q = 0; q < ng3; ++q) {
+        const SsPt& e = T[r * ng3 + q];
+        const float fx0 = e.fx0, fx1 = e.fx1, fy0 = e.fy0, fy1 = e.fy1;
+        const V3<float> dr = {fx0 * fa.x + fx1 * fb.x - fy0 * fc.x - fy1 * fd.x,
+                              fx0 * fa.y + fx1 * fb.y - fy0 * fc.y - fy1 * fd.y,
+                              fx0 * fa.z + fx1 * fb.z - fy0 * fc.z - fy1 * fd.z};
+        const float r2f = dr.x * dr.x + dr.y * dr.y + dr.z * dr.z;
+        const float yf = rsqrtf(r2f);
+        float SG[6] = {0, 0, 0, 0, 0, 0}, Sg[6] = {0, 0, 0, 0, 0, 0};
+        dyn_radial<NG>(rs, r2f * yf, fkr, fki, doC, SG, Sg);
+        const float cGf = e.fw * yf, cgf = cGf * yf * yf;
+        const float fm[9] = {1.0f, fx0, fx1, fy0, fy1, fx0 * fy0, fx0 * fy1, fx1 * fy0, fx1 * fy1};
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const int d = k == 0 ? 0 : (k < 5 ? 2 : 4);
+          const float a = cGf * fm[k];
+          dG[2 * k] = fmaf(a, SG[d], dG[2 * k]);
+          dG[2 * k + 1] = fmaf(a, SG[d + 1], dG[2 * k + 1]);
+          if (doC) {
+            const float b = cgf * fm[k];
+            dg[2 * k] = fmaf(b, Sg[d], dg[2 * k]);
+            dg[2 * k + 1] = fmaf(b, Sg[d + 1], dg[2 * k + 1]);
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < 18; ++q) {
+        DG[q] += (double)dG[q];
+        if (doC) Dg[q] += (double)dg[q];
+      }
+      continue;
+    }
     for (int q = 0; q < ng3; ++q) {
       const SsPt& e = T[r * ng3 + q];
       const double x0 = e.x0, x1 = e.x1, y0 = e.y0, y1 = e.y1;
@@ -1786,6 +1833,13 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
     for (int q = 0; q < 18; ++q) {
       DG[q] += (double)dG[q];
       if (doC) Dg[q] += (double)dg[q];
+    }
+  }
+  if (stat_out) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      stat_out[p * 18 + k] = TG[k];
+      stat_out[p * 18 + 9 + k] = Tg[k];
     }
   }
   const TriD& A = tri[sp.t1];
@@ -2117,14 +2171,38 @@ int launch_singular(const AssembleArgs& a) {
       }
       const SsRadial rs = ss_radial(g_rules);
       const unsigned g1 = (unsigned)((np + 127) / 128);
+      // the static sums depend on the geometry and the Gauss order only: the
+      // first launch that computes all of them keeps them, later ones read them
+      std::lock_guard<std::mutex> lk(s.static_mu);
+      if (s.sing_static.size() != s.sing.size()) s.sing_static.resize(s.sing.size());
+      Space::StaticSums& st = s.sing_static[d];
+      double* sout = nullptr;
+      const double* sin = nullptr;
+      if (st.ready && st.ng == g_rules.ng) {
+        if (cudaStreamWaitEvent(a.stream, st.done, 0) != cudaSuccess) {
+          prof_end(a.stream, tok);
+          return fail(CAL_ECUDA, "singular static sums: stream wait failed");
+        }
+        sin = st.buf;
+      } else if (!st.buf && wC) {
+        if (dalloc((void**)&st.buf, (size_t)np * 18 * sizeof(double), a.stream) == cudaSuccess &&
+            cudaEventCreateWithFlags(&st.done, cudaEventDisableTiming) == cudaSuccess) {
+          st.ng = g_rules.ng;
+          sout = st.buf;
+        } else {
+          cudaGetLastError();  // no cache: this launch runs in full
+        }
+      }
       if (g_rules.ng == 4)
         singular_split_kernel<4><<<g1, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge, s.d_slot_swd,
                                                            s.nslot, a.kr, a.ki, mikr, miki, c4r, c4i, wS, wC, tab,
-                                                           rs, make_sink<float>(a));
+                                                           rs, make_sink<float>(a), sout, sin);
       else
         singular_split_kernel<0><<<g1, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge, s.d_slot_swd,
                                                            s.nslot, a.kr, a.ki, mikr, miki, c4r, c4i, wS, wC, tab,
-                                                           rs, make_sink<float>(a));
+                                                           rs, make_sink<float>(a), sout, sin);
+      if (sout && cudaPeekAtLastError() == cudaSuccess && cudaEventRecord(st.done, a.stream) == cudaSuccess)
+        st.ready = true;
     } else {
       singular_kernel<double><<<grid, 128, 0, a.stream>>>(s.d_triD, s.d_sing[d], np, s.d_slot_edge,
                                                           s.d_slot_swd, s.nslot, a.kr, a.ki, mikr, miki,

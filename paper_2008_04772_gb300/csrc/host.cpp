@@ -776,6 +776,10 @@ Space::~Space() {
                   (void*)d_cell_tri_ptr, (void*)d_cell_tri, (void*)d_cell_edge_ptr, (void*)d_cell_edge})
     dfree(p, nullptr);
   for (auto p : d_sing) dfree(p, nullptr);
+  for (auto& e : sing_static) {
+    dfree(e.buf, nullptr);
+    if (e.done) cudaEventDestroy(e.done);
+  }
 }
 
 Op::~Op() {

@@ -144,6 +144,17 @@ struct Space {
   int* d_cell_edge_ptr = nullptr;  // BC: slot sl of every triangle of cell v is cell_edge[cell_edge_ptr[v] + sl]
   int* d_cell_edge = nullptr;
   std::vector<SingPair*> d_sing;
+  // k-independent float64 sums of the touching pairs (18 doubles per pair),
+  // per scatterer: filled by its first float32 singular launch that asks for
+  // C, read by later float32 launches with the same Gauss order
+  struct StaticSums {
+    double* buf = nullptr;
+    int ng = 0;
+    bool ready = false;
+    cudaEvent_t done = nullptr;  // recorded on the filling stream after the launch
+  };
+  mutable std::mutex static_mu;
+  mutable std::vector<StaticSums> sing_static;
   ~Space();
 };
 

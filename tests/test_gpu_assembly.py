@@ -226,3 +226,31 @@ def test_fp32_split_singular_matches_fp64(ctx, name, kind, k):
             x, y = x[0], y[0]
         assert rel(x, y) < 1e-6, (w, rel(x, y))
         assert np.abs(x - y).max() < 3e-6 * np.abs(y).max()
+
+
+@pytest.mark.parametrize("name,kind", [("sphere3", "BC"), ("prisms2", "RWG")])
+def test_fp32_split_singular_reuses_static_sums(ctx, name, kind):
+    """The float64 static sums of the touching pairs depend on the geometry and
+    the Gauss order only: the first float32 launch on a space that asks for C
+    keeps them and later float32 launches run the float32 remainder alone.
+    On a fresh space: an S-only launch (keeps nothing), a launch at k = 3 that
+    keeps the sums and a launch at k = 9 that reads them; the last one against
+    float64 at the split kernel's bars (1e-6 Frobenius, 3e-6 largest entry)."""
+    m = mesh(name)
+    msh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    sp = cal.Space(msh, cal.RWG if kind == "RWG" else cal.BC)
+    cut = dict(near_cutoff=1e-9) if kind == "BC" else {}
+    cal.assemble(ctx, cal.OP_S, 1.0, sp, precision=cal.FP32, **cut)
+    first = cal.assemble(ctx, 3, 3.0, sp, precision=cal.FP32, **cut)
+    a = cal.assemble(ctx, 3, 9.0, sp, precision=cal.FP32, **cut)
+    b = cal.assemble(ctx, 3, 9.0, cal.Space(msh, cal.RWG if kind == "RWG" else cal.BC),
+                     precision=cal.FP64, **cut)
+    b3 = cal.assemble(ctx, 3, 3.0, cal.Space(msh, cal.RWG if kind == "RWG" else cal.BC),
+                      precision=cal.FP64, **cut)
+    for w in (cal.OP_S, cal.OP_C):
+        for got, ref in ((a, b), (first, b3)):
+            x, y = got.export(w), ref.export(w)
+            if isinstance(x, tuple):
+                x, y = x[0], y[0]
+            assert rel(x, y) < 1e-6, (w, rel(x, y))
+            assert np.abs(x - y).max() < 3e-6 * np.abs(y).max()
