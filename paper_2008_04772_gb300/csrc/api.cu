@@ -133,9 +133,10 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     for (int v : cells) max_cell = std::max(max_cell, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
     // tiles (v, w), v <= w, grouped into units of one test cell and up to 16 trial
     // cells (or as many as fill the block of the float32 per-thread kernel)
+    const bool owner = bc_owner_width(sp, precision, max_cell, max_cell) > 0;
     auto unit_of = [&](int v) {
-      const int w = bc_owner_width(sp, precision, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
-      return w > 0 ? w : 16;
+      if (!owner) return 16;
+      return bc_owner_width(sp, precision, std::max(1, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]), max_cell);
     };
     std::vector<int> units;  // {v, begin, count, 0} per unit
     std::vector<int> wlist;

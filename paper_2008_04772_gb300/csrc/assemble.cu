@@ -964,25 +964,72 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
 // stage-2 records of bc_tile_kernel), so pair coefficients never go through
 // shared memory and the pair loop has no barrier. The records are then written
 // to shared memory once and contracted with the test slots per (j, a, b).
-// Units hold floor(TT / n1) trial cells so that the items fill the block.
+// Units hold up to floor(TT / n1) trial cells so that the items fill the
+// block. The trial triangles of a unit are staged in shared memory first, as
+// packed records (owner_rec_words float4 each), so the pair loop reads no
+// global memory except the points of the rare near and medium pairs.
 // ---------------------------------------------------------------------------
 constexpr int BC_OWN_SLOTS = 6;
-constexpr int BC_OWN_REC = 20;  // S record [0, 10), C record [10, 18), padding
+constexpr int BC_OWN_REC = 20;    // S record [0, 10), C record [10, 18), padding
+constexpr int BC_OWN_STAGE = 160;  // staged trial triangle rows per unit (count x max_cell)
+
+// packed trial record, in float4 words: the trial rule points (the far rule's
+// 3 in class mode), BC_OWN_SLOTS slot quadruples (zero past nslot), then
+// (hi.x, hi.y, hi.z, lo.x), (lo.y, lo.z, d, vid0), (vid1, vid2, 0, 0) with the
+// vertex ids stored as int bits
+template <int NREG> __host__ __device__ constexpr int owner_trial_pts() { return NREG > 0 ? NREG : 3; }
+template <int NREG> __host__ __device__ constexpr int owner_rec_words() {
+  return owner_trial_pts<NREG>() + BC_OWN_SLOTS + 3;
+}
+
+template <int NREG>
+__global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct, float4* __restrict__ rec) {
+  constexpr int NP = owner_trial_pts<NREG>(), RW = owner_rec_words<NREG>(), NS = staged_points<NREG>();
+  constexpr int OFF = NREG > 0 ? 0 : RULE_OFF_FAR;
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= nct * RW) return;
+  const int64_t t = q / RW;
+  const int u = (int)(q - t * RW);
+  float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+  if (u < NP) {
+    const P4<float> p = cd.pts[t * NS + OFF + u];
+    o = make_float4(p.x, p.y, p.z, p.w);
+  } else if (u < NP + BC_OWN_SLOTS) {
+    const int sl = u - NP;
+    if (sl < nslot) {
+      const P4<float> p = cd.sw[t * nslot + sl];
+      o = make_float4(p.x, p.y, p.z, p.w);
+    }
+  } else {
+    const Cent<float>& c = cd.cen[t];
+    const int* v = cd.vid + 3 * t;
+    const int k = u - NP - BC_OWN_SLOTS;
+    if (k == 0) o = make_float4(c.hi[0], c.hi[1], c.hi[2], c.lo[0]);
+    else if (k == 1) o = make_float4(c.lo[1], c.lo[2], c.d, __int_as_float(v[0]));
+    else o = make_float4(__int_as_float(v[1]), __int_as_float(v[2]), 0.0f, 0.0f);
+  }
+  rec[q] = o;
+}
 
 template <int NREG, int TT>
 __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     CellData<float> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
     const int* __restrict__ cell_edge, const BcUnit* __restrict__ units, int64_t nunits,
-    const int* __restrict__ wlist, float kr, float ki, float mikr, float miki, float c4r, float c4i, bool wantS,
-    bool wantC, Sink<float> out, int max_cell, unsigned long long* cnt) {
+    const int* __restrict__ wlist, const float4* __restrict__ trec, float kr, float ki, float mikr, float miki,
+    float c4r, float c4i, bool wantS, bool wantC, Sink<float> out, int max_cell, unsigned long long* cnt) {
   constexpr int NS = staged_points<NREG>();
   constexpr int NSL = BC_OWN_SLOTS;
+  constexpr int NP = owner_trial_pts<NREG>(), RW = owner_rec_words<NREG>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float* rec = reinterpret_cast<float*>(smem_raw);                                  // [TT][NSL][BC_OWN_REC]
-  P4<float>* ptsA = reinterpret_cast<P4<float>*>(rec + (size_t)TT * NSL * BC_OWN_REC);  // [max_cell][NS]
+  float4* trial = reinterpret_cast<float4*>(rec + (size_t)TT * NSL * BC_OWN_REC);   // [BC_OWN_STAGE][RW]
+  P4<float>* ptsA = reinterpret_cast<P4<float>*>(trial + (size_t)BC_OWN_STAGE * RW);  // [max_cell][NS]
   P4<float>* swA = ptsA + (size_t)max_cell * NS;                                    // [max_cell][nslot]
   Cent<float>* cA = reinterpret_cast<Cent<float>*>(swA + (size_t)max_cell * nslot);
   int* vidA = reinterpret_cast<int*>(cA + max_cell);                                // [max_cell][3]
+  int* jb = vidA + 3 * max_cell;                                                    // [TT] first trial triangle
+  int* jn = jb + TT;                                                                // [TT] trial triangles
+  int* jw = jn + TT;                                                                // [TT] trial cell
   unsigned evals = 0;
   for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
     const BcUnit U = units[uidx];
@@ -996,14 +1043,30 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       cA[q] = cd.cen[b1 + q];
       for (int c = 0; c < 3; ++c) vidA[3 * q + c] = cd.vid[(size_t)(b1 + q) * 3 + c];
     }
+    for (int j = threadIdx.x; j < U.count; j += TT) {
+      const int w = wlist[U.begin + j];
+      const int b = cell_ptr[w];
+      jw[j] = w;
+      jb[j] = b;
+      jn[j] = cell_ptr[w + 1] - b;
+    }
+    __syncthreads();
+    // trial records: cell j at rows [j max_cell, j max_cell + n2); the host
+    // keeps count x max_cell <= BC_OWN_STAGE
+    for (int q = threadIdx.x; q < U.count * max_cell * RW; q += TT) {
+      const int row = q / RW, u = q - row * RW;
+      const int j = row / max_cell, i2 = row - j * max_cell;
+      if (i2 < jn[j]) trial[q] = trec[(size_t)(jb[j] + i2) * RW + u];
+    }
     __syncthreads();
     const int items = n1 * U.count;
     // pair loop: thread t = j n1 + i1
     if ((int)threadIdx.x < items) {
       const int j = threadIdx.x / n1, i1 = threadIdx.x - j * n1;
-      const int w = wlist[U.begin + j];
-      const int b2 = cell_ptr[w], n2 = cell_ptr[w + 1] - b2;
+      const int w = jw[j];
+      const int b2 = jb[j], n2 = jn[j];
       const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
+      const float4* R2 = trial + (size_t)j * max_cell * RW;
       const Cent<float> ca = cA[i1];
       const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
       const P4<float>* X = ptsA + i1 * NS;
@@ -1013,42 +1076,43 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
 #pragma unroll
         for (int f = 0; f < 18; ++f) r[b][f] = 0.0f;
       for (int i2 = 0; i2 < n2; ++i2) {
-        const int t2 = b2 + i2;
-        // the pair's trial data in one batch of independent loads (the far-rule
-        // points speculatively: almost every pair is far), one latency per pair
-        const int* vb = cd.vid + (size_t)t2 * 3;
-        const int vb0 = vb[0], vb1 = vb[1], vb2 = vb[2];
-        const Cent<float> cb = cd.cen[t2];
-        const P4<float>* Y = cd.pts + (size_t)t2 * NS;
-        P4<float> yf[3];
-        if constexpr (NREG == 0) {
-#pragma unroll
-          for (int q = 0; q < 3; ++q) yf[q] = Y[RULE_OFF_FAR + q];
-        }
+        const float4* rr = R2 + i2 * RW;
+        const float4 k0 = rr[NP + NSL], k1 = rr[NP + NSL + 1], k2 = rr[NP + NSL + 2];
+        const int vb0 = __float_as_int(k1.w), vb1 = __float_as_int(k2.x), vb2 = __float_as_int(k2.y);
+        Cent<float> cb;
+        cb.hi[0] = k0.x; cb.hi[1] = k0.y; cb.hi[2] = k0.z;
+        cb.lo[0] = k0.w; cb.lo[1] = k1.x; cb.lo[2] = k1.y;
+        cb.d = k1.z;
+        // staged trial rule points (class mode: the far rule)
+        const P4<float>* Ys = reinterpret_cast<const P4<float>*>(rr);
         const bool touch = va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 ||
                            va2 == vb0 || va2 == vb1 || va2 == vb2;
         if (touch) continue;  // Sauter–Schwab pairs: the singular kernel
         const V3<float> D = ca.minus(cb);
         Mom<float> m;
         if constexpr (NREG > 0) {
-          regular_moments_staged<float, NREG>(X, Y, D, kr, ki, wantC, m);
+          regular_moments_staged<float, NREG>(X, Ys, D, kr, ki, wantC, m);
           evals += NREG * NREG;
         } else {
           const int c = pair_class<float>(D, ca.d, cb.d);
           if (c == 2) {
-            regular_moments_staged<float, 3>(X + RULE_OFF_FAR, yf, D, kr, ki, wantC, m);
+            regular_moments_staged<float, 3>(X + RULE_OFF_FAR, Ys, D, kr, ki, wantC, m);
             evals += 9;
-          } else if (c == 1) {
-            regular_moments_staged<float, 4>(X + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki, wantC, m);
-            evals += 16;
           } else {
-            regular_moments_staged<float, 6>(X, Y, D, kr, ki, wantC, m);
-            evals += 36;
+            // near and medium pairs (under 1%): points from global memory
+            const P4<float>* Y = cd.pts + (size_t)(b2 + i2) * NS;
+            if (c == 1) {
+              regular_moments_staged<float, 4>(X + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki, wantC, m);
+              evals += 16;
+            } else {
+              regular_moments_staged<float, 6>(X, Y, D, kr, ki, wantC, m);
+              evals += 36;
+            }
           }
         }
         float pc[36];
         pair_coeffs(m, D, pc);
-        const P4<float>* swb = cd.sw + (size_t)t2 * nslot;
+        const P4<float>* swb = Ys + NP;
 #pragma unroll
         for (int b = 0; b < NSL; ++b) {
           if (b >= ns2) break;
@@ -1089,7 +1153,7 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       const int j = q / (ns1 * NSL);
       const int rest = q - j * ns1 * NSL;
       const int sa_i = rest / NSL, sb_i = rest - (rest / NSL) * NSL;
-      const int w = wlist[U.begin + j];
+      const int w = jw[j];
       const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
       if (sb_i >= ns2) continue;
       float sr = 0, si = 0, cr = 0, ci = 0;
@@ -1120,11 +1184,14 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
 constexpr int BC_OWNER_TT = 128;
 
 // trial cells per unit for the one-thread-per-(test triangle, trial cell)
-// kernel with a test cell of n1 triangles; 0 when that kernel does not apply
-// (float64, or cells with more than BC_OWN_SLOTS edges)
-int bc_owner_width(const Space& s, int precision, int n1) {
-  if (precision != CAL_FP32 || s.nslot > BC_OWN_SLOTS || n1 < 1 || n1 > BC_OWNER_TT) return 0;
-  return std::max(1, BC_OWNER_TT / n1);
+// kernel with a test cell of n1 triangles and at most max_cell triangles per
+// cell; 0 when that kernel does not apply (float64, cells with more than
+// BC_OWN_SLOTS edges or more than BC_OWN_STAGE triangles)
+int bc_owner_width(const Space& s, int precision, int n1, int max_cell) {
+  if (precision != CAL_FP32 || s.nslot > BC_OWN_SLOTS || n1 < 1 || n1 > BC_OWNER_TT || max_cell < n1 ||
+      max_cell > BC_OWN_STAGE)
+    return 0;
+  return std::max(1, std::min(BC_OWNER_TT / n1, BC_OWN_STAGE / max_cell));
 }
 
 // ---------------------------------------------------------------------------
@@ -2084,14 +2151,26 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
   prep<<<(unsigned)((nct * nsp + 255) / 256), 256, 0, a.stream>>>(tri, sw, s.nslot, s.d_cell_tri, nct, g_rules, cd);
   note_launch();
   if constexpr (sizeof(R) == 4) {
-    if (bc_owner_width(s, a.precision, max_cell) > 0) {
+    if (bc_owner_width(s, a.precision, max_cell, max_cell) > 0) {
       // one thread per (test triangle, trial cell); units sized by bc_owner_width
       constexpr int OT = BC_OWNER_TT;
       auto okern = nreg == 6 ? bc_owner_kernel<6, OT> : (nreg == 1 ? bc_owner_kernel<1, OT> : bc_owner_kernel<0, OT>);
+      auto pack = nreg == 6 ? bc_trial_pack_kernel<6> : (nreg == 1 ? bc_trial_pack_kernel<1> : bc_trial_pack_kernel<0>);
+      const int rw = nreg == 6 ? owner_rec_words<6>() : (nreg == 1 ? owner_rec_words<1>() : owner_rec_words<0>());
+      float4* trec = nullptr;
+      if (cudaMallocAsync((void**)&trec, (size_t)std::max<int64_t>(nct, 1) * rw * sizeof(float4), a.stream) !=
+          cudaSuccess) {
+        cudaFreeAsync(buf, a.stream);
+        return fail(CAL_ENOMEM, "bc owner kernel: cannot allocate the trial records");
+      }
+      pack<<<(unsigned)((nct * rw + 255) / 256), 256, 0, a.stream>>>(cd, s.nslot, nct, trec);
+      note_launch();
       const int nsp_o = nreg > 0 ? nreg : RULE_POINTS_ALL;
       const size_t osmem = (size_t)OT * BC_OWN_SLOTS * BC_OWN_REC * sizeof(float) +
+                           (size_t)BC_OWN_STAGE * rw * sizeof(float4) +
                            (size_t)max_cell * nsp_o * sizeof(P4<float>) + (size_t)max_cell * s.nslot * sizeof(P4<float>) +
-                           (size_t)max_cell * sizeof(Cent<float>) + (size_t)max_cell * 3 * sizeof(int) + 64;
+                           (size_t)max_cell * sizeof(Cent<float>) + (size_t)max_cell * 3 * sizeof(int) +
+                           3 * (size_t)OT * sizeof(int) + 64;
       int rc = ensure_dyn_smem((const void*)okern, (int)osmem);
       int per_sm = 0;
       if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, OT, osmem) != cudaSuccess)
@@ -2101,12 +2180,13 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
         const int tok = prof_begin(a.stream, "bc_tile", work);
         unsigned long long* cnt = nreg == 0 ? prof_counter(tok, a.stream) : nullptr;
         okern<<<(unsigned)grid, OT, osmem, a.stream>>>(cd, s.nslot, s.d_cell_tri_ptr, s.d_cell_edge_ptr, s.d_cell_edge,
-                                                      units, nunits, wlist, (float)a.kr, (float)a.ki, mikr, miki, c4r,
-                                                      c4i, wS, wC, out, max_cell, cnt);
+                                                      units, nunits, wlist, trec, (float)a.kr, (float)a.ki, mikr, miki,
+                                                      c4r, c4i, wS, wC, out, max_cell, cnt);
         prof_end(a.stream, tok);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = fail(CAL_ECUDA, "bc owner kernel launch failed");
       }
+      cudaFreeAsync(trec, a.stream);
       cudaFreeAsync(buf, a.stream);
       return rc;
     }

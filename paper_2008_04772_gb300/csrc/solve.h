@@ -111,6 +111,6 @@ int launch_bc_regular_units(const AssembleArgs& a, const void* units, int64_t nu
                             int n_sm, double work);
 // trial cells per unit for a test cell of n1 triangles when the float32
 // one-thread-per-(test triangle, trial cell) kernel applies, else 0
-int bc_owner_width(const Space& s, int precision, int n1);
+int bc_owner_width(const Space& s, int precision, int n1, int max_cell);
 
 }  // namespace cal
