@@ -348,6 +348,14 @@ int cal_request_footprint(const cal_request* req, int64_t* resident_bytes, int64
    points evenly spread over [lo, hi] on the current device. Writes the max
    absolute error of (cos, sin) and the max relative error of exp. */
 int cal_check_elementary(int64_t n, double lo, double hi, double* err_cis, double* err_exp);
+/* The paper has no counterpart: a check of the bounded grid-wide barrier of
+   the Gram solver's cooperative kernel, on ctx's device. Four blocks pass
+   three barriers; when skip_block is in [0, 4) that block leaves before the
+   first one, so the others give up after their bounded wait (about a second
+   or two) and report it. *status = 0 when every block passed every barrier,
+   1 when a wait gave up. Returns CAL_OK unless the launch or a copy failed;
+   the context stays usable either way. */
+int cal_check_grid_barrier(cal_ctx* ctx, int skip_block, int* status);
 /* Number of kernels this library has launched since load (all contexts). */
 int64_t cal_kernel_launches(void);
 /* on != 0: bracket every assembly kernel launch with CUDA events on its own

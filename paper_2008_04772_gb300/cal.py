@@ -159,6 +159,7 @@ def lib():
                                   ctypes.c_int),
         "cal_kernel_launches": ([], i64),
         "cal_check_elementary": ([i64, d, d, ctypes.POINTER(d), ctypes.POINTER(d)], ctypes.c_int),
+        "cal_check_grid_barrier": ([ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cal_profile_enable": ([ctypes.c_int], ctypes.c_int),
         "cal_profile_read": ([ctypes.c_char_p, ctypes.POINTER(i64), ctypes.POINTER(d),
                               ctypes.POINTER(d)], ctypes.c_int),
@@ -189,6 +190,14 @@ class Context:
     @property
     def stream(self):
         return lib().cal_ctx_stream(self.h)
+
+    def check_grid_barrier(self, skip_block: int = -1) -> int:
+        """Bounded grid-barrier check (cal_check_grid_barrier): 0 when every
+        block passed, 1 when a wait gave up (skip_block in 0..3 makes one block
+        leave early)."""
+        st = ctypes.c_int(-1)
+        _check(lib().cal_check_grid_barrier(self.h, skip_block, ctypes.byref(st)))
+        return st.value
 
     def close(self):
         if self.h:

@@ -1352,6 +1352,10 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
     CAL_TRY_CUDA(cudaStreamSynchronize(st));
     if (herr) return fail(CAL_ETIMEOUT, "tensor-core product: a bounded wait gave up");
   }
+  if (P.gsA32 && (rc = P.gsA32->check(st))) return rc;
+  if (P.gsP32 && (rc = P.gsP32->check(st))) return rc;
+  if (P.gsA64 && (rc = P.gsA64->check(st))) return rc;
+  if (P.gsP64 && (rc = P.gsP64->check(st))) return rc;
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_end = now();
   sol->rwg = P.rwg;
@@ -1425,6 +1429,11 @@ void cal_solution_destroy(cal_solution* sol) { delete sol; }
 
 int cal_check_elementary(int64_t n, double lo, double hi, double* err_cis, double* err_exp) {
   return cal::check_elementary(n, lo, hi, err_cis, err_exp);
+}
+
+int cal_check_grid_barrier(cal_ctx* ctx, int skip_block, int* status) {
+  if (!ctx || !status) return fail(CAL_EINVAL, "cal_check_grid_barrier: NULL argument");
+  return cal::grid_barrier_check(skip_block, status, ctx->impl.stream);
 }
 
 int64_t cal_kernel_launches(void) { return cal::launches(); }

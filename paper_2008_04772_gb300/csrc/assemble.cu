@@ -92,9 +92,9 @@ __device__ __forceinline__ V3<R> cross3(const V3<R>& a, const V3<R>& b) {
 // ---------------------------------------------------------------------------
 // kernel values G = e^{ikr}/(4 pi r) and g = (ikr - 1) e^{ikr}/(4 pi r^3)
 // ---------------------------------------------------------------------------
-// w: quadrature weight folded into the amplitude (pass 1 for none)
-__device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, float& Gi,
-                                      float& gr, float& gi, float w = 1.0f) {
+// w4: quadrature weight over 4 pi, folded into the amplitude
+__device__ __forceinline__ void green4(float r2, float kr, float ki, float& Gr, float& Gi,
+                                       float& gr, float& gi, float w4) {
   const float rinv = rsqrtf(r2);
   const float r = r2 * rinv;
   const float ph = kr * r;
@@ -109,8 +109,7 @@ __device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, f
   th = fmaf(-n, TP_LO, th);
   float s, c;
   __sincosf(th, &s, &c);
-  constexpr float INV_4PI = (float)(0.25 / 3.14159265358979323846);
-  float amp = rinv * (w * INV_4PI);
+  float amp = rinv * w4;
   if (ki != 0.0f) amp *= __expf(-ki * r);
   Gr = amp * c;
   Gi = amp * s;
@@ -118,6 +117,14 @@ __device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, f
   const float fi = kr * rinv;
   gr = Gr * fr - Gi * fi;
   gi = Gr * fi + Gi * fr;
+}
+
+constexpr float INV_4PI_F = (float)(0.25 / 3.14159265358979323846);
+
+// w: quadrature weight folded into the amplitude (pass 1 for none)
+__device__ __forceinline__ void green(float r2, float kr, float ki, float& Gr, float& Gi,
+                                      float& gr, float& gi, float w = 1.0f) {
+  green4(r2, kr, ki, Gr, Gi, gr, gi, w * INV_4PI_F);
 }
 
 __device__ __forceinline__ void green(double r2, double kr, double ki, double& Gr, double& Gi,
@@ -974,7 +981,7 @@ constexpr int BC_OWN_REC = 20;    // S record [0, 10), C record [10, 18), paddin
 constexpr int BC_OWN_STAGE = 160;  // staged trial triangle rows per unit (count x max_cell)
 
 // packed trial record, in float4 words: the trial rule points (the far rule's
-// 3 in class mode), BC_OWN_SLOTS slot quadruples (zero past nslot), then
+// 3 in class mode) with their weights over 4 pi, BC_OWN_SLOTS slot quadruples (zero past nslot), then
 // (hi.x, hi.y, hi.z, lo.x), (lo.y, lo.z, d, vid0), (vid1, vid2, 0, 0) with the
 // vertex ids stored as int bits
 template <int NREG> __host__ __device__ constexpr int owner_trial_pts() { return NREG > 0 ? NREG : 3; }
@@ -993,7 +1000,7 @@ __global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct,
   float4 o = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
   if (u < NP) {
     const P4<float> p = cd.pts[t * NS + OFF + u];
-    o = make_float4(p.x, p.y, p.z, p.w);
+    o = make_float4(p.x, p.y, p.z, p.w * INV_4PI_F);
   } else if (u < NP + BC_OWN_SLOTS) {
     const int sl = u - NP;
     if (sl < nslot) {
@@ -1011,6 +1018,92 @@ __global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct,
   rec[q] = o;
 }
 
+// Moments of one regular pair for the owner kernel, every accumulation a
+// single fused multiply-add: test points X = (x, y, z, w) with XW = (w x, w y,
+// w z, w); trial points Y with weights over 4 pi when PRE (the packed
+// records), plain weights otherwise.
+template <int NP, bool PRE>
+__device__ __forceinline__ void owner_moments(const P4<float>* __restrict__ X, const P4<float>* __restrict__ XW,
+                                              const P4<float>* __restrict__ Y, const V3<float>& D, float kr,
+                                              float ki, bool wantC, Mom<float>& m) {
+  m.zero();
+#pragma unroll 2
+  for (int p = 0; p < NP; ++p) {
+    const P4<float> xp = X[p], xw = XW[p];
+    float s0r = 0, s0i = 0, t0r = 0, t0i = 0;
+    V3<float> ser = {0, 0, 0}, sei = {0, 0, 0}, ter = {0, 0, 0}, tei = {0, 0, 0};
+    const V3<float> dp = {D.x + xp.x, D.y + xp.y, D.z + xp.z};
+#pragma unroll
+    for (int q = 0; q < NP; ++q) {
+      const P4<float> yq = Y[q];
+      const float dx = dp.x - yq.x, dy = dp.y - yq.y, dz = dp.z - yq.z;
+      float Gr, Gi, gr, gi;
+      green4(dx * dx + dy * dy + dz * dz, kr, ki, Gr, Gi, gr, gi, PRE ? yq.w : yq.w * INV_4PI_F);
+      s0r += Gr; s0i += Gi;
+      ser.x = fmaf(Gr, yq.x, ser.x); ser.y = fmaf(Gr, yq.y, ser.y); ser.z = fmaf(Gr, yq.z, ser.z);
+      sei.x = fmaf(Gi, yq.x, sei.x); sei.y = fmaf(Gi, yq.y, sei.y); sei.z = fmaf(Gi, yq.z, sei.z);
+      if (wantC) {
+        t0r += gr; t0i += gi;
+        ter.x = fmaf(gr, yq.x, ter.x); ter.y = fmaf(gr, yq.y, ter.y); ter.z = fmaf(gr, yq.z, ter.z);
+        tei.x = fmaf(gi, yq.x, tei.x); tei.y = fmaf(gi, yq.y, tei.y); tei.z = fmaf(gi, yq.z, tei.z);
+      }
+    }
+    const float w = xw.w;
+    m.G0r = fmaf(w, s0r, m.G0r); m.G0i = fmaf(w, s0i, m.G0i);
+    m.Gxr.x = fmaf(xw.x, s0r, m.Gxr.x); m.Gxr.y = fmaf(xw.y, s0r, m.Gxr.y); m.Gxr.z = fmaf(xw.z, s0r, m.Gxr.z);
+    m.Gxi.x = fmaf(xw.x, s0i, m.Gxi.x); m.Gxi.y = fmaf(xw.y, s0i, m.Gxi.y); m.Gxi.z = fmaf(xw.z, s0i, m.Gxi.z);
+    m.Gyr.x = fmaf(w, ser.x, m.Gyr.x); m.Gyr.y = fmaf(w, ser.y, m.Gyr.y); m.Gyr.z = fmaf(w, ser.z, m.Gyr.z);
+    m.Gyi.x = fmaf(w, sei.x, m.Gyi.x); m.Gyi.y = fmaf(w, sei.y, m.Gyi.y); m.Gyi.z = fmaf(w, sei.z, m.Gyi.z);
+    m.Gxyr = fmaf(xw.z, ser.z, fmaf(xw.y, ser.y, fmaf(xw.x, ser.x, m.Gxyr)));
+    m.Gxyi = fmaf(xw.z, sei.z, fmaf(xw.y, sei.y, fmaf(xw.x, sei.x, m.Gxyi)));
+    if (wantC) {
+      m.g0r = fmaf(w, t0r, m.g0r); m.g0i = fmaf(w, t0i, m.g0i);
+      m.gxr.x = fmaf(xw.x, t0r, m.gxr.x); m.gxr.y = fmaf(xw.y, t0r, m.gxr.y); m.gxr.z = fmaf(xw.z, t0r, m.gxr.z);
+      m.gxi.x = fmaf(xw.x, t0i, m.gxi.x); m.gxi.y = fmaf(xw.y, t0i, m.gxi.y); m.gxi.z = fmaf(xw.z, t0i, m.gxi.z);
+      m.gyr.x = fmaf(w, ter.x, m.gyr.x); m.gyr.y = fmaf(w, ter.y, m.gyr.y); m.gyr.z = fmaf(w, ter.z, m.gyr.z);
+      m.gyi.x = fmaf(w, tei.x, m.gyi.x); m.gyi.y = fmaf(w, tei.y, m.gyi.y); m.gyi.z = fmaf(w, tei.z, m.gyi.z);
+      // gxy += (w x) x te
+      m.gxyr.x = fmaf(xw.y, ter.z, fmaf(-xw.z, ter.y, m.gxyr.x));
+      m.gxyr.y = fmaf(xw.z, ter.x, fmaf(-xw.x, ter.z, m.gxyr.y));
+      m.gxyr.z = fmaf(xw.x, ter.y, fmaf(-xw.y, ter.x, m.gxyr.z));
+      m.gxyi.x = fmaf(xw.y, tei.z, fmaf(-xw.z, tei.y, m.gxyi.x));
+      m.gxyi.y = fmaf(xw.z, tei.x, fmaf(-xw.x, tei.z, m.gxyi.y));
+      m.gxyi.z = fmaf(xw.x, tei.y, fmaf(-xw.y, tei.x, m.gxyi.z));
+    }
+  }
+}
+
+// pair_coeffs with fused multiply-adds (same layout)
+__device__ __forceinline__ void pair_coeffs_fused(const Mom<float>& m, const V3<float>& D, float* pc) {
+  pc[0] = m.G0r; pc[1] = m.G0i;
+  pc[2] = m.Gxr.x; pc[3] = m.Gxr.y; pc[4] = m.Gxr.z; pc[5] = m.Gxi.x; pc[6] = m.Gxi.y; pc[7] = m.Gxi.z;
+  pc[8] = m.Gyr.x; pc[9] = m.Gyr.y; pc[10] = m.Gyr.z; pc[11] = m.Gyi.x; pc[12] = m.Gyi.y; pc[13] = m.Gyi.z;
+  pc[14] = m.Gxyr; pc[15] = m.Gxyi;
+  pc[16] = fmaf(D.z, m.gxyr.z, fmaf(D.y, m.gxyr.y, D.x * m.gxyr.x));
+  pc[17] = fmaf(D.z, m.gxyi.z, fmaf(D.y, m.gxyi.y, D.x * m.gxyi.x));
+  // X1 = D x gx + gxy
+  pc[18] = fmaf(D.y, m.gxr.z, fmaf(-D.z, m.gxr.y, m.gxyr.x));
+  pc[19] = fmaf(D.z, m.gxr.x, fmaf(-D.x, m.gxr.z, m.gxyr.y));
+  pc[20] = fmaf(D.x, m.gxr.y, fmaf(-D.y, m.gxr.x, m.gxyr.z));
+  pc[21] = fmaf(D.y, m.gxi.z, fmaf(-D.z, m.gxi.y, m.gxyi.x));
+  pc[22] = fmaf(D.z, m.gxi.x, fmaf(-D.x, m.gxi.z, m.gxyi.y));
+  pc[23] = fmaf(D.x, m.gxi.y, fmaf(-D.y, m.gxi.x, m.gxyi.z));
+  // X2 = gy x D - gxy
+  pc[24] = fmaf(m.gyr.y, D.z, fmaf(-m.gyr.z, D.y, -m.gxyr.x));
+  pc[25] = fmaf(m.gyr.z, D.x, fmaf(-m.gyr.x, D.z, -m.gxyr.y));
+  pc[26] = fmaf(m.gyr.x, D.y, fmaf(-m.gyr.y, D.x, -m.gxyr.z));
+  pc[27] = fmaf(m.gyi.y, D.z, fmaf(-m.gyi.z, D.y, -m.gxyi.x));
+  pc[28] = fmaf(m.gyi.z, D.x, fmaf(-m.gyi.x, D.z, -m.gxyi.y));
+  pc[29] = fmaf(m.gyi.x, D.y, fmaf(-m.gyi.y, D.x, -m.gxyi.z));
+  // V = D g0 + gx - gy
+  pc[30] = fmaf(D.x, m.g0r, m.gxr.x - m.gyr.x);
+  pc[31] = fmaf(D.y, m.g0r, m.gxr.y - m.gyr.y);
+  pc[32] = fmaf(D.z, m.g0r, m.gxr.z - m.gyr.z);
+  pc[33] = fmaf(D.x, m.g0i, m.gxi.x - m.gyi.x);
+  pc[34] = fmaf(D.y, m.g0i, m.gxi.y - m.gyi.y);
+  pc[35] = fmaf(D.z, m.g0i, m.gxi.z - m.gyi.z);
+}
+
 template <int NREG, int TT>
 __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     CellData<float> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
@@ -1024,7 +1117,8 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   float* rec = reinterpret_cast<float*>(smem_raw);                                  // [TT][NSL][BC_OWN_REC]
   float4* trial = reinterpret_cast<float4*>(rec + (size_t)TT * NSL * BC_OWN_REC);   // [BC_OWN_STAGE][RW]
   P4<float>* ptsA = reinterpret_cast<P4<float>*>(trial + (size_t)BC_OWN_STAGE * RW);  // [max_cell][NS]
-  P4<float>* swA = ptsA + (size_t)max_cell * NS;                                    // [max_cell][nslot]
+  P4<float>* ptsW = ptsA + (size_t)max_cell * NS;                                   // [max_cell][NS] w (x, y, z), w
+  P4<float>* swA = ptsW + (size_t)max_cell * NS;                                    // [max_cell][nslot]
   Cent<float>* cA = reinterpret_cast<Cent<float>*>(swA + (size_t)max_cell * nslot);
   int* vidA = reinterpret_cast<int*>(cA + max_cell);                                // [max_cell][3]
   int* jb = vidA + 3 * max_cell;                                                    // [TT] first trial triangle
@@ -1037,7 +1131,11 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
     const int ns1 = cell_edge_ptr[v + 1] - cell_edge_ptr[v];
     __syncthreads();  // the previous unit is done with the test-cell data and the records
-    for (int q = threadIdx.x; q < n1 * NS; q += TT) ptsA[q] = cd.pts[(size_t)b1 * NS + q];
+    for (int q = threadIdx.x; q < n1 * NS; q += TT) {
+      const P4<float> x = cd.pts[(size_t)b1 * NS + q];
+      ptsA[q] = x;
+      ptsW[q] = {x.w * x.x, x.w * x.y, x.w * x.z, x.w};
+    }
     for (int q = threadIdx.x; q < n1 * nslot; q += TT) swA[q] = cd.sw[(size_t)b1 * nslot + q];
     for (int q = threadIdx.x; q < n1; q += TT) {
       cA[q] = cd.cen[b1 + q];
@@ -1070,6 +1168,7 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       const Cent<float> ca = cA[i1];
       const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
       const P4<float>* X = ptsA + i1 * NS;
+      const P4<float>* XW = ptsW + i1 * NS;
       float r[NSL][18];
 #pragma unroll
       for (int b = 0; b < NSL; ++b)
@@ -1085,55 +1184,66 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
         cb.d = k1.z;
         // staged trial rule points (class mode: the far rule)
         const P4<float>* Ys = reinterpret_cast<const P4<float>*>(rr);
-        const bool touch = va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 ||
-                           va2 == vb0 || va2 == vb1 || va2 == vb2;
-        if (touch) continue;  // Sauter–Schwab pairs: the singular kernel
         const V3<float> D = ca.minus(cb);
+        // Sauter–Schwab pairs (a shared vertex) are the singular kernel's; such
+        // pairs are always near: |c1 - c2| <= 2/3 (d1 + d2)
+        auto touch = [&]() {
+          return va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 || va2 == vb0 ||
+                 va2 == vb1 || va2 == vb2;
+        };
         Mom<float> m;
         if constexpr (NREG > 0) {
-          regular_moments_staged<float, NREG>(X, Ys, D, kr, ki, wantC, m);
+          if (touch()) continue;
+          owner_moments<NREG, true>(X, XW, Ys, D, kr, ki, wantC, m);
           evals += NREG * NREG;
         } else {
           const int c = pair_class<float>(D, ca.d, cb.d);
           if (c == 2) {
-            regular_moments_staged<float, 3>(X + RULE_OFF_FAR, Ys, D, kr, ki, wantC, m);
+            owner_moments<3, true>(X + RULE_OFF_FAR, XW + RULE_OFF_FAR, Ys, D, kr, ki, wantC, m);
             evals += 9;
           } else {
+            if (c == 0 && touch()) continue;
             // near and medium pairs (under 1%): points from global memory
             const P4<float>* Y = cd.pts + (size_t)(b2 + i2) * NS;
             if (c == 1) {
-              regular_moments_staged<float, 4>(X + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki, wantC, m);
+              owner_moments<4, false>(X + RULE_OFF_MEDIUM, XW + RULE_OFF_MEDIUM, Y + RULE_OFF_MEDIUM, D, kr, ki,
+                                      wantC, m);
               evals += 16;
             } else {
-              regular_moments_staged<float, 6>(X, Y, D, kr, ki, wantC, m);
+              owner_moments<6, false>(X, XW, Y, D, kr, ki, wantC, m);
               evals += 36;
             }
           }
         }
         float pc[36];
-        pair_coeffs(m, D, pc);
+        pair_coeffs_fused(m, D, pc);
         const P4<float>* swb = Ys + NP;
 #pragma unroll
         for (int b = 0; b < NSL; ++b) {
           if (b >= ns2) break;
           const P4<float> u = swb[b];
-          const float sb = u.x;
-          const V3<float> wb = {u.y, u.z, u.w};
+          const float sb = u.x, bx = u.y, by = u.z, bz = u.w;
           float* o = r[b];
           // S: AS (re, im), BS (re, im), WS_r, WS_i
-          o[0] += sb * pc[14] + wb.x * pc[2] + wb.y * pc[3] + wb.z * pc[4];
-          o[1] += sb * pc[15] + wb.x * pc[5] + wb.y * pc[6] + wb.z * pc[7];
-          o[2] += sb * pc[0];
-          o[3] += sb * pc[1];
-          o[4] += sb * pc[8] + wb.x * pc[0]; o[5] += sb * pc[9] + wb.y * pc[0]; o[6] += sb * pc[10] + wb.z * pc[0];
-          o[7] += sb * pc[11] + wb.x * pc[1]; o[8] += sb * pc[12] + wb.y * pc[1]; o[9] += sb * pc[13] + wb.z * pc[1];
-          // C: AC (re, im), WC_r, WC_i
-          o[10] += sb * pc[16] + wb.x * pc[18] + wb.y * pc[19] + wb.z * pc[20];
-          o[11] += sb * pc[17] + wb.x * pc[21] + wb.y * pc[22] + wb.z * pc[23];
-          const V3<float> Vr = {pc[30], pc[31], pc[32]}, Vi = {pc[33], pc[34], pc[35]};
-          const V3<float> cr = cross3(wb, Vr), ci = cross3(wb, Vi);
-          o[12] += sb * pc[24] + cr.x; o[13] += sb * pc[25] + cr.y; o[14] += sb * pc[26] + cr.z;
-          o[15] += sb * pc[27] + ci.x; o[16] += sb * pc[28] + ci.y; o[17] += sb * pc[29] + ci.z;
+          o[0] = fmaf(bz, pc[4], fmaf(by, pc[3], fmaf(bx, pc[2], fmaf(sb, pc[14], o[0]))));
+          o[1] = fmaf(bz, pc[7], fmaf(by, pc[6], fmaf(bx, pc[5], fmaf(sb, pc[15], o[1]))));
+          o[2] = fmaf(sb, pc[0], o[2]);
+          o[3] = fmaf(sb, pc[1], o[3]);
+          o[4] = fmaf(bx, pc[0], fmaf(sb, pc[8], o[4]));
+          o[5] = fmaf(by, pc[0], fmaf(sb, pc[9], o[5]));
+          o[6] = fmaf(bz, pc[0], fmaf(sb, pc[10], o[6]));
+          o[7] = fmaf(bx, pc[1], fmaf(sb, pc[11], o[7]));
+          o[8] = fmaf(by, pc[1], fmaf(sb, pc[12], o[8]));
+          o[9] = fmaf(bz, pc[1], fmaf(sb, pc[13], o[9]));
+          // C: AC (re, im), WC_r = sb X2r + wb x Vr, WC_i
+          o[10] = fmaf(bz, pc[20], fmaf(by, pc[19], fmaf(bx, pc[18], fmaf(sb, pc[16], o[10]))));
+          o[11] = fmaf(bz, pc[23], fmaf(by, pc[22], fmaf(bx, pc[21], fmaf(sb, pc[17], o[11]))));
+          o[12] = fmaf(by, pc[32], fmaf(-bz, pc[31], fmaf(sb, pc[24], o[12])));
+          o[13] = fmaf(bz, pc[30], fmaf(-bx, pc[32], fmaf(sb, pc[25], o[13])));
+          o[14] = fmaf(bx, pc[31], fmaf(-by, pc[30], fmaf(sb, pc[26], o[14])));
+          o[15] = fmaf(by, pc[35], fmaf(-bz, pc[34], fmaf(sb, pc[27], o[15])));
+          o[16] = fmaf(bz, pc[33], fmaf(-bx, pc[35], fmaf(sb, pc[28], o[16])));
+          o[17] = fmaf(bx, pc[34], fmaf(-by, pc[33], fmaf(sb, pc[29], o[17])));
         }
       }
       float* dst = rec + (size_t)threadIdx.x * NSL * BC_OWN_REC;
@@ -2168,9 +2278,9 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
       const int nsp_o = nreg > 0 ? nreg : RULE_POINTS_ALL;
       const size_t osmem = (size_t)OT * BC_OWN_SLOTS * BC_OWN_REC * sizeof(float) +
                            (size_t)BC_OWN_STAGE * rw * sizeof(float4) +
-                           (size_t)max_cell * nsp_o * sizeof(P4<float>) + (size_t)max_cell * s.nslot * sizeof(P4<float>) +
-                           (size_t)max_cell * sizeof(Cent<float>) + (size_t)max_cell * 3 * sizeof(int) +
-                           3 * (size_t)OT * sizeof(int) + 64;
+                           2 * (size_t)max_cell * nsp_o * sizeof(P4<float>) +
+                           (size_t)max_cell * s.nslot * sizeof(P4<float>) + (size_t)max_cell * sizeof(Cent<float>) +
+                           (size_t)max_cell * 3 * sizeof(int) + 3 * (size_t)OT * sizeof(int) + 64;
       int rc = ensure_dyn_smem((const void*)okern, (int)osmem);
       int per_sm = 0;
       if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, OT, osmem) != cudaSuccess)

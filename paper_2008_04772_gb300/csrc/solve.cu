@@ -601,9 +601,9 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 // ---------------------------------------------------------------------------
 // A6: BiCGStab on the real sparse Gram matrix for nsys complex systems that
-// share it (x, b: [nsys][n]); three kernels per iteration, scalars rebuilt in
-// every thread from float64 accumulators double-buffered by iteration parity.
-// acc layout per (parity, system): 0-1 r0^H v, 2-3 t^H s, 4 t^H t,
+// share it (x, b: [nsys][n]); three phases per iteration, scalars rebuilt in
+// every block from float64 accumulators double-buffered by iteration parity.
+// acc layout per (parity, bank, system): 0-1 r0^H v, 2-3 t^H s, 4 t^H t,
 // 5-6 r0^H r (next rho), 7 r^H r.
 // ---------------------------------------------------------------------------
 template <typename R>
@@ -615,13 +615,46 @@ struct BiArgs {
   int nsys;
   double neg;        // multiply the solution by this (M_P = -G^T)
   typename CT<R>::T *x, *r, *r0, *p0, *p1, *v0, *v1, *t;
-  double* acc;       // [2][nsys][8]
+  double* acc;       // [2][BI_BANKS][nsys][8]
   int* done;         // [nsys]
   double tol2;       // tol^2
   double* bnorm2;    // [nsys]
+  int lpr;           // lanes per (row, system)
+  GridBar* bar;      // barrier state of the cooperative launch
+  int* err;          // sticky: set when a barrier wait gave up
 };
 
-__device__ __forceinline__ double* ACC(double* acc, int nsys, int par, int s) { return acc + ((size_t)par * nsys + s) * 8; }
+// The per-system sums go to BI_BANKS copies (block b adds into bank b mod
+// BI_BANKS); readers add the banks in a fixed order. One bank measured best
+// on the 7680-unknown Gram systems: the reads of more banks sit on the
+// critical path of every phase, same-address atomics of a few hundred blocks
+// do not. Gathered columns are fetched BI_W at a time per lane.
+#ifndef BI_BANKS
+#define BI_BANKS 1
+#endif
+#ifndef BI_W
+#define BI_W 8
+#endif
+#ifndef BI_LPR
+#define BI_LPR 4
+#endif
+__device__ __forceinline__ double* ACC(double* acc, int nsys, int par, int bank, int s) {
+  return acc + (((size_t)par * BI_BANKS + bank) * nsys + s) * 8;
+}
+__device__ __forceinline__ void acc_read(double* acc, int nsys, int par, int s, double (&v)[8]) {
+#pragma unroll
+  for (int q = 0; q < 8; ++q) v[q] = 0.0;
+#pragma unroll
+  for (int b = 0; b < BI_BANKS; ++b) {
+    const double* a = ACC(acc, nsys, par, b, s);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] += a[q];
+  }
+}
+__device__ __forceinline__ void acc_zero(double* acc, int nsys, int par, int s, int q0, int q1) {
+  for (int b = 0; b < BI_BANKS; ++b)
+    for (int q = q0; q < q1; ++q) ACC(acc, nsys, par, b, s)[q] = 0.0;
+}
 
 __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
   const double d = br * br + bi * bi;
@@ -677,19 +710,32 @@ __device__ __forceinline__ void block_accumulate(double (&v)[NV], double* dst) {
 // Vectors are stored system-interleaved, element (i, s) at i * nsys + s, so
 // that the lanes of a warp (consecutive systems of one row, or consecutive
 // rows of few systems) read the entries of a gathered column contiguously and
-// load each matrix entry once. A block is nsys x rpb threads (rpb rows per
-// pass, grid-stride over rows); its first nsys threads form the per-system
-// scalars of the step once, in float64, from the sums of the previous step.
+// load each matrix entry once. A block is nsys x lpr x rpb threads: lpr lanes
+// share one (row, system) and split its gathered columns (their sums meet by
+// shuffles), rpb rows per pass, grid-stride over rows. The first nsys threads
+// of a block form the per-system scalars of the step once, in float64, from
+// the sums of the previous step.
 struct BiLayout {
-  int ns, rpb, s, r0;
-  __device__ BiLayout(int nsys) : ns(nsys), rpb(blockDim.x / nsys), s(threadIdx.x % nsys), r0(threadIdx.x / nsys) {}
-  __device__ int64_t first() const { return (int64_t)blockIdx.x * rpb + r0; }
+  int ns, lpr, rpb, s, sub, r0;
+  __device__ BiLayout(int nsys, int lanes)
+      : ns(nsys), lpr(lanes), rpb(blockDim.x / (nsys * lanes)), s(threadIdx.x % nsys),
+        sub((threadIdx.x / nsys) % lanes), r0(threadIdx.x / (nsys * lanes)) {}
+  // first row of this block's pass (uniform in the block) and the stride
+  __device__ int64_t base() const { return (int64_t)blockIdx.x * rpb; }
   __device__ int64_t step() const { return (int64_t)gridDim.x * rpb; }
 };
 
+// sum over the lpr lanes of one (row, system): lane bits [log2 ns, log2 ns +
+// log2 lpr) (ns and lpr powers of two with ns lpr dividing 32 whenever lpr > 1)
+template <typename R>
+__device__ __forceinline__ R lane_group_sum(const BiLayout& L, R v) {
+  for (int o = L.ns; o < L.ns * L.lpr; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // per-system sums of the block's partials (NV per thread), added to dst(s)
 // (nsys dividing 32: lanes of one system are nsys apart in a warp, summed by
-// shuffles first; otherwise each system's rpb partials are summed directly)
+// shuffles first; otherwise each system's partials are summed directly)
 template <int NV>
 __device__ __forceinline__ void system_sums(const BiLayout& L, double (&v)[NV], double* red) {
   const int ns = L.ns, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -712,11 +758,12 @@ __device__ __forceinline__ void system_sums(const BiLayout& L, double (&v)[NV], 
 #pragma unroll
     for (int q = 0; q < NV; ++q) red[q * blockDim.x + threadIdx.x] = v[q];
     __syncthreads();
+    const int groups = blockDim.x / ns;
     if (threadIdx.x < ns)
 #pragma unroll
       for (int q = 0; q < NV; ++q) {
         double a = 0.0;
-        for (int r = 0; r < L.rpb; ++r) a += red[q * blockDim.x + r * ns + threadIdx.x];
+        for (int r = 0; r < groups; ++r) a += red[q * blockDim.x + r * ns + threadIdx.x];
         v[q] = a;
       }
   }
@@ -732,17 +779,17 @@ __device__ __forceinline__ void system_accumulate(const BiLayout& L, const doubl
   if (threadIdx.x < L.ns)
 #pragma unroll
     for (int q = 0; q < NV; ++q)
-      if (w[q] != 0.0) atomicAdd(ACC(acc, nsys, par, threadIdx.x) + off + q, w[q]);
+      if (w[q] != 0.0) atomicAdd(ACC(acc, nsys, par, blockIdx.x % BI_BANKS, threadIdx.x) + off + q, w[q]);
 }
 
 template <typename R>
-__global__ void bicg_init(BiArgs<R> A, const typename CT<R>::T* __restrict__ b) {
+__device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typename CT<R>::T* __restrict__ b,
+                                                double* red) {
   // x = 0, r = r0 = b, p = v = 0; rho_0 = b^H b stored as "next rho" of parity 1
-  extern __shared__ double red[];
-  const BiLayout L(A.nsys);
+  const BiLayout L(A.nsys, A.lpr);
   double part[1] = {0.0};
-  if (L.r0 < L.rpb)
-    for (int64_t i = L.first(); i < A.n; i += L.step()) {
+  if (L.sub == 0)
+    for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
       const int64_t k = i * L.ns + L.s;
       const auto bv = b[(int64_t)L.s * A.n + i];
       A.x[k] = {0, 0};
@@ -756,27 +803,27 @@ __global__ void bicg_init(BiArgs<R> A, const typename CT<R>::T* __restrict__ b) 
 }
 
 template <typename R>
-__global__ void bicg_init2(BiArgs<R> A) {
+__device__ __forceinline__ void bicg_phase_init2(const BiArgs<R>& A) {
   const int s = threadIdx.x;
   if (s >= A.nsys) return;
-  for (int par = 0; par < 2; ++par)
-    for (int q = 0; q < 8; ++q) ACC(A.acc, A.nsys, par, s)[q] = 0.0;
-  ACC(A.acc, A.nsys, 1, s)[5] = A.bnorm2[s];
-  ACC(A.acc, A.nsys, 1, s)[7] = A.bnorm2[s];
+  for (int par = 0; par < 2; ++par) acc_zero(A.acc, A.nsys, par, s, 0, 8);
+  ACC(A.acc, A.nsys, 1, 0, s)[5] = A.bnorm2[s];
+  ACC(A.acc, A.nsys, 1, 0, s)[7] = A.bnorm2[s];
   A.done[s] = A.bnorm2[s] == 0.0;
 }
 
-// K1: p_k = r_k + beta (p_{k-1} - omega_{k-1} v_{k-1});  v_k = G p_k;  acc r0^H v
+// K1: p_k = r_k + beta (p_{k-1} - omega_{k-1} v_{k-1});  v_k = G p_k;  acc r0^H v.
+// Returns false (in every block alike) when no system is active any more.
 template <typename R>
-__global__ void bicg_k1(BiArgs<R> A, int k) {
-  extern __shared__ double red[];            // [3][blockDim] partials, then [nsys][5] scalars
-  double* sc = red + 3 * blockDim.x;
-  const BiLayout L(A.nsys);
+__device__ __forceinline__ bool bicg_phase_k1(const BiArgs<R>& A, int k, double* red) {
+  double* sc = red + 3 * blockDim.x;         // after [3][blockDim] partials: [nsys][5] scalars
+  const BiLayout L(A.nsys, A.lpr);
   const int P = k & 1;
   if (threadIdx.x < L.ns) {
     const int s = threadIdx.x;
-    double* a = ACC(A.acc, A.nsys, P, s);
-    double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+    double a[8], ap[8];
+    acc_read(A.acc, A.nsys, P, s, a);
+    acc_read(A.acc, A.nsys, P ^ 1, s, ap);
     bool act = !A.done[s];
     // convergence of r_k: r^H r from the previous K3 (or b^H b)
     if (act && ap[7] <= A.tol2 * A.bnorm2[s]) {
@@ -799,8 +846,11 @@ __global__ void bicg_k1(BiArgs<R> A, int k) {
     sc[5 * s + 1] = br; sc[5 * s + 2] = bi; sc[5 * s + 3] = omr; sc[5 * s + 4] = omi;
   }
   __syncthreads();
+  bool any = false;
+  for (int q = 0; q < L.ns; ++q) any |= sc[5 * q] != 0.0;
+  if (!any) return false;
   const int s = L.s;
-  const bool act = L.r0 < L.rpb && sc[5 * s] != 0.0;
+  const bool act = sc[5 * s] != 0.0;
   // vector arithmetic in the storage precision (float32 on the FP32 path: the
   // FP64 pipe is a small fraction of FP32 here); the dot products in float64
   const R bR = (R)sc[5 * s + 1], bI = (R)sc[5 * s + 2], oR = (R)sc[5 * s + 3], oI = (R)sc[5 * s + 4];
@@ -816,37 +866,58 @@ __global__ void bicg_k1(BiArgs<R> A, int k) {
     return typename CT<R>::T{rj.x + bR * dx - bI * dy, rj.y + bR * dy + bI * dx};
   };
   double part[2] = {0.0, 0.0};
-  if (act)
-    for (int64_t i = L.first(); i < A.n; i += L.step()) {
-      pcur[i * ns + s] = pj(i);
-      R vr = 0, vi = 0;
-      for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-        const auto pc = pj(A.col[q]);
-        const R g = A.val[q];
-        vr += g * pc.x;
-        vi += g * pc.y;
+  // the pass loop is uniform in the block (shuffles inside)
+  for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
+    const int64_t i = i0 + L.r0;
+    const bool live = act && i < A.n;
+    R vr = 0, vi = 0;
+    if (live) {
+      const int64_t q1 = A.rowptr[i + 1];
+      for (int64_t qb = A.rowptr[i] + L.sub; qb < q1; qb += (int64_t)BI_W * L.lpr) {
+        int cj[BI_W];
+        R gv[BI_W];
+#pragma unroll
+        for (int u = 0; u < BI_W; ++u) {
+          const int64_t q = qb + (int64_t)u * L.lpr;
+          cj[u] = q < q1 ? A.col[q] : -1;
+          gv[u] = q < q1 ? A.val[q] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < BI_W; ++u)
+          if (cj[u] >= 0) {
+            const auto pc = pj(cj[u]);
+            vr += gv[u] * pc.x;
+            vi += gv[u] * pc.y;
+          }
       }
+    }
+    vr = lane_group_sum(L, vr);
+    vi = lane_group_sum(L, vi);
+    if (live && L.sub == 0) {
+      pcur[i * ns + s] = pj(i);
       vcur[i * ns + s] = {vr, vi};
       const auto rh = A.r0[i * ns + s];
       part[0] += (double)(rh.x * vr + rh.y * vi);   // conj(r0) v
       part[1] += (double)(rh.x * vi - rh.y * vr);
     }
+  }
   system_accumulate<2>(L, part, red, A.acc, A.nsys, P, 0);
+  return true;
 }
 
 // K2: alpha = rho_k / (r0^H v_k); s = r - alpha v; t = G s; acc t^H s, t^H t
 template <typename R>
-__global__ void bicg_k2(BiArgs<R> A, int k) {
-  extern __shared__ double red[];
+__device__ __forceinline__ void bicg_phase_k2(const BiArgs<R>& A, int k, double* red) {
   double* sc = red + 3 * blockDim.x;         // [nsys][3]: active, alpha (re, im)
-  const BiLayout L(A.nsys);
+  const BiLayout L(A.nsys, A.lpr);
   const int P = k & 1;
   if (threadIdx.x < L.ns) {
     const int s = threadIdx.x;
-    double* a = ACC(A.acc, A.nsys, P, s);
-    double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+    double a[8], ap[8];
+    acc_read(A.acc, A.nsys, P, s, a);
+    acc_read(A.acc, A.nsys, P ^ 1, s, ap);
     bool act = !A.done[s];
-    if (act && blockIdx.x == 0) { a[5] = a[6] = a[7] = 0.0; }
+    if (act && blockIdx.x == 0) acc_zero(A.acc, A.nsys, P, s, 5, 8);
     if (a[0] == 0.0 && a[1] == 0.0) act = false;
     double alr = 0.0, ali = 0.0;
     if (act) cdiv_r<R>(ap[5], ap[6], a[0], a[1], alr, ali);
@@ -856,7 +927,7 @@ __global__ void bicg_k2(BiArgs<R> A, int k) {
   }
   __syncthreads();
   const int s = L.s, ns = L.ns;
-  const bool act = L.r0 < L.rpb && sc[3 * s] != 0.0;
+  const bool act = sc[3 * s] != 0.0;
   const R aR = (R)sc[3 * s + 1], aI = (R)sc[3 * s + 2];
   const auto* vcur = P ? A.v1 : A.v0;
   auto sj = [&](int64_t j) {
@@ -865,39 +936,56 @@ __global__ void bicg_k2(BiArgs<R> A, int k) {
     return typename CT<R>::T{rj.x - (aR * vv.x - aI * vv.y), rj.y - (aR * vv.y + aI * vv.x)};
   };
   double part[3] = {0, 0, 0};
-  if (act)
-    for (int64_t i = L.first(); i < A.n; i += L.step()) {
-      R tr = 0, ti = 0;
-      for (int64_t q = A.rowptr[i]; q < A.rowptr[i + 1]; ++q) {
-        const auto sc2 = sj(A.col[q]);
-        const R g = A.val[q];
-        tr += g * sc2.x;
-        ti += g * sc2.y;
+  for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
+    const int64_t i = i0 + L.r0;
+    const bool live = act && i < A.n;
+    R tr = 0, ti = 0;
+    if (live) {
+      const int64_t q1 = A.rowptr[i + 1];
+      for (int64_t qb = A.rowptr[i] + L.sub; qb < q1; qb += (int64_t)BI_W * L.lpr) {
+        int cj[BI_W];
+        R gv[BI_W];
+#pragma unroll
+        for (int u = 0; u < BI_W; ++u) {
+          const int64_t q = qb + (int64_t)u * L.lpr;
+          cj[u] = q < q1 ? A.col[q] : -1;
+          gv[u] = q < q1 ? A.val[q] : R(0);
+        }
+#pragma unroll
+        for (int u = 0; u < BI_W; ++u)
+          if (cj[u] >= 0) {
+            const auto sc2 = sj(cj[u]);
+            tr += gv[u] * sc2.x;
+            ti += gv[u] * sc2.y;
+          }
       }
+    }
+    tr = lane_group_sum(L, tr);
+    ti = lane_group_sum(L, ti);
+    if (live && L.sub == 0) {
       A.t[i * ns + s] = {tr, ti};
       const auto si = sj(i);
       part[0] += (double)(tr * si.x + ti * si.y);   // conj(t) s
       part[1] += (double)(tr * si.y - ti * si.x);
       part[2] += (double)(tr * tr + ti * ti);
     }
+  }
   system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 2);
 }
 
 // K3: omega = t^H s / t^H t; x += alpha p + omega s; r = s - omega t; acc rho, r^H r
 template <typename R>
-__global__ void bicg_k3(BiArgs<R> A, int k) {
-  extern __shared__ double red[];
+__device__ __forceinline__ void bicg_phase_k3(const BiArgs<R>& A, int k, double* red) {
   double* sc = red + 3 * blockDim.x;         // [nsys][5]: active, alpha, omega
-  const BiLayout L(A.nsys);
+  const BiLayout L(A.nsys, A.lpr);
   const int P = k & 1;
   if (threadIdx.x < L.ns) {
     const int s = threadIdx.x;
-    double* a = ACC(A.acc, A.nsys, P, s);
-    double* ap = ACC(A.acc, A.nsys, P ^ 1, s);
+    double a[8], ap[8];
+    acc_read(A.acc, A.nsys, P, s, a);
+    acc_read(A.acc, A.nsys, P ^ 1, s, ap);
     bool act = !A.done[s];
-    if (act && blockIdx.x == 0) {
-      for (int q = 0; q < 5; ++q) ap[q] = 0.0;   // parity P^1 is free for iteration k+1
-    }
+    if (act && blockIdx.x == 0) acc_zero(A.acc, A.nsys, P ^ 1, s, 0, 5);  // parity P^1 is free for iteration k+1
     if (act && ((a[0] == 0.0 && a[1] == 0.0) || a[4] == 0.0)) {
       act = false;
       if (blockIdx.x == 0) A.done[s] = 1;
@@ -912,13 +1000,13 @@ __global__ void bicg_k3(BiArgs<R> A, int k) {
   }
   __syncthreads();
   const int s = L.s, ns = L.ns;
-  const bool act = L.r0 < L.rpb && sc[5 * s] != 0.0;
+  const bool act = L.sub == 0 && sc[5 * s] != 0.0;
   const R aR = (R)sc[5 * s + 1], aI = (R)sc[5 * s + 2], oR = (R)sc[5 * s + 3], oI = (R)sc[5 * s + 4];
   const auto* pcur = P ? A.p1 : A.p0;
   const auto* vcur = P ? A.v1 : A.v0;
   double part[3] = {0, 0, 0};
   if (act)
-    for (int64_t i = L.first(); i < A.n; i += L.step()) {
+    for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
       const int64_t kk = i * ns + s;
       const auto vv = vcur[kk], ri = A.r[kk], pp = pcur[kk], tt = A.t[kk];
       const R sx = ri.x - (aR * vv.x - aI * vv.y), sy = ri.y - (aR * vv.y + aI * vv.x);
@@ -936,10 +1024,10 @@ __global__ void bicg_k3(BiArgs<R> A, int k) {
 }
 
 template <typename R>
-__global__ void bicg_finish(BiArgs<R> A, typename CT<R>::T* __restrict__ out) {
-  const BiLayout L(A.nsys);
-  if (L.r0 >= L.rpb) return;
-  for (int64_t i = L.first(); i < A.n; i += L.step()) {
+__device__ __forceinline__ void bicg_phase_finish(const BiArgs<R>& A, typename CT<R>::T* __restrict__ out) {
+  const BiLayout L(A.nsys, A.lpr);
+  if (L.sub != 0) return;
+  for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
     const auto v = A.x[i * L.ns + L.s];
     out[(size_t)L.s * A.n + i] = {(R)(A.neg * v.x), (R)(A.neg * v.y)};
   }
@@ -949,6 +1037,105 @@ template <typename R>
 __global__ void real_convert_kernel(const double* __restrict__ a, R* __restrict__ b, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (R)a[i];
+}
+
+// Grid-wide barrier of a cooperative launch (every block resident). Thread 0
+// of each block arrives on a counter; the last arrival resets it and moves the
+// generation on. Every wait is bounded: after GRID_BAR_SPINS polls the block
+// raises the error word (and the solver's sticky error), and every block
+// leaves at its next barrier.
+constexpr long long GRID_BAR_SPINS = 1LL << 22;
+
+__device__ __forceinline__ bool grid_sync(GridBar* gb, int* sticky, unsigned& gen) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned want = gen + 1;
+    __threadfence();
+    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
+      atomicExch(&gb->count, 0u);
+      __threadfence();
+      atomicExch(&gb->gen, want);
+    } else {
+      const volatile unsigned* g = &gb->gen;
+      const volatile int* e = &gb->err;
+      long long spins = 0;
+      while (*g != want) {
+        if (*e || ++spins > GRID_BAR_SPINS) {
+          atomicExch(&gb->err, 1);
+          atomicExch(sticky, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(32);
+      }
+    }
+    __threadfence();
+    if (*(const volatile int*)&gb->err) ok = 0;
+    s_ok = ok;
+  }
+  __syncthreads();
+  ++gen;
+  return s_ok != 0;
+}
+
+// A6, the whole BiCGStab solve in one cooperative launch: the phases of the
+// iteration (init, K1, K2, K3) separated by grid barriers instead of kernel
+// boundaries, and the loop left as soon as every system has converged.
+template <typename R>
+__global__ void __launch_bounds__(256) bicg_persistent(BiArgs<R> A, const typename CT<R>::T* __restrict__ b,
+                                                       typename CT<R>::T* __restrict__ out, int maxit) {
+  extern __shared__ double red[];
+  unsigned gen = 0;
+  bicg_phase_init<R>(A, b, red);
+  if (!grid_sync(A.bar, A.err, gen)) return;
+  if (blockIdx.x == 0) bicg_phase_init2<R>(A);
+  if (!grid_sync(A.bar, A.err, gen)) return;
+  for (int k = 0; k < maxit; ++k) {
+    if (!bicg_phase_k1<R>(A, k, red)) break;
+    if (!grid_sync(A.bar, A.err, gen)) return;
+    bicg_phase_k2<R>(A, k, red);
+    if (!grid_sync(A.bar, A.err, gen)) return;
+    bicg_phase_k3<R>(A, k, red);
+    if (!grid_sync(A.bar, A.err, gen)) return;
+  }
+  // x rows are this thread's own (same layout in K3 and here): no barrier
+  bicg_phase_finish<R>(A, out);
+}
+
+// Check of the bounded barrier: 4 blocks pass 3 barriers; block skip_block
+// (if in range) leaves at once, so the others give up after their bounded
+// wait. *status: 0 when every block passed every barrier, 1 when a wait gave up.
+__global__ void grid_barrier_check_kernel(GridBar* gb, int* sticky, int skip_block, int* passed) {
+  if ((int)blockIdx.x == skip_block) return;
+  unsigned gen = 0;
+  for (int i = 0; i < 3; ++i)
+    if (!grid_sync(gb, sticky, gen)) return;
+  if (threadIdx.x == 0) atomicAdd(passed, 1);
+}
+
+int grid_barrier_check(int skip_block, int* status, cudaStream_t st) {
+  constexpr unsigned nb = 4;
+  int* buf = nullptr;  // GridBar (4 ints), sticky, passed
+  CAL_TRY_CUDA(dalloc((void**)&buf, 8 * sizeof(int), st));
+  CAL_TRY_CUDA(cudaMemsetAsync(buf, 0, 8 * sizeof(int), st));
+  GridBar* gb = reinterpret_cast<GridBar*>(buf);
+  int* sticky = buf + 4;
+  int* passed = buf + 5;
+  void* args[] = {(void*)&gb, (void*)&sticky, (void*)&skip_block, (void*)&passed};
+  const cudaError_t e =
+      cudaLaunchCooperativeKernel((const void*)grid_barrier_check_kernel, dim3(nb), dim3(64), args, 0, st);
+  note_launch();
+  int h[2] = {0, 0};
+  if (e == cudaSuccess) CAL_TRY_CUDA(cudaMemcpyAsync(h, sticky, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  dfree(buf, st);
+  if (e != cudaSuccess) return fail(CAL_ECUDA, "barrier check launch: %s", cudaGetErrorString(e));
+  const unsigned expect = (skip_block >= 0 && skip_block < (int)nb) ? 0u : nb;
+  *status = h[0] ? 1 : 0;
+  if (!h[0] && (unsigned)h[1] != expect) return fail(CAL_ECUDA, "barrier check: %d blocks passed", h[1]);
+  return CAL_OK;
 }
 
 template <typename R>
@@ -961,6 +1148,7 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
   maxit = maxit_;
   d_rowptr = rowptr;
   d_col = col;
+  if (nsys < 1 || nsys > 256) return fail(CAL_EINVAL, "Gram solve: %d systems (1..256)", nsys);
   const size_t vb = (size_t)n * nsys * sizeof(C);
   CAL_TRY_CUDA(dalloc((void**)&d_val, nnz * sizeof(R), st));
   if (nnz > 0) {
@@ -969,21 +1157,44 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
     CAL_TRY_CUDA(cudaGetLastError());
   }
   CAL_TRY_CUDA(dalloc((void**)&d_work, 8 * vb, st));
-  CAL_TRY_CUDA(dalloc((void**)&d_acc, (2 * nsys * 8 + nsys) * sizeof(double), st));
+  // per solve: [2][BI_BANKS][nsys][8] sums, [nsys] |b|^2, then the barrier state
+  CAL_TRY_CUDA(dalloc((void**)&d_acc, acc_bytes(), st));
   CAL_TRY_CUDA(dalloc((void**)&d_done, nsys * sizeof(int), st));
+  CAL_TRY_CUDA(dalloc((void**)&d_err, sizeof(int), st));
+  CAL_TRY_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  // nsys x rpb threads per block, rows grid-strided over as many blocks as
+  // can be resident at once (the cooperative launch requires all of them)
+  // lanes per (row, system): several for few systems (their gathers split a
+  // row's columns), one when the systems alone fill the warps
+  const bool pow2 = (nsys & (nsys - 1)) == 0;
+  lpr = (pow2 && nsys <= 16) ? std::min(BI_LPR, 32 / nsys) : 1;
+  rpb = std::max(1, 256 / (nsys * lpr));
+  threads = nsys * lpr * rpb;
+  smem = (3 * (size_t)threads + 5 * (size_t)nsys) * sizeof(double);
+  int dev = 0, n_sm = 0, per_sm = 0;
+  CAL_TRY_CUDA(cudaGetDevice(&dev));
+  CAL_TRY_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
+  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicg_persistent<R>, threads, smem));
+  if (per_sm < 1) return fail(CAL_ECUDA, "Gram solve: the persistent kernel does not fit on an SM");
+  const int64_t row_blocks = (n + rpb - 1) / rpb;
+  grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(row_blocks, (int64_t)n_sm * std::min(per_sm, 8)));
   return CAL_OK;
 }
 
 template <typename R>
 GramSolver<R>::~GramSolver() {
-  if (graph_exec) cudaGraphExecDestroy(graph_exec);
   // every solve has completed when the solver is destroyed: release on the legacy stream
-  for (void* p : {(void*)d_in, (void*)d_out, (void*)d_val, (void*)d_work, (void*)d_acc, (void*)d_done})
-    dfree(p, nullptr);
+  for (void* p : {(void*)d_val, (void*)d_work, (void*)d_acc, (void*)d_done, (void*)d_err}) dfree(p, nullptr);
 }
 
 template <typename R>
-int GramSolver<R>::enqueue(const C* b, C* out, cudaStream_t st) {
+size_t GramSolver<R>::acc_bytes() const {
+  return (2 * (size_t)BI_BANKS * nsys * 8 + nsys) * sizeof(double) + sizeof(GridBar);
+}
+
+// One solve: clear the sums and the barrier, one cooperative launch.
+template <typename R>
+int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   BiArgs<R> A;
   A.rowptr = d_rowptr;
   A.col = d_col;
@@ -995,60 +1206,30 @@ int GramSolver<R>::enqueue(const C* b, C* out, cudaStream_t st) {
   A.x = d_work; A.r = d_work + nv; A.r0 = d_work + 2 * nv; A.p0 = d_work + 3 * nv;
   A.p1 = d_work + 4 * nv; A.v0 = d_work + 5 * nv; A.v1 = d_work + 6 * nv; A.t = d_work + 7 * nv;
   A.acc = d_acc;
-  A.bnorm2 = d_acc + 2 * nsys * 8;
+  A.bnorm2 = d_acc + 2 * BI_BANKS * nsys * 8;
+  A.bar = reinterpret_cast<GridBar*>(d_acc + 2 * BI_BANKS * nsys * 8 + nsys);
+  A.err = d_err;
   A.done = d_done;
   A.tol2 = tol * tol;
-  if (nsys < 1 || nsys > 256) return fail(CAL_EINVAL, "Gram solve: %d systems (1..256)", nsys);
-  // nsys x rpb threads per block, rows grid-strided over a few blocks per SM
-  const int rpb = std::max(1, 256 / nsys);
-  const int threads = nsys * rpb;
-  const int64_t row_blocks = (n + rpb - 1) / rpb;
-  int n_sm = 148;
-  {
-    int dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  }
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(row_blocks, (int64_t)n_sm * 8));
-  const size_t smem = (3 * (size_t)threads + 5 * (size_t)nsys) * sizeof(double);
-  CAL_TRY_CUDA(cudaMemsetAsync(A.bnorm2, 0, nsys * sizeof(double), st));
-  bicg_init<R><<<grid, threads, smem, st>>>(A, b);
-  bicg_init2<R><<<1, 32 * ((nsys + 31) / 32), 0, st>>>(A);
-  for (int k = 0; k < maxit; ++k) {
-    bicg_k1<R><<<grid, threads, smem, st>>>(A, k);
-    bicg_k2<R><<<grid, threads, smem, st>>>(A, k);
-    bicg_k3<R><<<grid, threads, smem, st>>>(A, k);
-  }
-  bicg_finish<R><<<grid, threads, 0, st>>>(A, out);
-  CAL_TRY_CUDA(cudaGetLastError());
+  A.lpr = lpr;
+  const int tok = prof_begin(st, "bicgstab", 0.0);
+  CAL_TRY_CUDA(cudaMemsetAsync(d_acc, 0, acc_bytes(), st));
+  int mi = maxit;
+  void* args[] = {(void*)&A, (void*)&b, (void*)&out, (void*)&mi};
+  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)bicg_persistent<R>, dim3(grid), dim3(threads), args,
+                                                    smem, st);
+  prof_end(st, tok);
+  note_launch();
+  if (e != cudaSuccess) return fail(CAL_ECUDA, "Gram solve launch: %s", cudaGetErrorString(e));
   return CAL_OK;
 }
 
-// The iteration sequence is captured once into a CUDA graph over fixed
-// input/output buffers; each solve copies in, replays it and copies out, so a
-// Gram solve costs one graph launch instead of 3 + 3 maxit kernel launches.
-// Systems that have converged turn the remaining iterations into no-ops.
 template <typename R>
-int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
-  const size_t vb = (size_t)n * nsys * sizeof(C);
-  if (!graph_exec) {
-    CAL_TRY_CUDA(dalloc((void**)&d_in, vb, st));
-    CAL_TRY_CUDA(dalloc((void**)&d_out, vb, st));
-    cudaGraph_t g;
-    CAL_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    const int rc = enqueue(d_in, d_out, st);
-    const cudaError_t e = cudaStreamEndCapture(st, &g);
-    if (rc) return rc;
-    if (e != cudaSuccess) return fail(CAL_ECUDA, "Gram solve capture: %s", cudaGetErrorString(e));
-    const cudaError_t ei = cudaGraphInstantiate(&graph_exec, g, 0);
-    cudaGraphDestroy(g);
-    if (ei != cudaSuccess) return fail(CAL_ECUDA, "Gram solve instantiate: %s", cudaGetErrorString(ei));
-  }
-  const int tok = prof_begin(st, "bicgstab", 0.0);
-  CAL_TRY_CUDA(cudaMemcpyAsync(d_in, b, vb, cudaMemcpyDeviceToDevice, st));
-  CAL_TRY_CUDA(cudaGraphLaunch(graph_exec, st));
-  CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, vb, cudaMemcpyDeviceToDevice, st));
-  prof_end(st, tok);
-  note_launch(3 + 3 * maxit);
+int GramSolver<R>::check(cudaStream_t st) const {
+  int h = 0;
+  CAL_TRY_CUDA(cudaMemcpyAsync(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  if (h) return fail(CAL_ETIMEOUT, "Gram solve: a bounded grid barrier gave up");
   return CAL_OK;
 }
 

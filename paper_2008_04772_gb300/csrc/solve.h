@@ -45,7 +45,16 @@ int zero_vec(void* y, int prec, int64_t n, cudaStream_t st);
 int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale, cudaStream_t st);
 int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st);
 
+// check of the bounded grid barrier (see cal_check_grid_barrier)
+int grid_barrier_check(int skip_block, int* status, cudaStream_t st);
+
 // BiCGStab on the real sparse Gram matrix, nsys complex systems sharing it
+// grid-wide barrier state of a cooperative launch (zeroed before the launch)
+struct GridBar {
+  unsigned count, gen;
+  int err, pad;
+};
+
 template <typename R>
 struct GramSolver {
   using C = typename std::conditional<sizeof(R) == 4, float2, double2>::type;
@@ -57,15 +66,19 @@ struct GramSolver {
   double neg = 1.0, tol = 1e-10;
   int maxit = 30;
   C* d_work = nullptr;
-  C* d_in = nullptr;
-  C* d_out = nullptr;
-  double* d_acc = nullptr;
+  double* d_acc = nullptr;   // per-solve sums, |b|^2 and the grid barrier state
   int* d_done = nullptr;
-  cudaGraphExec_t graph_exec = nullptr;
-  int enqueue(const C* b, C* out, cudaStream_t st);
+  int* d_err = nullptr;      // sticky: a bounded barrier wait gave up
+  int lpr = 1, rpb = 1, threads = 0;
+  unsigned grid = 0;
+  size_t smem = 0;
   int init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n, int nsys,
            int64_t nnz, double neg, double tol, int maxit, cudaStream_t st);
+  // x = neg G^{-1} b for the nsys systems (b, out: [nsys][n]), one cooperative launch
   int solve(const C* b, C* out, cudaStream_t st);
+  // CAL_ETIMEOUT if any solve since init gave up at a barrier (synchronises st)
+  int check(cudaStream_t st) const;
+  size_t acc_bytes() const;
   ~GramSolver();
 };
 

@@ -183,3 +183,15 @@ def test_errors_are_reported_not_faulted(ctx):
     assert sol.rc == cal.ENOTCONV and sol.info().converged == 0 and sol.info().iterations == 2
     # the context stays usable after every error
     assert cal.pmchwt_solve(ctx, gm, 2.0, EPS, INC).info().converged == 1
+
+
+def test_grid_barrier_wait_is_bounded(ctx):
+    """The Gram solver's cooperative kernel meets at a bounded grid barrier.
+    With every block present the check passes; with one block leaving before
+    the first barrier (an arrival that never comes) the others give up after
+    their bounded wait, report it, and the context stays usable."""
+    assert ctx.check_grid_barrier(-1) == 0
+    assert ctx.check_grid_barrier(2) == 1
+    assert ctx.check_grid_barrier(-1) == 0
+    gm = gmesh(ctx, "sphere1")
+    assert cal.pmchwt_solve(ctx, gm, 2.0, EPS, INC).info().converged == 1
