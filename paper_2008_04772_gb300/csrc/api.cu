@@ -14,6 +14,8 @@
 #include <cstring>
 #include <memory>
 #include <numeric>
+#include <string>
+#include <thread>
 #include <vector>
 
 #include "internal.h"
@@ -1035,11 +1037,34 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   }
   cudaStream_t st = ctx->impl.stream;
   int rc;
-  // spaces: the RWG space now; the BC space is built on the host while the
-  // device assembles A (the launches below are asynchronous)
+  // spaces: the BC space is built by a host thread while this thread builds
+  // the RWG space and enqueues A's assembly (the launches are asynchronous);
+  // both only read the mesh
+  const bool need_bc = o.precond != CAL_PRECOND_NONE;
+  struct BcBuild {
+    std::thread th;
+    int rc = CAL_OK;
+    std::string msg;
+    double seconds = 0.0;
+    ~BcBuild() { if (th.joinable()) th.join(); }
+    int join() {
+      if (th.joinable()) th.join();
+      return rc ? fail(rc, "%s", msg.c_str()) : CAL_OK;
+    }
+  } bcb;
+  if (need_bc) {
+    P.bc = std::make_shared<Space>();
+    Space* bcs = P.bc.get();
+    Mesh* mh = &mesh->impl;
+    bcb.th = std::thread([&bcb, bcs, mh]() {
+      const double tb = now();
+      bcb.rc = build_bc(*bcs, *mh);
+      if (bcb.rc) bcb.msg = last_error();
+      bcb.seconds = now() - tb;
+    });
+  }
   P.rwg = std::make_shared<Space>();
   if ((rc = build_rwg(*P.rwg, mesh->impl)) || (rc = upload_space(*P.rwg, st))) return rc;
-  const bool need_bc = o.precond != CAL_PRECOND_NONE;
   double t_setup_host = now() - t_start;
   // device phase times from events on the stream (the host does not wait in between)
   struct Ev {
@@ -1075,9 +1100,8 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   CAL_TRY_CUDA(cudaEventRecord(ev.e[1], st));
   if (need_bc) {
     const double tb = now();
-    P.bc = std::make_shared<Space>();
-    if ((rc = build_bc(*P.bc, mesh->impl)) || (rc = upload_space(*P.bc, st))) return rc;
-    t_setup_host += now() - tb;
+    if ((rc = bcb.join()) || (rc = upload_space(*P.bc, st))) return rc;
+    t_setup_host += now() - tb;  // the part of the BC build A's enqueue did not hide
   }
   CAL_TRY_CUDA(cudaEventRecord(ev.e[2], st));
   int64_t bytes_A = 0, bytes_P = 0, bytes_G = 0;

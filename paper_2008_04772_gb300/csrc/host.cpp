@@ -512,6 +512,9 @@ int build_bc(Space& s, Mesh& m) {
   return CAL_OK;
 }
 
+// Touching triangle pairs per scatterer. Triangles are split into contiguous
+// ranges over a few host threads; each range lists its pairs in (t, u) order
+// and the ranges are concatenated, so the list is the same for any thread count.
 void build_singular_pairs(Space& s) {
   const Mesh& m = *s.mesh;
   s.sing.assign(m.M, {});
@@ -529,59 +532,74 @@ void build_singular_pairs(Space& s) {
     for (int64_t t = 0; t < s.ntri; ++t)
       for (int a = 0; a < 3; ++a) vtri[fill[s.triD[t].vid[a]]++] = (int)t;
   }
-  std::vector<int> stamp(s.ntri, -1), nb;
   for (int64_t d = 0; d < m.M; ++d) {
     const int64_t t0 = s.tri_off[d], t1 = s.tri_off[d + 1];
-    auto& out = s.sing[d];
-    for (int64_t t = t0; t < t1; ++t) {
-      nb.clear();
-      const int* i1 = s.triD[t].vid;
-      for (int a = 0; a < 3; ++a)
-        for (int q = vptr[i1[a]]; q < vptr[i1[a] + 1]; ++q) {
-          const int u = vtri[q];
-          if (stamp[u] != (int)t) {
-            stamp[u] = (int)t;
-            nb.push_back(u);
+    const int nth = (int)std::max<int64_t>(
+        1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(), (t1 - t0) / 4096}));
+    std::vector<std::vector<SingPair>> part(nth);
+    auto work = [&](int w) {
+      const int64_t a0 = t0 + (t1 - t0) * w / nth, a1 = t0 + (t1 - t0) * (w + 1) / nth;
+      auto& out = part[w];
+      std::vector<int> stamp(s.ntri, -1), nb;
+      for (int64_t t = a0; t < a1; ++t) {
+        nb.clear();
+        const int* i1 = s.triD[t].vid;
+        for (int a = 0; a < 3; ++a)
+          for (int q = vptr[i1[a]]; q < vptr[i1[a] + 1]; ++q) {
+            const int u = vtri[q];
+            if (stamp[u] != (int)t) {
+              stamp[u] = (int)t;
+              nb.push_back(u);
+            }
           }
+        std::sort(nb.begin(), nb.end());
+        for (int u : nb) {
+          if (u < t0 || u >= t1) continue;  // touching triangles of one scatterer only
+          const int* i2 = s.triD[u].vid;
+          int shared = 0;
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) shared += i1[a] == i2[b];
+          // vertex-sharing pairs: keep one order, the kernel adds the transpose
+          if (shared == 1 && u < t) continue;
+          SingPair p{};
+          p.t1 = (int)t;
+          p.t2 = u;
+          int ns = 0;
+          int sh1[3], sh2[3];
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+              if (i1[a] == i2[b]) { sh1[ns] = a; sh2[ns] = b; ++ns; }
+          p.cls = (signed char)ns;
+          int n1 = 0, n2 = 0;
+          for (int q = 0; q < ns; ++q) { p.o1[n1++] = (signed char)sh1[q]; p.o2[n2++] = (signed char)sh2[q]; }
+          for (int a = 0; a < 3; ++a) {
+            bool u1 = false, u2 = false;
+            for (int q = 0; q < ns; ++q) { u1 |= sh1[q] == a; u2 |= sh2[q] == a; }
+            if (!u1) p.o1[n1++] = (signed char)a;
+            if (!u2) p.o2[n2++] = (signed char)a;
+          }
+          out.push_back(p);
         }
-      std::sort(nb.begin(), nb.end());
-      for (int u : nb) {
-        if (u < t0 || u >= t1) continue;  // touching triangles of one scatterer only
-        const int* i2 = s.triD[u].vid;
-        int shared = 0;
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b) shared += i1[a] == i2[b];
-        // vertex-sharing pairs: keep one order, the kernel adds the transpose
-        if (shared == 1 && u < t) continue;
-        SingPair p{};
-        p.t1 = (int)t;
-        p.t2 = u;
-        int ns = 0;
-        int sh1[3], sh2[3];
-        for (int a = 0; a < 3; ++a)
-          for (int b = 0; b < 3; ++b)
-            if (i1[a] == i2[b]) { sh1[ns] = a; sh2[ns] = b; ++ns; }
-        p.cls = (signed char)ns;
-        int n1 = 0, n2 = 0;
-        for (int q = 0; q < ns; ++q) { p.o1[n1++] = (signed char)sh1[q]; p.o2[n2++] = (signed char)sh2[q]; }
-        for (int a = 0; a < 3; ++a) {
-          bool u1 = false, u2 = false;
-          for (int q = 0; q < ns; ++q) { u1 |= sh1[q] == a; u2 |= sh2[q] == a; }
-          if (!u1) p.o1[n1++] = (signed char)a;
-          if (!u2) p.o2[n2++] = (signed char)a;
-        }
-        out.push_back(p);
       }
+    };
+    if (nth == 1) {
+      work(0);
+    } else {
+      std::vector<std::thread> th;
+      for (int w = 0; w < nth; ++w) th.emplace_back(work, w);
+      for (auto& x : th) x.join();
     }
     // grouped by class, costliest rules first: lanes of one warp then run the
     // same rule (the float32-output kernel takes one pair per lane)
     auto rank = [](const SingPair& q) { return q.cls == 2 ? 0 : (q.cls == 3 ? 1 : 2); };
     size_t cnt[4] = {0, 0, 0, 0};
-    for (const SingPair& q : out) ++cnt[rank(q) + 1];
+    for (const auto& pw : part)
+      for (const SingPair& q : pw) ++cnt[rank(q) + 1];
     for (int c = 0; c < 3; ++c) cnt[c + 1] += cnt[c];
-    std::vector<SingPair> sorted(out.size());
-    for (const SingPair& q : out) sorted[cnt[rank(q)]++] = q;
-    out.swap(sorted);
+    auto& out = s.sing[d];
+    out.resize(cnt[3]);
+    for (const auto& pw : part)
+      for (const SingPair& q : pw) out[cnt[rank(q)]++] = q;
   }
 }
 
