@@ -890,10 +890,11 @@ int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space*
   if (rc) return rc;
   CAL_TRY_CUDA(cudaStreamSynchronize(ctx->impl.stream));
   auto* o = new cal_op;
-  o->impl = std::move(*op);
+  o->impl = std::move(*op);  // a member-wise copy: the source gives up every device pointer
   op->d_S = op->d_C = nullptr;
   op->d_rowptr = nullptr;
   op->d_col = nullptr;
+  op->d_Sh = op->d_Sl = op->d_Ch = op->d_Cl = nullptr;
   *out = o;
   return CAL_OK;
 }
