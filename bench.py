@@ -44,7 +44,7 @@ Q = dict(q_regular_A=0, q_regular_P=0)
 METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one bc_tile launch (exterior pass of
 # the workload), from the ncu capture summarised in profiles/; None once the kernel changes
-BC_TILE_TRAFFIC = 3.537595e9 + 3.959544e9
+BC_TILE_TRAFFIC = None
 
 
 def _env_int(name, default):
@@ -285,7 +285,7 @@ def run_ours(args, rank, world):
                              "note": "singular pairs also in float32 (CAL_FP32_ALL)"},
         "gpu_launches": int(n_launch),
         "kernels_ms": {k: v["ms"] / args.steps for k, v in prof.items()},
-        "roofline": {"bound": "alu", "kernel": "bc_owner_kernel<0,128>",
+        "roofline": {"bound": "alu", "kernel": "bc_owner_kernel<0,128,true>",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak if peak else None, "traffic": BC_TILE_TRAFFIC,
                      "traffic_note": "dram read+write bytes of one exterior launch, one ncu capture "
