@@ -601,11 +601,18 @@ static inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t -
 
 // ---------------------------------------------------------------------------
 // A6: BiCGStab on the real sparse Gram matrix for nsys complex systems that
-// share it (x, b: [nsys][n]); three phases per iteration, scalars rebuilt in
-// every block from float64 accumulators double-buffered by iteration parity.
-// acc layout per (parity, bank, system): 0-1 r0^H v, 2-3 t^H s, 4 t^H t,
-// 5-6 r0^H r (next rho), 7 r^H r.
+// share it (x, b: [nsys][n]). Two phases per iteration k: K1 finishes step
+// k-1 (s = r - alpha v, r = s - omega t, x += alpha p + omega s, row by row)
+// and forms p_k and v_k = G p_k; K2 forms s_k and t_k = G s_k. rho_k comes
+// from the K2 sums by r0^H r_k = r0^H s - omega r0^H t, so no third pass over
+// the rows is needed. Float64 sums double-buffered by iteration parity; every
+// block rebuilds the step scalars from them and keeps rho, alpha, omega of
+// the previous step in shared memory (all blocks compute the same values).
+// acc layout per (parity, bank, system): 0-1 r0^H v_k, 2 |r_k|^2 (K1);
+// 3-4 t^H s, 5 t^H t, 6-7 r0^H s, 8-9 r0^H t (K2).
 // ---------------------------------------------------------------------------
+constexpr int BI_ACC = 10;
+
 template <typename R>
 struct BiArgs {
   const int64_t* rowptr;
@@ -614,9 +621,10 @@ struct BiArgs {
   int64_t n;
   int nsys;
   double neg;        // multiply the solution by this (M_P = -G^T)
-  typename CT<R>::T *x, *r, *r0, *p0, *p1, *v0, *v1, *t;
-  double* acc;       // [2][BI_BANKS][nsys][8]
-  int* done;         // [nsys]
+  // x, r (by parity: r_k in rr[k & 1]), the shadow residual r0, p and v (by
+  // parity), t
+  typename CT<R>::T *x, *rr0, *rr1, *rh, *p0, *p1, *v0, *v1, *t;
+  double* acc;       // [2][BI_BANKS][nsys][BI_ACC]
   double tol2;       // tol^2
   double* bnorm2;    // [nsys]
   int lpr;           // lanes per (row, system)
@@ -639,21 +647,21 @@ struct BiArgs {
 #define BI_LPR 4
 #endif
 __device__ __forceinline__ double* ACC(double* acc, int nsys, int par, int bank, int s) {
-  return acc + (((size_t)par * BI_BANKS + bank) * nsys + s) * 8;
+  return acc + (((size_t)par * BI_BANKS + bank) * nsys + s) * BI_ACC;
 }
-__device__ __forceinline__ void acc_read(double* acc, int nsys, int par, int s, double (&v)[8]) {
+__device__ __forceinline__ void acc_read(double* acc, int nsys, int par, int s, double (&v)[BI_ACC]) {
 #pragma unroll
-  for (int q = 0; q < 8; ++q) v[q] = 0.0;
+  for (int q = 0; q < BI_ACC; ++q) v[q] = 0.0;
 #pragma unroll
   for (int b = 0; b < BI_BANKS; ++b) {
     const double* a = ACC(acc, nsys, par, b, s);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) v[q] += a[q];
+    for (int q = 0; q < BI_ACC; ++q) v[q] += a[q];
   }
 }
-__device__ __forceinline__ void acc_zero(double* acc, int nsys, int par, int s, int q0, int q1) {
+__device__ __forceinline__ void acc_zero(double* acc, int nsys, int par, int s) {
   for (int b = 0; b < BI_BANKS; ++b)
-    for (int q = q0; q < q1; ++q) ACC(acc, nsys, par, b, s)[q] = 0.0;
+    for (int q = 0; q < BI_ACC; ++q) ACC(acc, nsys, par, b, s)[q] = 0.0;
 }
 
 __device__ __forceinline__ void cdiv(double ar, double ai, double br, double bi, double& cr, double& ci) {
@@ -782,10 +790,19 @@ __device__ __forceinline__ void system_accumulate(const BiLayout& L, const doubl
       if (w[q] != 0.0) atomicAdd(ACC(acc, nsys, par, blockIdx.x % BI_BANKS, threadIdx.x) + off + q, w[q]);
 }
 
+// per-block step state of each system (shared memory; the same in every block)
+struct BiState {
+  double rho_r, rho_i;  // rho_k = r0^H r_k
+  double al_r, al_i;    // alpha_k
+  double om_r, om_i;    // omega_k
+  double beta_r, beta_i;
+  int act;              // system still iterating
+};
+
 template <typename R>
 __device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typename CT<R>::T* __restrict__ b,
                                                 double* red) {
-  // x = 0, r = r0 = b, p = v = 0; rho_0 = b^H b stored as "next rho" of parity 1
+  // x = 0; r_{-1} (parity 1) = r0 = b; p_{-1} = v_{-1} = t = 0; |b|^2 per system
   const BiLayout L(A.nsys, A.lpr);
   double part[1] = {0.0};
   if (L.sub == 0)
@@ -793,80 +810,80 @@ __device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typena
       const int64_t k = i * L.ns + L.s;
       const auto bv = b[(int64_t)L.s * A.n + i];
       A.x[k] = {0, 0};
-      A.r[k] = bv;
-      A.r0[k] = bv;
-      A.p0[k] = A.p1[k] = A.v0[k] = A.v1[k] = {0, 0};
+      A.rr1[k] = bv;
+      A.rh[k] = bv;
+      A.p1[k] = A.v1[k] = A.t[k] = {0, 0};
       part[0] += (double)bv.x * bv.x + (double)bv.y * bv.y;
     }
   system_sums<1>(L, part, red);
   if (threadIdx.x < L.ns && part[0] != 0.0) atomicAdd(A.bnorm2 + threadIdx.x, part[0]);
 }
 
+// K1 of iteration k (parity P = k & 1): finish step k-1 row by row (s = r -
+// alpha v, r_k = s - omega t, x += alpha p + omega s) and form p_k = r_k +
+// beta (p_{k-1} - omega v_{k-1}) and v_k = G p_k, the gathered p_k rebuilt
+// from the step k-1 vectors; sums r0^H v_k and |r_k|^2.
 template <typename R>
-__device__ __forceinline__ void bicg_phase_init2(const BiArgs<R>& A) {
-  const int s = threadIdx.x;
-  if (s >= A.nsys) return;
-  for (int par = 0; par < 2; ++par) acc_zero(A.acc, A.nsys, par, s, 0, 8);
-  ACC(A.acc, A.nsys, 1, 0, s)[5] = A.bnorm2[s];
-  ACC(A.acc, A.nsys, 1, 0, s)[7] = A.bnorm2[s];
-  A.done[s] = A.bnorm2[s] == 0.0;
-}
-
-// K1: p_k = r_k + beta (p_{k-1} - omega_{k-1} v_{k-1});  v_k = G p_k;  acc r0^H v.
-// Returns false (in every block alike) when no system is active any more.
-template <typename R>
-__device__ __forceinline__ bool bicg_phase_k1(const BiArgs<R>& A, int k, double* red) {
-  double* sc = red + 3 * blockDim.x;         // after [3][blockDim] partials: [nsys][5] scalars
+__device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState* st, double* red) {
   const BiLayout L(A.nsys, A.lpr);
-  const int P = k & 1;
-  if (threadIdx.x < L.ns) {
+  const int P = k & 1, ns = L.ns;
+  if (threadIdx.x < ns) {
     const int s = threadIdx.x;
-    double a[8], ap[8];
-    acc_read(A.acc, A.nsys, P, s, a);
-    acc_read(A.acc, A.nsys, P ^ 1, s, ap);
-    bool act = !A.done[s];
-    // convergence of r_k: r^H r from the previous K3 (or b^H b)
-    if (act && ap[7] <= A.tol2 * A.bnorm2[s]) {
-      act = false;
-      if (blockIdx.x == 0) A.done[s] = 1;
+    BiState& z = st[s];
+    if (k == 0) {
+      z = BiState{};
+      z.rho_r = A.bnorm2[s];  // r0^H r_0 = |b|^2
+      z.om_r = 1.0;
+      z.act = A.bnorm2[s] > 0.0;
+    } else if (z.act) {
+      double a[BI_ACC];
+      acc_read(A.acc, A.nsys, P ^ 1, s, a);  // the K2 sums of step k-1
+      if (a[5] == 0.0) {
+        z.act = 0;  // t = 0: breakdown, x stays x_{k-1}
+      } else {
+        double omr, omi, rn_r, rn_i, tr, ti, br, bi;
+        cdiv_r<R>(a[3], a[4], a[5], 0.0, omr, omi);                        // omega_{k-1}
+        rn_r = a[6] - (omr * a[8] - omi * a[9]);                           // rho_k
+        rn_i = a[7] - (omr * a[9] + omi * a[8]);
+        cdiv_r<R>(rn_r, rn_i, z.rho_r, z.rho_i, br, bi);                  // rho_k / rho_{k-1}
+        cdiv_r<R>(z.al_r, z.al_i, omr, omi, tr, ti);                      // alpha_{k-1} / omega_{k-1}
+        z.beta_r = br * tr - bi * ti;
+        z.beta_i = br * ti + bi * tr;
+        z.om_r = omr;
+        z.om_i = omi;
+        z.rho_r = rn_r;
+        z.rho_i = rn_i;
+      }
     }
-    double br = 0.0, bi = 0.0, omr = 1.0, omi = 0.0;
-    if (act && k > 0) {
-      // beta = (rho_k / rho_{k-1}) (alpha_{k-1} / omega_{k-1})
-      double rr, ri, alr, ali;
-      cdiv_r<R>(ap[5], ap[6], a[5], a[6], rr, ri);           // rho_k / rho_{k-1}
-      cdiv_r<R>(a[5], a[6], ap[0], ap[1], alr, ali);         // alpha_{k-1} = rho_{k-1}/(r0^H v_{k-1})
-      cdiv_r<R>(ap[2], ap[3], ap[4], 0.0, omr, omi);         // omega_{k-1}
-      double tr, ti;
-      cdiv_r<R>(alr, ali, omr, omi, tr, ti);
-      br = rr * tr - ri * ti;
-      bi = rr * ti + ri * tr;
-    }
-    sc[5 * s] = act ? 1.0 : 0.0;
-    sc[5 * s + 1] = br; sc[5 * s + 2] = bi; sc[5 * s + 3] = omr; sc[5 * s + 4] = omi;
   }
   __syncthreads();
   bool any = false;
-  for (int q = 0; q < L.ns; ++q) any |= sc[5 * q] != 0.0;
-  if (!any) return false;
+  for (int q = 0; q < ns; ++q) any |= st[q].act != 0;
+  if (!any) return;
   const int s = L.s;
-  const bool act = sc[5 * s] != 0.0;
-  // vector arithmetic in the storage precision (float32 on the FP32 path: the
-  // FP64 pipe is a small fraction of FP32 here); the dot products in float64
-  const R bR = (R)sc[5 * s + 1], bI = (R)sc[5 * s + 2], oR = (R)sc[5 * s + 3], oI = (R)sc[5 * s + 4];
-  const auto* pprev = P ? A.p0 : A.p1;  // p_{k-1}
-  const auto* vprev = P ? A.v0 : A.v1;
+  const BiState& z = st[s];
+  const bool act = z.act != 0;
+  const bool first = k == 0;
+  // the scalars of step k-1 (zero at k = 0: r_{-1} = b gives r_0 = b, p_0 = b)
+  const R aR = first ? R(0) : (R)z.al_r, aI = first ? R(0) : (R)z.al_i;
+  const R oR = first ? R(0) : (R)z.om_r, oI = first ? R(0) : (R)z.om_i;
+  const R bR = first ? R(0) : (R)z.beta_r, bI = first ? R(0) : (R)z.beta_i;
+  const auto* rprev = P ? A.rr0 : A.rr1;
+  auto* rcur = P ? A.rr1 : A.rr0;
+  const auto* pprev = P ? A.p0 : A.p1;
   auto* pcur = P ? A.p1 : A.p0;
+  const auto* vprev = P ? A.v0 : A.v1;
   auto* vcur = P ? A.v1 : A.v0;
-  const int ns = L.ns;
-  auto pj = [&](int64_t j) {
+  // r_k and p_k at column j from step k-1 vectors
+  auto rp = [&](int64_t j, typename CT<R>::T& rk, typename CT<R>::T& pk, typename CT<R>::T& sk) {
     const int64_t kk = j * ns + s;
-    const auto pp = pprev[kk], vv = vprev[kk], rj = A.r[kk];
-    const R dx = pp.x - (oR * vv.x - oI * vv.y), dy = pp.y - (oR * vv.y + oI * vv.x);
-    return typename CT<R>::T{rj.x + bR * dx - bI * dy, rj.y + bR * dy + bI * dx};
+    const auto r1 = rprev[kk], v1 = vprev[kk], t1 = A.t[kk], p1 = pprev[kk];
+    sk = {r1.x - (aR * v1.x - aI * v1.y), r1.y - (aR * v1.y + aI * v1.x)};
+    rk = {sk.x - (oR * t1.x - oI * t1.y), sk.y - (oR * t1.y + oI * t1.x)};
+    const R dx = p1.x - (oR * v1.x - oI * v1.y), dy = p1.y - (oR * v1.y + oI * v1.x);
+    pk = {rk.x + bR * dx - bI * dy, rk.y + bR * dy + bI * dx};
   };
-  double part[2] = {0.0, 0.0};
-  // the pass loop is uniform in the block (shuffles inside)
+  double part[3] = {0.0, 0.0, 0.0};
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
@@ -885,57 +902,72 @@ __device__ __forceinline__ bool bicg_phase_k1(const BiArgs<R>& A, int k, double*
 #pragma unroll
         for (int u = 0; u < BI_W; ++u)
           if (cj[u] >= 0) {
-            const auto pc = pj(cj[u]);
-            vr += gv[u] * pc.x;
-            vi += gv[u] * pc.y;
+            typename CT<R>::T rk, pk, sk;
+            rp(cj[u], rk, pk, sk);
+            vr += gv[u] * pk.x;
+            vi += gv[u] * pk.y;
           }
       }
     }
     vr = lane_group_sum(L, vr);
     vi = lane_group_sum(L, vi);
     if (live && L.sub == 0) {
-      pcur[i * ns + s] = pj(i);
-      vcur[i * ns + s] = {vr, vi};
-      const auto rh = A.r0[i * ns + s];
-      part[0] += (double)(rh.x * vr + rh.y * vi);   // conj(r0) v
-      part[1] += (double)(rh.x * vi - rh.y * vr);
+      const int64_t kk = i * ns + s;
+      typename CT<R>::T rk, pk, sk;
+      rp(i, rk, pk, sk);
+      const auto p1 = pprev[kk], xi = A.x[kk];
+      A.x[kk] = {xi.x + (aR * p1.x - aI * p1.y) + (oR * sk.x - oI * sk.y),
+                 xi.y + (aR * p1.y + aI * p1.x) + (oR * sk.y + oI * sk.x)};
+      rcur[kk] = rk;
+      pcur[kk] = pk;
+      vcur[kk] = {vr, vi};
+      const auto h = A.rh[kk];
+      part[0] += (double)(h.x * vr + h.y * vi);   // conj(r0) v
+      part[1] += (double)(h.x * vi - h.y * vr);
+      part[2] += (double)rk.x * rk.x + (double)rk.y * rk.y;
     }
   }
-  system_accumulate<2>(L, part, red, A.acc, A.nsys, P, 0);
-  return true;
+  system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 0);
 }
 
-// K2: alpha = rho_k / (r0^H v_k); s = r - alpha v; t = G s; acc t^H s, t^H t
+// K2 of iteration k: convergence of r_k; alpha_k = rho_k / (r0^H v_k);
+// s = r_k - alpha v_k, t = G s (gathered s rebuilt); sums t^H s, t^H t,
+// r0^H s, r0^H t. Returns false (in every block alike) when no system is
+// active any more.
 template <typename R>
-__device__ __forceinline__ void bicg_phase_k2(const BiArgs<R>& A, int k, double* red) {
-  double* sc = red + 3 * blockDim.x;         // [nsys][3]: active, alpha (re, im)
+__device__ __forceinline__ bool bicg_phase_k2(const BiArgs<R>& A, int k, BiState* st, double* red) {
   const BiLayout L(A.nsys, A.lpr);
-  const int P = k & 1;
-  if (threadIdx.x < L.ns) {
+  const int P = k & 1, ns = L.ns;
+  if (threadIdx.x < ns) {
     const int s = threadIdx.x;
-    double a[8], ap[8];
-    acc_read(A.acc, A.nsys, P, s, a);
-    acc_read(A.acc, A.nsys, P ^ 1, s, ap);
-    bool act = !A.done[s];
-    if (act && blockIdx.x == 0) acc_zero(A.acc, A.nsys, P, s, 5, 8);
-    if (a[0] == 0.0 && a[1] == 0.0) act = false;
-    double alr = 0.0, ali = 0.0;
-    if (act) cdiv_r<R>(ap[5], ap[6], a[0], a[1], alr, ali);
-    sc[3 * s] = act ? 1.0 : 0.0;
-    sc[3 * s + 1] = alr;
-    sc[3 * s + 2] = ali;
+    BiState& z = st[s];
+    if (blockIdx.x == 0) acc_zero(A.acc, A.nsys, P ^ 1, s);  // read by this step's K1; K1 of k+1 adds there
+    if (z.act) {
+      double a[BI_ACC];
+      acc_read(A.acc, A.nsys, P, s, a);
+      if (a[2] <= A.tol2 * A.bnorm2[s] || (a[0] == 0.0 && a[1] == 0.0)) {
+        z.act = 0;  // converged (or breakdown): x_k is the solution
+      } else {
+        cdiv_r<R>(z.rho_r, z.rho_i, a[0], a[1], z.al_r, z.al_i);
+      }
+    }
   }
   __syncthreads();
-  const int s = L.s, ns = L.ns;
-  const bool act = sc[3 * s] != 0.0;
-  const R aR = (R)sc[3 * s + 1], aI = (R)sc[3 * s + 2];
+  bool any = false;
+  for (int q = 0; q < ns; ++q) any |= st[q].act != 0;
+  if (!any) return false;
+  const int s = L.s;
+  const BiState& z = st[s];
+  const bool act = z.act != 0;
+  const R aR = (R)z.al_r, aI = (R)z.al_i;
+  const auto* rcur = P ? A.rr1 : A.rr0;
   const auto* vcur = P ? A.v1 : A.v0;
   auto sj = [&](int64_t j) {
     const int64_t kk = j * ns + s;
-    const auto vv = vcur[kk], rj = A.r[kk];
+    const auto vv = vcur[kk], rj = rcur[kk];
     return typename CT<R>::T{rj.x - (aR * vv.x - aI * vv.y), rj.y - (aR * vv.y + aI * vv.x)};
   };
-  double part[3] = {0, 0, 0};
+  double part[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
@@ -963,64 +995,53 @@ __device__ __forceinline__ void bicg_phase_k2(const BiArgs<R>& A, int k, double*
     tr = lane_group_sum(L, tr);
     ti = lane_group_sum(L, ti);
     if (live && L.sub == 0) {
-      A.t[i * ns + s] = {tr, ti};
-      const auto si = sj(i);
+      const int64_t kk = i * ns + s;
+      A.t[kk] = {tr, ti};
+      const auto si = sj(i), h = A.rh[kk];
       part[0] += (double)(tr * si.x + ti * si.y);   // conj(t) s
       part[1] += (double)(tr * si.y - ti * si.x);
       part[2] += (double)(tr * tr + ti * ti);
+      part[3] += (double)(h.x * si.x + h.y * si.y); // conj(r0) s
+      part[4] += (double)(h.x * si.y - h.y * si.x);
+      part[5] += (double)(h.x * tr + h.y * ti);     // conj(r0) t
+      part[6] += (double)(h.x * ti - h.y * tr);
     }
   }
-  system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 2);
+  system_accumulate<7>(L, part, red, A.acc, A.nsys, P, 3);
+  return true;
 }
 
-// K3: omega = t^H s / t^H t; x += alpha p + omega s; r = s - omega t; acc rho, r^H r
+// After the last iteration (maxit reached) the systems still active take the
+// update of step k: x += alpha p_k + omega s with omega from the K2 sums.
 template <typename R>
-__device__ __forceinline__ void bicg_phase_k3(const BiArgs<R>& A, int k, double* red) {
-  double* sc = red + 3 * blockDim.x;         // [nsys][5]: active, alpha, omega
+__device__ __forceinline__ void bicg_phase_last(const BiArgs<R>& A, int k, BiState* st) {
   const BiLayout L(A.nsys, A.lpr);
-  const int P = k & 1;
-  if (threadIdx.x < L.ns) {
+  const int P = k & 1, ns = L.ns;
+  if (threadIdx.x < ns) {
     const int s = threadIdx.x;
-    double a[8], ap[8];
-    acc_read(A.acc, A.nsys, P, s, a);
-    acc_read(A.acc, A.nsys, P ^ 1, s, ap);
-    bool act = !A.done[s];
-    if (act && blockIdx.x == 0) acc_zero(A.acc, A.nsys, P ^ 1, s, 0, 5);  // parity P^1 is free for iteration k+1
-    if (act && ((a[0] == 0.0 && a[1] == 0.0) || a[4] == 0.0)) {
-      act = false;
-      if (blockIdx.x == 0) A.done[s] = 1;
+    BiState& z = st[s];
+    if (z.act) {
+      double a[BI_ACC];
+      acc_read(A.acc, A.nsys, P, s, a);
+      if (a[5] == 0.0) z.act = 0;
+      else cdiv_r<R>(a[3], a[4], a[5], 0.0, z.om_r, z.om_i);
     }
-    double alr = 0, ali = 0, omr = 0, omi = 0;
-    if (act) {
-      cdiv_r<R>(ap[5], ap[6], a[0], a[1], alr, ali);
-      cdiv_r<R>(a[2], a[3], a[4], 0.0, omr, omi);
-    }
-    sc[5 * s] = act ? 1.0 : 0.0;
-    sc[5 * s + 1] = alr; sc[5 * s + 2] = ali; sc[5 * s + 3] = omr; sc[5 * s + 4] = omi;
   }
   __syncthreads();
-  const int s = L.s, ns = L.ns;
-  const bool act = L.sub == 0 && sc[5 * s] != 0.0;
-  const R aR = (R)sc[5 * s + 1], aI = (R)sc[5 * s + 2], oR = (R)sc[5 * s + 3], oI = (R)sc[5 * s + 4];
-  const auto* pcur = P ? A.p1 : A.p0;
+  const int s = L.s;
+  const BiState& z = st[s];
+  if (!z.act || L.sub != 0) return;
+  const R aR = (R)z.al_r, aI = (R)z.al_i, oR = (R)z.om_r, oI = (R)z.om_i;
+  const auto* rcur = P ? A.rr1 : A.rr0;
   const auto* vcur = P ? A.v1 : A.v0;
-  double part[3] = {0, 0, 0};
-  if (act)
-    for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
-      const int64_t kk = i * ns + s;
-      const auto vv = vcur[kk], ri = A.r[kk], pp = pcur[kk], tt = A.t[kk];
-      const R sx = ri.x - (aR * vv.x - aI * vv.y), sy = ri.y - (aR * vv.y + aI * vv.x);
-      const auto xi = A.x[kk];
-      A.x[kk] = {xi.x + (aR * pp.x - aI * pp.y) + (oR * sx - oI * sy),
-                 xi.y + (aR * pp.y + aI * pp.x) + (oR * sy + oI * sx)};
-      const R rx = sx - (oR * tt.x - oI * tt.y), ry = sy - (oR * tt.y + oI * tt.x);
-      A.r[kk] = {rx, ry};
-      const auto rh = A.r0[kk];
-      part[0] += (double)(rh.x * rx + rh.y * ry);
-      part[1] += (double)(rh.x * ry - rh.y * rx);
-      part[2] += (double)(rx * rx + ry * ry);
-    }
-  system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 5);
+  const auto* pcur = P ? A.p1 : A.p0;
+  for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
+    const int64_t kk = i * ns + s;
+    const auto rk = rcur[kk], vv = vcur[kk], pp = pcur[kk], xi = A.x[kk];
+    const R sx = rk.x - (aR * vv.x - aI * vv.y), sy = rk.y - (aR * vv.y + aI * vv.x);
+    A.x[kk] = {xi.x + (aR * pp.x - aI * pp.y) + (oR * sx - oI * sy),
+               xi.y + (aR * pp.y + aI * pp.x) + (oR * sy + oI * sx)};
+  }
 }
 
 template <typename R>
@@ -1080,27 +1101,28 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, int* sticky, unsigned& ge
   return s_ok != 0;
 }
 
-// A6, the whole BiCGStab solve in one cooperative launch: the phases of the
-// iteration (init, K1, K2, K3) separated by grid barriers instead of kernel
-// boundaries, and the loop left as soon as every system has converged.
+// A6, the whole BiCGStab solve in one cooperative launch: the phases (init,
+// then K1 and K2 per iteration) separated by grid barriers instead of kernel
+// boundaries, and the loop left as soon as every system has converged. The
+// dynamic shared memory holds the reduction scratch and the BiState array.
 template <typename R>
 __global__ void __launch_bounds__(256) bicg_persistent(BiArgs<R> A, const typename CT<R>::T* __restrict__ b,
                                                        typename CT<R>::T* __restrict__ out, int maxit) {
   extern __shared__ double red[];
+  BiState* st = reinterpret_cast<BiState*>(red + 7 * blockDim.x);
   unsigned gen = 0;
   bicg_phase_init<R>(A, b, red);
   if (!grid_sync(A.bar, A.err, gen)) return;
-  if (blockIdx.x == 0) bicg_phase_init2<R>(A);
-  if (!grid_sync(A.bar, A.err, gen)) return;
-  for (int k = 0; k < maxit; ++k) {
-    if (!bicg_phase_k1<R>(A, k, red)) break;
+  int k = 0;
+  bool running = true;
+  for (; k < maxit; ++k) {
+    bicg_phase_k1<R>(A, k, st, red);
     if (!grid_sync(A.bar, A.err, gen)) return;
-    bicg_phase_k2<R>(A, k, red);
-    if (!grid_sync(A.bar, A.err, gen)) return;
-    bicg_phase_k3<R>(A, k, red);
+    if (!bicg_phase_k2<R>(A, k, st, red)) { running = false; break; }
     if (!grid_sync(A.bar, A.err, gen)) return;
   }
-  // x rows are this thread's own (same layout in K3 and here): no barrier
+  if (running && k > 0) bicg_phase_last<R>(A, k - 1, st);
+  // x rows are this thread's own (same layout in every phase): no barrier
   bicg_phase_finish<R>(A, out);
 }
 
@@ -1156,10 +1178,9 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
     note_launch();
     CAL_TRY_CUDA(cudaGetLastError());
   }
-  CAL_TRY_CUDA(dalloc((void**)&d_work, 8 * vb, st));
-  // per solve: [2][BI_BANKS][nsys][8] sums, [nsys] |b|^2, then the barrier state
+  CAL_TRY_CUDA(dalloc((void**)&d_work, 9 * vb, st));
+  // per solve: [2][BI_BANKS][nsys][BI_ACC] sums, [nsys] |b|^2, then the barrier state
   CAL_TRY_CUDA(dalloc((void**)&d_acc, acc_bytes(), st));
-  CAL_TRY_CUDA(dalloc((void**)&d_done, nsys * sizeof(int), st));
   CAL_TRY_CUDA(dalloc((void**)&d_err, sizeof(int), st));
   CAL_TRY_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
   // nsys x rpb threads per block, rows grid-strided over as many blocks as
@@ -1170,7 +1191,7 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
   lpr = (pow2 && nsys <= 16) ? std::min(BI_LPR, 32 / nsys) : 1;
   rpb = std::max(1, 256 / (nsys * lpr));
   threads = nsys * lpr * rpb;
-  smem = (3 * (size_t)threads + 5 * (size_t)nsys) * sizeof(double);
+  smem = 7 * (size_t)threads * sizeof(double) + (size_t)nsys * sizeof(BiState);  // reduction scratch, step state
   int dev = 0, n_sm = 0, per_sm = 0;
   CAL_TRY_CUDA(cudaGetDevice(&dev));
   CAL_TRY_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
@@ -1184,12 +1205,12 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
 template <typename R>
 GramSolver<R>::~GramSolver() {
   // every solve has completed when the solver is destroyed: release on the legacy stream
-  for (void* p : {(void*)d_val, (void*)d_work, (void*)d_acc, (void*)d_done, (void*)d_err}) dfree(p, nullptr);
+  for (void* p : {(void*)d_val, (void*)d_work, (void*)d_acc, (void*)d_err}) dfree(p, nullptr);
 }
 
 template <typename R>
 size_t GramSolver<R>::acc_bytes() const {
-  return (2 * (size_t)BI_BANKS * nsys * 8 + nsys) * sizeof(double) + sizeof(GridBar);
+  return (2 * (size_t)BI_BANKS * nsys * BI_ACC + nsys) * sizeof(double) + sizeof(GridBar);
 }
 
 // One solve: clear the sums and the barrier, one cooperative launch.
@@ -1203,13 +1224,12 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   A.nsys = nsys;
   A.neg = neg;
   const size_t nv = (size_t)n * nsys;
-  A.x = d_work; A.r = d_work + nv; A.r0 = d_work + 2 * nv; A.p0 = d_work + 3 * nv;
-  A.p1 = d_work + 4 * nv; A.v0 = d_work + 5 * nv; A.v1 = d_work + 6 * nv; A.t = d_work + 7 * nv;
+  A.x = d_work; A.rr0 = d_work + nv; A.rr1 = d_work + 2 * nv; A.rh = d_work + 3 * nv; A.p0 = d_work + 4 * nv;
+  A.p1 = d_work + 5 * nv; A.v0 = d_work + 6 * nv; A.v1 = d_work + 7 * nv; A.t = d_work + 8 * nv;
   A.acc = d_acc;
-  A.bnorm2 = d_acc + 2 * BI_BANKS * nsys * 8;
-  A.bar = reinterpret_cast<GridBar*>(d_acc + 2 * BI_BANKS * nsys * 8 + nsys);
+  A.bnorm2 = d_acc + 2 * BI_BANKS * nsys * BI_ACC;
+  A.bar = reinterpret_cast<GridBar*>(d_acc + 2 * BI_BANKS * nsys * BI_ACC + nsys);
   A.err = d_err;
-  A.done = d_done;
   A.tol2 = tol * tol;
   A.lpr = lpr;
   const int tok = prof_begin(st, "bicgstab", 0.0);

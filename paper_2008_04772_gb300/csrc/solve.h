@@ -67,7 +67,6 @@ struct GramSolver {
   int maxit = 30;
   C* d_work = nullptr;
   double* d_acc = nullptr;   // per-solve sums, |b|^2 and the grid barrier state
-  int* d_done = nullptr;
   int* d_err = nullptr;      // sticky: a bounded barrier wait gave up
   int lpr = 1, rpb = 1, threads = 0;
   unsigned grid = 0;
