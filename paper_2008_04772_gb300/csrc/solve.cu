@@ -741,18 +741,19 @@ __device__ __forceinline__ R lane_group_sum(const BiLayout& L, R v) {
   return v;
 }
 
-// per-system sums of the block's partials (NV per thread), added to dst(s)
-// (nsys dividing 32: lanes of one system are nsys apart in a warp, summed by
-// shuffles first; otherwise each system's partials are summed directly)
-template <int NV>
-__device__ __forceinline__ void system_sums(const BiLayout& L, double (&v)[NV], double* red) {
+// per-system sums of the block's partials (NV per thread of type T), returned
+// in v of the first nsys threads as float64 (nsys dividing 32: lanes of one
+// system are nsys apart in a warp, summed by shuffles in T first; otherwise
+// each system's partials are summed directly in float64)
+template <int NV, typename T>
+__device__ __forceinline__ void system_sums(const BiLayout& L, const T (&p)[NV], double (&v)[NV], double* red) {
   const int ns = L.ns, lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   if ((32 % ns) == 0 && (blockDim.x & 31) == 0) {
 #pragma unroll
     for (int q = 0; q < NV; ++q) {
-      double a = v[q];
+      T a = p[q];
       for (int o = 16; o >= ns; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane < ns) red[(q * nw + wid) * ns + lane] = a;
+      if (lane < ns) red[(q * nw + wid) * ns + lane] = (double)a;
     }
     __syncthreads();
     if (threadIdx.x < ns)
@@ -764,7 +765,7 @@ __device__ __forceinline__ void system_sums(const BiLayout& L, double (&v)[NV], 
       }
   } else {
 #pragma unroll
-    for (int q = 0; q < NV; ++q) red[q * blockDim.x + threadIdx.x] = v[q];
+    for (int q = 0; q < NV; ++q) red[q * blockDim.x + threadIdx.x] = (double)p[q];
     __syncthreads();
     const int groups = blockDim.x / ns;
     if (threadIdx.x < ns)
@@ -777,18 +778,23 @@ __device__ __forceinline__ void system_sums(const BiLayout& L, double (&v)[NV], 
   }
 }
 
-template <int NV>
-__device__ __forceinline__ void system_accumulate(const BiLayout& L, const double (&v)[NV], double* red,
-                                                  double* acc, int nsys, int par, int off) {
+template <int NV, typename T>
+__device__ __forceinline__ void system_accumulate(const BiLayout& L, const T (&p)[NV], double* red, double* acc,
+                                                  int nsys, int par, int off) {
   double w[NV];
-#pragma unroll
-  for (int q = 0; q < NV; ++q) w[q] = v[q];
-  system_sums<NV>(L, w, red);
+  system_sums<NV, T>(L, p, w, red);
   if (threadIdx.x < L.ns)
 #pragma unroll
     for (int q = 0; q < NV; ++q)
       if (w[q] != 0.0) atomicAdd(ACC(acc, nsys, par, blockIdx.x % BI_BANKS, threadIdx.x) + off + q, w[q]);
 }
+
+// Row partials of the dot products: float32 for float32 vectors (one row per
+// thread, a few terms per lane; float64 adds run at 1/64 of the float32 rate
+// here and were a third of the solve's time), float64 for float64 vectors;
+// the sums across warps and blocks are float64.
+template <typename R> struct DotT { using T = double; };
+template <> struct DotT<float> { using T = float; };
 
 // per-block step state of each system (shared memory; the same in every block)
 struct BiState {
@@ -804,7 +810,7 @@ __device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typena
                                                 double* red) {
   // x = 0; r_{-1} (parity 1) = r0 = b; p_{-1} = v_{-1} = t = 0; |b|^2 per system
   const BiLayout L(A.nsys, A.lpr);
-  double part[1] = {0.0};
+  double part[1] = {0.0}, sum[1];
   if (L.sub == 0)
     for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
       const int64_t k = i * L.ns + L.s;
@@ -815,8 +821,8 @@ __device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typena
       A.p1[k] = A.v1[k] = A.t[k] = {0, 0};
       part[0] += (double)bv.x * bv.x + (double)bv.y * bv.y;
     }
-  system_sums<1>(L, part, red);
-  if (threadIdx.x < L.ns && part[0] != 0.0) atomicAdd(A.bnorm2 + threadIdx.x, part[0]);
+  system_sums<1, double>(L, part, sum, red);
+  if (threadIdx.x < L.ns && sum[0] != 0.0) atomicAdd(A.bnorm2 + threadIdx.x, sum[0]);
 }
 
 // K1 of iteration k (parity P = k & 1): finish step k-1 row by row (s = r -
@@ -883,7 +889,8 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
     const R dx = p1.x - (oR * v1.x - oI * v1.y), dy = p1.y - (oR * v1.y + oI * v1.x);
     pk = {rk.x + bR * dx - bI * dy, rk.y + bR * dy + bI * dx};
   };
-  double part[3] = {0.0, 0.0, 0.0};
+  using D = typename DotT<R>::T;
+  D part[3] = {0, 0, 0};
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
@@ -922,12 +929,12 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
       pcur[kk] = pk;
       vcur[kk] = {vr, vi};
       const auto h = A.rh[kk];
-      part[0] += (double)(h.x * vr + h.y * vi);   // conj(r0) v
-      part[1] += (double)(h.x * vi - h.y * vr);
-      part[2] += (double)rk.x * rk.x + (double)rk.y * rk.y;
+      part[0] += (D)(h.x * vr + h.y * vi);   // conj(r0) v
+      part[1] += (D)(h.x * vi - h.y * vr);
+      part[2] += (D)rk.x * rk.x + (D)rk.y * rk.y;
     }
   }
-  system_accumulate<3>(L, part, red, A.acc, A.nsys, P, 0);
+  system_accumulate<3, D>(L, part, red, A.acc, A.nsys, P, 0);
 }
 
 // K2 of iteration k: convergence of r_k; alpha_k = rho_k / (r0^H v_k);
@@ -967,7 +974,8 @@ __device__ __forceinline__ bool bicg_phase_k2(const BiArgs<R>& A, int k, BiState
     const auto vv = vcur[kk], rj = rcur[kk];
     return typename CT<R>::T{rj.x - (aR * vv.x - aI * vv.y), rj.y - (aR * vv.y + aI * vv.x)};
   };
-  double part[7] = {0, 0, 0, 0, 0, 0, 0};
+  using D = typename DotT<R>::T;
+  D part[7] = {0, 0, 0, 0, 0, 0, 0};
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
@@ -998,16 +1006,16 @@ __device__ __forceinline__ bool bicg_phase_k2(const BiArgs<R>& A, int k, BiState
       const int64_t kk = i * ns + s;
       A.t[kk] = {tr, ti};
       const auto si = sj(i), h = A.rh[kk];
-      part[0] += (double)(tr * si.x + ti * si.y);   // conj(t) s
-      part[1] += (double)(tr * si.y - ti * si.x);
-      part[2] += (double)(tr * tr + ti * ti);
-      part[3] += (double)(h.x * si.x + h.y * si.y); // conj(r0) s
-      part[4] += (double)(h.x * si.y - h.y * si.x);
-      part[5] += (double)(h.x * tr + h.y * ti);     // conj(r0) t
-      part[6] += (double)(h.x * ti - h.y * tr);
+      part[0] += (D)(tr * si.x + ti * si.y);   // conj(t) s
+      part[1] += (D)(tr * si.y - ti * si.x);
+      part[2] += (D)(tr * tr + ti * ti);
+      part[3] += (D)(h.x * si.x + h.y * si.y); // conj(r0) s
+      part[4] += (D)(h.x * si.y - h.y * si.x);
+      part[5] += (D)(h.x * tr + h.y * ti);     // conj(r0) t
+      part[6] += (D)(h.x * ti - h.y * tr);
     }
   }
-  system_accumulate<7>(L, part, red, A.acc, A.nsys, P, 3);
+  system_accumulate<7, D>(L, part, red, A.acc, A.nsys, P, 3);
   return true;
 }
 
