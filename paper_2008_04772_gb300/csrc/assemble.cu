@@ -1808,12 +1808,49 @@ __global__ void __launch_bounds__(128) singular_kernel(
 // in float64. Both use the same quadrature points and weights as the float64
 // kernel, whose result this reproduces to float32 output accuracy.
 // ---------------------------------------------------------------------------
-struct SsPt {                      // one (region, e1, e2, e3) direction at xi = 1
-  double x0, x1, y0, y1;           // reference coordinates of x and y
-  double m00, m01, m10, m11;       // x0 y0, x0 y1, x1 y0, x1 y1
-  double w;                        // gw(e1) gw(e2) gw(e3) J(e)
-  float fx0, fx1, fy0, fy1, fw, pad;
+struct SsPt {                      // one (region, e1, e2, e3) direction at xi = 1, float pairs hi + lo
+  float x0h, x0l, x1h, x1l;        // reference coordinates of x
+  float y0h, y0l, y1h, y1l;        // and of y
+  float mh[4], ml[4];              // x0 y0, x0 y1, x1 y0, x1 y1
+  float wh, wl;                    // gw(e1) gw(e2) gw(e3) J(e)
 };
+
+// Double-float arithmetic (a value is h + l, |l| <= ulp(h) / 2) on the float32
+// pipes, from the error-free transformations: TwoProd by fused multiply-add
+// and Knuth's TwoSum. The rounded intrinsics keep the compiler from contracting
+// or reassociating them.
+struct DF { float h, l; };
+__device__ __forceinline__ DF df_two_prod(float a, float b) {
+  const float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ DF df_quick(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b), bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  DF p = df_two_prod(a.h, b.h);
+  p.l = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, p.l));
+  return df_quick(p.h, p.l);
+}
+// the low parts added without a second TwoSum: relative error about 2^-46 of
+// |a| + |b| (the terms summed here are of one sign, or their cancellation is
+// bounded by the quadrature geometry)
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = df_two_sum(a.h, b.h);
+  s.l = __fadd_rn(s.l, __fadd_rn(a.l, b.l));
+  return df_quick(s.h, s.l);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ DF df_of(double x) {
+  const float h = (float)x;
+  return {h, (float)(x - (double)h)};
+}
+__device__ __forceinline__ double df_val(DF a) { return (double)a.h + (double)a.l; }
 
 struct SsRadial {
   double sG[3], sg[3];             // sum_j w_j xi_j^{2+d}, -sum_j w_j xi_j^d (d = 0, 1, 2)
@@ -1906,20 +1943,22 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
   const int nreg = cls == 3 ? 6 : (cls == 2 ? 5 : 2);
   const SsPt* T = tab + (cls == 1 ? 0 : (cls == 2 ? 2 : 7)) * ng3;
   const float fkr = (float)kr, fki = (float)ki;
-  // static moments (real, float64) and dynamic moments ((re, im), float64 over regions)
-  double TG[9], Tg[9], DG[18], Dg[18];
+  // static moments (real: summed in double-float, held in float64) and dynamic
+  // moments ((re, im), float32 per region, float64 over regions)
+  DF STG[9], STg[9], DG[18], Dg[18];
 #pragma unroll
-  for (int q = 0; q < 9; ++q) TG[q] = Tg[q] = 0.0;
+  for (int q = 0; q < 9; ++q) STG[q] = STg[q] = DF{0.0f, 0.0f};
 #pragma unroll
-  for (int q = 0; q < 18; ++q) DG[q] = Dg[q] = 0.0;
+  for (int q = 0; q < 18; ++q) DG[q] = Dg[q] = DF{0.0f, 0.0f};
   const V3<float> fa = {(float)ea.x, (float)ea.y, (float)ea.z}, fb = {(float)eb.x, (float)eb.y, (float)eb.z};
   const V3<float> fc = {(float)ec.x, (float)ec.y, (float)ec.z}, fd = {(float)ed.x, (float)ed.y, (float)ed.z};
-  if (stat_in) {
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
-      TG[k] = stat_in[p * 18 + k];
-      Tg[k] = stat_in[p * 18 + 9 + k];
-    }
+  // the edge vectors in double-float for the static sums
+  DF EA[3], EB[3], EC[3], ED[3];
+  if (!stat_in) {
+    EA[0] = df_of(ea.x); EA[1] = df_of(ea.y); EA[2] = df_of(ea.z);
+    EB[0] = df_of(eb.x); EB[1] = df_of(eb.y); EB[2] = df_of(eb.z);
+    EC[0] = df_of(ec.x); EC[1] = df_of(ec.y); EC[2] = df_of(ec.z);
+    ED[0] = df_of(ed.x); ED[1] = df_of(ed.y); ED[2] = df_of(ed.z);
   }
   for (int r = 0; r < nreg; ++r) {
     float dG[18], dg[18];
@@ -1930,7 +1969,7 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
       // float32 (its rounding near the singular set touches only O((kr)^2) terms)
       for (int q = 0; q < ng3; ++q) {
         const SsPt& e = T[r * ng3 + q];
-        const float fx0 = e.fx0, fx1 = e.fx1, fy0 = e.fy0, fy1 = e.fy1;
+        const float fx0 = e.x0h, fx1 = e.x1h, fy0 = e.y0h, fy1 = e.y1h;
         const V3<float> dr = {fx0 * fa.x + fx1 * fb.x - fy0 * fc.x - fy1 * fd.x,
                               fx0 * fa.y + fx1 * fb.y - fy0 * fc.y - fy1 * fd.y,
                               fx0 * fa.z + fx1 * fb.z - fy0 * fc.z - fy1 * fd.z};
@@ -1938,7 +1977,7 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
         const float yf = rsqrtf(r2f);
         float SG[6] = {0, 0, 0, 0, 0, 0}, Sg[6] = {0, 0, 0, 0, 0, 0};
         dyn_radial<NG>(rs, r2f * yf, fkr, fki, doC, SG, Sg);
-        const float cGf = e.fw * yf, cgf = cGf * yf * yf;
+        const float cGf = e.wh * yf, cgf = cGf * yf * yf;
         const float fm[9] = {1.0f, fx0, fx1, fy0, fy1, fx0 * fy0, fx0 * fy1, fx1 * fy0, fx1 * fy1};
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -1955,46 +1994,53 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
       }
 #pragma unroll
       for (int q = 0; q < 18; ++q) {
-        DG[q] += (double)dG[q];
-        if (doC) Dg[q] += (double)dg[q];
+        DG[q] = df_add(DG[q], DF{dG[q], 0.0f});
+        if (doC) Dg[q] = df_add(Dg[q], DF{dg[q], 0.0f});
       }
       continue;
     }
     for (int q = 0; q < ng3; ++q) {
       const SsPt& e = T[r * ng3 + q];
-      const double x0 = e.x0, x1 = e.x1, y0 = e.y0, y1 = e.y1;
-      // x - y at xi = 1; the shared vertex cancels exactly
-      const V3<double> dr = {x0 * ea.x + x1 * eb.x - y0 * ec.x - y1 * ed.x,
-                             x0 * ea.y + x1 * eb.y - y0 * ec.y - y1 * ed.y,
-                             x0 * ea.z + x1 * eb.z - y0 * ec.z - y1 * ed.z};
-      const double r2 = dot3(dr, dr);
-      const float r2f = (float)r2;
-      float yf;
-      double y;
-      if (r2f > 1e-30f && r2f < 1e30f) {
-        // float32 seed and one Newton step y <- y + y (1 - r2 y^2) / 2 for
-        // r2^{-1/2}: relative error about 1.5 e0^2 < 1e-13
-        yf = rsqrtf(r2f);
-        const double y0 = (double)yf;
-        const double h = fma(-r2 * y0, y0, 1.0);
-        y = fma(0.5 * y0, h, y0);
-      } else {
-        y = 1.0 / sqrt(r2);
-        yf = (float)y;
+      const DF X0{e.x0h, e.x0l}, X1{e.x1h, e.x1l}, Y0{e.y0h, e.y0l}, Y1{e.y1h, e.y1l};
+      // x - y at xi = 1 in double-float; the shared vertex cancels exactly
+      DF dr[3];
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        DF s = df_mul(X0, EA[c]);
+        s = df_add(s, df_mul(X1, EB[c]));
+        s = df_add(s, df_neg(df_mul(Y0, EC[c])));
+        dr[c] = df_add(s, df_neg(df_mul(Y1, ED[c])));
       }
-      const double cG = e.w * y, cg = cG * (y * y);
-      const double mono[9] = {1.0, x0, x1, y0, y1, e.m00, e.m01, e.m10, e.m11};
+      const DF r2 = df_add(df_add(df_mul(dr[0], dr[0]), df_mul(dr[1], dr[1])), df_mul(dr[2], dr[2]));
+      const float r2f = r2.h;
+      float yf;
+      DF y;
+      if (r2f > 1e-30f && r2f < 1e30f) {
+        // float32 seed and one double-float Newton step y <- y + y (1 - r2 y^2) / 2
+        // for r2^{-1/2}: relative error about 1.5 e0^2 plus the double-float rounding
+        yf = rsqrtf(r2f);
+        const DF hh = df_add(DF{1.0f, 0.0f}, df_neg(df_mul(r2, df_two_prod(yf, yf))));
+        y = df_add(DF{yf, 0.0f}, df_two_prod(yf, 0.5f * hh.h));
+      } else {
+        const double yd = 1.0 / sqrt(df_val(r2));
+        y = df_of(yd);
+        yf = y.h;
+      }
+      const DF cG = df_mul(DF{e.wh, e.wl}, y);
+      const DF mono[9] = {DF{1.0f, 0.0f}, X0, X1, Y0, Y1, DF{e.mh[0], e.ml[0]}, DF{e.mh[1], e.ml[1]},
+                          DF{e.mh[2], e.ml[2]}, DF{e.mh[3], e.ml[3]}};
 #pragma unroll
-      for (int k = 0; k < 9; ++k) TG[k] = fma(cG, mono[k], TG[k]);
+      for (int k = 0; k < 9; ++k) STG[k] = df_add(STG[k], df_mul(cG, mono[k]));
       if (doC) {
+        const DF cg = df_mul(cG, df_mul(y, y));
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Tg[k] = fma(cg, mono[k], Tg[k]);
+        for (int k = 0; k < 9; ++k) STg[k] = df_add(STg[k], df_mul(cg, mono[k]));
       }
       // dynamic part in float32
       float SG[6] = {0, 0, 0, 0, 0, 0}, Sg[6] = {0, 0, 0, 0, 0, 0};
       dyn_radial<NG>(rs, r2f * yf, fkr, fki, doC, SG, Sg);
-      const float cGf = e.fw * yf, cgf = cGf * yf * yf;
-      const float fx0 = e.fx0, fx1 = e.fx1, fy0 = e.fy0, fy1 = e.fy1;
+      const float cGf = e.wh * yf, cgf = cGf * yf * yf;
+      const float fx0 = e.x0h, fx1 = e.x1h, fy0 = e.y0h, fy1 = e.y1h;
       const float fm[9] = {1.0f, fx0, fx1, fy0, fy1, fx0 * fy0, fx0 * fy1, fx1 * fy0, fx1 * fy1};
 #pragma unroll
       for (int k = 0; k < 9; ++k) {
@@ -2011,9 +2057,15 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
     }
 #pragma unroll
     for (int q = 0; q < 18; ++q) {
-      DG[q] += (double)dG[q];
-      if (doC) Dg[q] += (double)dg[q];
+      DG[q] = df_add(DG[q], DF{dG[q], 0.0f});
+      if (doC) Dg[q] = df_add(Dg[q], DF{dg[q], 0.0f});
     }
+  }
+  double TG[9], Tg[9];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    TG[k] = stat_in ? stat_in[p * 18 + k] : df_val(STG[k]);
+    Tg[k] = stat_in ? stat_in[p * 18 + 9 + k] : df_val(STg[k]);
   }
   if (stat_out) {
 #pragma unroll
@@ -2036,10 +2088,10 @@ __global__ void __launch_bounds__(128) singular_split_kernel(
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     const int d = k == 0 ? 0 : (k < 5 ? 1 : 2);
-    MG[2 * k] = sc * fma(rs.sG[d], TG[k], DG[2 * k]);
-    MG[2 * k + 1] = sc * DG[2 * k + 1];
-    Mg[2 * k] = sc * fma(rs.sg[d], Tg[k], Dg[2 * k]);
-    Mg[2 * k + 1] = sc * Dg[2 * k + 1];
+    MG[2 * k] = sc * fma(rs.sG[d], TG[k], df_val(DG[2 * k]));
+    MG[2 * k + 1] = sc * df_val(DG[2 * k + 1]);
+    Mg[2 * k] = sc * fma(rs.sg[d], Tg[k], df_val(Dg[2 * k]));
+    Mg[2 * k + 1] = sc * df_val(Dg[2 * k + 1]);
   }
   sing_emit(MG, Mg, Q1, Q2, ea, eb, ec, ed, D, sp, slot_edge, slot_sw, nslot, mikr, miki, c4r, c4i, wantS, doC, 0,
             1, out);
@@ -2065,12 +2117,17 @@ static const SsPt* ss_table(int ng, const double* gx, const double* gw, cudaStre
       double xh[2], yh[2], jac;
       ss_map(cls_of[c], r, 1.0, gx[a1], gx[a2], gx[a3], xh, yh, jac);
       SsPt& e = h[(size_t)off_of[c] * ng3 + idx];
-      e.x0 = xh[0]; e.x1 = xh[1]; e.y0 = yh[0]; e.y1 = yh[1];
-      e.m00 = xh[0] * yh[0]; e.m01 = xh[0] * yh[1]; e.m10 = xh[1] * yh[0]; e.m11 = xh[1] * yh[1];
-      e.w = gw[a1] * gw[a2] * gw[a3] * jac;
-      e.fx0 = (float)xh[0]; e.fx1 = (float)xh[1]; e.fy0 = (float)yh[0]; e.fy1 = (float)yh[1];
-      e.fw = (float)e.w;
-      e.pad = 0.0f;
+      auto split = [](double x, float& hi, float& lo) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+      };
+      split(xh[0], e.x0h, e.x0l);
+      split(xh[1], e.x1h, e.x1l);
+      split(yh[0], e.y0h, e.y0l);
+      split(yh[1], e.y1h, e.y1l);
+      const double m[4] = {xh[0] * yh[0], xh[0] * yh[1], xh[1] * yh[0], xh[1] * yh[1]};
+      for (int k = 0; k < 4; ++k) split(m[k], e.mh[k], e.ml[k]);
+      split(gw[a1] * gw[a2] * gw[a3] * jac, e.wh, e.wl);
     }
   SsPt* d = nullptr;
   if (cudaMalloc((void**)&d, h.size() * sizeof(SsPt)) != cudaSuccess) return nullptr;
