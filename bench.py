@@ -262,7 +262,7 @@ def run_ours(args, rank, world):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "f32 bulk (f64 singular pairs, GMRES and refinement)",
+        "dtype": "f32 bulk (singular static sums and refinement residuals in double-float, GMRES recurrences f64)",
         "data": "synthetic (seeded icosphere, plane wave)",
         "config": {"workload": W["name"], "triangles": int(len(m.tris)), "unknowns": N,
                    "k_ext": W["k"], "eps_r": [W["eps"].real, W["eps"].imag],
