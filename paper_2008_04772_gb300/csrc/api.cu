@@ -395,12 +395,98 @@ struct Pmchwt {
   float* d_ZC = nullptr;
   int* d_gemm_err = nullptr;
   int64_t matvecs = 0;
+  // float32 combined blocks for the one-vector float32 product (reading 18):
+  // C = C_e + C_i, S1 = alpha_e S_e + alpha_i S_i, S2 = beta_e S_e + beta_i S_i
+  struct Combo {
+    void* C = nullptr;
+    void* S1 = nullptr;
+    void* S2 = nullptr;
+    int64_t rows = 0, off = 0;
+  };
+  Combo cA;
+  std::vector<Combo> cP;
   ~Pmchwt() {
     cudaStream_t st = nullptr;  // every solve has completed: the legacy stream orders the release
     for (void* p : {(void*)d_grp, (void*)d_gcol, (void*)d_grpT, (void*)d_gcolT, (void*)d_gval, (void*)d_gvalT, t1,
                     t2, (void*)d_gath, d_xt, (void*)d_Bt, (void*)d_Bh, (void*)d_Bl, (void*)d_ZS, (void*)d_ZC,
                     (void*)d_gemm_err})
       dfree(p, st);
+    free_combo(cA);
+    for (auto& c : cP) free_combo(c);
+  }
+  static void free_combo(Combo& c) {
+    for (void* p : {c.C, c.S1, c.S2}) dfree(p, nullptr);
+    c = Combo{};
+  }
+  int alloc_combo(Combo& c, int64_t rows, int64_t off, cudaStream_t st) {
+    c.rows = rows;
+    c.off = off;
+    const size_t bytes = (size_t)rows * rows * sizeof(float2);
+    for (void** p : {&c.C, &c.S1, &c.S2})
+      if (dalloc(p, std::max<size_t>(bytes, 16), st) != cudaSuccess) {
+        free_combo(c);
+        cudaGetLastError();
+        return fail(CAL_ENOMEM, "combined block: cannot allocate %zu bytes", bytes);
+      }
+    return CAL_OK;
+  }
+  // A: the exterior pair on the union with every interior pair on its diagonal
+  int build_combo_A(cudaStream_t st) {
+    if (o.precision != CAL_FP32 || o.matrix_free || !A_ext || A_ext->format != CAL_DENSE || !A_ext->d_S ||
+        !A_ext->d_C || A_ext->rows % 2)
+      return CAL_OK;
+    for (auto& a : A_int)
+      if (!a || a->format != CAL_DENSE || !a->d_S || !a->d_C) return CAL_OK;
+    int rc = alloc_combo(cA, N, 0, st);
+    if (rc) return rc;
+    const std::complex<double> ae = 1.0 / k_e, be = -k_e;
+    const bool whole = M == 1 && A_int[0]->rows == N;
+    if (!whole && (rc = combine_blocks(A_ext->d_S, A_ext->d_C, N, ae, be, nullptr, nullptr, 0, 0, 0.0, 0.0, cA.C,
+                                       cA.S1, cA.S2, true, ctx->n_sm, st)))
+      return rc;
+    for (int m = 0; m < M; ++m) {
+      const std::complex<double> am = mu_m[m] / k_m[m], bm = -k_m[m] / mu_m[m];
+      if ((rc = combine_blocks(A_ext->d_S, A_ext->d_C, N, ae, be, A_int[m]->d_S, A_int[m]->d_C, A_int[m]->rows,
+                               A_int[m]->row_offset, am, bm, cA.C, cA.S1, cA.S2, false, ctx->n_sm, st)))
+        return rc;
+    }
+    return CAL_OK;
+  }
+  // P = D: the exterior and interior pairs of each scatterer
+  int build_combo_P(cudaStream_t st) {
+    if (o.precision != CAL_FP32 || o.precond != CAL_PRECOND_D || (int)P_ext.size() != M || (int)P_int.size() != M)
+      return CAL_OK;
+    // the streaming kernel reads x in 16-byte words: even offsets and N
+    for (int m = 0; m < M; ++m)
+      for (Op* a : {P_ext[m].get(), P_int[m].get()})
+        if (!a || a->format != CAL_DENSE || !a->d_S || !a->d_C || a->rows % 2 || a->row_offset % 2 || N % 2)
+          return CAL_OK;
+    cP.resize(M);
+    for (int m = 0; m < M; ++m) {
+      const int64_t n = P_ext[m]->rows;
+      int rc = alloc_combo(cP[m], n, P_ext[m]->row_offset, st);
+      if (!rc)
+        rc = combine_blocks(P_ext[m]->d_S, P_ext[m]->d_C, n, 1.0 / k_e, -k_e, P_int[m]->d_S, P_int[m]->d_C, n, 0,
+                            mu_m[m] / k_m[m], -k_m[m] / mu_m[m], cP[m].C, cP[m].S1, cP[m].S2, false, ctx->n_sm,
+                            st);
+      if (rc) {
+        for (auto& c : cP) free_combo(c);
+        cP.clear();
+        return rc;
+      }
+    }
+    return CAL_OK;
+  }
+  // one float32 vector through a combined block: y += (C x1 + S1 x2, C x2 + S2 x1)
+  int apply_combo(const Combo& c, const void* x, void* y) {
+    BlockRef b;
+    b.C = c.C;
+    b.S = c.S1;
+    b.S2 = c.S2;
+    b.rows = b.cols = c.rows;
+    b.row_off = b.col_off = c.off;
+    b.precision = CAL_FP32;
+    return pair_apply(b, CAL_FP32, x, y, N, 1.0, 0.0, 1.0, 0.0, ctx->stream);
   }
 
   BlockRef ref(const Op& op, bool withS = true, bool withC = true) const {
@@ -532,6 +618,11 @@ struct Pmchwt {
     cudaStream_t st = ctx->stream;
     int rc = zero_vec(y, vec_prec, 2 * N * nrhs, st);
     if (rc) return rc;
+    if (vec_prec == CAL_FP32 && nrhs == 1 && cA.C) {
+      if ((rc = apply_combo(cA, x, y))) return rc;
+      matvecs += 4LL * M * M + 4LL * M;
+      return CAL_OK;
+    }
     const std::complex<double> ae = 1.0 / k_e, be = -k_e;  // mu_e = 1
     if ((rc = apply_block(ref(*A_ext), x, y, vec_prec, nrhs, ae, be))) return rc;
     if (o.matrix_free &&
@@ -559,6 +650,12 @@ struct Pmchwt {
     const bool ext = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DE || pc == CAL_PRECOND_SE;
     const bool in = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DI || pc == CAL_PRECOND_SI;
     const bool onlyS = pc == CAL_PRECOND_SE || pc == CAL_PRECOND_SI;
+    if (vec_prec == CAL_FP32 && nrhs == 1 && !cP.empty()) {
+      for (const Combo& c : cP)
+        if ((rc = apply_combo(c, x, y))) return rc;
+      matvecs += 8LL * M;
+      return CAL_OK;
+    }
     for (int m = 0; m < M; ++m) {
       if (ext && (rc = apply_block(ref(*P_ext[m], true, !onlyS), x, y, vec_prec, nrhs, 1.0 / k_e, -k_e))) return rc;
       if (in && (rc = apply_block(ref(*P_int[m], true, !onlyS), x, y, vec_prec, nrhs, mu_m[m] / k_m[m],
@@ -1098,6 +1195,7 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
                                o.q_regular_A, o.q_singular_A, aprec, P.A_int[m])))
         return rc;
   }
+  if ((rc = P.build_combo_A(st))) return rc;
   CAL_TRY_CUDA(cudaEventRecord(ev.e[1], st));
   if (need_bc) {
     const double tb = now();
@@ -1161,6 +1259,9 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
       return rc;
     bytes_G = 2 * ((n + 1) * 8 + P.gnnz * (4 + 8));
   }
+  if ((rc = P.build_combo_P(st))) return rc;
+  if (P.cA.C) bytes_A += 3 * P.cA.rows * P.cA.rows * 8;
+  for (const auto& c : P.cP) bytes_P += 3 * c.rows * c.rows * 8;
   CAL_TRY_CUDA(cudaEventRecord(ev.e[3], st));
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   float ms_A = 0.0f, ms_P = 0.0f;

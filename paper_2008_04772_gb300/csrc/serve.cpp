@@ -51,6 +51,7 @@ int64_t resident_bytes(const Mesh& m, const std::vector<double>& area_m, const c
       const int64_t n = m.edge_off[d + 1] - m.edge_off[d];
       b += 2 * n * n * esz;  // S, C at k_m
     }
+    if (o.precision != CAL_FP64) b += 3 * N * N * 8;  // combined float32 blocks of A
   }
   if (o.precond != CAL_PRECOND_NONE) {
     const int pc = o.precond;
@@ -71,6 +72,8 @@ int64_t resident_bytes(const Mesh& m, const std::vector<double>& area_m, const c
         idx = (n + 1) * 8 + nnz * 4;
       }
       b += sides * (ops * nnz * esz + idx);
+      if (pc == CAL_PRECOND_D && o.precision != CAL_FP64 && !std::isfinite(o.near_cutoff_P))
+        b += 3 * n * n * 8;  // combined float32 blocks of P
     }
     b += 2 * ((N + 1) * 8 + 40 * N * 12);  // Gram G and G^T (about 40 entries per row)
     b += m.nt * 6 * 256;                    // barycentric space records

@@ -8,6 +8,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdint>
 #include <type_traits>
 
@@ -280,11 +281,15 @@ __device__ __forceinline__ void atomic_add_v(double2* p, double x, double y) {
   atomicAdd(&p->y, y);
 }
 
-template <typename VT, typename AT>
-__global__ void __launch_bounds__(256, 3) pair_gemv_units_kernel(
+// TWO_S: a combined block (reading 18) with separate S matrices for the two
+// halves, y1 += C x1 + S x2 and y2 += C x2 + S2 x1 (the caller passes
+// alpha = beta = 1); three matrices are read instead of two per block pair.
+template <typename VT, typename AT, bool TWO_S = false>
+__global__ void __launch_bounds__(256, TWO_S ? 2 : 3) pair_gemv_units_kernel(
     const float4* __restrict__ S, const float4* __restrict__ C, int64_t nr, int64_t nc2,
     int64_t ld2, int64_t chunk2, const VT* __restrict__ x1, const VT* __restrict__ x2,
-    VT* __restrict__ y1, VT* __restrict__ y2, double ar, double ai, double br, double bi) {
+    VT* __restrict__ y1, VT* __restrict__ y2, double ar, double ai, double br, double bi,
+    const float4* __restrict__ S2 = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t nsplit = (nc2 + chunk2 - 1) / chunk2;
   const int64_t nunits = nr * nsplit;
@@ -295,10 +300,11 @@ __global__ void __launch_bounds__(256, 3) pair_gemv_units_kernel(
     const int64_t c_lo = (u % nsplit) * chunk2, c_hi = min(c_lo + chunk2, nc2);
     const float4* Cr = C + r * ld2;
     const float4* Sr = S + r * ld2;
+    const float4* S2r = TWO_S ? S2 + r * ld2 : nullptr;
     AT cx1 = {0, 0}, cx2 = {0, 0}, sx1 = {0, 0}, sx2 = {0, 0};
     constexpr int U = 4;
     int64_t c2 = c_lo + lane;
-    auto consume = [&](float4 mc, float4 ms, int64_t c) {
+    auto consume = [&](float4 mc, float4 ms, float4 ms2, int64_t c) {
       VT u0, u1, v0, v1;
       Pair2<VT>::load(x1, c, u0, u1);
       Pair2<VT>::load(x2, c, v0, v1);
@@ -312,25 +318,32 @@ __global__ void __launch_bounds__(256, 3) pair_gemv_units_kernel(
       }
       if (hasS) {
         const AT m0 = {(E)ms.x, (E)ms.y}, m1 = {(E)ms.z, (E)ms.w};
-        cfma(sx1, m0, fu0); cfma(sx1, m1, fu1);
+        if (TWO_S) {
+          const AT n0 = {(E)ms2.x, (E)ms2.y}, n1 = {(E)ms2.z, (E)ms2.w};
+          cfma(sx1, n0, fu0); cfma(sx1, n1, fu1);
+        } else {
+          cfma(sx1, m0, fu0); cfma(sx1, m1, fu1);
+        }
         cfma(sx2, m0, fv0); cfma(sx2, m1, fv1);
       }
     };
     for (; c2 + 32 * (U - 1) < c_hi; c2 += 32 * U) {
-      float4 mc[U], ms[U];
+      float4 mc[U], ms[U], ms2[U];
 #pragma unroll
       for (int k = 0; k < U; ++k) {
         if (hasC) mc[k] = __ldcs(Cr + c2 + 32 * k);
         if (hasS) ms[k] = __ldcs(Sr + c2 + 32 * k);
+        if (TWO_S) ms2[k] = __ldcs(S2r + c2 + 32 * k);
       }
 #pragma unroll
-      for (int k = 0; k < U; ++k) consume(mc[k], ms[k], c2 + 32 * k);
+      for (int k = 0; k < U; ++k) consume(mc[k], ms[k], TWO_S ? ms2[k] : ms[k], c2 + 32 * k);
     }
     for (; c2 < c_hi; c2 += 32) {
-      float4 mc = {0, 0, 0, 0}, ms = {0, 0, 0, 0};
+      float4 mc = {0, 0, 0, 0}, ms = {0, 0, 0, 0}, ms2 = {0, 0, 0, 0};
       if (hasC) mc = __ldcs(Cr + c2);
       if (hasS) ms = __ldcs(Sr + c2);
-      consume(mc, ms, c2);
+      if (TWO_S) ms2 = __ldcs(S2r + c2);
+      consume(mc, ms, ms2, c2);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -345,6 +358,70 @@ __global__ void __launch_bounds__(256, 3) pair_gemv_units_kernel(
       atomic_add_v(y2 + r, (E)(cx2.x + br * sx1.x - bi * sx1.y), (E)(cx2.y + br * sx1.y + bi * sx1.x));
     }
   }
+}
+
+// Combined block of two operator pairs on one set of unknowns (reading 18):
+// C' = C_a + C_b, S1 = alpha_a S_a + alpha_b S_b, S2 = beta_a S_a + beta_b S_b.
+// The first pair covers the whole [rows][ld] block; the second, of side nb,
+// sits on its diagonal at (off, off) (an interior block inside the union, or
+// the same rows when off = 0 and nb = rows). Float32 fused multiply-adds: the
+// pass streams five matrices in and three out at HBM speed.
+__device__ __forceinline__ float2 cmul_f(float ar, float ai, float2 s) {
+  return make_float2(fmaf(ar, s.x, -ai * s.y), fmaf(ar, s.y, ai * s.x));
+}
+__device__ __forceinline__ float2 cmul2_f(float ar, float ai, float2 s, float br, float bi, float2 u) {
+  return make_float2(fmaf(ar, s.x, fmaf(-ai, s.y, fmaf(br, u.x, -bi * u.y))),
+                     fmaf(ar, s.y, fmaf(ai, s.x, fmaf(br, u.y, bi * u.x))));
+}
+
+__global__ void combine_init_kernel(const float2* __restrict__ S, const float2* __restrict__ C, int64_t n,
+                                    float ar, float ai, float br, float bi, float2* __restrict__ Co,
+                                    float2* __restrict__ S1, float2* __restrict__ S2) {
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+    const float2 s = __ldcs(S + q);
+    Co[q] = __ldcs(C + q);
+    S1[q] = cmul_f(ar, ai, s);
+    S2[q] = cmul_f(br, bi, s);
+  }
+}
+
+// rows by blockIdx.y (grid-stride), columns by the x dimension
+__global__ void combine_add_kernel(const float2* __restrict__ Sa, const float2* __restrict__ Ca,
+                                   const float2* __restrict__ Sb, const float2* __restrict__ Cb, int64_t nb,
+                                   int64_t ld, int64_t off, float a1r, float a1i, float b1r, float b1i, float a2r,
+                                   float a2i, float b2r, float b2i, float2* __restrict__ Co,
+                                   float2* __restrict__ S1, float2* __restrict__ S2) {
+  for (int64_t i = blockIdx.y; i < nb; i += gridDim.y)
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nb; j += (int64_t)gridDim.x * blockDim.x) {
+      const int64_t at = (off + i) * ld + off + j, q = i * nb + j;
+      const float2 sa = __ldcs(Sa + at), ca = __ldcs(Ca + at), sb = __ldcs(Sb + q), cb = __ldcs(Cb + q);
+      Co[at] = make_float2(ca.x + cb.x, ca.y + cb.y);
+      S1[at] = cmul2_f(a1r, a1i, sa, a2r, a2i, sb);
+      S2[at] = cmul2_f(b1r, b1i, sa, b2r, b2i, sb);
+    }
+}
+
+int combine_blocks(const void* Sa, const void* Ca, int64_t rows, std::complex<double> aa, std::complex<double> ba,
+                   const void* Sb, const void* Cb, int64_t nb, int64_t off, std::complex<double> ab,
+                   std::complex<double> bb, void* Co, void* S1, void* S2, bool init, int n_sm, cudaStream_t st) {
+  if (init) {
+    combine_init_kernel<<<(unsigned)std::max(1, n_sm * 8), 256, 0, st>>>(
+        (const float2*)Sa, (const float2*)Ca, rows * rows, (float)aa.real(), (float)aa.imag(), (float)ba.real(),
+        (float)ba.imag(), (float2*)Co, (float2*)S1, (float2*)S2);
+    note_launch();
+  }
+  if (Sb) {
+    if (off < 0 || off + nb > rows) return fail(CAL_EINVAL, "combined block: inner block out of range");
+    const dim3 grid((unsigned)std::max<int64_t>(1, std::min<int64_t>((nb + 255) / 256, 8)),
+                    (unsigned)std::max<int64_t>(1, std::min<int64_t>(nb, 65535)));
+    combine_add_kernel<<<grid, 256, 0, st>>>(
+        (const float2*)Sa, (const float2*)Ca, (const float2*)Sb, (const float2*)Cb, nb, rows, off,
+        (float)aa.real(), (float)aa.imag(), (float)ba.real(), (float)ba.imag(), (float)ab.real(), (float)ab.imag(),
+        (float)bb.real(), (float)bb.imag(), (float2*)Co, (float2*)S1, (float2*)S2);
+    note_launch();
+  }
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
 }
 
 // pair_gemv_units_kernel for one float64 vector on float32 blocks, in
@@ -1277,13 +1354,19 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
   const MT* S = reinterpret_cast<const MT*>(b.S);
   const MT* C = reinterpret_cast<const MT*>(b.C);
   if (b.rowptr) {
+    if (b.S2) return fail(CAL_EINVAL, "combined block: dense blocks only");
     const int tok = prof_begin(st, "pair_spmv", 0.0);
     pair_spmv_kernel<MT, VT, AT><<<blocks_for(b.rows * 32, 256), 256, 0, st>>>(
         S, C, b.rowptr, b.col, b.rows, x1, x2, y1, y2, ar, ai, br, bi);
     prof_end(st, tok);
     note_launch();
   } else {
-    const double bytes = (double)b.rows * b.cols * sizeof(MT) * ((S ? 1 : 0) + (C ? 1 : 0));
+    // a combined block (S2 set) runs only on the float32-vector streaming kernel
+    const bool s2_ok = std::is_same<MT, float2>::value && std::is_same<VT, float2>::value && S && C &&
+                       b.cols % 2 == 0 && (uintptr_t)S % 16 == 0 && (uintptr_t)C % 16 == 0 &&
+                       (uintptr_t)b.S2 % 16 == 0 && (uintptr_t)x1 % 16 == 0 && (uintptr_t)x2 % 16 == 0;
+    if (b.S2 && !s2_ok) return fail(CAL_EINVAL, "combined block: float32 dense blocks and vectors only");
+    const double bytes = (double)b.rows * b.cols * sizeof(MT) * ((S ? 1 : 0) + (C ? 1 : 0) + (b.S2 ? 1 : 0));
     const int tok = prof_begin(st, "pair_gemv", bytes);
     const bool aligned16 = ((uintptr_t)S % 16 == 0) && ((uintptr_t)C % 16 == 0) &&
                            ((uintptr_t)x1 % 16 == 0) && ((uintptr_t)x2 % 16 == 0);
@@ -1323,9 +1406,14 @@ static int pair_apply_t(const BlockRef& b, const VT* x, VT* y, int64_t n, double
         const int64_t chunk2 = std::min<int64_t>(nc2, 1024);
         const int64_t units = b.rows * ((nc2 + chunk2 - 1) / chunk2);
         const int64_t grid = std::min<int64_t>((units + 7) / 8, (int64_t)nsm * 3);
-        pair_gemv_units_kernel<VT, AT><<<(unsigned)grid, 256, 0, st>>>(
-            reinterpret_cast<const float4*>(S), reinterpret_cast<const float4*>(C), b.rows, nc2,
-            b.cols / 2, chunk2, x1, x2, y1, y2, ar, ai, br, bi);
+        if (b.S2 && S && C)
+          pair_gemv_units_kernel<VT, AT, true><<<(unsigned)std::min<int64_t>(grid, (int64_t)nsm * 2), 256, 0, st>>>(
+              reinterpret_cast<const float4*>(S), reinterpret_cast<const float4*>(C), b.rows, nc2, b.cols / 2,
+              chunk2, x1, x2, y1, y2, ar, ai, br, bi, reinterpret_cast<const float4*>(b.S2));
+        else
+          pair_gemv_units_kernel<VT, AT><<<(unsigned)grid, 256, 0, st>>>(
+              reinterpret_cast<const float4*>(S), reinterpret_cast<const float4*>(C), b.rows, nc2,
+              b.cols / 2, chunk2, x1, x2, y1, y2, ar, ai, br, bi);
         prof_end(st, tok);
         note_launch();
         CAL_TRY_CUDA(cudaGetLastError());

@@ -1,6 +1,7 @@
 // Solver-side internal interfaces (operator application, Gram solves, GMRES).
 #pragma once
 
+#include <complex>
 #include <type_traits>
 #include <vector>
 
@@ -23,6 +24,8 @@ struct BlockRef {
   int precision = CAL_FP64;
   const int64_t* rowptr = nullptr;  // CSR when non-null
   const int* col = nullptr;
+  // combined block (float32 dense, one vector): y1 += C x1 + S x2, y2 += C x2 + S2 x1
+  const void* S2 = nullptr;
   const float* Sh = nullptr;  // split copies for the tensor-core product (float32 dense)
   const float* Sl = nullptr;
   const float* Ch = nullptr;
@@ -44,6 +47,14 @@ int pair_spmv_multi(const BlockRef& b, int vec_prec, const void* x, void* y, int
 int zero_vec(void* y, int prec, int64_t n, cudaStream_t st);
 int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale, cudaStream_t st);
 int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st);
+
+// Combined float32 block of two operator pairs on one set of unknowns:
+// C = Ca + Cb, S1 = aa Sa + ab Sb, S2 = ba Sa + bb Sb, with (Sa, Ca) dense
+// [rows][rows] and (Sb, Cb) [nb][nb] on its diagonal at (off, off). init:
+// first fill C, S1, S2 from (Sa, Ca) alone; Sb == nullptr: no inner block.
+int combine_blocks(const void* Sa, const void* Ca, int64_t rows, std::complex<double> aa, std::complex<double> ba,
+                   const void* Sb, const void* Cb, int64_t nb, int64_t off, std::complex<double> ab,
+                   std::complex<double> bb, void* Co, void* S1, void* S2, bool init, int n_sm, cudaStream_t st);
 
 // check of the bounded grid barrier (see cal_check_grid_barrier)
 int grid_barrier_check(int skip_block, int* status, cudaStream_t st);
