@@ -219,7 +219,8 @@ typedef struct {
   double t_setup, t_assemble_A, t_assemble_P, t_solve;  /* seconds: host time of the
                             spaces (the BC space is built while A is assembled), device time of
                             A's and P's assembly, wall time of the solve                       */
-  int64_t bytes_A, bytes_P; /* device bytes of the stored operators             */
+  int64_t bytes_A, bytes_P; /* device bytes of the stored operators (with the
+                               combined float32 blocks of the one-vector product) */
   int64_t n_unknowns;       /* 2N                                               */
 } cal_solve_info;
 
@@ -258,7 +259,8 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
 typedef struct {
   int64_t n_unknowns;                 /* 2N                                        */
   int32_t n_scatterers, precision, precond;
-  int64_t bytes_A, bytes_P, bytes_G;  /* stored blocks and Gram CSR (device bytes) */
+  int64_t bytes_A, bytes_P, bytes_G;  /* stored blocks (with the combined float32
+                                         blocks) and Gram CSR (device bytes)      */
   int64_t bytes_batch;                /* work vectors and Gram-solver state kept for
                                          the last batch width (0 before a solve)  */
   int32_t batch_width;                /* right-hand sides per lockstep batch       */
