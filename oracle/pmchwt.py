@@ -25,7 +25,9 @@ for interior traces and A^e u^inc = u^inc / 2 for the entire incident field,
 so the total traces u^i = u^s + u^inc solve (A^e + A^i) u^i = u^inc. The
 default system therefore uses b = <u^inc, dual>, and the solution is the
 total (= interior) trace. The paper's scattered-trace form is
-``rhs_mode='scattered'``.
+``rhs_mode='scattered'`` (D^i applied to the L2 projection of u^inc onto
+RWG); its solution is u^s, and the far field of either trace is the same
+(the incident traces radiate nothing outside).
 """
 from __future__ import annotations
 
@@ -268,12 +270,14 @@ class PMCHWT:
         return MP
 
     # ------------------------------------------------------------------
-    def rhs(self, inc):
-        """b for one incident plane wave inc = (d_hat, p_hat) (6 numbers).
+    def _incident_fields(self, inc):
+        """Rule points of every primal triangle and the two incident traces there.
 
-        u^inc = [E^inc x n ; (k_e/mu_e) (d x p) e^{ik_e d.x} x n]; with
-        <a x n, phi> = -int a . phi for tangential phi, tested by the
-        swapped pairing: row (phi_i, 0) takes component 2, (0, phi_i) component 1.
+        u^inc = (E x n, (k_e/mu_e) gamma_N E) with E = p e^{ik_e d.x}: gamma_N E =
+        (1/(ik)) (curl E) x n = (d x p) e^{ik_e d.x} x n.
+        Returns x [nt,q,3], f [nt,q,3,3] (RWG-local functions), weights w |T| [nt,q],
+        E [nt,q,3] and (k_e/mu_e)(d x p) e^{ik_e d.x} [nt,q,3] (fields, not yet crossed
+        with n).
         """
         d = np.asarray(inc[:3], dtype=np.float64)
         p = np.asarray(inc[3:6], dtype=np.float64)
@@ -284,17 +288,76 @@ class PMCHWT:
         x, f = rwg.values(np.arange(nt), bary)             # x [nt,q,3], f [nt,q,3,3]
         ph = np.exp(1j * self.k_e * (x @ d))               # [nt, q]
         wA = w[None, :] * rwg.area[:, None]
-        loc1 = -np.einsum("tq,tq,tqac,c->ta", wA, ph, f, p)
-        loc2 = -(self.k_e / self.mu_e) * np.einsum("tq,tq,tqac,c->ta", wA, ph, f, dxp)
-        b1 = rwg.B @ loc1.reshape(-1)
-        b2 = rwg.B @ loc2.reshape(-1)
-        if self.rhs_mode != "total":
-            raise NotImplementedError("scattered-trace right-hand side")
+        E1 = ph[:, :, None] * p[None, None, :]
+        E2 = (self.k_e / self.mu_e) * ph[:, :, None] * dxp[None, None, :]
+        return x, f, wA, E1, E2
+
+    def _paper_order(self, v1, v2):
+        """Per scatterer [v1_m; v2_m] from two edge-indexed vectors."""
         out = np.zeros(2 * self.N_e, dtype=np.complex128)
         for (a, c) in self.edge_ranges:
             nb = c - a
-            out[2 * a:2 * a + nb] = b2[a:c]
-            out[2 * a + nb:2 * c] = b1[a:c]
+            out[2 * a:2 * a + nb] = v1[a:c]
+            out[2 * a + nb:2 * c] = v2[a:c]
+        return out
+
+    def _tested_incident(self, inc):
+        """<u^inc, dual> in the swapped pairing (paper ordering of the test rows).
+
+        With <a x n, phi> = -int a . phi for tangential phi, the row (phi_i, 0)
+        takes component 2 and (0, phi_i) component 1.
+        """
+        _, f, wA, E1, E2 = self._incident_fields(inc)
+        loc1 = -np.einsum("tq,tqac,tqc->ta", wA, f, E1)
+        loc2 = -np.einsum("tq,tqac,tqc->ta", wA, f, E2)
+        b1 = self.rwg.B @ loc1.reshape(-1)
+        b2 = self.rwg.B @ loc2.reshape(-1)
+        return self._paper_order(b2, b1)
+
+    def incident_coefficients(self, inc):
+        """L2 projection of u^inc onto RWG: paper-ordered coefficients c (reading:
+        the paper applies D^i to u^inc without saying how u^inc enters the
+        discrete space; here it is the L2-orthogonal projection, the Gram matrix
+        being int phi_i . phi_j and the load int phi_i . (field x n))."""
+        rwg = self.rwg
+        _, f, wA, E1, E2 = self._incident_fields(inc)
+        nrm = rwg.normal                                   # [nt, 3]
+        T1 = np.cross(E1, nrm[:, None, :])                 # E x n
+        T2 = np.cross(E2, nrm[:, None, :])
+        l1 = np.einsum("tq,tqac,tqc->ta", wA, f, T1)
+        l2 = np.einsum("tq,tqac,tqc->ta", wA, f, T2)
+        loc = np.einsum("tq,tqac,tqbc->tab", wA, f, f)    # local RT0 mass, exact (degree 2)
+        nt = loc.shape[0]
+        import scipy.sparse as sp
+        rows = np.repeat(np.arange(3 * nt), 3)
+        cols = (3 * np.arange(nt)[:, None, None] + np.arange(3)[None, None, :]).repeat(3, 1).reshape(-1)
+        Lm = sp.csr_matrix((loc.reshape(-1), (rows, cols)), shape=(3 * nt, 3 * nt))
+        Mass = (rwg.B @ Lm @ rwg.B.T).toarray()
+        c1 = np.linalg.solve(Mass, rwg.B @ l1.reshape(-1))
+        c2 = np.linalg.solve(Mass, rwg.B @ l2.reshape(-1))
+        return self._paper_order(c1, c2)
+
+    def rhs(self, inc):
+        """b for one incident plane wave inc = (d_hat, p_hat) (6 numbers).
+
+        total (default): b = <u^inc, dual>; the solution is the total trace.
+        scattered (eq. PMCHWT_multiple_scatterers): b = <(1/2 I - D^i) u^inc, dual>
+        with D^i = diag(A^i_m): the identity term tested exactly, D^i applied to the
+        L2 projection of u^inc onto RWG (``incident_coefficients``); the solution
+        is the scattered trace u^s.
+        """
+        b = self._tested_incident(inc)
+        if self.rhs_mode == "total":
+            return b
+        if self.rhs_mode != "scattered":
+            raise ValueError(self.rhs_mode)
+        if not self._assembled:
+            self.assemble()
+        c = self.incident_coefficients(inc)
+        out = 0.5 * b
+        for m, (a, e) in enumerate(self.edge_ranges):
+            blk = self._block(self.C_i[m], self.S_i[m], self.k_m[m], self.mu_r[m])
+            out[2 * a:2 * e] -= blk @ c[2 * a:2 * e]
         return out
 
     def solve(self, inc, tol=1e-6, restart=200, maxit=2000):
