@@ -30,6 +30,9 @@ problems" (arXiv 2008.04772), step by step, in the paper's notation:
   (Section 4), matvec counting (Table tab:matvecs) and the far field.
 * ``mie``         Mie series of a dielectric sphere (Bohren & Huffman), the
   external pin of the whole solve.
+* ``field``       the electric field at points off the surface from the
+  Stratton–Chu representations (eqs. StrattonChu_int, StrattonChu_ext) with
+  the potential operators of Section 2, for the |E|^2 plots of Section 5.
 
 Where the paper is silent or garbled, the reading taken is stated in the
 function that needs it.
