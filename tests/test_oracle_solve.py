@@ -251,3 +251,23 @@ def test_scattered_and_total_trace_far_fields_agree():
     assert diffs[1] < 1e-2 and diffs[1] < 0.5 * diffs[0], diffs
     Fm = mie.far_field(2.0, 1.0, EPS, dirs)
     assert np.linalg.norm(F["scattered"] - Fm) / np.linalg.norm(Fm) < 0.05
+
+
+def test_three_cube_iterations_near_table2():
+    """The three-cube benchmark of Section 4 at k_e = 2.1 (cube side 0.4, corners
+    at x = -1, 0, 1, n = 1.311 + 2.289e-9 i, E^inc = z e^{ik_e x}, h = 2 pi/(10 k_e),
+    GMRES tol 1e-5, restart 200) with P = D. The paper's mesh has N = 378, ours
+    N = 216, so the comparison with Table 2 is soft: its first rows print 6
+    iterations for q_P = (4,3,2,6) and 7 for (1,1,1,1); the oracle gives 6 and 8."""
+    k = 2.1
+    eps = (1.311 + 2.289e-9j) ** 2
+    inc = np.array([1.0, 0.0, 0.0, 0.0, 0.0, 1.0])
+    m = meshgen.three_cubes(2 * math.pi / (10 * k))
+    its = {}
+    for rules_P in ((6, 4), (1, 1)):
+        pb = pmchwt.PMCHWT(m.verts, m.tris, m.domain, k, eps, precond="D", rules_P=rules_P)
+        pb.assemble()
+        _, info = pb.solve(inc, tol=1e-5, restart=200, maxit=2000)
+        its[rules_P] = info["iterations"]
+    assert 5 <= its[(6, 4)] <= 8 and 6 <= its[(1, 1)] <= 10, its
+    assert its[(1, 1)] >= its[(6, 4)]
