@@ -30,6 +30,8 @@ problems" (arXiv 2008.04772), step by step, in the paper's notation:
   (Section 4), matvec counting (Table tab:matvecs) and the far field.
 * ``mie``         Mie series of a dielectric sphere (Bohren & Huffman), the
   external pin of the whole solve.
+* ``mixed``       the mixed (RWG, BC) discretisation of eq. mixed_discretisation:
+  RWG rewritten on the barycentric mesh, cross blocks C(RWG, BC), C(BC, RWG).
 * ``field``       the electric field at points off the surface from the
   Stratton–Chu representations (eqs. StrattonChu_int, StrattonChu_ext) with
   the potential operators of Section 2, for the |E|^2 plots of Section 5.
