@@ -30,6 +30,9 @@ problems" (arXiv 2008.04772), step by step, in the paper's notation:
   (Section 4), matvec counting (Table tab:matvecs) and the far field.
 * ``mie``         Mie series of a dielectric sphere (Bohren & Huffman), the
   external pin of the whole solve.
+* ``hmatrix``     the H-matrix model of Section 3.3: cluster trees, admissible
+  blocks (disjoint boxes), ACA to a tolerance nu, the block-level cutoff chi
+  (eq. nf_condition); ``pmchwt.PMCHWT(aca_P=(nu, chi))`` applies it to P.
 * ``mixed``       the mixed (RWG, BC) discretisation of eq. mixed_discretisation:
   RWG rewritten on the barycentric mesh, cross blocks C(RWG, BC), C(BC, RWG).
 * ``field``       the electric field at points off the surface from the

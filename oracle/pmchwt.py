@@ -133,7 +133,7 @@ class PMCHWT:
 
     def __init__(self, verts, tris, domain, k_ext, eps_r, mu_r=None,
                  rules_A=(6, 4), rules_P=(6, 4), precond="D", chi_P=math.inf,
-                 rhs_mode="total"):
+                 rhs_mode="total", aca_P=None):
         self.topo = Topology(verts, tris, domain)
         self.M = int(np.max(domain)) + 1
         eps_r = np.atleast_1d(np.asarray(eps_r, dtype=np.complex128))
@@ -153,6 +153,11 @@ class PMCHWT:
             raise ValueError(precond)
         self.precond = precond
         self.chi_P = chi_P
+        # aca_P = (nu_P, chi_P): P's blocks as H-matrices (hmatrix.compress: ACA to
+        # nu_P on admissible blocks within chi_P, Section 3.3) instead of the
+        # entry-level cutoff chi_P
+        self.aca_P = aca_P
+        self.P_stored = None
         self.rhs_mode = rhs_mode
         self.rwg = rwg_space(self.topo)
         self.N_e = self.topo.n_edges
@@ -183,7 +188,7 @@ class PMCHWT:
     def _assemble_P(self):
         bc = self.bc
         self.P_blocks = []
-        mask = bem.near_field_mask(bc, bc, self.chi_P)
+        mask = bem.near_field_mask(bc, bc, math.inf if self.aca_P else self.chi_P)
         pc = self.precond
         for m, (a, b) in enumerate(self.edge_ranges):
             idx = np.arange(a, b)
@@ -197,6 +202,13 @@ class PMCHWT:
                 want = 1 if pc == "Si" else 3
                 S, C = bem.assemble(bc, bc, self.k_m[m], self.rules_P, want=want, rows=idx, cols=idx)
                 blk["S_i"], blk["C_i"] = S * msk, C * msk
+            if self.aca_P:
+                from . import hmatrix
+                nu, chi = self.aca_P
+                keys = sorted(blk)
+                comp, stored = hmatrix.compress([blk[q] for q in keys], bc.aabb_lo[idx], bc.aabb_hi[idx], nu, chi)
+                blk = dict(zip(keys, comp))
+                self.P_stored = (self.P_stored or 0) + stored
             self.P_blocks.append(blk)
         if pc == "A":
             S, C = bem.assemble(bc, bc, self.k_e, self.rules_P)
