@@ -8,14 +8,14 @@
 //   Bt[2j+1][2c] = Im X(c,j), Bt[2j+1][2c+1] = Re X(c,j)
 // give Z[r][2j] = Re (A X)(r,j), Z[r][2j+1] = Im (A X)(r,j).
 //
-// One CTA of 128 threads owns a 128-row tile, all NB (<= 256) columns and a
-// slice of K (split-K, atomic epilogue). Per 32-wide K tile: TMA brings the
-// float32 A and Bt tiles into 128-byte-swizzled shared memory, the threads
-// round them to TF32 in place and write the low parts next to them, one thread issues 3 x 4
-// tcgen05.mma.kind::tf32 (M = 128, N = NB, K = 8) into a TMEM accumulator and
-// commits to an mbarrier that releases the stage. Two stages in flight.
-// Every mbarrier wait is bounded; on timeout the CTA records an error flag,
-// waits (bounded) for its own copies and returns its TMEM.
+// One CTA owns a 128-row tile, a block of at most 128 of the NB columns and a
+// slice of K (split-K, atomic epilogue). Per 32-wide K tile TMA brings the
+// operand tiles into 128-byte-swizzled shared memory and one thread issues
+// 3 x 4 tcgen05.mma.kind::tf32 (M = 128, N = block width, K = 8) into a TMEM
+// accumulator; the partial product of each K tile is read back and summed in
+// registers with round-to-nearest float32 additions (see the kernel). Every
+// mbarrier wait is bounded; on timeout the CTA records an error flag, waits
+// (bounded) for its own copies and MMAs, and returns its TMEM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -31,8 +31,6 @@ namespace {
 
 constexpr int BM = 128;          // rows per CTA (TMEM lanes)
 constexpr int BK = 32;           // float32 per K tile = 128 bytes = one swizzle row
-constexpr int STAGES = 2;
-constexpr int THREADS = 128;
 constexpr unsigned long long WAIT_LIMIT = 1ull << 20;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -116,180 +114,50 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
+// Roles (192 threads): warps 0-3 own TMEM lanes 32w..32w+31 (one output row per
+// thread) and keep the running float32 sums of their row in registers; warp 4
+// lane 0 issues the TMA loads of a ring of stages; warp 5 lane 0 issues the MMAs.
+//
+// The tensor core adds the products of an MMA into its float32 accumulator
+// without rounding to nearest, so a long chain of MMAs into one accumulator
+// drifts (a 7680-column block with 96 K tiles per accumulator chain measured
+// 1.0e-5 relative, 25 times the float32 floor). Here every K tile (3 products
+// x 4 steps of K = 8) starts a fresh accumulator; the four row warps read it
+// with tcgen05.ld and add it to their register sums with ordinary
+// round-to-nearest additions, while the MMAs of the next tiles go into the
+// other accumulators of a ring of up to four. The chain in TMEM is thus 12 MMAs
+// long whatever K is.
+//
+// PRESPLIT: A = Ah + Al and B = Bh + Bl are split beforehand and the producer
+// loads all four tiles. Otherwise the producer loads the float32 A and B tiles
+// into the "h" slots and the row warps round them to TF32 in place and write
+// the low parts beside them before the MMA warp may use the stage.
+constexpr int STAGES = 3;
+constexpr int ROW_THREADS = 128;
+constexpr int THREADS = ROW_THREADS + 64;
+constexpr int MAX_BN = 128;   // columns per CTA: 128 float32 sums per row thread
+constexpr int MAX_ACC = 4;
+
 struct __align__(8) Bars {
-  uint64_t full[STAGES];
-  uint64_t done[STAGES];
+  uint64_t full[STAGES];    // TMA bytes of the stage landed
+  uint64_t ready[STAGES];   // in-kernel split of the stage done (row warps)
+  uint64_t empty[STAGES];   // MMAs reading the stage completed
+  uint64_t accf[MAX_ACC];   // accumulator holds a finished K tile
+  uint64_t acce[MAX_ACC];   // accumulator read out by the four row warps
   uint32_t tmem_base;
   uint32_t fail;
+  int32_t issued;           // K tiles whose loads were issued
+  int32_t committed;        // K tiles whose MMAs were committed
 };
 
-__global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
-    const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float* __restrict__ Z,
-    int64_t M, int NB, int BN, int64_t K, int ktiles_per_cta, int* err) {
-  extern __shared__ __align__(1024) unsigned char smem_raw[];
-  // 1024-byte aligned tiles: per stage Ah [BM][BK], Bh [BN][BK], Al, Bl
-  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const int a_bytes = BM * BK * 4, b_bytes = BN * BK * 4;
-  const int stage_bytes = 2 * (a_bytes + b_bytes);
-  Bars* bars = reinterpret_cast<Bars*>(base + STAGES * stage_bytes);
-  auto Ah = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes); };
-  auto Bh = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + a_bytes); };
-  auto Al = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + a_bytes + b_bytes); };
-  auto Bl = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + 2 * a_bytes + b_bytes); };
-
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int64_t row0 = (int64_t)blockIdx.x * BM;
-  const int64_t ktotal = (K + BK - 1) / BK;
-  const int64_t kt0 = (int64_t)blockIdx.y * ktiles_per_cta;
-  const int64_t nk_full = ktotal - kt0 < (int64_t)ktiles_per_cta ? ktotal - kt0 : (int64_t)ktiles_per_cta;
-  const int nk = nk_full > 0 ? (int)nk_full : 0;
-  if (nk == 0) return;
-  int acc_cols = 32;
-  while (acc_cols < BN) acc_cols <<= 1;
-  // up to 4 accumulators taking the K tiles in turn (at most 256 TMEM columns,
-  // so that two CTAs share an SM): the tensor core adds each MMA step into its
-  // float32 accumulator without a round-to-nearest, so the error grows with the
-  // chain length; the epilogue adds the partial sums
-  const int nacc_max = min(4, 256 / acc_cols) > 1 ? min(4, 256 / acc_cols) : 1;
-  const int nacc = nacc_max < nk ? nacc_max : nk;
-  const int tmem_cols = acc_cols * (nacc <= 1 ? 1 : (nacc <= 2 ? 2 : 4));
-
-  if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&bars->full[s], 1);
-      mbar_init(&bars->done[s], 1);
-    }
-    bars->fail = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&bars->tmem_base)),
-                 "r"(tmem_cols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t tmem = bars->tmem_base;
-  const uint32_t idesc = instr_desc(BN);
-  const unsigned tx_bytes = (unsigned)(a_bytes + b_bytes);
-
-  bool ok = true;
-  if (tid == 0) {
-    mbar_expect_tx(&bars->full[0], tx_bytes);
-    tma_load_2d(Ah(0), &mapA, &bars->full[0], (int)(kt0 * BK), (int)row0);
-    tma_load_2d(Bh(0), &mapB, &bars->full[0], (int)(kt0 * BK), 0);
-  }
-  for (int kt = 0; kt < nk; ++kt) {
-    const int s = kt & 1;
-    if (tid == 0 && kt + 1 < nk) {
-      // stage s^1 is free once the MMAs of tile kt-1 have completed
-      if (kt >= 1 && !mbar_wait(&bars->done[s ^ 1], ((kt - 1) >> 1) & 1)) atomicOr(&bars->fail, 1u);
-      mbar_expect_tx(&bars->full[s ^ 1], tx_bytes);
-      tma_load_2d(Ah(s ^ 1), &mapA, &bars->full[s ^ 1], (int)((kt0 + kt + 1) * BK), (int)row0);
-      tma_load_2d(Bh(s ^ 1), &mapB, &bars->full[s ^ 1], (int)((kt0 + kt + 1) * BK), 0);
-    }
-    if (!mbar_wait(&bars->full[s], (kt >> 1) & 1)) atomicOr(&bars->fail, 1u);
-    __syncthreads();
-    if (bars->fail) { ok = false; break; }
-    // hi (rounded to TF32 in place) and lo parts, same swizzled positions
-    float* ah = Ah(s);
-    float* bh = Bh(s);
-    float* al = Al(s);
-    float* bl = Bl(s);
-    for (int i = tid; i < BM * BK; i += THREADS) {
-      const float x = ah[i], h = tf32_round(x);
-      ah[i] = h;
-      al[i] = x - h;
-    }
-    for (int i = tid; i < BN * BK; i += THREADS) {
-      const float x = bh[i], h = tf32_round(x);
-      bh[i] = h;
-      bl[i] = x - h;
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-      const uint32_t tacc = tmem + (uint32_t)((kt % nacc) * acc_cols);
-      for (int k8 = 0; k8 < BK / 8; ++k8) {
-        const uint64_t a_h = smem_desc(Ah(s) + 8 * k8), b_h = smem_desc(Bh(s) + 8 * k8);
-        const uint64_t a_l = smem_desc(Al(s) + 8 * k8), b_l = smem_desc(Bl(s) + 8 * k8);
-        const uint32_t first = (kt < nacc && k8 == 0) ? 0u : 1u;
-        mma_tf32(tacc, a_h, b_h, idesc, first);
-        mma_tf32(tacc, a_h, b_l, idesc, 1u);
-        mma_tf32(tacc, a_l, b_h, idesc, 1u);
-      }
-      mma_commit(&bars->done[s]);
-    }
-  }
-  // wait for the last MMAs (their commit also covers all earlier ones)
-  if (tid == 0 && ok) {
-    if (!mbar_wait(&bars->done[(nk - 1) & 1], ((nk - 1) >> 1) & 1)) atomicOr(&bars->fail, 1u);
-  }
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!bars->fail) {
-    // epilogue: warp w owns TMEM lanes 32w..32w+31 (rows), 32 columns per load
-    const int64_t row = row0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float sum[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) sum[q] = 0.f;
-      for (int a = 0; a < nacc; ++a) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * acc_cols + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 32; ++q) sum[q] += __uint_as_float(v[q]);
-      }
-      if (row < M) {
-        float* zr = Z + row * NB + c0;
-#pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (c0 + q < NB) atomicAdd(zr + q, sum[q]);
-      }
-    }
-  } else if (tid == 0) {
-    atomicOr(err, 1);
-    // bounded drain of copies that may still be in flight
-    for (int s = 0; s < STAGES; ++s) mbar_wait(&bars->full[s], 0);
-  }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncthreads();
-  if (warp == 0)
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// ---------------------------------------------------------------------------
-// The same product with both operands split beforehand (A = Ah + Al stored
-// once per operator, B = Bh + Bl per call), so no thread touches a tile: one
-// thread issues the TMA loads of a ring of stages, one thread issues the MMAs
-// (3 per K step into up to 4 round-robin accumulators) and commits each stage
-// back to the producer, and all warps run the epilogue. STAGES_S stages of
-// (Ah, Al, Bh, Bl) tiles are in flight.
-// ---------------------------------------------------------------------------
-constexpr int STAGES_S = 3;
+__device__ __forceinline__ bool failed(Bars* b) { return *(volatile uint32_t*)&b->fail != 0; }
 
-struct __align__(8) BarsS {
-  uint64_t full[STAGES_S];
-  uint64_t empty[STAGES_S];
-  uint32_t tmem_base;
-  uint32_t fail;
-  int32_t issued;  // K tiles whose loads were issued
-};
-
-__global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_split_kernel(
+template <bool PRESPLIT>
+__global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
     const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
     const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, float* __restrict__ Z,
     int64_t M, int NB, int BN, int64_t K, int ktiles_per_cta, int* err) {
@@ -297,7 +165,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_split_kernel(
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_bytes = BM * BK * 4, b_bytes = BN * BK * 4;
   const int stage_bytes = 2 * (a_bytes + b_bytes);
-  BarsS* bars = reinterpret_cast<BarsS*>(base + STAGES_S * stage_bytes);
+  Bars* bars = reinterpret_cast<Bars*>(base + STAGES * stage_bytes);
   auto Ah = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes); };
   auto Al = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + a_bytes); };
   auto Bh = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + 2 * a_bytes); };
@@ -305,6 +173,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_split_kernel(
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int64_t row0 = (int64_t)blockIdx.x * BM;
+  const int col0 = blockIdx.z * BN;  // first column of this CTA's column block
   const int64_t ktotal = (K + BK - 1) / BK;
   const int64_t kt0 = (int64_t)blockIdx.y * ktiles_per_cta;
   const int64_t nk_full = ktotal - kt0 < (int64_t)ktiles_per_cta ? ktotal - kt0 : (int64_t)ktiles_per_cta;
@@ -312,17 +181,22 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_split_kernel(
   if (nk == 0) return;
   int acc_cols = 32;
   while (acc_cols < BN) acc_cols <<= 1;
-  const int nacc_max = min(4, 512 / acc_cols) > 1 ? min(4, 512 / acc_cols) : 1;
-  const int nacc = nacc_max < nk ? nacc_max : nk;
-  const int tmem_cols = acc_cols * (nacc <= 1 ? 1 : (nacc <= 2 ? 2 : 4));
+  const int nacc = min(MAX_ACC, 512 / acc_cols);  // 4 for BN <= 128
+  const int tmem_cols = acc_cols * nacc;
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES_S; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&bars->full[s], 1);
+      mbar_init(&bars->ready[s], ROW_THREADS);
       mbar_init(&bars->empty[s], 1);
+    }
+    for (int a = 0; a < MAX_ACC; ++a) {
+      mbar_init(&bars->accf[a], 1);
+      mbar_init(&bars->acce[a], ROW_THREADS);
     }
     bars->fail = 0;
     bars->issued = 0;
+    bars->committed = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -335,91 +209,140 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_split_kernel(
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = bars->tmem_base;
-  const uint32_t idesc = instr_desc(BN);
-  const unsigned tx_bytes = (unsigned)(2 * (a_bytes + b_bytes));
 
-  if (tid == 0) {
-    // producer: stage s is free again once the MMAs of the tile that last used it completed
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES_S;
-      if (kt >= STAGES_S && !mbar_wait(&bars->empty[s], ((kt / STAGES_S) - 1) & 1)) {
-        atomicOr(&bars->fail, 1u);
-        break;
-      }
-      if (*(volatile uint32_t*)&bars->fail) break;
-      const int x = (int)((kt0 + kt) * BK);
-      mbar_expect_tx(&bars->full[s], tx_bytes);
-      tma_load_2d(Ah(s), &mapAh, &bars->full[s], x, (int)row0);
-      tma_load_2d(Al(s), &mapAl, &bars->full[s], x, (int)row0);
-      tma_load_2d(Bh(s), &mapBh, &bars->full[s], x, 0);
-      tma_load_2d(Bl(s), &mapBl, &bars->full[s], x, 0);
-      *(volatile int32_t*)&bars->issued = kt + 1;
-    }
-  } else if (tid == 32) {
-    // MMA issuer
-    int last = -1;  // last tile whose MMAs were committed
-    for (int kt = 0; kt < nk; ++kt) {
-      const int s = kt % STAGES_S;
-      if (!mbar_wait(&bars->full[s], (kt / STAGES_S) & 1)) {
-        atomicOr(&bars->fail, 1u);
-        break;
-      }
-      if (*(volatile uint32_t*)&bars->fail) break;
-      last = kt;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t tacc = tmem + (uint32_t)((kt % nacc) * acc_cols);
+  float acc[MAX_BN];
 #pragma unroll
-      for (int k8 = 0; k8 < BK / 8; ++k8) {
-        const uint64_t a_h = smem_desc(Ah(s) + 8 * k8), b_h = smem_desc(Bh(s) + 8 * k8);
-        const uint64_t a_l = smem_desc(Al(s) + 8 * k8), b_l = smem_desc(Bl(s) + 8 * k8);
-        const uint32_t first = (kt < nacc && k8 == 0) ? 0u : 1u;
-        mma_tf32(tacc, a_h, b_h, idesc, first);
-        mma_tf32(tacc, a_h, b_l, idesc, 1u);
-        mma_tf32(tacc, a_l, b_h, idesc, 1u);
+  for (int q = 0; q < MAX_BN; ++q) acc[q] = 0.f;
+
+  if (warp == 4) {
+    if (lane == 0) {
+      // producer: stage s is free again once the MMAs of the tile that last used it completed
+      const unsigned tx = (unsigned)((PRESPLIT ? 2 : 1) * (a_bytes + b_bytes));
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES;
+        if (kt >= STAGES && !mbar_wait(&bars->empty[s], ((kt / STAGES) - 1) & 1)) {
+          atomicOr(&bars->fail, 1u);
+          break;
+        }
+        if (failed(bars)) break;
+        const int x = (int)((kt0 + kt) * BK);
+        mbar_expect_tx(&bars->full[s], tx);
+        tma_load_2d(Ah(s), &mapAh, &bars->full[s], x, (int)row0);
+        tma_load_2d(Bh(s), &mapBh, &bars->full[s], x, col0);
+        if (PRESPLIT) {
+          tma_load_2d(Al(s), &mapAl, &bars->full[s], x, (int)row0);
+          tma_load_2d(Bl(s), &mapBl, &bars->full[s], x, col0);
+        }
+        *(volatile int32_t*)&bars->issued = kt + 1;
       }
-      mma_commit(&bars->empty[s]);
     }
-    // the commit of the last issued tile covers every earlier MMA; wait for it
-    // (bounded) also after a failure, before the TMEM is returned
-    if (last >= 0 && !mbar_wait(&bars->empty[last % STAGES_S], (last / STAGES_S) & 1)) atomicOr(&bars->fail, 1u);
-    if (last != nk - 1) atomicOr(&bars->fail, 1u);
+  } else if (warp == 5) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(BN);
+      for (int kt = 0; kt < nk; ++kt) {
+        const int s = kt % STAGES, a = kt % nacc, use = kt / nacc;
+        uint64_t* in_bar = PRESPLIT ? &bars->full[s] : &bars->ready[s];
+        if (!mbar_wait(in_bar, (kt / STAGES) & 1) || (use >= 1 && !mbar_wait(&bars->acce[a], (use - 1) & 1))) {
+          atomicOr(&bars->fail, 1u);
+          break;
+        }
+        if (failed(bars)) break;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t tacc = tmem + (uint32_t)(a * acc_cols);
+#pragma unroll
+        for (int k8 = 0; k8 < BK / 8; ++k8) {
+          const uint64_t a_h = smem_desc(Ah(s) + 8 * k8), b_h = smem_desc(Bh(s) + 8 * k8);
+          const uint64_t a_l = smem_desc(Al(s) + 8 * k8), b_l = smem_desc(Bl(s) + 8 * k8);
+          mma_tf32(tacc, a_h, b_h, idesc, k8 == 0 ? 0u : 1u);  // a fresh accumulator per K tile
+          mma_tf32(tacc, a_h, b_l, idesc, 1u);
+          mma_tf32(tacc, a_l, b_h, idesc, 1u);
+        }
+        mma_commit(&bars->empty[s]);
+        mma_commit(&bars->accf[a]);
+        *(volatile int32_t*)&bars->committed = kt + 1;
+      }
+    }
+  } else {
+    // row warps: split the stage (in-kernel variant), then read out the
+    // accumulator of the previous tile and add it to the register sums
+    auto drain = [&](int kt) -> bool {
+      const int a = kt % nacc;
+      // warp-uniform outcome: tcgen05.ld below is a warp-collective instruction
+      if (!__all_sync(0xffffffffu, mbar_wait(&bars->accf[a], (kt / nacc) & 1))) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+      for (int c0 = 0; c0 < MAX_BN; c0 += 32) {
+        if (c0 < BN) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * acc_cols + c0);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int q = 0; q < 32; ++q) acc[c0 + q] += __uint_as_float(v[q]);
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      mbar_arrive(&bars->acce[a]);
+      return true;
+    };
+    bool ok = true;
+    for (int kt = 0; kt < nk && ok; ++kt) {
+      if (!PRESPLIT) {
+        const int s = kt % STAGES;
+        if (!__all_sync(0xffffffffu, mbar_wait(&bars->full[s], (kt / STAGES) & 1))) { ok = false; break; }
+        float* ah = Ah(s);
+        float* bh = Bh(s);
+        float* al = Al(s);
+        float* bl = Bl(s);
+        for (int i = tid; i < BM * BK; i += ROW_THREADS) {
+          const float x = ah[i], h = tf32_round(x);
+          ah[i] = h;
+          al[i] = x - h;
+        }
+        for (int i = tid; i < BN * BK; i += ROW_THREADS) {
+          const float x = bh[i], h = tf32_round(x);
+          bh[i] = h;
+          bl[i] = x - h;
+        }
+        // the generic-proxy writes must be visible to the tensor core's reads
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&bars->ready[s]);
+      }
+      if (kt >= 1 && !drain(kt - 1)) ok = false;
+      if (__any_sync(0xffffffffu, failed(bars))) ok = false;
+    }
+    if (ok && !drain(nk - 1)) ok = false;
+    if (!ok) atomicOr(&bars->fail, 1u);
   }
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!bars->fail) {
-    const int64_t row = row0 + warp * 32 + lane;
-    for (int c0 = 0; c0 < BN; c0 += 32) {
-      float sum[32];
-#pragma unroll
-      for (int q = 0; q < 32; ++q) sum[q] = 0.f;
-      for (int a = 0; a < nacc; ++a) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(a * acc_cols + c0);
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-              "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < 32; ++q) sum[q] += __uint_as_float(v[q]);
-      }
+  if (!failed(bars)) {
+    if (warp < 4) {
+      const int64_t row = row0 + warp * 32 + lane;
       if (row < M) {
-        float* zr = Z + row * NB + c0;
+        float* zr = Z + row * NB + col0;
 #pragma unroll
-        for (int q = 0; q < 32; ++q)
-          if (c0 + q < NB) atomicAdd(zr + q, sum[q]);
+        for (int q = 0; q < MAX_BN; ++q)
+          if (q < BN && col0 + q < NB) atomicAdd(zr + q, acc[q]);
       }
     }
   } else if (tid == 0) {
     atomicOr(err, 1);
-    // bounded drain of the loads that were issued, so no copy lands after exit
+    // bounded drains, so that neither a copy nor an MMA lands after the exit:
+    // the loads that were issued, and the last committed MMA group (its commit
+    // covers every earlier MMA of this thread)
     const int issued = bars->issued;
-    for (int kt = (issued > STAGES_S ? issued - STAGES_S : 0); kt < issued; ++kt)
-      mbar_wait(&bars->full[kt % STAGES_S], (kt / STAGES_S) & 1);
+    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
+      mbar_wait(&bars->full[kt % STAGES], (kt / STAGES) & 1);
+    const int committed = bars->committed;
+    if (committed > 0) mbar_wait(&bars->empty[(committed - 1) % STAGES], ((committed - 1) / STAGES) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -520,6 +443,51 @@ int make_map(CUtensorMap* map, const float* ptr, int64_t inner, int64_t outer, i
   return CAL_OK;
 }
 
+// Launch shape of one product: column blocks of at most MAX_BN columns, and
+// the number of K slices (split-K) that minimises the makespan
+// waves x (K tiles per slice + a fixed per-CTA cost) at one CTA per SM.
+struct GemmPlan {
+  int BN, nz, per;
+  int64_t mt, split;
+};
+
+GemmPlan plan_gemm(int64_t M, int64_t K, int NB, int n_sm) {
+  GemmPlan p;
+  p.BN = NB <= MAX_BN ? NB : 16 * ((NB + 31) / 32);
+  p.nz = (NB + p.BN - 1) / p.BN;
+  p.mt = (M + BM - 1) / BM;
+  const int64_t ktotal = (K + BK - 1) / BK;
+  const int64_t base = p.mt * p.nz;
+  const int64_t sm = std::max(1, n_sm);
+  int64_t best_split = 1, best_cost = INT64_MAX;
+  const int64_t max_split = std::min<int64_t>(ktotal, std::max<int64_t>(1, 8 * sm / base + 1));
+  for (int64_t sp = 1; sp <= max_split; ++sp) {
+    const int64_t per = (ktotal + sp - 1) / sp, used = (ktotal + per - 1) / per;
+    const int64_t waves = (base * used + sm - 1) / sm;
+    const int64_t cost = waves * (per + 8);
+    if (cost < best_cost) { best_cost = cost; best_split = used; }
+  }
+  p.per = (int)((ktotal + best_split - 1) / best_split);
+  p.split = (ktotal + p.per - 1) / p.per;
+  return p;
+}
+
+template <bool PRESPLIT>
+int launch_gemm(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUtensorMap& mBh, const CUtensorMap& mBl,
+                const GemmPlan& p, int64_t M, int64_t K, int NB, float* Z, int* d_err, cudaStream_t st) {
+  const int smem = STAGES * 2 * (BM * BK * 4 + p.BN * BK * 4) + (int)sizeof(Bars) + 1024;
+  if (smem > 227 * 1024) return fail(CAL_EINVAL, "gemm: %d columns do not fit the pipeline", p.BN);
+  if (int rc = ensure_dyn_smem((const void*)gemm_tf32x3_kernel<PRESPLIT>, smem)) return rc;
+  CAL_TRY_CUDA(cudaMemsetAsync(Z, 0, (size_t)M * NB * sizeof(float), st));
+  const int tok = prof_begin(st, "gemm_tc", 2.0 * 3.0 * (double)M * K * NB);
+  gemm_tf32x3_kernel<PRESPLIT><<<dim3((unsigned)p.mt, (unsigned)p.split, (unsigned)p.nz), THREADS, smem, st>>>(
+      mAh, mAl, mBh, mBl, Z, M, NB, p.BN, K, p.per, d_err);
+  prof_end(st, tok);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
 }  // namespace
 
 bool gemm_tc_supported(int64_t cols, int nrhs) {
@@ -528,29 +496,17 @@ bool gemm_tc_supported(int64_t cols, int nrhs) {
   return (cols % 2 == 0) && nrhs >= 1 && 4 * nrhs <= 256;
 }
 
-// Z[M][NB] = A[M][K] Bt[NB][K]^T (Z is zeroed here), float32 via 3xTF32
+// Z[M][NB] = A[M][K] Bt[NB][K]^T (Z is zeroed here), float32 via 3xTF32 with
+// the split into TF32 parts done in the kernel
 int gemm_tf32x3(const float* A, int64_t M, int64_t K, const float* Bt, int NB, float* Z, int* d_err,
                 int n_sm, cudaStream_t st) {
   if (NB < 16 || NB > 256 || NB % 16) return fail(CAL_EINVAL, "gemm: NB must be a multiple of 16 in [16, 256]");
   if ((uintptr_t)A % 16 || (uintptr_t)Bt % 16 || (K * 4) % 16) return fail(CAL_EINVAL, "gemm: operands not 16-byte aligned");
+  const GemmPlan p = plan_gemm(M, K, NB, n_sm);
   CUtensorMap mA, mB;
   int rc;
-  if ((rc = make_map(&mA, A, K, M, BM))) return rc;
-  if ((rc = make_map(&mB, Bt, K, NB, NB))) return rc;
-  CAL_TRY_CUDA(cudaMemsetAsync(Z, 0, (size_t)M * NB * sizeof(float), st));
-  const int64_t mt = (M + BM - 1) / BM;
-  const int64_t ktotal = (K + BK - 1) / BK;
-  int64_t split = std::max<int64_t>(1, std::min<int64_t>(ktotal, (2 * (int64_t)n_sm + mt - 1) / mt));
-  const int per = (int)((ktotal + split - 1) / split);
-  split = (ktotal + per - 1) / per;
-  const int smem = STAGES * 2 * (BM * BK * 4 + NB * BK * 4) + (int)sizeof(Bars) + 1024;
-  if (int rc = ensure_dyn_smem((const void*)gemm_tf32x3_kernel, smem)) return rc;
-  const int tok = prof_begin(st, "gemm_tc", 2.0 * 3.0 * (double)M * K * NB);
-  gemm_tf32x3_kernel<<<dim3((unsigned)mt, (unsigned)split), THREADS, smem, st>>>(mA, mB, Z, M, NB, NB, K, per, d_err);
-  prof_end(st, tok);
-  note_launch();
-  CAL_TRY_CUDA(cudaGetLastError());
-  return CAL_OK;
+  if ((rc = make_map(&mA, A, K, M, BM)) || (rc = make_map(&mB, Bt, K, NB, p.BN))) return rc;
+  return launch_gemm<false>(mA, mA, mB, mB, p, M, K, NB, Z, d_err, st);
 }
 
 int split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
@@ -568,28 +524,13 @@ int gemm_tf32x3_split(const float* Ah, const float* Al, int64_t M, int64_t K, co
   for (const float* p : {Ah, Al, Bh, Bl})
     if ((uintptr_t)p % 16) return fail(CAL_EINVAL, "gemm: operands not 16-byte aligned");
   if ((K * 4) % 16) return fail(CAL_EINVAL, "gemm: rows not 16-byte aligned");
+  const GemmPlan p = plan_gemm(M, K, NB, n_sm);
   CUtensorMap mAh, mAl, mBh, mBl;
   int rc;
   if ((rc = make_map(&mAh, Ah, K, M, BM)) || (rc = make_map(&mAl, Al, K, M, BM)) ||
-      (rc = make_map(&mBh, Bh, K, NB, NB)) || (rc = make_map(&mBl, Bl, K, NB, NB)))
+      (rc = make_map(&mBh, Bh, K, NB, p.BN)) || (rc = make_map(&mBl, Bl, K, NB, p.BN)))
     return rc;
-  CAL_TRY_CUDA(cudaMemsetAsync(Z, 0, (size_t)M * NB * sizeof(float), st));
-  const int64_t mt = (M + BM - 1) / BM;
-  const int64_t ktotal = (K + BK - 1) / BK;
-  const int smem = STAGES_S * 2 * (BM * BK * 4 + NB * BK * 4) + (int)sizeof(BarsS) + 1024;
-  if (smem > 227 * 1024) return fail(CAL_EINVAL, "gemm: %d columns do not fit the split-operand pipeline", NB);
-  if (int rc2 = ensure_dyn_smem((const void*)gemm_tf32x3_split_kernel, smem)) return rc2;
-  // one CTA per SM; about two waves of (row tile, K slice) units
-  int64_t split = std::max<int64_t>(1, std::min<int64_t>(ktotal, (2 * (int64_t)n_sm + mt - 1) / mt));
-  const int per = (int)((ktotal + split - 1) / split);
-  split = (ktotal + per - 1) / per;
-  const int tok = prof_begin(st, "gemm_tc", 2.0 * 3.0 * (double)M * K * NB);
-  gemm_tf32x3_split_kernel<<<dim3((unsigned)mt, (unsigned)split), THREADS, smem, st>>>(mAh, mAl, mBh, mBl, Z, M, NB,
-                                                                                      NB, K, per, d_err);
-  prof_end(st, tok);
-  note_launch();
-  CAL_TRY_CUDA(cudaGetLastError());
-  return CAL_OK;
+  return launch_gemm<true>(mAh, mAl, mBh, mBl, p, M, K, NB, Z, d_err, st);
 }
 
 template <typename VT>

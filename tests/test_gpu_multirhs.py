@@ -37,28 +37,36 @@ def _product(ctx, name, nrhs, which, seed=0, with_f32=False):
     return y, yr
 
 
-@pytest.mark.parametrize("nrhs", [4, 5, 8, 32, 64])
+@pytest.mark.parametrize("nrhs", [4, 5, 8, 32, 64, 127])
 @pytest.mark.parametrize("which", [cal.OP_S, cal.OP_C])
 def test_tensor_core_product_matches_float64(ctx, nrhs, which):
-    # 3xTF32 keeps float32 accuracy: relative error of the product ~1e-6
-    y, yr = _product(ctx, "sphere2", nrhs, which)
-    assert rel(y, yr) < 1e-5
+    # 3xTF32 with round-to-nearest sums of the per-K-tile partial products keeps
+    # float32 accuracy: within 3x the error of a float32 GEMM of the same data
+    y, yr, y32 = _product(ctx, "sphere2", nrhs, which, with_f32=True)
+    floor = rel(y32, yr)
+    assert rel(y, yr) < max(3 * floor, 1e-6), (rel(y, yr), floor)
     # every column, not only the aggregate
     for j in range(nrhs):
-        assert rel(y[j], yr[j]) < 2e-5
+        assert rel(y[j], yr[j]) < max(3 * rel(y32[j], yr[j]), 2e-6), j
 
 
 def test_tensor_core_product_full_size(ctx):
     # 7680 x 7680 block, 32 vectors (the multi-RHS shape of the solve): each
-    # entry is a 15360-term sum. The tensor-core accumulator adds each K=8 MMA
-    # step into float32 without the round-to-nearest of a scalar FMA chain, so
-    # its error grows with the ~320 steps one CTA accumulates (measured 1.0e-5,
-    # against 3.9e-7 for numpy's blocked complex64 GEMM of the same data); the
-    # bar is the float32-path bar of the assembled blocks divided by 5.
+    # entry is a 15360-term sum. The tensor core adds MMA products into its
+    # float32 accumulator without rounding to nearest, so the kernel starts a
+    # fresh accumulator every K tile and sums the tiles in registers; the
+    # product must stay within 3x the error of a float32 GEMM of the same data.
     y, yr, y32 = _product(ctx, "sphere4", 32, cal.OP_S, seed=3, with_f32=True)
     floor = rel(y32, yr)
     assert floor < 2e-6
-    assert rel(y, yr) < 2e-5, (rel(y, yr), floor)
+    assert rel(y, yr) < max(3 * floor, 1e-6), (rel(y, yr), floor)
+
+
+def test_tensor_core_product_full_size_wide(ctx):
+    # 128 vectors: 256 real columns, two column blocks of the kernel
+    y, yr, y32 = _product(ctx, "sphere4", 128, cal.OP_C, seed=4, with_f32=True)
+    floor = rel(y32, yr)
+    assert rel(y, yr) < max(3 * floor, 1e-6), (rel(y, yr), floor)
 
 
 def test_lockstep_solve_equals_solo_solves(ctx):
