@@ -42,8 +42,9 @@ WORKLOAD = {"name": "sphere5120_k5_D_dense", "level": 4, "k": 5.0, "eps": 3.17 +
 # default orders (4, 3, 2); 6 = the 6-point rule for every regular pair
 Q = dict(q_regular_A=0, q_regular_P=0)
 METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5)"
-# dram__bytes_read.sum + dram__bytes_write.sum of one bc_tile launch (exterior pass of
-# the workload), from the ncu capture summarised in profiles/; None once the kernel changes
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the float32 BC-pair
+# kernel (exterior pass of the workload) from one ncu capture; None once the kernel
+# has changed since the counters were taken
 BC_TILE_TRAFFIC = 3.731466e9 + 4.173925e9
 
 
@@ -288,8 +289,8 @@ def run_ours(args, rank, world):
         "roofline": {"bound": "alu", "kernel": "bc_owner_kernel<0,128,true>",
                      "achieved": achieved / 1e9, "peak": peak / 1e9, "unit": "Geval/s",
                      "frac": achieved / peak if peak else None, "traffic": BC_TILE_TRAFFIC,
-                     "traffic_note": "dram read+write bytes of one exterior launch, one ncu capture "
-                                     "(profiles/bc_owner_kernel_sphere5120.md); the per-launch work is "
+                     "traffic_note": "dram read+write bytes of one exterior launch, one ncu capture; "
+                                     "the per-launch work is "
                                      f"{bc['units'] / max(bc['launches'], 1) / 1e9:.1f} G evaluations",
                      "peak_source": f"derived: {n_sm} SMs x 3.05 eval/clk x {sm_max:.0f} MHz"},
         "clocks": clocks,
@@ -666,12 +667,69 @@ def run_reference(args, rank, world):
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def run_case(which: str) -> None:
+    """One profiling case on the 5120-triangle sphere (k = 5), with the bench's
+    regular rules (near / medium / far classes at the paper's default orders 4, 3, 2):
+      bc    one dense FP32 assembly of S and C on the Buffa–Christiansen space
+            (the BC-pair kernel and the split Sauter–Schwab kernel);
+      gemv  an unpreconditioned FP32 solve capped at 3 GMRES iterations (the PMCHWT
+            GEMV launches on the stored A blocks);
+      gemm  the tensor-core product of the stored 7680 x 7680 complex64 S block with
+            32 vectors (cal_matvec, 3xTF32 on tcgen05), three times;
+      free  three FP32 GMRES iterations with the matrix-free PMCHWT operator;
+      solve one complete solve of the bench workload (FP32 bulk, full D, tol 1e-5);
+      multi one FP32 solve of 32 incident directions with the near-field reduced
+            preconditioner Di (chi = 2h).
+    """
+    import torch
+
+    from paper_2008_04772_gb300 import build, cal, meshgen
+    build.build()
+    ctx = cal.Context(0)
+    m = meshgen.icosphere(4)
+    mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    k, eps, inc = 5.0, 3.17 + 0.01j, meshgen.plane_wave_x_along_z()
+    if which == "bc":
+        bc = cal.Space(mesh, cal.BC)
+        cal.assemble(ctx, cal.OP_S | cal.OP_C, k, bc, q_regular=0, precision=cal.FP32)
+    elif which == "gemm":
+        op = cal.assemble(ctx, cal.OP_S, k, cal.Space(mesh, cal.RWG), precision=cal.FP32)
+        n = op.info().cols
+        x = torch.randn((32, 2 * n), dtype=torch.float32, device="cuda")
+        y = torch.zeros((32, 2 * n), dtype=torch.float32, device="cuda")
+        torch.cuda.synchronize()
+        for _ in range(3):
+            op.matvec(cal.OP_S, x.data_ptr(), y.data_ptr(), nrhs=32)
+        torch.cuda.synchronize()
+    elif which == "free":
+        cal.pmchwt_solve(ctx, mesh, k, eps, inc, allow_not_converged=True,
+                         opts=cal.solve_opts(precond="none", precision=cal.FP32, maxit=3, refine=0,
+                                             matrix_free=1, q_regular_A=0))
+    elif which == "gemv":
+        cal.pmchwt_solve(ctx, mesh, k, eps, inc, allow_not_converged=True,
+                         opts=cal.solve_opts(precond="none", precision=cal.FP32, maxit=3, refine=0))
+    elif which == "multi":
+        d = meshgen.fibonacci_directions(32)
+        cal.pmchwt_solve(ctx, mesh, k, eps, np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1),
+                         opts=cal.solve_opts(precond="Di", near_cutoff_P=2.0, precision=cal.FP32, tol=1e-5, **Q))
+    elif which == "solve":
+        sol = cal.pmchwt_solve(ctx, mesh, k, eps, inc,
+                               opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-5, **Q))
+        sol.far_field(meshgen.sphere_cut_directions(181))
+    else:
+        raise SystemExit(f"unknown case {which!r}")
+    torch.cuda.synchronize()
+    print("case done:", which)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", default=None, choices=["bc", "gemv", "gemm", "free", "solve", "multi"],
+                    help="run one profiling case and exit (no JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=24, help="test triangles per space for the oracle sample")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
@@ -683,6 +741,9 @@ def main():
     ap.add_argument("--no-matrix-free", dest="matrix_free", action="store_false",
                     help="skip the stored versus matrix-free comparison")
     args = ap.parse_args()
+    if args.case:
+        run_case(args.case)
+        return
     world = _env_int("WORLD_SIZE", 1)
     rank = _env_int("RANK", 0)
     if world > 1 and args.impl == "ours":

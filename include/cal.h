@@ -56,8 +56,12 @@ extern "C" {
 #define CAL_OP_C 2         /* magnetic operator C = gamma_D H (Section 2)          */
 
 #define CAL_FP64 1         /* all assembly and storage in float64 (complex128)    */
-#define CAL_FP32 2         /* regular pairs in float32, singular pairs in float64,
-                              storage complex64 ("FP32 bulk")                      */
+#define CAL_FP32 2         /* "FP32 bulk": regular pairs in float32; singular
+                              (Sauter-Schwab) pairs split into the static kernel
+                              parts 1/(4 pi r), -1/(4 pi r^3), summed in
+                              double-float (pairs of floats, ~2^-46 relative),
+                              and the smooth remainder in float32; storage
+                              complex64                                          */
 #define CAL_FP32_ALL 3     /* regular and singular pairs in float32 (singular point
                               differences formed in reference coordinates, so no
                               cancellation), storage complex64                     */
@@ -165,7 +169,8 @@ int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int6
    the op's precision, both device pointers; enqueued on `stream`
    (cudaStream_t, NULL = the context stream). For a float32 dense operator and
    4 <= nrhs <= 128 vectors (even cols) the product runs on the tensor cores
-   as a 3xTF32 GEMM (float32 accuracy; the first such call keeps the TF32 part
+   as a 3xTF32 GEMM (float32 accuracy: each 32-wide K tile's partial product is
+   summed in registers with round-to-nearest; the first such call keeps the TF32 part
    and the float32 remainder of the operator with it, twice its size);
    otherwise one GEMV/SpMV per vector. */
 int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
@@ -180,10 +185,15 @@ int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs
    16*ceil(ceil(nrhs/2)/4), plus (nrhs+1)*cols*8 for odd nrhs, plus a flag
    (each part rounded up to 256 bytes): a 7680 x 7680 block fits every nrhs up
    to 128. Larger requests return CAL_EINVAL, with the sizes in
-   cal_last_error(), before any GPU work. All calls share the array: calls whose GPU
-   work overlaps (other streams, other host threads) race on it and must be
-   serialised by the caller. Returns after the product has completed on
-   `stream`; CAL_ETIMEOUT if a bounded wait of the product gave up. */
+   cal_last_error(), before any GPU work. x and y must be device memory of the
+   operator's device (CAL_EINVAL otherwise). All calls share the array: calls
+   whose GPU work overlaps (other streams, other host threads) race on it and
+   must be serialised by the caller. The first call on a device looks up the
+   array's device address (cudaGetSymbolAddress) and keeps it, so make that
+   first call before any stream capture, and do not use the library across a
+   cudaDeviceReset. The caller's current device is unchanged on return.
+   Returns after the product has completed on `stream`; CAL_ETIMEOUT if a
+   bounded wait of the product gave up. */
 #define CAL_MATVEC_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 #define CAL_MATVEC_STATIC_MAX_NRHS 128
 int cal_matvec_static(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);

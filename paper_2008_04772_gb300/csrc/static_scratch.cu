@@ -29,8 +29,10 @@ static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 std::mutex g_scratch_mu;
 void* g_scratch_base[kMaxDevices] = {};
 
-// Device address of g_scratch on `device`, looked up once per device with that
-// device current (the caller has made it current).
+// Device address of g_scratch on `device`, looked up on the first call on that
+// device with the device current (the caller has made it current) and kept for
+// the life of the process: a cudaDeviceReset of that device would leave the
+// kept address stale, so the library is not to be used across one.
 int scratch_base(int device, unsigned char** out) {
   if (device < 0 || device >= kMaxDevices) return fail(CAL_EINVAL, "static scratch: device %d out of range", device);
   std::lock_guard<std::mutex> lock(g_scratch_mu);
@@ -85,7 +87,6 @@ extern "C" int cal_matvec_static(const cal_op* op, int which, const void* x, voi
                 "cal_matvec_static: %lld x %lld operator with %d vectors needs %zu scratch bytes, above the "
                 "fixed maximum of %zu",
                 (long long)rows, (long long)cols, n, need, kScratchBytes);
-  CAL_TRY_CUDA(cudaSetDevice(o.ctx->device));
   cudaPointerAttributes ax{}, ay{};
   if (cudaPointerGetAttributes(&ax, x) != cudaSuccess || cudaPointerGetAttributes(&ay, y) != cudaSuccess ||
       (ax.type != cudaMemoryTypeDevice && ax.type != cudaMemoryTypeManaged) ||
@@ -93,6 +94,17 @@ extern "C" int cal_matvec_static(const cal_op* op, int which, const void* x, voi
     cudaGetLastError();
     return fail(CAL_EINVAL, "cal_matvec_static: x and y must be device pointers");
   }
+  if ((ax.type == cudaMemoryTypeDevice && ax.device != o.ctx->device) ||
+      (ay.type == cudaMemoryTypeDevice && ay.device != o.ctx->device))
+    return fail(CAL_EINVAL, "cal_matvec_static: x and y must be on the operator's device %d", o.ctx->device);
+  // the caller's current device is put back on every return path
+  int prev_device = -1;
+  CAL_TRY_CUDA(cudaGetDevice(&prev_device));
+  struct Restore {
+    int dev;
+    ~Restore() { if (dev >= 0) cudaSetDevice(dev); }
+  } restore{prev_device};
+  CAL_TRY_CUDA(cudaSetDevice(o.ctx->device));
   unsigned char* base;
   int rc = scratch_base(o.ctx->device, &base);
   if (rc) return rc;
