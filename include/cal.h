@@ -214,7 +214,13 @@ typedef struct {
   int32_t restart;          /* GMRES restart (paper: 200)                       */
   int32_t maxit;            /* iteration cap                                    */
   int32_t refine;           /* FP32 path: outer FP64 iterative refinement steps */
-  int32_t rhs_mode;         /* 0 = total traces (A^e + A^i) u = u^inc           */
+  int32_t rhs_mode;         /* 0 = total traces (A^e + A^i) u = u^inc; 1 = the
+                               paper's scattered traces (eq.
+                               PMCHWT_multiple_scatterers): (A^e + A^i) u^s =
+                               (1/2 I - D^i) u^inc, D^i = diag(A^i_m) applied to
+                               the L2 projection of u^inc onto RWG (mass matrix
+                               int phi_i.phi_j, loads int phi_i.(field x n)); the
+                               solution holds u^s, with the same far field        */
   int32_t matrix_free;      /* 1: A is not stored; its regular pairs are
                                recomputed in every application (only the
                                touching-pair entries are kept, sparse)          */
@@ -247,6 +253,22 @@ int cal_solution_coefficients(const cal_solution* sol, double* dst_host);
 /* Far-field pattern E_inf(x_hat), E^s ~ E_inf e^{ik r}/r, for unit directions
    dirs [ndir][3]: out [nrhs][ndir][3] complex128 (host). */
 int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, double* out);
+/* Total electric field at points off the surface (the |E|^2 maps of Section 5),
+   from the Stratton–Chu representations (eqs. StrattonChu_int, StrattonChu_ext)
+   with the potential operators E_k, H_k of Section 2:
+     exterior:       E = E^inc - [H_ke(u_1) + E_ke((mu_e/k_e) u_2)] over all surfaces,
+     inside Gamma_m: E = H_km(u_1) + E_km((mu_m/k_m) u_2) over Gamma_m,
+   with the solution's total traces (a scattered-trace solution, rhs_mode 1,
+   adds the L2 projection of u^inc it was built from). points [npt][3];
+   levels 0..4: each triangle is split into 4^levels congruent sub-triangles
+   with the 6-point rule on each (points should stay a few sub-triangle sizes
+   away from the surface); region_in [npt] (-1 exterior, m inside Gamma_m) or
+   NULL to take each point's region from the winding numbers of the closed
+   meshes; region_out [npt] (may be NULL) receives the regions used.
+   out [nrhs][npt][3] complex128 (host). Evaluated in float32 for float32-bulk
+   solutions, float64 for CAL_FP64 ones. */
+int cal_near_field(const cal_solution* sol, const double* points, int64_t npt, int levels,
+                   const int32_t* region_in, int32_t* region_out, double* out);
 void cal_solution_destroy(cal_solution* sol);
 
 /* ---- resident problems --------------------------------------------------- */

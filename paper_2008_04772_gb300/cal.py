@@ -137,6 +137,7 @@ def lib():
         "cal_op_export": ([P, ctypes.c_int, P, P, P], ctypes.c_int),
         "cal_matvec": ([P, ctypes.c_int, P, P, i64, P], ctypes.c_int),
         "cal_matvec_static": ([P, ctypes.c_int, P, P, i64, P], ctypes.c_int),
+        "cal_near_field": ([P, P, i64, ctypes.c_int, P, P, P], ctypes.c_int),
         "cal_gram_export": ([P, P, P], ctypes.c_int),
         "cal_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
         "cal_pmchwt_solve": ([P, P, d, P, P, P, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(P)],
@@ -332,6 +333,16 @@ class Solution:
         out = np.zeros((self.nrhs, len(d), 3), dtype=np.complex128)
         _check(lib().cal_farfield(self.h, _ptr(d), len(d), _ptr(out)))
         return out
+
+    def near_field(self, points, levels: int = 2, region=None):
+        """Total E at points off the surface: ([nrhs][npt][3] complex, regions [npt])."""
+        p = np.ascontiguousarray(np.atleast_2d(points), dtype=np.float64)
+        out = np.zeros((self.nrhs, len(p), 3), dtype=np.complex128)
+        reg_out = np.zeros(len(p), dtype=np.int32)
+        reg_in = None if region is None else np.ascontiguousarray(region, dtype=np.int32)
+        _check(lib().cal_near_field(self.h, _ptr(p), len(p), int(levels),
+                                    None if reg_in is None else _ptr(reg_in), _ptr(reg_out), _ptr(out)))
+        return out, reg_out
 
     def __del__(self):
         if getattr(self, "h", None):

@@ -349,11 +349,20 @@ struct cal_solution {
   Ctx* ctx = nullptr;
   std::shared_ptr<Space> rwg;  // shared with the problem it came from
   double2* d_x = nullptr;  // [nrhs][2N]
+  // rhs_mode 1: the L2 projection of u^inc onto RWG [nrhs][2N], so that the total
+  // trace is d_x + d_cinc (the interior representation needs total traces)
+  double2* d_cinc = nullptr;
   int64_t nrhs = 0, ne = 0;
   double k_e = 0.0, mu_e = 1.0;
+  std::vector<std::complex<double>> k_m, mu_m;  // per scatterer
+  std::vector<double> inc;                      // [nrhs][6] incident plane waves
+  int rhs_mode = 0;
   int precision = CAL_FP64;  // of the solve: float32 bulk evaluates its far field in float32
   cal_solve_info info{};
-  ~cal_solution() { dfree(d_x, nullptr); }  // far-field and copy calls are synchronous
+  ~cal_solution() {  // far-field and copy calls are synchronous
+    dfree(d_x, nullptr);
+    dfree(d_cinc, nullptr);
+  }
 };
 
 namespace {
@@ -379,6 +388,13 @@ struct Pmchwt {
   int64_t gnnz = 0;
   std::unique_ptr<GramSolver<float>> gsA32, gsP32;
   std::unique_ptr<GramSolver<double>> gsA64, gsP64;
+  // RWG mass matrix (int phi_i . phi_j) and its solver, for the L2 projection of
+  // u^inc in the scattered-trace right-hand side; built on first use
+  int64_t* d_mrp = nullptr;
+  int* d_mcol = nullptr;
+  double* d_mval = nullptr;
+  int64_t mnnz = 0;
+  std::unique_ptr<GramSolver<double>> gsM;
   // batch of right-hand sides advanced in lockstep
   int nb = 1;
   // work vectors [nb][2N] (complex128-sized)
@@ -409,7 +425,7 @@ struct Pmchwt {
     cudaStream_t st = nullptr;  // every solve has completed: the legacy stream orders the release
     for (void* p : {(void*)d_grp, (void*)d_gcol, (void*)d_grpT, (void*)d_gcolT, (void*)d_gval, (void*)d_gvalT, t1,
                     t2, (void*)d_gath, d_xt, (void*)d_Bt, (void*)d_Bh, (void*)d_Bl, (void*)d_ZS, (void*)d_ZC,
-                    (void*)d_gemm_err})
+                    (void*)d_gemm_err, (void*)d_mrp, (void*)d_mcol, (void*)d_mval})
       dfree(p, st);
     free_combo(cA);
     for (auto& c : cP) free_combo(c);
@@ -639,6 +655,91 @@ struct Pmchwt {
     }
     matvecs += (4LL * M * M + 4LL * M) * nrhs;
     return CAL_OK;
+  }
+
+  // y = A^i x = diag(A^i_m) x, the interior blocks only (y overwritten)
+  int apply_Ai(const void* x, void* y, int vec_prec, int nrhs) {
+    cudaStream_t st = ctx->stream;
+    int rc = zero_vec(y, vec_prec, 2 * N * nrhs, st);
+    if (rc) return rc;
+    for (int m = 0; m < M; ++m) {
+      const std::complex<double> am = mu_m[m] / k_m[m], bm = -k_m[m] / mu_m[m];
+      if ((rc = apply_block(ref(*A_int[m]), x, y, vec_prec, nrhs, am, bm))) return rc;
+      if (o.matrix_free &&
+          (rc = launch_rwg_free(*rwg, m, k_m[m].real(), k_m[m].imag(), o.q_regular_A, o.precision, vec_prec, x, y,
+                                N, nrhs, am.real(), am.imag(), bm.real(), bm.imag(), st)))
+        return rc;
+    }
+    return CAL_OK;
+  }
+
+  // RWG mass matrix on the device: the pattern holds every pair of edges of one
+  // triangle, the values come from one kernel
+  int build_mass() {
+    if (d_mval) return CAL_OK;
+    cudaStream_t st = ctx->stream;
+    const Space& sp = *rwg;
+    std::vector<std::vector<int>> rows(N);
+    for (int64_t t = 0; t < sp.ntri; ++t)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          const int ea = sp.slot_edge[3 * t + a], eb = sp.slot_edge[3 * t + b];
+          if (ea >= 0 && eb >= 0) rows[ea].push_back(eb);
+        }
+    std::vector<int64_t> rp(N + 1, 0);
+    std::vector<int> col;
+    for (int64_t i = 0; i < N; ++i) {
+      std::sort(rows[i].begin(), rows[i].end());
+      rows[i].erase(std::unique(rows[i].begin(), rows[i].end()), rows[i].end());
+      col.insert(col.end(), rows[i].begin(), rows[i].end());
+      rp[i + 1] = (int64_t)col.size();
+    }
+    mnnz = (int64_t)col.size();
+    CAL_TRY_CUDA(dalloc((void**)&d_mrp, (N + 1) * sizeof(int64_t), st));
+    CAL_TRY_CUDA(dalloc((void**)&d_mcol, std::max<int64_t>(mnnz, 1) * sizeof(int), st));
+    CAL_TRY_CUDA(dalloc((void**)&d_mval, std::max<int64_t>(mnnz, 1) * sizeof(double), st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(d_mrp, rp.data(), (N + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(d_mcol, col.data(), mnnz * sizeof(int), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemsetAsync(d_mval, 0, mnnz * sizeof(double), st));
+    int rc = launch_rwg_mass(sp, d_mrp, d_mcol, d_mval, st);
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));  // the host pattern is read by the copies
+    return rc;
+  }
+
+  // The paper's scattered-trace right-hand side (eq. PMCHWT_multiple_scatterers):
+  // b = (1/2 I - D^i) u^inc tested, D^i = diag(A^i_m). The identity term is the
+  // exactly tested incident trace (b_tot, the total-trace right-hand side, on
+  // entry); D^i acts on the L2 projection c of u^inc onto RWG (mass matrix
+  // int phi_i . phi_j, loads int phi_i . (field x n)). b [nrhs][2N] is replaced by
+  // b_tot / 2 - A^i c; c [nrhs][2N] is kept (the incident part of the total
+  // trace). Batches of nb right-hand sides.
+  int scattered_rhs(const double* d_inc, int64_t nrhs, double2* b, double2* c) {
+    cudaStream_t st = ctx->stream;
+    int rc;
+    if ((rc = build_mass())) return rc;
+    const int64_t n2 = 2 * N;
+    double2* load = nullptr;
+    double2* y = nullptr;
+    CAL_TRY_CUDA(dalloc((void**)&load, (size_t)nb * n2 * sizeof(double2), st));
+    if (dalloc((void**)&y, (size_t)nb * n2 * sizeof(double2), st) != cudaSuccess) {
+      dfree(load, st);
+      return fail(CAL_ENOMEM, "scattered right-hand side: cannot allocate work vectors");
+    }
+    for (int64_t q0 = 0; q0 < nrhs && !rc; q0 += nb) {
+      const int nq = (int)std::min<int64_t>(nb, nrhs - q0);
+      if (!gsM || gsM->nsys != 2 * nq) {
+        gsM = std::make_unique<GramSolver<double>>();
+        if ((rc = gsM->init(d_mrp, d_mcol, d_mval, N, 2 * nq, mnnz, 1.0, 1e-13, 200, st))) break;
+      }
+      if ((rc = launch_rhs(*rwg, d_inc + 6 * q0, nq, k_e, 1.0, load, st, 1))) break;
+      if ((rc = gsM->solve(load, c + q0 * n2, st))) break;
+      if ((rc = apply_Ai(c + q0 * n2, y, CAL_FP64, nq))) break;
+      if ((rc = vec_axpby(b + q0 * n2, 0.5, y, -1.0, b + q0 * n2, nq * n2, st))) break;
+    }
+    dfree(load, st);
+    dfree(y, st);
+    if (!rc && gsM) rc = gsM->check(st);
+    return rc;
   }
 
   // y = P x on BC coefficients (y overwritten)
@@ -1123,7 +1224,8 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     return fail(CAL_EINVAL, "solve: bad precision");
   if (o.precond < CAL_PRECOND_NONE || o.precond > CAL_PRECOND_SI) return fail(CAL_EINVAL, "solve: bad preconditioner");
   if (!(o.tol > 0) || o.restart < 1 || o.maxit < 1) return fail(CAL_EINVAL, "solve: bad tolerance/restart/maxit");
-  if (o.rhs_mode != 0) return fail(CAL_EINVAL, "solve: only the total-trace right-hand side is implemented");
+  if (o.rhs_mode != 0 && o.rhs_mode != 1)
+    return fail(CAL_EINVAL, "solve: rhs_mode must be 0 (total traces) or 1 (the paper's scattered traces)");
   for (int m = 0; m < P.M; ++m) {
     std::complex<double> e(eps_r[2 * m], eps_r[2 * m + 1]);
     std::complex<double> u = mu_r ? std::complex<double>(mu_r[2 * m], mu_r[2 * m + 1]) : 1.0;
@@ -1333,8 +1435,8 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   if (!ctx || !prob || !inc || nrhs < 1 || !out) return fail(CAL_EINVAL, "cal_problem_solve: bad argument");
   if (solver && (!(solver->tol > 0) || solver->restart < 1 || solver->maxit < 1 || solver->refine < 0))
     return fail(CAL_EINVAL, "cal_problem_solve: bad tolerance/restart/maxit/refine");
-  if (solver && solver->rhs_mode != 0)
-    return fail(CAL_EINVAL, "solve: only the total-trace right-hand side is implemented");
+  if (solver && solver->rhs_mode != 0 && solver->rhs_mode != 1)
+    return fail(CAL_EINVAL, "solve: rhs_mode must be 0 (total traces) or 1 (the paper's scattered traces)");
   if (ctx->impl.device != prob->device)
     return fail(CAL_EINVAL, "cal_problem_solve: the problem lives on device %d", prob->device);
   for (int64_t q = 0; q < 6 * nrhs; ++q)
@@ -1357,6 +1459,7 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
     P.o.restart = solver->restart;
     P.o.maxit = solver->maxit;
     P.o.refine = solver->refine;
+    P.o.rhs_mode = solver->rhs_mode;
   }
   const cal_solve_opts& o = P.o;
   const int prec = o.precision;
@@ -1373,6 +1476,10 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   sol->ne = P.N;
   sol->k_e = P.k_e;
   sol->precision = P.o.precision == CAL_FP64 ? CAL_FP64 : CAL_FP32;
+  sol->k_m = P.k_m;
+  sol->mu_m = P.mu_m;
+  sol->inc.assign(inc, inc + 6 * nrhs);
+  sol->rhs_mode = o.rhs_mode;
   const int64_t n2 = 2 * P.N;
   double* d_inc;
   double2 *d_b, *d_rhs, *d_r;
@@ -1390,6 +1497,10 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   };
   Guard g1{d_b, st}, g2{d_rhs, st}, g3{d_r, st}, g4{d_inc, st};
   if ((rc = launch_rhs(*P.rwg, d_inc, (int)nrhs, P.k_e, 1.0, d_b, st))) return rc;
+  if (o.rhs_mode == 1) {
+    CAL_TRY_CUDA(dalloc((void**)&sol->d_cinc, nrhs * n2 * sizeof(double2), st));
+    if ((rc = P.scattered_rhs(d_inc, nrhs, d_b, sol->d_cinc))) return rc;
+  }
   P.matvecs = 0;
   int total_it = 0;
   double worst_res = 0.0;
@@ -1549,6 +1660,75 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
   dfree(d_dirs, st);
   dfree(d_out, st);
   return rc;
+}
+
+int cal_near_field(const cal_solution* sol, const double* points, int64_t npt, int levels,
+                   const int32_t* region_in, int32_t* region_out, double* out) {
+  if (!sol || !points || !out || npt < 1) return fail(CAL_EINVAL, "cal_near_field: bad argument");
+  if (levels < 0 || levels > 4) return fail(CAL_EINVAL, "cal_near_field: levels must be in [0, 4]");
+  for (int64_t q = 0; q < 3 * npt; ++q)
+    if (!std::isfinite(points[q])) return fail(CAL_EINVAL, "cal_near_field: non-finite point");
+  const Space& sp = *sol->rwg;
+  const int M = (int)sp.tri_off.size() - 1;
+  if (region_in)
+    for (int64_t i = 0; i < npt; ++i)
+      if (region_in[i] < -1 || region_in[i] >= M)
+        return fail(CAL_EINVAL, "cal_near_field: region %d of point %lld outside [-1, %d)", region_in[i],
+                    (long long)i, M);
+  if ((int)sol->k_m.size() != M) return fail(CAL_EINVAL, "cal_near_field: solution without material data");
+  CAL_TRY_CUDA(cudaSetDevice(sol->ctx->device));
+  cudaStream_t st = sol->ctx->stream;
+  double* d_pts = nullptr;
+  double* d_inc = nullptr;
+  double2* d_out = nullptr;
+  int32_t* d_reg = nullptr;
+  struct Free {
+    std::vector<void*> p;
+    cudaStream_t s;
+    ~Free() { for (void* q : p) dfree(q, s); }
+  } fr{{}, st};
+  const size_t out_bytes = (size_t)sol->nrhs * npt * 3 * sizeof(double2);
+  CAL_TRY_CUDA(dalloc((void**)&d_pts, 3 * npt * sizeof(double), st));
+  fr.p.push_back(d_pts);
+  CAL_TRY_CUDA(dalloc((void**)&d_inc, sol->inc.size() * sizeof(double), st));
+  fr.p.push_back(d_inc);
+  CAL_TRY_CUDA(dalloc((void**)&d_out, out_bytes, st));
+  fr.p.push_back(d_out);
+  CAL_TRY_CUDA(cudaMemcpyAsync(d_pts, points, 3 * npt * sizeof(double), cudaMemcpyHostToDevice, st));
+  CAL_TRY_CUDA(cudaMemcpyAsync(d_inc, sol->inc.data(), sol->inc.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  std::vector<int> reg(npt);
+  if (region_in) {
+    std::copy(region_in, region_in + npt, reg.begin());
+  } else {
+    CAL_TRY_CUDA(dalloc((void**)&d_reg, npt * sizeof(int32_t), st));
+    fr.p.push_back(d_reg);
+    int rc = launch_regions(sp, M, d_pts, npt, d_reg, st);
+    if (rc) return rc;
+    CAL_TRY_CUDA(cudaMemcpyAsync(reg.data(), d_reg, npt * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  }
+  FieldArgs f;
+  f.rwg = &sp;
+  f.M = M;
+  f.levels = levels;
+  f.precision = sol->precision;
+  f.nrhs = (int)sol->nrhs;
+  f.x = sol->d_x;
+  f.xinc = sol->d_cinc;  // scattered-trace solutions: total trace = u^s + projected u^inc
+  f.d_pts = d_pts;
+  f.npt = npt;
+  f.d_inc = d_inc;
+  f.d_out = d_out;
+  f.k_e = sol->k_e;
+  f.mu_e = sol->mu_e;
+  f.k_m = sol->k_m;
+  f.mu_m = sol->mu_m;
+  int rc = launch_near_field(f, reg, st);
+  if (rc) return rc;
+  CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, st));
+  CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  if (region_out) std::copy(reg.begin(), reg.end(), region_out);
+  return CAL_OK;
 }
 
 void cal_solution_destroy(cal_solution* sol) { delete sol; }

@@ -1919,10 +1919,14 @@ int vec_gather(const double2* src, int64_t bsrc, double2* dst, int64_t n, int nr
 // u1 = E x n, u2 = (k/mu) (d x p) e^{ik d.x} x n, <a x n, phi> = -int a.phi,
 // 6-point rule per triangle, float64.
 // ---------------------------------------------------------------------------
+// mode 0: the tested incident traces b = (-int phi.E, -(k/mu) int phi.(d x p) e^{ik d.x})
+// (the identity pairing of eq. dualpairingGammam with tangential test functions);
+// mode 1: the L2 loads (int phi.(E x n), (k/mu) int phi.((d x p) e^{ik d.x} x n)) of the
+// projection of u^inc onto RWG, written as F.(n x phi)
 __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
                            const double* __restrict__ slot_sw, int64_t nt, const double* inc,
                            int nrhs, double k, double mu, Rules6 rl, int64_t ne,
-                           double2* __restrict__ b) {
+                           double2* __restrict__ b, int mode) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
   if (t >= nt || q >= nrhs) return;
@@ -1930,6 +1934,21 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
   const double d[3] = {inc[6 * q], inc[6 * q + 1], inc[6 * q + 2]};
   const double p[3] = {inc[6 * q + 3], inc[6 * q + 4], inc[6 * q + 5]};
   const double dxp[3] = {d[1] * p[2] - d[2] * p[1], d[2] * p[0] - d[0] * p[2], d[0] * p[1] - d[1] * p[0]};
+  // unit outward normal (vertices counter-clockwise seen from outside)
+  double nrm[3];
+  {
+    double e1[3], e2[3];
+    for (int c = 0; c < 3; ++c) {
+      e1[c] = T.off[1][c] - T.off[0][c];
+      e2[c] = T.off[2][c] - T.off[0][c];
+    }
+    nrm[0] = e1[1] * e2[2] - e1[2] * e2[1];
+    nrm[1] = e1[2] * e2[0] - e1[0] * e2[2];
+    nrm[2] = e1[0] * e2[1] - e1[1] * e2[0];
+    const double il = 1.0 / sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+    for (int c = 0; c < 3; ++c) nrm[c] *= il;
+  }
+  const double sgn = mode == 0 ? -1.0 : 1.0;
   double acc1[3][2] = {}, acc2[3][2] = {};
   for (int u = 0; u < 6; ++u) {
     double xi[3];
@@ -1944,12 +1963,17 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
       const double* sw = slot_sw + (3 * t + a) * 4;
       double phi[3];
       for (int c = 0; c < 3; ++c) phi[c] = sw[0] * xi[c] + sw[1 + c];
+      if (mode == 1) {  // n x phi
+        const double v[3] = {nrm[1] * phi[2] - nrm[2] * phi[1], nrm[2] * phi[0] - nrm[0] * phi[2],
+                             nrm[0] * phi[1] - nrm[1] * phi[0]};
+        for (int c = 0; c < 3; ++c) phi[c] = v[c];
+      }
       const double e1 = p[0] * phi[0] + p[1] * phi[1] + p[2] * phi[2];
       const double e2 = dxp[0] * phi[0] + dxp[1] * phi[1] + dxp[2] * phi[2];
-      acc1[a][0] -= w * co * e1;
-      acc1[a][1] -= w * s * e1;
-      acc2[a][0] -= (k / mu) * w * co * e2;
-      acc2[a][1] -= (k / mu) * w * s * e2;
+      acc1[a][0] += sgn * w * co * e1;
+      acc1[a][1] += sgn * w * s * e1;
+      acc2[a][0] += sgn * (k / mu) * w * co * e2;
+      acc2[a][1] += sgn * (k / mu) * w * s * e2;
     }
   }
   for (int a = 0; a < 3; ++a) {
@@ -1965,12 +1989,58 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
 // Far field E_inf(xh) = -(ik/4pi) [xh x Ja - xh x (xh x Jb)],
 // Ja = int a e^{-ik xh.y}, Jb = (mu/k) int (sum d_e RWG_e) e^{-ik xh.y}.
 int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
-               cudaStream_t st) {
+               cudaStream_t st, int mode) {
   Rules6 rl = rules6();
   CAL_TRY_CUDA(cudaMemsetAsync(d_b, 0, (size_t)nrhs * 2 * rwg.nbasis * sizeof(double2), st));
   dim3 grid(blocks_for(rwg.ntri, 128), nrhs);
   rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_inc, nrhs,
-                                   k, mu, rl, rwg.nbasis, d_b);
+                                   k, mu, rl, rwg.nbasis, d_b, mode);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+// RWG mass matrix M_ij = int phi_i . phi_j (degree-2 integrand: the 6-point rule
+// is exact), accumulated per triangle into a CSR pattern that holds every pair
+// of edges of one triangle; the column of an entry is found by a scan of its row
+__global__ void rwg_mass_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
+                                const double* __restrict__ slot_sw, int64_t nt, Rules6 rl,
+                                const int64_t* __restrict__ rowptr, const int* __restrict__ col,
+                                double* __restrict__ val) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nt) return;
+  const TriD T = tri[t];
+  for (int a = 0; a < 3; ++a) {
+    const int ea = slot_edge[3 * t + a];
+    if (ea < 0) continue;
+    const double* sa = slot_sw + (3 * t + a) * 4;
+    for (int b = 0; b < 3; ++b) {
+      const int eb = slot_edge[3 * t + b];
+      if (eb < 0) continue;
+      const double* sb = slot_sw + (3 * t + b) * 4;
+      double m = 0.0;
+      for (int u = 0; u < 6; ++u) {
+        double dot = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          const double xi = rl.b[3 * u] * T.off[0][c] + rl.b[3 * u + 1] * T.off[1][c] + rl.b[3 * u + 2] * T.off[2][c];
+          dot += (sa[0] * xi + sa[1 + c]) * (sb[0] * xi + sb[1 + c]);
+        }
+        m += rl.w[u] * dot;
+      }
+      m *= T.area;
+      for (int64_t q = rowptr[ea]; q < rowptr[ea + 1]; ++q)
+        if (col[q] == eb) {
+          atomicAdd(val + q, m);
+          break;
+        }
+    }
+  }
+}
+
+int launch_rwg_mass(const Space& rwg, const int64_t* rowptr, const int* col, double* val, cudaStream_t st) {
+  Rules6 rl = rules6();
+  rwg_mass_kernel<<<blocks_for(rwg.ntri, 128), 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd,
+                                                             rwg.ntri, rl, rowptr, col, val);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;

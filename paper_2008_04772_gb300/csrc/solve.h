@@ -122,10 +122,33 @@ template <typename VT>
 int combine_rhs(const float* ZS, const float* ZC, int64_t rows, int NB, int nrhs, int64_t n_total, int64_t row_off,
                 VT* Y, double ar, double ai, double br, double bi, cudaStream_t st);
 
+// mode 0: tested incident traces (the total-trace right-hand side); mode 1: the
+// loads int phi.(field x n) of the L2 projection of u^inc onto RWG
 int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double mu, double2* d_b,
-               cudaStream_t st);
+               cudaStream_t st, int mode = 0);
+// values of the RWG mass matrix int phi_i . phi_j on a CSR pattern holding every
+// pair of edges of a triangle (values zeroed by the caller)
+int launch_rwg_mass(const Space& rwg, const int64_t* rowptr, const int* col, double* val, cudaStream_t st);
 int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,
                     double k, double mu, double2* d_out, int precision, cudaStream_t st);
+
+// Near field (field.cu): the Stratton–Chu representations of the solved traces
+// at points off the surface
+struct FieldArgs {
+  const Space* rwg = nullptr;
+  int M = 1, levels = 2, precision = CAL_FP64, nrhs = 1;
+  const double2* x = nullptr;     // [nrhs][2N] coefficients (c, d)
+  const double2* xinc = nullptr;  // optional [nrhs][2N] added to x (total traces)
+  const double* d_pts = nullptr;  // [npt][3]
+  int64_t npt = 0;
+  const double* d_inc = nullptr;  // [nrhs][6] incident plane waves
+  double2* d_out = nullptr;       // [nrhs][npt][3]
+  double k_e = 1.0, mu_e = 1.0;
+  std::vector<std::complex<double>> k_m, mu_m;
+};
+// region of each point: the scatterer m whose mesh winds around it, or -1
+int launch_regions(const Space& rwg, int M, const double* d_pts, int64_t npt, int32_t* d_region, cudaStream_t st);
+int launch_near_field(const FieldArgs& f, const std::vector<int>& region, cudaStream_t st);
 
 // BC tile launcher (assemble.cu)
 // A5 over units: units [nunits] of {v, begin, count, pad} ints, each a test
