@@ -969,7 +969,9 @@ __global__ void __launch_bounds__(TT, sizeof(R) == 4 ? 4 : 2) bc_tile_kernel(
 // triangles tau2 of w_j, forms each pair's moments and pair coefficients and
 // contracts them with w_j's trial slots at once into register sums (the
 // stage-2 records of bc_tile_kernel), so pair coefficients never go through
-// shared memory and the pair loop has no barrier. The records are then written
+// shared memory and the pair loop has no barrier. The divergence parts of the
+// slots factor as s_b / |tau2| over a cell, so their terms are one sum per
+// thread rather than one per slot. The records are then written
 // to shared memory once and contracted with the test slots per (j, a, b).
 // Units hold up to floor(TT / n1) trial cells so that the items fill the
 // block. The trial triangles of a unit are staged in shared memory first, as
@@ -982,7 +984,7 @@ constexpr int BC_OWN_STAGE = 160;  // staged trial triangle rows per unit (count
 
 // packed trial record, in float4 words: the trial rule points (the far rule's
 // 3 in class mode) with their weights over 4 pi, BC_OWN_SLOTS slot quadruples (zero past nslot), then
-// (hi.x, hi.y, hi.z, lo.x), (lo.y, lo.z, d, vid0), (vid1, vid2, 0, 0) with the
+// (hi.x, hi.y, hi.z, lo.x), (lo.y, lo.z, d, vid0), (vid1, vid2, 1/|tau|, 0) with the
 // vertex ids stored as int bits
 template <int NREG> __host__ __device__ constexpr int owner_trial_pts() { return NREG > 0 ? NREG : 3; }
 template <int NREG> __host__ __device__ constexpr int owner_rec_words() {
@@ -990,7 +992,8 @@ template <int NREG> __host__ __device__ constexpr int owner_rec_words() {
 }
 
 template <int NREG>
-__global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct, float4* __restrict__ rec) {
+__global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct, const TriF* __restrict__ tri,
+                                     const int* __restrict__ cell_tri, float4* __restrict__ rec) {
   constexpr int NP = owner_trial_pts<NREG>(), RW = owner_rec_words<NREG>(), NS = staged_points<NREG>();
   constexpr int OFF = NREG > 0 ? 0 : RULE_OFF_FAR;
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1013,7 +1016,7 @@ __global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct,
     const int k = u - NP - BC_OWN_SLOTS;
     if (k == 0) o = make_float4(c.hi[0], c.hi[1], c.hi[2], c.lo[0]);
     else if (k == 1) o = make_float4(c.lo[1], c.lo[2], c.d, __int_as_float(v[0]));
-    else o = make_float4(__int_as_float(v[1]), __int_as_float(v[2]), 0.0f, 0.0f);
+    else o = make_float4(__int_as_float(v[1]), __int_as_float(v[2]), 1.0f / tri[cell_tri[t]].area, 0.0f);
   }
   rec[q] = o;
 }
@@ -1110,8 +1113,9 @@ template <int NREG, int TT, bool BOTH>
 __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     CellData<float> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
     const int* __restrict__ cell_edge, const BcUnit* __restrict__ units, int64_t nunits,
-    const int* __restrict__ wlist, const float4* __restrict__ trec, float kr, float ki, float mikr, float miki,
-    float c4r, float c4i, bool wantS, bool wantC, Sink<float> out, int max_cell, unsigned long long* cnt) {
+    const int* __restrict__ wlist, const float4* __restrict__ trec, const float* __restrict__ cell_slot_s, float kr,
+    float ki, float mikr, float miki, float c4r, float c4i, bool wantS, bool wantC, Sink<float> out, int max_cell,
+    unsigned long long* cnt) {
   constexpr int NS = staged_points<NREG>();
   constexpr int NSL = BC_OWN_SLOTS;
   constexpr int NP = owner_trial_pts<NREG>(), RW = owner_rec_words<NREG>();
@@ -1126,6 +1130,7 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   int* jb = vidA + 3 * max_cell;                                                    // [TT] first trial triangle
   int* jn = jb + TT;                                                                // [TT] trial triangles
   int* jw = jn + TT;                                                                // [TT] trial cell
+  float* js = reinterpret_cast<float*>(jw + TT);                                    // [TT][NSL] s_b of cell j
   if (BOTH) wantS = wantC = true;  // S and C: the branches on them fold away
   unsigned evals = 0;
   for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
@@ -1150,6 +1155,9 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       jw[j] = w;
       jb[j] = b;
       jn[j] = cell_ptr[w + 1] - b;
+      const int e0 = cell_edge_ptr[w], ns = cell_edge_ptr[w + 1] - e0;
+#pragma unroll
+      for (int sl = 0; sl < NSL; ++sl) js[j * NSL + sl] = sl < ns ? cell_slot_s[e0 + sl] : 0.0f;
     }
     __syncthreads();
     // trial records: cell j at rows [j max_cell, j max_cell + n2); the host
@@ -1172,11 +1180,18 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
       const P4<float>* X = ptsA + i1 * NS;
       const P4<float>* XW = ptsW + i1 * NS;
+      // slot b on tau2 is sigma_b (y - c2) + w_b with sigma_b = s_b / |tau2| (s_b
+      // constant over the cell): the sigma terms of all slots are one sum a[]
+      // over tau2 of the pair coefficients times 1/|tau2|, scaled by s_b at the
+      // end; r[b] holds the w_b terms (components 2 and 3 have none)
       float r[NSL][18];
+      float a[18];
 #pragma unroll
       for (int b = 0; b < NSL; ++b)
 #pragma unroll
         for (int f = 0; f < 18; ++f) r[b][f] = 0.0f;
+#pragma unroll
+      for (int f = 0; f < 18; ++f) a[f] = 0.0f;
       for (int i2 = 0; i2 < n2; ++i2) {
         const float4* rr = R2 + i2 * RW;
         const float4 k0 = rr[NP + NSL], k1 = rr[NP + NSL + 1], k2 = rr[NP + NSL + 2];
@@ -1220,42 +1235,53 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
         }
         float pc[36];
         pair_coeffs_fused(m, D, pc);
+        // sigma terms: the pair coefficients that multiply sigma_b, times 1/|tau2|
+        const float beta = k2.z;
+        a[0] = fmaf(beta, pc[14], a[0]);
+        a[1] = fmaf(beta, pc[15], a[1]);
+        a[2] = fmaf(beta, pc[0], a[2]);
+        a[3] = fmaf(beta, pc[1], a[3]);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) a[4 + f] = fmaf(beta, pc[8 + f], a[4 + f]);
+        a[10] = fmaf(beta, pc[16], a[10]);
+        a[11] = fmaf(beta, pc[17], a[11]);
+#pragma unroll
+        for (int f = 0; f < 6; ++f) a[12 + f] = fmaf(beta, pc[24 + f], a[12 + f]);
         const P4<float>* swb = Ys + NP;
 #pragma unroll
         for (int b = 0; b < NSL; ++b) {
           if (b >= ns2) break;
           const P4<float> u = swb[b];
-          const float sb = u.x, bx = u.y, by = u.z, bz = u.w;
+          const float bx = u.y, by = u.z, bz = u.w;
           float* o = r[b];
-          // S: AS (re, im), BS (re, im), WS_r, WS_i
-          o[0] = fmaf(bz, pc[4], fmaf(by, pc[3], fmaf(bx, pc[2], fmaf(sb, pc[14], o[0]))));
-          o[1] = fmaf(bz, pc[7], fmaf(by, pc[6], fmaf(bx, pc[5], fmaf(sb, pc[15], o[1]))));
-          o[2] = fmaf(sb, pc[0], o[2]);
-          o[3] = fmaf(sb, pc[1], o[3]);
-          o[4] = fmaf(bx, pc[0], fmaf(sb, pc[8], o[4]));
-          o[5] = fmaf(by, pc[0], fmaf(sb, pc[9], o[5]));
-          o[6] = fmaf(bz, pc[0], fmaf(sb, pc[10], o[6]));
-          o[7] = fmaf(bx, pc[1], fmaf(sb, pc[11], o[7]));
-          o[8] = fmaf(by, pc[1], fmaf(sb, pc[12], o[8]));
-          o[9] = fmaf(bz, pc[1], fmaf(sb, pc[13], o[9]));
-          // C: AC (re, im), WC_r = sb X2r + wb x Vr, WC_i
-          o[10] = fmaf(bz, pc[20], fmaf(by, pc[19], fmaf(bx, pc[18], fmaf(sb, pc[16], o[10]))));
-          o[11] = fmaf(bz, pc[23], fmaf(by, pc[22], fmaf(bx, pc[21], fmaf(sb, pc[17], o[11]))));
-          o[12] = fmaf(by, pc[32], fmaf(-bz, pc[31], fmaf(sb, pc[24], o[12])));
-          o[13] = fmaf(bz, pc[30], fmaf(-bx, pc[32], fmaf(sb, pc[25], o[13])));
-          o[14] = fmaf(bx, pc[31], fmaf(-by, pc[30], fmaf(sb, pc[26], o[14])));
-          o[15] = fmaf(by, pc[35], fmaf(-bz, pc[34], fmaf(sb, pc[27], o[15])));
-          o[16] = fmaf(bz, pc[33], fmaf(-bx, pc[35], fmaf(sb, pc[28], o[16])));
-          o[17] = fmaf(bx, pc[34], fmaf(-by, pc[33], fmaf(sb, pc[29], o[17])));
+          // S: AS (re, im), WS_r, WS_i (w_b terms)
+          o[0] = fmaf(bz, pc[4], fmaf(by, pc[3], fmaf(bx, pc[2], o[0])));
+          o[1] = fmaf(bz, pc[7], fmaf(by, pc[6], fmaf(bx, pc[5], o[1])));
+          o[4] = fmaf(bx, pc[0], o[4]);
+          o[5] = fmaf(by, pc[0], o[5]);
+          o[6] = fmaf(bz, pc[0], o[6]);
+          o[7] = fmaf(bx, pc[1], o[7]);
+          o[8] = fmaf(by, pc[1], o[8]);
+          o[9] = fmaf(bz, pc[1], o[9]);
+          // C: AC (re, im), WC_r = w_b x Vr, WC_i
+          o[10] = fmaf(bz, pc[20], fmaf(by, pc[19], fmaf(bx, pc[18], o[10])));
+          o[11] = fmaf(bz, pc[23], fmaf(by, pc[22], fmaf(bx, pc[21], o[11])));
+          o[12] = fmaf(by, pc[32], fmaf(-bz, pc[31], o[12]));
+          o[13] = fmaf(bz, pc[30], fmaf(-bx, pc[32], o[13]));
+          o[14] = fmaf(bx, pc[31], fmaf(-by, pc[30], o[14]));
+          o[15] = fmaf(by, pc[35], fmaf(-bz, pc[34], o[15]));
+          o[16] = fmaf(bz, pc[33], fmaf(-bx, pc[35], o[16]));
+          o[17] = fmaf(bx, pc[34], fmaf(-by, pc[33], o[17]));
         }
       }
       float* dst = rec + (size_t)threadIdx.x * NSL * BC_OWN_REC;
 #pragma unroll
       for (int b = 0; b < NSL; ++b) {
         if (b >= ns2) break;
+        const float sb = js[j * NSL + b];
         __align__(16) float tmp[BC_OWN_REC];
 #pragma unroll
-        for (int f = 0; f < 18; ++f) tmp[f] = r[b][f];
+        for (int f = 0; f < 18; ++f) tmp[f] = fmaf(sb, a[f], r[b][f]);
         tmp[18] = tmp[19] = 0.0f;
         vcopy(dst + b * BC_OWN_REC, tmp, BC_OWN_REC);
       }
@@ -1301,8 +1327,8 @@ constexpr int BC_OWNER_TT = 128;
 // cell; 0 when that kernel does not apply (float64, cells with more than
 // BC_OWN_SLOTS edges or more than BC_OWN_STAGE triangles)
 int bc_owner_width(const Space& s, int precision, int n1, int max_cell) {
-  if (precision != CAL_FP32 || s.nslot > BC_OWN_SLOTS || n1 < 1 || n1 > BC_OWNER_TT || max_cell < n1 ||
-      max_cell > BC_OWN_STAGE)
+  if (precision != CAL_FP32 || s.nslot > BC_OWN_SLOTS || !s.sigma_factors || n1 < 1 || n1 > BC_OWNER_TT ||
+      max_cell < n1 || max_cell > BC_OWN_STAGE)
     return 0;
   return std::max(1, std::min(BC_OWNER_TT / n1, BC_OWN_STAGE / max_cell));
 }
@@ -2336,14 +2362,15 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
         cudaFreeAsync(buf, a.stream);
         return fail(CAL_ENOMEM, "bc owner kernel: cannot allocate the trial records");
       }
-      pack<<<(unsigned)((nct * rw + 255) / 256), 256, 0, a.stream>>>(cd, s.nslot, nct, trec);
+      pack<<<(unsigned)((nct * rw + 255) / 256), 256, 0, a.stream>>>(cd, s.nslot, nct, s.d_triF, s.d_cell_tri, trec);
       note_launch();
       const int nsp_o = nreg > 0 ? nreg : RULE_POINTS_ALL;
       const size_t osmem = (size_t)OT * BC_OWN_SLOTS * BC_OWN_REC * sizeof(float) +
                            (size_t)BC_OWN_STAGE * rw * sizeof(float4) +
                            2 * (size_t)max_cell * nsp_o * sizeof(P4<float>) +
                            (size_t)max_cell * s.nslot * sizeof(P4<float>) + (size_t)max_cell * sizeof(Cent<float>) +
-                           (size_t)max_cell * 3 * sizeof(int) + 3 * (size_t)OT * sizeof(int) + 64;
+                           (size_t)max_cell * 3 * sizeof(int) + 3 * (size_t)OT * sizeof(int) +
+                           (size_t)OT * BC_OWN_SLOTS * sizeof(float) + 64;
       int rc = ensure_dyn_smem((const void*)okern, (int)osmem);
       int per_sm = 0;
       if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, OT, osmem) != cudaSuccess)
@@ -2353,8 +2380,8 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
         const int tok = prof_begin(a.stream, "bc_tile", work);
         unsigned long long* cnt = nreg == 0 ? prof_counter(tok, a.stream) : nullptr;
         okern<<<(unsigned)grid, OT, osmem, a.stream>>>(cd, s.nslot, s.d_cell_tri_ptr, s.d_cell_edge_ptr, s.d_cell_edge,
-                                                      units, nunits, wlist, trec, (float)a.kr, (float)a.ki, mikr, miki,
-                                                      c4r, c4i, wS, wC, out, max_cell, cnt);
+                                                      units, nunits, wlist, trec, s.d_cell_slot_s, (float)a.kr,
+                                                      (float)a.ki, mikr, miki, c4r, c4i, wS, wC, out, max_cell, cnt);
         prof_end(a.stream, tok);
         note_launch();
         if (cudaGetLastError() != cudaSuccess) rc = fail(CAL_ECUDA, "bc owner kernel launch failed");

@@ -773,6 +773,28 @@ int upload_space(Space& s, cudaStream_t st) {
   if ((rc = upload(&s.d_slot_swf, swf.data(), swf.size(), st))) return rc;
   if ((rc = upload(&s.d_slot_swd, s.slot_sw.data(), s.slot_sw.size(), st))) return rc;
   if (s.kind == CAL_BC) {
+    // sigma_{b,tau} |tau| per cell slot, and whether it is one constant over the cell
+    const int64_t nv = (int64_t)s.cell_tri_ptr.size() - 1;
+    s.cell_slot_s.assign(s.cell_edge.size(), 0.0f);
+    bool ok = true;
+    for (int64_t v = 0; v < nv && ok; ++v) {
+      const int t0 = s.cell_tri_ptr[v], t1 = s.cell_tri_ptr[v + 1];
+      const int e0 = s.cell_edge_ptr[v], ns = s.cell_edge_ptr[v + 1] - e0;
+      if (t1 == t0) continue;
+      for (int sl = 0; sl < ns && ok; ++sl) {
+        const int tau0 = s.cell_tri[t0];
+        const double sb = s.slot_sw[((size_t)tau0 * s.nslot + sl) * 4] * s.triD[tau0].area;
+        for (int q = t0; q < t1 && ok; ++q) {
+          const int tau = s.cell_tri[q];
+          const double v2 = s.slot_sw[((size_t)tau * s.nslot + sl) * 4] * s.triD[tau].area;
+          ok = std::abs(v2 - sb) <= 1e-9 * std::abs(sb) + 1e-300;
+        }
+        s.cell_slot_s[e0 + sl] = (float)sb;
+      }
+    }
+    s.sigma_factors = ok;
+    if ((rc = upload(&s.d_cell_slot_s, s.cell_slot_s.data(), std::max<size_t>(s.cell_slot_s.size(), 1), st)))
+      return rc;
     if ((rc = upload(&s.d_cell_tri_ptr, s.cell_tri_ptr.data(), s.cell_tri_ptr.size(), st))) return rc;
     if ((rc = upload(&s.d_cell_tri, s.cell_tri.data(), s.cell_tri.size(), st))) return rc;
     if ((rc = upload(&s.d_cell_edge_ptr, s.cell_edge_ptr.data(), s.cell_edge_ptr.size(), st))) return rc;
@@ -791,7 +813,8 @@ int upload_space(Space& s, cudaStream_t st) {
 // context (whose stream might already be destroyed) is needed at that point.
 Space::~Space() {
   for (void* p : {(void*)d_triF, (void*)d_triD, (void*)d_slot_edge, (void*)d_slot_swf, (void*)d_slot_swd,
-                  (void*)d_cell_tri_ptr, (void*)d_cell_tri, (void*)d_cell_edge_ptr, (void*)d_cell_edge})
+                  (void*)d_cell_tri_ptr, (void*)d_cell_tri, (void*)d_cell_edge_ptr, (void*)d_cell_edge,
+                  (void*)d_cell_slot_s})
     dfree(p, nullptr);
   for (auto p : d_sing) dfree(p, nullptr);
   for (auto& e : sing_static) {

@@ -144,6 +144,13 @@ struct Space {
   int* d_cell_edge_ptr = nullptr;  // BC: slot sl of every triangle of cell v is cell_edge[cell_edge_ptr[v] + sl]
   int* d_cell_edge = nullptr;
   std::vector<SingPair*> d_sing;
+  // BC: on every small triangle tau of a dual cell the divergence of each of the
+  // cell's functions is +-l_e/(2N_v)/|tau|, so sigma_{b,tau} = s_b / |tau| with s_b
+  // constant over the cell: cell_slot_s[cell_edge_ptr[v] + sl] = s_b (float), and
+  // sigma_factors records that the slot table satisfies this to 1e-9
+  std::vector<float> cell_slot_s;
+  float* d_cell_slot_s = nullptr;
+  bool sigma_factors = false;
   // k-independent float64 sums of the touching pairs (18 doubles per pair),
   // per scatterer: filled by its first float32 singular launch that asks for
   // C, read by later float32 launches with the same Gauss order

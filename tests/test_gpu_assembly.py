@@ -195,6 +195,27 @@ def test_full_size_sampled_rows(ctx, sphere4):
         del S, C, op
 
 
+@pytest.mark.parametrize("k", [5.0, 5.0 * np.sqrt(EPS)])
+def test_full_size_class_rule_rows(ctx, sphere4, k):
+    """The benched instance: float32 blocks with the near / medium / far rules
+    (q_regular = 0, the paper's default orders) at the headline's exterior and
+    interior wavenumbers. On the 5120-triangle sphere 99% of the barycentric
+    pairs are far, so this is the float32 BC-pair kernel's far-pair path at its
+    full launch size; sampled rows against the oracle computed row by row."""
+    topo, rwg_o, bc_o = oracle_spaces("sphere4")
+    rng = np.random.default_rng(11)
+    rows = np.sort(rng.choice(topo.n_edges, 3, replace=False))
+    for sp_gpu, sp_o, nrows in ((sphere4[1], bc_o, 3), (sphere4[0], rwg_o, 2)):
+        op = cal.assemble(ctx, 3, k, sp_gpu, q_regular=0, precision=cal.FP32)
+        S, C = op.export(cal.OP_S), op.export(cal.OP_C)
+        So, Co = bem.assemble(sp_o, sp_o, k, bem.Rules(0, 4), rows=rows[:nrows])
+        assert rel(S[rows[:nrows]], So) < 1e-5, rel(S[rows[:nrows]], So)
+        assert rel(C[rows[:nrows]], Co) < 1e-5, rel(C[rows[:nrows]], Co)
+        for j in range(nrows):  # every sampled row on its own
+            assert rel(S[rows[j]], So[j]) < 1e-5 and rel(C[rows[j]], Co[j]) < 1e-5, j
+        del S, C, op
+
+
 @pytest.mark.parametrize("lo,hi", [(-3.2, 3.2), (-60.0, 60.0), (0.0, 700.0)])
 def test_singular_kernel_elementary_functions(ctx, lo, hi):
     # the singular-pair kernel's own double cis/exp against CUDA's sincos/exp
