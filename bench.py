@@ -304,7 +304,11 @@ def run_ours(args, rank, world):
     if args.serving:
         out["serving"] = run_serving(dev)
     if args.variants:
-        out["preconditioners"] = run_variants(dev, F64, dirs)
+        out["preconditioners"] = run_variants(dev, dirs)
+    if args.table2:
+        out["three_cubes_table2"] = run_table2(dev)
+    if args.near_field:
+        out["near_field"] = run_near_field(dev)
     if args.cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_sample)
     return out
@@ -329,10 +333,13 @@ VARIANTS = [
 ]
 
 
-def run_variants(dev, F64, dirs):
+def run_variants(dev, dirs):
     """Every preconditioner of the headline workload: solves/s (median of 3 solves
-    after one warm-up), GMRES iterations, stored P bytes, assembly times and the
-    far-field error against the float64 GPU solve with D."""
+    after one warm-up), GMRES iterations, stored P bytes and assembly times, and the
+    float32 error of each: against the float64 GPU solve with the same
+    preconditioner and tolerance, and its floor (float32 at tol 1e-9) against a
+    converged float64 solve (tol 1e-10; the discrete solution does not depend on
+    the preconditioner)."""
     import ctypes
 
     import torch
@@ -344,10 +351,19 @@ def run_variants(dev, F64, dirs):
     m = meshgen.icosphere(W["level"])
     mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
     inc = meshgen.plane_wave_x_along_z()
-    out = {"workload": W["name"], "reference": "far field of the float64 GPU solve with D",
-           "note": "every variant stops at a preconditioned residual of 1e-5; its distance to the float64 "
-                   "D solution is set by that stopping point, not by float32 arithmetic (see the headline "
-                   "err_farfield_fp32_vs_fp64 for the same preconditioner)",
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))  # noqa: E731
+    conv = {}  # converged float64 far field per rule of A (the discrete solution's only dependence)
+
+    def converged(qa):
+        if qa not in conv:
+            conv[qa] = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], inc, opts=cal.solve_opts(
+                precond="D", precision=cal.FP64, tol=1e-10, restart=W["restart"], maxit=2000, q_regular_A=qa,
+                q_regular_P=0)).far_field(dirs)[0]
+        return conv[qa]
+    out = {"workload": W["name"],
+           "reference": "err_fp32_vs_fp64: float64 GPU solve with the same preconditioner and tol 1e-5; "
+                        "fp32_floor: float32 at tol 1e-9 against a converged float64 solve (tol 1e-10) with the "
+                        "same rules for A; err_vs_converged: the timed float32 solve (tol 1e-5) against it",
            "rules": "q_regular 0 = near/medium/far classes at the paper's default orders (4,3,2) for A and P, "
                     "6 = the 6-point rule for all regular pairs (D_uniform6), bi-parametric P (1, 1) (the *_bp_q11 lines)"}
     for name, o in VARIANTS:
@@ -371,11 +387,20 @@ def run_variants(dev, F64, dirs):
                 fam[kn] = round(ms_.value, 3)
         L.cal_profile_enable(0)
         info = sol.info()
-        out[name] = {"solves_per_s": 1.0 / statistics.median(ts), "iterations": int(info.iterations),
-                     "converged": int(info.converged), "bytes_P_mb": info.bytes_P / 1e6,
-                     "assemble_P_s": info.t_assemble_P, "solve_s": info.t_solve,
-                     "err_farfield_vs_fp64": float(np.linalg.norm(F[0] - F64[0]) / np.linalg.norm(F64[0])),
-                     "kernels_ms": fam}
+        o64 = dict(o, precision=cal.FP64, tol=W["tol"], restart=W["restart"])
+        F64 = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], inc, opts=cal.solve_opts(**o64),
+                               allow_not_converged=True).far_field(dirs)
+        Fc = converged(o.get("q_regular_A", 0))
+        res = {"solves_per_s": 1.0 / statistics.median(ts), "iterations": int(info.iterations),
+               "converged": int(info.converged), "bytes_P_mb": info.bytes_P / 1e6,
+               "assemble_P_s": info.t_assemble_P, "solve_s": info.t_solve,
+               "err_fp32_vs_fp64": rel(F[0], F64[0]), "err_vs_converged": rel(F[0], Fc), "kernels_ms": fam}
+        if info.converged:  # the floor of a solve that stops at maxit says nothing about float32
+            o9 = dict(o, precision=cal.FP32, tol=1e-9, restart=W["restart"], maxit=2000)
+            F9 = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], inc, opts=cal.solve_opts(**o9),
+                                  allow_not_converged=True).far_field(dirs)
+            res["fp32_floor"] = rel(F9[0], Fc)
+        out[name] = res
     return out
 
 
@@ -436,13 +461,16 @@ def run_multirhs(dev):
     }
 
 
-MATRIX_FREE = {"name": "aggregate8x1000_kD40_Di_near3h", "prisms": 8, "tris_per_prism": 1000, "seed": 0,
+MATRIX_FREE = {"name": "aggregate8x4000_kD40_Di_near3h", "prisms": 8, "tris_per_prism": 4000, "seed": 0,
                "k": 40.0, "eps": 3.17 + 0.01j, "precond": "Di", "near_cutoff_P": 3.0, "tol": 1e-5}
 
 
 def run_matrix_free(dev):
-    """Stored versus matrix-free A on a scaled-down version of the largest aggregate:
-    the same solve both ways, with the time per operator application."""
+    """The largest single-GPU aggregate (8 prisms, ~32k triangles, ~96k unknowns,
+    kD = 40): stored dense complex64 A versus matrix-free A, the same FP32-bulk
+    solve with float64 refinement both ways, the time per operator application,
+    the HBM fraction of the stored product and the ALU fraction of the
+    matrix-free kernel, and the far-field difference between the two."""
     import ctypes
 
     import torch
@@ -481,6 +509,8 @@ def run_matrix_free(dev):
                                                                  "assemble_P": info.t_assemble_P,
                                                                  "solve": info.t_solve},
                     "kernels_ms": {k: round(v[1], 3) for k, v in fam.items() if v[0]}}
+        apps = max(1, int(info.matvecs) // (4 * W["prisms"] ** 2 + 4 * W["prisms"]))
+        out[key]["operator_applications"] = apps
         if free and fam["rwg_free"][0]:
             n_, ms_, u_ = fam["rwg_free"]
             n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
@@ -488,20 +518,127 @@ def run_matrix_free(dev):
             out[key]["rwg_free"] = {"launches": n_, "ms_per_launch": ms_ / n_,
                                     "roofline": {"bound": "alu", "achieved": u_ / (ms_ / 1e3) / 1e9,
                                                  "peak": peak / 1e9, "unit": "Geval/s",
-                                                 "frac": u_ / (ms_ / 1e3) / peak}}
+                                                 "frac": u_ / (ms_ / 1e3) / peak,
+                                                 "note": "evaluations counted on the device; class rules put 9 "
+                                                         "evaluations on a far pair, so the per-pair work (moments, "
+                                                         "the 3 x 3 local S and C, their application) dominates"}}
+        if not free and fam["pair_gemv"][0]:
+            n_, ms_, u_ = fam["pair_gemv"]
+            hbm = _measured_peaks().get("hbm_gbs", 6783.5)
+            out[key]["pair_gemv"] = {"launches": n_, "ms_per_launch": ms_ / n_,
+                                     "roofline": {"bound": "hbm", "achieved": u_ / (ms_ / 1e3) / 1e9, "peak": hbm,
+                                                  "unit": "GB/s", "frac": u_ / (ms_ / 1e3) / 1e9 / hbm}}
     out["far_field_rel_diff"] = float(np.linalg.norm(far[1] - far[0]) / np.linalg.norm(far[0]))
     return out
 
 
-SERVING = {"name": "aggregate_requests_scaled", "requests": 48, "seed": 0, "prisms": (1, 8),
-           "tris_per_prism": (100, 600), "k": (1.0, 10.0), "eps_re": (2.5, 3.5), "eps_im": 0.01,
+# Section 4 Table table:multiple_particle: the three cubes (side 0.4, corners at x =
+# -1, 0, 1), n = 1.311 + 2.289e-9 i, E^inc = z e^{ik_e x}, 10 elements per
+# wavelength; P = D with (chi_P, q_P) of the rows the GPU path has (entry-level
+# cutoff in place of ACA: nu_P is not used). Printed values: iterations (matvecs)
+# for k_e = 2.1 and 11.4 (the "7 (582)" rows read as 528, Table tab:matvecs).
+TABLE2 = {"n": 1.311 + 2.289e-9j, "k": (2.1, 11.4), "tol": 1e-5, "restart": 200,
+          "rows": [("inf, (4,3,2,6)", math.inf, (0, 4), ((6, 456), (9, 672))),
+                   ("inf, (1,1,1,1)", math.inf, (1, 1), ((7, 528), (9, 672))),
+                   ("1.0, (1,1,1,1)", 1.0, (1, 1), ((7, 528), (9, 672))),
+                   ("0.1, (1,1,1,1)", 0.1, (1, 1), ((84, 6072), (16, 1176))),
+                   ("0, (1,1,1,1)", 0.0, (1, 1), ((198, 14280), (36, 2616)))]}
+
+
+def run_table2(dev):
+    """The three-cube benchmark of Section 4 on the GPU (float64, the paper's
+    scattered-trace right-hand side), iterations and matvecs beside Table 2's, and
+    the real-index rerun (n = 1.311) of the first row."""
+    from paper_2008_04772_gb300 import cal, meshgen
+    T = TABLE2
+    ctx = cal.Context(dev)
+    inc = np.array([[1.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
+    out = {"workload": "three cubes of side 0.4, n = 1.311 + 2.289e-9i, E^inc = z e^{ik x}, h = 2 pi / (10 k)",
+           "precision": "float64", "rhs": "scattered traces (rhs_mode 1)", "tol": T["tol"],
+           "note": "chi_P absolute (cutoff between supports, reading 7); nu_P (ACA) not used: P is dense or "
+                   "near-field CSR", "rows": {}}
+    for ki, k in enumerate(T["k"]):
+        m = meshgen.three_cubes(2 * math.pi / (10 * k))
+        mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+        h = mesh.info().h
+        key = f"k={k}"
+        out[key] = {"triangles": int(len(m.tris)), "unknowns": 2 * int(mesh.info().n_edges)}
+        for name, chi, (qr, qs), printed in T["rows"]:
+            opts = cal.solve_opts(precond="D", precision=cal.FP64, tol=T["tol"], restart=T["restart"], maxit=2000,
+                                  rhs_mode=1, q_regular_A=0, q_singular_A=4, q_regular_P=qr, q_singular_P=qs,
+                                  near_cutoff_P=(chi / h if math.isfinite(chi) else math.inf))
+            t0 = time.perf_counter()
+            info = cal.pmchwt_solve(ctx, mesh, k, T["n"] ** 2, inc, opts=opts, allow_not_converged=True).info()
+            out["rows"].setdefault(name, {})[key] = {
+                "iterations": int(info.iterations), "matvecs": int(info.matvecs),
+                "paper": {"iterations": printed[ki][0], "matvecs": printed[ki][1]},
+                "bytes_P_mb": info.bytes_P / 1e6, "seconds": time.perf_counter() - t0}
+        opts = cal.solve_opts(precond="D", precision=cal.FP64, tol=T["tol"], restart=T["restart"], maxit=2000,
+                              rhs_mode=1, q_regular_A=0, q_regular_P=0)
+        info = cal.pmchwt_solve(ctx, mesh, k, T["n"].real ** 2, inc, opts=opts, allow_not_converged=True).info()
+        out[key]["real_index_row1"] = {"iterations": int(info.iterations), "matvecs": int(info.matvecs)}
+    return out
+
+
+NEAR_FIELD = {"plane": "z = 0", "extent": 2.0, "grid": 128, "levels": 2}
+
+
+def run_near_field(dev):
+    """|E|^2 on a plane through the headline sphere (the maps of Section 5): the
+    float32 near-field kernel over the solved traces, timed, with its rate in
+    point-source interactions per second against the FP32-pipe bound."""
+    import ctypes
+
+    import torch
+
+    from paper_2008_04772_gb300 import cal, meshgen
+    W, NF = WORKLOAD, NEAR_FIELD
+    L = cal.lib()
+    ctx = cal.Context(dev)
+    m = meshgen.icosphere(W["level"])
+    mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    sol = cal.pmchwt_solve(ctx, mesh, W["k"], W["eps"], meshgen.plane_wave_x_along_z(),
+                           opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=W["tol"], **Q))
+    g = np.linspace(-NF["extent"], NF["extent"], NF["grid"])
+    X, Y = np.meshgrid(g, g, indexing="ij")
+    pts = np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], 1)
+    sol.near_field(pts[:64], levels=NF["levels"])  # warm-up
+    L.cal_profile_enable(1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E, reg = sol.near_field(pts, levels=NF["levels"])
+    t = time.perf_counter() - t0
+    n_, ms_, u_ = ctypes.c_int64(), ctypes.c_double(), ctypes.c_double()
+    L.cal_profile_read(b"near_field", ctypes.byref(n_), ctypes.byref(ms_), ctypes.byref(u_))
+    L.cal_profile_enable(0)
+    nsrc = len(m.tris) * 6 * 4 ** NF["levels"]
+    n_in = int(np.sum(reg >= 0))
+    inter = (len(pts) - n_in) * nsrc + n_in * nsrc  # one scatterer: all sources either way
+    n_sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_max = _measured_peaks().get("sm_max_mhz", 2070.0)
+    # per interaction ~76 FP32-pipe instructions (distance 7, phase with Cody-Waite 8,
+    # amplitude and G 5, g 10, sums: G u_2 12, g div u_2 (x - y) 10, curl 24) and
+    # 3 XU (rsqrt, sin, cos): the FP32 pipe binds
+    peak = n_sm * 128.0 / 76.0 * sm_max * 1e6
+    rate = inter / (ms_.value / 1e3) if ms_.value > 0 else 0.0
+    I2 = np.sum(np.abs(E[0]) ** 2, 1)
+    return {"workload": f"{W['name']} |E|^2 on the plane {NF['plane']}, {NF['grid']}^2 points in "
+                        f"[-{NF['extent']}, {NF['extent']}]^2, 6-point rule on 4^{NF['levels']} sub-triangles",
+            "points": len(pts), "inside": n_in, "sources": nsrc, "seconds": t, "kernel_ms": ms_.value,
+            "interactions_per_s": rate, "max_E2": float(I2.max()), "mean_E2_outside": float(I2[reg < 0].mean()),
+            "roofline": {"bound": "alu", "achieved": rate / 1e9, "peak": peak / 1e9, "unit": "Ginteractions/s",
+                         "frac": rate / peak, "peak_source": f"derived: {n_sm} SMs x 128/76 per clk x {sm_max:.0f} MHz"}}
+
+
+SERVING = {"name": "aggregate_requests_scaled", "requests": 64, "seed": 0, "prisms": (1, 8),
+           "tris_per_prism": (250, 2000), "k": (1.0, 10.0), "eps_re": (2.5, 3.5), "eps_im": 0.01,
            "nrhs": (1, 16), "ndir": 64, "precond": "D", "near_cutoff_P": math.inf, "tol": 1e-5,
            "slots": 4, "load": 0.8}
 
 
 def serving_requests(n, seed):
     """Seeded request mix shaped like the aggregate serving workload, scaled down
-    in triangles per prism so that the whole run takes well under a minute."""
+    in requests and triangles per prism (see SERVING) so that it fits the bench."""
     from paper_2008_04772_gb300 import meshgen
     S = SERVING
     rng = np.random.default_rng(seed)
@@ -580,6 +717,10 @@ def run_serving(dev):
     return {
         "workload": S["name"],
         "requests": len(reqs),
+        "scale": "the serving configuration states 512 requests with 500-4000 triangles per prism; this run "
+                 f"takes {len(reqs)} requests (1/{512 // len(reqs)}) with {S['tris_per_prism'][0]}-"
+                 f"{S['tris_per_prism'][1]} triangles per prism (half the stated range) so that both loops fit the "
+                 "bench's minutes",
         "mix": {"prisms": list(S["prisms"]), "tris_per_prism": list(S["tris_per_prism"]),
                 "triangles": [int(min(tri)), int(max(tri))], "k": list(S["k"]),
                 "eps_r": f"U{list(S['eps_re'])} + {S['eps_im']}i", "nrhs": list(S["nrhs"]),
@@ -602,15 +743,20 @@ def run_serving(dev):
     }
 
 
-def cpu_baseline(sample_tris: int):
-    """The oracle (plain FP64 C + numpy) on a bounded sample of the workload.
+def _host_cores() -> int:
+    """Cores this process may run on (what nproc prints)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
 
-    Times the oracle's local blocks for `sample_tris` test triangles against
-    all trial triangles — barycentric (P) and primal (A) — at k_e and k_i, and
-    extrapolates by the number of triangle pairs of one solve (P: 2 passes over
-    30720^2 barycentric pairs, A: 2 passes over 5120^2 primal pairs). GMRES
-    and far field (a few % of the oracle's time) are not included.
-    """
+
+def oracle_sample(sample_tris: int, seed: int = 0):
+    """The oracle's local blocks for `sample_tris` test triangles against all trial
+    triangles, barycentric (P) and primal (A), at k_e and k_i on the headline
+    workload. Returns (measured seconds, seconds extrapolated by triangle-pair
+    count to the assembly of one solve: P 2 passes over 30720^2 barycentric
+    pairs, A 2 passes over 5120^2 primal pairs, description)."""
     from oracle import bem, spaces
     from paper_2008_04772_gb300 import meshgen
     W = WORKLOAD
@@ -619,10 +765,9 @@ def cpu_baseline(sample_tris: int):
     rwg, bc = spaces.rwg_space(topo), spaces.bc_space(topo)
     rules = bem.Rules(W["q_regular"], 4)
     km = W["k"] * np.sqrt(W["eps"])
-    rng = np.random.default_rng(0)
-    t_total = 0.0
-    pairs_sampled = 0
-    sample_desc = []
+    rng = np.random.default_rng(seed)
+    t_meas = t_extra = 0.0
+    desc = []
     for sp, name in ((bc, "barycentric"), (rwg, "primal")):
         X, ids = bem._space_tri_arrays(sp)
         nt = sp.tri_xyz.shape[0]
@@ -633,37 +778,91 @@ def cpu_baseline(sample_tris: int):
             a = time.perf_counter()
             bem.local_blocks(X, ids, test, trial, k, rules)
             t += time.perf_counter() - a
-        per_pair = t / (2 * len(test) * nt)
-        t_total += per_pair * 2 * nt * nt
-        pairs_sampled += 2 * len(test) * nt
-        sample_desc.append(f"{len(test)} {name} test triangles x {nt}")
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": 1.0 / t_total, "unit": "solves/s", "cores": cores, "kind": "oracle",
-            "sample": "oracle local blocks for " + " and ".join(sample_desc) +
-                      " at k_e and k_i, extrapolated by triangle-pair count to one solve "
-                      f"({pairs_sampled} pairs timed); GMRES and far field excluded"}
+        t_meas += t
+        t_extra += t / (2 * len(test) * nt) * 2 * nt * nt
+        desc.append(f"{len(test)} {name} test triangles x {nt}")
+    return t_meas, t_extra, " and ".join(desc)
+
+
+def oracle_c1_solve():
+    """One complete oracle solve of the 320-triangle sphere (k = 2, full D, 6-point
+    and order-4 rules, GMRES to 1e-6, far field on 362 directions): phase times."""
+    from oracle import bem, pmchwt
+    from paper_2008_04772_gb300 import meshgen
+    bem.build()
+    m = meshgen.icosphere(2)
+    inc = meshgen.plane_wave_x_along_z()
+    t0 = time.perf_counter()
+    pb = pmchwt.PMCHWT(m.verts, m.tris, m.domain, 2.0, 3.17 + 0.01j, precond="D")
+    pb.assemble()
+    t1 = time.perf_counter()
+    x, info = pb.solve(inc[0], tol=1e-6)
+    t2 = time.perf_counter()
+    pb.far_field(x, meshgen.sphere_cut_directions(181))
+    t3 = time.perf_counter()
+    return {"assemble_s": t1 - t0, "gmres_s": t2 - t1, "far_field_s": t3 - t2, "total_s": t3 - t0,
+            "iterations": int(info["iterations"]), "solves_per_s": 1.0 / (t3 - t0)}
+
+
+def _one_core(args):
+    """Run `bench.py <args>` with one thread for OpenMP and the BLAS; its JSON line."""
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    r = subprocess.run([sys.executable, os.path.abspath(__file__), *args], env=env, capture_output=True, text=True,
+                       timeout=600)
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(sample_tris: int):
+    """The oracle (plain FP64 C + numpy) on the host cores, reported beside the GPU.
+
+    value: the headline workload (5120-triangle sphere), extrapolated from a
+    sample of the oracle's assembly (`oracle_sample`; GMRES and far field are
+    excluded there: on the complete 320-triangle solve below they are a few % of
+    the time). Also: the complete 320-triangle solve on all cores, and the same
+    sample on one core.
+    """
+    from oracle import bem
+    bem.build()
+    cores = _host_cores()
+    t_meas, t_extra, desc = oracle_sample(sample_tris)
+    c1 = oracle_c1_solve()
+    one = _one_core(["--oracle-sample", str(max(2, sample_tris // 4))])
+    return {"value": 1.0 / t_extra, "unit": "solves/s", "cores": cores, "kind": "oracle", "extrapolated": True,
+            "sample": f"oracle local blocks for {desc} at k_e and k_i ({t_meas:.2f} s measured), extrapolated by "
+                      "triangle-pair count to the assembly of one solve; GMRES and far field excluded",
+            "c1_full_solve_all_cores": c1,
+            "one_core": {"value": 1.0 / one["extrapolated_s"], "unit": "solves/s", "cores": 1,
+                         "sample": one["sample"], "measured_s": one["measured_s"]}}
 
 
 def run_reference(args, rank, world):
-    """The oracle as it stands on the host cores (rank 0 only)."""
+    """The oracle as it stands on the host cores (rank 0 only): each step is the
+    bounded sample of the headline workload's assembly, the value its
+    extrapolation to one solve (labelled), ms_per_step the time each step took."""
     if rank != 0:
         return None
     from oracle import bem
     bem.build()
     for _ in range(args.warmup):
-        cpu_baseline(4)
-    vals = []
-    for _ in range(args.steps):
-        vals.append(cpu_baseline(args.cpu_sample))
-    v = statistics.median([x["value"] for x in vals])
-    cb = dict(vals[-1])
-    cb["value"] = v
+        oracle_sample(2)
+    meas, vals = [], []
+    desc = ""
+    for q in range(args.steps):
+        t_meas, t_extra, desc = oracle_sample(args.cpu_sample, seed=q)
+        meas.append(t_meas)
+        vals.append(1.0 / t_extra)
+    v = statistics.median(vals)
+    cores = _host_cores()
     return {"metric": "PMCHWT solves/s", "value": v, "unit": "solves/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / v,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(meas),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic (seeded icosphere, plane wave)", "impl": "reference",
-            "config": {"workload": WORKLOAD["name"], "parallelism": "host cores"},
-            "cpu_baseline": cb,
+            "config": {"workload": WORKLOAD["name"], "parallelism": f"host cores ({cores})"},
+            "extrapolated": True,
+            "note": "each step times the oracle's assembly of a sample of test triangles (ms_per_step); value is "
+                    "that sample extrapolated by triangle-pair count to one solve of the workload",
+            "cpu_baseline": {"value": v, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                             "sample": f"oracle local blocks for {desc} at k_e and k_i per step, extrapolated"},
             "e2e": {"value": v, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -731,6 +930,7 @@ def main():
     ap.add_argument("--case", default=None, choices=["bc", "gemv", "gemm", "free", "solve", "multi"],
                     help="run one profiling case and exit (no JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=24, help="test triangles per space for the oracle sample")
+    ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--no-serving", dest="serving", action="store_false",
                     help="skip the request-queue (continuous batching) run")
@@ -738,9 +938,19 @@ def main():
                     help="skip the 32-direction aggregate run")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="skip the preconditioner variants of the headline workload")
+    ap.add_argument("--no-table2", dest="table2", action="store_false",
+                    help="skip the three-cube benchmark of Section 4")
+    ap.add_argument("--no-near-field", dest="near_field", action="store_false",
+                    help="skip the |E|^2 plane map")
     ap.add_argument("--no-matrix-free", dest="matrix_free", action="store_false",
                     help="skip the stored versus matrix-free comparison")
     args = ap.parse_args()
+    if args.oracle_sample:  # one oracle sample, as one JSON line (the one-core baseline runs this)
+        from oracle import bem
+        bem.build()
+        t_meas, t_extra, desc = oracle_sample(args.oracle_sample)
+        print(json.dumps({"measured_s": t_meas, "extrapolated_s": t_extra, "sample": desc}))
+        return
     if args.case:
         run_case(args.case)
         return

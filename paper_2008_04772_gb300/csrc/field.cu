@@ -127,8 +127,18 @@ __global__ void field_sources_kernel(const TriD* __restrict__ tri, const int* __
 }
 
 __device__ __forceinline__ void cis_exp(float kr, float ki, float r, float& c, float& s, float& amp) {
-  sincosf(kr * r, &s, &c);  // full-range reduction: kr r reaches ~100 on the aggregates
-  amp = expf(-ki * r);
+  // phase reduced to [-pi, pi] by Cody–Waite with 2 pi split in two floats (kr r
+  // reaches ~100 on the aggregates), then the hardware sine and cosine
+  constexpr double TWO_PI = 6.283185307179586476925286766559;
+  constexpr float TP_HI = (float)TWO_PI;
+  constexpr float TP_LO = (float)(TWO_PI - (double)(float)TWO_PI);
+  constexpr float INV_TP = (float)(1.0 / TWO_PI);
+  const float ph = kr * r;
+  const float n = rintf(ph * INV_TP);
+  float th = fmaf(-n, TP_HI, ph);
+  th = fmaf(-n, TP_LO, th);
+  __sincosf(th, &s, &c);
+  amp = ki != 0.0f ? __expf(-ki * r) : 1.0f;
 }
 __device__ __forceinline__ void cis_exp(double kr, double ki, double r, double& c, double& s, double& amp) {
   sincos(kr * r, &s, &c);
