@@ -68,6 +68,7 @@ extern "C" {
 
 #define CAL_DENSE 1
 #define CAL_CSR 2
+#define CAL_HMAT 3         /* H-matrix: dense and low-rank (ACA) leaves, Section 3.3 */
 
 /* preconditioners of Section 3.1 (P = A is available for one scatterer, where
    it equals D) */
@@ -198,6 +199,21 @@ int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs
 #define CAL_MATVEC_STATIC_MAX_NRHS 128
 int cal_matvec_static(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
 
+/* H-matrix form of a dense square operator (Section 3.3; the assembly of the
+   paper's software, approximated from the assembled entries): a cluster tree
+   of the basis functions of `space` in the block (median split of the support
+   boxes' centres along the longest side of the cluster box, at most 16 per
+   leaf cluster); a block of two clusters is admissible when their support
+   boxes are disjoint (eq. admissibility), otherwise split down to leaf
+   clusters and kept dense. Admissible leaves within chi of each other are
+   approximated by partially pivoted ACA to the relative tolerance nu (stop when
+   |u_r||v_r| <= nu |sum u_k v_k^T|_F), the others dropped (eq. nf_condition,
+   chi = INFINITY keeps all). The result (format CAL_HMAT) can be exported
+   (densely expanded), applied with cal_matvec, and its info's nnz is the number
+   of stored complex entries of all its operators (S and C together). */
+int cal_op_compress(cal_ctx* ctx, const cal_op* dense, const cal_space* space, double nu, double chi,
+                    cal_op** out);
+
 /* Gram matrix G_ij = <BC_j, RWG_i> = int BC_j . (n x RWG_i) (eqs. MassA,
    MassP: M_A = diag(G, G), M_P = diag(-G^T, -G^T) in the unknown ordering above)
    written densely to dst_host [N][N] float64. For tests of small meshes. */
@@ -224,6 +240,13 @@ typedef struct {
   int32_t matrix_free;      /* 1: A is not stored; its regular pairs are
                                recomputed in every application (only the
                                touching-pair entries are kept, sparse)          */
+  double aca_nu_P;          /* > 0: P's blocks as H-matrices (Section 3.3):
+                               admissible leaves (disjoint support boxes)
+                               within chi_P = near_cutoff_P * h of each other by
+                               ACA to this tolerance, the others dropped,
+                               inadmissible leaves dense (the block-level reading
+                               of eq. nf_condition); 0: dense or entry-level
+                               near-field P                                     */
 } cal_solve_opts;
 void cal_solve_opts_default(cal_solve_opts* opts);
 

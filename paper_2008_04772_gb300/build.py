@@ -20,7 +20,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libcal.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["assemble.cu", "solve.cu", "gemm_tc.cu", "api.cu", "static_scratch.cu", "field.cu"]
+CU_SOURCES = ["assemble.cu", "solve.cu", "gemm_tc.cu", "api.cu", "static_scratch.cu", "field.cu", "hmat.cu"]
 CXX_SOURCES = ["host.cpp", "serve.cpp"]
 
 

@@ -21,7 +21,7 @@ OK, EINVAL, EMESH, ENOMEM, ENOTCONV, ETIMEOUT, ECUDA = 0, -1, -2, -3, -4, -5, -6
 RWG, BC = 1, 2
 OP_S, OP_C = 1, 2
 FP64, FP32, FP32_ALL = 1, 2, 3
-DENSE, CSR = 1, 2
+DENSE, CSR, HMAT = 1, 2, 3
 PRECOND = {"none": 0, "D": 1, "De": 2, "Di": 3, "Se": 4, "Si": 5}
 
 _lib = None
@@ -52,7 +52,7 @@ class SolveOpts(ctypes.Structure):
                 ("near_cutoff_P", ctypes.c_double), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("rhs_mode", ctypes.c_int32),
-                ("matrix_free", ctypes.c_int32)]
+                ("matrix_free", ctypes.c_int32), ("aca_nu_P", ctypes.c_double)]
 
 
 class SolveInfo(ctypes.Structure):
@@ -138,6 +138,7 @@ def lib():
         "cal_matvec": ([P, ctypes.c_int, P, P, i64, P], ctypes.c_int),
         "cal_matvec_static": ([P, ctypes.c_int, P, P, i64, P], ctypes.c_int),
         "cal_near_field": ([P, P, i64, ctypes.c_int, P, P, P], ctypes.c_int),
+        "cal_op_compress": ([P, P, P, ctypes.c_double, ctypes.c_double, P], ctypes.c_int),
         "cal_gram_export": ([P, P, P], ctypes.c_int),
         "cal_solve_opts_default": ([ctypes.POINTER(SolveOpts)], None),
         "cal_pmchwt_solve": ([P, P, d, P, P, P, i64, ctypes.POINTER(SolveOpts), ctypes.POINTER(P)],
@@ -258,6 +259,10 @@ class Operator:
         """Dense [rows, cols] complex array, or (values, row_ptr, col_idx) for CSR."""
         inf = self.info()
         dt = np.complex64 if inf.precision == FP32 else np.complex128
+        if inf.format == HMAT:  # expanded densely
+            vals = np.zeros(inf.rows * inf.cols, dtype=dt)
+            _check(lib().cal_op_export(self.h, which, _ptr(vals), None, None))
+            return vals.reshape(inf.rows, inf.cols)
         vals = np.zeros(inf.nnz, dtype=dt)
         if inf.format == DENSE:
             _check(lib().cal_op_export(self.h, which, _ptr(vals), None, None))
@@ -281,6 +286,14 @@ class Operator:
     def __del__(self):
         if getattr(self, "h", None):
             lib().cal_op_destroy(self.h)
+
+
+def compress(ctx: Context, op: Operator, space: Space, nu: float, chi: float = math.inf) -> Operator:
+    """H-matrix form of a dense square operator (ACA to nu, admissible leaves
+    within chi kept)."""
+    h = ctypes.c_void_p()
+    _check(lib().cal_op_compress(ctx.h, op.h, space.h, float(nu), float(chi), ctypes.byref(h)))
+    return Operator(h, ctx)
 
 
 def assemble(ctx: Context, op_mask: int, k: complex, space: Space, scatterer: int = -1,

@@ -517,6 +517,10 @@ struct Pmchwt {
     b.col = op.format == CAL_CSR ? op.d_col : nullptr;
     if (withS) { b.Sh = op.d_Sh; b.Sl = op.d_Sl; }
     if (withC) { b.Ch = op.d_Ch; b.Cl = op.d_Cl; }
+    if (op.hmat) {
+      b.hmat = op.hmat;
+      b.hmask = (withS ? 1 : 0) | (withC ? 2 : 0);
+    }
     return b;
   }
 
@@ -590,6 +594,16 @@ struct Pmchwt {
   int apply_block(const BlockRef& b, const void* x, void* y, int vec_prec, int nrhs, std::complex<double> al,
                   std::complex<double> be) {
     cudaStream_t st = ctx->stream;
+    if (b.hmat) {
+      const size_t vsz = vec_prec == CAL_FP64 ? sizeof(double2) : sizeof(float2);
+      for (int q = 0; q < nrhs; ++q) {
+        int rc = hmat_pair_apply(*b.hmat, b.hmask & 1, b.hmask & 2, vec_prec, (const char*)x + q * 2 * N * vsz,
+                                 (char*)y + q * 2 * N * vsz, N, b.row_off, al.real(), al.imag(), be.real(), be.imag(),
+                                 st);
+        if (rc) return rc;
+      }
+      return CAL_OK;
+    }
     const bool dense32 = b.precision == CAL_FP32 && !b.rowptr && vec_prec == CAL_FP32;
     if (dense32 && d_Bt && nrhs == nb && gemm_tc_supported(b.cols, nrhs)) {
       int rc;
@@ -957,6 +971,7 @@ void opts_default(cal_solve_opts* o) {
   o->refine = 3;
   o->rhs_mode = 0;
   o->matrix_free = 0;
+  o->aca_nu_P = 0.0;
 }
 
 }  // namespace
@@ -1093,6 +1108,7 @@ int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space*
   op->d_rowptr = nullptr;
   op->d_col = nullptr;
   op->d_Sh = op->d_Sl = op->d_Ch = op->d_Cl = nullptr;
+  op->hmat = nullptr;
   *out = o;
   return CAL_OK;
 }
@@ -1119,6 +1135,21 @@ int cal_op_get_info(const cal_op* op, cal_op_info* info) {
 int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int64_t* col_idx) {
   if (!op || !dst) return fail(CAL_EINVAL, "cal_op_export: NULL argument");
   const Op& o = op->impl;
+  if (o.hmat) {
+    const int q = which == CAL_OP_S ? 0 : (which == CAL_OP_C ? 1 : -1);
+    if (q < 0 || !o.hmat->d_near[q]) return fail(CAL_EINVAL, "cal_op_export: operator %d was not assembled", which);
+    const size_t bytes = (size_t)o.rows * o.cols * (o.precision == CAL_FP32 ? 8 : 16);
+    cudaStream_t st = o.ctx->stream;
+    void* tmp = nullptr;
+    CAL_TRY_CUDA(dalloc(&tmp, bytes, st));
+    int rc = hmat_expand(*o.hmat, q, tmp, st);
+    if (!rc && cudaMemcpyAsync(dst, tmp, bytes, is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                               st) != cudaSuccess)
+      rc = fail(CAL_ECUDA, "cal_op_export: copy failed");
+    dfree(tmp, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = fail(CAL_ECUDA, "cal_op_export: stream failed");
+    return rc;
+  }
   const void* src = which == CAL_OP_S ? o.d_S : (which == CAL_OP_C ? o.d_C : nullptr);
   if (!src) return fail(CAL_EINVAL, "cal_op_export: operator %d was not assembled", which);
   const size_t bytes = (size_t)o.nnz * (o.precision == CAL_FP32 ? 8 : 16);
@@ -1134,6 +1165,25 @@ int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int6
 int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream) {
   if (!op || !x || !y || nrhs < 1) return fail(CAL_EINVAL, "cal_matvec: bad argument");
   const Op& o = op->impl;
+  if (o.hmat) {
+    const int q = which == CAL_OP_S ? 0 : (which == CAL_OP_C ? 1 : -1);
+    if (q < 0 || !o.hmat->d_near[q]) return fail(CAL_EINVAL, "cal_matvec: operator %d was not assembled", which);
+    if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(CAL_EINVAL, "cal_matvec: x and y must be device pointers");
+    cudaStream_t st = stream ? (cudaStream_t)stream : o.ctx->stream;
+    const size_t vsz = o.precision == CAL_FP64 ? sizeof(double2) : sizeof(float2);
+    void* junk = nullptr;  // the second half of the pair form, discarded
+    CAL_TRY_CUDA(dalloc(&junk, o.rows * vsz, st));
+    int rc = CAL_OK;
+    for (int64_t v = 0; v < nrhs && !rc; ++v) {
+      const char* xv = (const char*)x + v * o.cols * vsz;
+      char* yv = (char*)y + v * o.rows * vsz;
+      CAL_TRY_CUDA(cudaMemsetAsync(yv, 0, o.rows * vsz, st));
+      // S: y1 += 1 * S x2 (x2 = x); C: y1 += C x1 (x1 = x)
+      rc = hmat_apply_halves(*o.hmat, q == 0, q == 1, o.precision, xv, xv, yv, junk, 1.0, 0.0, 0.0, 0.0, st);
+    }
+    dfree(junk, st);
+    return rc;
+  }
   const void* X = which == CAL_OP_S ? o.d_S : (which == CAL_OP_C ? o.d_C : nullptr);
   if (!X) return fail(CAL_EINVAL, "cal_matvec: operator %d was not assembled", which);
   if (!is_device_ptr(x) || !is_device_ptr(y)) return fail(CAL_EINVAL, "cal_matvec: x and y must be device pointers");
@@ -1150,6 +1200,26 @@ int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs
                            Xh, Xl);
   }
   return single_apply(o, X, x, y, nrhs, st);
+}
+
+int cal_op_compress(cal_ctx* ctx, const cal_op* dense, const cal_space* space, double nu, double chi,
+                    cal_op** out) {
+  if (!ctx || !dense || !space || !out) return fail(CAL_EINVAL, "cal_op_compress: NULL argument");
+  const Op& d = dense->impl;
+  if (d.format != CAL_DENSE || d.rows != d.cols) return fail(CAL_EINVAL, "cal_op_compress: needs a dense square operator");
+  if (d.row_offset + d.rows > space->impl.nbasis)
+    return fail(CAL_EINVAL, "cal_op_compress: the operator's rows lie outside the space");
+  if (!(nu > 0) || !(chi >= 0)) return fail(CAL_EINVAL, "cal_op_compress: nu must be > 0 and chi >= 0");
+  CAL_TRY_CUDA(cudaSetDevice(ctx->impl.device));
+  auto* o = new cal_op;
+  int rc = hmat_compress(d, space->impl, nu, chi, 512, o->impl, ctx->impl.stream);
+  if (!rc && cudaStreamSynchronize(ctx->impl.stream) != cudaSuccess) rc = fail(CAL_ECUDA, "cal_op_compress: stream failed");
+  if (rc) {
+    delete o;
+    return rc;
+  }
+  *out = o;
+  return CAL_OK;
 }
 
 int cal_gram_export(cal_space* rwg, cal_space* bc, double* dst_host) {
@@ -1224,6 +1294,7 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     return fail(CAL_EINVAL, "solve: bad precision");
   if (o.precond < CAL_PRECOND_NONE || o.precond > CAL_PRECOND_SI) return fail(CAL_EINVAL, "solve: bad preconditioner");
   if (!(o.tol > 0) || o.restart < 1 || o.maxit < 1) return fail(CAL_EINVAL, "solve: bad tolerance/restart/maxit");
+  if (!(o.aca_nu_P >= 0) || !std::isfinite(o.aca_nu_P)) return fail(CAL_EINVAL, "solve: aca_nu_P must be >= 0");
   if (o.rhs_mode != 0 && o.rhs_mode != 1)
     return fail(CAL_EINVAL, "solve: rhs_mode must be 0 (total traces) or 1 (the paper's scattered traces)");
   for (int m = 0; m < P.M; ++m) {
@@ -1315,20 +1386,35 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     const bool ext = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DE || pc == CAL_PRECOND_SE;
     const bool in = pc == CAL_PRECOND_D || pc == CAL_PRECOND_DI || pc == CAL_PRECOND_SI;
     const int want = (pc == CAL_PRECOND_SE || pc == CAL_PRECOND_SI) ? 1 : 3;
-    const double chi = std::isinf(o.near_cutoff_P) ? INFINITY : o.near_cutoff_P * mesh->impl.h;
+    const double chi_abs = std::isinf(o.near_cutoff_P) ? INFINITY : o.near_cutoff_P * mesh->impl.h;
+    const bool aca = o.aca_nu_P > 0;
+    // with ACA the cutoff acts on admissible H-matrix leaves, not on entries
+    const double chi = aca ? INFINITY : chi_abs;
     P.P_ext.resize(P.M);
     P.P_int.resize(P.M);
+    auto to_hmat = [&](std::unique_ptr<Op>& op) -> int {
+      if (!aca || !op) return CAL_OK;
+      auto h = std::make_unique<Op>();
+      int r = hmat_compress(*op, *P.bc, o.aca_nu_P, chi_abs, 512, *h, st);
+      if (r) return r;
+      op = std::move(h);  // the dense block is released in stream order
+      return CAL_OK;
+    };
     for (int m = 0; m < P.M; ++m) {
-      if (ext && (rc = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P,
-                                      o.q_singular_P, aprec, P.P_ext[m])))
+      if (ext && ((rc = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P,
+                                       o.q_singular_P, aprec, P.P_ext[m])) ||
+                  (rc = to_hmat(P.P_ext[m]))))
         return rc;
-      if (in && (rc = assemble_block(ctx->impl, want, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, chi,
-                                     o.q_regular_P, o.q_singular_P, aprec, P.P_int[m])))
+      if (in && ((rc = assemble_block(ctx->impl, want, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, chi,
+                                      o.q_regular_P, o.q_singular_P, aprec, P.P_int[m])) ||
+                 (rc = to_hmat(P.P_int[m]))))
         return rc;
       for (auto* op : {P.P_ext[m].get(), P.P_int[m].get()})
         if (op)
-          bytes_P += op->nnz * esz * ((want & 2) ? 2 : 1) +
-                     (op->format == CAL_CSR ? (int64_t)(op->h_rowptr.size() * 8 + op->h_col.size() * 4) : 0);
+          bytes_P += op->hmat ? op->hmat->stored * (int64_t)esz
+                              : op->nnz * esz * ((want & 2) ? 2 : 1) +
+                                    (op->format == CAL_CSR ? (int64_t)(op->h_rowptr.size() * 8 + op->h_col.size() * 4)
+                                                           : 0);
     }
     // Gram G (rows RWG, cols BC) and its transpose
     std::vector<int64_t> rp, rpT;

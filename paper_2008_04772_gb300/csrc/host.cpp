@@ -823,7 +823,17 @@ Space::~Space() {
   }
 }
 
+HMat::~HMat() {
+  dfree(d_idx, nullptr);
+  dfree(d_near_tab, nullptr);
+  dfree(d_roff_near, nullptr);
+  dfree(d_roff_far, nullptr);
+  for (int q = 0; q < 2; ++q)
+    for (void* p : {d_near[q], d_U[q], d_V[q], (void*)d_far_tab[q], (void*)d_koff[q]}) dfree(p, nullptr);
+}
+
 Op::~Op() {
+  delete hmat;
   dfree(d_S, nullptr);
   dfree(d_C, nullptr);
   for (void* p : {(void*)d_Sh, (void*)d_Sl, (void*)d_Ch, (void*)d_Cl}) dfree(p, nullptr);

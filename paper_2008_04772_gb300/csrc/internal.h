@@ -165,6 +165,47 @@ struct Space {
   ~Space();
 };
 
+// H-matrix form of a square operator block (Section 3.3): the leaves of a block
+// cluster tree over the supports' bounding boxes; inadmissible leaves are kept
+// dense, admissible ones within the cutoff as U V^T from ACA, the rest dropped.
+// Up to two operators (S, C) share the leaves; each has its own ranks.
+struct HLeafD {  // device record of a low-rank leaf
+  int64_t r0, c0, uoff, voff;  // index-list offsets; offsets of U [rank][nr] and V [rank][nc]
+  int nr, nc, rank, pad;
+};
+struct HNearD {  // device record of a dense leaf
+  int64_t r0, c0, off;  // index-list offsets; offset of its [nr][nc] values
+  int nr, nc;
+};
+struct HMat {
+  int64_t n = 0;                 // dofs of the (square) block
+  int precision = CAL_FP64;
+  std::vector<int> idx;          // local dof lists of the leaves, concatenated
+  struct Leaf {
+    int64_t r0, c0;              // offsets into idx
+    int nr, nc;
+    double dist;                 // distance of the cluster boxes
+  };
+  std::vector<Leaf> near, far;   // inadmissible; admissible within the cutoff
+  int64_t near_entries = 0;
+  int* d_idx = nullptr;
+  HNearD* d_near_tab = nullptr;
+  void* d_near[2] = {nullptr, nullptr};     // per operator (0 = S, 1 = C)
+  void* d_U[2] = {nullptr, nullptr};
+  void* d_V[2] = {nullptr, nullptr};
+  HLeafD* d_far_tab[2] = {nullptr, nullptr};
+  std::vector<int> rank[2];
+  // prefix sums for the product: rows of the dense and of the low-rank leaves,
+  // ranks per operator (device copies)
+  int64_t* d_roff_near = nullptr;
+  int64_t* d_roff_far = nullptr;
+  int64_t* d_koff[2] = {nullptr, nullptr};
+  int64_t near_rows = 0, far_rows = 0, ktot[2] = {0, 0};
+  int64_t stored = 0;            // stored complex entries, all operators
+  int max_rank_seen = 0;
+  ~HMat();
+};
+
 struct Op {
   Ctx* ctx = nullptr;
   int op_mask = 0, precision = 0, format = 0;
@@ -182,6 +223,7 @@ struct Op {
   int* d_col = nullptr;
   std::vector<int64_t> h_rowptr; // CSR pattern on the host
   std::vector<int> h_col;
+  HMat* hmat = nullptr;          // CAL_HMAT: the H-matrix form (owned)
   ~Op();
 };
 

@@ -489,6 +489,7 @@ int cal_queue_submit(cal_queue* q, const cal_request* req, int64_t* ticket) {
                          o.q_regular_P, o.q_singular_P, o.matrix_free};
   append_bytes(id, ai, 7);
   append_bytes(id, &o.near_cutoff_P, 1);
+  append_bytes(id, &o.aca_nu_P, 1);
   const std::vector<double> area = scatterer_areas(r->verts, r->tris, r->domain, M);
   r->fp.resident = resident_bytes(r->mesh, area, o);
   r->fp.solve = solve_bytes(r->mesh, o, r->nrhs, r->ndir, r->fp.resident);

@@ -30,6 +30,8 @@ struct BlockRef {
   const float* Sl = nullptr;
   const float* Ch = nullptr;
   const float* Cl = nullptr;
+  const HMat* hmat = nullptr;  // CAL_HMAT block: S and C in H-matrix form
+  int hmask = 0;               // with hmat: bit 1 apply S, bit 2 apply C
 };
 
 // y1 += C x1 + alpha S x2, y2 += C x2 + beta S x1 on the block's rows/cols;
@@ -131,6 +133,16 @@ int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double
 int launch_rwg_mass(const Space& rwg, const int64_t* rowptr, const int* col, double* val, cudaStream_t st);
 int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,
                     double k, double mu, double2* d_out, int precision, cudaStream_t st);
+
+// H-matrix form with ACA (hmat.cu, Section 3.3): out gets the CAL_HMAT form of the
+// dense square block (S and/or C) on the space's supports; leaves within chi
+// kept (ACA to nu, at most max_rank), inadmissible leaves dense
+int hmat_compress(const Op& dense, const Space& sp, double nu, double chi, int max_rank, Op& out, cudaStream_t st);
+int hmat_pair_apply(const HMat& h, bool withS, bool withC, int vec_prec, const void* x, void* y, int64_t ntot,
+                    int64_t off, double ar, double ai, double br, double bi, cudaStream_t st);
+int hmat_apply_halves(const HMat& h, bool withS, bool withC, int vec_prec, const void* x1, const void* x2, void* y1,
+                      void* y2, double ar, double ai, double br, double bi, cudaStream_t st);
+int hmat_expand(const HMat& h, int which, void* dst, cudaStream_t st);
 
 // Near field (field.cu): the Stratton–Chu representations of the solved traces
 // at points off the surface
