@@ -534,49 +534,69 @@ def run_matrix_free(dev):
 
 # Section 4 Table table:multiple_particle: the three cubes (side 0.4, corners at x =
 # -1, 0, 1), n = 1.311 + 2.289e-9 i, E^inc = z e^{ik_e x}, 10 elements per
-# wavelength; P = D with (chi_P, q_P) of the rows the GPU path has (entry-level
-# cutoff in place of ACA: nu_P is not used). Printed values: iterations (matvecs)
-# for k_e = 2.1 and 11.4 (the "7 (582)" rows read as 528, Table tab:matvecs).
+# wavelength; P = D with (chi_P, nu_P, q_P) per row, P's blocks as H-matrices with
+# ACA to nu_P and the block-level cutoff chi_P. Printed values per row: iterations
+# (matvecs) and Mem(P) relative to row 1, for k_e = 2.1 and 11.4 (the "7 (582)"
+# rows read as 528, Table tab:matvecs).
 TABLE2 = {"n": 1.311 + 2.289e-9j, "k": (2.1, 11.4), "tol": 1e-5, "restart": 200,
-          "rows": [("inf, (4,3,2,6)", math.inf, (0, 4), ((6, 456), (9, 672))),
-                   ("inf, (1,1,1,1)", math.inf, (1, 1), ((7, 528), (9, 672))),
-                   ("1.0, (1,1,1,1)", 1.0, (1, 1), ((7, 528), (9, 672))),
-                   ("0.1, (1,1,1,1)", 0.1, (1, 1), ((84, 6072), (16, 1176))),
-                   ("0, (1,1,1,1)", 0.0, (1, 1), ((198, 14280), (36, 2616)))]}
+          "rows": [(math.inf, 0.001, (0, 4), ((6, 456, 1.0), (9, 672, 1.0))),
+                   (math.inf, 0.001, (1, 1), ((7, 528, 1.0), (9, 672, 1.0))),
+                   (math.inf, 0.01, (0, 4), ((6, 456, 0.78), (9, 672, 0.70))),
+                   (math.inf, 0.01, (1, 1), ((7, 528, 0.78), (9, 672, 0.71))),
+                   (math.inf, 0.1, (1, 1), ((7, 528, 0.57), (9, 672, 0.44))),
+                   (math.inf, 0.5, (1, 1), ((9, 672, 0.41), (11, 816, 0.31))),
+                   (1.0, 0.1, (1, 1), ((7, 528, 0.57), (9, 672, 0.44))),
+                   (0.1, 0.1, (1, 1), ((84, 6072, 0.41), (16, 1176, 0.29))),
+                   (0.0, 0.1, (1, 1), ((198, 14280, 0.36), (36, 2616, 0.18)))]}
 
 
 def run_table2(dev):
     """The three-cube benchmark of Section 4 on the GPU (float64, the paper's
-    scattered-trace right-hand side), iterations and matvecs beside Table 2's, and
-    the real-index rerun (n = 1.311) of the first row."""
+    scattered-trace right-hand side, P's blocks as H-matrices with ACA), every
+    row of Table 2 with its iterations, matvecs and Mem(P) relative to row 1
+    beside the printed values, and the real-index rerun of row 1."""
     from paper_2008_04772_gb300 import cal, meshgen
     T = TABLE2
     ctx = cal.Context(dev)
     inc = np.array([[1.0, 0.0, 0.0, 0.0, 0.0, 1.0]])
     out = {"workload": "three cubes of side 0.4, n = 1.311 + 2.289e-9i, E^inc = z e^{ik x}, h = 2 pi / (10 k)",
            "precision": "float64", "rhs": "scattered traces (rhs_mode 1)", "tol": T["tol"],
-           "note": "chi_P absolute (cutoff between supports, reading 7); nu_P (ACA) not used: P is dense or "
-                   "near-field CSR", "rows": {}}
+           "note": "A is dense (the paper's A is an H-matrix with nu_A = 0.001); P = D as H-matrices (ACA to nu_P, "
+                   "admissible leaves beyond chi_P dropped); q_P (4,3,2,6) = class rules and order-4 singular rules",
+           "rows": {}}
     for ki, k in enumerate(T["k"]):
         m = meshgen.three_cubes(2 * math.pi / (10 * k))
         mesh = cal.Mesh(ctx, m.verts, m.tris, m.domain)
         h = mesh.info().h
         key = f"k={k}"
         out[key] = {"triangles": int(len(m.tris)), "unknowns": 2 * int(mesh.info().n_edges)}
-        for name, chi, (qr, qs), printed in T["rows"]:
+        mem1 = None
+        for chi, nu, (qr, qs), printed in T["rows"]:
+            name = f"chi={chi}, nu={nu}, q={'(4,3,2,6)' if qr == 0 else '(1,1,1,1)'}"
             opts = cal.solve_opts(precond="D", precision=cal.FP64, tol=T["tol"], restart=T["restart"], maxit=2000,
                                   rhs_mode=1, q_regular_A=0, q_singular_A=4, q_regular_P=qr, q_singular_P=qs,
-                                  near_cutoff_P=(chi / h if math.isfinite(chi) else math.inf))
+                                  aca_nu_P=nu, near_cutoff_P=(chi / h if math.isfinite(chi) else math.inf))
             t0 = time.perf_counter()
             info = cal.pmchwt_solve(ctx, mesh, k, T["n"] ** 2, inc, opts=opts, allow_not_converged=True).info()
+            mem1 = mem1 or info.bytes_P
             out["rows"].setdefault(name, {})[key] = {
                 "iterations": int(info.iterations), "matvecs": int(info.matvecs),
-                "paper": {"iterations": printed[ki][0], "matvecs": printed[ki][1]},
-                "bytes_P_mb": info.bytes_P / 1e6, "seconds": time.perf_counter() - t0}
+                "mem_P_rel": info.bytes_P / mem1, "bytes_P_mb": info.bytes_P / 1e6,
+                "paper": {"iterations": printed[ki][0], "matvecs": printed[ki][1], "mem_P_rel": printed[ki][2]},
+                "seconds": time.perf_counter() - t0}
         opts = cal.solve_opts(precond="D", precision=cal.FP64, tol=T["tol"], restart=T["restart"], maxit=2000,
-                              rhs_mode=1, q_regular_A=0, q_regular_P=0)
+                              rhs_mode=1, q_regular_A=0, q_regular_P=0, aca_nu_P=0.001)
         info = cal.pmchwt_solve(ctx, mesh, k, T["n"].real ** 2, inc, opts=opts, allow_not_converged=True).info()
         out[key]["real_index_row1"] = {"iterations": int(info.iterations), "matvecs": int(info.matvecs)}
+        # the last row: the mixed discretisation (P = D from A's blocks, dense, total traces)
+        t0 = time.perf_counter()
+        opts = cal.solve_opts(precond="D", precision=cal.FP64, tol=T["tol"], restart=T["restart"], maxit=2000,
+                              q_regular_A=0, discretisation=1)
+        info = cal.pmchwt_solve(ctx, mesh, k, T["n"] ** 2, inc, opts=opts, allow_not_converged=True).info()
+        out["rows"].setdefault("mixed discretisation, P = D", {})[key] = {
+            "iterations": int(info.iterations), "matvecs": int(info.matvecs),
+            "paper": {"iterations": (5, 9)[ki], "matvecs": (384, 672)[ki]},
+            "bytes_A_plus_P_mb": (info.bytes_A + info.bytes_P) / 1e6, "seconds": time.perf_counter() - t0}
     return out
 
 

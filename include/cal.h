@@ -247,6 +247,14 @@ typedef struct {
                                inadmissible leaves dense (the block-level reading
                                of eq. nf_condition); 0: dense or entry-level
                                near-field P                                     */
+  int32_t discretisation;   /* 0: eq. RWG_discretisation1 (RWG for A, BC for P);
+                               1: the mixed discretisation of eq.
+                               mixed_discretisation: each scatterer's traces in
+                               (RWG_m, BC_m) for trial and test alike, RWG
+                               written on the barycentric refinement for the
+                               blocks C(RWG, BC), C(BC, RWG); P = D reuses A's
+                               diagonal blocks; float64 (CAL_FP64) only, precond
+                               CAL_PRECOND_D, total-trace right-hand side       */
 } cal_solve_opts;
 void cal_solve_opts_default(cal_solve_opts* opts);
 

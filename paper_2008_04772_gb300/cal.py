@@ -52,7 +52,8 @@ class SolveOpts(ctypes.Structure):
                 ("near_cutoff_P", ctypes.c_double), ("tol", ctypes.c_double),
                 ("restart", ctypes.c_int32), ("maxit", ctypes.c_int32),
                 ("refine", ctypes.c_int32), ("rhs_mode", ctypes.c_int32),
-                ("matrix_free", ctypes.c_int32), ("aca_nu_P", ctypes.c_double)]
+                ("matrix_free", ctypes.c_int32), ("aca_nu_P", ctypes.c_double),
+                ("discretisation", ctypes.c_int32)]
 
 
 class SolveInfo(ctypes.Structure):

@@ -348,6 +348,7 @@ std::complex<double> interior_k(double k_e, std::complex<double> eps, std::compl
 struct cal_solution {
   Ctx* ctx = nullptr;
   std::shared_ptr<Space> rwg;  // shared with the problem it came from
+  std::shared_ptr<Space> bc;   // the mixed discretisation: the space of the second trace
   double2* d_x = nullptr;  // [nrhs][2N]
   // rhs_mode 1: the L2 projection of u^inc onto RWG [nrhs][2N], so that the total
   // trace is d_x + d_cinc (the interior representation needs total traces)
@@ -395,6 +396,20 @@ struct Pmchwt {
   double* d_mval = nullptr;
   int64_t mnnz = 0;
   std::unique_ptr<GramSolver<double>> gsM;
+  // the mixed discretisation (eq. mixed_discretisation, float64): S on RWG (A_ext,
+  // A_int), S on BC (Sb_ext on the union, Sb_int per scatterer), C between RWG on
+  // the barycentric refinement and BC (dense, rows first: Crb = <C BC, RWG>,
+  // Cbr = <C RWG, BC>), the RWG slots on the barycentric triangles, and one Gram
+  // solver per half
+  bool mixed = false;
+  std::unique_ptr<Op> Sb_ext;
+  std::vector<std::unique_ptr<Op>> Sb_int;
+  double2* Crb_ext = nullptr;
+  double2* Cbr_ext = nullptr;
+  std::vector<double2*> Crb_int, Cbr_int;
+  int* d_redge = nullptr;
+  double* d_rsw = nullptr;
+  std::unique_ptr<GramSolver<double>> gmA, gmP;
   // batch of right-hand sides advanced in lockstep
   int nb = 1;
   // work vectors [nb][2N] (complex128-sized)
@@ -429,6 +444,9 @@ struct Pmchwt {
       dfree(p, st);
     free_combo(cA);
     for (auto& c : cP) free_combo(c);
+    for (void* p : {(void*)Crb_ext, (void*)Cbr_ext, (void*)d_redge, (void*)d_rsw}) dfree(p, st);
+    for (auto* v : {&Crb_int, &Cbr_int})
+      for (double2* p : *v) dfree(p, st);
   }
   static void free_combo(Combo& c) {
     for (void* p : {c.C, c.S1, c.S2}) dfree(p, nullptr);
@@ -544,7 +562,14 @@ struct Pmchwt {
     gsP64.reset();
     cudaStream_t st = ctx->stream;
     int rc;
-    if (o.precond != CAL_PRECOND_NONE) {
+    if (mixed) {
+      gmA.reset();
+      gmP.reset();
+      gmA = std::make_unique<GramSolver<double>>();
+      gmP = std::make_unique<GramSolver<double>>();
+      if ((rc = gmA->init(d_grp, d_gcol, d_gval, N, 1, gnnz, 1.0, 1e-13, 30, st))) return rc;
+      if ((rc = gmP->init(d_grpT, d_gcolT, d_gvalT, N, 1, gnnz, -1.0, 1e-13, 30, st))) return rc;
+    } else if (o.precond != CAL_PRECOND_NONE) {
       // M_A = diag(G, G); M_P = diag(-G^T, -G^T): two component systems per vector
       if (o.precision == CAL_FP64) {
         gsA64 = std::make_unique<GramSolver<double>>();
@@ -671,6 +696,78 @@ struct Pmchwt {
     return CAL_OK;
   }
 
+  // ---- the mixed discretisation ------------------------------------------
+  // RWG on the barycentric refinement: on a child tau of primal triangle t the
+  // piece sigma (x - c_t) + w_t is sigma (x - c_tau) + (w_t + sigma (c_tau - c_t))
+  int build_rwgb(cudaStream_t st) {
+    const Space& R = *rwg;
+    const Space& B = *bc;
+    std::vector<int> edge(3 * B.ntri);
+    std::vector<double> sw(12 * B.ntri);
+    for (int64_t tau = 0; tau < B.ntri; ++tau) {
+      const int t = B.parent[tau];
+      for (int a = 0; a < 3; ++a) {
+        edge[3 * tau + a] = R.slot_edge[3 * t + a];
+        const double* ps = &R.slot_sw[(3 * (size_t)t + a) * 4];
+        double* q = &sw[(3 * (size_t)tau + a) * 4];
+        q[0] = ps[0];
+        for (int c = 0; c < 3; ++c) q[1 + c] = ps[1 + c] + ps[0] * (B.triD[tau].c[c] - R.triD[t].c[c]);
+      }
+    }
+    CAL_TRY_CUDA(dalloc((void**)&d_redge, edge.size() * sizeof(int), st));
+    CAL_TRY_CUDA(dalloc((void**)&d_rsw, sw.size() * sizeof(double), st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(d_redge, edge.data(), edge.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(d_rsw, sw.data(), sw.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));  // the host tables are read by the copies
+    return CAL_OK;
+  }
+
+  // y += the mixed block of one wavenumber on rows/cols [off, off + n):
+  // y1 += -(k/mu) Srr x1 + Crb x2, y2 += Cbr x1 + (mu/k) Sbb x2, the four
+  // matrices at (r0, r0) of their storage with leading dimension ld
+  int mixed_block(const double2* Srr, const double2* Sbb, const double2* Crb, const double2* Cbr, int64_t ld,
+                  int64_t r0, int64_t off, int64_t n, std::complex<double> k, std::complex<double> mu,
+                  const double2* x, double2* y) {
+    cudaStream_t st = ctx->stream;
+    const int64_t at = r0 * ld + r0;
+    const double2 *x1 = x + off, *x2 = x + N + off;
+    double2 *y1 = y + off, *y2 = y + N + off;
+    int rc;
+    if ((rc = gemv_acc(Srr + at, ld, n, n, x1, y1, -k / mu, st)) || (rc = gemv_acc(Crb + at, ld, n, n, x2, y1, 1.0, st)) ||
+        (rc = gemv_acc(Cbr + at, ld, n, n, x1, y2, 1.0, st)) || (rc = gemv_acc(Sbb + at, ld, n, n, x2, y2, mu / k, st)))
+      return rc;
+    return CAL_OK;
+  }
+
+  // y = A x (diag_only: the diagonal blocks, P = D), float64, one vector
+  int mixed_apply(const double2* x, double2* y, bool diag_only) {
+    cudaStream_t st = ctx->stream;
+    int rc = zero_vec(y, CAL_FP64, 2 * N, st);
+    if (rc) return rc;
+    const double2* SeR = (const double2*)A_ext->d_S;
+    const double2* SeB = (const double2*)Sb_ext->d_S;
+    if (!diag_only) {
+      if ((rc = mixed_block(SeR, SeB, Crb_ext, Cbr_ext, N, 0, 0, N, k_e, 1.0, x, y))) return rc;
+    }
+    for (int m = 0; m < M; ++m) {
+      const int64_t off = A_int[m]->row_offset, n = A_int[m]->rows;
+      if (diag_only && (rc = mixed_block(SeR, SeB, Crb_ext, Cbr_ext, N, off, off, n, k_e, 1.0, x, y))) return rc;
+      if ((rc = mixed_block((const double2*)A_int[m]->d_S, (const double2*)Sb_int[m]->d_S, Crb_int[m], Cbr_int[m], n,
+                            0, off, n, k_m[m], mu_m[m], x, y)))
+        return rc;
+    }
+    matvecs += diag_only ? 8LL * M : 4LL * M * M + 4LL * M;
+    return CAL_OK;
+  }
+
+  // w = M^-1 y with M = [[0, G], [-G^T, 0]]: w2 = G^-1 y1, w1 = -G^-T y2
+  int mixed_minv(const double2* y, double2* w) {
+    cudaStream_t st = ctx->stream;
+    int rc;
+    if ((rc = gmA->solve(y, w + N, st))) return rc;
+    return gmP->solve(y + N, w, st);
+  }
+
   // y = A^i x = diag(A^i_m) x, the interior blocks only (y overwritten)
   int apply_Ai(const void* x, void* y, int vec_prec, int nrhs) {
     cudaStream_t st = ctx->stream;
@@ -786,6 +883,12 @@ struct Pmchwt {
     cudaStream_t st = ctx->stream;
     int rc;
     const int64_t n2 = 2 * N * nrhs;
+    if (mixed) {  // w = M^-1 D M^-1 y (one vector)
+      double2* a = (double2*)t1;
+      double2* b = (double2*)t2;
+      if ((rc = mixed_minv(y, a)) || (rc = mixed_apply(a, b, true))) return rc;
+      return mixed_minv(b, w);
+    }
     if (o.precond == CAL_PRECOND_NONE) {
       CAL_TRY_CUDA(cudaMemcpyAsync(w, y, n2 * sizeof(double2), cudaMemcpyDeviceToDevice, st));
       return CAL_OK;
@@ -811,6 +914,10 @@ struct Pmchwt {
     int rc;
     cudaStream_t st = ctx->stream;
     const int64_t n2 = 2 * N * nb;
+    if (mixed) {
+      if ((rc = mixed_apply(v, scratch, false))) return rc;
+      return apply_precond(scratch, w, 1);
+    }
     if (o.precision == CAL_FP64) {
       if ((rc = apply_A(v, scratch, CAL_FP64, nb))) return rc;
       return apply_precond(scratch, w, nb);
@@ -972,6 +1079,7 @@ void opts_default(cal_solve_opts* o) {
   o->rhs_mode = 0;
   o->matrix_free = 0;
   o->aca_nu_P = 0.0;
+  o->discretisation = 0;
 }
 
 }  // namespace
@@ -1295,6 +1403,11 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   if (o.precond < CAL_PRECOND_NONE || o.precond > CAL_PRECOND_SI) return fail(CAL_EINVAL, "solve: bad preconditioner");
   if (!(o.tol > 0) || o.restart < 1 || o.maxit < 1) return fail(CAL_EINVAL, "solve: bad tolerance/restart/maxit");
   if (!(o.aca_nu_P >= 0) || !std::isfinite(o.aca_nu_P)) return fail(CAL_EINVAL, "solve: aca_nu_P must be >= 0");
+  if (o.discretisation != 0 && o.discretisation != 1) return fail(CAL_EINVAL, "solve: discretisation must be 0 or 1");
+  if (o.discretisation == 1 && (o.precision != CAL_FP64 || o.precond != CAL_PRECOND_D || o.matrix_free ||
+                                o.rhs_mode != 0 || o.aca_nu_P > 0))
+    return fail(CAL_EINVAL,
+                "solve: the mixed discretisation needs CAL_FP64, CAL_PRECOND_D, stored A, rhs_mode 0 and no ACA");
   if (o.rhs_mode != 0 && o.rhs_mode != 1)
     return fail(CAL_EINVAL, "solve: rhs_mode must be 0 (total traces) or 1 (the paper's scattered traces)");
   for (int m = 0; m < P.M; ++m) {
@@ -1360,11 +1473,13 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
                                         aprec, P.A_int[m])))
         return rc;
   } else {
-    if ((rc = assemble_block(ctx->impl, 3, k_ext, 0.0, *P.rwg, -1, INFINITY, o.q_regular_A, o.q_singular_A,
+    P.mixed = o.discretisation == 1;
+    const int wantA = P.mixed ? 1 : 3;  // the mixed form takes C between RWG and BC instead
+    if ((rc = assemble_block(ctx->impl, wantA, k_ext, 0.0, *P.rwg, -1, INFINITY, o.q_regular_A, o.q_singular_A,
                              aprec, P.A_ext)))
       return rc;
     for (int m = 0; m < P.M; ++m)
-      if ((rc = assemble_block(ctx->impl, 3, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, INFINITY,
+      if ((rc = assemble_block(ctx->impl, wantA, P.k_m[m].real(), P.k_m[m].imag(), *P.rwg, m, INFINITY,
                                o.q_regular_A, o.q_singular_A, aprec, P.A_int[m])))
         return rc;
   }
@@ -1400,7 +1515,42 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
       op = std::move(h);  // the dense block is released in stream order
       return CAL_OK;
     };
-    for (int m = 0; m < P.M; ++m) {
+    if (P.mixed) {
+      // S on BC (union and per scatterer) and C between RWG and BC, A's rules
+      if ((rc = P.build_rwgb(st))) return rc;
+      if ((rc = assemble_block(ctx->impl, 1, k_ext, 0.0, *P.bc, -1, INFINITY, o.q_regular_A, o.q_singular_A,
+                               CAL_FP64, P.Sb_ext)))
+        return rc;
+      const size_t b2 = (size_t)P.N * P.N * sizeof(double2);
+      CAL_TRY_CUDA(dalloc((void**)&P.Crb_ext, b2, st));
+      CAL_TRY_CUDA(dalloc((void**)&P.Cbr_ext, b2, st));
+      CAL_TRY_CUDA(cudaMemsetAsync(P.Crb_ext, 0, b2, st));
+      CAL_TRY_CUDA(cudaMemsetAsync(P.Cbr_ext, 0, b2, st));
+      if ((rc = launch_cross_c(*P.bc, P.d_redge, P.d_rsw, -1, k_ext, 0.0, o.q_regular_A, o.q_singular_A, 0, P.N,
+                               (double*)P.Crb_ext, (double*)P.Cbr_ext, st)))
+        return rc;
+      bytes_P += (int64_t)(b2 * 2 + P.Sb_ext->nnz * 16);
+      P.Sb_int.resize(P.M);
+      P.Crb_int.assign(P.M, nullptr);
+      P.Cbr_int.assign(P.M, nullptr);
+      for (int m = 0; m < P.M; ++m) {
+        if ((rc = assemble_block(ctx->impl, 1, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, INFINITY, o.q_regular_A,
+                                 o.q_singular_A, CAL_FP64, P.Sb_int[m])))
+          return rc;
+        const int64_t nm = P.Sb_int[m]->rows;
+        const size_t bm = (size_t)nm * nm * sizeof(double2);
+        CAL_TRY_CUDA(dalloc((void**)&P.Crb_int[m], bm, st));
+        CAL_TRY_CUDA(dalloc((void**)&P.Cbr_int[m], bm, st));
+        CAL_TRY_CUDA(cudaMemsetAsync(P.Crb_int[m], 0, bm, st));
+        CAL_TRY_CUDA(cudaMemsetAsync(P.Cbr_int[m], 0, bm, st));
+        if ((rc = launch_cross_c(*P.bc, P.d_redge, P.d_rsw, m, P.k_m[m].real(), P.k_m[m].imag(), o.q_regular_A,
+                                 o.q_singular_A, P.Sb_int[m]->row_offset, nm, (double*)P.Crb_int[m],
+                                 (double*)P.Cbr_int[m], st)))
+          return rc;
+        bytes_P += (int64_t)(bm * 2 + P.Sb_int[m]->nnz * 16);
+      }
+    }
+    for (int m = 0; m < P.M && !P.mixed; ++m) {
       if (ext && ((rc = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P,
                                        o.q_singular_P, aprec, P.P_ext[m])) ||
                   (rc = to_hmat(P.P_ext[m]))))
@@ -1488,7 +1638,12 @@ int cal_problem_apply(cal_ctx* ctx, cal_problem* prob, const double* x, double* 
   }
   int rc = CAL_OK;
   if (cudaMemcpyAsync(dx, x, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) rc = fail(CAL_ECUDA, "copy failed");
-  if (!rc) rc = P.apply_A(dx, dy, CAL_FP64, (int)nrhs);
+  if (!rc && P.mixed) {
+    for (int64_t q = 0; q < nrhs && !rc; ++q)
+      rc = P.mixed_apply((const double2*)dx + q * 2 * P.N, (double2*)dy + q * 2 * P.N, false);
+  } else if (!rc) {
+    rc = P.apply_A(dx, dy, CAL_FP64, (int)nrhs);
+  }
   if (!rc && cudaMemcpyAsync(y, dy, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess) rc = fail(CAL_ECUDA, "copy failed");
   dfree(dx, st);
   dfree(dy, st);
@@ -1552,7 +1707,8 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   cudaStream_t st = ctx->impl.stream;
   const double t0 = now();
   int rc;
-  const int nbatch = (int)std::min<int64_t>(nrhs, 32);
+  const int nbatch = P.mixed ? 1 : (int)std::min<int64_t>(nrhs, 32);
+  if (P.mixed && P.o.rhs_mode != 0) return fail(CAL_EINVAL, "solve: the mixed discretisation takes rhs_mode 0");
   if ((rc = P.setup_batch(nbatch))) return rc;
   if (P.d_gemm_err) CAL_TRY_CUDA(cudaMemsetAsync(P.d_gemm_err, 0, sizeof(int), st));
   // right-hand sides and solves
@@ -1583,6 +1739,21 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   };
   Guard g1{d_b, st}, g2{d_rhs, st}, g3{d_r, st}, g4{d_inc, st};
   if ((rc = launch_rhs(*P.rwg, d_inc, (int)nrhs, P.k_e, 1.0, d_b, st))) return rc;
+  if (P.mixed) {
+    // rows tested with RWG take the second trace component, rows tested with BC
+    // the first: b = (b_RWG second half, b_BC first half)
+    double2* d_bb = nullptr;
+    CAL_TRY_CUDA(dalloc((void**)&d_bb, nrhs * n2 * sizeof(double2), st));
+    Guard gbb{d_bb, st};
+    if ((rc = launch_rhs(*P.bc, d_inc, (int)nrhs, P.k_e, 1.0, d_bb, st))) return rc;
+    for (int64_t q = 0; q < nrhs; ++q) {
+      CAL_TRY_CUDA(cudaMemcpyAsync(d_b + q * n2, d_b + q * n2 + P.N, P.N * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                   st));
+      CAL_TRY_CUDA(cudaMemcpyAsync(d_b + q * n2 + P.N, d_bb + q * n2, P.N * sizeof(double2), cudaMemcpyDeviceToDevice,
+                                   st));
+    }
+    CAL_TRY_CUDA(cudaStreamSynchronize(st));
+  }
   if (o.rhs_mode == 1) {
     CAL_TRY_CUDA(dalloc((void**)&sol->d_cinc, nrhs * n2 * sizeof(double2), st));
     if ((rc = P.scattered_rhs(d_inc, nrhs, d_b, sol->d_cinc))) return rc;
@@ -1679,9 +1850,12 @@ int cal_problem_solve(cal_ctx* ctx, cal_problem* prob, const double* inc, int64_
   if (P.gsP32 && (rc = P.gsP32->check(st))) return rc;
   if (P.gsA64 && (rc = P.gsA64->check(st))) return rc;
   if (P.gsP64 && (rc = P.gsP64->check(st))) return rc;
+  if (P.gmA && (rc = P.gmA->check(st))) return rc;
+  if (P.gmP && (rc = P.gmP->check(st))) return rc;
   CAL_TRY_CUDA(cudaStreamSynchronize(st));
   const double t_end = now();
   sol->rwg = P.rwg;
+  if (P.mixed) sol->bc = P.bc;  // the second trace is expanded in BC
   cal_solve_info& info = sol->info;
   info.iterations = total_it;
   info.converged = all_conv;
@@ -1737,8 +1911,10 @@ int cal_farfield(const cal_solution* sol, const double* dirs, int64_t ndir, doub
   CAL_TRY_CUDA(dalloc((void**)&d_dirs, 3 * ndir * sizeof(double), st));
   CAL_TRY_CUDA(dalloc((void**)&d_out, sol->nrhs * ndir * 3 * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemcpyAsync(d_dirs, dirs, 3 * ndir * sizeof(double), cudaMemcpyHostToDevice, st));
-  int rc = launch_farfield(*sol->rwg, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e, sol->mu_e, d_out,
-                           sol->precision, st);
+  int rc = sol->bc ? launch_farfield_mixed(*sol->rwg, *sol->bc, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e,
+                                           sol->mu_e, d_out, st)
+                   : launch_farfield(*sol->rwg, sol->d_x, (int)sol->nrhs, d_dirs, ndir, sol->k_e, sol->mu_e, d_out,
+                                     sol->precision, st);
   if (!rc) {
     CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, sol->nrhs * ndir * 3 * sizeof(double2), cudaMemcpyDeviceToHost, st));
     CAL_TRY_CUDA(cudaStreamSynchronize(st));
@@ -1762,6 +1938,7 @@ int cal_near_field(const cal_solution* sol, const double* points, int64_t npt, i
         return fail(CAL_EINVAL, "cal_near_field: region %d of point %lld outside [-1, %d)", region_in[i],
                     (long long)i, M);
   if ((int)sol->k_m.size() != M) return fail(CAL_EINVAL, "cal_near_field: solution without material data");
+  if (sol->bc) return fail(CAL_EINVAL, "cal_near_field: not available for the mixed discretisation");
   CAL_TRY_CUDA(cudaSetDevice(sol->ctx->device));
   cudaStream_t st = sol->ctx->stream;
   double* d_pts = nullptr;

@@ -1664,15 +1664,12 @@ __device__ __forceinline__ void radial_sums(const double* gx, const double* gw, 
 // Reference-coordinate moments MG, Mg (18 reals each: (re, im) of the nine
 // monomials) -> centroid-relative moments -> pair coefficients -> entries of
 // the (test slot, trial slot) combinations q = first, first + step, ...
-template <typename RO>
-__device__ __forceinline__ void sing_emit(const double* MG, const double* Mg, const V3<double>* Q1,
-                                          const V3<double>* Q2, const V3<double>& ea, const V3<double>& eb,
-                                          const V3<double>& ec, const V3<double>& ed, const V3<double>& D,
-                                          const SingPair& sp, const int* __restrict__ slot_edge,
-                                          const double* __restrict__ slot_sw, int nslot, double mikr, double miki,
-                                          double c4r, double c4i, bool wantS, bool doC, int first, int step,
-                                          const Sink<RO>& out) {
-  const int cls = sp.cls;
+// pair coefficients (the layout of pair_coeffs) of a touching pair from its
+// float64 monomial moments and parametrisation
+__device__ __forceinline__ void sing_pair_coeffs(const double* MG, const double* Mg, const V3<double>* Q1,
+                                                 const V3<double>* Q2, const V3<double>& ea, const V3<double>& eb,
+                                                 const V3<double>& ec, const V3<double>& ed, const V3<double>& D,
+                                                 double* pc) {
   // x = q0 + x0 a + x1 b, y = p0 + y0 c + y1 d
   const V3<double> q0 = Q1[0], p0 = Q2[0];
   const V3<double> vx[3] = {q0, ea, eb};  // factors of 1, x0, x1
@@ -1710,8 +1707,20 @@ __device__ __forceinline__ void sing_emit(const double* MG, const double* Mg, co
       m.g0i = g0; m.gxi = gx; m.gyi = gy; m.gxyi = gxy;
     }
   }
-  double pc[36];
   pair_coeffs(m, D, pc);
+}
+
+template <typename RO>
+__device__ __forceinline__ void sing_emit(const double* MG, const double* Mg, const V3<double>* Q1,
+                                          const V3<double>* Q2, const V3<double>& ea, const V3<double>& eb,
+                                          const V3<double>& ec, const V3<double>& ed, const V3<double>& D,
+                                          const SingPair& sp, const int* __restrict__ slot_edge,
+                                          const double* __restrict__ slot_sw, int nslot, double mikr, double miki,
+                                          double c4r, double c4i, bool wantS, bool doC, int first, int step,
+                                          const Sink<RO>& out) {
+  const int cls = sp.cls;
+  double pc[36];
+  sing_pair_coeffs(MG, Mg, Q1, Q2, ea, eb, ec, ed, D, pc);
   for (int q = first; q < nslot * nslot; q += step) {
     const int a = q / nslot, b = q % nslot;
     const int e1 = slot_edge[(size_t)sp.t1 * nslot + a];
@@ -1736,38 +1745,35 @@ __device__ __forceinline__ void sing_emit(const double* MG, const double* Mg, co
 // each (region, e1, e2, e3) a lane therefore forms rho and the monomials once
 // and sums the kernel over the Gauss nodes of xi in three radial sums (xi^0,
 // xi^1, xi^2); the same quadrature points and weights as the direct form.
-template <typename RO>
-__global__ void __launch_bounds__(128) singular_kernel(
-    const TriD* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
-    const int* __restrict__ slot_edge, const double* __restrict__ slot_sw, int nslot, double kr,
-    double ki, double mikr, double miki, double c4r, double c4i, bool wantS, bool wantC,
-    Rules rl, Sink<RO> out) {
-  const int lane = threadIdx.x & 31;
-  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (p >= np) return;
-  const SingPair sp = pairs[p];
-  const TriD A = tri[sp.t1];
-  const TriD B = tri[sp.t2];
+// The float64 monomial moments of one ordered touching pair, summed over the
+// warp (every lane gets them), with the pair's parametrisation: corners Q1, Q2
+// relative to each centroid (shared vertices first), edge vectors and D.
+struct SingGeom {
+  V3<double> Q1[3], Q2[3], ea, eb, ec, ed, D;
+};
+
+__device__ __forceinline__ void sing_pair_moments(const TriD& A, const TriD& B, const SingPair& sp, double kr,
+                                                  double ki, bool doC, const Rules& rl, int lane, SingGeom& gm,
+                                                  double* MG, double* Mg) {
   const int cls = sp.cls;
-  const bool doC = wantC && cls != 3;  // flat identical panels: C vanishes
-  // parametrisation corners relative to each centroid, shared vertices first
-  V3<double> Q1[3], Q2[3];
+  V3<double>* Q1 = gm.Q1;
+  V3<double>* Q2 = gm.Q2;
   for (int a = 0; a < 3; ++a) {
     Q1[a] = {A.off[sp.o1[a]][0], A.off[sp.o1[a]][1], A.off[sp.o1[a]][2]};
     Q2[a] = {B.off[sp.o2[a]][0], B.off[sp.o2[a]][1], B.off[sp.o2[a]][2]};
   }
-  const V3<double> ea = {Q1[1].x - Q1[0].x, Q1[1].y - Q1[0].y, Q1[1].z - Q1[0].z};
-  const V3<double> eb = {Q1[2].x - Q1[1].x, Q1[2].y - Q1[1].y, Q1[2].z - Q1[1].z};
-  const V3<double> ec = {Q2[1].x - Q2[0].x, Q2[1].y - Q2[0].y, Q2[1].z - Q2[0].z};
-  const V3<double> ed = {Q2[2].x - Q2[1].x, Q2[2].y - Q2[1].y, Q2[2].z - Q2[1].z};
-  const V3<double> D = {A.c[0] - B.c[0], A.c[1] - B.c[1], A.c[2] - B.c[2]};
+  gm.ea = {Q1[1].x - Q1[0].x, Q1[1].y - Q1[0].y, Q1[1].z - Q1[0].z};
+  gm.eb = {Q1[2].x - Q1[1].x, Q1[2].y - Q1[1].y, Q1[2].z - Q1[1].z};
+  gm.ec = {Q2[1].x - Q2[0].x, Q2[1].y - Q2[0].y, Q2[1].z - Q2[0].z};
+  gm.ed = {Q2[2].x - Q2[1].x, Q2[2].y - Q2[1].y, Q2[2].z - Q2[1].z};
+  gm.D = {A.c[0] - B.c[0], A.c[1] - B.c[1], A.c[2] - B.c[2]};
+  const V3<double> ea = gm.ea, eb = gm.eb, ec = gm.ec, ed = gm.ed;
   const double scale = 4.0 * A.area * B.area;
   const int ng = rl.ng, nreg = (cls == 3 ? 6 : (cls == 2 ? 5 : 2));
   const int ng2 = ng * ng, ng3 = ng2 * ng;
   constexpr double INV_4PI = 0.25 / 3.14159265358979323846;
   // monomial moments sum K w m(x, y), m in {1, x0, x1, y0, y1, x0 y0, x0 y1,
   // x1 y0, x1 y1} (reference coordinates), K = G and g; (re, im) pairs
-  double MG[18], Mg[18];
 #pragma unroll
   for (int q = 0; q < 18; ++q) MG[q] = Mg[q] = 0.0;
   for (int idx = lane; idx < nreg * ng3; idx += 32) {
@@ -1816,8 +1822,26 @@ __global__ void __launch_bounds__(128) singular_kernel(
     MG[q] = v;
     Mg[q] = u;
   }
-  sing_emit(MG, Mg, Q1, Q2, ea, eb, ec, ed, D, sp, slot_edge, slot_sw, nslot, mikr, miki, c4r, c4i, wantS, doC,
-            lane, 32, out);
+}
+
+template <typename RO>
+__global__ void __launch_bounds__(128) singular_kernel(
+    const TriD* __restrict__ tri, const SingPair* __restrict__ pairs, int64_t np,
+    const int* __restrict__ slot_edge, const double* __restrict__ slot_sw, int nslot, double kr,
+    double ki, double mikr, double miki, double c4r, double c4i, bool wantS, bool wantC,
+    Rules rl, Sink<RO> out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= np) return;
+  const SingPair sp = pairs[p];
+  const TriD A = tri[sp.t1];
+  const TriD B = tri[sp.t2];
+  const bool doC = wantC && sp.cls != 3;  // flat identical panels: C vanishes
+  SingGeom gm;
+  double MG[18], Mg[18];
+  sing_pair_moments(A, B, sp, kr, ki, doC, rl, lane, gm, MG, Mg);
+  sing_emit(MG, Mg, gm.Q1, gm.Q2, gm.ea, gm.eb, gm.ec, gm.ed, gm.D, sp, slot_edge, slot_sw, nslot, mikr, miki, c4r,
+            c4i, wantS, doC, lane, 32, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -2561,6 +2585,146 @@ int launch_rwg_free(const Space& s, int scat, double kr, double ki, int nreg, in
                                               ai, br, bi, st);
   return rwg_free_t<float, float2, float>(s, scat, kr, ki, nreg, (const float2*)x, (float2*)y, n, nrhs, ar, ai, br,
                                           bi, st);
+}
+
+// ---------------------------------------------------------------------------
+// The mixed discretisation (eq. mixed_discretisation): C between RWG written
+// on the barycentric refinement (RWG_b: the three RWG pieces of a primal
+// triangle restricted to each of its six children) and BC, float64. The
+// regular pairs tau1 < tau2 of the block's barycentric triangles are formed
+// once and give, by the symmetry of the bilinear form and of the tensor rule,
+// both orientations and both blocks: C(RWG_b, BC) and C(BC, RWG_b) = its
+// transpose there. The touching pairs take the float64 Sauter–Schwab rules in
+// their listed orders (vertex pairs, listed once, also in the swapped order),
+// each order contracted separately for the two blocks.
+// ---------------------------------------------------------------------------
+struct CrossSlots {
+  const int* redge;      // [ntri][3] RWG_b edges
+  const double* rsw;     // [ntri][3][4]
+  const int* bedge;      // [ntri][nslot] BC edges
+  const double* bsw;     // [ntri][nslot][4]
+  int nslot;
+};
+
+__device__ __forceinline__ void cross_add(const double* pc, const double* swa, const double* swb, int ea, int eb,
+                                          const Sink<double>& out) {
+  double Sr = 0, Si = 0, Cr = 0, Ci = 0;
+  const V3<double> wa = {swa[1], swa[2], swa[3]}, wb = {swb[1], swb[2], swb[3]};
+  entry_from_pc(pc, swa[0], wa, swb[0], wb, 0.0, 0.0, 0.0, 0.0, false, true, Sr, Si, Cr, Ci);
+  out.add(ea, eb, false, true, Sr, Si, Cr, Ci);
+}
+
+template <int NREG>
+__global__ void __launch_bounds__(256) cross_regular_kernel(const TriD* __restrict__ tri, CrossSlots cs, int64_t t0,
+                                                            int64_t ntr, double kr, double ki, Rules rl,
+                                                            Sink<double> rb, Sink<double> br) {
+  const int bi = blockIdx.y, bj = blockIdx.x;
+  if (bi > bj) return;
+  const int64_t i1 = (int64_t)bi * 16 + threadIdx.y;
+  const int64_t i2 = (int64_t)bj * 16 + threadIdx.x;
+  if (i1 >= ntr || i2 >= ntr || i1 >= i2) return;
+  const int64_t t1 = t0 + i1, t2 = t0 + i2;
+  const TriD A = tri[t1];
+  const TriD B = tri[t2];
+  if (touching(A, B)) return;
+  const V3<double> D = centroid_delta(A, B);
+  Mom<double> m;
+  pair_moments<double, NREG>(A, B, rl, D, kr, ki, true, m);
+  double pc[36];
+  pair_coeffs(m, D, pc);
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < cs.nslot; ++b) {
+      // RWG_b on t1 (test) with BC on t2 (trial), and BC on t1 with RWG_b on t2
+      const int r1 = cs.redge[3 * t1 + a], c2 = cs.bedge[(size_t)t2 * cs.nslot + b];
+      if (r1 >= 0 && c2 >= 0) {
+        double Sr = 0, Si = 0, Cr = 0, Ci = 0;
+        const double* swa = cs.rsw + (3 * t1 + a) * 4;
+        const double* swb = cs.bsw + ((size_t)t2 * cs.nslot + b) * 4;
+        entry_from_pc(pc, swa[0], V3<double>{swa[1], swa[2], swa[3]}, swb[0], V3<double>{swb[1], swb[2], swb[3]},
+                      0.0, 0.0, 0.0, 0.0, false, true, Sr, Si, Cr, Ci);
+        rb.add(r1, c2, false, true, Sr, Si, Cr, Ci);
+        br.add(c2, r1, false, true, Sr, Si, Cr, Ci);
+      }
+      const int c1 = cs.bedge[(size_t)t1 * cs.nslot + b], r2 = cs.redge[3 * t2 + a];
+      if (c1 >= 0 && r2 >= 0) {
+        double Sr = 0, Si = 0, Cr = 0, Ci = 0;
+        const double* swa = cs.bsw + ((size_t)t1 * cs.nslot + b) * 4;
+        const double* swb = cs.rsw + (3 * t2 + a) * 4;
+        entry_from_pc(pc, swa[0], V3<double>{swa[1], swa[2], swa[3]}, swb[0], V3<double>{swb[1], swb[2], swb[3]},
+                      0.0, 0.0, 0.0, 0.0, false, true, Sr, Si, Cr, Ci);
+        br.add(c1, r2, false, true, Sr, Si, Cr, Ci);
+        rb.add(r2, c1, false, true, Sr, Si, Cr, Ci);
+      }
+    }
+}
+
+__global__ void __launch_bounds__(128) cross_singular_kernel(const TriD* __restrict__ tri,
+                                                             const SingPair* __restrict__ pairs, int64_t np,
+                                                             CrossSlots cs, double kr, double ki, Rules rl,
+                                                             Sink<double> rb, Sink<double> br) {
+  const int lane = threadIdx.x & 31;
+  const int64_t p = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (p >= np) return;
+  const SingPair sp = pairs[p];
+  if (sp.cls == 3) return;  // flat identical panels: C vanishes
+  const TriD A = tri[sp.t1];
+  const TriD B = tri[sp.t2];
+  SingGeom gm;
+  double MG[18], Mg[18];
+  sing_pair_moments(A, B, sp, kr, ki, true, rl, lane, gm, MG, Mg);
+  double pc[36];
+  sing_pair_coeffs(MG, Mg, gm.Q1, gm.Q2, gm.ea, gm.eb, gm.ec, gm.ed, gm.D, pc);
+  const int ns = cs.nslot;
+  for (int q = lane; q < 3 * ns; q += 32) {
+    const int a = q / ns, b = q - a * ns;
+    // test RWG_b on t1, trial BC on t2 -> C(RWG_b, BC); test BC on t1, trial RWG_b on t2 -> C(BC, RWG_b)
+    const int r1 = cs.redge[3 * sp.t1 + a], c2 = cs.bedge[(size_t)sp.t2 * ns + b];
+    const int c1 = cs.bedge[(size_t)sp.t1 * ns + b], r2 = cs.redge[3 * sp.t2 + a];
+    const double* rs1 = cs.rsw + (3 * sp.t1 + a) * 4;
+    const double* bs2 = cs.bsw + ((size_t)sp.t2 * ns + b) * 4;
+    const double* bs1 = cs.bsw + ((size_t)sp.t1 * ns + b) * 4;
+    const double* rs2 = cs.rsw + (3 * sp.t2 + a) * 4;
+    if (r1 >= 0 && c2 >= 0) {
+      cross_add(pc, rs1, bs2, r1, c2, rb);
+      // a vertex pair's rule maps onto itself with the triangles swapped: the
+      // (t2, t1) order, BC on t2 tested against RWG_b on t1, is the same value
+      if (sp.cls == 1) cross_add(pc, rs1, bs2, c2, r1, br);
+    }
+    if (c1 >= 0 && r2 >= 0) {
+      cross_add(pc, bs1, rs2, c1, r2, br);
+      if (sp.cls == 1) cross_add(pc, bs1, rs2, r2, c1, rb);
+    }
+  }
+}
+
+int launch_cross_c(const Space& bc, const int* d_redge, const double* d_rsw, int scat, double kr, double ki, int nreg,
+                   int nsing, int64_t row_off, int64_t ld, double* Crb, double* Cbr, cudaStream_t st) {
+  int rc = set_quadrature_tables(nreg, nsing);
+  if (rc) return rc;
+  const int64_t t0 = scat < 0 ? 0 : bc.tri_off[scat];
+  const int64_t ntr = (scat < 0 ? bc.ntri : bc.tri_off[scat + 1]) - t0;
+  const int64_t nb = (ntr + 15) / 16;
+  if (nb > 65535) return fail(CAL_EINVAL, "too many triangles for the regular-pair grid (%lld)", (long long)ntr);
+  CrossSlots cs{d_redge, d_rsw, bc.d_slot_edge, bc.d_slot_swd, bc.nslot};
+  Sink<double> rb{nullptr, Crb, row_off, ld, nullptr, nullptr};
+  Sink<double> br{nullptr, Cbr, row_off, ld, nullptr, nullptr};
+  const int tok = prof_begin(st, "cross", 0.0);
+  auto kern = nreg == 6 ? cross_regular_kernel<6> : (nreg == 1 ? cross_regular_kernel<1> : cross_regular_kernel<0>);
+  if (ntr > 1) {
+    kern<<<dim3((unsigned)nb, (unsigned)nb), dim3(16, 16), 0, st>>>(bc.d_triD, cs, t0, ntr, kr, ki, g_rules, rb, br);
+    note_launch();
+  }
+  const int d0 = scat < 0 ? 0 : scat, d1 = scat < 0 ? (int)bc.sing.size() : scat + 1;
+  for (int d = d0; d < d1; ++d) {
+    const int64_t np = (int64_t)bc.sing[d].size();
+    if (np == 0) continue;
+    cross_singular_kernel<<<(unsigned)((np + 3) / 4), 128, 0, st>>>(bc.d_triD, bc.d_sing[d], np, cs, kr, ki, g_rules,
+                                                                    rb, br);
+    note_launch();
+  }
+  prof_end(st, tok);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
 }
 
 }  // namespace cal

@@ -278,6 +278,13 @@ int launch_singular(const AssembleArgs& a);
 int launch_rwg_free(const Space& s, int scat, double kr, double ki, int nreg, int precision, int vec_prec,
                     const void* x, void* y, int64_t n, int nrhs, double ar, double ai, double br, double bi,
                     cudaStream_t st);
+// C of the mixed discretisation in float64: Crb [rows][ld] = <C BC_j, RWG_i> with
+// RWG written on the barycentric refinement (d_redge [ntri][3], d_rsw
+// [ntri][3][4] on the BC space's triangles) and Cbr = <C RWG_j, BC_i>, dense,
+// block of scatterer scat (-1: union) at row/col offset row_off; zeroed by the
+// caller; nreg: 6, 1 or 0 (classes)
+int launch_cross_c(const Space& bc, const int* d_redge, const double* d_rsw, int scat, double kr, double ki, int nreg,
+                   int nsing, int64_t row_off, int64_t ld, double* Crb, double* Cbr, cudaStream_t st);
 int launch_gram(const Space& rwg, const Space& bc, const int64_t* rowptr, const int* col,
                 const int64_t* rowptrT, const int* colT, double* vals, double* valsT,
                 cudaStream_t stream);

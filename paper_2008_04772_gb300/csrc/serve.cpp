@@ -485,9 +485,9 @@ int cal_queue_submit(cal_queue* q, const cal_request* req, int64_t* ticket) {
   append_bytes(id, r->eps.data(), r->eps.size());
   append_bytes(id, r->mu.data(), r->mu.size());
   const cal_solve_opts& o = r->opts;
-  const int32_t ai[7] = {o.precond,     o.precision,   o.q_regular_A, o.q_singular_A,
-                         o.q_regular_P, o.q_singular_P, o.matrix_free};
-  append_bytes(id, ai, 7);
+  const int32_t ai[8] = {o.precond,     o.precision,   o.q_regular_A, o.q_singular_A,
+                         o.q_regular_P, o.q_singular_P, o.matrix_free, o.discretisation};
+  append_bytes(id, ai, 8);
   append_bytes(id, &o.near_cutoff_P, 1);
   append_bytes(id, &o.aca_nu_P, 1);
   const std::vector<double> area = scatterer_areas(r->verts, r->tris, r->domain, M);

@@ -1657,6 +1657,40 @@ int convert_vec(const void* a, int pa, void* b, int pb, int64_t n, double scale,
   return CAL_OK;
 }
 
+// y[i] += alpha sum_j X[i ld + j] x[j], i < rows, j < cols (float64, warp per row)
+__global__ void gemv_acc_kernel(const double2* __restrict__ X, int64_t ld, int64_t rows, int64_t cols,
+                                const double2* __restrict__ x, double2* __restrict__ y, double ar, double ai) {
+  const int lane = threadIdx.x & 31;
+  const int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (r >= rows) return;
+  const double2* Xr = X + r * ld;
+  double sr = 0, si = 0;
+  for (int64_t j = lane; j < cols; j += 32) {
+    const double2 m = Xr[j], v = x[j];
+    sr += m.x * v.x - m.y * v.y;
+    si += m.x * v.y + m.y * v.x;
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(0xffffffffu, sr, o);
+    si += __shfl_xor_sync(0xffffffffu, si, o);
+  }
+  if (lane == 0) {
+    y[r].x += ar * sr - ai * si;
+    y[r].y += ar * si + ai * sr;
+  }
+}
+
+int gemv_acc(const double2* X, int64_t ld, int64_t rows, int64_t cols, const double2* x, double2* y,
+             std::complex<double> alpha, cudaStream_t st) {
+  if (rows <= 0 || cols <= 0) return CAL_OK;
+  const int tok = prof_begin(st, "pair_gemv", (double)rows * cols * 16.0);
+  gemv_acc_kernel<<<blocks_for(rows * 32, 256), 256, 0, st>>>(X, ld, rows, cols, x, y, alpha.real(), alpha.imag());
+  prof_end(st, tok);
+  note_launch();
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
 int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nrhs, cudaStream_t st) {
   for (int64_t q = 0; q < nrhs; ++q) {
     note_launch();
@@ -1924,7 +1958,7 @@ int vec_gather(const double2* src, int64_t bsrc, double2* dst, int64_t n, int nr
 // mode 1: the L2 loads (int phi.(E x n), (k/mu) int phi.((d x p) e^{ik d.x} x n)) of the
 // projection of u^inc onto RWG, written as F.(n x phi)
 __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
-                           const double* __restrict__ slot_sw, int64_t nt, const double* inc,
+                           const double* __restrict__ slot_sw, int nslot, int64_t nt, const double* inc,
                            int nrhs, double k, double mu, Rules6 rl, int64_t ne,
                            double2* __restrict__ b, int mode) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1949,7 +1983,8 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
     for (int c = 0; c < 3; ++c) nrm[c] *= il;
   }
   const double sgn = mode == 0 ? -1.0 : 1.0;
-  double acc1[3][2] = {}, acc2[3][2] = {};
+  constexpr int MAXS = 16;  // slots per triangle (BC: the valence)
+  double acc1[MAXS][2] = {}, acc2[MAXS][2] = {};
   for (int u = 0; u < 6; ++u) {
     double xi[3];
     for (int c = 0; c < 3; ++c)
@@ -1959,8 +1994,8 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
     double s, co;
     sincos(k * ph, &s, &co);
     const double w = rl.w[u] * T.area;
-    for (int a = 0; a < 3; ++a) {
-      const double* sw = slot_sw + (3 * t + a) * 4;
+    for (int a = 0; a < nslot; ++a) {
+      const double* sw = slot_sw + ((size_t)t * nslot + a) * 4;
       double phi[3];
       for (int c = 0; c < 3; ++c) phi[c] = sw[0] * xi[c] + sw[1 + c];
       if (mode == 1) {  // n x phi
@@ -1976,8 +2011,9 @@ __global__ void rhs_kernel(const TriD* __restrict__ tri, const int* __restrict__
       acc2[a][1] += sgn * (k / mu) * w * s * e2;
     }
   }
-  for (int a = 0; a < 3; ++a) {
-    const int e = slot_edge[3 * t + a];
+  for (int a = 0; a < nslot; ++a) {
+    const int e = slot_edge[(size_t)t * nslot + a];
+    if (e < 0) continue;
     double2* bq = b + (size_t)q * 2 * ne;
     atomicAdd(&bq[e].x, acc1[a][0]);
     atomicAdd(&bq[e].y, acc1[a][1]);
@@ -1993,7 +2029,8 @@ int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double
   Rules6 rl = rules6();
   CAL_TRY_CUDA(cudaMemsetAsync(d_b, 0, (size_t)nrhs * 2 * rwg.nbasis * sizeof(double2), st));
   dim3 grid(blocks_for(rwg.ntri, 128), nrhs);
-  rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_inc, nrhs,
+  if (rwg.nslot > 16) return fail(CAL_EINVAL, "right-hand side: %d slots per triangle (at most 16)", rwg.nslot);
+  rhs_kernel<<<grid, 128, 0, st>>>(rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.nslot, rwg.ntri, d_inc, nrhs,
                                    k, mu, rl, rwg.nbasis, d_b, mode);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
@@ -2058,20 +2095,27 @@ struct FfPoint {
   AT j[12];  // J_a (re, im) per component, then J_b
 };
 
+// comps: bit 1 takes J_a from the first half of x, bit 2 J_b from the second
+// (the mixed discretisation expands the two traces in different spaces);
+// points of right-hand side q at pts + q * stride
 template <typename AT>
 __global__ void ff_points_kernel(const TriD* __restrict__ tri, const int* __restrict__ slot_edge,
-                                 const double* __restrict__ slot_sw, int64_t nt, const double2* __restrict__ x,
-                                 int64_t ne, double k, double mu, Rules6 rl, FfPoint<AT>* __restrict__ pts) {
+                                 const double* __restrict__ slot_sw, int nslot, int64_t nt,
+                                 const double2* __restrict__ x, int64_t ne, double k, double mu, Rules6 rl, int comps,
+                                 int64_t stride, FfPoint<AT>* __restrict__ pts) {
   const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int q = blockIdx.y;
   if (t >= nt) return;
   const TriD T = tri[t];
   const double2* xq = x + (size_t)q * 2 * ne;
-  double ca[3][2], cb[3][2];
-  for (int a = 0; a < 3; ++a) {
-    const int e = slot_edge[3 * t + a];
-    ca[a][0] = xq[e].x; ca[a][1] = xq[e].y;
-    cb[a][0] = xq[ne + e].x * (mu / k); cb[a][1] = xq[ne + e].y * (mu / k);
+  constexpr int MAXS = 16;
+  double ca[MAXS][2], cb[MAXS][2];
+  for (int a = 0; a < nslot; ++a) {
+    const int e = slot_edge[(size_t)t * nslot + a];
+    const bool ok = e >= 0;
+    ca[a][0] = ok && (comps & 1) ? xq[e].x : 0.0; ca[a][1] = ok && (comps & 1) ? xq[e].y : 0.0;
+    cb[a][0] = ok && (comps & 2) ? xq[ne + e].x * (mu / k) : 0.0;
+    cb[a][1] = ok && (comps & 2) ? xq[ne + e].y * (mu / k) : 0.0;
   }
   for (int u = 0; u < 6; ++u) {
     double xi[3];
@@ -2079,15 +2123,15 @@ __global__ void ff_points_kernel(const TriD* __restrict__ tri, const int* __rest
       xi[c] = rl.b[3 * u] * T.off[0][c] + rl.b[3 * u + 1] * T.off[1][c] + rl.b[3 * u + 2] * T.off[2][c];
     const double w = rl.w[u] * T.area;
     double J[12] = {};
-    for (int a = 0; a < 3; ++a) {
-      const double* sw = slot_sw + (3 * t + a) * 4;
+    for (int a = 0; a < nslot; ++a) {
+      const double* sw = slot_sw + ((size_t)t * nslot + a) * 4;
       for (int c = 0; c < 3; ++c) {
         const double phi = w * (sw[0] * xi[c] + sw[1 + c]);
         J[2 * c] += ca[a][0] * phi; J[2 * c + 1] += ca[a][1] * phi;
         J[6 + 2 * c] += cb[a][0] * phi; J[6 + 2 * c + 1] += cb[a][1] * phi;
       }
     }
-    FfPoint<AT>& o = pts[((size_t)q * nt + t) * 6 + u];
+    FfPoint<AT>& o = pts[(size_t)q * stride + t * 6 + u];
     for (int c = 0; c < 3; ++c) o.x[c] = (AT)(T.c[c] + xi[c]);
     for (int c = 0; c < 12; ++c) o.j[c] = (AT)J[c];
   }
@@ -2165,12 +2209,37 @@ static int farfield_t(const Space& rwg, const double2* d_x, int nrhs, const doub
   if (dalloc((void**)&pts, (size_t)nrhs * npts * sizeof(FfPoint<AT>), st) != cudaSuccess)
     return fail(CAL_ENOMEM, "far field: scratch allocation failed");
   ff_points_kernel<AT><<<dim3(blocks_for(rwg.ntri, 128), nrhs), 128, 0, st>>>(
-      rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.ntri, d_x, rwg.nbasis, k, mu, rl, pts);
+      rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.nslot, rwg.ntri, d_x, rwg.nbasis, k, mu, rl, 3, npts, pts);
   ff_sum_kernel<AT><<<dim3((unsigned)ndir, nrhs), 256, 0, st>>>(pts, npts, d_dirs, ndir, k, d_out);
   note_launch(2);
   dfree(pts, st);
   CAL_TRY_CUDA(cudaGetLastError());
   return CAL_OK;
+}
+
+// the mixed discretisation: u_1 in RWG (the primal space), u_2 in BC
+static int farfield_mixed_t(const Space& rwg, const Space& bc, const double2* d_x, int nrhs, const double* d_dirs,
+                            int64_t ndir, double k, double mu, double2* d_out, cudaStream_t st) {
+  if (bc.nslot > 16) return fail(CAL_EINVAL, "far field: %d slots per triangle (at most 16)", bc.nslot);
+  Rules6 rl = rules6();
+  const int64_t n1 = rwg.ntri * 6, npts = n1 + bc.ntri * 6;
+  FfPoint<double>* pts = nullptr;
+  if (dalloc((void**)&pts, (size_t)nrhs * npts * sizeof(FfPoint<double>), st) != cudaSuccess)
+    return fail(CAL_ENOMEM, "far field: scratch allocation failed");
+  ff_points_kernel<double><<<dim3(blocks_for(rwg.ntri, 128), nrhs), 128, 0, st>>>(
+      rwg.d_triD, rwg.d_slot_edge, rwg.d_slot_swd, rwg.nslot, rwg.ntri, d_x, rwg.nbasis, k, mu, rl, 1, npts, pts);
+  ff_points_kernel<double><<<dim3(blocks_for(bc.ntri, 128), nrhs), 128, 0, st>>>(
+      bc.d_triD, bc.d_slot_edge, bc.d_slot_swd, bc.nslot, bc.ntri, d_x, bc.nbasis, k, mu, rl, 2, npts, pts + n1);
+  ff_sum_kernel<double><<<dim3((unsigned)ndir, nrhs), 256, 0, st>>>(pts, npts, d_dirs, ndir, k, d_out);
+  note_launch(3);
+  dfree(pts, st);
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
+int launch_farfield_mixed(const Space& rwg, const Space& bc, const double2* d_x, int nrhs, const double* d_dirs,
+                          int64_t ndir, double k, double mu, double2* d_out, cudaStream_t st) {
+  return farfield_mixed_t(rwg, bc, d_x, nrhs, d_dirs, ndir, k, mu, d_out, st);
 }
 
 int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,

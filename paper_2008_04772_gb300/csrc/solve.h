@@ -133,6 +133,12 @@ int launch_rhs(const Space& rwg, const double* d_inc, int nrhs, double k, double
 int launch_rwg_mass(const Space& rwg, const int64_t* rowptr, const int* col, double* val, cudaStream_t st);
 int launch_farfield(const Space& rwg, const double2* d_x, int nrhs, const double* d_dirs, int64_t ndir,
                     double k, double mu, double2* d_out, int precision, cudaStream_t st);
+// the mixed discretisation's far field: u_1 in RWG, u_2 in BC (float64)
+int launch_farfield_mixed(const Space& rwg, const Space& bc, const double2* d_x, int nrhs, const double* d_dirs,
+                          int64_t ndir, double k, double mu, double2* d_out, cudaStream_t st);
+// y += alpha X x for a dense float64 block X [rows][ld] (rows x cols used)
+int gemv_acc(const double2* X, int64_t ld, int64_t rows, int64_t cols, const double2* x, double2* y,
+             std::complex<double> alpha, cudaStream_t st);
 
 // H-matrix form with ACA (hmat.cu, Section 3.3): out gets the CAL_HMAT form of the
 // dense square block (S and/or C) on the space's supports; leaves within chi
