@@ -45,7 +45,7 @@ METRIC = "PMCHWT solves/s (FP32 bulk, full Calderon D, 5120-triangle sphere, k=5
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the float32 BC-pair
 # kernel (exterior pass of the workload) from one ncu capture; None once the kernel
 # has changed since the counters were taken
-BC_TILE_TRAFFIC = 3.731466e9 + 4.173925e9
+BC_TILE_TRAFFIC = 3.768004e9 + 4.203311e9
 
 
 def _env_int(name, default):
@@ -898,7 +898,8 @@ def run_case(which: str) -> None:
       free  three FP32 GMRES iterations with the matrix-free PMCHWT operator;
       solve one complete solve of the bench workload (FP32 bulk, full D, tol 1e-5);
       multi one FP32 solve of 32 incident directions with the near-field reduced
-            preconditioner Di (chi = 2h).
+            preconditioner Di (chi = 2h);
+      near  one FP32 solve, then |E|^2 on a 64^2 grid of the plane z = 0 (composite level 2).
     """
     import torch
 
@@ -931,6 +932,11 @@ def run_case(which: str) -> None:
         d = meshgen.fibonacci_directions(32)
         cal.pmchwt_solve(ctx, mesh, k, eps, np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1),
                          opts=cal.solve_opts(precond="Di", near_cutoff_P=2.0, precision=cal.FP32, tol=1e-5, **Q))
+    elif which == "near":
+        sol = cal.pmchwt_solve(ctx, mesh, k, eps, inc, opts=cal.solve_opts(precond="D", precision=cal.FP32, **Q))
+        g = np.linspace(-2.0, 2.0, 64)
+        X, Y = np.meshgrid(g, g, indexing="ij")
+        sol.near_field(np.stack([X.ravel(), Y.ravel(), np.zeros(X.size)], 1), levels=2)
     elif which == "solve":
         sol = cal.pmchwt_solve(ctx, mesh, k, eps, inc,
                                opts=cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-5, **Q))
@@ -947,7 +953,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--case", default=None, choices=["bc", "gemv", "gemm", "free", "solve", "multi"],
+    ap.add_argument("--case", default=None, choices=["bc", "gemv", "gemm", "free", "solve", "multi", "near"],
                     help="run one profiling case and exit (no JSON line)")
     ap.add_argument("--cpu-sample", type=int, default=24, help="test triangles per space for the oracle sample")
     ap.add_argument("--oracle-sample", type=int, default=0, help=argparse.SUPPRESS)

@@ -171,9 +171,9 @@ int cal_op_export(const cal_op* op, int which, void* dst, int64_t* row_ptr, int6
    (cudaStream_t, NULL = the context stream). For a float32 dense operator and
    4 <= nrhs <= 128 vectors (even cols) the product runs on the tensor cores
    as a 3xTF32 GEMM (float32 accuracy: each 32-wide K tile's partial product is
-   summed in registers with round-to-nearest; the first such call keeps the TF32 part
-   and the float32 remainder of the operator with it, twice its size);
-   otherwise one GEMV/SpMV per vector. */
+   summed in registers with round-to-nearest; the operator is read once, as
+   float32, and split into its TF32 parts in shared memory, so no copy of it is
+   kept); otherwise one GEMV/SpMV per vector. */
 int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs, void* stream);
 
 /* The paper has no counterpart to this entry point: it serves callers that

@@ -316,24 +316,6 @@ int assemble_singular_block(Ctx& ctx, double kr, double ki, const Space& sp, int
   return CAL_OK;
 }
 
-// TF32 part and float32 remainder of a dense float32 operator, made once and
-// kept with it: the split-operand tensor-core product reads them by TMA
-int ensure_split(Op& op, cudaStream_t st) {
-  if (op.format != CAL_DENSE || op.precision != CAL_FP32) return CAL_OK;
-  const int64_t n = op.rows * op.cols * 2;  // floats
-  if (op.d_S && !op.d_Sh) {
-    CAL_TRY_CUDA(dalloc((void**)&op.d_Sh, n * sizeof(float), st));
-    CAL_TRY_CUDA(dalloc((void**)&op.d_Sl, n * sizeof(float), st));
-    if (int rc = split_tf32((const float*)op.d_S, op.d_Sh, op.d_Sl, n, st)) return rc;
-  }
-  if (op.d_C && !op.d_Ch) {
-    CAL_TRY_CUDA(dalloc((void**)&op.d_Ch, n * sizeof(float), st));
-    CAL_TRY_CUDA(dalloc((void**)&op.d_Cl, n * sizeof(float), st));
-    if (int rc = split_tf32((const float*)op.d_C, op.d_Ch, op.d_Cl, n, st)) return rc;
-  }
-  return CAL_OK;
-}
-
 std::complex<double> interior_k(double k_e, std::complex<double> eps, std::complex<double> mu) {
   std::complex<double> km = k_e * std::sqrt(eps * mu);
   if (km.imag() < 0) km = -km;
@@ -533,8 +515,6 @@ struct Pmchwt {
     b.precision = op.precision;
     b.rowptr = op.format == CAL_CSR ? op.d_rowptr : nullptr;
     b.col = op.format == CAL_CSR ? op.d_col : nullptr;
-    if (withS) { b.Sh = op.d_Sh; b.Sl = op.d_Sl; }
-    if (withC) { b.Ch = op.d_Ch; b.Cl = op.d_Cl; }
     if (op.hmat) {
       b.hmat = op.hmat;
       b.hmask = (withS ? 1 : 0) | (withC ? 2 : 0);
@@ -597,13 +577,6 @@ struct Pmchwt {
     if (o.precision == CAL_FP32 && nb >= 4 && gemm_tc_supported(2, nb)) {
       NB = ((4 * nb + 15) / 16) * 16;
       int64_t maxrows = A_ext->rows;
-      // split copies of the dense float32 blocks for the tensor-core product
-      int rc;
-      for (Op* op : {A_ext.get()})
-        if ((rc = ensure_split(*op, st))) return rc;
-      for (auto* v : {&A_int, &P_ext, &P_int})
-        for (auto& op : *v)
-          if (op && (rc = ensure_split(*op, st))) return rc;
       CAL_TRY_CUDA(dalloc((void**)&d_Bt, (size_t)NB * 2 * maxrows * sizeof(float), st));
       CAL_TRY_CUDA(dalloc((void**)&d_Bh, (size_t)NB * 2 * maxrows * sizeof(float), st));
       CAL_TRY_CUDA(dalloc((void**)&d_Bl, (size_t)NB * 2 * maxrows * sizeof(float), st));
@@ -635,20 +608,19 @@ struct Pmchwt {
       const float2* X = (const float2*)x;
       if ((rc = embed_rhs<float2>(X, nrhs, N, b.col_off, b.cols, d_Bt, NB, st))) return rc;
       const int64_t K = 2 * b.cols;
-      const bool split = NB <= 128 && (!b.S || b.Sh) && (!b.C || b.Ch);
-      if (split && (rc = split_tf32(d_Bt, d_Bh, d_Bl, (int64_t)NB * K, st))) return rc;
+      // the vectors are split into TF32 parts once per product; the operator is
+      // read as float32 and split in the kernel
+      if ((rc = split_tf32(d_Bt, d_Bh, d_Bl, (int64_t)NB * K, st))) return rc;
       const float* ZS = nullptr;
       const float* ZC = nullptr;
       if (b.S) {
-        rc = split ? gemm_tf32x3_split(b.Sh, b.Sl, b.rows, K, d_Bh, d_Bl, NB, d_ZS, d_gemm_err, ctx->n_sm, st)
-                   : gemm_tf32x3((const float*)b.S, b.rows, K, d_Bt, NB, d_ZS, d_gemm_err, ctx->n_sm, st);
-        if (rc) return rc;
+        if ((rc = gemm_tf32x3_bsplit((const float*)b.S, b.rows, K, d_Bh, d_Bl, NB, d_ZS, d_gemm_err, ctx->n_sm, st)))
+          return rc;
         ZS = d_ZS;
       }
       if (b.C) {
-        rc = split ? gemm_tf32x3_split(b.Ch, b.Cl, b.rows, K, d_Bh, d_Bl, NB, d_ZC, d_gemm_err, ctx->n_sm, st)
-                   : gemm_tf32x3((const float*)b.C, b.rows, K, d_Bt, NB, d_ZC, d_gemm_err, ctx->n_sm, st);
-        if (rc) return rc;
+        if ((rc = gemm_tf32x3_bsplit((const float*)b.C, b.rows, K, d_Bh, d_Bl, NB, d_ZC, d_gemm_err, ctx->n_sm, st)))
+          return rc;
         ZC = d_ZC;
       }
       return combine_rhs<float2>(ZS, ZC, b.rows, NB, nrhs, N, b.row_off, (float2*)y, al.real(), al.imag(),
@@ -1097,14 +1069,6 @@ struct cal_problem {
     int64_t b = 3 * (int64_t)P.nb * n2 * 16;
     if (P.d_Bt) {
       b += 3 * (int64_t)P.NB * 2 * P.A_ext->rows * 4 + 2 * (int64_t)P.A_ext->rows * P.NB * 4;
-      // split copies of the dense float32 blocks (twice their size)
-      auto add = [&](const Op* op) {
-        if (op && op->d_Sh) b += 2 * op->nnz * 8;
-        if (op && op->d_Ch) b += 2 * op->nnz * 8;
-      };
-      add(P.A_ext.get());
-      for (auto* v : {&P.A_int, &P.P_ext, &P.P_int})
-        for (auto& op : *v) add(op.get());
     }
     const int64_t csz = P.o.precision == CAL_FP64 ? 16 : 8, rsz = csz / 2;
     if (P.o.precond != CAL_PRECOND_NONE) b += 2 * (P.gnnz * rsz + 10 * (int64_t)P.nb * P.N * csz);
@@ -1215,7 +1179,6 @@ int cal_assemble(cal_ctx* ctx, int op_mask, double k_re, double k_im, cal_space*
   op->d_S = op->d_C = nullptr;
   op->d_rowptr = nullptr;
   op->d_col = nullptr;
-  op->d_Sh = op->d_Sl = op->d_Ch = op->d_Cl = nullptr;
   op->hmat = nullptr;
   *out = o;
   return CAL_OK;
@@ -1299,13 +1262,7 @@ int cal_matvec(const cal_op* op, int which, const void* x, void* y, int64_t nrhs
   // several vectors on a float32 dense operator: the tensor-core 3xTF32 product
   if (o.precision == CAL_FP32 && o.format == CAL_DENSE && nrhs >= 4 && (nrhs + 1) / 2 * 4 <= 256 && o.cols % 2 == 0)
   {
-    // the split copies are made once and kept with the operator
-    Op& mo = const_cast<Op&>(o);
-    if (int rc = ensure_split(mo, st)) return rc;
-    const float* Xh = which == CAL_OP_S ? mo.d_Sh : mo.d_Ch;
-    const float* Xl = which == CAL_OP_S ? mo.d_Sl : mo.d_Cl;
-    return multi_matvec_tc((const float2*)X, o.rows, o.cols, (const float2*)x, (float2*)y, (int)nrhs, o.ctx->n_sm, st,
-                           Xh, Xl);
+    return multi_matvec_tc((const float2*)X, o.rows, o.cols, (const float2*)x, (float2*)y, (int)nrhs, o.ctx->n_sm, st);
   }
   return single_apply(o, X, x, y, nrhs, st);
 }

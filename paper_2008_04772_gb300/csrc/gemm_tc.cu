@@ -114,7 +114,7 @@ __device__ __forceinline__ float tf32_round(float x) {
   return __uint_as_float(r);
 }
 
-// Roles (192 threads): warps 0-3 own TMEM lanes 32w..32w+31 (one output row per
+// Roles (256 threads): warps 0-3 own TMEM lanes 32w..32w+31 (one output row per
 // thread) and keep the running float32 sums of their row in registers; warp 4
 // lane 0 issues the TMA loads of a ring of stages; warp 5 lane 0 issues the MMAs.
 //
@@ -128,20 +128,23 @@ __device__ __forceinline__ float tf32_round(float x) {
 // other accumulators of a ring of up to four. The chain in TMEM is thus 12 MMAs
 // long whatever K is.
 //
-// PRESPLIT: A = Ah + Al and B = Bh + Bl are split beforehand and the producer
-// loads all four tiles. Otherwise the producer loads the float32 A and B tiles
-// into the "h" slots and the row warps round them to TF32 in place and write
-// the low parts beside them before the MMA warp may use the stage.
-constexpr int STAGES = 3;
+// A is loaded as float32 into the "h" slot of a stage, and two more warps
+// (6, 7) round it to TF32 in place and write the low parts beside it before
+// the MMA warp may use the stage, so the operator crosses HBM once, as
+// float32, and needs no split copy. MODE 0: B is loaded and split the same
+// way. MODE 1: B = Bh + Bl is split beforehand (the vectors are small and
+// reused by every row block) and the producer loads both parts.
+constexpr int MAX_STAGES = 3;  // stages of the ring (a deeper ring measured no faster)
 constexpr int ROW_THREADS = 128;
-constexpr int THREADS = ROW_THREADS + 64;
+constexpr int SPLIT_THREADS = 64;  // two warps: eight in all, two per SM sub-partition (register file)
+constexpr int GEMM_THREADS = ROW_THREADS + 64 + SPLIT_THREADS;
 constexpr int MAX_BN = 128;   // columns per CTA: 128 float32 sums per row thread
 constexpr int MAX_ACC = 4;
 
 struct __align__(8) Bars {
-  uint64_t full[STAGES];    // TMA bytes of the stage landed
-  uint64_t ready[STAGES];   // in-kernel split of the stage done (row warps)
-  uint64_t empty[STAGES];   // MMAs reading the stage completed
+  uint64_t full[MAX_STAGES];    // TMA bytes of the stage landed
+  uint64_t ready[MAX_STAGES];   // in-kernel split of the stage done (split warps)
+  uint64_t empty[MAX_STAGES];   // MMAs reading the stage completed
   uint64_t accf[MAX_ACC];   // accumulator holds a finished K tile
   uint64_t acce[MAX_ACC];   // accumulator read out by the four row warps
   uint32_t tmem_base;
@@ -156,16 +159,16 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __device__ __forceinline__ bool failed(Bars* b) { return *(volatile uint32_t*)&b->fail != 0; }
 
-template <bool PRESPLIT>
-__global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
-    const __grid_constant__ CUtensorMap mapAh, const __grid_constant__ CUtensorMap mapAl,
-    const __grid_constant__ CUtensorMap mapBh, const __grid_constant__ CUtensorMap mapBl, float* __restrict__ Z,
-    int64_t M, int NB, int BN, int64_t K, int ktiles_per_cta, int* err) {
+template <int MODE>
+__global__ void __launch_bounds__(GEMM_THREADS, 1) gemm_tf32x3_kernel(
+    const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapBh,
+    const __grid_constant__ CUtensorMap mapBl, float* __restrict__ Z,
+    int64_t M, int NB, int BN, int64_t K, int ktiles_per_cta, int stages, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int a_bytes = BM * BK * 4, b_bytes = BN * BK * 4;
   const int stage_bytes = 2 * (a_bytes + b_bytes);
-  Bars* bars = reinterpret_cast<Bars*>(base + STAGES * stage_bytes);
+  Bars* bars = reinterpret_cast<Bars*>(base + stages * stage_bytes);
   auto Ah = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes); };
   auto Al = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + a_bytes); };
   auto Bh = [&](int s) { return reinterpret_cast<float*>(base + s * stage_bytes + 2 * a_bytes); };
@@ -185,9 +188,9 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
   const int tmem_cols = acc_cols * nacc;
 
   if (tid == 0) {
-    for (int s = 0; s < STAGES; ++s) {
+    for (int s = 0; s < stages; ++s) {
       mbar_init(&bars->full[s], 1);
-      mbar_init(&bars->ready[s], ROW_THREADS);
+      mbar_init(&bars->ready[s], SPLIT_THREADS);
       mbar_init(&bars->empty[s], 1);
     }
     for (int a = 0; a < MAX_ACC; ++a) {
@@ -217,22 +220,19 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
   if (warp == 4) {
     if (lane == 0) {
       // producer: stage s is free again once the MMAs of the tile that last used it completed
-      const unsigned tx = (unsigned)((PRESPLIT ? 2 : 1) * (a_bytes + b_bytes));
+      const unsigned tx = (unsigned)(a_bytes + (MODE == 0 ? 1 : 2) * b_bytes);
       for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt % STAGES;
-        if (kt >= STAGES && !mbar_wait(&bars->empty[s], ((kt / STAGES) - 1) & 1)) {
+        const int s = kt % stages;
+        if (kt >= stages && !mbar_wait(&bars->empty[s], ((kt / stages) - 1) & 1)) {
           atomicOr(&bars->fail, 1u);
           break;
         }
         if (failed(bars)) break;
         const int x = (int)((kt0 + kt) * BK);
         mbar_expect_tx(&bars->full[s], tx);
-        tma_load_2d(Ah(s), &mapAh, &bars->full[s], x, (int)row0);
+        tma_load_2d(Ah(s), &mapA, &bars->full[s], x, (int)row0);
         tma_load_2d(Bh(s), &mapBh, &bars->full[s], x, col0);
-        if (PRESPLIT) {
-          tma_load_2d(Al(s), &mapAl, &bars->full[s], x, (int)row0);
-          tma_load_2d(Bl(s), &mapBl, &bars->full[s], x, col0);
-        }
+        if (MODE == 1) tma_load_2d(Bl(s), &mapBl, &bars->full[s], x, col0);
         *(volatile int32_t*)&bars->issued = kt + 1;
       }
     }
@@ -240,9 +240,8 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
     if (lane == 0) {
       const uint32_t idesc = instr_desc(BN);
       for (int kt = 0; kt < nk; ++kt) {
-        const int s = kt % STAGES, a = kt % nacc, use = kt / nacc;
-        uint64_t* in_bar = PRESPLIT ? &bars->full[s] : &bars->ready[s];
-        if (!mbar_wait(in_bar, (kt / STAGES) & 1) || (use >= 1 && !mbar_wait(&bars->acce[a], (use - 1) & 1))) {
+        const int s = kt % stages, a = kt % nacc, use = kt / nacc;
+        if (!mbar_wait(&bars->ready[s], (kt / stages) & 1) || (use >= 1 && !mbar_wait(&bars->acce[a], (use - 1) & 1))) {
           atomicOr(&bars->fail, 1u);
           break;
         }
@@ -262,9 +261,42 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
         *(volatile int32_t*)&bars->committed = kt + 1;
       }
     }
+  } else if (warp >= 6) {
+    // split warps: round the stage's float32 tiles to TF32 in place (the low
+    // parts beside them), vector by vector
+    const int st_id = tid - (ROW_THREADS + 64);
+    for (int kt = 0; kt < nk; ++kt) {
+      const int s = kt % stages;
+      if (!mbar_wait(&bars->full[s], (kt / stages) & 1) || failed(bars)) {
+        atomicOr(&bars->fail, 1u);
+        break;
+      }
+      float4* ah = reinterpret_cast<float4*>(Ah(s));
+      float4* al = reinterpret_cast<float4*>(Al(s));
+#pragma unroll 4
+      for (int i = st_id; i < BM * BK / 4; i += SPLIT_THREADS) {
+        const float4 x = ah[i];
+        const float4 h = {tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w)};
+        ah[i] = h;
+        al[i] = {x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w};
+      }
+      if (MODE == 0) {
+        float4* bh = reinterpret_cast<float4*>(Bh(s));
+        float4* bl = reinterpret_cast<float4*>(Bl(s));
+        for (int i = st_id; i < BN * BK / 4; i += SPLIT_THREADS) {
+          const float4 x = bh[i];
+          const float4 h = {tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w)};
+          bh[i] = h;
+          bl[i] = {x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w};
+        }
+      }
+      // the generic-proxy writes must be visible to the tensor core's reads
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      mbar_arrive(&bars->ready[s]);
+    }
   } else {
-    // row warps: split the stage (in-kernel variant), then read out the
-    // accumulator of the previous tile and add it to the register sums
+    // row warps: read out the accumulator of each tile and add it to the
+    // register sums
     auto drain = [&](int kt) -> bool {
       const int a = kt % nacc;
       // warp-uniform outcome: tcgen05.ld below is a warp-collective instruction
@@ -295,27 +327,6 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
     };
     bool ok = true;
     for (int kt = 0; kt < nk && ok; ++kt) {
-      if (!PRESPLIT) {
-        const int s = kt % STAGES;
-        if (!__all_sync(0xffffffffu, mbar_wait(&bars->full[s], (kt / STAGES) & 1))) { ok = false; break; }
-        float* ah = Ah(s);
-        float* bh = Bh(s);
-        float* al = Al(s);
-        float* bl = Bl(s);
-        for (int i = tid; i < BM * BK; i += ROW_THREADS) {
-          const float x = ah[i], h = tf32_round(x);
-          ah[i] = h;
-          al[i] = x - h;
-        }
-        for (int i = tid; i < BN * BK; i += ROW_THREADS) {
-          const float x = bh[i], h = tf32_round(x);
-          bh[i] = h;
-          bl[i] = x - h;
-        }
-        // the generic-proxy writes must be visible to the tensor core's reads
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&bars->ready[s]);
-      }
       if (kt >= 1 && !drain(kt - 1)) ok = false;
       if (__any_sync(0xffffffffu, failed(bars))) ok = false;
     }
@@ -339,10 +350,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tf32x3_kernel(
     // the loads that were issued, and the last committed MMA group (its commit
     // covers every earlier MMA of this thread)
     const int issued = bars->issued;
-    for (int kt = (issued > STAGES ? issued - STAGES : 0); kt < issued; ++kt)
-      mbar_wait(&bars->full[kt % STAGES], (kt / STAGES) & 1);
+    for (int kt = (issued > stages ? issued - stages : 0); kt < issued; ++kt)
+      mbar_wait(&bars->full[kt % stages], (kt / stages) & 1);
     const int committed = bars->committed;
-    if (committed > 0) mbar_wait(&bars->empty[(committed - 1) % STAGES], ((committed - 1) / STAGES) & 1);
+    if (committed > 0) mbar_wait(&bars->empty[(committed - 1) % stages], ((committed - 1) / stages) & 1);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
@@ -472,16 +483,17 @@ GemmPlan plan_gemm(int64_t M, int64_t K, int NB, int n_sm) {
   return p;
 }
 
-template <bool PRESPLIT>
-int launch_gemm(const CUtensorMap& mAh, const CUtensorMap& mAl, const CUtensorMap& mBh, const CUtensorMap& mBl,
-                const GemmPlan& p, int64_t M, int64_t K, int NB, float* Z, int* d_err, cudaStream_t st) {
-  const int smem = STAGES * 2 * (BM * BK * 4 + p.BN * BK * 4) + (int)sizeof(Bars) + 1024;
-  if (smem > 227 * 1024) return fail(CAL_EINVAL, "gemm: %d columns do not fit the pipeline", p.BN);
-  if (int rc = ensure_dyn_smem((const void*)gemm_tf32x3_kernel<PRESPLIT>, smem)) return rc;
+template <int MODE>
+int launch_gemm(const CUtensorMap& mA, const CUtensorMap& mBh, const CUtensorMap& mBl, const GemmPlan& p, int64_t M, int64_t K, int NB, float* Z, int* d_err, cudaStream_t st) {
+  const int stage_bytes = 2 * (BM * BK * 4 + p.BN * BK * 4);
+  const int stages = std::min(MAX_STAGES, (227 * 1024 - (int)sizeof(Bars) - 1024) / stage_bytes);
+  if (stages < 2) return fail(CAL_EINVAL, "gemm: %d columns do not fit the pipeline", p.BN);
+  const int smem = stages * stage_bytes + (int)sizeof(Bars) + 1024;
+  if (int rc = ensure_dyn_smem((const void*)gemm_tf32x3_kernel<MODE>, smem)) return rc;
   CAL_TRY_CUDA(cudaMemsetAsync(Z, 0, (size_t)M * NB * sizeof(float), st));
   const int tok = prof_begin(st, "gemm_tc", 2.0 * 3.0 * (double)M * K * NB);
-  gemm_tf32x3_kernel<PRESPLIT><<<dim3((unsigned)p.mt, (unsigned)p.split, (unsigned)p.nz), THREADS, smem, st>>>(
-      mAh, mAl, mBh, mBl, Z, M, NB, p.BN, K, p.per, d_err);
+  gemm_tf32x3_kernel<MODE><<<dim3((unsigned)p.mt, (unsigned)p.split, (unsigned)p.nz), GEMM_THREADS, smem, st>>>(
+      mA, mBh, mBl, Z, M, NB, p.BN, K, p.per, stages, d_err);
   prof_end(st, tok);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
@@ -506,7 +518,7 @@ int gemm_tf32x3(const float* A, int64_t M, int64_t K, const float* Bt, int NB, f
   CUtensorMap mA, mB;
   int rc;
   if ((rc = make_map(&mA, A, K, M, BM)) || (rc = make_map(&mB, Bt, K, NB, p.BN))) return rc;
-  return launch_gemm<false>(mA, mA, mB, mB, p, M, K, NB, Z, d_err, st);
+  return launch_gemm<0>(mA, mB, mB, p, M, K, NB, Z, d_err, st);
 }
 
 int split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st) {
@@ -517,20 +529,20 @@ int split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st)
   return CAL_OK;
 }
 
-// Z[M][NB] = (Ah + Al)[M][K] (Bh + Bl)[NB][K]^T (Z is zeroed here), 3xTF32
-int gemm_tf32x3_split(const float* Ah, const float* Al, int64_t M, int64_t K, const float* Bh, const float* Bl, int NB,
-                      float* Z, int* d_err, int n_sm, cudaStream_t st) {
+// Z[M][NB] = A[M][K] (Bh + Bl)[NB][K]^T (Z is zeroed here), 3xTF32 with A split
+// in the kernel and B split beforehand: A crosses HBM once, as float32
+int gemm_tf32x3_bsplit(const float* A, int64_t M, int64_t K, const float* Bh, const float* Bl, int NB, float* Z,
+                       int* d_err, int n_sm, cudaStream_t st) {
   if (NB < 16 || NB > 256 || NB % 16) return fail(CAL_EINVAL, "gemm: NB must be a multiple of 16 in [16, 256]");
-  for (const float* p : {Ah, Al, Bh, Bl})
+  for (const float* p : {A, Bh, Bl})
     if ((uintptr_t)p % 16) return fail(CAL_EINVAL, "gemm: operands not 16-byte aligned");
   if ((K * 4) % 16) return fail(CAL_EINVAL, "gemm: rows not 16-byte aligned");
   const GemmPlan p = plan_gemm(M, K, NB, n_sm);
-  CUtensorMap mAh, mAl, mBh, mBl;
+  CUtensorMap mA, mBh, mBl;
   int rc;
-  if ((rc = make_map(&mAh, Ah, K, M, BM)) || (rc = make_map(&mAl, Al, K, M, BM)) ||
-      (rc = make_map(&mBh, Bh, K, NB, p.BN)) || (rc = make_map(&mBl, Bl, K, NB, p.BN)))
+  if ((rc = make_map(&mA, A, K, M, BM)) || (rc = make_map(&mBh, Bh, K, NB, p.BN)) || (rc = make_map(&mBl, Bl, K, NB, p.BN)))
     return rc;
-  return launch_gemm<true>(mAh, mAl, mBh, mBl, p, M, K, NB, Z, d_err, st);
+  return launch_gemm<1>(mA, mBh, mBl, p, M, K, NB, Z, d_err, st);
 }
 
 template <typename VT>
@@ -563,7 +575,7 @@ __global__ void unembed_kernel(const float* __restrict__ Z, int64_t rows, int NB
 // Y[nrhs][rows] = X^T applied: plain complex product of a float32 dense operator
 // with nrhs vectors x [nrhs][cols] through the tensor-core path
 int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2* x, float2* y, int nrhs, int n_sm,
-                    cudaStream_t st, const float* Xh, const float* Xl) {
+                    cudaStream_t st) {
   const int npair = (nrhs + 1) / 2;  // the embedding works on (x1, x2) column pairs
   const int NB = ((4 * npair + 15) / 16) * 16;
   if (NB > 256 || cols % 2) return fail(CAL_EINVAL, "multi-vector product: unsupported size");
@@ -582,17 +594,16 @@ int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2*
     xin = xp;
   }
   int rc = embed_rhs<float2>(xin, npair, cols, 0, cols, Bt, NB, st);
-  float* Bs = nullptr;  // split operand: [2][NB][2 cols]
-  const bool split = Xh && Xl && NB <= 128;
-  if (!rc && split) {
+  float* Bs = nullptr;  // the vectors' TF32 parts: [2][NB][2 cols]
+  if (!rc) {
     if (cudaMallocAsync((void**)&Bs, (size_t)2 * NB * 2 * cols * sizeof(float), st) != cudaSuccess)
-      rc = fail(CAL_ENOMEM, "multi-vector product: cannot allocate the split operand");
+      rc = fail(CAL_ENOMEM, "multi-vector product: cannot allocate the split vectors");
     else
       rc = split_tf32(Bt, Bs, Bs + (size_t)NB * 2 * cols, (int64_t)NB * 2 * cols, st);
   }
   if (!rc)
-    rc = split ? gemm_tf32x3_split(Xh, Xl, rows, 2 * cols, Bs, Bs + (size_t)NB * 2 * cols, NB, Z, err, n_sm, st)
-               : gemm_tf32x3(reinterpret_cast<const float*>(Xop), rows, 2 * cols, Bt, NB, Z, err, n_sm, st);
+    rc = gemm_tf32x3_bsplit(reinterpret_cast<const float*>(Xop), rows, 2 * cols, Bs, Bs + (size_t)NB * 2 * cols, NB,
+                            Z, err, n_sm, st);
   if (!rc) {
     unembed_kernel<<<dim3((unsigned)((rows + 255) / 256), nrhs), 256, 0, st>>>(Z, rows, NB, nrhs, y);
     note_launch();

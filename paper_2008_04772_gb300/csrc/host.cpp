@@ -836,7 +836,6 @@ Op::~Op() {
   delete hmat;
   dfree(d_S, nullptr);
   dfree(d_C, nullptr);
-  for (void* p : {(void*)d_Sh, (void*)d_Sl, (void*)d_Ch, (void*)d_Cl}) dfree(p, nullptr);
   dfree(d_rowptr, nullptr);
   dfree(d_col, nullptr);
 }

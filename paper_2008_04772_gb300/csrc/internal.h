@@ -213,12 +213,6 @@ struct Op {
   int64_t row_offset = 0;
   void* d_S = nullptr;           // dense [rows][cols] or CSR values
   void* d_C = nullptr;
-  // float32 dense only, made on first use by the tensor-core product: the
-  // TF32 part and the float32 remainder of S and C (x = hi + lo exactly)
-  float* d_Sh = nullptr;
-  float* d_Sl = nullptr;
-  float* d_Ch = nullptr;
-  float* d_Cl = nullptr;
   int64_t* d_rowptr = nullptr;   // CSR
   int* d_col = nullptr;
   std::vector<int64_t> h_rowptr; // CSR pattern on the host

@@ -26,10 +26,6 @@ struct BlockRef {
   const int* col = nullptr;
   // combined block (float32 dense, one vector): y1 += C x1 + S x2, y2 += C x2 + S2 x1
   const void* S2 = nullptr;
-  const float* Sh = nullptr;  // split copies for the tensor-core product (float32 dense)
-  const float* Sl = nullptr;
-  const float* Ch = nullptr;
-  const float* Cl = nullptr;
   const HMat* hmat = nullptr;  // CAL_HMAT block: S and C in H-matrix form
   int hmask = 0;               // with hmat: bit 1 apply S, bit 2 apply C
 };
@@ -111,12 +107,12 @@ int vec_gather(const double2* src, int64_t bsrc, double2* dst, int64_t n, int nr
 // A10 (gemm_tc.cu): tensor-core 3xTF32 product and the right-hand-side embedding
 bool gemm_tc_supported(int64_t cols, int nrhs);
 int multi_matvec_tc(const float2* Xop, int64_t rows, int64_t cols, const float2* x, float2* y, int nrhs, int n_sm,
-                    cudaStream_t st, const float* Xh = nullptr, const float* Xl = nullptr);
+                    cudaStream_t st);
 int split_tf32(const float* x, float* hi, float* lo, int64_t n, cudaStream_t st);
-int gemm_tf32x3_split(const float* Ah, const float* Al, int64_t M, int64_t K, const float* Bh, const float* Bl, int NB,
-                      float* Z, int* d_err, int n_sm, cudaStream_t st);
 int gemm_tf32x3(const float* A, int64_t M, int64_t K, const float* Bt, int NB, float* Z, int* d_err,
                 int n_sm, cudaStream_t st);
+int gemm_tf32x3_bsplit(const float* A, int64_t M, int64_t K, const float* Bh, const float* Bl, int NB, float* Z,
+                       int* d_err, int n_sm, cudaStream_t st);
 template <typename VT>
 int embed_rhs(const VT* X, int nrhs, int64_t n_total, int64_t col_off, int64_t ncols, float* Bt, int NB,
               cudaStream_t st);
