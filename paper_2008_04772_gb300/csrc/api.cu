@@ -58,6 +58,112 @@ std::vector<int> cell_list(const Space& s, int scat) {
   return out;
 }
 
+// Bounding ball of a dual cell for the class rules (Section 3.3): C the mean of
+// its triangle centroids, rho the largest distance of one of them from C, dm
+// the longest edge of its triangles.
+struct CellBall {
+  double c[3] = {0, 0, 0}, rho = 0, dm = 0;
+};
+
+std::vector<CellBall> cell_balls(const Space& sp, const std::vector<int>& cells, int nv) {
+  std::vector<CellBall> B(nv);
+  for (int v : cells) {
+    CellBall& b = B[v];
+    const int t0 = sp.cell_tri_ptr[v], t1 = sp.cell_tri_ptr[v + 1];
+    for (int q = t0; q < t1; ++q)
+      for (int c = 0; c < 3; ++c) b.c[c] += sp.triD[sp.cell_tri[q]].c[c] / (t1 - t0);
+    for (int q = t0; q < t1; ++q) {
+      const TriD& t = sp.triD[sp.cell_tri[q]];
+      double d2 = 0;
+      for (int c = 0; c < 3; ++c) d2 += (t.c[c] - b.c[c]) * (t.c[c] - b.c[c]);
+      b.rho = std::max(b.rho, std::sqrt(d2));
+      b.dm = std::max(b.dm, t.diam);
+    }
+  }
+  return B;
+}
+
+// Every triangle pair of cells v and w takes the far rule: the pair's centroid
+// distance is at least |C_v - C_w| - rho_v - rho_w, and the far class asks for
+// more than 4 max(d1, d2). The relative margin 1e-4 covers the float32
+// rounding of the kernels' own per-pair test, so a pair in such a cell pair is
+// classed far there too and its arithmetic is the same either way.
+constexpr double FAR_MARGIN = 1.0 + 1e-4;
+double far_reach(const CellBall& b) { return b.rho + 4.0 * FAR_MARGIN * b.dm; }
+bool cells_far(const CellBall& a, const CellBall& b) {
+  double d2 = 0;
+  for (int c = 0; c < 3; ++c) d2 += (a.c[c] - b.c[c]) * (a.c[c] - b.c[c]);
+  return std::sqrt(d2) - a.rho - b.rho > 4.0 * FAR_MARGIN * std::max(a.dm, b.dm);
+}
+
+// cells in Morton order of their centres: the cells of one edge's two ends come
+// close together in the unit order, so the rows of the output they accumulate
+// into stay in L2 while they are written
+void spatial_order(std::vector<int>& cells, const std::vector<CellBall>& B) {
+  if (cells.size() < 2) return;
+  double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v : cells)
+    for (int c = 0; c < 3; ++c) { lo[c] = std::min(lo[c], B[v].c[c]); hi[c] = std::max(hi[c], B[v].c[c]); }
+  double ext = 0;
+  for (int c = 0; c < 3; ++c) ext = std::max(ext, hi[c] - lo[c]);
+  if (!(ext > 0)) return;
+  auto spread = [](uint64_t x) {  // 21 bits -> every third bit
+    x &= 0x1fffff;
+    x = (x | x << 32) & 0x1f00000000ffffull;
+    x = (x | x << 16) & 0x1f0000ff0000ffull;
+    x = (x | x << 8) & 0x100f00f00f00f00full;
+    x = (x | x << 4) & 0x10c30c30c30c30c3ull;
+    x = (x | x << 2) & 0x1249249249249249ull;
+    return x;
+  };
+  std::vector<std::pair<uint64_t, int>> key;
+  key.reserve(cells.size());
+  for (int v : cells) {
+    uint64_t code = 0;
+    for (int c = 0; c < 3; ++c) {
+      const double f = (B[v].c[c] - lo[c]) / ext;
+      code |= spread((uint64_t)std::min(2097151.0, std::max(0.0, f * 2097151.0))) << c;
+    }
+    key.push_back({code, v});
+  }
+  std::sort(key.begin(), key.end());
+  for (size_t q = 0; q < key.size(); ++q) cells[q] = key[q].second;
+}
+
+// per position i of cells, the positions j >= i whose cell pair is not all
+// far (sorted), found through a uniform grid of spacing twice the largest reach
+std::vector<std::vector<int>> near_cells(const std::vector<int>& cells, const std::vector<CellBall>& B) {
+  const int nc = (int)cells.size();
+  std::vector<std::vector<int>> out(nc);
+  if (nc == 0) return out;
+  double g = 0;
+  for (int v : cells) g = std::max(g, 2.0 * far_reach(B[v]));
+  g = std::max(g, 1e-300);
+  auto cell_key = [&](int v, int dx, int dy, int dz) {
+    const int64_t x = (int64_t)std::floor(B[v].c[0] / g) + dx, y = (int64_t)std::floor(B[v].c[1] / g) + dy,
+                  z = (int64_t)std::floor(B[v].c[2] / g) + dz;
+    return (uint64_t)((x & 0x1fffff) | (y & 0x1fffff) << 21 | (z & 0x1fffff) << 42);
+  };
+  std::vector<std::pair<uint64_t, int>> grid;
+  grid.reserve(nc);
+  for (int j = 0; j < nc; ++j) grid.push_back({cell_key(cells[j], 0, 0, 0), j});
+  std::sort(grid.begin(), grid.end());
+  for (int i = 0; i < nc; ++i) {
+    const int v = cells[i];
+    for (int dx = -1; dx <= 1; ++dx)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dz = -1; dz <= 1; ++dz) {
+          const uint64_t k = cell_key(v, dx, dy, dz);
+          auto it = std::lower_bound(grid.begin(), grid.end(), std::make_pair(k, -1));
+          for (; it != grid.end() && it->first == k; ++it)
+            if (it->second >= i && !cells_far(B[v], B[cells[it->second]])) out[i].push_back(it->second);
+        }
+    std::sort(out[i].begin(), out[i].end());
+    out[i].erase(std::unique(out[i].begin(), out[i].end()), out[i].end());
+  }
+  return out;
+}
+
 // Assemble S and/or C of one block (scat = -1: union; else scatterer scat).
 int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, int scat, double chi,
                    int nreg, int nsing, int precision, std::unique_ptr<Op>& out) {
@@ -140,9 +246,15 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       if (!owner) return 16;
       return bc_owner_width(sp, precision, std::max(1, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]), max_cell);
     };
-    std::vector<int> units;  // {v, begin, count, 0} per unit
+    // {v, begin, count, flag} per unit; flag -1: per-pair class test; flag >= 0
+    // (class rules, per-thread kernel): every pair of the unit is far, and bit j
+    // of flag drops trial cell j (a cell pair left to a flag -1 unit)
+    std::vector<int> units;
     std::vector<int> wlist;
     std::vector<int2> tiles;
+    const bool split_far = owner && nreg == 0;
+    std::vector<CellBall> balls;
+    if (split_far) balls = cell_balls(sp, cells, (int)m.nv);
     if (!dense) {
       // tiles (v, w), v <= w, of the cell pairs that hold a kept entry (i, j):
       // v and w end cells of i and j; per test cell a stamp array deduplicates
@@ -176,6 +288,9 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
           }
         }
         std::sort(ws.begin(), ws.end());
+        // with class rules: the cell pairs that are not all far first
+        if (split_far)
+          std::stable_partition(ws.begin(), ws.end(), [&](int w) { return !cells_far(balls[v], balls[w]); });
         for (int w : ws) tiles.push_back(make_int2(v, w));
       }
       wlist.resize(tiles.size());
@@ -183,16 +298,42 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       for (size_t q = 0; q < tiles.size();) {
         size_t e = q;
         const size_t unit = (size_t)unit_of(tiles[q].x);
-        while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < unit) ++e;
-        units.insert(units.end(), {tiles[q].x, (int)q, (int)(e - q), 0});
+        const bool far = split_far && cells_far(balls[tiles[q].x], balls[tiles[q].y]);
+        while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < unit &&
+               (!split_far || cells_far(balls[tiles[e].x], balls[tiles[e].y]) == far))
+          ++e;
+        units.insert(units.end(), {tiles[q].x, (int)q, (int)(e - q), far ? 0 : -1});
         q = e;
+      }
+    } else if (split_far) {
+      // all trial ranges are runs of cells; the cell pairs that are not all far
+      // also get units of their own, listed after the cells in wlist
+      spatial_order(cells, balls);
+      wlist = cells;
+      const int nc = (int)cells.size();
+      const std::vector<std::vector<int>> nearj = near_cells(cells, balls);
+      for (int i = 0; i < nc; ++i) {
+        const int unit = std::min(31, unit_of(cells[i]));  // the drop mask has 31 bits
+        const std::vector<int>& nj = nearj[i];
+        for (size_t q = 0; q < nj.size(); q += unit) {
+          const int cnt = (int)std::min<size_t>(unit, nj.size() - q);
+          units.insert(units.end(), {cells[i], (int)wlist.size(), cnt, -1});
+          for (int k = 0; k < cnt; ++k) wlist.push_back(cells[nj[q + k]]);
+        }
+        size_t p = 0;  // next entry of nj
+        for (int j0 = i; j0 < nc; j0 += unit) {
+          const int cnt = std::min(unit, nc - j0);
+          int mask = 0;
+          while (p < nj.size() && nj[p] < j0 + cnt) mask |= 1 << (nj[p++] - j0);
+          if (mask != (int)((1u << cnt) - 1)) units.insert(units.end(), {cells[i], j0, cnt, mask});
+        }
       }
     } else {
       wlist = cells;
       const int nc = (int)cells.size();
       for (int i = 0; i < nc; ++i) {
         const int unit = unit_of(cells[i]);
-        for (int j0 = i; j0 < nc; j0 += unit) units.insert(units.end(), {cells[i], j0, std::min(unit, nc - j0), 0});
+        for (int j0 = i; j0 < nc; j0 += unit) units.insert(units.end(), {cells[i], j0, std::min(unit, nc - j0), -1});
       }
     }
     const int64_t nunits = (int64_t)units.size() / 4;

@@ -718,7 +718,8 @@ struct BcUnit {
   int v;      // test cell (vertex id)
   int begin;  // first trial cell in the w list
   int count;  // trial cells
-  int pad;
+  int flag;   // -1: classify each pair; >= 0 (class rules, bc_owner_kernel):
+              // every pair is far, and bit j drops trial cell j
 };
 
 template <typename R> struct Vec4Of;
@@ -1021,22 +1022,41 @@ __global__ void bc_trial_pack_kernel(CellData<float> cd, int nslot, int64_t nct,
   rec[q] = o;
 }
 
-// Moments of one regular pair for the owner kernel, every accumulation a
-// single fused multiply-add: test points X = (x, y, z, w) with XW = (w x, w y,
-// w z, w); trial points Y with weights over 4 pi when PRE (the packed
-// records), plain weights otherwise.
+// Packed float32 pairs: one FFMA2 / FADD2 / FMUL2 does two round-to-nearest
+// float32 operations, here the real and imaginary parts of one complex
+// quantity (or of its three components), so the owner kernel's arithmetic is
+// that of plain float32 at about half the issued instructions.
+__device__ __forceinline__ float2 dup2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+
+// moments of one regular pair, each complex value a (re, im) pair: S needs
+// int G, int G x, int G y and int G x.y; C the same of the gradient factor g,
+// with int g x cross y in place of the dot product (x, y relative to the
+// centroids)
+struct Mom2 {
+  float2 G0, Gx[3], Gy[3], Gxy;
+  float2 g0, gx[3], gy[3], gxy[3];
+};
+
+// Moments of one regular pair for the owner kernel: test points X = (x, y, z,
+// w) with XW = (w x, w y, w z, w); trial points Y with weights over 4 pi when
+// PRE (the packed records), plain weights otherwise.
 template <int NP, bool PRE, bool FULL>
 __device__ __forceinline__ void owner_moments(const P4<float>* __restrict__ X, const P4<float>* __restrict__ XW,
                                               const P4<float>* __restrict__ Y, const V3<float>& D, float kr,
-                                              float ki, bool wantC, Mom<float>& m) {
-  m.zero();
-  // FULL (S and C fixed at compile time): all test points unrolled (measured
-  // 7% faster there); otherwise two at a time
+                                              float ki, bool wantC, Mom2& m) {
+  const float2 z0 = make_float2(0.f, 0.f);
+  m.G0 = m.Gxy = m.g0 = z0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) m.Gx[c] = m.Gy[c] = m.gx[c] = m.gy[c] = m.gxy[c] = z0;
+  // FULL (S and C fixed at compile time): all test points unrolled; otherwise
+  // two at a time
 #pragma unroll(FULL ? NP : 2)
   for (int p = 0; p < NP; ++p) {
     const P4<float> xp = X[p], xw = XW[p];
-    float s0r = 0, s0i = 0, t0r = 0, t0i = 0;
-    V3<float> ser = {0, 0, 0}, sei = {0, 0, 0}, ter = {0, 0, 0}, tei = {0, 0, 0};
+    float2 s0 = z0, t0 = z0, se[3] = {z0, z0, z0}, te[3] = {z0, z0, z0};
     const V3<float> dp = {D.x + xp.x, D.y + xp.y, D.z + xp.z};
 #pragma unroll
     for (int q = 0; q < NP; ++q) {
@@ -1044,69 +1064,65 @@ __device__ __forceinline__ void owner_moments(const P4<float>* __restrict__ X, c
       const float dx = dp.x - yq.x, dy = dp.y - yq.y, dz = dp.z - yq.z;
       float Gr, Gi, gr, gi;
       green4(dx * dx + dy * dy + dz * dz, kr, ki, Gr, Gi, gr, gi, PRE ? yq.w : yq.w * INV_4PI_F);
-      s0r += Gr; s0i += Gi;
-      ser.x = fmaf(Gr, yq.x, ser.x); ser.y = fmaf(Gr, yq.y, ser.y); ser.z = fmaf(Gr, yq.z, ser.z);
-      sei.x = fmaf(Gi, yq.x, sei.x); sei.y = fmaf(Gi, yq.y, sei.y); sei.z = fmaf(Gi, yq.z, sei.z);
+      const float2 G = make_float2(Gr, Gi);
+      s0 = add2(s0, G);
+      se[0] = fma2(G, dup2(yq.x), se[0]);
+      se[1] = fma2(G, dup2(yq.y), se[1]);
+      se[2] = fma2(G, dup2(yq.z), se[2]);
       if (wantC) {
-        t0r += gr; t0i += gi;
-        ter.x = fmaf(gr, yq.x, ter.x); ter.y = fmaf(gr, yq.y, ter.y); ter.z = fmaf(gr, yq.z, ter.z);
-        tei.x = fmaf(gi, yq.x, tei.x); tei.y = fmaf(gi, yq.y, tei.y); tei.z = fmaf(gi, yq.z, tei.z);
+        const float2 g = make_float2(gr, gi);
+        t0 = add2(t0, g);
+        te[0] = fma2(g, dup2(yq.x), te[0]);
+        te[1] = fma2(g, dup2(yq.y), te[1]);
+        te[2] = fma2(g, dup2(yq.z), te[2]);
       }
     }
-    const float w = xw.w;
-    m.G0r = fmaf(w, s0r, m.G0r); m.G0i = fmaf(w, s0i, m.G0i);
-    m.Gxr.x = fmaf(xw.x, s0r, m.Gxr.x); m.Gxr.y = fmaf(xw.y, s0r, m.Gxr.y); m.Gxr.z = fmaf(xw.z, s0r, m.Gxr.z);
-    m.Gxi.x = fmaf(xw.x, s0i, m.Gxi.x); m.Gxi.y = fmaf(xw.y, s0i, m.Gxi.y); m.Gxi.z = fmaf(xw.z, s0i, m.Gxi.z);
-    m.Gyr.x = fmaf(w, ser.x, m.Gyr.x); m.Gyr.y = fmaf(w, ser.y, m.Gyr.y); m.Gyr.z = fmaf(w, ser.z, m.Gyr.z);
-    m.Gyi.x = fmaf(w, sei.x, m.Gyi.x); m.Gyi.y = fmaf(w, sei.y, m.Gyi.y); m.Gyi.z = fmaf(w, sei.z, m.Gyi.z);
-    m.Gxyr = fmaf(xw.z, ser.z, fmaf(xw.y, ser.y, fmaf(xw.x, ser.x, m.Gxyr)));
-    m.Gxyi = fmaf(xw.z, sei.z, fmaf(xw.y, sei.y, fmaf(xw.x, sei.x, m.Gxyi)));
+    const float2 w2 = dup2(xw.w), x2 = dup2(xw.x), y2 = dup2(xw.y), z2 = dup2(xw.z);
+    m.G0 = fma2(w2, s0, m.G0);
+    m.Gx[0] = fma2(x2, s0, m.Gx[0]);
+    m.Gx[1] = fma2(y2, s0, m.Gx[1]);
+    m.Gx[2] = fma2(z2, s0, m.Gx[2]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) m.Gy[c] = fma2(w2, se[c], m.Gy[c]);
+    m.Gxy = fma2(z2, se[2], fma2(y2, se[1], fma2(x2, se[0], m.Gxy)));
     if (wantC) {
-      m.g0r = fmaf(w, t0r, m.g0r); m.g0i = fmaf(w, t0i, m.g0i);
-      m.gxr.x = fmaf(xw.x, t0r, m.gxr.x); m.gxr.y = fmaf(xw.y, t0r, m.gxr.y); m.gxr.z = fmaf(xw.z, t0r, m.gxr.z);
-      m.gxi.x = fmaf(xw.x, t0i, m.gxi.x); m.gxi.y = fmaf(xw.y, t0i, m.gxi.y); m.gxi.z = fmaf(xw.z, t0i, m.gxi.z);
-      m.gyr.x = fmaf(w, ter.x, m.gyr.x); m.gyr.y = fmaf(w, ter.y, m.gyr.y); m.gyr.z = fmaf(w, ter.z, m.gyr.z);
-      m.gyi.x = fmaf(w, tei.x, m.gyi.x); m.gyi.y = fmaf(w, tei.y, m.gyi.y); m.gyi.z = fmaf(w, tei.z, m.gyi.z);
-      // gxy += (w x) x te
-      m.gxyr.x = fmaf(xw.y, ter.z, fmaf(-xw.z, ter.y, m.gxyr.x));
-      m.gxyr.y = fmaf(xw.z, ter.x, fmaf(-xw.x, ter.z, m.gxyr.y));
-      m.gxyr.z = fmaf(xw.x, ter.y, fmaf(-xw.y, ter.x, m.gxyr.z));
-      m.gxyi.x = fmaf(xw.y, tei.z, fmaf(-xw.z, tei.y, m.gxyi.x));
-      m.gxyi.y = fmaf(xw.z, tei.x, fmaf(-xw.x, tei.z, m.gxyi.y));
-      m.gxyi.z = fmaf(xw.x, tei.y, fmaf(-xw.y, tei.x, m.gxyi.z));
+      m.g0 = fma2(w2, t0, m.g0);
+      m.gx[0] = fma2(x2, t0, m.gx[0]);
+      m.gx[1] = fma2(y2, t0, m.gx[1]);
+      m.gx[2] = fma2(z2, t0, m.gx[2]);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) m.gy[c] = fma2(w2, te[c], m.gy[c]);
+      // gxy += (w x) cross te
+      m.gxy[0] = fma2(y2, te[2], fma2(dup2(-xw.z), te[1], m.gxy[0]));
+      m.gxy[1] = fma2(z2, te[0], fma2(dup2(-xw.x), te[2], m.gxy[1]));
+      m.gxy[2] = fma2(x2, te[1], fma2(dup2(-xw.y), te[0], m.gxy[2]));
     }
   }
 }
 
-// pair_coeffs with fused multiply-adds (same layout)
-__device__ __forceinline__ void pair_coeffs_fused(const Mom<float>& m, const V3<float>& D, float* pc) {
-  pc[0] = m.G0r; pc[1] = m.G0i;
-  pc[2] = m.Gxr.x; pc[3] = m.Gxr.y; pc[4] = m.Gxr.z; pc[5] = m.Gxi.x; pc[6] = m.Gxi.y; pc[7] = m.Gxi.z;
-  pc[8] = m.Gyr.x; pc[9] = m.Gyr.y; pc[10] = m.Gyr.z; pc[11] = m.Gyi.x; pc[12] = m.Gyi.y; pc[13] = m.Gyi.z;
-  pc[14] = m.Gxyr; pc[15] = m.Gxyi;
-  pc[16] = fmaf(D.z, m.gxyr.z, fmaf(D.y, m.gxyr.y, D.x * m.gxyr.x));
-  pc[17] = fmaf(D.z, m.gxyi.z, fmaf(D.y, m.gxyi.y, D.x * m.gxyi.x));
-  // X1 = D x gx + gxy
-  pc[18] = fmaf(D.y, m.gxr.z, fmaf(-D.z, m.gxr.y, m.gxyr.x));
-  pc[19] = fmaf(D.z, m.gxr.x, fmaf(-D.x, m.gxr.z, m.gxyr.y));
-  pc[20] = fmaf(D.x, m.gxr.y, fmaf(-D.y, m.gxr.x, m.gxyr.z));
-  pc[21] = fmaf(D.y, m.gxi.z, fmaf(-D.z, m.gxi.y, m.gxyi.x));
-  pc[22] = fmaf(D.z, m.gxi.x, fmaf(-D.x, m.gxi.z, m.gxyi.y));
-  pc[23] = fmaf(D.x, m.gxi.y, fmaf(-D.y, m.gxi.x, m.gxyi.z));
-  // X2 = gy x D - gxy
-  pc[24] = fmaf(m.gyr.y, D.z, fmaf(-m.gyr.z, D.y, -m.gxyr.x));
-  pc[25] = fmaf(m.gyr.z, D.x, fmaf(-m.gyr.x, D.z, -m.gxyr.y));
-  pc[26] = fmaf(m.gyr.x, D.y, fmaf(-m.gyr.y, D.x, -m.gxyr.z));
-  pc[27] = fmaf(m.gyi.y, D.z, fmaf(-m.gyi.z, D.y, -m.gxyi.x));
-  pc[28] = fmaf(m.gyi.z, D.x, fmaf(-m.gyi.x, D.z, -m.gxyi.y));
-  pc[29] = fmaf(m.gyi.x, D.y, fmaf(-m.gyi.y, D.x, -m.gxyi.z));
-  // V = D g0 + gx - gy
-  pc[30] = fmaf(D.x, m.g0r, m.gxr.x - m.gyr.x);
-  pc[31] = fmaf(D.y, m.g0r, m.gxr.y - m.gyr.y);
-  pc[32] = fmaf(D.z, m.g0r, m.gxr.z - m.gyr.z);
-  pc[33] = fmaf(D.x, m.g0i, m.gxi.x - m.gyi.x);
-  pc[34] = fmaf(D.y, m.g0i, m.gxi.y - m.gyi.y);
-  pc[35] = fmaf(D.z, m.g0i, m.gxi.z - m.gyi.z);
+// the C pair coefficients from the moments (D = c1 - c2): D . gxy; X1 = D x gx
+// + gxy; Y2 = gxy - gy x D (the coefficient gy x D - gxy with its sign
+// flipped); V = D g0 + gx - gy and nV = -V
+struct PairC2 {
+  float2 Dgxy, X1[3], Y2[3], V[3], nV[3];
+};
+
+__device__ __forceinline__ void pair_c_coeffs(const Mom2& m, const V3<float>& D, PairC2& pc) {
+  const float2 dx = dup2(D.x), dy = dup2(D.y), dz = dup2(D.z);
+  const float2 ndx = dup2(-D.x), ndy = dup2(-D.y), ndz = dup2(-D.z), mone = dup2(-1.f);
+  pc.Dgxy = fma2(dz, m.gxy[2], fma2(dy, m.gxy[1], mul2(dx, m.gxy[0])));
+  pc.X1[0] = fma2(dy, m.gx[2], fma2(ndz, m.gx[1], m.gxy[0]));
+  pc.X1[1] = fma2(dz, m.gx[0], fma2(ndx, m.gx[2], m.gxy[1]));
+  pc.X1[2] = fma2(dx, m.gx[1], fma2(ndy, m.gx[0], m.gxy[2]));
+  pc.Y2[0] = fma2(m.gy[2], dy, fma2(m.gy[1], ndz, m.gxy[0]));
+  pc.Y2[1] = fma2(m.gy[0], dz, fma2(m.gy[2], ndx, m.gxy[1]));
+  pc.Y2[2] = fma2(m.gy[1], dx, fma2(m.gy[0], ndy, m.gxy[2]));
+  pc.V[0] = fma2(dx, m.g0, fma2(mone, m.gy[0], m.gx[0]));
+  pc.V[1] = fma2(dy, m.g0, fma2(mone, m.gy[1], m.gx[1]));
+  pc.V[2] = fma2(dz, m.g0, fma2(mone, m.gy[2], m.gx[2]));
+  pc.nV[0] = fma2(ndx, m.g0, fma2(mone, m.gx[0], m.gy[0]));
+  pc.nV[1] = fma2(ndy, m.g0, fma2(mone, m.gx[1], m.gy[1]));
+  pc.nV[2] = fma2(ndz, m.g0, fma2(mone, m.gx[2], m.gy[2]));
 }
 
 template <int NREG, int TT, bool BOTH>
@@ -1136,6 +1152,11 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
     const BcUnit U = units[uidx];
     const int v = U.v;
+    // class rules: a unit whose pairs are all far (decided per cell pair on the
+    // host, with a margin over this kernel's own test) skips the per-pair class
+    // test, so its warps never split between rules; uniform over the block
+    const bool all_far = NREG == 0 && U.flag >= 0;
+    const int drop = U.flag > 0 ? U.flag : 0;
     const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
     const int ns1 = cell_edge_ptr[v + 1] - cell_edge_ptr[v];
     __syncthreads();  // the previous unit is done with the test-cell data and the records
@@ -1154,7 +1175,7 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       const int b = cell_ptr[w];
       jw[j] = w;
       jb[j] = b;
-      jn[j] = cell_ptr[w + 1] - b;
+      jn[j] = (drop >> j) & 1 ? 0 : cell_ptr[w + 1] - b;  // a dropped cell has no pairs here
       const int e0 = cell_edge_ptr[w], ns = cell_edge_ptr[w + 1] - e0;
 #pragma unroll
       for (int sl = 0; sl < NSL; ++sl) js[j * NSL + sl] = sl < ns ? cell_slot_s[e0 + sl] : 0.0f;
@@ -1183,15 +1204,17 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       // slot b on tau2 is sigma_b (y - c2) + w_b with sigma_b = s_b / |tau2| (s_b
       // constant over the cell): the sigma terms of all slots are one sum a[]
       // over tau2 of the pair coefficients times 1/|tau2|, scaled by s_b at the
-      // end; r[b] holds the w_b terms (components 2 and 3 have none)
-      float r[NSL][18];
-      float a[18];
+      // end; r[b] holds the w_b terms. Record layout, complex (re, im) pairs:
+      // S: AS, BS, WS[3]; C: AC, WC[3] (BS has no w_b term).
+      const float2 z0 = make_float2(0.f, 0.f);
+      float2 r[NSL][8];
+      float2 a[9];
 #pragma unroll
       for (int b = 0; b < NSL; ++b)
 #pragma unroll
-        for (int f = 0; f < 18; ++f) r[b][f] = 0.0f;
+        for (int f = 0; f < 8; ++f) r[b][f] = z0;
 #pragma unroll
-      for (int f = 0; f < 18; ++f) a[f] = 0.0f;
+      for (int f = 0; f < 9; ++f) a[f] = z0;
       for (int i2 = 0; i2 < n2; ++i2) {
         const float4* rr = R2 + i2 * RW;
         const float4 k0 = rr[NP + NSL], k1 = rr[NP + NSL + 1], k2 = rr[NP + NSL + 2];
@@ -1209,11 +1232,14 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
           return va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 || va2 == vb0 ||
                  va2 == vb1 || va2 == vb2;
         };
-        Mom<float> m;
+        Mom2 m;
         if constexpr (NREG > 0) {
           if (touch()) continue;
           owner_moments<NREG, true, BOTH>(X, XW, Ys, D, kr, ki, wantC, m);
           evals += NREG * NREG;
+        } else if (all_far) {
+          owner_moments<3, true, BOTH>(X + RULE_OFF_FAR, XW + RULE_OFF_FAR, Ys, D, kr, ki, wantC, m);
+          evals += 9;
         } else {
           const int c = pair_class<float>(D, ca.d, cb.d);
           if (c == 2) {
@@ -1233,88 +1259,80 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
             }
           }
         }
-        float pc[36];
-        pair_coeffs_fused(m, D, pc);
+        PairC2 pc;
+        pair_c_coeffs(m, D, pc);
         // sigma terms: the pair coefficients that multiply sigma_b, times 1/|tau2|
-        const float beta = k2.z;
-        a[0] = fmaf(beta, pc[14], a[0]);
-        a[1] = fmaf(beta, pc[15], a[1]);
-        a[2] = fmaf(beta, pc[0], a[2]);
-        a[3] = fmaf(beta, pc[1], a[3]);
+        const float2 beta = dup2(k2.z), nbeta = dup2(-k2.z);
+        a[0] = fma2(beta, m.Gxy, a[0]);
+        a[1] = fma2(beta, m.G0, a[1]);
 #pragma unroll
-        for (int f = 0; f < 6; ++f) a[4 + f] = fmaf(beta, pc[8 + f], a[4 + f]);
-        a[10] = fmaf(beta, pc[16], a[10]);
-        a[11] = fmaf(beta, pc[17], a[11]);
+        for (int c = 0; c < 3; ++c) a[2 + c] = fma2(beta, m.Gy[c], a[2 + c]);
+        a[5] = fma2(beta, pc.Dgxy, a[5]);
 #pragma unroll
-        for (int f = 0; f < 6; ++f) a[12 + f] = fmaf(beta, pc[24 + f], a[12 + f]);
+        for (int c = 0; c < 3; ++c) a[6 + c] = fma2(nbeta, pc.Y2[c], a[6 + c]);
         const P4<float>* swb = Ys + NP;
 #pragma unroll
         for (int b = 0; b < NSL; ++b) {
           if (b >= ns2) break;
           const P4<float> u = swb[b];
-          const float bx = u.y, by = u.z, bz = u.w;
-          float* o = r[b];
-          // S: AS (re, im), WS_r, WS_i (w_b terms)
-          o[0] = fmaf(bz, pc[4], fmaf(by, pc[3], fmaf(bx, pc[2], o[0])));
-          o[1] = fmaf(bz, pc[7], fmaf(by, pc[6], fmaf(bx, pc[5], o[1])));
-          o[4] = fmaf(bx, pc[0], o[4]);
-          o[5] = fmaf(by, pc[0], o[5]);
-          o[6] = fmaf(bz, pc[0], o[6]);
-          o[7] = fmaf(bx, pc[1], o[7]);
-          o[8] = fmaf(by, pc[1], o[8]);
-          o[9] = fmaf(bz, pc[1], o[9]);
-          // C: AC (re, im), WC_r = w_b x Vr, WC_i
-          o[10] = fmaf(bz, pc[20], fmaf(by, pc[19], fmaf(bx, pc[18], o[10])));
-          o[11] = fmaf(bz, pc[23], fmaf(by, pc[22], fmaf(bx, pc[21], o[11])));
-          o[12] = fmaf(by, pc[32], fmaf(-bz, pc[31], o[12]));
-          o[13] = fmaf(bz, pc[30], fmaf(-bx, pc[32], o[13]));
-          o[14] = fmaf(bx, pc[31], fmaf(-by, pc[30], o[14]));
-          o[15] = fmaf(by, pc[35], fmaf(-bz, pc[34], o[15]));
-          o[16] = fmaf(bz, pc[33], fmaf(-bx, pc[35], o[16]));
-          o[17] = fmaf(bx, pc[34], fmaf(-by, pc[33], o[17]));
+          const float2 bx = dup2(u.y), by = dup2(u.z), bz = dup2(u.w);
+          float2* o = r[b];
+          // S: AS = w_b . Gx, WS = w_b G0
+          o[0] = fma2(bz, m.Gx[2], fma2(by, m.Gx[1], fma2(bx, m.Gx[0], o[0])));
+          o[1] = fma2(bx, m.G0, o[1]);
+          o[2] = fma2(by, m.G0, o[2]);
+          o[3] = fma2(bz, m.G0, o[3]);
+          // C: AC = w_b . X1, WC = w_b x V
+          o[4] = fma2(bz, pc.X1[2], fma2(by, pc.X1[1], fma2(bx, pc.X1[0], o[4])));
+          o[5] = fma2(by, pc.V[2], fma2(bz, pc.nV[1], o[5]));
+          o[6] = fma2(bz, pc.V[0], fma2(bx, pc.nV[2], o[6]));
+          o[7] = fma2(bx, pc.V[1], fma2(by, pc.nV[0], o[7]));
         }
       }
       float* dst = rec + (size_t)threadIdx.x * NSL * BC_OWN_REC;
 #pragma unroll
       for (int b = 0; b < NSL; ++b) {
         if (b >= ns2) break;
-        const float sb = js[j * NSL + b];
-        __align__(16) float tmp[BC_OWN_REC];
+        const float2 sb = dup2(js[j * NSL + b]);
+        __align__(16) float2 tmp[BC_OWN_REC / 2];
+        tmp[0] = fma2(sb, a[0], r[b][0]);  // AS
+        tmp[1] = mul2(sb, a[1]);           // BS
 #pragma unroll
-        for (int f = 0; f < 18; ++f) tmp[f] = fmaf(sb, a[f], r[b][f]);
-        tmp[18] = tmp[19] = 0.0f;
-        vcopy(dst + b * BC_OWN_REC, tmp, BC_OWN_REC);
+        for (int c = 0; c < 3; ++c) tmp[2 + c] = fma2(sb, a[2 + c], r[b][1 + c]);  // WS
+        tmp[5] = fma2(sb, a[5], r[b][4]);  // AC
+#pragma unroll
+        for (int c = 0; c < 3; ++c) tmp[6 + c] = fma2(sb, a[6 + c], r[b][5 + c]);  // WC
+        tmp[9] = z0;
+        vcopy(dst + b * BC_OWN_REC, reinterpret_cast<const float*>(tmp), BC_OWN_REC);
       }
     }
     __syncthreads();
-    // test-side contraction per (j, a, b), S and C together, summed over tau1
+    // test-side contraction per (j, a, b), S and C together, summed over tau1;
+    // the constants -ik and c4 of the S entry factor out of the sum
     for (int q = threadIdx.x; q < U.count * ns1 * NSL; q += TT) {
       const int j = q / (ns1 * NSL);
       const int rest = q - j * ns1 * NSL;
       const int sa_i = rest / NSL, sb_i = rest - (rest / NSL) * NSL;
       const int w = jw[j];
       const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
-      if (sb_i >= ns2) continue;
-      float sr = 0, si = 0, cr = 0, ci = 0;
+      if (sb_i >= ns2 || jn[j] == 0) continue;
+      float2 P = make_float2(0.f, 0.f), Q = P, Cs = P;
       for (int i1 = 0; i1 < n1; ++i1) {
         const P4<float> u = swA[i1 * nslot + sa_i];
-        const float sa = u.x;
-        const V3<float> wa = {u.y, u.z, u.w};
-        __align__(16) float o[BC_OWN_REC];
-        vcopy(o, rec + ((size_t)(j * n1 + i1) * NSL + sb_i) * BC_OWN_REC, BC_OWN_REC);
-        // S: sa (mik AS + c4 BS) + mik (wa . WS)
-        const float pr = sa * o[0] + wa.x * o[4] + wa.y * o[5] + wa.z * o[6];
-        const float pi = sa * o[1] + wa.x * o[7] + wa.y * o[8] + wa.z * o[9];
-        sr += mikr * pr - miki * pi + sa * (c4r * o[2] - c4i * o[3]);
-        si += mikr * pi + miki * pr + sa * (c4r * o[3] + c4i * o[2]);
-        // C: sa AC + wa . WC
-        cr += sa * o[10] + wa.x * o[12] + wa.y * o[13] + wa.z * o[14];
-        ci += sa * o[11] + wa.x * o[15] + wa.y * o[16] + wa.z * o[17];
+        const float2 sa = dup2(u.x), wx = dup2(u.y), wy = dup2(u.z), wz = dup2(u.w);
+        __align__(16) float2 o[BC_OWN_REC / 2];
+        vcopy(reinterpret_cast<float*>(o), rec + ((size_t)(j * n1 + i1) * NSL + sb_i) * BC_OWN_REC, BC_OWN_REC);
+        // S: sa AS + wa . WS (times -ik), sa BS (times c4); C: sa AC + wa . WC
+        P = fma2(wz, o[4], fma2(wy, o[3], fma2(wx, o[2], fma2(sa, o[0], P))));
+        Q = fma2(sa, o[1], Q);
+        Cs = fma2(wz, o[8], fma2(wy, o[7], fma2(wx, o[6], fma2(sa, o[5], Cs))));
       }
+      const float sr = mikr * P.x - miki * P.y + c4r * Q.x - c4i * Q.y;
+      const float si = mikr * P.y + miki * P.x + c4r * Q.y + c4i * Q.x;
       const int ea = cell_edge[cell_edge_ptr[v] + sa_i];
       const int eb = cell_edge[cell_edge_ptr[w] + sb_i];
-      out.add(ea, eb, wantS, wantC, sr, si, cr, ci);
-      if (v != w) out.add(eb, ea, wantS, wantC, sr, si, cr, ci);
+      out.add(ea, eb, wantS, wantC, sr, si, Cs.x, Cs.y);
+      if (v != w) out.add(eb, ea, wantS, wantC, sr, si, Cs.x, Cs.y);
     }
   }
   count_add(cnt, evals);
