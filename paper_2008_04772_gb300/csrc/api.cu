@@ -93,7 +93,8 @@ double far_reach(const CellBall& b) { return b.rho + 4.0 * FAR_MARGIN * b.dm; }
 bool cells_far(const CellBall& a, const CellBall& b) {
   double d2 = 0;
   for (int c = 0; c < 3; ++c) d2 += (a.c[c] - b.c[c]) * (a.c[c] - b.c[c]);
-  return std::sqrt(d2) - a.rho - b.rho > 4.0 * FAR_MARGIN * std::max(a.dm, b.dm);
+  const double t = a.rho + b.rho + 4.0 * FAR_MARGIN * std::max(a.dm, b.dm);  // |C_v - C_w| > t
+  return d2 > t * t;
 }
 
 // cells in Morton order of their centres: the cells of one edge's two ends come

@@ -1125,6 +1125,18 @@ __device__ __forceinline__ void pair_c_coeffs(const Mom2& m, const V3<float>& D,
   pc.nV[2] = fma2(ndz, m.g0, fma2(mone, m.gx[2], m.gy[2]));
 }
 
+// asynchronous global -> shared copies (complete at cp.async.wait_all of the
+// issuing thread; a barrier after that makes them visible to the block)
+__device__ __forceinline__ void cp_async4(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int NREG, int TT, bool BOTH>
 __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     CellData<float> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
@@ -1147,10 +1159,25 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   int* jn = jb + TT;                                                                // [TT] trial triangles
   int* jw = jn + TT;                                                                // [TT] trial cell
   float* js = reinterpret_cast<float*>(jw + TT);                                    // [TT][NSL] s_b of cell j
+  int* jns = reinterpret_cast<int*>(js + TT * NSL);                                 // [TT] slots of cell j
+  int* jeb = jns + TT;                                                              // [TT][NSL] edge of slot b
+  int* eaS = jeb + TT * NSL;                                                        // [NSL] edge of test slot a
+  int* wnext = eaS + NSL;                                                           // [TT] next unit's trial cells
+  BcUnit* nextU = reinterpret_cast<BcUnit*>((reinterpret_cast<uintptr_t>(wnext + TT) + 15) & ~uintptr_t(15));
   if (BOTH) wantS = wantC = true;  // S and C: the branches on them fold away
   unsigned evals = 0;
+  // The next unit's descriptor and trial-cell list are copied into shared
+  // memory while the current unit computes (cp.async), so a unit starts two
+  // dependent global loads closer to its data.
+  if (threadIdx.x == 0 && (int64_t)blockIdx.x < nunits) cp_async16(nextU, units + blockIdx.x);
+  cp_async_wait_all();
+  __syncthreads();
+  if ((int64_t)blockIdx.x < nunits && (int)threadIdx.x < nextU->count)
+    cp_async4(wnext + threadIdx.x, wlist + nextU->begin + threadIdx.x);
+  cp_async_wait_all();
   for (int64_t uidx = blockIdx.x; uidx < nunits; uidx += gridDim.x) {
-    const BcUnit U = units[uidx];
+    __syncthreads();  // the previous unit is done with every buffer; nextU and wnext have landed
+    const BcUnit U = *nextU;
     const int v = U.v;
     // class rules: a unit whose pairs are all far (decided per cell pair on the
     // host, with a margin over this kernel's own test) skips the per-pair class
@@ -1158,8 +1185,8 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     const bool all_far = NREG == 0 && U.flag >= 0;
     const int drop = U.flag > 0 ? U.flag : 0;
     const int b1 = cell_ptr[v], n1 = cell_ptr[v + 1] - b1;
-    const int ns1 = cell_edge_ptr[v + 1] - cell_edge_ptr[v];
-    __syncthreads();  // the previous unit is done with the test-cell data and the records
+    const int ea0 = cell_edge_ptr[v], ns1 = cell_edge_ptr[v + 1] - ea0;
+    for (int q = threadIdx.x; q < ns1; q += TT) eaS[q] = cell_edge[ea0 + q];
     for (int q = threadIdx.x; q < n1 * NS; q += TT) {
       const P4<float> x = cd.pts[(size_t)b1 * NS + q];
       ptsA[q] = x;
@@ -1171,31 +1198,39 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       for (int c = 0; c < 3; ++c) vidA[3 * q + c] = cd.vid[(size_t)(b1 + q) * 3 + c];
     }
     for (int j = threadIdx.x; j < U.count; j += TT) {
-      const int w = wlist[U.begin + j];
+      const int w = wnext[j];
       const int b = cell_ptr[w];
       jw[j] = w;
       jb[j] = b;
       jn[j] = (drop >> j) & 1 ? 0 : cell_ptr[w + 1] - b;  // a dropped cell has no pairs here
       const int e0 = cell_edge_ptr[w], ns = cell_edge_ptr[w + 1] - e0;
+      jns[j] = ns;
 #pragma unroll
-      for (int sl = 0; sl < NSL; ++sl) js[j * NSL + sl] = sl < ns ? cell_slot_s[e0 + sl] : 0.0f;
+      for (int sl = 0; sl < NSL; ++sl) {
+        js[j * NSL + sl] = sl < ns ? cell_slot_s[e0 + sl] : 0.0f;
+        jeb[j * NSL + sl] = sl < ns ? cell_edge[e0 + sl] : -1;
+      }
     }
     __syncthreads();
     // trial records: cell j at rows [j max_cell, j max_cell + n2); the host
     // keeps count x max_cell <= BC_OWN_STAGE
+    // (asynchronous copies: all of a thread's rows are in flight at once)
     for (int q = threadIdx.x; q < U.count * max_cell * RW; q += TT) {
       const int row = q / RW, u = q - row * RW;
       const int j = row / max_cell, i2 = row - j * max_cell;
-      if (i2 < jn[j]) trial[q] = trec[(size_t)(jb[j] + i2) * RW + u];
+      if (i2 < jn[j]) cp_async16(trial + q, trec + (size_t)(jb[j] + i2) * RW + u);
     }
+    cp_async_wait_all();
     __syncthreads();
+    // every thread has read nextU and wnext: copy the next unit's descriptor
+    const bool more = uidx + gridDim.x < nunits;
+    if (threadIdx.x == 0 && more) cp_async16(nextU, units + uidx + gridDim.x);
     const int items = n1 * U.count;
     // pair loop: thread t = j n1 + i1
     if ((int)threadIdx.x < items) {
       const int j = threadIdx.x / n1, i1 = threadIdx.x - j * n1;
-      const int w = jw[j];
       const int b2 = jb[j], n2 = jn[j];
-      const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
+      const int ns2 = jns[j];
       const float4* R2 = trial + (size_t)j * max_cell * RW;
       const Cent<float> ca = cA[i1];
       const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
@@ -1306,7 +1341,10 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
         vcopy(dst + b * BC_OWN_REC, reinterpret_cast<const float*>(tmp), BC_OWN_REC);
       }
     }
-    __syncthreads();
+    if (threadIdx.x == 0) cp_async_wait_all();
+    __syncthreads();  // records written; the next descriptor has landed
+    // the next unit's trial-cell list (wnext was read in this unit's staging)
+    if (more && (int)threadIdx.x < nextU->count) cp_async4(wnext + threadIdx.x, wlist + nextU->begin + threadIdx.x);
     // test-side contraction per (j, a, b), S and C together, summed over tau1;
     // the constants -ik and c4 of the S entry factor out of the sum
     for (int q = threadIdx.x; q < U.count * ns1 * NSL; q += TT) {
@@ -1314,8 +1352,7 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       const int rest = q - j * ns1 * NSL;
       const int sa_i = rest / NSL, sb_i = rest - (rest / NSL) * NSL;
       const int w = jw[j];
-      const int ns2 = cell_edge_ptr[w + 1] - cell_edge_ptr[w];
-      if (sb_i >= ns2 || jn[j] == 0) continue;
+      if (sb_i >= jns[j] || jn[j] == 0) continue;
       float2 P = make_float2(0.f, 0.f), Q = P, Cs = P;
       for (int i1 = 0; i1 < n1; ++i1) {
         const P4<float> u = swA[i1 * nslot + sa_i];
@@ -1329,11 +1366,12 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
       }
       const float sr = mikr * P.x - miki * P.y + c4r * Q.x - c4i * Q.y;
       const float si = mikr * P.y + miki * P.x + c4r * Q.y + c4i * Q.x;
-      const int ea = cell_edge[cell_edge_ptr[v] + sa_i];
-      const int eb = cell_edge[cell_edge_ptr[w] + sb_i];
+      const int ea = eaS[sa_i];
+      const int eb = jeb[j * NSL + sb_i];
       out.add(ea, eb, wantS, wantC, sr, si, Cs.x, Cs.y);
       if (v != w) out.add(eb, ea, wantS, wantC, sr, si, Cs.x, Cs.y);
     }
+    cp_async_wait_all();  // this thread's copies of the next trial-cell list
   }
   count_add(cnt, evals);
 }
@@ -2412,7 +2450,10 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
                            2 * (size_t)max_cell * nsp_o * sizeof(P4<float>) +
                            (size_t)max_cell * s.nslot * sizeof(P4<float>) + (size_t)max_cell * sizeof(Cent<float>) +
                            (size_t)max_cell * 3 * sizeof(int) + 3 * (size_t)OT * sizeof(int) +
-                           (size_t)OT * BC_OWN_SLOTS * sizeof(float) + 64;
+                           (size_t)OT * BC_OWN_SLOTS * sizeof(float) +
+                           // slot counts, slot edges, test edges, next trial cells, next descriptor
+                           (size_t)OT * sizeof(int) + (size_t)OT * BC_OWN_SLOTS * sizeof(int) +
+                           BC_OWN_SLOTS * sizeof(int) + (size_t)OT * sizeof(int) + 2 * sizeof(BcUnit) + 64;
       int rc = ensure_dyn_smem((const void*)okern, (int)osmem);
       int per_sm = 0;
       if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, OT, osmem) != cudaSuccess)
