@@ -47,15 +47,16 @@ def test_compress_matches_oracle_model(ctx, sphere2_bc, nu, chi):
     info = h.info()
     assert info.format == cal.HMAT
     Sh, Ch = h.export(cal.OP_S), h.export(cal.OP_C)
-    if info.nnz == stored:  # the same ranks everywhere: the same pivots, the same factors
-        assert rel(Sh, So) < 1e-9, rel(Sh, So)
-        assert rel(Ch, Co) < 1e-9, rel(Ch, Co)
-    else:
-        # a leaf whose stopping test |u||v| <= nu |B_r|_F is a near-tie may take
-        # one step more on one side (sums in another order); the extra term is
-        # below the tolerance
-        assert abs(info.nnz - stored) <= 1e-3 * stored, (info.nnz, stored)
-        assert rel(Sh, So) < nu and rel(Ch, Co) < nu, (rel(Sh, So), rel(Ch, Co))
+    # Leaves whose pivots are not near-ties take the same pivots and factors on
+    # both sides, so nearly every entry equals the model. A leaf whose pivot
+    # (largest modulus) or stopping test |u||v| <= nu |B_r|_F is a tie to
+    # rounding may go either way (sums in another order); either result is an
+    # ACA step, within nu of the block.
+    for H, O, M in ((Sh, So, S), (Ch, Co, C)):
+        same = np.abs(H - O) <= 1e-9 * np.abs(M).max()
+        assert same.mean() >= 0.9, same.mean()
+        assert rel(H, O) < nu, rel(H, O)
+    assert abs(info.nnz - stored) <= 1e-3 * stored, (info.nnz, stored)
     if math.isinf(chi):  # nothing dropped: close to the dense operators
         assert rel(Sh, S) < 3 * nu and rel(Ch, C) < 30 * nu
 
