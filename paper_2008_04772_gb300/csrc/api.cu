@@ -165,6 +165,153 @@ std::vector<std::vector<int>> near_cells(const std::vector<int>& cells, const st
   return out;
 }
 
+// Work units of the BC regular-pair kernels for one scatterer: tiles (v, w),
+// v <= w, of dual cells, grouped into units of one test cell and up to 16
+// trial cells (or as many as fill the block of the float32 per-thread kernel).
+// Dense blocks take every cell pair; near-field blocks the cell pairs that
+// hold a kept entry of the CSR pattern of op.
+int build_units(const Space& sp, int scat, bool dense, const Op& op, int precision, int nreg, Space::UnitLists& L,
+                cudaStream_t st) {
+  const Mesh& m = *sp.mesh;
+  std::vector<int> cells = cell_list(sp, scat);
+  int max_cell = 0;
+  for (int v : cells) max_cell = std::max(max_cell, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
+  // tiles (v, w), v <= w, grouped into units of one test cell and up to 16 trial
+  // cells (or as many as fill the block of the float32 per-thread kernel)
+  const bool owner = bc_owner_width(sp, precision, max_cell, max_cell) > 0;
+  auto unit_of = [&](int v) {
+    if (!owner) return 16;
+    return bc_owner_width(sp, precision, std::max(1, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]), max_cell);
+  };
+  // {v, begin, count, flag} per unit; flag -1: per-pair class test; flag >= 0
+  // (class rules, per-thread kernel): every pair of the unit is far, and bit j
+  // of flag drops trial cell j (a cell pair left to a flag -1 unit)
+  std::vector<int> units;
+  std::vector<int> wlist;
+  std::vector<int2> tiles;
+  const bool split_far = owner && nreg == 0;
+  std::vector<CellBall> balls;
+  if (split_far) balls = cell_balls(sp, cells, (int)m.nv);
+  if (!dense) {
+    // tiles (v, w), v <= w, of the cell pairs that hold a kept entry (i, j):
+    // v and w end cells of i and j; per test cell a stamp array deduplicates
+    const int64_t off = op.row_offset;
+    std::vector<int> cell_rows_ptr(m.nv + 1, 0), cell_rows;
+    for (int64_t i = 0; i < op.rows; ++i) {
+      ++cell_rows_ptr[m.e_lo[off + i] + 1];
+      ++cell_rows_ptr[m.e_hi[off + i] + 1];
+    }
+    for (int64_t v = 0; v < m.nv; ++v) cell_rows_ptr[v + 1] += cell_rows_ptr[v];
+    cell_rows.resize(cell_rows_ptr[m.nv]);
+    {
+      std::vector<int> fill(cell_rows_ptr.begin(), cell_rows_ptr.end() - 1);
+      for (int64_t i = 0; i < op.rows; ++i) {
+        cell_rows[fill[m.e_lo[off + i]]++] = (int)i;
+        cell_rows[fill[m.e_hi[off + i]]++] = (int)i;
+      }
+    }
+    std::vector<int> stamp(m.nv, -1), ws;
+    for (int v : cells) {
+      ws.clear();
+      for (int r = cell_rows_ptr[v]; r < cell_rows_ptr[v + 1]; ++r) {
+        const int64_t i = cell_rows[r];
+        for (int64_t q = op.h_rowptr[i]; q < op.h_rowptr[i + 1]; ++q) {
+          const int64_t j = off + op.h_col[q];
+          for (int w : {m.e_lo[j], m.e_hi[j]})
+            if (w >= v && stamp[w] != v) {
+              stamp[w] = v;
+              ws.push_back(w);
+            }
+        }
+      }
+      std::sort(ws.begin(), ws.end());
+      // with class rules: the cell pairs that are not all far first
+      if (split_far)
+        std::stable_partition(ws.begin(), ws.end(), [&](int w) { return !cells_far(balls[v], balls[w]); });
+      for (int w : ws) tiles.push_back(make_int2(v, w));
+    }
+    wlist.resize(tiles.size());
+    for (size_t q = 0; q < tiles.size(); ++q) wlist[q] = tiles[q].y;
+    for (size_t q = 0; q < tiles.size();) {
+      size_t e = q;
+      const size_t unit = (size_t)unit_of(tiles[q].x);
+      const bool far = split_far && cells_far(balls[tiles[q].x], balls[tiles[q].y]);
+      while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < unit &&
+             (!split_far || cells_far(balls[tiles[e].x], balls[tiles[e].y]) == far))
+        ++e;
+      units.insert(units.end(), {tiles[q].x, (int)q, (int)(e - q), far ? 0 : -1});
+      q = e;
+    }
+  } else if (split_far) {
+    // all trial ranges are runs of cells; the cell pairs that are not all far
+    // also get units of their own, listed after the cells in wlist
+    spatial_order(cells, balls);
+    wlist = cells;
+    const int nc = (int)cells.size();
+    units.reserve((size_t)4 * nc * (nc / std::max(1, unit_of(cells[0])) + 4));
+    const std::vector<std::vector<int>> nearj = near_cells(cells, balls);
+    for (int i = 0; i < nc; ++i) {
+      const int unit = std::min(31, unit_of(cells[i]));  // the drop mask has 31 bits
+      const std::vector<int>& nj = nearj[i];
+      for (size_t q = 0; q < nj.size(); q += unit) {
+        const int cnt = (int)std::min<size_t>(unit, nj.size() - q);
+        units.insert(units.end(), {cells[i], (int)wlist.size(), cnt, -1});
+        for (int k = 0; k < cnt; ++k) wlist.push_back(cells[nj[q + k]]);
+      }
+      size_t p = 0;  // next entry of nj
+      for (int j0 = i; j0 < nc; j0 += unit) {
+        const int cnt = std::min(unit, nc - j0);
+        int mask = 0;
+        while (p < nj.size() && nj[p] < j0 + cnt) mask |= 1 << (nj[p++] - j0);
+        if (mask != (int)((1u << cnt) - 1)) units.insert(units.end(), {cells[i], j0, cnt, mask});
+      }
+    }
+  } else {
+    wlist = cells;
+    const int nc = (int)cells.size();
+    units.reserve((size_t)4 * nc * (nc / std::max(1, unit_of(cells[0])) + 2));
+    for (int i = 0; i < nc; ++i) {
+      const int unit = unit_of(cells[i]);
+      for (int j0 = i; j0 < nc; j0 += unit) units.insert(units.end(), {cells[i], j0, std::min(unit, nc - j0), -1});
+    }
+  }
+  L.nunits = (int64_t)units.size() / 4;
+  L.max_cell = max_cell;
+  if (L.nunits > 0) {
+    // pageable sources: the copies have read them when they return
+    CAL_TRY_CUDA(dalloc((void**)&L.d_units, units.size() * sizeof(int), st));
+    CAL_TRY_CUDA(dalloc((void**)&L.d_wlist, std::max<size_t>(wlist.size(), 1) * sizeof(int), st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(L.d_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CAL_TRY_CUDA(cudaMemcpyAsync(L.d_wlist, wlist.data(), wlist.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+  }
+  CAL_TRY_CUDA(cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming));
+  CAL_TRY_CUDA(cudaEventRecord(L.done, st));
+  // algorithmic work: cell-pair triangle pairs minus touching ones, times rule points squared
+  double pairs = 0.0;
+  if (dense) {
+    double s1 = 0, s2 = 0;
+    for (int v : cells) { const double n = sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]; s1 += n; s2 += n * n; }
+    pairs = 0.5 * (s1 * s1 + s2);
+  } else {
+    for (const int2& t : tiles)
+      pairs += (double)(sp.cell_tri_ptr[t.x + 1] - sp.cell_tri_ptr[t.x]) * (sp.cell_tri_ptr[t.y + 1] - sp.cell_tri_ptr[t.y]);
+  }
+  {
+    // dual cell of each small triangle of the listed cells
+    std::vector<int> tri_cell(sp.triD.size(), -1);
+    for (int v : cells)
+      for (int q = sp.cell_tri_ptr[v]; q < sp.cell_tri_ptr[v + 1]; ++q) tri_cell[sp.cell_tri[q]] = v;
+    const int d0 = scat < 0 ? 0 : scat, d1 = scat < 0 ? (int)sp.sing.size() : scat + 1;
+    for (int d = d0; d < d1; ++d)
+      for (const SingPair& q : sp.sing[d]) {
+        const double mult = q.cls == 1 ? 2.0 : 1.0;  // vertex pairs are listed once
+        pairs -= mult * (tri_cell[q.t1] == tri_cell[q.t2] ? 1.0 : 0.5);
+      }
+  }
+  L.pairs = pairs;
+  return CAL_OK;
+}
+
 // Assemble S and/or C of one block (scat = -1: union; else scatterer scat).
 int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, int scat, double chi,
                    int nreg, int nsing, int precision, std::unique_ptr<Op>& out) {
@@ -189,7 +336,23 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
   op->format = dense ? CAL_DENSE : CAL_CSR;
   if (!dense) {
     if (!(chi >= 0)) return fail(CAL_EINVAL, "assemble: near_cutoff must be >= 0 or INFINITY");
-    near_pattern(sp, scat, chi, op->h_rowptr, op->h_col);
+    {
+      // the pattern depends on the geometry and the cutoff only: built once per space
+      std::lock_guard<std::mutex> lk(sp.static_mu);
+      const Space::NearPattern* np = nullptr;
+      for (auto& q : sp.near_patterns)
+        if (q->scat == scat && q->chi == chi) np = q.get();
+      if (!np) {
+        auto q = std::make_unique<Space::NearPattern>();
+        q->scat = scat;
+        q->chi = chi;
+        near_pattern(sp, scat, chi, q->rowptr, q->col);
+        np = q.get();
+        sp.near_patterns.push_back(std::move(q));
+      }
+      op->h_rowptr = np->rowptr;
+      op->h_col = np->col;
+    }
     op->nnz = op->h_rowptr.back();
   } else {
     op->nnz = op->rows * op->cols;
@@ -237,144 +400,29 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
   if (sp.kind == CAL_RWG) {
     if ((rc = launch_rwg_regular(a))) return rc;
   } else {
-    std::vector<int> cells = cell_list(sp, scat);
-    int max_cell = 0;
-    for (int v : cells) max_cell = std::max(max_cell, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]);
-    // tiles (v, w), v <= w, grouped into units of one test cell and up to 16 trial
-    // cells (or as many as fill the block of the float32 per-thread kernel)
-    const bool owner = bc_owner_width(sp, precision, max_cell, max_cell) > 0;
-    auto unit_of = [&](int v) {
-      if (!owner) return 16;
-      return bc_owner_width(sp, precision, std::max(1, sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]), max_cell);
-    };
-    // {v, begin, count, flag} per unit; flag -1: per-pair class test; flag >= 0
-    // (class rules, per-thread kernel): every pair of the unit is far, and bit j
-    // of flag drops trial cell j (a cell pair left to a flag -1 unit)
-    std::vector<int> units;
-    std::vector<int> wlist;
-    std::vector<int2> tiles;
-    const bool split_far = owner && nreg == 0;
-    std::vector<CellBall> balls;
-    if (split_far) balls = cell_balls(sp, cells, (int)m.nv);
-    if (!dense) {
-      // tiles (v, w), v <= w, of the cell pairs that hold a kept entry (i, j):
-      // v and w end cells of i and j; per test cell a stamp array deduplicates
-      const int64_t off = op->row_offset;
-      std::vector<int> cell_rows_ptr(m.nv + 1, 0), cell_rows;
-      for (int64_t i = 0; i < op->rows; ++i) {
-        ++cell_rows_ptr[m.e_lo[off + i] + 1];
-        ++cell_rows_ptr[m.e_hi[off + i] + 1];
-      }
-      for (int64_t v = 0; v < m.nv; ++v) cell_rows_ptr[v + 1] += cell_rows_ptr[v];
-      cell_rows.resize(cell_rows_ptr[m.nv]);
-      {
-        std::vector<int> fill(cell_rows_ptr.begin(), cell_rows_ptr.end() - 1);
-        for (int64_t i = 0; i < op->rows; ++i) {
-          cell_rows[fill[m.e_lo[off + i]]++] = (int)i;
-          cell_rows[fill[m.e_hi[off + i]]++] = (int)i;
-        }
-      }
-      std::vector<int> stamp(m.nv, -1), ws;
-      for (int v : cells) {
-        ws.clear();
-        for (int r = cell_rows_ptr[v]; r < cell_rows_ptr[v + 1]; ++r) {
-          const int64_t i = cell_rows[r];
-          for (int64_t q = op->h_rowptr[i]; q < op->h_rowptr[i + 1]; ++q) {
-            const int64_t j = off + op->h_col[q];
-            for (int w : {m.e_lo[j], m.e_hi[j]})
-              if (w >= v && stamp[w] != v) {
-                stamp[w] = v;
-                ws.push_back(w);
-              }
-          }
-        }
-        std::sort(ws.begin(), ws.end());
-        // with class rules: the cell pairs that are not all far first
-        if (split_far)
-          std::stable_partition(ws.begin(), ws.end(), [&](int w) { return !cells_far(balls[v], balls[w]); });
-        for (int w : ws) tiles.push_back(make_int2(v, w));
-      }
-      wlist.resize(tiles.size());
-      for (size_t q = 0; q < tiles.size(); ++q) wlist[q] = tiles[q].y;
-      for (size_t q = 0; q < tiles.size();) {
-        size_t e = q;
-        const size_t unit = (size_t)unit_of(tiles[q].x);
-        const bool far = split_far && cells_far(balls[tiles[q].x], balls[tiles[q].y]);
-        while (e < tiles.size() && tiles[e].x == tiles[q].x && e - q < unit &&
-               (!split_far || cells_far(balls[tiles[e].x], balls[tiles[e].y]) == far))
-          ++e;
-        units.insert(units.end(), {tiles[q].x, (int)q, (int)(e - q), far ? 0 : -1});
-        q = e;
-      }
-    } else if (split_far) {
-      // all trial ranges are runs of cells; the cell pairs that are not all far
-      // also get units of their own, listed after the cells in wlist
-      spatial_order(cells, balls);
-      wlist = cells;
-      const int nc = (int)cells.size();
-      const std::vector<std::vector<int>> nearj = near_cells(cells, balls);
-      for (int i = 0; i < nc; ++i) {
-        const int unit = std::min(31, unit_of(cells[i]));  // the drop mask has 31 bits
-        const std::vector<int>& nj = nearj[i];
-        for (size_t q = 0; q < nj.size(); q += unit) {
-          const int cnt = (int)std::min<size_t>(unit, nj.size() - q);
-          units.insert(units.end(), {cells[i], (int)wlist.size(), cnt, -1});
-          for (int k = 0; k < cnt; ++k) wlist.push_back(cells[nj[q + k]]);
-        }
-        size_t p = 0;  // next entry of nj
-        for (int j0 = i; j0 < nc; j0 += unit) {
-          const int cnt = std::min(unit, nc - j0);
-          int mask = 0;
-          while (p < nj.size() && nj[p] < j0 + cnt) mask |= 1 << (nj[p++] - j0);
-          if (mask != (int)((1u << cnt) - 1)) units.insert(units.end(), {cells[i], j0, cnt, mask});
-        }
-      }
-    } else {
-      wlist = cells;
-      const int nc = (int)cells.size();
-      for (int i = 0; i < nc; ++i) {
-        const int unit = unit_of(cells[i]);
-        for (int j0 = i; j0 < nc; j0 += unit) units.insert(units.end(), {cells[i], j0, std::min(unit, nc - j0), -1});
-      }
-    }
-    const int64_t nunits = (int64_t)units.size() / 4;
-    int* d_units = nullptr;
-    int* d_wlist = nullptr;
-    if (nunits > 0) {
-      CAL_TRY_CUDA(cudaMallocAsync((void**)&d_units, units.size() * sizeof(int), st));
-      CAL_TRY_CUDA(cudaMallocAsync((void**)&d_wlist, std::max<size_t>(wlist.size(), 1) * sizeof(int), st));
-      CAL_TRY_CUDA(cudaMemcpyAsync(d_units, units.data(), units.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-      CAL_TRY_CUDA(cudaMemcpyAsync(d_wlist, wlist.data(), wlist.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    }
-    // algorithmic work: cell-pair triangle pairs minus touching ones, times rule points squared
-    double pairs = 0.0;
-    if (dense) {
-      double s1 = 0, s2 = 0;
-      for (int v : cells) { const double n = sp.cell_tri_ptr[v + 1] - sp.cell_tri_ptr[v]; s1 += n; s2 += n * n; }
-      pairs = 0.5 * (s1 * s1 + s2);
-    } else {
-      for (const int2& t : tiles)
-        pairs += (double)(sp.cell_tri_ptr[t.x + 1] - sp.cell_tri_ptr[t.x]) * (sp.cell_tri_ptr[t.y + 1] - sp.cell_tri_ptr[t.y]);
-    }
+    // the work units are the same for every wavenumber: built once per space
+    const bool fp32 = precision == CAL_FP32;
+    Space::UnitLists* L = nullptr;
     {
-      auto cell_of = [&](int tau) {
-        for (int q = 0; q < 3; ++q)
-          if (sp.triD[tau].vid[q] < m.nv) return sp.triD[tau].vid[q];
-        return -1;
-      };
-      const int d0 = scat < 0 ? 0 : scat, d1 = scat < 0 ? (int)sp.sing.size() : scat + 1;
-      for (int d = d0; d < d1; ++d)
-        for (const SingPair& q : sp.sing[d]) {
-          const double mult = q.cls == 1 ? 2.0 : 1.0;  // vertex pairs are listed once
-          pairs -= mult * (cell_of(q.t1) == cell_of(q.t2) ? 1.0 : 0.5);
-        }
+      std::lock_guard<std::mutex> lk(sp.static_mu);
+      for (auto& u : sp.unit_lists)
+        if (u->scat == scat && u->chi == chi && u->nreg == nreg && u->owner == fp32) L = u.get();
+      if (L) {
+        CAL_TRY_CUDA(cudaStreamWaitEvent(st, L->done, 0));
+      } else {
+        auto u = std::make_unique<Space::UnitLists>();
+        u->scat = scat;
+        u->chi = chi;
+        u->nreg = nreg;
+        u->owner = fp32;
+        if ((rc = build_units(sp, scat, dense, *op, precision, nreg, *u, st))) return rc;
+        L = u.get();
+        sp.unit_lists.push_back(std::move(u));
+      }
     }
-    if (nunits > 0)
-      rc = launch_bc_regular_units(a, d_units, nunits, d_wlist, max_cell, ctx.n_sm, pairs * nreg * nreg);
-    // the unit lists must outlive the kernel: free in stream order; the host
-    // vectors are read by the copies before this function returns (pageable)
-    if (d_units) cudaFreeAsync(d_units, st);
-    if (d_wlist) cudaFreeAsync(d_wlist, st);
+    if (L->nunits > 0)
+      rc = launch_bc_regular_units(a, L->d_units, L->nunits, L->d_wlist, L->max_cell, ctx.n_sm,
+                                   L->pairs * nreg * nreg);
     if (rc) return rc;
   }
   if ((rc = launch_singular(a))) return rc;

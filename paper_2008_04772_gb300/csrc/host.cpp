@@ -821,6 +821,11 @@ Space::~Space() {
     dfree(e.buf, nullptr);
     if (e.done) cudaEventDestroy(e.done);
   }
+  for (auto& u : unit_lists) {
+    dfree(u->d_units, nullptr);
+    dfree(u->d_wlist, nullptr);
+    if (u->done) cudaEventDestroy(u->done);
+  }
 }
 
 HMat::~HMat() {

@@ -11,6 +11,7 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <utility>
@@ -162,6 +163,31 @@ struct Space {
   };
   mutable std::mutex static_mu;
   mutable std::vector<StaticSums> sing_static;
+  // BC regular-pair work units (a test cell and a run of trial cells) of one
+  // scatterer, cutoff, rule and kernel: built and uploaded by the first
+  // assembly that asks, read by the later ones (a problem's exterior and
+  // interior blocks take the same lists); guarded by static_mu
+  struct UnitLists {
+    int scat = 0, nreg = 0;
+    double chi = 0;
+    bool owner = false;
+    int max_cell = 0;
+    int64_t nunits = 0;
+    double pairs = 0;  // regular triangle pairs (the work count)
+    int* d_units = nullptr;
+    int* d_wlist = nullptr;
+    cudaEvent_t done = nullptr;  // the uploads, recorded on the stream that made them
+  };
+  mutable std::vector<std::unique_ptr<UnitLists>> unit_lists;
+  // near-field patterns (CSR over the scatterer's edges) per (scatterer,
+  // cutoff); guarded by static_mu
+  struct NearPattern {
+    int scat = 0;
+    double chi = 0;
+    std::vector<int64_t> rowptr;
+    std::vector<int> col;
+  };
+  mutable std::vector<std::unique_ptr<NearPattern>> near_patterns;
   ~Space();
 };
 
