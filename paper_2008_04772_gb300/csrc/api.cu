@@ -8,6 +8,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -56,6 +57,29 @@ std::vector<int> cell_list(const Space& s, int scat) {
   for (int64_t v = 0; v < m.nv; ++v)
     if (used[v]) out.push_back((int)v);
   return out;
+}
+
+// f(i) for i in [0, n) on up to 16 host threads (chunks of 32 taken in turn);
+// f must only write what belongs to its own i
+template <class F>
+void parallel_for(int n, const F& f) {
+  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 16));
+  if (nt == 1 || n < 512) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (;;) {
+      const int i0 = next.fetch_add(32);
+      if (i0 >= n) return;
+      for (int i = i0; i < std::min(n, i0 + 32); ++i) f(i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto& x : th) x.join();
 }
 
 // Bounding ball of a dual cell for the class rules (Section 3.3): C the mean of
@@ -132,36 +156,59 @@ void spatial_order(std::vector<int>& cells, const std::vector<CellBall>& B) {
 }
 
 // per position i of cells, the positions j >= i whose cell pair is not all
-// far (sorted), found through a uniform grid of spacing twice the largest reach
+// far (sorted), found through a uniform grid of buckets: a pair that is not
+// all far is closer than R_v = rho_v + rho_max + 4 margin max(dm_v, dm_max),
+// so it lies within ceil(R_v / b) buckets per axis of bucket size b; a bucket
+// lists its cells in increasing position and is scanned from position i on
 std::vector<std::vector<int>> near_cells(const std::vector<int>& cells, const std::vector<CellBall>& B) {
   const int nc = (int)cells.size();
   std::vector<std::vector<int>> out(nc);
   if (nc == 0) return out;
-  double g = 0;
-  for (int v : cells) g = std::max(g, 2.0 * far_reach(B[v]));
-  g = std::max(g, 1e-300);
-  auto cell_key = [&](int v, int dx, int dy, int dz) {
-    const int64_t x = (int64_t)std::floor(B[v].c[0] / g) + dx, y = (int64_t)std::floor(B[v].c[1] / g) + dy,
-                  z = (int64_t)std::floor(B[v].c[2] / g) + dz;
-    return (uint64_t)((x & 0x1fffff) | (y & 0x1fffff) << 21 | (z & 0x1fffff) << 42);
-  };
-  std::vector<std::pair<uint64_t, int>> grid;
-  grid.reserve(nc);
-  for (int j = 0; j < nc; ++j) grid.push_back({cell_key(cells[j], 0, 0, 0), j});
-  std::sort(grid.begin(), grid.end());
-  for (int i = 0; i < nc; ++i) {
+  double rho_max = 0, dm_max = 0, lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+  for (int v : cells) {
+    rho_max = std::max(rho_max, B[v].rho);
+    dm_max = std::max(dm_max, B[v].dm);
+    for (int c = 0; c < 3; ++c) { lo[c] = std::min(lo[c], B[v].c[c]); hi[c] = std::max(hi[c], B[v].c[c]); }
+  }
+  auto reach = [&](const CellBall& a) { return a.rho + rho_max + 4.0 * FAR_MARGIN * std::max(a.dm, dm_max); };
+  const double g = 2.0 * rho_max + 4.0 * FAR_MARGIN * dm_max;  // the largest R_v
+  // bucket size g / 2, grown until there are at most 8 buckets per cell
+  double b = std::max(0.5 * g, 1e-300);
+  int64_t nb[3];
+  for (;;) {
+    for (int c = 0; c < 3; ++c) nb[c] = (int64_t)((hi[c] - lo[c]) / b) + 1;
+    if (nb[0] * nb[1] * nb[2] <= 8 * (int64_t)nc + 64) break;
+    b *= 1.5;
+  }
+  auto coord = [&](int v, int c) { return std::min<int64_t>(nb[c] - 1, (int64_t)((B[v].c[c] - lo[c]) / b)); };
+  const int64_t nbt = nb[0] * nb[1] * nb[2];
+  std::vector<int> start(nbt + 1, 0), ent(nc);
+  std::vector<int64_t> bid(nc);
+  for (int j = 0; j < nc; ++j) {
+    const int v = cells[j];
+    bid[j] = (coord(v, 2) * nb[1] + coord(v, 1)) * nb[0] + coord(v, 0);
+    ++start[bid[j] + 1];
+  }
+  for (int64_t q = 0; q < nbt; ++q) start[q + 1] += start[q];
+  {
+    std::vector<int> fill(start.begin(), start.end() - 1);
+    for (int j = 0; j < nc; ++j) ent[fill[bid[j]]++] = j;  // increasing j within a bucket
+  }
+  parallel_for(nc, [&](int i) {
     const int v = cells[i];
-    for (int dx = -1; dx <= 1; ++dx)
-      for (int dy = -1; dy <= 1; ++dy)
-        for (int dz = -1; dz <= 1; ++dz) {
-          const uint64_t k = cell_key(v, dx, dy, dz);
-          auto it = std::lower_bound(grid.begin(), grid.end(), std::make_pair(k, -1));
-          for (; it != grid.end() && it->first == k; ++it)
-            if (it->second >= i && !cells_far(B[v], B[cells[it->second]])) out[i].push_back(it->second);
+    const CellBall& bv = B[v];
+    const int64_t x0 = coord(v, 0), y0 = coord(v, 1), z0 = coord(v, 2);
+    const int r = (int)std::ceil(reach(bv) / b);
+    for (int64_t z = std::max<int64_t>(0, z0 - r); z <= std::min(nb[2] - 1, z0 + r); ++z)
+      for (int64_t y = std::max<int64_t>(0, y0 - r); y <= std::min(nb[1] - 1, y0 + r); ++y)
+        for (int64_t x = std::max<int64_t>(0, x0 - r); x <= std::min(nb[0] - 1, x0 + r); ++x) {
+          const int64_t q = (z * nb[1] + y) * nb[0] + x;
+          for (const int* e = std::lower_bound(ent.data() + start[q], ent.data() + start[q + 1], i);
+               e < ent.data() + start[q + 1]; ++e)
+            if (!cells_far(bv, B[cells[*e]])) out[i].push_back(*e);
         }
     std::sort(out[i].begin(), out[i].end());
-    out[i].erase(std::unique(out[i].begin(), out[i].end()), out[i].end());
-  }
+  });
   return out;
 }
 
@@ -248,24 +295,58 @@ int build_units(const Space& sp, int scat, bool dense, const Op& op, int precisi
     spatial_order(cells, balls);
     wlist = cells;
     const int nc = (int)cells.size();
-    units.reserve((size_t)4 * nc * (nc / std::max(1, unit_of(cells[0])) + 4));
     const std::vector<std::vector<int>> nearj = near_cells(cells, balls);
-    for (int i = 0; i < nc; ++i) {
+    // per test cell: its units (mixed first, then the runs with drop masks),
+    // counted, placed by prefix sums and written in parallel
+    std::vector<int64_t> uoff(nc + 1, 0), woff(nc + 1, 0);
+    auto far_mask = [&](const std::vector<int>& nj, size_t& p, int j0, int cnt) {
+      int mask = 0;
+      while (p < nj.size() && nj[p] < j0 + cnt) mask |= 1 << (nj[p++] - j0);
+      return mask;
+    };
+    parallel_for(nc, [&](int i) {
       const int unit = std::min(31, unit_of(cells[i]));  // the drop mask has 31 bits
       const std::vector<int>& nj = nearj[i];
-      for (size_t q = 0; q < nj.size(); q += unit) {
-        const int cnt = (int)std::min<size_t>(unit, nj.size() - q);
-        units.insert(units.end(), {cells[i], (int)wlist.size(), cnt, -1});
-        for (int k = 0; k < cnt; ++k) wlist.push_back(cells[nj[q + k]]);
-      }
-      size_t p = 0;  // next entry of nj
+      int64_t nu = (int64_t)((nj.size() + unit - 1) / unit);
+      size_t p = 0;
       for (int j0 = i; j0 < nc; j0 += unit) {
         const int cnt = std::min(unit, nc - j0);
-        int mask = 0;
-        while (p < nj.size() && nj[p] < j0 + cnt) mask |= 1 << (nj[p++] - j0);
-        if (mask != (int)((1u << cnt) - 1)) units.insert(units.end(), {cells[i], j0, cnt, mask});
+        if (far_mask(nj, p, j0, cnt) != (int)((1u << cnt) - 1)) ++nu;
       }
+      uoff[i + 1] = nu;
+      woff[i + 1] = (int64_t)nj.size();
+    });
+    for (int i = 0; i < nc; ++i) {
+      uoff[i + 1] += uoff[i];
+      woff[i + 1] += woff[i];
     }
+    units.resize((size_t)4 * uoff[nc]);
+    wlist.resize((size_t)nc + woff[nc]);
+    parallel_for(nc, [&](int i) {
+      const int unit = std::min(31, unit_of(cells[i]));
+      const std::vector<int>& nj = nearj[i];
+      int* u = units.data() + 4 * uoff[i];
+      int64_t w = nc + woff[i];
+      for (size_t q = 0; q < nj.size(); q += unit) {
+        const int cnt = (int)std::min<size_t>(unit, nj.size() - q);
+        *u++ = cells[i];
+        *u++ = (int)w;
+        *u++ = cnt;
+        *u++ = -1;
+        for (int k = 0; k < cnt; ++k) wlist[w++] = cells[nj[q + k]];
+      }
+      size_t p = 0;
+      for (int j0 = i; j0 < nc; j0 += unit) {
+        const int cnt = std::min(unit, nc - j0);
+        const int mask = far_mask(nj, p, j0, cnt);
+        if (mask != (int)((1u << cnt) - 1)) {
+          *u++ = cells[i];
+          *u++ = j0;
+          *u++ = cnt;
+          *u++ = mask;
+        }
+      }
+    });
   } else {
     wlist = cells;
     const int nc = (int)cells.size();
