@@ -59,29 +59,6 @@ std::vector<int> cell_list(const Space& s, int scat) {
   return out;
 }
 
-// f(i) for i in [0, n) on up to 16 host threads (chunks of 32 taken in turn);
-// f must only write what belongs to its own i
-template <class F>
-void parallel_for(int n, const F& f) {
-  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 16));
-  if (nt == 1 || n < 512) {
-    for (int i = 0; i < n; ++i) f(i);
-    return;
-  }
-  std::atomic<int> next(0);
-  auto work = [&]() {
-    for (;;) {
-      const int i0 = next.fetch_add(32);
-      if (i0 >= n) return;
-      for (int i = i0; i < std::min(n, i0 + 32); ++i) f(i);
-    }
-  };
-  std::vector<std::thread> th;
-  for (int t = 1; t < nt; ++t) th.emplace_back(work);
-  work();
-  for (auto& x : th) x.join();
-}
-
 // Bounding ball of a dual cell for the class rules (Section 3.3): C the mean of
 // its triangle centroids, rho the largest distance of one of them from C, dm
 // the longest edge of its triangles.

@@ -402,7 +402,7 @@ int build_bc(Space& s, Mesh& m) {
   s.triD.resize(s.ntri);
   s.parent.resize(s.ntri);
   std::vector<int> ids(3 * s.ntri);
-  for (int64_t t = 0; t < nt; ++t) {
+  parallel_for((int)nt, [&](int t) {
     int v0 = m.T[3 * t], v1 = m.T[3 * t + 1], v2 = m.T[3 * t + 2];
     // edges opposite local vertices: a=2 -> (v0,v1), a=0 -> (v1,v2), a=1 -> (v2,v0)
     int m01 = (int)nv + m.tri_edge[3 * t + 2];
@@ -417,7 +417,7 @@ int build_bc(Space& s, Mesh& m) {
                              sub[k][1], sub[k][2]);
       s.parent[tau] = (int)t;
     }
-  }
+  });
   // dual cells: barycentric triangles touching each primal vertex
   s.cell_tri_ptr.assign(nv + 1, 0);
   for (int64_t tau = 0; tau < s.ntri; ++tau)
@@ -445,25 +445,26 @@ int build_bc(Space& s, Mesh& m) {
   }
   s.slot_edge.assign((size_t)s.ntri * s.nslot, -1);
   s.slot_sw.assign((size_t)s.ntri * s.nslot * 4, 0.0);
-  for (int64_t tau = 0; tau < s.ntri; ++tau) {
+  parallel_for((int)s.ntri, [&](int tau) {
     int v = -1;
     for (int a = 0; a < 3; ++a)
       if (ids[3 * tau + a] < nv) v = ids[3 * tau + a];
     for (int q = s.cell_edge_ptr[v], sl = 0; q < s.cell_edge_ptr[v + 1]; ++q, ++sl)
       s.slot_edge[(size_t)tau * s.nslot + sl] = s.cell_edge[q];
-  }
+  });
   // BC_e on each dual cell: walk counter-clockwise around v from the spoke
   // (v, mid(e)); spoke j carries flux F_j = sgn l (j/2N - 1/2) (F_0 = 0), the
   // two triangles at mid(e) carry sgn l/2 through the dual edge, and every
   // small triangle gets divergence integral sgn l/(2N).
-  std::vector<std::pair<int, int>> succ;  // s -> (tau, s')
-  std::vector<int> succ_key;
-  for (int64_t v = 0; v < nv; ++v) {
+  // cells are independent (each writes the slots of its own triangles); the
+  // first cell that is not a closed fan is reported
+  std::atomic<int64_t> bad_fan(-1), bad_walk(-1);
+  parallel_for((int)nv, [&](int v) {
+    std::vector<std::pair<int, int>> succ;  // s -> (tau, s')
+    std::vector<int> succ_key;
     int b0 = s.cell_tri_ptr[v], b1 = s.cell_tri_ptr[v + 1];
     int twoN = b1 - b0;
-    if (twoN == 0) continue;
-    succ_key.clear();
-    succ.clear();
+    if (twoN == 0) return;
     for (int q = b0; q < b1; ++q) {
       int tau = s.cell_tri[q];
       int k = 0;
@@ -479,7 +480,11 @@ int build_bc(Space& s, Mesh& m) {
       int sp = (int)nv + e;
       for (int j = 0; j < twoN; ++j) {
         int pos = (int)(std::find(succ_key.begin(), succ_key.end(), sp) - succ_key.begin());
-        if (pos >= twoN) return fail(CAL_EMESH, "space_create(BC): dual cell of vertex %lld is not a closed fan", (long long)v);
+        if (pos >= twoN) {
+          int64_t none = -1;
+          bad_fan.compare_exchange_strong(none, v);
+          return;
+        }
         int tau = succ[pos].first, sn = succ[pos].second;
         double beta[3] = {0, 0, 0};
         for (int a = 0; a < 3; ++a) {
@@ -496,16 +501,25 @@ int build_bc(Space& s, Mesh& m) {
           sw[1 + c] = -(beta[0] * T.off[0][c] + beta[1] * T.off[1][c] + beta[2] * T.off[2][c]) / (2.0 * T.area);
         sp = sn;
       }
-      if (sp != (int)nv + e) return fail(CAL_EMESH, "space_create(BC): dual cell walk did not close at vertex %lld", (long long)v);
+      if (sp != (int)nv + e) {
+        int64_t none = -1;
+        bad_walk.compare_exchange_strong(none, v);
+        return;
+      }
     }
-  }
+  });
+  if (bad_fan >= 0)
+    return fail(CAL_EMESH, "space_create(BC): dual cell of vertex %lld is not a closed fan", (long long)bad_fan.load());
+  if (bad_walk >= 0)
+    return fail(CAL_EMESH, "space_create(BC): dual cell walk did not close at vertex %lld", (long long)bad_walk.load());
   // support boxes: union of both dual cells
   s.box_lo.assign(3 * ne, 1e300);
   s.box_hi.assign(3 * ne, -1e300);
-  for (int64_t e = 0; e < ne; ++e)
+  parallel_for((int)ne, [&](int e) {
     for (int v : {m.e_lo[e], m.e_hi[e]})
       for (int q = s.cell_tri_ptr[v]; q < s.cell_tri_ptr[v + 1]; ++q)
         for (int a = 0; a < 3; ++a) box_add(s.box_lo, s.box_hi, e, &Xb[3 * ids[3 * s.cell_tri[q] + a]]);
+  });
   s.tri_off.resize(m.M + 1);
   for (int64_t d = 0; d <= m.M; ++d) s.tri_off[d] = 6 * m.tri_off[d];
   build_singular_pairs(s);

@@ -9,6 +9,9 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+#include <thread>
 #include <cstdint>
 #include <map>
 #include <memory>
@@ -85,6 +88,29 @@ struct SingPair {
   signed char o1[3], o2[3];
   signed char pad;
 };
+
+// f(i) for i in [0, n) on up to 16 host threads (chunks of 32 taken in turn);
+// f must only write what belongs to its own i
+template <class F>
+inline void parallel_for(int n, const F& f) {
+  const int nt = std::max(1, std::min<int>((int)std::thread::hardware_concurrency(), 16));
+  if (nt == 1 || n < 512) {
+    for (int i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int> next(0);
+  auto work = [&]() {
+    for (;;) {
+      const int i0 = next.fetch_add(32);
+      if (i0 >= n) return;
+      for (int i = i0; i < std::min(n, i0 + 32); ++i) f(i);
+    }
+  };
+  std::vector<std::thread> th;
+  for (int t = 1; t < nt; ++t) th.emplace_back(work);
+  work();
+  for (auto& x : th) x.join();
+}
 
 // ---- host objects --------------------------------------------------------------
 struct Ctx {
