@@ -1376,6 +1376,244 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   count_add(cnt, evals);
 }
 
+// ---------------------------------------------------------------------------
+// A8, float32 operator and float32 vectors: the product of rwg_free_kernel
+// with the tile's 16 + 16 triangles staged in shared memory once (rule points
+// with the test weights folded in and the trial weights over 4 pi, centroids,
+// vertex ids, slots), and the moments, pair coefficients, entries and their
+// application on packed (re, im) float32 pairs (FFMA2 / FADD2 / FMUL2).
+// ---------------------------------------------------------------------------
+template <int NREG>
+__global__ void __launch_bounds__(256) rwg_free_f32_kernel(
+    const TriF* __restrict__ tri, const int* __restrict__ slot_edge, const float* __restrict__ slot_sw, int64_t t0,
+    int64_t ntr, float kr, float ki, float mikr, float miki, float c4r, float c4i, Rules rl,
+    const float2* __restrict__ x, float2* __restrict__ y, int64_t n, int nrhs, float ar, float ai, float br,
+    float bi, unsigned long long* cnt) {
+  constexpr int NS = staged_points<NREG>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  P4<float>* X = reinterpret_cast<P4<float>*>(smem_raw);  // [16][NS] test points (rows)
+  P4<float>* XW = X + 16 * NS;                             // [16][NS] w (x, y, z), w
+  P4<float>* Y = XW + 16 * NS;                             // [16][NS] trial points, w / 4 pi (columns)
+  P4<float>* SWR = Y + 16 * NS;                            // [16][3] row slots (sigma, w)
+  P4<float>* SWC = SWR + 48;                               // [16][3] column slots
+  Cent<float>* CR = reinterpret_cast<Cent<float>*>(SWC + 48);  // [16]
+  Cent<float>* CC = CR + 16;                                   // [16]
+  int* VR = reinterpret_cast<int*>(CC + 16);                   // [16][3]
+  int* VC = VR + 48;                                           // [16][3]
+  int* ER = VC + 48;                                           // [16][3] row slot edges
+  int* EC = ER + 48;                                           // [16][3]
+  float* acc = reinterpret_cast<float*>(EC + 48);              // as rwg_free_kernel
+  const int tbi = blockIdx.y, tbj = blockIdx.x;
+  if (tbi > tbj) return;  // the whole block: the tile lies below the diagonal
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+  const int nacc = 2 * 16 * 3 * 2 * nrhs * 2;
+  for (int q = tid; q < nacc; q += 256) acc[q] = 0.f;
+  // staging: side 0 = rows (tbi), 1 = columns (tbj)
+  for (int q = tid; q < 2 * 16 * NS; q += 256) {
+    const int side = q / (16 * NS), rest = q - side * 16 * NS, t = rest / NS, u = rest - t * NS;
+    const int64_t it = (int64_t)(side == 0 ? tbi : tbj) * 16 + t;
+    if (it >= ntr) continue;
+    const TriF T = tri[t0 + it];
+    const P4<float> p = staged_point(T, rl, u);
+    if (side == 0) {
+      X[t * NS + u] = p;
+      XW[t * NS + u] = {p.w * p.x, p.w * p.y, p.w * p.z, p.w};
+    } else {
+      Y[t * NS + u] = {p.x, p.y, p.z, p.w * INV_4PI_F};
+    }
+    if (u == 0) {
+      (side == 0 ? CR : CC)[t].set(T);
+      int* v = (side == 0 ? VR : VC) + 3 * t;
+      int* e = (side == 0 ? ER : EC) + 3 * t;
+      P4<float>* w = (side == 0 ? SWR : SWC) + 3 * t;
+      for (int a = 0; a < 3; ++a) {
+        v[a] = T.vid[a];
+        e[a] = slot_edge[3 * (t0 + it) + a];
+        w[a] = reinterpret_cast<const P4<float>*>(slot_sw)[3 * (t0 + it) + a];
+      }
+    }
+  }
+  __syncthreads();
+  const int64_t i1 = (int64_t)tbi * 16 + ty, i2 = (int64_t)tbj * 16 + tx;
+  bool active = i1 < ntr && i2 < ntr && i1 < i2;
+  const float2 z0 = make_float2(0.f, 0.f);
+  float2 S[9], C[9];  // entries (a, b) of the pair, complex
+#pragma unroll
+  for (int q = 0; q < 9; ++q) S[q] = C[q] = z0;
+  if (active) {
+    const int* va = VR + 3 * ty;
+    const int* vb = VC + 3 * tx;
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+      for (int b = 0; b < 3; ++b) active &= va[a] != vb[b];
+  }
+  if (active) {
+    const Cent<float> ca = CR[ty], cb = CC[tx];
+    const V3<float> D = ca.minus(cb);
+    const P4<float>* Xa = X + ty * NS;
+    const P4<float>* XWa = XW + ty * NS;
+    const P4<float>* Yb = Y + tx * NS;
+    Mom2 m;
+    unsigned ev;
+    if constexpr (NREG > 0) {
+      owner_moments<NREG, true, true>(Xa, XWa, Yb, D, kr, ki, true, m);
+      ev = NREG * NREG;
+    } else {
+      const int c = pair_class<float>(D, ca.d, cb.d);
+      if (c == 2) {
+        owner_moments<3, true, true>(Xa + RULE_OFF_FAR, XWa + RULE_OFF_FAR, Yb + RULE_OFF_FAR, D, kr, ki, true, m);
+        ev = 9;
+      } else if (c == 1) {
+        owner_moments<4, true, true>(Xa + RULE_OFF_MEDIUM, XWa + RULE_OFF_MEDIUM, Yb + RULE_OFF_MEDIUM, D, kr, ki,
+                                     true, m);
+        ev = 16;
+      } else {
+        owner_moments<6, true, true>(Xa, XWa, Yb, D, kr, ki, true, m);
+        ev = 36;
+      }
+    }
+    count_add(cnt, ev * (unsigned)nrhs);
+    PairC2 pc;
+    pair_c_coeffs(m, D, pc);
+    // S_ab = -ik [s_a s_b Gxy + s_a w_b.Gx + s_b w_a.Gy + w_a.w_b G0] + c4 s_a s_b G0
+    // C_ab = s_a s_b D.gxy + s_a w_b.X1 + s_b w_a.X2 + (w_a x w_b).V, X2 = -Y2
+    const float2 c4G0 = make_float2(c4r * m.G0.x - c4i * m.G0.y, c4r * m.G0.y + c4i * m.G0.x);
+    float2 wbGx[3], wbX1[3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const P4<float> u = SWC[3 * tx + b];
+      wbGx[b] = fma2(dup2(u.w), m.Gx[2], fma2(dup2(u.z), m.Gx[1], mul2(dup2(u.y), m.Gx[0])));
+      wbX1[b] = fma2(dup2(u.w), pc.X1[2], fma2(dup2(u.z), pc.X1[1], mul2(dup2(u.y), pc.X1[0])));
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const P4<float> ua = SWR[3 * ty + a];
+      const float2 waGy = fma2(dup2(ua.w), m.Gy[2], fma2(dup2(ua.z), m.Gy[1], mul2(dup2(ua.y), m.Gy[0])));
+      const float2 waY2 = fma2(dup2(ua.w), pc.Y2[2], fma2(dup2(ua.z), pc.Y2[1], mul2(dup2(ua.y), pc.Y2[0])));
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const P4<float> ub = SWC[3 * tx + b];
+        const float ss = ua.x * ub.x;
+        const float ww = ua.y * ub.y + ua.z * ub.z + ua.w * ub.w;
+        const float2 B = fma2(dup2(ss), m.Gxy, fma2(dup2(ua.x), wbGx[b], fma2(dup2(ub.x), waGy, mul2(dup2(ww), m.G0))));
+        S[3 * a + b] = make_float2(mikr * B.x - miki * B.y + ss * c4G0.x, mikr * B.y + miki * B.x + ss * c4G0.y);
+        const float cx = ua.z * ub.w - ua.w * ub.z, cy = ua.w * ub.y - ua.y * ub.w, cz = ua.y * ub.z - ua.z * ub.y;
+        const float2 VW = fma2(dup2(cz), pc.V[2], fma2(dup2(cy), pc.V[1], mul2(dup2(cx), pc.V[0])));
+        C[3 * a + b] = fma2(dup2(ss), pc.Dgxy, fma2(dup2(ua.x), wbX1[b], fma2(dup2(-ub.x), waY2, VW)));
+      }
+    }
+  }
+  int ea[3], eb[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    ea[a] = ER[3 * ty + a];
+    eb[a] = EC[3 * tx + a];
+  }
+  // complex product e v accumulated into acc: (er v + ei (-v.y, v.x))
+  auto cmac = [](float2 e, float2 v, float2 vs, float2 a) { return fma2(dup2(e.y), vs, fma2(dup2(e.x), v, a)); };
+  for (int r = 0; r < nrhs; ++r) {
+    const float2* x1 = x + (int64_t)r * 2 * n;
+    const float2* x2 = x1 + n;
+    float2 u1[3], u2[3], v1[3], v2[3], u1s[3], u2s[3], v1s[3], v2s[3];  // x at t1 (u) and t2 (v); swapped
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      u1[a] = u2[a] = v1[a] = v2[a] = z0;
+      if (active) {
+        u1[a] = x1[ea[a]];
+        u2[a] = x2[ea[a]];
+        v1[a] = x1[eb[a]];
+        v2[a] = x2[eb[a]];
+      }
+      u1s[a] = make_float2(-u1[a].y, u1[a].x);
+      u2s[a] = make_float2(-u2[a].y, u2[a].x);
+      v1s[a] = make_float2(-v1[a].y, v1[a].x);
+      v2s[a] = make_float2(-v2[a].y, v2[a].x);
+    }
+    float row[12], col[12];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      float2 c1 = z0, c2 = z0, s1 = z0, s2 = z0;
+#pragma unroll
+      for (int b = 0; b < 3; ++b) {
+        const int k = 3 * a + b;
+        c1 = cmac(C[k], v1[b], v1s[b], c1);
+        c2 = cmac(C[k], v2[b], v2s[b], c2);
+        s1 = cmac(S[k], v1[b], v1s[b], s1);
+        s2 = cmac(S[k], v2[b], v2s[b], s2);
+      }
+      row[4 * a + 0] = c1.x + ar * s2.x - ai * s2.y;
+      row[4 * a + 1] = c1.y + ar * s2.y + ai * s2.x;
+      row[4 * a + 2] = c2.x + br * s1.x - bi * s1.y;
+      row[4 * a + 3] = c2.y + br * s1.y + bi * s1.x;
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      float2 c1 = z0, c2 = z0, s1 = z0, s2 = z0;
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int k = 3 * a + b;
+        c1 = cmac(C[k], u1[a], u1s[a], c1);
+        c2 = cmac(C[k], u2[a], u2s[a], c2);
+        s1 = cmac(S[k], u1[a], u1s[a], s1);
+        s2 = cmac(S[k], u2[a], u2s[a], s2);
+      }
+      col[4 * b + 0] = c1.x + ar * s2.x - ai * s2.y;
+      col[4 * b + 1] = c1.y + ar * s2.y + ai * s2.x;
+      col[4 * b + 2] = c2.x + br * s1.x - bi * s1.y;
+      col[4 * b + 3] = c2.y + br * s1.y + bi * s1.x;
+    }
+    // rows share t1 across the 16 lanes of a half warp; columns share t2
+    // across the two half warps
+#pragma unroll
+    for (int q = 0; q < 12; ++q) {
+      float v = row[q];
+#pragma unroll
+      for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      row[q] = v;
+      col[q] += __shfl_xor_sync(0xffffffffu, col[q], 16);
+    }
+    if (tx == 0) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float* o = acc + ((((0 * 16 + ty) * 3 + a) * 2 + h) * nrhs + r) * 2;
+          o[0] += row[4 * a + 2 * h];
+          o[1] += row[4 * a + 2 * h + 1];
+        }
+    }
+    if ((ty & 1) == 0) {
+#pragma unroll
+      for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float* o = acc + ((((1 * 16 + tx) * 3 + b) * 2 + h) * nrhs + r) * 2;
+          atomicAdd(o, col[4 * b + 2 * h]);
+          atomicAdd(o + 1, col[4 * b + 2 * h + 1]);
+        }
+    }
+  }
+  __syncthreads();
+  // flush: one atomic per (side, triangle, slot, half, rhs)
+  for (int q = tid; q < nacc / 2; q += 256) {
+    const int r = q % nrhs;
+    int rest = q / nrhs;
+    const int h = rest % 2;
+    rest /= 2;
+    const int slot = rest % 3;
+    rest /= 3;
+    const int t = rest % 16, side = rest / 16;
+    const int64_t tt = (int64_t)(side == 0 ? tbi : tbj) * 16 + t;
+    if (tt >= ntr) continue;
+    const float vr = acc[2 * q], vi = acc[2 * q + 1];
+    if (vr == 0.f && vi == 0.f) continue;
+    const int e = (side == 0 ? ER : EC)[3 * t + slot];
+    if (e < 0) continue;
+    atomicAdd(y + (int64_t)r * 2 * n + (int64_t)h * n + e, make_float2(vr, vi));
+  }
+}
+
 constexpr int BC_OWNER_TT = 128;
 
 // trial cells per unit for the one-thread-per-(test triangle, trial cell)
@@ -2614,6 +2852,29 @@ static int rwg_free_t(const Space& s, int scat, double kr, double ki, int nreg, 
     for (const SingPair& q : s.sing[d]) nsing += q.cls == 1 ? 2 : 1;
   const double units = ((double)ntr * (ntr - 1) / 2 - (double)(nsing - ntr) / 2) * nreg * nreg;
   dim3 grid((unsigned)nb, (unsigned)nb), block(16, 16);
+  if constexpr (sizeof(R) == 4 && sizeof(VT) == 8) {
+    // float32 vectors: the staged, packed-pair kernel
+    constexpr int NSP = RULE_POINTS_ALL;  // the largest staging (class rules)
+    for (int r0 = 0; r0 < nrhs; r0 += 32) {
+      const int nr = std::min(32, nrhs - r0);
+      const int nsp = nreg > 0 ? nreg : NSP;
+      const int smem = 3 * 16 * nsp * (int)sizeof(P4<float>) + 2 * 48 * (int)sizeof(P4<float>) +
+                       32 * (int)sizeof(Cent<float>) + 4 * 48 * (int)sizeof(int) + 2 * 16 * 3 * 2 * nr * 2 * 4;
+      auto kern = nreg == 6 ? rwg_free_f32_kernel<6> : (nreg == 1 ? rwg_free_f32_kernel<1> : rwg_free_f32_kernel<0>);
+      if (int rc = ensure_dyn_smem((const void*)kern, smem)) return rc;
+      const int tok = prof_begin(st, "rwg_free", units * nr);
+      unsigned long long* cnt = nreg == 0 ? prof_counter(tok, st) : nullptr;
+      kern<<<grid, block, smem, st>>>(tri, s.d_slot_edge, sw, t0, ntr, (float)kr, (float)ki, (float)mikr,
+                                      (float)miki, (float)c4r, (float)c4i, g_rules,
+                                      reinterpret_cast<const float2*>(x) + (int64_t)r0 * 2 * n,
+                                      reinterpret_cast<float2*>(y) + (int64_t)r0 * 2 * n, n, nr, (float)ar,
+                                      (float)ai, (float)br, (float)bi, cnt);
+      prof_end(st, tok);
+      note_launch();
+      CAL_TRY_CUDA(cudaGetLastError());
+    }
+    return CAL_OK;
+  }
   for (int r0 = 0; r0 < nrhs; r0 += 32) {
     const int nr = std::min(32, nrhs - r0);
     const int smem = 2 * 16 * 3 * 2 * nr * 2 * (int)sizeof(AT);
