@@ -2191,6 +2191,7 @@ int cal_near_field(const cal_solution* sol, const double* points, int64_t npt, i
   f.mu_e = sol->mu_e;
   f.k_m = sol->k_m;
   f.mu_m = sol->mu_m;
+  f.n_sm = sol->ctx->n_sm;
   int rc = launch_near_field(f, reg, st);
   if (rc) return rc;
   CAL_TRY_CUDA(cudaMemcpyAsync(out, d_out, out_bytes, cudaMemcpyDeviceToHost, st));

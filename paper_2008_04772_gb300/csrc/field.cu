@@ -154,11 +154,14 @@ constexpr int FIELD_THREADS = 128;
 // out = sgn [H_k(u_1) + scale E_k(u_2)] (+ E^inc at k_e when add_inc)
 template <typename AT>
 __global__ void __launch_bounds__(FIELD_THREADS) field_eval_kernel(
-    const Src<AT>* __restrict__ src, int64_t nsrc_total, int64_t s0, int64_t s1, const int* __restrict__ idx,
-    int64_t np, const double* __restrict__ pts, double kr, double ki, double sgn, double scr, double sci, int add_inc,
-    double ke, const double* __restrict__ inc, double2* __restrict__ out, int64_t npt_total) {
+    const Src<AT>* __restrict__ src, int64_t nsrc_total, int64_t s0, int64_t s1, int64_t chunk,
+    const int* __restrict__ idx, int64_t np, const double* __restrict__ pts, double kr, double ki,
+    AT* __restrict__ part) {
   __shared__ Src<AT> tile[FIELD_THREADS];
   const int q = blockIdx.y;
+  // this block's chunk of the source points (blockIdx.z of the split)
+  const int64_t a0 = s0 + (int64_t)blockIdx.z * chunk;
+  const int64_t a1 = a0 + chunk < s1 ? a0 + chunk : s1;
   const int64_t p = (int64_t)blockIdx.x * FIELD_THREADS + threadIdx.x;
   const bool live = p < np;
   const int i = live ? idx[p] : 0;
@@ -168,8 +171,8 @@ __global__ void __launch_bounds__(FIELD_THREADS) field_eval_kernel(
   // S1 = sum w G u_2, S2 = sum w g div u_2 (x - y), H = sum w g (x - y) x u_1
   AT S1[6] = {}, S2[6] = {}, H[6] = {};
   const Src<AT>* sq = src + (size_t)q * nsrc_total;
-  for (int64_t b0 = s0; b0 < s1; b0 += FIELD_THREADS) {
-    const int nb = (int)(s1 - b0 < FIELD_THREADS ? s1 - b0 : FIELD_THREADS);
+  for (int64_t b0 = a0; b0 < a1; b0 += FIELD_THREADS) {
+    const int nb = (int)(a1 - b0 < FIELD_THREADS ? a1 - b0 : FIELD_THREADS);
     __syncthreads();
     if (threadIdx.x < nb) tile[threadIdx.x] = sq[b0 + threadIdx.x];
     __syncthreads();
@@ -206,11 +209,42 @@ __global__ void __launch_bounds__(FIELD_THREADS) field_eval_kernel(
     }
   }
   if (!live) return;
-  // E_k(u_2) = ik S1 - (1/(ik)) S2 in float64; ik = i kr - ki
+  // partial sums of this chunk: part[((split * nrhs + q) * np + p) * 18 + k]
+  AT* o = part + (((size_t)blockIdx.z * gridDim.y + q) * np + p) * 18;
+#pragma unroll
+  for (int k = 0; k < 6; ++k) {
+    o[k] = S1[k];
+    o[6 + k] = S2[k];
+    o[12 + k] = H[k];
+  }
+}
+
+// the field at each point of a region from the chunks' partial sums (added in
+// float64): E_k(u_2) = ik S1 - (1/(ik)) S2, then the representation's sign,
+// scale and, outside, the incident field
+template <typename AT>
+__global__ void field_finish_kernel(const AT* __restrict__ part, int nsplit, int nrhs, const int* __restrict__ idx,
+                                    int64_t np, const double* __restrict__ pts, double kr, double ki, double sgn,
+                                    double scr, double sci, int add_inc, double ke, const double* __restrict__ inc,
+                                    double2* __restrict__ out, int64_t npt_total) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int q = blockIdx.y;
+  if (p >= np) return;
+  const int i = idx[p];
+  double S[18];
+  for (int k = 0; k < 18; ++k) S[k] = 0.0;
+  for (int c = 0; c < nsplit; ++c) {
+    const AT* o = part + (((size_t)c * nrhs + q) * np + p) * 18;
+    for (int k = 0; k < 18; ++k) S[k] += (double)o[k];
+  }
+  const double* S1 = S;
+  const double* S2 = S + 6;
+  const double* H = S + 12;
+  // E_k(u_2) = ik S1 - (1/(ik)) S2; ik = i kr - ki
   const double ikr = -ki, iki = kr;
   const double den = ikr * ikr + iki * iki;
   const double jr = ikr / den, ji = -iki / den;  // 1/(ik)
-  double2* o = out + ((size_t)q * npt_total + i) * 3;
+  double2* ot = out + ((size_t)q * npt_total + i) * 3;
   double einc[3][2] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
   if (add_inc) {
     const double* dq = inc + 6 * q;
@@ -223,13 +257,13 @@ __global__ void __launch_bounds__(FIELD_THREADS) field_eval_kernel(
     }
   }
   for (int cc = 0; cc < 3; ++cc) {
-    const double s1r = (double)S1[2 * cc], s1i = (double)S1[2 * cc + 1];
-    const double s2r = (double)S2[2 * cc], s2i = (double)S2[2 * cc + 1];
+    const double s1r = S1[2 * cc], s1i = S1[2 * cc + 1];
+    const double s2r = S2[2 * cc], s2i = S2[2 * cc + 1];
     const double er = (ikr * s1r - iki * s1i) - (jr * s2r - ji * s2i);
     const double ei = (ikr * s1i + iki * s1r) - (jr * s2i + ji * s2r);
-    const double tr = (double)H[2 * cc] + (scr * er - sci * ei);
-    const double ti = (double)H[2 * cc + 1] + (scr * ei + sci * er);
-    o[cc] = make_double2(einc[cc][0] + sgn * tr, einc[cc][1] + sgn * ti);
+    const double tr = H[2 * cc] + (scr * er - sci * ei);
+    const double ti = H[2 * cc + 1] + (scr * ei + sci * er);
+    ot[cc] = make_double2(einc[cc][0] + sgn * tr, einc[cc][1] + sgn * ti);
   }
 }
 
@@ -329,10 +363,30 @@ int near_field_t(const FieldArgs& f, const std::vector<int>& reg_h, cudaStream_t
       s1 = sp.tri_off[r + 1] * Q;
     }
     const double sgn = r < 0 ? -1.0 : 1.0;
-    field_eval_kernel<AT><<<dim3(blocks_of(np, FIELD_THREADS), f.nrhs), FIELD_THREADS, 0, st>>>(
-        d_src, nsrc, s0, s1, d_idx + start[r + 1], np, f.d_pts, k.real(), k.imag(), sgn, scale.real(),
+    // the sources are split into chunks so that the grid fills the GPU (a
+    // region may hold only a few thousand points): about 8 blocks per SM,
+    // each chunk at least 8 tiles of sources, the partial sums within 256 MB
+    const int64_t tiles = (int64_t)blocks_of(np, FIELD_THREADS) * f.nrhs;
+    const int64_t ns = s1 - s0;
+    int64_t nsplit = std::max<int64_t>(1, (8LL * std::max(1, f.n_sm) + tiles - 1) / tiles);
+    nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, ns / (8 * FIELD_THREADS)));
+    nsplit = std::min<int64_t>(nsplit, std::max<int64_t>(1, (256LL << 20) / ((int64_t)f.nrhs * np * 18 * sizeof(AT))));
+    nsplit = std::min<int64_t>(nsplit, 65535);
+    const int64_t chunk = (ns + nsplit - 1) / nsplit;
+    AT* d_part = nullptr;
+    if (dalloc((void**)&d_part, (size_t)nsplit * f.nrhs * np * 18 * sizeof(AT), st) != cudaSuccess) {
+      prof_end(st, tok);
+      cleanup();
+      return fail(CAL_ENOMEM, "near field: cannot allocate the partial sums");
+    }
+    field_eval_kernel<AT><<<dim3(blocks_of(np, FIELD_THREADS), f.nrhs, (unsigned)nsplit), FIELD_THREADS, 0, st>>>(
+        d_src, nsrc, s0, s1, chunk, d_idx + start[r + 1], np, f.d_pts, k.real(), k.imag(), d_part);
+    note_launch();
+    field_finish_kernel<AT><<<dim3(blocks_of(np, 128), f.nrhs), 128, 0, st>>>(
+        d_part, (int)nsplit, f.nrhs, d_idx + start[r + 1], np, f.d_pts, k.real(), k.imag(), sgn, scale.real(),
         scale.imag(), r < 0 ? 1 : 0, f.k_e, f.d_inc, f.d_out, f.npt);
     note_launch();
+    dfree(d_part, st);
   }
   prof_end(st, tok);
   cudaError_t e = cudaGetLastError();

@@ -151,6 +151,7 @@ int hmat_expand(const HMat& h, int which, void* dst, cudaStream_t st);
 struct FieldArgs {
   const Space* rwg = nullptr;
   int M = 1, levels = 2, precision = CAL_FP64, nrhs = 1;
+  int n_sm = 0;                   // SMs of the device (grid sizing)
   const double2* x = nullptr;     // [nrhs][2N] coefficients (c, d)
   const double2* xinc = nullptr;  // optional [nrhs][2N] added to x (total traces)
   const double* d_pts = nullptr;  // [npt][3]
@@ -165,7 +166,7 @@ int launch_regions(const Space& rwg, int M, const double* d_pts, int64_t npt, in
 int launch_near_field(const FieldArgs& f, const std::vector<int>& region, cudaStream_t st);
 
 // BC tile launcher (assemble.cu)
-// A5 over units: units [nunits] of {v, begin, count, pad} ints, each a test
+// A5 over units: units [nunits] of {v, begin, count, flag} ints, each a test
 // cell v with the trial cells wlist[begin .. begin + count)
 int launch_bc_regular_units(const AssembleArgs& a, const void* units, int64_t nunits, const int* wlist, int max_cell,
                             int n_sm, double work);
