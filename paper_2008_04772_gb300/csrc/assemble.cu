@@ -1137,8 +1137,78 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Tensor memory as per-thread scratch rows (tcgen05): in a CTA of 128
+// threads, warp w may reach TMEM lanes 32w .. 32w + 31, so thread t owns lane
+// t; a load or store moves 16 or 32 consecutive 32-bit columns of that lane.
+// These are warp-collective (.sync.aligned): every lane of the warp executes
+// them together. tcgen05.ld results are valid after tm_wait_ld; a load of
+// columns written by tcgen05.st sees them after tm_wait_st.
+__device__ __forceinline__ uint32_t tm_lane_addr(uint32_t base) {
+  return base + ((uint32_t)(threadIdx.x & ~31u) << 16);
+}
+__device__ __forceinline__ void tm_ld16(uint32_t ta, float* v) {
+  uint32_t u[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15])
+               : "r"(ta));
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(u[i]);
+}
+__device__ __forceinline__ void tm_ld32(uint32_t ta, float* v) {
+  uint32_t u[32];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+               : "=r"(u[0]), "=r"(u[1]), "=r"(u[2]), "=r"(u[3]), "=r"(u[4]), "=r"(u[5]), "=r"(u[6]), "=r"(u[7]), "=r"(u[8]), "=r"(u[9]), "=r"(u[10]), "=r"(u[11]), "=r"(u[12]), "=r"(u[13]), "=r"(u[14]), "=r"(u[15]), "=r"(u[16]), "=r"(u[17]), "=r"(u[18]), "=r"(u[19]), "=r"(u[20]), "=r"(u[21]), "=r"(u[22]), "=r"(u[23]), "=r"(u[24]), "=r"(u[25]), "=r"(u[26]), "=r"(u[27]), "=r"(u[28]), "=r"(u[29]), "=r"(u[30]), "=r"(u[31])
+               : "r"(ta));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(u[i]);
+}
+__device__ __forceinline__ void tm_st16(uint32_t ta, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+               :: "r"(ta), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15]))
+               : "memory");
+}
+__device__ __forceinline__ void tm_st32(uint32_t ta, const float* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};"
+               :: "r"(ta), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31]))
+               : "memory");
+}
+__device__ __forceinline__ void tm_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tm_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+constexpr int BC_OWN_TMEM_COLS = 128;  // tensor-memory columns per CTA (96 used: six slots x 16)
+
+// bytes of the shared region that holds the staged trial records and test
+// points, then the per-thread records (16-byte multiple)
+__host__ __device__ inline size_t owner_region_bytes(int tt, int rw, int ns, int max_cell) {
+  const size_t staging = (size_t)BC_OWN_STAGE * rw * 16 + 2 * (size_t)max_cell * ns * 16;
+  const size_t records = (size_t)tt * BC_OWN_SLOTS * BC_OWN_REC * sizeof(float);
+  return staging > records ? staging : records;
+}
+
+// the w_b terms of one pair for one trial slot, added to its 8 complex sums
+// f[0..16): S: AS = w_b . Gx, WS = w_b G0; C: AC = w_b . X1, WC = w_b x V
+__device__ __forceinline__ void owner_slot_update(float* f, float2 bx, float2 by, float2 bz, const Mom2& m,
+                                                  const PairC2& pc) {
+  float2 o[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) o[k] = make_float2(f[2 * k], f[2 * k + 1]);
+  o[0] = fma2(bz, m.Gx[2], fma2(by, m.Gx[1], fma2(bx, m.Gx[0], o[0])));
+  o[1] = fma2(bx, m.G0, o[1]);
+  o[2] = fma2(by, m.G0, o[2]);
+  o[3] = fma2(bz, m.G0, o[3]);
+  o[4] = fma2(bz, pc.X1[2], fma2(by, pc.X1[1], fma2(bx, pc.X1[0], o[4])));
+  o[5] = fma2(by, pc.V[2], fma2(bz, pc.nV[1], o[5]));
+  o[6] = fma2(bz, pc.V[0], fma2(bx, pc.nV[2], o[6]));
+  o[7] = fma2(bx, pc.V[1], fma2(by, pc.nV[0], o[7]));
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    f[2 * k] = o[k].x;
+    f[2 * k + 1] = o[k].y;
+  }
+}
+
 template <int NREG, int TT, bool BOTH>
-__global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
+__global__ void __launch_bounds__(TT, 3) bc_owner_kernel(
     CellData<float> cd, int nslot, const int* __restrict__ cell_ptr, const int* __restrict__ cell_edge_ptr,
     const int* __restrict__ cell_edge, const BcUnit* __restrict__ units, int64_t nunits,
     const int* __restrict__ wlist, const float4* __restrict__ trec, const float* __restrict__ cell_slot_s, float kr,
@@ -1148,11 +1218,14 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   constexpr int NSL = BC_OWN_SLOTS;
   constexpr int NP = owner_trial_pts<NREG>(), RW = owner_rec_words<NREG>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float* rec = reinterpret_cast<float*>(smem_raw);                                  // [TT][NSL][BC_OWN_REC]
-  float4* trial = reinterpret_cast<float4*>(rec + (size_t)TT * NSL * BC_OWN_REC);   // [BC_OWN_STAGE][RW]
+  // one region holds the staged trial records and test points during the pair
+  // loop, and the per-thread records after it (a barrier in between)
+  float4* trial = reinterpret_cast<float4*>(smem_raw);                             // [BC_OWN_STAGE][RW]
   P4<float>* ptsA = reinterpret_cast<P4<float>*>(trial + (size_t)BC_OWN_STAGE * RW);  // [max_cell][NS]
   P4<float>* ptsW = ptsA + (size_t)max_cell * NS;                                   // [max_cell][NS] w (x, y, z), w
-  P4<float>* swA = ptsW + (size_t)max_cell * NS;                                    // [max_cell][nslot]
+  float* rec = reinterpret_cast<float*>(smem_raw);                                  // [TT][NSL][BC_OWN_REC]
+  const size_t region = owner_region_bytes(TT, RW, NS, max_cell);
+  P4<float>* swA = reinterpret_cast<P4<float>*>(smem_raw + region);                 // [max_cell][nslot]
   Cent<float>* cA = reinterpret_cast<Cent<float>*>(swA + (size_t)max_cell * nslot);
   int* vidA = reinterpret_cast<int*>(cA + max_cell);                                // [max_cell][3]
   int* jb = vidA + 3 * max_cell;                                                    // [TT] first trial triangle
@@ -1164,8 +1237,22 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
   int* eaS = jeb + TT * NSL;                                                        // [NSL] edge of test slot a
   int* wnext = eaS + NSL;                                                           // [TT] next unit's trial cells
   BcUnit* nextU = reinterpret_cast<BcUnit*>((reinterpret_cast<uintptr_t>(wnext + TT) + 15) & ~uintptr_t(15));
+  uint32_t* tm_base = reinterpret_cast<uint32_t*>(nextU + 1);
   if (BOTH) wantS = wantC = true;  // S and C: the branches on them fold away
   unsigned evals = 0;
+  // the trial-slot sums of each thread live in its tensor-memory lane (96 of
+  // 128 columns), so that they hold no registers during the evaluations
+  if (threadIdx.x < 32) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     (unsigned)__cvta_generic_to_shared(tm_base)),
+                 "r"(BC_OWN_TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmr = tm_lane_addr(*tm_base);
   // The next unit's descriptor and trial-cell list are copied into shared
   // memory while the current unit computes (cp.async), so a unit starts two
   // dependent global loads closer to its data.
@@ -1226,40 +1313,51 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     const bool more = uidx + gridDim.x < nunits;
     if (threadIdx.x == 0 && more) cp_async16(nextU, units + uidx + gridDim.x);
     const int items = n1 * U.count;
-    // pair loop: thread t = j n1 + i1
-    if ((int)threadIdx.x < items) {
-      const int j = threadIdx.x / n1, i1 = threadIdx.x - j * n1;
-      const int b2 = jb[j], n2 = jn[j];
-      const int ns2 = jns[j];
-      const float4* R2 = trial + (size_t)j * max_cell * RW;
-      const Cent<float> ca = cA[i1];
-      const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
-      const P4<float>* X = ptsA + i1 * NS;
-      const P4<float>* XW = ptsW + i1 * NS;
-      // slot b on tau2 is sigma_b (y - c2) + w_b with sigma_b = s_b / |tau2| (s_b
-      // constant over the cell): the sigma terms of all slots are one sum a[]
-      // over tau2 of the pair coefficients times 1/|tau2|, scaled by s_b at the
-      // end; r[b] holds the w_b terms. Record layout, complex (re, im) pairs:
-      // S: AS, BS, WS[3]; C: AC, WC[3] (BS has no w_b term).
-      const float2 z0 = make_float2(0.f, 0.f);
-      float2 r[NSL][8];
-      float2 a[9];
+    // pair loop: thread t = j n1 + i1. Every lane of a warp runs the warp's
+    // largest trip count (the tensor-memory moves are warp-collective); a lane
+    // past its own pairs, or a thread with no item, only takes part in them.
+    const bool item = (int)threadIdx.x < items;
+    const int j = item ? (int)threadIdx.x / n1 : 0, i1 = item ? (int)threadIdx.x - j * n1 : 0;
+    const int b2 = jb[j], n2 = item ? jn[j] : 0;
+    const int ns2 = jns[j];
+    const float4* R2 = trial + (size_t)j * max_cell * RW;
+    const Cent<float> ca = cA[i1];
+    const int va0 = vidA[3 * i1], va1 = vidA[3 * i1 + 1], va2 = vidA[3 * i1 + 2];
+    const P4<float>* X = ptsA + i1 * NS;
+    const P4<float>* XW = ptsW + i1 * NS;
+    // slot b on tau2 is sigma_b (y - c2) + w_b with sigma_b = s_b / |tau2| (s_b
+    // constant over the cell): the sigma terms of all slots are one sum a[]
+    // over tau2 of the pair coefficients times 1/|tau2|, scaled by s_b at the
+    // end; the w_b terms of slot b are 8 complex sums in tensor-memory columns
+    // 16 b .. 16 b + 15. Record layout, complex (re, im) pairs: S: AS, BS,
+    // WS[3]; C: AC, WC[3] (BS has no w_b term).
+    const float2 z0 = make_float2(0.f, 0.f);
+    float2 a[9];
 #pragma unroll
-      for (int b = 0; b < NSL; ++b)
+    for (int f = 0; f < 9; ++f) a[f] = z0;
+    {
+      float zz[32];
 #pragma unroll
-        for (int f = 0; f < 8; ++f) r[b][f] = z0;
-#pragma unroll
-      for (int f = 0; f < 9; ++f) a[f] = z0;
-      for (int i2 = 0; i2 < n2; ++i2) {
-        const float4* rr = R2 + i2 * RW;
+      for (int q = 0; q < 32; ++q) zz[q] = 0.f;
+      tm_wait_st();  // the previous unit's stores (read back below) are complete
+      tm_st32(tmr, zz);
+      tm_st32(tmr + 32, zz);
+      tm_st32(tmr + 64, zz);
+    }
+    const int n2w = __reduce_max_sync(0xffffffffu, n2);
+    for (int i2 = 0; i2 < n2w; ++i2) {
+      bool act = i2 < n2;
+      const float4* rr = R2 + i2 * RW;
+      const P4<float>* Ys = reinterpret_cast<const P4<float>*>(rr);
+      Mom2 m;
+      PairC2 pc;
+      if (act) {
         const float4 k0 = rr[NP + NSL], k1 = rr[NP + NSL + 1], k2 = rr[NP + NSL + 2];
         const int vb0 = __float_as_int(k1.w), vb1 = __float_as_int(k2.x), vb2 = __float_as_int(k2.y);
         Cent<float> cb;
         cb.hi[0] = k0.x; cb.hi[1] = k0.y; cb.hi[2] = k0.z;
         cb.lo[0] = k0.w; cb.lo[1] = k1.x; cb.lo[2] = k1.y;
         cb.d = k1.z;
-        // staged trial rule points (class mode: the far rule)
-        const P4<float>* Ys = reinterpret_cast<const P4<float>*>(rr);
         const V3<float> D = ca.minus(cb);
         // Sauter–Schwab pairs (a shared vertex) are the singular kernel's; such
         // pairs are always near: |c1 - c2| <= 2/3 (d1 + d2)
@@ -1267,11 +1365,13 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
           return va0 == vb0 || va0 == vb1 || va0 == vb2 || va1 == vb0 || va1 == vb1 || va1 == vb2 || va2 == vb0 ||
                  va2 == vb1 || va2 == vb2;
         };
-        Mom2 m;
         if constexpr (NREG > 0) {
-          if (touch()) continue;
-          owner_moments<NREG, true, BOTH>(X, XW, Ys, D, kr, ki, wantC, m);
-          evals += NREG * NREG;
+          if (touch()) {
+            act = false;
+          } else {
+            owner_moments<NREG, true, BOTH>(X, XW, Ys, D, kr, ki, wantC, m);
+            evals += NREG * NREG;
+          }
         } else if (all_far) {
           owner_moments<3, true, BOTH>(X + RULE_OFF_FAR, XW + RULE_OFF_FAR, Ys, D, kr, ki, wantC, m);
           evals += 9;
@@ -1280,8 +1380,9 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
           if (c == 2) {
             owner_moments<3, true, BOTH>(X + RULE_OFF_FAR, XW + RULE_OFF_FAR, Ys, D, kr, ki, wantC, m);
             evals += 9;
+          } else if (c == 0 && touch()) {
+            act = false;
           } else {
-            if (c == 0 && touch()) continue;
             // near and medium pairs (under 1%): points from global memory
             const P4<float>* Y = cd.pts + (size_t)(b2 + i2) * NS;
             if (c == 1) {
@@ -1294,51 +1395,66 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
             }
           }
         }
-        PairC2 pc;
-        pair_c_coeffs(m, D, pc);
-        // sigma terms: the pair coefficients that multiply sigma_b, times 1/|tau2|
-        const float2 beta = dup2(k2.z), nbeta = dup2(-k2.z);
-        a[0] = fma2(beta, m.Gxy, a[0]);
-        a[1] = fma2(beta, m.G0, a[1]);
+        if (act) {
+          pair_c_coeffs(m, D, pc);
+          // sigma terms: the pair coefficients that multiply sigma_b, times 1/|tau2|
+          const float2 beta = dup2(k2.z), nbeta = dup2(-k2.z);
+          a[0] = fma2(beta, m.Gxy, a[0]);
+          a[1] = fma2(beta, m.G0, a[1]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a[2 + c] = fma2(beta, m.Gy[c], a[2 + c]);
-        a[5] = fma2(beta, pc.Dgxy, a[5]);
+          for (int c = 0; c < 3; ++c) a[2 + c] = fma2(beta, m.Gy[c], a[2 + c]);
+          a[5] = fma2(beta, pc.Dgxy, a[5]);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) a[6 + c] = fma2(nbeta, pc.Y2[c], a[6 + c]);
-        const P4<float>* swb = Ys + NP;
-#pragma unroll
-        for (int b = 0; b < NSL; ++b) {
-          if (b >= ns2) break;
-          const P4<float> u = swb[b];
-          const float2 bx = dup2(u.y), by = dup2(u.z), bz = dup2(u.w);
-          float2* o = r[b];
-          // S: AS = w_b . Gx, WS = w_b G0
-          o[0] = fma2(bz, m.Gx[2], fma2(by, m.Gx[1], fma2(bx, m.Gx[0], o[0])));
-          o[1] = fma2(bx, m.G0, o[1]);
-          o[2] = fma2(by, m.G0, o[2]);
-          o[3] = fma2(bz, m.G0, o[3]);
-          // C: AC = w_b . X1, WC = w_b x V
-          o[4] = fma2(bz, pc.X1[2], fma2(by, pc.X1[1], fma2(bx, pc.X1[0], o[4])));
-          o[5] = fma2(by, pc.V[2], fma2(bz, pc.nV[1], o[5]));
-          o[6] = fma2(bz, pc.V[0], fma2(bx, pc.nV[2], o[6]));
-          o[7] = fma2(bx, pc.V[1], fma2(by, pc.nV[0], o[7]));
+          for (int c = 0; c < 3; ++c) a[6 + c] = fma2(nbeta, pc.Y2[c], a[6 + c]);
         }
       }
+      // the w_b terms, three slots at a time through registers
+      const P4<float>* swb = Ys + NP;
+      __syncwarp();
+      tm_wait_st();
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        float rf[48];
+        tm_ld32(tmr + 48 * h, rf);
+        tm_ld16(tmr + 48 * h + 32, rf + 32);
+        tm_wait_ld();
+        if (act) {
+#pragma unroll
+          for (int bb = 0; bb < 3; ++bb) {
+            const int b = 3 * h + bb;
+            if (b < ns2) {
+              const P4<float> u = swb[b];
+              owner_slot_update(rf + 16 * bb, dup2(u.y), dup2(u.z), dup2(u.w), m, pc);
+            }
+          }
+        }
+        __syncwarp();
+        tm_st32(tmr + 48 * h, rf);
+        tm_st16(tmr + 48 * h + 32, rf + 32);
+      }
+    }
+    __syncthreads();  // every thread is done with the staged trial records: the records overwrite them
+    tm_wait_st();
+    {
       float* dst = rec + (size_t)threadIdx.x * NSL * BC_OWN_REC;
 #pragma unroll
       for (int b = 0; b < NSL; ++b) {
-        if (b >= ns2) break;
-        const float2 sb = dup2(js[j * NSL + b]);
-        __align__(16) float2 tmp[BC_OWN_REC / 2];
-        tmp[0] = fma2(sb, a[0], r[b][0]);  // AS
-        tmp[1] = mul2(sb, a[1]);           // BS
+        float f[16];
+        tm_ld16(tmr + 16 * b, f);
+        tm_wait_ld();
+        if (item && b < ns2) {
+          const float2 sb = dup2(js[j * NSL + b]);
+          __align__(16) float2 tmp[BC_OWN_REC / 2];
+          tmp[0] = fma2(sb, a[0], make_float2(f[0], f[1]));  // AS
+          tmp[1] = mul2(sb, a[1]);                           // BS
 #pragma unroll
-        for (int c = 0; c < 3; ++c) tmp[2 + c] = fma2(sb, a[2 + c], r[b][1 + c]);  // WS
-        tmp[5] = fma2(sb, a[5], r[b][4]);  // AC
+          for (int c = 0; c < 3; ++c) tmp[2 + c] = fma2(sb, a[2 + c], make_float2(f[2 + 2 * c], f[3 + 2 * c]));  // WS
+          tmp[5] = fma2(sb, a[5], make_float2(f[8], f[9]));  // AC
 #pragma unroll
-        for (int c = 0; c < 3; ++c) tmp[6 + c] = fma2(sb, a[6 + c], r[b][5 + c]);  // WC
-        tmp[9] = z0;
-        vcopy(dst + b * BC_OWN_REC, reinterpret_cast<const float*>(tmp), BC_OWN_REC);
+          for (int c = 0; c < 3; ++c) tmp[6 + c] = fma2(sb, a[6 + c], make_float2(f[10 + 2 * c], f[11 + 2 * c]));  // WC
+          tmp[9] = z0;
+          vcopy(dst + b * BC_OWN_REC, reinterpret_cast<const float*>(tmp), BC_OWN_REC);
+        }
       }
     }
     if (threadIdx.x == 0) cp_async_wait_all();
@@ -1373,6 +1489,11 @@ __global__ void __launch_bounds__(TT, 2) bc_owner_kernel(
     }
     cp_async_wait_all();  // this thread's copies of the next trial-cell list
   }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (threadIdx.x < 32)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(*tm_base), "r"(BC_OWN_TMEM_COLS)
+                 : "memory");
   count_add(cnt, evals);
 }
 
@@ -2683,19 +2804,36 @@ static int bc_regular_t(const AssembleArgs& a, const BcUnit* units, int64_t nuni
       pack<<<(unsigned)((nct * rw + 255) / 256), 256, 0, a.stream>>>(cd, s.nslot, nct, s.d_triF, s.d_cell_tri, trec);
       note_launch();
       const int nsp_o = nreg > 0 ? nreg : RULE_POINTS_ALL;
-      const size_t osmem = (size_t)OT * BC_OWN_SLOTS * BC_OWN_REC * sizeof(float) +
-                           (size_t)BC_OWN_STAGE * rw * sizeof(float4) +
-                           2 * (size_t)max_cell * nsp_o * sizeof(P4<float>) +
+      const size_t osmem = owner_region_bytes(OT, rw, nsp_o, max_cell) +
                            (size_t)max_cell * s.nslot * sizeof(P4<float>) + (size_t)max_cell * sizeof(Cent<float>) +
                            (size_t)max_cell * 3 * sizeof(int) + 3 * (size_t)OT * sizeof(int) +
                            (size_t)OT * BC_OWN_SLOTS * sizeof(float) +
                            // slot counts, slot edges, test edges, next trial cells, next descriptor
                            (size_t)OT * sizeof(int) + (size_t)OT * BC_OWN_SLOTS * sizeof(int) +
-                           BC_OWN_SLOTS * sizeof(int) + (size_t)OT * sizeof(int) + 2 * sizeof(BcUnit) + 64;
+                           BC_OWN_SLOTS * sizeof(int) + (size_t)OT * sizeof(int) + 2 * sizeof(BcUnit) + 16 + 64;
       int rc = ensure_dyn_smem((const void*)okern, (int)osmem);
+      // three CTAs of ~72 KB need the largest shared-memory carveout
+      if (!rc && cudaFuncSetAttribute((const void*)okern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      cudaSharedmemCarveoutMaxShared) != cudaSuccess)
+        rc = fail(CAL_ECUDA, "bc owner kernel: carveout preference failed");
+      // CTAs per SM from the kernel's registers, shared memory and tensor-memory
+      // columns. The runtime's occupancy query answers 1 for this kernel
+      // (measured, with 3 fitting), which would leave a third of the SM idle.
       int per_sm = 0;
-      if (!rc && cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, okern, OT, osmem) != cudaSuccess)
-        rc = fail(CAL_ECUDA, "bc owner kernel: occupancy query failed");
+      if (!rc) {
+        cudaFuncAttributes fa{};
+        int dev = 0, regs_sm = 0, smem_sm = 0, smem_res = 0;
+        if (cudaFuncGetAttributes(&fa, (const void*)okern) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&smem_res, cudaDevAttrReservedSharedMemoryPerBlock, dev) != cudaSuccess) {
+          rc = fail(CAL_ECUDA, "bc owner kernel: attribute query failed");
+        } else {
+          const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * OT;  // allocated per warp in units of 8 x 32
+          const size_t smem_cta = osmem + fa.sharedSizeBytes + smem_res;
+          per_sm = std::min({regs_sm / std::max(1, regs_cta), (int)(smem_sm / smem_cta), 512 / BC_OWN_TMEM_COLS});
+        }
+      }
       if (!rc) {
         const int64_t grid = std::min<int64_t>(nunits, (int64_t)std::max(1, per_sm) * n_sm * 2);
         const int tok = prof_begin(a.stream, "bc_tile", work);
@@ -2874,23 +3012,24 @@ static int rwg_free_t(const Space& s, int scat, double kr, double ki, int nreg, 
       CAL_TRY_CUDA(cudaGetLastError());
     }
     return CAL_OK;
+  } else {
+    for (int r0 = 0; r0 < nrhs; r0 += 32) {
+      const int nr = std::min(32, nrhs - r0);
+      const int smem = 2 * 16 * 3 * 2 * nr * 2 * (int)sizeof(AT);
+      auto kern = nreg == 6 ? rwg_free_kernel<R, 6, VT, AT>
+                            : (nreg == 1 ? rwg_free_kernel<R, 1, VT, AT> : rwg_free_kernel<R, 0, VT, AT>);
+      if (int rc = ensure_dyn_smem((const void*)kern, smem)) return rc;
+      const int tok = prof_begin(st, "rwg_free", units * nr);
+      unsigned long long* cnt = nreg == 0 ? prof_counter(tok, st) : nullptr;
+      kern<<<grid, block, smem, st>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)kr, (R)ki, mikr, miki, c4r, c4i, g_rules,
+                                      x + (int64_t)r0 * 2 * n, y + (int64_t)r0 * 2 * n, n, nr, (AT)ar, (AT)ai,
+                                      (AT)br, (AT)bi, cnt);
+      prof_end(st, tok);
+      note_launch();
+      CAL_TRY_CUDA(cudaGetLastError());
+    }
+    return CAL_OK;
   }
-  for (int r0 = 0; r0 < nrhs; r0 += 32) {
-    const int nr = std::min(32, nrhs - r0);
-    const int smem = 2 * 16 * 3 * 2 * nr * 2 * (int)sizeof(AT);
-    auto kern = nreg == 6 ? rwg_free_kernel<R, 6, VT, AT>
-                          : (nreg == 1 ? rwg_free_kernel<R, 1, VT, AT> : rwg_free_kernel<R, 0, VT, AT>);
-    if (int rc = ensure_dyn_smem((const void*)kern, smem)) return rc;
-    const int tok = prof_begin(st, "rwg_free", units * nr);
-    unsigned long long* cnt = nreg == 0 ? prof_counter(tok, st) : nullptr;
-    kern<<<grid, block, smem, st>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)kr, (R)ki, mikr, miki, c4r, c4i, g_rules,
-                                    x + (int64_t)r0 * 2 * n, y + (int64_t)r0 * 2 * n, n, nr, (AT)ar, (AT)ai,
-                                    (AT)br, (AT)bi, cnt);
-    prof_end(st, tok);
-    note_launch();
-    CAL_TRY_CUDA(cudaGetLastError());
-  }
-  return CAL_OK;
 }
 
 int launch_rwg_free(const Space& s, int scat, double kr, double ki, int nreg, int precision, int vec_prec,
