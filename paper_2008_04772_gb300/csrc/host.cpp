@@ -5,6 +5,7 @@
 // (RWG on the primal mesh, BC on its barycentric refinement) of
 // arXiv 2008.04772. All O(N) setup; the O(N^2) numerics run on the GPU.
 #include <algorithm>
+#include <array>
 #include <thread>
 #include <atomic>
 #include <mutex>
@@ -549,11 +550,12 @@ void build_singular_pairs(Space& s) {
   for (int64_t d = 0; d < m.M; ++d) {
     const int64_t t0 = s.tri_off[d], t1 = s.tri_off[d + 1];
     const int nth = (int)std::max<int64_t>(
-        1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(), (t1 - t0) / 4096}));
+        1, std::min<int64_t>({16, (int64_t)std::thread::hardware_concurrency(), (t1 - t0) / 1024}));
     std::vector<std::vector<SingPair>> part(nth);
     auto work = [&](int w) {
       const int64_t a0 = t0 + (t1 - t0) * w / nth, a1 = t0 + (t1 - t0) * (w + 1) / nth;
       auto& out = part[w];
+      out.reserve((size_t)(a1 - a0) * 12);
       std::vector<int> stamp(s.ntri, -1), nb;
       for (int64_t t = a0; t < a1; ++t) {
         nb.clear();
@@ -605,15 +607,33 @@ void build_singular_pairs(Space& s) {
     }
     // grouped by class, costliest rules first: lanes of one warp then run the
     // same rule (the float32-output kernel takes one pair per lane)
+    // (each range's pairs of a class go after those of the earlier ranges, so
+    // the order does not depend on the thread count; the ranges copy in parallel)
     auto rank = [](const SingPair& q) { return q.cls == 2 ? 0 : (q.cls == 3 ? 1 : 2); };
-    size_t cnt[4] = {0, 0, 0, 0};
-    for (const auto& pw : part)
-      for (const SingPair& q : pw) ++cnt[rank(q) + 1];
-    for (int c = 0; c < 3; ++c) cnt[c + 1] += cnt[c];
+    std::vector<std::array<size_t, 3>> cnt(nth, {0, 0, 0});
+    parallel_for(nth, [&](int w) {
+      for (const SingPair& q : part[w]) ++cnt[w][rank(q)];
+    });
+    std::vector<std::array<size_t, 3>> off(nth);
+    size_t pos = 0;
+    for (int c = 0; c < 3; ++c)
+      for (int w = 0; w < nth; ++w) {
+        off[w][c] = pos;
+        pos += cnt[w][c];
+      }
     auto& out = s.sing[d];
-    out.resize(cnt[3]);
-    for (const auto& pw : part)
-      for (const SingPair& q : pw) out[cnt[rank(q)]++] = q;
+    out.resize(pos);
+    auto copy = [&](int w) {
+      std::array<size_t, 3> o = off[w];
+      for (const SingPair& q : part[w]) out[o[rank(q)]++] = q;
+    };
+    if (nth == 1) {
+      copy(0);
+    } else {
+      std::vector<std::thread> th;
+      for (int w = 0; w < nth; ++w) th.emplace_back(copy, w);
+      for (auto& x : th) x.join();
+    }
   }
 }
 
