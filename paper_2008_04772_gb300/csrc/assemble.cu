@@ -1419,13 +1419,12 @@ __global__ void __launch_bounds__(TT, 3) bc_owner_kernel(
         tm_ld16(tmr + 48 * h + 32, rf + 32);
         tm_wait_ld();
         if (act) {
+          // every slot: past the cell's own, the records hold w_b = 0, so those
+          // sums stay zero (and are never written out) without a branch here
 #pragma unroll
           for (int bb = 0; bb < 3; ++bb) {
-            const int b = 3 * h + bb;
-            if (b < ns2) {
-              const P4<float> u = swb[b];
-              owner_slot_update(rf + 16 * bb, dup2(u.y), dup2(u.z), dup2(u.w), m, pc);
-            }
+            const P4<float> u = swb[3 * h + bb];
+            owner_slot_update(rf + 16 * bb, dup2(u.y), dup2(u.z), dup2(u.w), m, pc);
           }
         }
         __syncwarp();
