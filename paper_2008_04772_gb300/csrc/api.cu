@@ -193,9 +193,9 @@ std::vector<std::vector<int>> near_cells(const std::vector<int>& cells, const st
 // v <= w, of dual cells, grouped into units of one test cell and up to 16
 // trial cells (or as many as fill the block of the float32 per-thread kernel).
 // Dense blocks take every cell pair; near-field blocks the cell pairs that
-// hold a kept entry of the CSR pattern of op.
-int build_units(const Space& sp, int scat, bool dense, const Op& op, int precision, int nreg, Space::UnitLists& L,
-                cudaStream_t st) {
+// hold a kept entry of the CSR pattern np.
+int build_units(const Space& sp, int scat, bool dense, int64_t rows, int64_t row_offset,
+                const Space::NearPattern* np, int precision, int nreg, Space::UnitLists& L, cudaStream_t st) {
   const Mesh& m = *sp.mesh;
   std::vector<int> cells = cell_list(sp, scat);
   int max_cell = 0;
@@ -219,9 +219,9 @@ int build_units(const Space& sp, int scat, bool dense, const Op& op, int precisi
   if (!dense) {
     // tiles (v, w), v <= w, of the cell pairs that hold a kept entry (i, j):
     // v and w end cells of i and j; per test cell a stamp array deduplicates
-    const int64_t off = op.row_offset;
+    const int64_t off = row_offset;
     std::vector<int> cell_rows_ptr(m.nv + 1, 0), cell_rows;
-    for (int64_t i = 0; i < op.rows; ++i) {
+    for (int64_t i = 0; i < rows; ++i) {
       ++cell_rows_ptr[m.e_lo[off + i] + 1];
       ++cell_rows_ptr[m.e_hi[off + i] + 1];
     }
@@ -229,7 +229,7 @@ int build_units(const Space& sp, int scat, bool dense, const Op& op, int precisi
     cell_rows.resize(cell_rows_ptr[m.nv]);
     {
       std::vector<int> fill(cell_rows_ptr.begin(), cell_rows_ptr.end() - 1);
-      for (int64_t i = 0; i < op.rows; ++i) {
+      for (int64_t i = 0; i < rows; ++i) {
         cell_rows[fill[m.e_lo[off + i]]++] = (int)i;
         cell_rows[fill[m.e_hi[off + i]]++] = (int)i;
       }
@@ -239,8 +239,8 @@ int build_units(const Space& sp, int scat, bool dense, const Op& op, int precisi
       ws.clear();
       for (int r = cell_rows_ptr[v]; r < cell_rows_ptr[v + 1]; ++r) {
         const int64_t i = cell_rows[r];
-        for (int64_t q = op.h_rowptr[i]; q < op.h_rowptr[i + 1]; ++q) {
-          const int64_t j = off + op.h_col[q];
+        for (int64_t q = np->rowptr[i]; q < np->rowptr[i + 1]; ++q) {
+          const int64_t j = off + np->col[q];
           for (int w : {m.e_lo[j], m.e_hi[j]})
             if (w >= v && stamp[w] != v) {
               stamp[w] = v;
@@ -370,6 +370,47 @@ int build_units(const Space& sp, int scat, bool dense, const Op& op, int precisi
   return CAL_OK;
 }
 
+// the near-field pattern of (scatterer, cutoff), built once per space
+const Space::NearPattern& cached_near_pattern(const Space& sp, int scat, double chi) {
+  std::lock_guard<std::mutex> lk(sp.static_mu);
+  for (auto& q : sp.near_patterns)
+    if (q->scat == scat && q->chi == chi) return *q;
+  auto q = std::make_unique<Space::NearPattern>();
+  q->scat = scat;
+  q->chi = chi;
+  near_pattern(sp, scat, chi, q->rowptr, q->col);
+  sp.near_patterns.push_back(std::move(q));
+  return *sp.near_patterns.back();
+}
+
+// the BC work units of (scatterer, cutoff, rule, kernel), built and uploaded
+// once per space; a caller on another stream waits for the upload
+int cached_unit_lists(const Space& sp, int scat, double chi, int nreg, int precision, cudaStream_t st,
+                      Space::UnitLists** out) {
+  const Mesh& m = *sp.mesh;
+  const bool dense = std::isinf(chi);
+  const Space::NearPattern* np = dense ? nullptr : &cached_near_pattern(sp, scat, chi);
+  const bool fp32 = precision == CAL_FP32;
+  std::lock_guard<std::mutex> lk(sp.static_mu);
+  for (auto& u : sp.unit_lists)
+    if (u->scat == scat && u->chi == chi && u->nreg == nreg && u->owner == fp32) {
+      CAL_TRY_CUDA(cudaStreamWaitEvent(st, u->done, 0));
+      if (out) *out = u.get();
+      return CAL_OK;
+    }
+  auto u = std::make_unique<Space::UnitLists>();
+  u->scat = scat;
+  u->chi = chi;
+  u->nreg = nreg;
+  u->owner = fp32;
+  const int64_t off = scat < 0 ? 0 : m.edge_off[scat];
+  const int64_t rows = (scat < 0 ? m.ne : m.edge_off[scat + 1]) - off;
+  if (int rc = build_units(sp, scat, dense, rows, off, np, precision, nreg, *u, st)) return rc;
+  if (out) *out = u.get();
+  sp.unit_lists.push_back(std::move(u));
+  return CAL_OK;
+}
+
 // Assemble S and/or C of one block (scat = -1: union; else scatterer scat).
 int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, int scat, double chi,
                    int nreg, int nsing, int precision, std::unique_ptr<Op>& out) {
@@ -396,20 +437,9 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     if (!(chi >= 0)) return fail(CAL_EINVAL, "assemble: near_cutoff must be >= 0 or INFINITY");
     {
       // the pattern depends on the geometry and the cutoff only: built once per space
-      std::lock_guard<std::mutex> lk(sp.static_mu);
-      const Space::NearPattern* np = nullptr;
-      for (auto& q : sp.near_patterns)
-        if (q->scat == scat && q->chi == chi) np = q.get();
-      if (!np) {
-        auto q = std::make_unique<Space::NearPattern>();
-        q->scat = scat;
-        q->chi = chi;
-        near_pattern(sp, scat, chi, q->rowptr, q->col);
-        np = q.get();
-        sp.near_patterns.push_back(std::move(q));
-      }
-      op->h_rowptr = np->rowptr;
-      op->h_col = np->col;
+      const Space::NearPattern& np = cached_near_pattern(sp, scat, chi);
+      op->h_rowptr = np.rowptr;
+      op->h_col = np.col;
     }
     op->nnz = op->h_rowptr.back();
   } else {
@@ -459,25 +489,8 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     if ((rc = launch_rwg_regular(a))) return rc;
   } else {
     // the work units are the same for every wavenumber: built once per space
-    const bool fp32 = precision == CAL_FP32;
     Space::UnitLists* L = nullptr;
-    {
-      std::lock_guard<std::mutex> lk(sp.static_mu);
-      for (auto& u : sp.unit_lists)
-        if (u->scat == scat && u->chi == chi && u->nreg == nreg && u->owner == fp32) L = u.get();
-      if (L) {
-        CAL_TRY_CUDA(cudaStreamWaitEvent(st, L->done, 0));
-      } else {
-        auto u = std::make_unique<Space::UnitLists>();
-        u->scat = scat;
-        u->chi = chi;
-        u->nreg = nreg;
-        u->owner = fp32;
-        if ((rc = build_units(sp, scat, dense, *op, precision, nreg, *u, st))) return rc;
-        L = u.get();
-        sp.unit_lists.push_back(std::move(u));
-      }
-    }
+    if ((rc = cached_unit_lists(sp, scat, chi, nreg, precision, st, &L))) return rc;
     if (L->nunits > 0)
       rc = launch_bc_regular_units(a, L->d_units, L->nunits, L->d_wlist, L->max_cell, ctx.n_sm,
                                    L->pairs * nreg * nreg);
@@ -1645,10 +1658,28 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     P.bc = std::make_shared<Space>();
     Space* bcs = P.bc.get();
     Mesh* mh = &mesh->impl;
-    bcb.th = std::thread([&bcb, bcs, mh]() {
+    // P's blocks (one per scatterer, exterior and interior alike) need the work
+    // units of the BC regular-pair kernels: the same thread builds them, on a
+    // stream of its own, while this thread's A assembly runs on the device
+    const bool prebuild = o.discretisation == 0;
+    const double chi_units =
+        (o.aca_nu_P > 0 || std::isinf(o.near_cutoff_P)) ? INFINITY : o.near_cutoff_P * mesh->impl.h;
+    const int prec_units = o.precision == CAL_FP64 ? CAL_FP64 : CAL_FP32;
+    const int nreg_units = o.q_regular_P, dev = ctx->impl.device, M = P.M;
+    bcb.th = std::thread([&bcb, bcs, mh, prebuild, chi_units, prec_units, nreg_units, dev, M]() {
       const double tb = now();
       bcb.rc = build_bc(*bcs, *mh);
       if (bcb.rc) bcb.msg = last_error();
+      if (!bcb.rc && prebuild && set_quadrature_tables(nreg_units, 1) == CAL_OK) {
+        // a failure here only leaves the lists to the assembly itself
+        cudaStream_t ps = nullptr;
+        if (cudaSetDevice(dev) == cudaSuccess && cudaStreamCreateWithFlags(&ps, cudaStreamNonBlocking) == cudaSuccess) {
+          for (int m = 0; m < M; ++m)
+            if (cached_unit_lists(*bcs, m, chi_units, nreg_units, prec_units, ps, nullptr) != CAL_OK) break;
+          cudaStreamDestroy(ps);
+        }
+        cudaGetLastError();
+      }
       bcb.seconds = now() - tb;
     });
   }

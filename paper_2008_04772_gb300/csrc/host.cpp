@@ -383,6 +383,30 @@ int build_rwg(Space& s, Mesh& m) {
   return CAL_OK;
 }
 
+// BC: sigma_{b,tau} |tau| per cell slot (cell_slot_s), and whether it is one
+// constant over each cell (sigma_factors), to 1e-9
+static void bc_sigma_factors(Space& s) {
+  const int64_t nv = (int64_t)s.cell_tri_ptr.size() - 1;
+  s.cell_slot_s.assign(s.cell_edge.size(), 0.0f);
+  bool ok = true;
+  for (int64_t v = 0; v < nv && ok; ++v) {
+    const int t0 = s.cell_tri_ptr[v], t1 = s.cell_tri_ptr[v + 1];
+    const int e0 = s.cell_edge_ptr[v], ns = s.cell_edge_ptr[v + 1] - e0;
+    if (t1 == t0) continue;
+    for (int sl = 0; sl < ns && ok; ++sl) {
+      const int tau0 = s.cell_tri[t0];
+      const double sb = s.slot_sw[((size_t)tau0 * s.nslot + sl) * 4] * s.triD[tau0].area;
+      for (int q = t0; q < t1 && ok; ++q) {
+        const int tau = s.cell_tri[q];
+        const double v2 = s.slot_sw[((size_t)tau * s.nslot + sl) * 4] * s.triD[tau].area;
+        ok = std::abs(v2 - sb) <= 1e-9 * std::abs(sb) + 1e-300;
+      }
+      s.cell_slot_s[e0 + sl] = (float)sb;
+    }
+  }
+  s.sigma_factors = ok;
+}
+
 int build_bc(Space& s, Mesh& m) {
   s.mesh = &m;
   s.kind = CAL_BC;
@@ -523,6 +547,7 @@ int build_bc(Space& s, Mesh& m) {
   });
   s.tri_off.resize(m.M + 1);
   for (int64_t d = 0; d <= m.M; ++d) s.tri_off[d] = 6 * m.tri_off[d];
+  bc_sigma_factors(s);
   build_singular_pairs(s);
   return CAL_OK;
 }
@@ -807,26 +832,6 @@ int upload_space(Space& s, cudaStream_t st) {
   if ((rc = upload(&s.d_slot_swf, swf.data(), swf.size(), st))) return rc;
   if ((rc = upload(&s.d_slot_swd, s.slot_sw.data(), s.slot_sw.size(), st))) return rc;
   if (s.kind == CAL_BC) {
-    // sigma_{b,tau} |tau| per cell slot, and whether it is one constant over the cell
-    const int64_t nv = (int64_t)s.cell_tri_ptr.size() - 1;
-    s.cell_slot_s.assign(s.cell_edge.size(), 0.0f);
-    bool ok = true;
-    for (int64_t v = 0; v < nv && ok; ++v) {
-      const int t0 = s.cell_tri_ptr[v], t1 = s.cell_tri_ptr[v + 1];
-      const int e0 = s.cell_edge_ptr[v], ns = s.cell_edge_ptr[v + 1] - e0;
-      if (t1 == t0) continue;
-      for (int sl = 0; sl < ns && ok; ++sl) {
-        const int tau0 = s.cell_tri[t0];
-        const double sb = s.slot_sw[((size_t)tau0 * s.nslot + sl) * 4] * s.triD[tau0].area;
-        for (int q = t0; q < t1 && ok; ++q) {
-          const int tau = s.cell_tri[q];
-          const double v2 = s.slot_sw[((size_t)tau * s.nslot + sl) * 4] * s.triD[tau].area;
-          ok = std::abs(v2 - sb) <= 1e-9 * std::abs(sb) + 1e-300;
-        }
-        s.cell_slot_s[e0 + sl] = (float)sb;
-      }
-    }
-    s.sigma_factors = ok;
     if ((rc = upload(&s.d_cell_slot_s, s.cell_slot_s.data(), std::max<size_t>(s.cell_slot_s.size(), 1), st)))
       return rc;
     if ((rc = upload(&s.d_cell_tri_ptr, s.cell_tri_ptr.data(), s.cell_tri_ptr.size(), st))) return rc;
