@@ -1497,11 +1497,128 @@ __global__ void __launch_bounds__(TT, 3) bc_owner_kernel(
 }
 
 // ---------------------------------------------------------------------------
-// A8, float32 operator and float32 vectors: the product of rwg_free_kernel
-// with the tile's 16 + 16 triangles staged in shared memory once (rule points
+// Float32 RWG pairs in 16 x 16 tiles (rows: triangles tbi 16 + t, columns
+// tbj 16 + t): the tile's triangles staged in shared memory once (rule points
 // with the test weights folded in and the trial weights over 4 pi, centroids,
-// vertex ids, slots), and the moments, pair coefficients, entries and their
-// application on packed (re, im) float32 pairs (FFMA2 / FADD2 / FMUL2).
+// vertex ids, slots and their edges), and each pair's moments, pair
+// coefficients and 3 x 3 local S and C on packed (re, im) float32 pairs
+// (FFMA2 / FADD2 / FMUL2). Used by the matrix-free product and by the stored
+// assembly.
+// ---------------------------------------------------------------------------
+template <int NS>
+struct RwgTile {
+  P4<float> X[16 * NS];   // test points (rows)
+  P4<float> XW[16 * NS];  // w (x, y, z), w
+  P4<float> Y[16 * NS];   // trial points, w / 4 pi (columns)
+  P4<float> SWR[48], SWC[48];  // slots (sigma, w) of rows and columns
+  Cent<float> CR[16], CC[16];
+  int VR[48], VC[48];  // vertex ids
+  int ER[48], EC[48];  // slot edges
+};
+
+template <int NS>
+__device__ __forceinline__ void rwg_tile_stage(RwgTile<NS>& T, const TriF* __restrict__ tri,
+                                               const int* __restrict__ slot_edge, const float* __restrict__ slot_sw,
+                                               int64_t t0, int64_t ntr, int tbi, int tbj, const Rules& rl, int tid) {
+  for (int q = tid; q < 2 * 16 * NS; q += 256) {
+    const int side = q / (16 * NS), rest = q - side * 16 * NS, t = rest / NS, u = rest - t * NS;
+    const int64_t it = (int64_t)(side == 0 ? tbi : tbj) * 16 + t;
+    if (it >= ntr) continue;
+    const TriF tr = tri[t0 + it];
+    const P4<float> p = staged_point(tr, rl, u);
+    if (side == 0) {
+      T.X[t * NS + u] = p;
+      T.XW[t * NS + u] = {p.w * p.x, p.w * p.y, p.w * p.z, p.w};
+    } else {
+      T.Y[t * NS + u] = {p.x, p.y, p.z, p.w * INV_4PI_F};
+    }
+    if (u == 0) {
+      (side == 0 ? T.CR : T.CC)[t].set(tr);
+      int* v = (side == 0 ? T.VR : T.VC) + 3 * t;
+      int* e = (side == 0 ? T.ER : T.EC) + 3 * t;
+      P4<float>* w = (side == 0 ? T.SWR : T.SWC) + 3 * t;
+      for (int a = 0; a < 3; ++a) {
+        v[a] = tr.vid[a];
+        e[a] = slot_edge[3 * (t0 + it) + a];
+        w[a] = reinterpret_cast<const P4<float>*>(slot_sw)[3 * (t0 + it) + a];
+      }
+    }
+  }
+}
+
+// The 3 x 3 local S and C of the pair (row ty, column tx) of a staged tile;
+// false (and nothing formed) for touching pairs, whose entries are the
+// singular kernel's. ev: the point-pair evaluations.
+template <int NREG, int NS>
+__device__ __forceinline__ bool rwg_tile_entries(const RwgTile<NS>& T, int ty, int tx, float kr, float ki, float mikr,
+                                                 float miki, float c4r, float c4i, float2* S, float2* C,
+                                                 unsigned& ev) {
+  const int* va = T.VR + 3 * ty;
+  const int* vb = T.VC + 3 * tx;
+  bool touch = false;
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int b = 0; b < 3; ++b) touch |= va[a] == vb[b];
+  if (touch) return false;
+  const Cent<float> ca = T.CR[ty], cb = T.CC[tx];
+  const V3<float> D = ca.minus(cb);
+  const P4<float>* Xa = T.X + ty * NS;
+  const P4<float>* XWa = T.XW + ty * NS;
+  const P4<float>* Yb = T.Y + tx * NS;
+  Mom2 m;
+  if constexpr (NREG > 0) {
+    owner_moments<NREG, true, true>(Xa, XWa, Yb, D, kr, ki, true, m);
+    ev = NREG * NREG;
+  } else {
+    const int c = pair_class<float>(D, ca.d, cb.d);
+    if (c == 2) {
+      owner_moments<3, true, true>(Xa + RULE_OFF_FAR, XWa + RULE_OFF_FAR, Yb + RULE_OFF_FAR, D, kr, ki, true, m);
+      ev = 9;
+    } else if (c == 1) {
+      owner_moments<4, true, true>(Xa + RULE_OFF_MEDIUM, XWa + RULE_OFF_MEDIUM, Yb + RULE_OFF_MEDIUM, D, kr, ki, true,
+                                   m);
+      ev = 16;
+    } else {
+      owner_moments<6, true, true>(Xa, XWa, Yb, D, kr, ki, true, m);
+      ev = 36;
+    }
+  }
+  PairC2 pc;
+  pair_c_coeffs(m, D, pc);
+  // S_ab = -ik [s_a s_b Gxy + s_a w_b.Gx + s_b w_a.Gy + w_a.w_b G0] + c4 s_a s_b G0
+  // C_ab = s_a s_b D.gxy + s_a w_b.X1 + s_b w_a.X2 + (w_a x w_b).V, X2 = -Y2
+  const float2 c4G0 = make_float2(c4r * m.G0.x - c4i * m.G0.y, c4r * m.G0.y + c4i * m.G0.x);
+  float2 wbGx[3], wbX1[3];
+#pragma unroll
+  for (int b = 0; b < 3; ++b) {
+    const P4<float> u = T.SWC[3 * tx + b];
+    wbGx[b] = fma2(dup2(u.w), m.Gx[2], fma2(dup2(u.z), m.Gx[1], mul2(dup2(u.y), m.Gx[0])));
+    wbX1[b] = fma2(dup2(u.w), pc.X1[2], fma2(dup2(u.z), pc.X1[1], mul2(dup2(u.y), pc.X1[0])));
+  }
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const P4<float> ua = T.SWR[3 * ty + a];
+    const float2 waGy = fma2(dup2(ua.w), m.Gy[2], fma2(dup2(ua.z), m.Gy[1], mul2(dup2(ua.y), m.Gy[0])));
+    const float2 waY2 = fma2(dup2(ua.w), pc.Y2[2], fma2(dup2(ua.z), pc.Y2[1], mul2(dup2(ua.y), pc.Y2[0])));
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const P4<float> ub = T.SWC[3 * tx + b];
+      const float ss = ua.x * ub.x;
+      const float ww = ua.y * ub.y + ua.z * ub.z + ua.w * ub.w;
+      const float2 B = fma2(dup2(ss), m.Gxy, fma2(dup2(ua.x), wbGx[b], fma2(dup2(ub.x), waGy, mul2(dup2(ww), m.G0))));
+      S[3 * a + b] = make_float2(mikr * B.x - miki * B.y + ss * c4G0.x, mikr * B.y + miki * B.x + ss * c4G0.y);
+      const float cx = ua.z * ub.w - ua.w * ub.z, cy = ua.w * ub.y - ua.y * ub.w, cz = ua.y * ub.z - ua.z * ub.y;
+      const float2 VW = fma2(dup2(cz), pc.V[2], fma2(dup2(cy), pc.V[1], mul2(dup2(cx), pc.V[0])));
+      C[3 * a + b] = fma2(dup2(ss), pc.Dgxy, fma2(dup2(ua.x), wbX1[b], fma2(dup2(-ub.x), waY2, VW)));
+    }
+  }
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// A8, float32 operator and float32 vectors: the product of rwg_free_kernel on
+// a staged tile with packed-pair arithmetic.
 // ---------------------------------------------------------------------------
 template <int NREG>
 __global__ void __launch_bounds__(256) rwg_free_f32_kernel(
@@ -1511,48 +1628,16 @@ __global__ void __launch_bounds__(256) rwg_free_f32_kernel(
     float bi, unsigned long long* cnt) {
   constexpr int NS = staged_points<NREG>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  P4<float>* X = reinterpret_cast<P4<float>*>(smem_raw);  // [16][NS] test points (rows)
-  P4<float>* XW = X + 16 * NS;                             // [16][NS] w (x, y, z), w
-  P4<float>* Y = XW + 16 * NS;                             // [16][NS] trial points, w / 4 pi (columns)
-  P4<float>* SWR = Y + 16 * NS;                            // [16][3] row slots (sigma, w)
-  P4<float>* SWC = SWR + 48;                               // [16][3] column slots
-  Cent<float>* CR = reinterpret_cast<Cent<float>*>(SWC + 48);  // [16]
-  Cent<float>* CC = CR + 16;                                   // [16]
-  int* VR = reinterpret_cast<int*>(CC + 16);                   // [16][3]
-  int* VC = VR + 48;                                           // [16][3]
-  int* ER = VC + 48;                                           // [16][3] row slot edges
-  int* EC = ER + 48;                                           // [16][3]
-  float* acc = reinterpret_cast<float*>(EC + 48);              // as rwg_free_kernel
+  RwgTile<NS>& T = *reinterpret_cast<RwgTile<NS>*>(smem_raw);
+  float* acc = reinterpret_cast<float*>(&T + 1);  // as rwg_free_kernel
+  const int* ER = T.ER;
+  const int* EC = T.EC;
   const int tbi = blockIdx.y, tbj = blockIdx.x;
   if (tbi > tbj) return;  // the whole block: the tile lies below the diagonal
   const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
   const int nacc = 2 * 16 * 3 * 2 * nrhs * 2;
   for (int q = tid; q < nacc; q += 256) acc[q] = 0.f;
-  // staging: side 0 = rows (tbi), 1 = columns (tbj)
-  for (int q = tid; q < 2 * 16 * NS; q += 256) {
-    const int side = q / (16 * NS), rest = q - side * 16 * NS, t = rest / NS, u = rest - t * NS;
-    const int64_t it = (int64_t)(side == 0 ? tbi : tbj) * 16 + t;
-    if (it >= ntr) continue;
-    const TriF T = tri[t0 + it];
-    const P4<float> p = staged_point(T, rl, u);
-    if (side == 0) {
-      X[t * NS + u] = p;
-      XW[t * NS + u] = {p.w * p.x, p.w * p.y, p.w * p.z, p.w};
-    } else {
-      Y[t * NS + u] = {p.x, p.y, p.z, p.w * INV_4PI_F};
-    }
-    if (u == 0) {
-      (side == 0 ? CR : CC)[t].set(T);
-      int* v = (side == 0 ? VR : VC) + 3 * t;
-      int* e = (side == 0 ? ER : EC) + 3 * t;
-      P4<float>* w = (side == 0 ? SWR : SWC) + 3 * t;
-      for (int a = 0; a < 3; ++a) {
-        v[a] = T.vid[a];
-        e[a] = slot_edge[3 * (t0 + it) + a];
-        w[a] = reinterpret_cast<const P4<float>*>(slot_sw)[3 * (t0 + it) + a];
-      }
-    }
-  }
+  rwg_tile_stage<NS>(T, tri, slot_edge, slot_sw, t0, ntr, tbi, tbj, rl, tid);
   __syncthreads();
   const int64_t i1 = (int64_t)tbi * 16 + ty, i2 = (int64_t)tbj * 16 + tx;
   bool active = i1 < ntr && i2 < ntr && i1 < i2;
@@ -1561,68 +1646,9 @@ __global__ void __launch_bounds__(256) rwg_free_f32_kernel(
 #pragma unroll
   for (int q = 0; q < 9; ++q) S[q] = C[q] = z0;
   if (active) {
-    const int* va = VR + 3 * ty;
-    const int* vb = VC + 3 * tx;
-#pragma unroll
-    for (int a = 0; a < 3; ++a)
-#pragma unroll
-      for (int b = 0; b < 3; ++b) active &= va[a] != vb[b];
-  }
-  if (active) {
-    const Cent<float> ca = CR[ty], cb = CC[tx];
-    const V3<float> D = ca.minus(cb);
-    const P4<float>* Xa = X + ty * NS;
-    const P4<float>* XWa = XW + ty * NS;
-    const P4<float>* Yb = Y + tx * NS;
-    Mom2 m;
-    unsigned ev;
-    if constexpr (NREG > 0) {
-      owner_moments<NREG, true, true>(Xa, XWa, Yb, D, kr, ki, true, m);
-      ev = NREG * NREG;
-    } else {
-      const int c = pair_class<float>(D, ca.d, cb.d);
-      if (c == 2) {
-        owner_moments<3, true, true>(Xa + RULE_OFF_FAR, XWa + RULE_OFF_FAR, Yb + RULE_OFF_FAR, D, kr, ki, true, m);
-        ev = 9;
-      } else if (c == 1) {
-        owner_moments<4, true, true>(Xa + RULE_OFF_MEDIUM, XWa + RULE_OFF_MEDIUM, Yb + RULE_OFF_MEDIUM, D, kr, ki,
-                                     true, m);
-        ev = 16;
-      } else {
-        owner_moments<6, true, true>(Xa, XWa, Yb, D, kr, ki, true, m);
-        ev = 36;
-      }
-    }
-    count_add(cnt, ev * (unsigned)nrhs);
-    PairC2 pc;
-    pair_c_coeffs(m, D, pc);
-    // S_ab = -ik [s_a s_b Gxy + s_a w_b.Gx + s_b w_a.Gy + w_a.w_b G0] + c4 s_a s_b G0
-    // C_ab = s_a s_b D.gxy + s_a w_b.X1 + s_b w_a.X2 + (w_a x w_b).V, X2 = -Y2
-    const float2 c4G0 = make_float2(c4r * m.G0.x - c4i * m.G0.y, c4r * m.G0.y + c4i * m.G0.x);
-    float2 wbGx[3], wbX1[3];
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const P4<float> u = SWC[3 * tx + b];
-      wbGx[b] = fma2(dup2(u.w), m.Gx[2], fma2(dup2(u.z), m.Gx[1], mul2(dup2(u.y), m.Gx[0])));
-      wbX1[b] = fma2(dup2(u.w), pc.X1[2], fma2(dup2(u.z), pc.X1[1], mul2(dup2(u.y), pc.X1[0])));
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const P4<float> ua = SWR[3 * ty + a];
-      const float2 waGy = fma2(dup2(ua.w), m.Gy[2], fma2(dup2(ua.z), m.Gy[1], mul2(dup2(ua.y), m.Gy[0])));
-      const float2 waY2 = fma2(dup2(ua.w), pc.Y2[2], fma2(dup2(ua.z), pc.Y2[1], mul2(dup2(ua.y), pc.Y2[0])));
-#pragma unroll
-      for (int b = 0; b < 3; ++b) {
-        const P4<float> ub = SWC[3 * tx + b];
-        const float ss = ua.x * ub.x;
-        const float ww = ua.y * ub.y + ua.z * ub.z + ua.w * ub.w;
-        const float2 B = fma2(dup2(ss), m.Gxy, fma2(dup2(ua.x), wbGx[b], fma2(dup2(ub.x), waGy, mul2(dup2(ww), m.G0))));
-        S[3 * a + b] = make_float2(mikr * B.x - miki * B.y + ss * c4G0.x, mikr * B.y + miki * B.x + ss * c4G0.y);
-        const float cx = ua.z * ub.w - ua.w * ub.z, cy = ua.w * ub.y - ua.y * ub.w, cz = ua.y * ub.z - ua.z * ub.y;
-        const float2 VW = fma2(dup2(cz), pc.V[2], fma2(dup2(cy), pc.V[1], mul2(dup2(cx), pc.V[0])));
-        C[3 * a + b] = fma2(dup2(ss), pc.Dgxy, fma2(dup2(ua.x), wbX1[b], fma2(dup2(-ub.x), waY2, VW)));
-      }
-    }
+    unsigned ev = 0;
+    active = rwg_tile_entries<NREG, NS>(T, ty, tx, kr, ki, mikr, miki, c4r, c4i, S, C, ev);
+    if (active) count_add(cnt, ev * (unsigned)nrhs);
   }
   int ea[3], eb[3];
 #pragma unroll
@@ -1731,6 +1757,112 @@ __global__ void __launch_bounds__(256) rwg_free_f32_kernel(
     const int e = (side == 0 ? ER : EC)[3 * t + slot];
     if (e < 0) continue;
     atomicAdd(y + (int64_t)r * 2 * n + (int64_t)h * n + e, make_float2(vr, vi));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// A3, float32: the stored regular RWG pairs on a staged tile with packed-pair
+// arithmetic. The tile's 48 row slots and 48 column slots map to their
+// distinct edges (neighbouring triangles share edges); each pair adds its
+// 3 x 3 S and C into a shared edge x edge accumulator, and each non-zero
+// cell goes to the block once, with its mirror (both operators are
+// symmetric on regular pairs).
+// ---------------------------------------------------------------------------
+constexpr int RWG_TILE_SLOTS = 48;
+
+template <int NREG>
+__global__ void __launch_bounds__(256) rwg_regular_f32_kernel(
+    const TriF* __restrict__ tri, const int* __restrict__ slot_edge, const float* __restrict__ slot_sw, int64_t t0,
+    int64_t ntr, float kr, float ki, float mikr, float miki, float c4r, float c4i, bool wantS, bool wantC, Rules rl,
+    Sink<float> out, unsigned long long* cnt) {
+  constexpr int NS = staged_points<NREG>();
+  constexpr int NE = RWG_TILE_SLOTS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  RwgTile<NS>& T = *reinterpret_cast<RwgTile<NS>*>(smem_raw);
+  float* accS = reinterpret_cast<float*>(&T + 1);  // [NE][NE] complex
+  float* accC = accS + 2 * NE * NE;
+  int* UR = reinterpret_cast<int*>(accC + 2 * NE * NE);  // slot -> distinct row edge (or -1)
+  int* UC = UR + NE;
+  int* firstR = UC + NE;  // 1 where a slot holds the first occurrence of its edge
+  int* firstC = firstR + NE;
+  int* uER = firstC + NE;  // the distinct row edges, in slot order of first occurrence
+  int* uEC = uER + NE;
+  int* nU = uEC + NE;     // distinct row and column edges
+  const int tbi = blockIdx.y, tbj = blockIdx.x;
+  if (tbi > tbj) return;  // the whole block: the tile lies below the diagonal
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 16 + tx;
+  for (int q = tid; q < 4 * NE * NE; q += 256) accS[q] = 0.f;  // accS and accC
+  rwg_tile_stage<NS>(T, tri, slot_edge, slot_sw, t0, ntr, tbi, tbj, rl, tid);
+  __syncthreads();
+  // distinct edges: slot q (rows: threads 0..47, columns: 64..111) is a first
+  // occurrence when no earlier slot of its side has its edge; its index is
+  // the count of first occurrences before its first occurrence
+  const int side = tid < 64 ? 0 : 1, q = tid - 64 * side;
+  const int* E = side == 0 ? T.ER : T.EC;
+  const int64_t base = (int64_t)(side == 0 ? tbi : tbj) * 16;
+  int first = -1;
+  if (tid < 128 && q < NE && base + q / 3 < ntr && E[q] >= 0) {
+    first = q;
+    for (int r = 0; r < q; ++r)
+      if (base + r / 3 < ntr && E[r] == E[q]) {
+        first = r;
+        break;
+      }
+    (side == 0 ? firstR : firstC)[q] = first == q;
+  } else if (tid < 128 && q < NE) {
+    (side == 0 ? firstR : firstC)[q] = 0;
+  }
+  __syncthreads();
+  if (tid < 128 && q < NE) {
+    const int* F = side == 0 ? firstR : firstC;
+    int u = -1;
+    if (first >= 0) {
+      u = 0;
+      for (int r = 0; r < first; ++r) u += F[r];
+    }
+    (side == 0 ? UR : UC)[q] = u;
+    if (first == q) (side == 0 ? uER : uEC)[u] = E[q];
+    if (q == NE - 1) {
+      int n = 0;
+      for (int r = 0; r < NE; ++r) n += F[r];
+      nU[side] = n;
+    }
+  }
+  __syncthreads();
+  const int64_t i1 = (int64_t)tbi * 16 + ty, i2 = (int64_t)tbj * 16 + tx;
+  if (i1 < ntr && i2 < ntr && i1 < i2) {
+    float2 S[9], C[9];
+    unsigned ev = 0;
+    if (rwg_tile_entries<NREG, NS>(T, ty, tx, kr, ki, mikr, miki, c4r, c4i, S, C, ev)) {
+      count_add(cnt, ev);
+#pragma unroll
+      for (int a = 0; a < 3; ++a) {
+        const int ur = UR[3 * ty + a];
+        if (ur < 0) continue;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const int uc = UC[3 * tx + b];
+          if (uc < 0) continue;
+          const int k = 2 * (ur * NE + uc);
+          atomicAdd(accS + k, S[3 * a + b].x);
+          atomicAdd(accS + k + 1, S[3 * a + b].y);
+          atomicAdd(accC + k, C[3 * a + b].x);
+          atomicAdd(accC + k + 1, C[3 * a + b].y);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // flush: the distinct edges of each side (slot order of first occurrences)
+  const int nr = nU[0], nc = nU[1];
+  for (int q2 = tid; q2 < nr * nc; q2 += 256) {
+    const int ur = q2 / nc, uc = q2 - ur * nc;
+    const int k = 2 * (ur * NE + uc);
+    const float sr = accS[k], si = accS[k + 1], cr = accC[k], ci = accC[k + 1];
+    if (sr == 0.f && si == 0.f && cr == 0.f && ci == 0.f) continue;
+    const int er = uER[ur], ec = uEC[uc];
+    out.add(er, ec, wantS, wantC, sr, si, cr, ci);
+    out.add(ec, er, wantS, wantC, sr, si, cr, ci);
   }
 }
 
@@ -2722,9 +2854,23 @@ static int rwg_regular_t(const AssembleArgs& a) {
   const int tok = prof_begin(a.stream, "rwg_regular", units);
   // by class the evaluations depend on the geometry: counted on the device
   unsigned long long* cnt = a.nreg == 0 ? prof_counter(tok, a.stream) : nullptr;
-  auto kern = a.nreg == 6 ? rwg_regular_kernel<R, 6> : (a.nreg == 1 ? rwg_regular_kernel<R, 1> : rwg_regular_kernel<R, 0>);
-  kern<<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
-                                     g_rules, out, cnt);
+  if constexpr (sizeof(R) == 4) {
+    // float32: the staged tile with a shared edge x edge accumulator
+    constexpr int NSP = RULE_POINTS_ALL;
+    const int tile = a.nreg == 6 ? (int)sizeof(RwgTile<6>) : (a.nreg == 1 ? (int)sizeof(RwgTile<1>) : (int)sizeof(RwgTile<NSP>));
+    const int smem = tile + 4 * RWG_TILE_SLOTS * RWG_TILE_SLOTS * (int)sizeof(float) + (6 * RWG_TILE_SLOTS + 2) * (int)sizeof(int);
+    auto fk = a.nreg == 6 ? rwg_regular_f32_kernel<6> : (a.nreg == 1 ? rwg_regular_f32_kernel<1> : rwg_regular_f32_kernel<0>);
+    if (int rc = ensure_dyn_smem((const void*)fk, smem)) {
+      prof_end(a.stream, tok);
+      return rc;
+    }
+    fk<<<grid, block, smem, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (float)a.kr, (float)a.ki, mikr, miki, c4r,
+                                        c4i, wS, wC, g_rules, out, cnt);
+  } else {
+    auto kern = a.nreg == 6 ? rwg_regular_kernel<R, 6> : (a.nreg == 1 ? rwg_regular_kernel<R, 1> : rwg_regular_kernel<R, 0>);
+    kern<<<grid, block, 0, a.stream>>>(tri, s.d_slot_edge, sw, t0, ntr, (R)a.kr, (R)a.ki, mikr, miki, c4r, c4i, wS, wC,
+                                       g_rules, out, cnt);
+  }
   prof_end(a.stream, tok);
   note_launch();
   CAL_TRY_CUDA(cudaGetLastError());
@@ -2994,9 +3140,8 @@ static int rwg_free_t(const Space& s, int scat, double kr, double ki, int nreg, 
     constexpr int NSP = RULE_POINTS_ALL;  // the largest staging (class rules)
     for (int r0 = 0; r0 < nrhs; r0 += 32) {
       const int nr = std::min(32, nrhs - r0);
-      const int nsp = nreg > 0 ? nreg : NSP;
-      const int smem = 3 * 16 * nsp * (int)sizeof(P4<float>) + 2 * 48 * (int)sizeof(P4<float>) +
-                       32 * (int)sizeof(Cent<float>) + 4 * 48 * (int)sizeof(int) + 2 * 16 * 3 * 2 * nr * 2 * 4;
+      const int tile = nreg == 6 ? (int)sizeof(RwgTile<6>) : (nreg == 1 ? (int)sizeof(RwgTile<1>) : (int)sizeof(RwgTile<NSP>));
+      const int smem = tile + 2 * 16 * 3 * 2 * nr * 2 * 4;
       auto kern = nreg == 6 ? rwg_free_f32_kernel<6> : (nreg == 1 ? rwg_free_f32_kernel<1> : rwg_free_f32_kernel<0>);
       if (int rc = ensure_dyn_smem((const void*)kern, smem)) return rc;
       const int tok = prof_begin(st, "rwg_free", units * nr);
