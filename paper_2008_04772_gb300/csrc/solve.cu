@@ -705,6 +705,7 @@ struct BiArgs {
   double tol2;       // tol^2
   double* bnorm2;    // [nsys]
   int lpr;           // lanes per (row, system)
+  int three;         // three passes per iteration (many systems): p_k stored before v_k = G p_k
   GridBar* bar;      // barrier state of the cooperative launch
   int* err;          // sticky: set when a barrier wait gave up
 };
@@ -905,12 +906,16 @@ __device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typena
 // K1 of iteration k (parity P = k & 1): finish step k-1 row by row (s = r -
 // alpha v, r_k = s - omega t, x += alpha p + omega s) and form p_k = r_k +
 // beta (p_{k-1} - omega v_{k-1}) and v_k = G p_k, the gathered p_k rebuilt
-// from the step k-1 vectors; sums r0^H v_k and |r_k|^2.
+// from the step k-1 vectors; sums r0^H v_k and |r_k|^2 (mode 0). With many
+// systems the rebuild (four loads per gathered entry and system) costs more
+// than a grid barrier, so the phase runs in two passes: mode 1 does the row
+// updates and stores p_k (sum |r_k|^2), mode 2, after a barrier, forms v_k =
+// G p_k from the stored p_k (sum r0^H v_k).
 template <typename R>
-__device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState* st, double* red) {
+__device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState* st, double* red, int mode) {
   const BiLayout L(A.nsys, A.lpr);
   const int P = k & 1, ns = L.ns;
-  if (threadIdx.x < ns) {
+  if (threadIdx.x < ns && mode != 2) {
     const int s = threadIdx.x;
     BiState& z = st[s];
     if (k == 0) {
@@ -968,6 +973,23 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
   };
   using D = typename DotT<R>::T;
   D part[3] = {0, 0, 0};
+  if (mode == 1) {
+    // row updates only: x, r_k and p_k of this thread's own rows
+    if (act && L.sub == 0)
+      for (int64_t i = L.base() + L.r0; i < A.n; i += L.step()) {
+        const int64_t kk = i * ns + s;
+        typename CT<R>::T rk, pk, sk;
+        rp(i, rk, pk, sk);
+        const auto p1 = pprev[kk], xi = A.x[kk];
+        A.x[kk] = {xi.x + (aR * p1.x - aI * p1.y) + (oR * sk.x - oI * sk.y),
+                   xi.y + (aR * p1.y + aI * p1.x) + (oR * sk.y + oI * sk.x)};
+        rcur[kk] = rk;
+        pcur[kk] = pk;
+        part[2] += (D)rk.x * rk.x + (D)rk.y * rk.y;
+      }
+    system_accumulate<3, D>(L, part, red, A.acc, A.nsys, P, 0);
+    return;
+  }
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
@@ -983,19 +1005,35 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
           cj[u] = q < q1 ? A.col[q] : -1;
           gv[u] = q < q1 ? A.val[q] : R(0);
         }
+        if (mode == 2) {
 #pragma unroll
-        for (int u = 0; u < BI_W; ++u)
-          if (cj[u] >= 0) {
-            typename CT<R>::T rk, pk, sk;
-            rp(cj[u], rk, pk, sk);
-            vr += gv[u] * pk.x;
-            vi += gv[u] * pk.y;
-          }
+          for (int u = 0; u < BI_W; ++u)
+            if (cj[u] >= 0) {
+              const auto pk = pcur[(int64_t)cj[u] * ns + s];
+              vr += gv[u] * pk.x;
+              vi += gv[u] * pk.y;
+            }
+        } else {
+#pragma unroll
+          for (int u = 0; u < BI_W; ++u)
+            if (cj[u] >= 0) {
+              typename CT<R>::T rk, pk, sk;
+              rp(cj[u], rk, pk, sk);
+              vr += gv[u] * pk.x;
+              vi += gv[u] * pk.y;
+            }
+        }
       }
     }
     vr = lane_group_sum(L, vr);
     vi = lane_group_sum(L, vi);
-    if (live && L.sub == 0) {
+    if (live && L.sub == 0 && mode == 2) {
+      const int64_t kk = i * ns + s;
+      vcur[kk] = {vr, vi};
+      const auto h = A.rh[kk];
+      part[0] += (D)(h.x * vr + h.y * vi);   // conj(r0) v
+      part[1] += (D)(h.x * vi - h.y * vr);
+    } else if (live && L.sub == 0) {
       const int64_t kk = i * ns + s;
       typename CT<R>::T rk, pk, sk;
       rp(i, rk, pk, sk);
@@ -1201,7 +1239,13 @@ __global__ void __launch_bounds__(256) bicg_persistent(BiArgs<R> A, const typena
   int k = 0;
   bool running = true;
   for (; k < maxit; ++k) {
-    bicg_phase_k1<R>(A, k, st, red);
+    if (A.three) {
+      bicg_phase_k1<R>(A, k, st, red, 1);
+      if (!grid_sync(A.bar, A.err, gen)) return;
+      bicg_phase_k1<R>(A, k, st, red, 2);
+    } else {
+      bicg_phase_k1<R>(A, k, st, red, 0);
+    }
     if (!grid_sync(A.bar, A.err, gen)) return;
     if (!bicg_phase_k2<R>(A, k, st, red)) { running = false; break; }
     if (!grid_sync(A.bar, A.err, gen)) return;
@@ -1317,6 +1361,7 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   A.err = d_err;
   A.tol2 = tol * tol;
   A.lpr = lpr;
+  A.three = nsys >= 16 ? 1 : 0;
   const int tok = prof_begin(st, "bicgstab", 0.0);
   CAL_TRY_CUDA(cudaMemsetAsync(d_acc, 0, acc_bytes(), st));
   int mi = maxit;
