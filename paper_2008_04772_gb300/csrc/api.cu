@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <condition_variable>
 #include <cstring>
 #include <memory>
 #include <numeric>
@@ -391,7 +392,7 @@ int cached_unit_lists(const Space& sp, int scat, double chi, int nreg, int preci
   const bool dense = std::isinf(chi);
   const Space::NearPattern* np = dense ? nullptr : &cached_near_pattern(sp, scat, chi);
   const bool fp32 = precision == CAL_FP32;
-  std::lock_guard<std::mutex> lk(sp.static_mu);
+  std::lock_guard<std::mutex> lk(sp.unit_mu);
   for (auto& u : sp.unit_lists)
     if (u->scat == scat && u->chi == chi && u->nreg == nreg && u->owner == fp32) {
       CAL_TRY_CUDA(cudaStreamWaitEvent(st, u->done, 0));
@@ -411,9 +412,58 @@ int cached_unit_lists(const Space& sp, int scat, double chi, int nreg, int preci
   return CAL_OK;
 }
 
+// Kernel arguments of one allocated block.
+static AssembleArgs block_args(const Op& op, double kr, double ki, const Space& sp, int scat, int nreg, int nsing,
+                               int precision, bool sing32) {
+  AssembleArgs a{};
+  a.sp = &sp;
+  a.scat = scat;
+  a.kr = kr;
+  a.ki = ki;
+  a.want = op.op_mask;
+  a.nreg = nreg;
+  a.nsing = nsing;
+  a.precision = precision;
+  a.sing32 = sing32;
+  a.format = op.format;
+  a.row_off = op.row_offset;
+  a.ld = op.cols;
+  a.rowptr = op.d_rowptr;
+  a.col = op.d_col;
+  a.S = op.d_S;
+  a.C = op.d_C;
+  a.stream = op.ctx->stream;
+  return a;
+}
+
+// The regular (non-touching) pairs of an allocated block.
+static int assemble_regular(Ctx& ctx, const Op& op, double kr, double ki, const Space& sp, int scat, double chi,
+                            int nreg, int nsing, int precision, bool sing32) {
+  const AssembleArgs a = block_args(op, kr, ki, sp, scat, nreg, nsing, precision, sing32);
+  int rc = CAL_OK;
+  if (sp.kind == CAL_RWG) {
+    rc = launch_rwg_regular(a);
+  } else {
+    // the work units are the same for every wavenumber: built once per space
+    Space::UnitLists* L = nullptr;
+    if ((rc = cached_unit_lists(sp, scat, chi, nreg, precision, a.stream, &L))) return rc;
+    if (L->nunits > 0)
+      rc = launch_bc_regular_units(a, L->d_units, L->nunits, L->d_wlist, L->max_cell, ctx.n_sm,
+                                   L->pairs * nreg * nreg);
+  }
+  if (rc) return rc;
+  CAL_TRY_CUDA(cudaGetLastError());
+  return CAL_OK;
+}
+
 // Assemble S and/or C of one block (scat = -1: union; else scatterer scat).
+// parts: 1 allocates the zeroed block and enqueues its touching (singular)
+// pairs; 2 enqueues the regular pairs of the block that part 1 left in out,
+// given the same arguments; 3 does both. Every kernel adds into the zeroed
+// block, so the parts may run in either order: a caller can enqueue part 1
+// of several blocks while the work units of part 2 are still being built.
 int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, int scat, double chi,
-                   int nreg, int nsing, int precision, std::unique_ptr<Op>& out) {
+                   int nreg, int nsing, int precision, std::unique_ptr<Op>& out, int parts = 3) {
   const Mesh& m = *sp.mesh;
   if (scat >= m.M) return fail(CAL_EINVAL, "assemble: scatterer %d out of range", scat);
   if (!(want & 3)) return fail(CAL_EINVAL, "assemble: op_mask must contain CAL_OP_S or CAL_OP_C");
@@ -425,6 +475,10 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
     return fail(CAL_EINVAL, "assemble: wavenumber must be finite and non-zero");
   int rc = set_quadrature_tables(nreg, nsing);
   if (rc) return rc;
+  if (!(parts & 1)) {
+    if (!out || out->op_mask != want) return fail(CAL_EINVAL, "assemble: no block from the first part");
+    return assemble_regular(ctx, *out, kr, ki, sp, scat, chi, nreg, nsing, precision, sing32);
+  }
   auto op = std::make_unique<Op>();
   op->ctx = &ctx;
   op->op_mask = want;
@@ -467,37 +521,10 @@ int assemble_block(Ctx& ctx, int want, double kr, double ki, const Space& sp, in
       CAL_TRY_CUDA(cudaMemcpyAsync(op->d_col, op->h_col.data(), op->h_col.size() * sizeof(int),
                                    cudaMemcpyHostToDevice, st));
   }
-  AssembleArgs a{};
-  a.sp = &sp;
-  a.scat = scat;
-  a.kr = kr;
-  a.ki = ki;
-  a.want = want;
-  a.nreg = nreg;
-  a.nsing = nsing;
-  a.precision = precision;
-  a.sing32 = sing32;
-  a.format = op->format;
-  a.row_off = op->row_offset;
-  a.ld = op->cols;
-  a.rowptr = op->d_rowptr;
-  a.col = op->d_col;
-  a.S = op->d_S;
-  a.C = op->d_C;
-  a.stream = st;
-  if (sp.kind == CAL_RWG) {
-    if ((rc = launch_rwg_regular(a))) return rc;
-  } else {
-    // the work units are the same for every wavenumber: built once per space
-    Space::UnitLists* L = nullptr;
-    if ((rc = cached_unit_lists(sp, scat, chi, nreg, precision, st, &L))) return rc;
-    if (L->nunits > 0)
-      rc = launch_bc_regular_units(a, L->d_units, L->nunits, L->d_wlist, L->max_cell, ctx.n_sm,
-                                   L->pairs * nreg * nreg);
-    if (rc) return rc;
-  }
-  if ((rc = launch_singular(a))) return rc;
+  if ((rc = launch_singular(block_args(*op, kr, ki, sp, scat, nreg, nsing, precision, sing32)))) return rc;
   CAL_TRY_CUDA(cudaGetLastError());
+  if ((parts & 2) && (rc = assemble_regular(ctx, *op, kr, ki, sp, scat, chi, nreg, nsing, precision, sing32)))
+    return rc;
   out = std::move(op);
   return CAL_OK;
 }
@@ -1648,7 +1675,22 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     int rc = CAL_OK;
     std::string msg;
     double seconds = 0.0;
+    std::mutex mu;
+    std::condition_variable cv;
+    bool built = false;  // the space is built (its work units may still be in progress)
     ~BcBuild() { if (th.joinable()) th.join(); }
+    void set_built() {
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        built = true;
+      }
+      cv.notify_all();
+    }
+    int wait_built() {
+      std::unique_lock<std::mutex> lk(mu);
+      cv.wait(lk, [this] { return built; });
+      return rc ? fail(rc, "%s", msg.c_str()) : CAL_OK;
+    }
     int join() {
       if (th.joinable()) th.join();
       return rc ? fail(rc, "%s", msg.c_str()) : CAL_OK;
@@ -1659,8 +1701,9 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     Space* bcs = P.bc.get();
     Mesh* mh = &mesh->impl;
     // P's blocks (one per scatterer, exterior and interior alike) need the work
-    // units of the BC regular-pair kernels: the same thread builds them, on a
-    // stream of its own, while this thread's A assembly runs on the device
+    // units of the BC regular-pair kernels: once the space is built, the same
+    // thread builds them, on a stream of its own, while the device runs A and
+    // the touching pairs of P that this thread enqueues meanwhile
     const bool prebuild = o.discretisation == 0;
     const double chi_units =
         (o.aca_nu_P > 0 || std::isinf(o.near_cutoff_P)) ? INFINITY : o.near_cutoff_P * mesh->impl.h;
@@ -1670,6 +1713,7 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
       const double tb = now();
       bcb.rc = build_bc(*bcs, *mh);
       if (bcb.rc) bcb.msg = last_error();
+      bcb.set_built();
       if (!bcb.rc && prebuild && set_quadrature_tables(nreg_units, 1) == CAL_OK) {
         // a failure here only leaves the lists to the assembly itself
         cudaStream_t ps = nullptr;
@@ -1723,7 +1767,7 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
   CAL_TRY_CUDA(cudaEventRecord(ev.e[1], st));
   if (need_bc) {
     const double tb = now();
-    if ((rc = bcb.join()) || (rc = upload_space(*P.bc, st))) return rc;
+    if ((rc = bcb.wait_built()) || (rc = upload_space(*P.bc, st))) return rc;
     t_setup_host += now() - tb;  // the part of the BC build A's enqueue did not hide
   }
   CAL_TRY_CUDA(cudaEventRecord(ev.e[2], st));
@@ -1753,7 +1797,7 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     };
     if (P.mixed) {
       // S on BC (union and per scatterer) and C between RWG and BC, A's rules
-      if ((rc = P.build_rwgb(st))) return rc;
+      if ((rc = bcb.join()) || (rc = P.build_rwgb(st))) return rc;
       if ((rc = assemble_block(ctx->impl, 1, k_ext, 0.0, *P.bc, -1, INFINITY, o.q_regular_A, o.q_singular_A,
                                CAL_FP64, P.Sb_ext)))
         return rc;
@@ -1786,22 +1830,20 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
         bytes_P += (int64_t)(bm * 2 + P.Sb_int[m]->nnz * 16);
       }
     }
-    for (int m = 0; m < P.M && !P.mixed; ++m) {
-      if (ext && ((rc = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P,
-                                       o.q_singular_P, aprec, P.P_ext[m])) ||
-                  (rc = to_hmat(P.P_ext[m]))))
-        return rc;
-      if (in && ((rc = assemble_block(ctx->impl, want, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, chi,
-                                      o.q_regular_P, o.q_singular_P, aprec, P.P_int[m])) ||
-                 (rc = to_hmat(P.P_int[m]))))
-        return rc;
-      for (auto* op : {P.P_ext[m].get(), P.P_int[m].get()})
-        if (op)
-          bytes_P += op->hmat ? op->hmat->stored * (int64_t)esz
-                              : op->nnz * esz * ((want & 2) ? 2 : 1) +
-                                    (op->format == CAL_CSR ? (int64_t)(op->h_rowptr.size() * 8 + op->h_col.size() * 4)
-                                                           : 0);
-    }
+    // the touching pairs of every block and the Gram matrix need the space
+    // only: the device runs them while the other thread finishes the work units
+    auto assemble_P = [&](int m, int parts) -> int {
+      int r = CAL_OK;
+      if (ext && (r = assemble_block(ctx->impl, want, k_ext, 0.0, *P.bc, m, chi, o.q_regular_P, o.q_singular_P,
+                                     aprec, P.P_ext[m], parts)))
+        return r;
+      if (in && (r = assemble_block(ctx->impl, want, P.k_m[m].real(), P.k_m[m].imag(), *P.bc, m, chi,
+                                    o.q_regular_P, o.q_singular_P, aprec, P.P_int[m], parts)))
+        return r;
+      return CAL_OK;
+    };
+    for (int m = 0; m < P.M && !P.mixed; ++m)
+      if ((rc = assemble_P(m, 1))) return rc;
     // Gram G (rows RWG, cols BC) and its transpose
     std::vector<int64_t> rp, rpT;
     std::vector<int> col, colT;
@@ -1832,6 +1874,16 @@ int cal_problem_create(cal_ctx* ctx, cal_mesh* mesh, double k_ext, const double*
     if ((rc = launch_gram(*P.rwg, *P.bc, P.d_grp, P.d_gcol, P.d_grpT, P.d_gcolT, P.d_gval, P.d_gvalT, st)))
       return rc;
     bytes_G = 2 * ((n + 1) * 8 + P.gnnz * (4 + 8));
+    if ((rc = bcb.join())) return rc;
+    for (int m = 0; m < P.M && !P.mixed; ++m) {
+      if ((rc = assemble_P(m, 2)) || (rc = to_hmat(P.P_ext[m])) || (rc = to_hmat(P.P_int[m]))) return rc;
+      for (auto* op : {P.P_ext[m].get(), P.P_int[m].get()})
+        if (op)
+          bytes_P += op->hmat ? op->hmat->stored * (int64_t)esz
+                              : op->nnz * esz * ((want & 2) ? 2 : 1) +
+                                    (op->format == CAL_CSR ? (int64_t)(op->h_rowptr.size() * 8 + op->h_col.size() * 4)
+                                                           : 0);
+    }
   }
   if ((rc = P.build_combo_P(st))) return rc;
   if (P.cA.C) bytes_A += 3 * P.cA.rows * P.cA.rows * 8;

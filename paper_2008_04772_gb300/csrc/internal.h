@@ -192,7 +192,9 @@ struct Space {
   // BC regular-pair work units (a test cell and a run of trial cells) of one
   // scatterer, cutoff, rule and kernel: built and uploaded by the first
   // assembly that asks, read by the later ones (a problem's exterior and
-  // interior blocks take the same lists); guarded by static_mu
+  // interior blocks take the same lists); guarded by unit_mu, which is held
+  // while a list is built (the singular launches' static_mu is not)
+  mutable std::mutex unit_mu;
   struct UnitLists {
     int scat = 0, nreg = 0;
     double chi = 0;
