@@ -1183,40 +1183,50 @@ __global__ void real_convert_kernel(const double* __restrict__ a, R* __restrict_
   if (i < n) b[i] = (R)a[i];
 }
 
-// Grid-wide barrier of a cooperative launch (every block resident). Thread 0
-// of each block arrives on a counter; the last arrival resets it and moves the
-// generation on. Every wait is bounded: after GRID_BAR_SPINS polls the block
-// raises the error word (and the solver's sticky error), and every block
-// leaves at its next barrier.
+// Grid-wide barrier of a cooperative launch (every block resident). The
+// barrier state is zeroed before the launch; count only grows, so barrier g
+// (1-based) is passed once count reaches g x gridDim.x. Thread 0 of each block
+// arrives with an acquire-release add (its block's writes, ordered before it
+// by the block barrier, are released; the last arrival acquires everyone
+// else's) and polls with acquire loads: no reset and no second word on the
+// critical path. Every wait is bounded: after GRID_BAR_SPINS polls the block
+// raises the error word (and the solver's sticky error) and leaves; a block
+// that sees the error word while it waits leaves too.
 constexpr long long GRID_BAR_SPINS = 1LL << 22;
+
+__device__ __forceinline__ unsigned atom_add_acq_rel_gpu(unsigned* p, unsigned v) {
+  unsigned old;
+  asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ int ld_relaxed_gpu(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
 
 __device__ __forceinline__ bool grid_sync(GridBar* gb, int* sticky, unsigned& gen) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
     int ok = 1;
-    const unsigned want = gen + 1;
-    __threadfence();
-    if (atomicAdd(&gb->count, 1u) == gridDim.x - 1) {
-      atomicExch(&gb->count, 0u);
-      __threadfence();
-      atomicExch(&gb->gen, want);
-    } else {
-      const volatile unsigned* g = &gb->gen;
-      const volatile int* e = &gb->err;
-      long long spins = 0;
-      while (*g != want) {
-        if (*e || ++spins > GRID_BAR_SPINS) {
-          atomicExch(&gb->err, 1);
-          atomicExch(sticky, 1);
-          ok = 0;
-          break;
-        }
-        __nanosleep(32);
+    const unsigned want = (gen + 1) * gridDim.x;
+    unsigned c = atom_add_acq_rel_gpu(&gb->count, 1u) + 1u;
+    long long spins = 0;
+    while (c < want) {
+      if (((++spins & 255) == 0 && ld_relaxed_gpu(&gb->err)) || spins > GRID_BAR_SPINS) {
+        atomicExch(&gb->err, 1);
+        atomicExch(sticky, 1);
+        ok = 0;
+        break;
       }
+      c = ld_acquire_gpu(&gb->count);
     }
-    __threadfence();
-    if (*(const volatile int*)&gb->err) ok = 0;
     s_ok = ok;
   }
   __syncthreads();

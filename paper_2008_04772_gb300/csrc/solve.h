@@ -58,10 +58,11 @@ int combine_blocks(const void* Sa, const void* Ca, int64_t rows, std::complex<do
 int grid_barrier_check(int skip_block, int* status, cudaStream_t st);
 
 // BiCGStab on the real sparse Gram matrix, nsys complex systems sharing it
-// grid-wide barrier state of a cooperative launch (zeroed before the launch)
+// grid-wide barrier state of a cooperative launch (zeroed before the launch):
+// count of arrivals since the launch, the error word of a wait that gave up
 struct GridBar {
-  unsigned count, gen;
-  int err, pad;
+  unsigned count, pad0;
+  int err, pad1;
 };
 
 template <typename R>
