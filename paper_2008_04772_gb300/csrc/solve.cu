@@ -874,6 +874,75 @@ __device__ __forceinline__ void system_accumulate(const BiLayout& L, const T (&p
 template <typename R> struct DotT { using T = double; };
 template <> struct DotT<float> { using T = float; };
 
+// The Gram matrix does not change during a solve: when one sweep of the grid
+// covers every row (each thread has at most one row) and the row has at most
+// BI_W entries per lane, the lane keeps its entries in registers for the whole
+// solve, and no pass reloads the row pointers, columns and values. The kernel
+// with the cache is a separate instance (more registers, two blocks per SM);
+// the float32 one without keeps three blocks per SM for solves of many rows.
+template <typename R>
+struct RowCache {
+  int cj[BI_W];
+  R gv[BI_W];
+  bool ok;
+};
+
+template <typename R>
+__device__ __forceinline__ void row_cache_load(const BiArgs<R>& A, RowCache<R>& rc) {
+  const BiLayout L(A.nsys, A.lpr);
+  const int64_t i = L.base() + L.r0;
+  rc.ok = false;
+#pragma unroll
+  for (int u = 0; u < BI_W; ++u) {
+    rc.cj[u] = -1;
+    rc.gv[u] = R(0);
+  }
+  if (L.step() < A.n || i >= A.n) return;
+  const int64_t q0 = A.rowptr[i], q1 = A.rowptr[i + 1];
+  if (q1 - q0 > (int64_t)BI_W * L.lpr) return;
+#pragma unroll
+  for (int u = 0; u < BI_W; ++u) {
+    const int64_t q = q0 + L.sub + (int64_t)u * L.lpr;
+    if (q < q1) {
+      rc.cj[u] = A.col[q];
+      rc.gv[u] = A.val[q];
+    }
+  }
+  rc.ok = true;
+}
+
+// (vr, vi) += this lane's share of sum_j g_ij f(j) over row i: from the
+// register cache when it holds the row, else loaded BI_W entries at a time
+template <typename R, typename F>
+__device__ __forceinline__ void row_gather(const BiArgs<R>& A, const BiLayout& L, const RowCache<R>& rc, int64_t i,
+                                           F f, R& vr, R& vi) {
+  auto take = [&](const int (&cj)[BI_W], const R (&gv)[BI_W]) {
+#pragma unroll
+    for (int u = 0; u < BI_W; ++u)
+      if (cj[u] >= 0) {
+        const auto w = f(cj[u]);
+        vr += gv[u] * w.x;
+        vi += gv[u] * w.y;
+      }
+  };
+  if (rc.ok) {
+    take(rc.cj, rc.gv);
+    return;
+  }
+  const int64_t q1 = A.rowptr[i + 1];
+  for (int64_t qb = A.rowptr[i] + L.sub; qb < q1; qb += (int64_t)BI_W * L.lpr) {
+    int cj[BI_W];
+    R gv[BI_W];
+#pragma unroll
+    for (int u = 0; u < BI_W; ++u) {
+      const int64_t q = qb + (int64_t)u * L.lpr;
+      cj[u] = q < q1 ? A.col[q] : -1;
+      gv[u] = q < q1 ? A.val[q] : R(0);
+    }
+    take(cj, gv);
+  }
+}
+
 // per-block step state of each system (shared memory; the same in every block)
 struct BiState {
   double rho_r, rho_i;  // rho_k = r0^H r_k
@@ -912,7 +981,8 @@ __device__ __forceinline__ void bicg_phase_init(const BiArgs<R>& A, const typena
 // updates and stores p_k (sum |r_k|^2), mode 2, after a barrier, forms v_k =
 // G p_k from the stored p_k (sum r0^H v_k).
 template <typename R>
-__device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState* st, double* red, int mode) {
+__device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, const RowCache<R>& rc, int k, BiState* st,
+                                              double* red, int mode) {
   const BiLayout L(A.nsys, A.lpr);
   const int P = k & 1, ns = L.ns;
   if (threadIdx.x < ns && mode != 2) {
@@ -962,14 +1032,17 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
   auto* pcur = P ? A.p1 : A.p0;
   const auto* vprev = P ? A.v0 : A.v1;
   auto* vcur = P ? A.v1 : A.v0;
-  // r_k and p_k at column j from step k-1 vectors
-  auto rp = [&](int64_t j, typename CT<R>::T& rk, typename CT<R>::T& pk, typename CT<R>::T& sk) {
-    const int64_t kk = j * ns + s;
-    const auto r1 = rprev[kk], v1 = vprev[kk], t1 = A.t[kk], p1 = pprev[kk];
+  using V = typename CT<R>::T;
+  // r_k and p_k from the step k-1 entries r, v, t, p of one row
+  auto rp_of = [&](V r1, V v1, V t1, V p1, V& rk, V& pk, V& sk) {
     sk = {r1.x - (aR * v1.x - aI * v1.y), r1.y - (aR * v1.y + aI * v1.x)};
     rk = {sk.x - (oR * t1.x - oI * t1.y), sk.y - (oR * t1.y + oI * t1.x)};
     const R dx = p1.x - (oR * v1.x - oI * v1.y), dy = p1.y - (oR * v1.y + oI * v1.x);
     pk = {rk.x + bR * dx - bI * dy, rk.y + bR * dy + bI * dx};
+  };
+  auto rp = [&](int64_t j, V& rk, V& pk, V& sk) {
+    const int64_t kk = j * ns + s;
+    rp_of(rprev[kk], vprev[kk], A.t[kk], pprev[kk], rk, pk, sk);
   };
   using D = typename DotT<R>::T;
   D part[3] = {0, 0, 0};
@@ -993,57 +1066,45 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
+    const bool own = live && L.sub == 0;
+    const int64_t kk = i * ns + s;
+    // the row's own entries, loaded before the gathers so that both are in flight
+    V r1{}, v1{}, t1{}, p1{}, xi{}, h{};
+    if (own) {
+      h = A.rh[kk];
+      if (mode != 2) {
+        r1 = rprev[kk];
+        v1 = vprev[kk];
+        t1 = A.t[kk];
+        p1 = pprev[kk];
+        xi = A.x[kk];
+      }
+    }
     R vr = 0, vi = 0;
     if (live) {
-      const int64_t q1 = A.rowptr[i + 1];
-      for (int64_t qb = A.rowptr[i] + L.sub; qb < q1; qb += (int64_t)BI_W * L.lpr) {
-        int cj[BI_W];
-        R gv[BI_W];
-#pragma unroll
-        for (int u = 0; u < BI_W; ++u) {
-          const int64_t q = qb + (int64_t)u * L.lpr;
-          cj[u] = q < q1 ? A.col[q] : -1;
-          gv[u] = q < q1 ? A.val[q] : R(0);
-        }
-        if (mode == 2) {
-#pragma unroll
-          for (int u = 0; u < BI_W; ++u)
-            if (cj[u] >= 0) {
-              const auto pk = pcur[(int64_t)cj[u] * ns + s];
-              vr += gv[u] * pk.x;
-              vi += gv[u] * pk.y;
-            }
-        } else {
-#pragma unroll
-          for (int u = 0; u < BI_W; ++u)
-            if (cj[u] >= 0) {
-              typename CT<R>::T rk, pk, sk;
-              rp(cj[u], rk, pk, sk);
-              vr += gv[u] * pk.x;
-              vi += gv[u] * pk.y;
-            }
-        }
-      }
+      if (mode == 2)
+        row_gather<R>(A, L, rc, i, [&](int j) { return pcur[(int64_t)j * ns + s]; }, vr, vi);
+      else
+        row_gather<R>(A, L, rc, i, [&](int j) {
+          V rk, pk, sk;
+          rp(j, rk, pk, sk);
+          return pk;
+        }, vr, vi);
     }
     vr = lane_group_sum(L, vr);
     vi = lane_group_sum(L, vi);
-    if (live && L.sub == 0 && mode == 2) {
-      const int64_t kk = i * ns + s;
+    if (own && mode == 2) {
       vcur[kk] = {vr, vi};
-      const auto h = A.rh[kk];
       part[0] += (D)(h.x * vr + h.y * vi);   // conj(r0) v
       part[1] += (D)(h.x * vi - h.y * vr);
-    } else if (live && L.sub == 0) {
-      const int64_t kk = i * ns + s;
-      typename CT<R>::T rk, pk, sk;
-      rp(i, rk, pk, sk);
-      const auto p1 = pprev[kk], xi = A.x[kk];
+    } else if (own) {
+      V rk, pk, sk;
+      rp_of(r1, v1, t1, p1, rk, pk, sk);
       A.x[kk] = {xi.x + (aR * p1.x - aI * p1.y) + (oR * sk.x - oI * sk.y),
                  xi.y + (aR * p1.y + aI * p1.x) + (oR * sk.y + oI * sk.x)};
       rcur[kk] = rk;
       pcur[kk] = pk;
       vcur[kk] = {vr, vi};
-      const auto h = A.rh[kk];
       part[0] += (D)(h.x * vr + h.y * vi);   // conj(r0) v
       part[1] += (D)(h.x * vi - h.y * vr);
       part[2] += (D)rk.x * rk.x + (D)rk.y * rk.y;
@@ -1057,7 +1118,8 @@ __device__ __forceinline__ void bicg_phase_k1(const BiArgs<R>& A, int k, BiState
 // r0^H s, r0^H t. Returns false (in every block alike) when no system is
 // active any more.
 template <typename R>
-__device__ __forceinline__ bool bicg_phase_k2(const BiArgs<R>& A, int k, BiState* st, double* red) {
+__device__ __forceinline__ bool bicg_phase_k2(const BiArgs<R>& A, const RowCache<R>& rc, int k, BiState* st,
+                                              double* red) {
   const BiLayout L(A.nsys, A.lpr);
   const int P = k & 1, ns = L.ns;
   if (threadIdx.x < ns) {
@@ -1094,33 +1156,22 @@ __device__ __forceinline__ bool bicg_phase_k2(const BiArgs<R>& A, int k, BiState
   for (int64_t i0 = L.base(); i0 < A.n; i0 += L.step()) {
     const int64_t i = i0 + L.r0;
     const bool live = act && i < A.n;
-    R tr = 0, ti = 0;
-    if (live) {
-      const int64_t q1 = A.rowptr[i + 1];
-      for (int64_t qb = A.rowptr[i] + L.sub; qb < q1; qb += (int64_t)BI_W * L.lpr) {
-        int cj[BI_W];
-        R gv[BI_W];
-#pragma unroll
-        for (int u = 0; u < BI_W; ++u) {
-          const int64_t q = qb + (int64_t)u * L.lpr;
-          cj[u] = q < q1 ? A.col[q] : -1;
-          gv[u] = q < q1 ? A.val[q] : R(0);
-        }
-#pragma unroll
-        for (int u = 0; u < BI_W; ++u)
-          if (cj[u] >= 0) {
-            const auto sc2 = sj(cj[u]);
-            tr += gv[u] * sc2.x;
-            ti += gv[u] * sc2.y;
-          }
-      }
+    const bool own = live && L.sub == 0;
+    const int64_t kk = i * ns + s;
+    // the row's own entries, loaded before the gathers so that both are in flight
+    typename CT<R>::T vo{}, ro{}, h{};
+    if (own) {
+      vo = vcur[kk];
+      ro = rcur[kk];
+      h = A.rh[kk];
     }
+    R tr = 0, ti = 0;
+    if (live) row_gather<R>(A, L, rc, i, sj, tr, ti);
     tr = lane_group_sum(L, tr);
     ti = lane_group_sum(L, ti);
-    if (live && L.sub == 0) {
-      const int64_t kk = i * ns + s;
+    if (own) {
       A.t[kk] = {tr, ti};
-      const auto si = sj(i), h = A.rh[kk];
+      const typename CT<R>::T si{ro.x - (aR * vo.x - aI * vo.y), ro.y - (aR * vo.y + aI * vo.x)};
       part[0] += (D)(tr * si.x + ti * si.y);   // conj(t) s
       part[1] += (D)(tr * si.y - ti * si.x);
       part[2] += (D)(tr * tr + ti * ti);
@@ -1238,26 +1289,30 @@ __device__ __forceinline__ bool grid_sync(GridBar* gb, int* sticky, unsigned& ge
 // then K1 and K2 per iteration) separated by grid barriers instead of kernel
 // boundaries, and the loop left as soon as every system has converged. The
 // dynamic shared memory holds the reduction scratch and the BiState array.
-template <typename R>
-__global__ void __launch_bounds__(256) bicg_persistent(BiArgs<R> A, const typename CT<R>::T* __restrict__ b,
-                                                       typename CT<R>::T* __restrict__ out, int maxit) {
+template <typename R, bool CACHE>
+__global__ void __launch_bounds__(256, (CACHE || sizeof(R) == 8) ? 2 : 3)
+    bicg_persistent(BiArgs<R> A, const typename CT<R>::T* __restrict__ b, typename CT<R>::T* __restrict__ out,
+                    int maxit) {
   extern __shared__ double red[];
   BiState* st = reinterpret_cast<BiState*>(red + 7 * blockDim.x);
   unsigned gen = 0;
+  RowCache<R> rc;
+  if constexpr (CACHE) row_cache_load<R>(A, rc);
+  else rc.ok = false;
   bicg_phase_init<R>(A, b, red);
   if (!grid_sync(A.bar, A.err, gen)) return;
   int k = 0;
   bool running = true;
   for (; k < maxit; ++k) {
     if (A.three) {
-      bicg_phase_k1<R>(A, k, st, red, 1);
+      bicg_phase_k1<R>(A, rc, k, st, red, 1);
       if (!grid_sync(A.bar, A.err, gen)) return;
-      bicg_phase_k1<R>(A, k, st, red, 2);
+      bicg_phase_k1<R>(A, rc, k, st, red, 2);
     } else {
-      bicg_phase_k1<R>(A, k, st, red, 0);
+      bicg_phase_k1<R>(A, rc, k, st, red, 0);
     }
     if (!grid_sync(A.bar, A.err, gen)) return;
-    if (!bicg_phase_k2<R>(A, k, st, red)) { running = false; break; }
+    if (!bicg_phase_k2<R>(A, rc, k, st, red)) { running = false; break; }
     if (!grid_sync(A.bar, A.err, gen)) return;
   }
   if (running && k > 0) bicg_phase_last<R>(A, k - 1, st);
@@ -1334,9 +1389,14 @@ int GramSolver<R>::init(const int64_t* rowptr, const int* col, const double* val
   int dev = 0, n_sm = 0, per_sm = 0;
   CAL_TRY_CUDA(cudaGetDevice(&dev));
   CAL_TRY_CUDA(cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev));
-  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicg_persistent<R>, threads, smem));
-  if (per_sm < 1) return fail(CAL_ECUDA, "Gram solve: the persistent kernel does not fit on an SM");
   const int64_t row_blocks = (n + rpb - 1) / rpb;
+  // the instance that keeps the row entries in registers when its resident
+  // blocks cover every row in one sweep, else the one with more blocks
+  CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicg_persistent<R, true>, threads, smem));
+  cached = per_sm >= 1 && row_blocks <= (int64_t)n_sm * std::min(per_sm, 8);
+  if (!cached)
+    CAL_TRY_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, bicg_persistent<R, false>, threads, smem));
+  if (per_sm < 1) return fail(CAL_ECUDA, "Gram solve: the persistent kernel does not fit on an SM");
   grid = (unsigned)std::max<int64_t>(1, std::min<int64_t>(row_blocks, (int64_t)n_sm * std::min(per_sm, 8)));
   return CAL_OK;
 }
@@ -1376,8 +1436,8 @@ int GramSolver<R>::solve(const C* b, C* out, cudaStream_t st) {
   CAL_TRY_CUDA(cudaMemsetAsync(d_acc, 0, acc_bytes(), st));
   int mi = maxit;
   void* args[] = {(void*)&A, (void*)&b, (void*)&out, (void*)&mi};
-  const cudaError_t e = cudaLaunchCooperativeKernel((const void*)bicg_persistent<R>, dim3(grid), dim3(threads), args,
-                                                    smem, st);
+  const void* kern = cached ? (const void*)bicg_persistent<R, true> : (const void*)bicg_persistent<R, false>;
+  const cudaError_t e = cudaLaunchCooperativeKernel(kern, dim3(grid), dim3(threads), args, smem, st);
   prof_end(st, tok);
   note_launch();
   if (e != cudaSuccess) return fail(CAL_ECUDA, "Gram solve launch: %s", cudaGetErrorString(e));

@@ -81,6 +81,7 @@ struct GramSolver {
   int lpr = 1, rpb = 1, threads = 0;
   unsigned grid = 0;
   size_t smem = 0;
+  bool cached = false;  // one sweep covers the rows: the row entries stay in registers
   int init(const int64_t* rowptr, const int* col, const double* vals_dev, int64_t n, int nsys,
            int64_t nnz, double neg, double tol, int maxit, cudaStream_t st);
   // x = neg G^{-1} b for the nsys systems (b, out: [nsys][n]), one cooperative launch
