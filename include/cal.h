@@ -398,6 +398,14 @@ int cal_queue_submit(cal_queue* q, const cal_request* req, int64_t* ticket);
    is still pending or running; CAL_EINVAL for an unknown ticket. */
 int cal_queue_wait(cal_queue* q, int64_t ticket, double timeout_s, cal_request_result* res,
                    double* farfield);
+/* Request states of cal_queue_poll */
+#define CAL_REQ_PENDING 0  /* queued: not yet admitted (waits for HBM budget or a slot) */
+#define CAL_REQ_RUNNING 1  /* admitted: its batch is being assembled or solved        */
+#define CAL_REQ_DONE    2  /* finished: cal_queue_wait returns at once                */
+/* Non-blocking: *state = CAL_REQ_PENDING, CAL_REQ_RUNNING or CAL_REQ_DONE. The
+   ticket stays valid (only cal_queue_wait releases it); CAL_EINVAL for an
+   unknown or already released ticket. */
+int cal_queue_poll(cal_queue* q, int64_t ticket, int* state);
 int cal_queue_get_stats(cal_queue* q, cal_queue_stats* stats);
 /* Finishes the batches that are running, drops pending requests, frees the
    resident operators and the worker contexts. */

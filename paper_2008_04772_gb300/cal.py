@@ -23,6 +23,7 @@ OP_S, OP_C = 1, 2
 FP64, FP32, FP32_ALL = 1, 2, 3
 DENSE, CSR, HMAT = 1, 2, 3
 PRECOND = {"none": 0, "D": 1, "De": 2, "Di": 3, "Se": 4, "Si": 5}
+REQ_PENDING, REQ_RUNNING, REQ_DONE = 0, 1, 2
 
 _lib = None
 
@@ -156,6 +157,7 @@ def lib():
         "cal_queue_create": ([ctypes.c_int, ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(P)], ctypes.c_int),
         "cal_queue_submit": ([P, ctypes.POINTER(Request), ctypes.POINTER(i64)], ctypes.c_int),
         "cal_queue_wait": ([P, i64, d, ctypes.POINTER(RequestResult), P], ctypes.c_int),
+        "cal_queue_poll": ([P, i64, ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "cal_queue_get_stats": ([P, ctypes.POINTER(QueueStats)], ctypes.c_int),
         "cal_queue_destroy": ([P], None),
         "cal_request_footprint": ([ctypes.POINTER(Request), ctypes.POINTER(i64), ctypes.POINTER(i64)],
@@ -487,6 +489,12 @@ class Queue:
         self._shape.pop(ticket, None)
         ok = res.status in (OK, ENOTCONV)
         return res, (far if ok else None)
+
+    def poll(self, ticket: int) -> int:
+        """REQ_PENDING, REQ_RUNNING or REQ_DONE, without waiting."""
+        st = ctypes.c_int()
+        _check(lib().cal_queue_poll(self.h, ticket, ctypes.byref(st)))
+        return st.value
 
     def stats(self) -> QueueStats:
         out = QueueStats()

@@ -527,6 +527,18 @@ int cal_queue_wait(cal_queue* q, int64_t ticket, double timeout_s, cal_request_r
   return CAL_OK;
 }
 
+int cal_queue_poll(cal_queue* q, int64_t ticket, int* state) {
+  if (!q || !state) return fail(CAL_EINVAL, "cal_queue_poll: NULL argument");
+  std::lock_guard<std::mutex> lk(q->mu);
+  auto it = q->requests.find(ticket);
+  if (it == q->requests.end()) return fail(CAL_EINVAL, "cal_queue_poll: unknown ticket %lld", (long long)ticket);
+  const Request* r = it->second.get();
+  if (r->done) *state = CAL_REQ_DONE;
+  else if (std::find(q->pending.begin(), q->pending.end(), r) != q->pending.end()) *state = CAL_REQ_PENDING;
+  else *state = CAL_REQ_RUNNING;
+  return CAL_OK;
+}
+
 int cal_queue_get_stats(cal_queue* q, cal_queue_stats* stats) {
   if (!q || !stats) return fail(CAL_EINVAL, "cal_queue_get_stats: NULL argument");
   std::lock_guard<std::mutex> lk(q->mu);

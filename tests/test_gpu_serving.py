@@ -128,6 +128,29 @@ def test_queue_merges_pending_requests_of_one_problem(ctx, solo):
     q.close()
 
 
+def test_queue_poll_reports_states_without_waiting(ctx, solo):
+    """cal_queue_poll: a submitted request is pending or running, then done; a
+    done request's wait returns at once with its result, and the released
+    ticket is unknown to poll."""
+    import time
+    q = cal.Queue(0, slots=1)
+    t0, t1 = _submit(q, 1), _submit(q, 0)
+    states = {q.poll(t0), q.poll(t1)}
+    assert states <= {cal.REQ_PENDING, cal.REQ_RUNNING, cal.REQ_DONE}
+    deadline = time.monotonic() + 600
+    while q.poll(t1) != cal.REQ_DONE and time.monotonic() < deadline:
+        time.sleep(0.01)
+    assert q.poll(t1) == cal.REQ_DONE
+    r1, F1 = q.wait(t1, timeout=0)
+    assert r1.status == cal.OK and rel(F1, solo[0]) < FAR_TOL
+    with pytest.raises(cal.CalError) as e:
+        q.poll(t1)
+    assert e.value.code == cal.EINVAL
+    r0, F0 = q.wait(t0, timeout=600)
+    assert rel(F0, solo[1]) < FAR_TOL
+    q.close()
+
+
 def test_queue_keeps_operators_resident(ctx, solo):
     q = cal.Queue(0, slots=2)
     r1, F1 = q.wait(_submit(q, 0), timeout=600)
