@@ -1831,23 +1831,41 @@ int single_apply(const Op& op, const void* X, const void* x, void* y, int64_t nr
 // classical Gram–Schmidt with one reorthogonalisation, Givens rotations and
 // the triangular solve on the device.
 // ---------------------------------------------------------------------------
-__global__ void multi_dot_kernel(const double2* __restrict__ V, int64_t bV, int m,
-                                 const double2* __restrict__ w, int64_t n, double2* h, int64_t bh) {
-  // h[q][i] += V_q,i^H w_q for i < m; block-partial sums, one atomic per (block, i)
+// h[q][i] += V_q,i^H w_q for i < m. Each thread takes E elements of the column
+// (blockDim.x apart) and sums their products before the warp reduction: the
+// float64 shuffle adds, not the products, dominated at one element per thread
+// (float64 runs at 1/64 of the float32 rate here). Per basis vector the
+// block's sum goes to h with one atomic.
+template <int E>
+__global__ void __launch_bounds__(256) multi_dot_kernel(const double2* __restrict__ V, int64_t bV, int m,
+                                                        const double2* __restrict__ w, int64_t n, double2* h,
+                                                        int64_t bh) {
   __shared__ double sr[8][32], si[8][32];
   const int q = blockIdx.y;
   V += q * bV;
   w += q * n;
   h += q * bh;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double2 wk = k < n ? w[k] : double2{0, 0};
+  const int64_t k0 = (int64_t)blockIdx.x * blockDim.x * E + threadIdx.x;
+  double2 wk[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) {
+    const int64_t k = k0 + (int64_t)e * blockDim.x;
+    wk[e] = k < n ? w[k] : double2{0, 0};
+  }
   for (int i = 0; i < m; ++i) {
+    const double2* Vi = V + (size_t)i * n;
     double ar = 0, ai = 0;
-    if (k < n) {
-      const double2 v = V[(size_t)i * n + k];
-      ar = v.x * wk.x + v.y * wk.y;
-      ai = v.x * wk.y - v.y * wk.x;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const int64_t k = k0 + (int64_t)e * blockDim.x;
+      if (k < n) {
+        const double2 v = Vi[k];
+        ar = fma(v.x, wk[e].x, ar);
+        ar = fma(v.y, wk[e].y, ar);
+        ai = fma(v.x, wk[e].y, ai);
+        ai = fma(-v.y, wk[e].x, ai);
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -2002,9 +2020,18 @@ int gmres_cgs_step(const double2* V, int64_t bV, int64_t n, int j, double2* w, d
   CAL_TRY_CUDA(cudaMemsetAsync(h1, 0, nrhs * bh * sizeof(double2), st));
   CAL_TRY_CUDA(cudaMemsetAsync(h2, 0, nrhs * bh * sizeof(double2), st));
   for (int q = 0; q < nrhs; ++q) CAL_TRY_CUDA(cudaMemsetAsync(wn2 + q * bwn, 0, sizeof(double), st));
-  multi_dot_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, w, n, h1, bh);
+  // elements per thread of the dot products: as many as keep about four
+  // blocks per SM busy (one for short columns of a single right-hand side)
+  int dev = 0, n_sm = 152;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return fail(CAL_ECUDA, "gmres: device query failed");
+  int E = 8;
+  while (E > 1 && (int64_t)blocks_for(n, 256 * E) * nrhs < 4LL * n_sm) E >>= 1;
+  const dim3 gd(blocks_for(n, 256 * E), nrhs);
+  auto dot = E == 8 ? multi_dot_kernel<8> : E == 4 ? multi_dot_kernel<4> : E == 2 ? multi_dot_kernel<2> : multi_dot_kernel<1>;
+  dot<<<gd, 256, 0, st>>>(V, bV, j + 1, w, n, h1, bh);
   multi_axpy_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, h1, bh, w, n);
-  multi_dot_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, w, n, h2, bh);
+  dot<<<gd, 256, 0, st>>>(V, bV, j + 1, w, n, h2, bh);
   multi_axpy_kernel<<<g, 256, 0, st>>>(V, bV, j + 1, h2, bh, w, n);
   norm2_kernel<<<g, 256, 0, st>>>(w, n, wn2, bwn);
   prof_end(st, tok);
