@@ -131,6 +131,21 @@ def _alu_peak(n_sm, sm_max_mhz):
     return per_sm_clk * n_sm * sm_max_mhz * 1e6
 
 
+def max_over_ranks(vals):
+    """Each value's maximum over the ranks of the process group (the values
+    themselves without one). The tensor lives where the backend reduces: on
+    the rank's GPU for NCCL, on the host for gloo."""
+    import torch
+    import torch.distributed as tdist
+    vals = [float(v) for v in vals]
+    if not (tdist.is_available() and tdist.is_initialized()) or tdist.get_world_size() == 1:
+        return vals
+    dev = torch.device("cuda", torch.cuda.current_device()) if tdist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(vals, dtype=torch.float64, device=dev)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(x) for x in t.cpu()]
+
+
 def run_ours(args, rank, world):
     import torch
 
@@ -198,11 +213,7 @@ def run_ours(args, rank, world):
         L.cal_profile_read(name.encode(), ctypes.byref(n), ctypes.byref(ms), ctypes.byref(u))
         prof[name] = {"launches": n.value, "ms": ms.value, "units": u.value}
     L.cal_profile_enable(0)
-    t_dev = sum(lat) / 1e3
-    if dist:
-        tt = torch.tensor([t_dev, t_wall], dtype=torch.float64)
-        tdist.all_reduce(tt, op=tdist.ReduceOp.MAX)
-        t_dev, t_wall = float(tt[0]), float(tt[1])
+    t_dev, t_wall = max_over_ranks([sum(lat) / 1e3, t_wall])
     # e2e through host buffers: mesh arrays in, far field out, every step
     t_e2e = []
     for _ in range(max(1, min(args.steps, 3))):
