@@ -85,3 +85,22 @@ def test_lockstep_solve_equals_solo_solves(ctx):
         assert rel(Fm[q], solo) < 2e-5
     # matvec accounting covers every column
     assert info.matvecs >= 8 * 16 * 5
+
+
+def test_lockstep_solve_of_32_columns_on_the_5120_sphere(ctx):
+    """32 columns of 15,360 unknowns: the Arnoldi dot products sum two elements
+    per thread ahead of their float64 warp reduction (a single column, and the
+    small meshes above, take one); the batch must equal solo solves of its
+    first and last columns."""
+    d = meshgen.fibonacci_directions(32)
+    inc = np.concatenate([d, meshgen.perpendicular_polarisation(d)], 1)
+    m = mesh("sphere4")
+    gm = cal.Mesh(ctx, m.verts, m.tris, m.domain)
+    opts = cal.solve_opts(precond="D", precision=cal.FP32, tol=1e-7)
+    dirs = meshgen.fibonacci_directions(32)
+    multi = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc, opts=opts)
+    Fm = multi.far_field(dirs)
+    assert multi.info().converged == 1
+    for q in (0, 31):
+        solo = cal.pmchwt_solve(ctx, gm, 2.0, EPS, inc[q:q + 1], opts=opts).far_field(dirs)[0]
+        assert rel(Fm[q], solo) < 2e-5, (q, rel(Fm[q], solo))
